@@ -1,0 +1,223 @@
+"""Pins of the CPU oracle against hand-worked byte vectors, closed forms
+and brute force (no GPU).  The oracle itself is test infrastructure; these
+tests check it against things other than itself."""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import delta, hybrid, snappy, thrift
+from oracle import reader as R
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_vectors.json")))
+
+
+def hx(s):
+    return bytes.fromhex(s.replace(" ", ""))
+
+
+# ------------------------------------------------------------------ thrift
+
+def test_page_header_hand_vector_decode():
+    g = GOLD["page_header_v1"]
+    p = R.parse_page_header(hx(g["hex"]), 0, len(hx(g["hex"])))
+    v = g["value"]
+    assert (p.page_type, p.uncompressed, p.compressed) == (v["type"], v["uncompressed_page_size"], v["compressed_page_size"])
+    d = v["data_page_header"]
+    assert (p.num_values, p.encoding) == (d["num_values"], d["encoding"])
+    assert p.header_len == 19
+
+
+def test_page_header_hand_vector_encode():
+    g = GOLD["page_header_v1"]
+    enc = thrift.encode_struct([(1, thrift.I32, 0), (2, thrift.I32, 100), (3, thrift.I32, 100),
+                                (5, thrift.STRUCT, [(1, thrift.I32, 8), (2, thrift.I32, 0),
+                                                    (3, thrift.I32, 3), (4, thrift.I32, 3)])])
+    assert enc == hx(g["hex"])
+
+
+@pytest.mark.parametrize("n,zz", [(0, 0), (-1, 1), (1, 2), (-2, 3), (2, 4), (2**31 - 1, 2**32 - 2),
+                                  (-2**31, 2**32 - 1), (-2**63, 2**64 - 1)])
+def test_zigzag_closed_form(n, zz):
+    assert thrift.zigzag(n) == zz
+    assert thrift.unzigzag(zz) == n
+
+
+@pytest.mark.parametrize("n,enc", [(0, "00"), (1, "01"), (127, "7F"), (128, "80 01"), (300, "AC 02"),
+                                   (2**64 - 1, "FF FF FF FF FF FF FF FF FF 01")])
+def test_uleb128_closed_form(n, enc):
+    assert thrift.uleb128(n) == hx(enc)
+    assert thrift.read_uleb128(hx(enc), 0) == (n, len(hx(enc)))
+
+
+def test_thrift_long_field_delta_and_list_header():
+    # field id jump of 16 forces the long form: type byte then zigzag id
+    enc = thrift.encode_struct([(1, thrift.I32, 5), (17, thrift.I64, -1)])
+    assert enc == hx("15 0A 06 22 01 00")
+    d, end = thrift.decode_struct(enc)
+    assert d == {1: 5, 17: -1} and end == len(enc)
+    # list of 20 i32: header 0xF5 + ULEB size
+    enc = thrift.encode_struct([(1, thrift.LIST, (thrift.I32, list(range(20))))])
+    assert enc[:3] == hx("19 F5 14")
+    assert thrift.decode_struct(enc)[0] == {1: list(range(20))}
+
+
+def test_thrift_bool_fields_and_truncation():
+    enc = thrift.encode_struct([(1, thrift.BOOL_TRUE, True), (2, thrift.BOOL_TRUE, False)])
+    assert enc == hx("11 12 00")
+    assert thrift.decode_struct(enc)[0] == {1: True, 2: False}
+    with pytest.raises(thrift.ThriftError):
+        thrift.decode_struct(enc[:-1])
+
+
+# ------------------------------------------------------------------ hybrid
+
+def _bigint_unpack(data, bit_offset, count, width):
+    """An independent statement of LSB-first packing: the stream is one
+    little-endian integer; value i is bits [i*w, (i+1)*w) of it."""
+    big = int.from_bytes(bytes(data), "little")
+    return [(big >> (bit_offset + i * width)) & ((1 << width) - 1) for i in range(count)]
+
+
+def test_hybrid_hand_vectors():
+    g = GOLD["hybrid_bitpacked_bw3"]
+    vals, end = hybrid.decode(hx(g["hex"]), 0, 4, 3, 8)
+    assert vals.tolist() == g["values"] and end == 4
+    assert hybrid.encode(g["values"], 3, "packed") == hx(g["hex"])
+    g = GOLD["hybrid_rle_bw3"]
+    vals, _ = hybrid.decode(hx(g["hex"]), 0, 3, 3, 100)
+    assert vals.tolist() == [5] * 100
+    assert hybrid.encode([5] * 100, 3, "default") == hx(g["hex"])
+    g = GOLD["def_levels_v1"]
+    b = hx(g["hex"])
+    n = int.from_bytes(b[:4], "little")
+    vals, _ = hybrid.decode(b, 4, 4 + n, 1, 8)
+    assert vals.tolist() == g["values"]
+
+
+@pytest.mark.parametrize("width", [0, 1, 2, 3, 4])
+def test_hybrid_brute_force_small(width):
+    """Every sequence of length <= 6 over an alphabet of up to 3 symbols (or
+    the whole range for width <= 1): every writer policy decodes back."""
+    alphabet = list(range(min(3, 1 << width))) if width else [0]
+    rng = np.random.default_rng(width)
+    for n in range(0, 7):
+        for seq in itertools.product(alphabet, repeat=n):
+            for pol in ("default", "rle", "packed", "mixed"):
+                enc = hybrid.encode(seq, width, pol, rng)
+                dec, end = hybrid.decode(enc, 0, len(enc), width, n)
+                assert dec.tolist() == list(seq), (seq, pol)
+                assert end == len(enc) or n == 0
+
+
+@pytest.mark.parametrize("width", [1, 5, 7, 10, 13, 20, 31, 32, 33, 63, 64])
+def test_bitpack_against_bigint_definition(width):
+    rng = np.random.default_rng(width)
+    vals = rng.integers(0, 2**63, size=77, dtype=np.uint64) & np.uint64((1 << width) - 1 if width < 64 else 2**64 - 1)
+    if width == 64:
+        vals = vals | np.uint64(1 << 63)
+    packed = hybrid.pack_lsb(vals, width)
+    assert len(packed) == (77 * width + 7) // 8
+    for off in (0, width * 3):
+        got = hybrid.unpack_lsb(packed, off, 77 - off // width if width else 77, width)
+        assert got.tolist() == _bigint_unpack(packed, off, len(got), width)
+    assert hybrid.unpack_lsb(packed, 0, 77, width).tolist() == [int(v) for v in vals]
+
+
+def test_hybrid_padding_ignored_and_errors():
+    # 3 values bit-packed in one padded group; trailing pad is ignored
+    enc = hybrid.encode([1, 0, 1], 1, "packed")
+    assert hybrid.decode(enc, 0, len(enc), 1, 3)[0].tolist() == [1, 0, 1]
+    with pytest.raises(hybrid.HybridError):
+        hybrid.decode(hx("05 FF"), 0, 2, 1, 16)   # 2 groups announced, 1 byte present
+    with pytest.raises(ValueError):
+        hybrid.decode(hx("04"), 0, 1, 3, 2)       # repeated value missing
+    with pytest.raises(hybrid.HybridError):
+        hybrid.decode(hx("04 09"), 0, 2, 3, 2)    # repeated value wider than 3 bits
+
+
+# ------------------------------------------------------------------ delta
+
+def test_delta_hand_vectors():
+    for key in ("delta_int32_descending", "delta_single_value"):
+        g = GOLD[key]
+        b = hx(g["hex"])
+        vals, end = delta.decode(b, 0, len(b), g["bits"])
+        assert vals == g["values"] and end == len(b)
+        assert delta.encode(g["values"], g["bits"]) == b
+
+
+@pytest.mark.parametrize("bits", [32, 64])
+def test_delta_wraparound_extremes(bits):
+    lo, hi = -(1 << (bits - 1)), (1 << (bits - 1)) - 1
+    seqs = [[lo, hi, lo, hi], [hi, lo, 0, -1, hi], [0, hi, hi, lo, lo, 0], [lo] * 300, list(range(hi - 200, hi + 1))]
+    for s in seqs:
+        enc = delta.encode(s, bits)
+        assert delta.decode(enc, 0, len(enc), bits)[0] == s
+
+
+def test_delta_sorted_keys_and_random():
+    rng = np.random.default_rng(7)
+    for n in (0, 1, 2, 31, 32, 33, 127, 128, 129, 130, 1000, 4097):
+        for bits in (32, 64):
+            s = np.cumsum(rng.integers(0, 8, size=n)).tolist()
+            r = rng.integers(-(1 << (bits - 1)), (1 << (bits - 1)), size=n, dtype=np.int64).tolist()
+            for seq in (s, r):
+                enc = delta.encode(seq, bits)
+                assert delta.decode(enc, 0, len(enc), bits)[0] == seq
+
+
+def test_delta_block_structure_closed_form():
+    # 1 + 128*2 values with constant step 3: min delta 3, all packed deltas 0,
+    # so each block is zigzag(3)=1 byte + 4 zero width bytes, no bodies.
+    seq = [10 + 3 * i for i in range(257)]
+    enc = delta.encode(seq, 64)
+    assert enc == hx("80 01 04 81 02 14") + (hx("06 00 00 00 00") * 2)
+
+
+def test_delta_errors():
+    with pytest.raises(delta.DeltaError):
+        delta.decode(hx("81 01 04 02 00"), 0, 5, 32)      # block size 129
+    with pytest.raises(delta.DeltaError):
+        delta.decode(hx("80 01 04 02 00 00 21 00 00 00"), 0, 10, 32)  # width 33 on INT32
+    with pytest.raises(ValueError):
+        delta.decode(hx("80 01 04 03 00 00 01 00 00 00"), 0, 10, 32)  # body missing
+
+
+# ------------------------------------------------------------------ snappy
+
+def test_snappy_hand_vectors():
+    for key in ("snappy_copy2", "snappy_copy1"):
+        g = GOLD[key]
+        assert snappy.decompress(hx(g["hex"])) == g["text"].encode()
+
+
+def test_snappy_brute_force_short_strings():
+    for n in range(0, 9):
+        for t in itertools.product(b"ab", repeat=n):
+            s = bytes(t)
+            for enc in (snappy.compress(s), snappy.compress(s, allow_copy1=False),
+                        snappy.compress_literal_only(s)):
+                assert snappy.decompress(enc) == s
+
+
+def test_snappy_long_literals_and_far_copies():
+    rng = np.random.default_rng(3)
+    blob = rng.integers(0, 256, size=70000, dtype=np.uint8).tobytes()
+    data = blob + b"x" * 100 + blob[:5000]       # copy with offset > 65535
+    enc = snappy.compress(data)
+    assert snappy.decompress(enc) == data
+    assert any(enc[i] & 3 == 3 for i in range(len(enc)))  # some 4-byte-offset copy
+    lit = snappy.compress_literal_only(blob)
+    assert snappy.decompress(lit) == blob
+
+
+def test_snappy_errors():
+    with pytest.raises(snappy.SnappyError):
+        snappy.decompress(hx("04 01 05 00"))          # copy before any output
+    with pytest.raises(snappy.SnappyError):
+        snappy.decompress(hx("05 0C 61 62 63 64"))    # shorter than declared
+    with pytest.raises(snappy.SnappyError):
+        snappy.decompress(hx("02 0C 61 62 63 64"))    # longer than declared
