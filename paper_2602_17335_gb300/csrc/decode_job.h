@@ -1,0 +1,56 @@
+// Host <-> device job descriptors of the decode kernels.
+#pragma once
+#include <stdint.h>
+
+#include <cuda_runtime.h>
+
+#include "pq_internal.h"
+#include "snappy_job.h"
+
+namespace pqi {
+
+// K6: one dictionary page to decode.
+struct DictJob {
+  const uint8_t* body;  // dictionary page body (decompressed)
+  int32_t body_len;
+  int32_t n;            // entries (page header num_values)
+  int32_t ptype;
+  int32_t width;
+  int32_t page;         // page-table row
+  int32_t chunk;        // DictDev row
+  uint8_t* values;      // fixed width: n * width bytes (16-byte aligned)
+  uint32_t* str_pos;    // BYTE_ARRAY: n entries
+  uint32_t* str_len;    // BYTE_ARRAY: n entries
+};
+
+struct DecodeArgs {
+  const ChunkDev* chunks;
+  const PageDev* pages;
+  const DictDev* dicts;
+  PlanPage* pps;
+  Item* items;
+  const OutCol* cols;
+  DevStatus* st;
+  uint32_t* item_counter;  // persistent expansion: next item to take
+  int n_pp;
+  int n_items;
+};
+
+void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, DictDev* dicts, int n_sms,
+                 DevStatus* st, cudaStream_t s);
+void launch_walk(const DecodeArgs& a, int grid, cudaStream_t s);
+void launch_expand(const DecodeArgs& a, int grid, cudaStream_t s);
+void launch_strings(const DecodeArgs& a, const int* str_cols, int n_str_cols, int n_cols_total, int grid,
+                    cudaStream_t s);
+// Plain baseline: pages [pp_begin, pp_begin + n) decoded one page per block.
+void launch_plain_pages(const DecodeArgs& a, int pp_begin, int n, cudaStream_t s);
+void launch_prepare(const DecodeArgs& a, int n_cols, int grid, cudaStream_t s);
+int expand_blocks_per_sm();
+int walk_blocks_per_sm();
+void launch_snappy(const SnappyJob* jobs, int n_jobs, int n_sms, DevStatus* st, cudaStream_t s);
+void launch_index_walk(const ChunkDev* chunks, int n_chunks, PageDev* pages, uint32_t* counts, int mode,
+                       DevStatus* st, cudaStream_t s);
+void launch_index_oi(const ChunkDev* chunks, int n_chunks, const int64_t* chunk_file_off, PageDev* pages,
+                     int n_pages, DevStatus* st, cudaStream_t s);
+
+}  // namespace pqi

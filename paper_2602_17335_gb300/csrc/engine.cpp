@@ -1,0 +1,983 @@
+// Host engine behind the C ABI: context, page index, planner and scan.
+//
+// Index (paper Section 2 hierarchy): footers are read with one small
+// device-to-host copy per file and parsed on the host; the page headers are
+// walked on the device (K0) and the page table comes back to the host,
+// which plans with it.  Plan: the pages overlapping the request become
+// ITEM_ROWS-row work items (paper Section 3, Insight 1: parallelism finer
+// than a page), compressed pages get decompression buffers.  Scan: prepare
+// -> Snappy -> dictionaries -> page walk -> expansion -> strings, all on one
+// stream, optionally captured once into a CUDA graph and replayed.
+#include "engine.h"
+
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+
+namespace pqe {
+
+static size_t round_size(size_t n) {
+  if (n <= 4096) return 4096;
+  return (n + 65535) & ~size_t(65535);
+}
+
+void* DevPool::alloc(size_t n) {
+  n = round_size(n);
+  std::lock_guard<std::mutex> g(mu_);
+  auto it = free_.lower_bound(n);
+  if (it != free_.end() && it->first <= 2 * n) {
+    void* p = it->second;
+    size_t sz = it->first;
+    free_.erase(it);
+    used_[p] = sz;
+    return p;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    for (auto& kv : free_) cudaFree(kv.second);
+    free_.clear();
+    e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+  }
+  used_[p] = n;
+  return p;
+}
+
+void DevPool::free(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> g(mu_);
+  auto it = used_.find(p);
+  if (it == used_.end()) return;
+  free_.emplace(it->second, p);
+  used_.erase(it);
+}
+
+void DevPool::trim() {
+  std::lock_guard<std::mutex> g(mu_);
+  for (auto& kv : free_) cudaFree(kv.second);
+  free_.clear();
+}
+
+DevPool::~DevPool() {
+  for (auto& kv : free_) cudaFree(kv.second);
+  for (auto& kv : used_) cudaFree(kv.first);
+}
+
+bool Pinned::reserve(size_t n) {
+  if (n <= cap) return true;
+  if (p) cudaFreeHost(p);
+  p = nullptr;
+  cap = 0;
+  size_t c = std::max<size_t>(n, 4096);
+  if (cudaMallocHost(&p, c) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    return false;
+  }
+  cap = c;
+  return true;
+}
+
+Pinned::~Pinned() {
+  if (p) cudaFreeHost(p);
+}
+
+pq_status fail(pq_ctx* ctx, pq_status s, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return s;
+}
+
+pq_status cuda_fail(pq_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, PQ_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+pqi::DecodeArgs decode_args(pq_plan* plan) {
+  pqi::DecodeArgs a{};
+  a.chunks = plan->idx->d_chunks;
+  a.pages = plan->idx->d_pages;
+  a.dicts = plan->idx->d_dicts;
+  a.pps = plan->d_pps;
+  a.items = plan->d_items;
+  a.cols = plan->d_cols;
+  a.st = plan->d_status;
+  a.item_counter = plan->d_counter;
+  a.n_pp = static_cast<int>(plan->pps.size());
+  a.n_items = static_cast<int>(plan->items.size());
+  return a;
+}
+
+static const char* where_name(int w) {
+  switch (w) {
+    case pqi::WHERE_INDEX: return "page-header index";
+    case pqi::WHERE_SNAPPY: return "snappy";
+    case pqi::WHERE_DICT: return "dictionary";
+    case pqi::WHERE_WALK_LEVELS: return "definition levels";
+    case pqi::WHERE_WALK_VALUES: return "value stream walk";
+    case pqi::WHERE_EXPAND: return "value expansion";
+    case pqi::WHERE_STRINGS: return "strings";
+    default: return "device";
+  }
+}
+
+static pq_status status_from_device(pq_ctx* ctx, const pqi::DevStatus& st) {
+  if (!st.flags) return PQ_OK;
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s at page %d (code %d)", where_name(st.where),
+           (st.flags & pqi::DERR_TIMEOUT) ? "bounded wait ran out"
+           : (st.flags & pqi::DERR_CAPACITY) ? "output buffer too small"
+           : (st.flags & pqi::DERR_UNSUPPORTED) ? "unsupported feature"
+                                                : "corrupt data",
+           st.first_page, st.detail);
+  pq_status s = (st.flags & pqi::DERR_TIMEOUT) ? PQ_ERR_TIMEOUT
+                : (st.flags & pqi::DERR_CORRUPT) ? PQ_ERR_CORRUPT
+                : (st.flags & pqi::DERR_UNSUPPORTED) ? PQ_ERR_UNSUPPORTED
+                                                     : PQ_ERR_CAPACITY;
+  return fail(ctx, s, buf);
+}
+
+}  // namespace pqe
+
+using namespace pqe;
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+extern "C" {
+
+const char* pq_version(void) { return "pqscan-gb300 0.1 (sm_103a)"; }
+
+const char* pq_status_string(pq_status s) {
+  switch (s) {
+    case PQ_OK: return "ok";
+    case PQ_ERR_INVALID_ARG: return "invalid argument";
+    case PQ_ERR_CORRUPT: return "corrupt data";
+    case PQ_ERR_UNSUPPORTED: return "unsupported";
+    case PQ_ERR_OOM: return "out of memory";
+    case PQ_ERR_BUDGET: return "over budget";
+    case PQ_ERR_TIMEOUT: return "timeout";
+    case PQ_ERR_CUDA: return "cuda error";
+    case PQ_ERR_CAPACITY: return "capacity";
+  }
+  return "unknown";
+}
+
+pq_status pq_ctx_create(int device, pq_ctx** out) {
+  if (!out) return PQ_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return PQ_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return PQ_ERR_CUDA;
+  pq_ctx* ctx = new pq_ctx();
+  ctx->device = device;
+  cudaDeviceGetAttribute(&ctx->n_sms, cudaDevAttrMultiProcessorCount, device);
+  if (ctx->n_sms <= 0) ctx->n_sms = 1;
+  *out = ctx;
+  return PQ_OK;
+}
+
+void pq_ctx_destroy(pq_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  delete ctx;
+}
+
+const char* pq_last_error(const pq_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+// ------------------------------------------------------------------ index
+
+static void free_index_device(pq_index* idx) {
+  DevPool& pool = idx->ctx->pool;
+  pool.free(idx->d_chunks);
+  pool.free(idx->d_pages);
+  pool.free(idx->d_dicts);
+  pool.free(idx->d_chunk_file_off);
+  pool.free(idx->d_status);
+  for (auto p : idx->dict_values) pool.free(p);
+  for (auto p : idx->dict_str_pos) pool.free(p);
+  for (auto p : idx->dict_str_len) pool.free(p);
+  for (auto p : idx->dict_body) pool.free(p);
+}
+
+void pq_free_index(pq_index* idx) {
+  if (!idx) return;
+  cudaSetDevice(idx->ctx->device);
+  cudaDeviceSynchronize();
+  free_index_device(idx);
+  delete idx;
+}
+
+static bool env_flag(const char* name) {
+  const char* v = getenv(name);
+  return v && *v && strcmp(v, "0") != 0;
+}
+
+pq_status pq_index_chunks(pq_ctx* ctx, const pq_file* files, int n_files, void* stream, pq_index** out) {
+  if (!ctx || !out || (!files && n_files > 0) || n_files <= 0)
+    return fail(ctx, PQ_ERR_INVALID_ARG, "pq_index_chunks: bad arguments");
+  *out = nullptr;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  // 1. footers: one copy of each file's head magic + tail
+  const size_t kTail = 64 * 1024;
+  std::vector<size_t> toff(n_files), tlen(n_files);
+  size_t total = 0;
+  for (int f = 0; f < n_files; ++f) {
+    if (!files[f].data || files[f].size < 12)
+      return fail(ctx, PQ_ERR_CORRUPT, "file " + std::to_string(f) + " is too small for Parquet");
+    tlen[f] = static_cast<size_t>(std::min<uint64_t>(files[f].size, kTail));
+    toff[f] = total;
+    total += tlen[f] + 16;
+  }
+  if (!ctx->tail.reserve(total)) return fail(ctx, PQ_ERR_OOM, "pinned staging");
+  for (int f = 0; f < n_files; ++f) {
+    const uint8_t* base = static_cast<const uint8_t*>(files[f].data);
+    CK(cudaMemcpyAsync(ctx->tail.p + toff[f], base, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->tail.p + toff[f] + 16, base + files[f].size - tlen[f], tlen[f],
+                       cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  auto idx = std::make_unique<pq_index>();
+  idx->ctx = ctx;
+  idx->files.assign(files, files + n_files);
+  idx->metas.resize(n_files);
+  std::vector<uint8_t> big;
+  for (int f = 0; f < n_files; ++f) {
+    const uint8_t* head = ctx->tail.p + toff[f];
+    const uint8_t* tail = ctx->tail.p + toff[f] + 16;
+    const size_t tl = tlen[f];
+    if (memcmp(head, "PAR1", 4) || memcmp(tail + tl - 4, "PAR1", 4))
+      return fail(ctx, PQ_ERR_CORRUPT, "file " + std::to_string(f) + ": missing PAR1 magic");
+    uint32_t flen;
+    memcpy(&flen, tail + tl - 8, 4);
+    if (static_cast<uint64_t>(flen) + 12 > files[f].size || flen < 8)
+      return fail(ctx, PQ_ERR_CORRUPT, "file " + std::to_string(f) + ": bad footer length");
+    const uint8_t* fp;
+    if (flen + 8 <= tl) {
+      fp = tail + tl - 8 - flen;
+    } else {
+      big.resize(flen);
+      const uint8_t* base = static_cast<const uint8_t*>(files[f].data);
+      CK(cudaMemcpy(big.data(), base + files[f].size - 8 - flen, flen, cudaMemcpyDeviceToHost));
+      fp = big.data();
+    }
+    std::string err;
+    int rc = pqh::parse_file_metadata(fp, flen, &idx->metas[f], &err);
+    if (rc != pqh::META_OK)
+      return fail(ctx, rc == pqh::META_UNSUPPORTED ? PQ_ERR_UNSUPPORTED : PQ_ERR_CORRUPT,
+                  "file " + std::to_string(f) + ": " + err);
+    idx->metas[f].footer_len = flen;
+  }
+  // 2. schema
+  idx->schema = idx->metas[0].columns;
+  idx->n_columns = static_cast<int>(idx->schema.size());
+  for (int f = 1; f < n_files; ++f) {
+    const auto& c = idx->metas[f].columns;
+    bool same = c.size() == idx->schema.size();
+    for (size_t i = 0; same && i < c.size(); ++i)
+      same = c[i].name == idx->schema[i].name && c[i].type == idx->schema[i].type &&
+             c[i].repetition == idx->schema[i].repetition;
+    if (!same) return fail(ctx, PQ_ERR_INVALID_ARG, "files do not share one schema");
+  }
+  for (auto& c : idx->schema) {
+    if (c.type != pqi::T_INT32 && c.type != pqi::T_INT64 && c.type != pqi::T_DOUBLE && c.type != pqi::T_FLOAT &&
+        c.type != pqi::T_BYTE_ARRAY)
+      return fail(ctx, PQ_ERR_UNSUPPORTED, "column " + c.name + ": physical type not supported");
+  }
+  // 3. chunks
+  int64_t row = 0;
+  bool all_oi = !env_flag("PQ_NO_OFFSET_INDEX");
+  for (int f = 0; f < n_files; ++f) {
+    const auto& m = idx->metas[f];
+    const uint64_t fsize = files[f].size;
+    for (const auto& g : m.rgs) {
+      for (int c = 0; c < idx->n_columns; ++c) {
+        const auto& cm = g.chunks[c];
+        const int64_t start = cm.start();
+        if (cm.type != idx->schema[c].type)
+          return fail(ctx, PQ_ERR_CORRUPT, "chunk type differs from the schema");
+        if (cm.num_values != g.num_rows)
+          return fail(ctx, PQ_ERR_CORRUPT, "chunk value count differs from its row group (nested data?)");
+        if (cm.codec != pqi::CODEC_NONE && cm.codec != pqi::CODEC_SNAPPY)
+          return fail(ctx, PQ_ERR_UNSUPPORTED, "codec " + std::to_string(cm.codec) + " not supported");
+        if (start < 4 || cm.total_compressed < 0 ||
+            static_cast<uint64_t>(start) + static_cast<uint64_t>(cm.total_compressed) + 8 + m.footer_len > fsize)
+          return fail(ctx, PQ_ERR_CORRUPT, "chunk byte range outside the file");
+        pqi::ChunkDev cd{};
+        cd.base = static_cast<const uint8_t*>(files[f].data) + start;
+        cd.size = static_cast<uint64_t>(cm.total_compressed);
+        cd.num_values = cm.num_values;
+        cd.ptype = cm.type;
+        cd.codec = cm.codec;
+        cd.max_def = idx->schema[c].repetition == 1 ? 1 : 0;
+        cd.width = pqi::type_width(cm.type);
+        cd.dict_page = -1;
+        cd.file = f;
+        idx->chunks.push_back(cd);
+        idx->chunk_col.push_back(c);
+        idx->chunk_first_row.push_back(row);
+        idx->chunk_file_off.push_back(start);
+        idx->chunk_ba_bytes.push_back(cm.byte_array_bytes);
+        idx->stored_bytes += cd.size;
+        if (cm.oi_offset < 0 || cm.oi_length <= 0 ||
+            static_cast<uint64_t>(cm.oi_offset) + static_cast<uint64_t>(cm.oi_length) > fsize)
+          all_oi = false;
+      }
+      row += g.num_rows;
+      idx->n_row_groups++;
+    }
+  }
+  idx->num_rows = row;
+  const int nch = static_cast<int>(idx->chunks.size());
+  DevPool& pool = ctx->pool;
+  idx->d_chunks = static_cast<pqi::ChunkDev*>(pool.alloc(sizeof(pqi::ChunkDev) * std::max(nch, 1)));
+  idx->d_status = static_cast<pqi::DevStatus*>(pool.alloc(sizeof(pqi::DevStatus)));
+  idx->d_dicts = static_cast<pqi::DictDev*>(pool.alloc(sizeof(pqi::DictDev) * std::max(nch, 1)));
+  idx->d_chunk_file_off = static_cast<int64_t*>(pool.alloc(sizeof(int64_t) * std::max(nch, 1)));
+  if (!idx->d_chunks || !idx->d_status || !idx->d_dicts || !idx->d_chunk_file_off) {
+    free_index_device(idx.get());
+    return fail(ctx, PQ_ERR_OOM, "index allocation");
+  }
+  pqi::DevStatus st0{0, -1, 0, 0};
+  CK(cudaMemcpyAsync(idx->d_status, &st0, sizeof st0, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(idx->d_dicts, 0, sizeof(pqi::DictDev) * std::max(nch, 1), s));
+  CK(cudaMemcpyAsync(idx->d_chunk_file_off, idx->chunk_file_off.data(), sizeof(int64_t) * nch,
+                     cudaMemcpyHostToDevice, s));
+  int64_t n_pages = 0;
+  if (all_oi && nch > 0) {
+    // 4a. OffsetIndex: page counts from the list headers, then one thread per page
+    std::vector<uint8_t> oi;
+    int ci = 0;
+    for (int f = 0; f < n_files; ++f) {
+      for (const auto& g : idx->metas[f].rgs) {
+        for (int c = 0; c < idx->n_columns; ++c, ++ci) {
+          const auto& cm = g.chunks[c];
+          oi.resize(std::min<int32_t>(cm.oi_length, 16));
+          const uint8_t* base = static_cast<const uint8_t*>(files[f].data);
+          CK(cudaMemcpyAsync(oi.data(), base + cm.oi_offset, oi.size(), cudaMemcpyDeviceToHost, s));
+          CK(cudaStreamSynchronize(s));
+          int64_t np = 0;
+          if (pqh::offset_index_pages(oi.data(), oi.size(), &np) != pqh::META_OK || np < 0) {
+            free_index_device(idx.get());
+            return fail(ctx, PQ_ERR_CORRUPT, "malformed OffsetIndex");
+          }
+          auto& cd = idx->chunks[ci];
+          cd.oi_base = base + cm.oi_offset;
+          cd.oi_len = static_cast<uint32_t>(cm.oi_length);
+          cd.oi_pages = static_cast<uint32_t>(np);
+          cd.page_begin = static_cast<uint32_t>(n_pages);
+          cd.page_count = static_cast<uint32_t>(np + (cm.has_dict() ? 1 : 0));
+          cd.dict_page = cm.has_dict() ? static_cast<int32_t>(n_pages) : -1;
+          n_pages += cd.page_count;
+        }
+      }
+    }
+    idx->d_pages = static_cast<pqi::PageDev*>(pool.alloc(sizeof(pqi::PageDev) * std::max<int64_t>(n_pages, 1)));
+    if (!idx->d_pages) {
+      free_index_device(idx.get());
+      return fail(ctx, PQ_ERR_OOM, "page table");
+    }
+    CK(cudaMemcpyAsync(idx->d_chunks, idx->chunks.data(), sizeof(pqi::ChunkDev) * nch, cudaMemcpyHostToDevice, s));
+    pqi::launch_index_oi(idx->d_chunks, nch, idx->d_chunk_file_off, idx->d_pages, static_cast<int>(n_pages),
+                         idx->d_status, s);
+    idx->used_oi = true;
+  } else if (nch > 0) {
+    // 4b. serial header walk: count, size, fill
+    CK(cudaMemcpyAsync(idx->d_chunks, idx->chunks.data(), sizeof(pqi::ChunkDev) * nch, cudaMemcpyHostToDevice, s));
+    uint32_t* d_counts = static_cast<uint32_t*>(pool.alloc(sizeof(uint32_t) * nch));
+    if (!d_counts) {
+      free_index_device(idx.get());
+      return fail(ctx, PQ_ERR_OOM, "page counts");
+    }
+    pqi::launch_index_walk(idx->d_chunks, nch, nullptr, d_counts, 0, idx->d_status, s);
+    std::vector<uint32_t> counts(nch);
+    pqi::DevStatus st{};
+    CK(cudaMemcpyAsync(counts.data(), d_counts, sizeof(uint32_t) * nch, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&st, idx->d_status, sizeof st, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    pool.free(d_counts);
+    if (st.flags) {
+      pq_status r = status_from_device(ctx, st);
+      free_index_device(idx.get());
+      return r;
+    }
+    for (int c = 0; c < nch; ++c) {
+      idx->chunks[c].page_begin = static_cast<uint32_t>(n_pages);
+      idx->chunks[c].page_count = counts[c];
+      n_pages += counts[c];
+    }
+    idx->d_pages = static_cast<pqi::PageDev*>(pool.alloc(sizeof(pqi::PageDev) * std::max<int64_t>(n_pages, 1)));
+    if (!idx->d_pages) {
+      free_index_device(idx.get());
+      return fail(ctx, PQ_ERR_OOM, "page table");
+    }
+    CK(cudaMemcpyAsync(idx->d_chunks, idx->chunks.data(), sizeof(pqi::ChunkDev) * nch, cudaMemcpyHostToDevice, s));
+    pqi::launch_index_walk(idx->d_chunks, nch, idx->d_pages, nullptr, 1, idx->d_status, s);
+  }
+  // 5. page table back to the host
+  idx->pages.resize(n_pages);
+  pqi::DevStatus st{};
+  if (n_pages)
+    CK(cudaMemcpyAsync(idx->pages.data(), idx->d_pages, sizeof(pqi::PageDev) * n_pages, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&st, idx->d_status, sizeof st, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  if (st.flags) {
+    pq_status r = status_from_device(ctx, st);
+    free_index_device(idx.get());
+    return r;
+  }
+  // 6. host checks, dictionary buffers
+  idx->dict_values.assign(nch, nullptr);
+  idx->dict_str_pos.assign(nch, nullptr);
+  idx->dict_str_len.assign(nch, nullptr);
+  idx->dict_body.assign(nch, nullptr);
+  idx->dict_resident.assign(nch, 0);
+  for (int c = 0; c < nch; ++c) {
+    auto& cd = idx->chunks[c];
+    cd.dict_page = -1;
+    for (uint32_t k = 0; k < cd.page_count; ++k) {
+      const auto& pg = idx->pages[cd.page_begin + k];
+      if (pg.page_type == pqi::PAGE_DICT) {
+        cd.dict_page = static_cast<int32_t>(cd.page_begin + k);
+      } else {
+        idx->n_data_pages++;
+      }
+      if (cd.codec == pqi::CODEC_NONE && pg.compressed != pg.uncompressed) {
+        free_index_device(idx.get());
+        return fail(ctx, PQ_ERR_CORRUPT, "uncompressed page with differing sizes");
+      }
+      idx->uncompressed_bytes += static_cast<uint64_t>(pg.header_len) + static_cast<uint64_t>(pg.uncompressed);
+    }
+    if (cd.dict_page >= 0) {
+      const auto& dp = idx->pages[cd.dict_page];
+      if (dp.num_values < 0 || (dp.encoding != pqi::ENC_PLAIN && dp.encoding != pqi::ENC_PLAIN_DICT)) {
+        free_index_device(idx.get());
+        return fail(ctx, PQ_ERR_UNSUPPORTED, "dictionary page encoding");
+      }
+      const size_t n = static_cast<size_t>(dp.num_values);
+      if (cd.ptype == pqi::T_BYTE_ARRAY) {
+        idx->dict_str_pos[c] = static_cast<uint32_t*>(pool.alloc(4 * n + 16));
+        idx->dict_str_len[c] = static_cast<uint32_t*>(pool.alloc(4 * n + 16));
+        if (!idx->dict_str_pos[c] || !idx->dict_str_len[c]) {
+          free_index_device(idx.get());
+          return fail(ctx, PQ_ERR_OOM, "dictionary");
+        }
+      } else {
+        idx->dict_values[c] = static_cast<uint8_t*>(pool.alloc(n * cd.width + 16));
+        if (!idx->dict_values[c]) {
+          free_index_device(idx.get());
+          return fail(ctx, PQ_ERR_OOM, "dictionary");
+        }
+      }
+      if (cd.codec != pqi::CODEC_NONE) {
+        idx->dict_body[c] = static_cast<uint8_t*>(pool.alloc(static_cast<size_t>(dp.uncompressed) + 32));
+        if (!idx->dict_body[c]) {
+          free_index_device(idx.get());
+          return fail(ctx, PQ_ERR_OOM, "dictionary page buffer");
+        }
+      }
+    }
+  }
+  CK(cudaMemcpyAsync(idx->d_chunks, idx->chunks.data(), sizeof(pqi::ChunkDev) * std::max(nch, 0),
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  *out = idx.release();
+  return PQ_OK;
+}
+
+pq_status pq_index_get_info(const pq_index* idx, pq_index_info* out) {
+  if (!idx || !out) return PQ_ERR_INVALID_ARG;
+  memset(out, 0, sizeof *out);
+  out->n_files = static_cast<int32_t>(idx->files.size());
+  out->n_columns = idx->n_columns;
+  out->n_row_groups = idx->n_row_groups;
+  out->n_chunks = static_cast<int32_t>(idx->chunks.size());
+  out->n_pages = static_cast<int64_t>(idx->pages.size());
+  out->n_data_pages = idx->n_data_pages;
+  out->num_rows = idx->num_rows;
+  out->stored_bytes = idx->stored_bytes;
+  out->uncompressed_bytes = idx->uncompressed_bytes;
+  out->used_offset_index = idx->used_oi ? 1 : 0;
+  return PQ_OK;
+}
+
+pq_status pq_index_get_column(const pq_index* idx, int column, pq_column_info* out) {
+  if (!idx || !out || column < 0 || column >= idx->n_columns) return PQ_ERR_INVALID_ARG;
+  memset(out, 0, sizeof *out);
+  const auto& c = idx->schema[column];
+  strncpy(out->name, c.name.c_str(), sizeof(out->name) - 1);
+  out->type = c.type;
+  out->optional = c.repetition == 1;
+  out->type_length = pqi::type_width(c.type);
+  return PQ_OK;
+}
+
+pq_status pq_index_copy_pages(const pq_index* idx, pq_page_info* out, int64_t cap, int64_t* n_out) {
+  if (!idx || (!out && cap > 0)) return PQ_ERR_INVALID_ARG;
+  const int64_t n = static_cast<int64_t>(idx->pages.size());
+  if (n_out) *n_out = n;
+  for (int64_t i = 0; i < n && i < cap; ++i) {
+    const auto& pg = idx->pages[i];
+    const auto& cd = idx->chunks[pg.chunk];
+    pq_page_info& o = out[i];
+    o.header_offset = idx->chunk_file_off[pg.chunk] + static_cast<int64_t>(pg.offset);
+    o.file = cd.file;
+    o.chunk = static_cast<int32_t>(pg.chunk);
+    o.page_type = pg.page_type;
+    o.encoding = pg.encoding;
+    o.header_len = pg.header_len;
+    o.uncompressed_size = pg.uncompressed;
+    o.compressed_size = pg.compressed;
+    o.num_values = pg.num_values;
+    o.num_nulls = pg.num_nulls;
+    o.def_len = pg.def_len;
+    o.first_row = pg.first_row;
+  }
+  return PQ_OK;
+}
+
+// ------------------------------------------------------------------ plan
+
+static void free_plan_device(pq_plan* plan) {
+  for (void* p : plan->owned) plan->ctx->pool.free(p);
+  plan->owned.clear();
+}
+
+void pq_free_plan(pq_plan* plan) {
+  if (!plan) return;
+  cudaSetDevice(plan->ctx->device);
+  if (plan->done) {
+    cudaEventSynchronize(plan->done);
+    cudaEventDestroy(plan->done);
+  }
+  if (plan->graph) cudaGraphExecDestroy(plan->graph);
+  free_plan_device(plan);
+  delete plan;
+}
+
+static void* plan_alloc_bytes(pq_plan* plan, size_t bytes) {
+  void* p = plan->ctx->pool.alloc(std::max<size_t>(bytes, 1));
+  plan->owned.push_back(p);
+  return p;
+}
+#define plan_alloc(T, plan, count) static_cast<T*>(plan_alloc_bytes(plan, std::max<size_t>(count, 1) * sizeof(T)))
+
+pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_plan** out, pq_out_size* sizes) {
+  if (!ctx || !idx || !req || !out) return fail(ctx, PQ_ERR_INVALID_ARG, "pq_plan_scan: bad arguments");
+  *out = nullptr;
+  CK(cudaSetDevice(ctx->device));
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto plan = std::make_unique<pq_plan>();
+  plan->ctx = ctx;
+  plan->idx = idx;
+  plan->flags = req->flags;
+  if (req->columns) {
+    for (int i = 0; i < req->n_columns; ++i) {
+      if (req->columns[i] < 0 || req->columns[i] >= idx->n_columns)
+        return fail(ctx, PQ_ERR_INVALID_ARG, "column id out of range");
+      plan->cols.push_back(req->columns[i]);
+    }
+  } else {
+    for (int i = 0; i < idx->n_columns; ++i) plan->cols.push_back(i);
+  }
+  if (req->row_begin < 0 || req->row_begin > idx->num_rows)
+    return fail(ctx, PQ_ERR_INVALID_ARG, "row range outside the indexed rows");
+  const int64_t rb = req->row_begin;
+  const int64_t re = req->row_count < 0 ? idx->num_rows : rb + req->row_count;
+  if (re > idx->num_rows) return fail(ctx, PQ_ERR_INVALID_ARG, "row range outside the indexed rows");
+  plan->row_begin = rb;
+  plan->n_rows = re - rb;
+  const bool plain = (req->flags & PQ_SCAN_PLAIN) != 0;
+  const int64_t item_rows_max = pqi::ITEM_ROWS;
+  uint64_t scratch = 0;
+  std::vector<int64_t> data_job_off;  // scratch offset per data snappy job
+  std::vector<int32_t> dict_job_of_chunk(idx->chunks.size(), -1);
+  for (size_t oc = 0; oc < plan->cols.size(); ++oc) {
+    const int c = plan->cols[oc];
+    const auto& cm = idx->schema[c];
+    pqi::OutCol col{};
+    col.n_rows = plan->n_rows;
+    col.ptype = cm.type;
+    col.width = pqi::type_width(cm.type);
+    col.optional = cm.repetition == 1;
+    col.item_begin = static_cast<uint32_t>(plan->items.size());
+    pq_out_size sz{};
+    sz.n_rows = plan->n_rows;
+    sz.type = cm.type;
+    sz.optional = col.optional;
+    sz.values_bytes = cm.type == pqi::T_BYTE_ARRAY ? static_cast<uint64_t>(plan->n_rows + 1) * 8
+                                                   : static_cast<uint64_t>(plan->n_rows) * col.width;
+    sz.validity_bytes = col.optional ? static_cast<uint64_t>((plan->n_rows + 31) / 32) * 4 : 0;
+    uint64_t chars = 0;
+    for (size_t ch = 0; ch < idx->chunks.size(); ++ch) {
+      if (idx->chunk_col[ch] != c) continue;
+      const auto& cd = idx->chunks[ch];
+      const int64_t c0 = idx->chunk_first_row[ch];
+      const int64_t c1 = c0 + cd.num_values;
+      if (c1 <= rb || c0 >= re) continue;
+      if (cm.type == pqi::T_BYTE_ARRAY) {
+        if (idx->chunk_ba_bytes[ch] < 0) {
+          return fail(ctx, PQ_ERR_UNSUPPORTED,
+                      "BYTE_ARRAY chunk without size statistics (unencoded_byte_array_data_bytes)");
+        }
+        chars += static_cast<uint64_t>(idx->chunk_ba_bytes[ch]);
+      }
+      const int32_t pp_first = static_cast<int32_t>(plan->pps.size());
+      // dictionary of this chunk
+      int32_t dict = -1;
+      if (cd.dict_page >= 0) {
+        dict = static_cast<int32_t>(ch);
+        if (dict_job_of_chunk[ch] < 0) {
+          const auto& dp = idx->pages[cd.dict_page];
+          pqi::DictJob dj{};
+          const uint8_t* stored = cd.base + dp.offset + dp.header_len;
+          if (cd.codec != pqi::CODEC_NONE) {
+            pqi::SnappyJob sj{};
+            sj.src = stored;
+            sj.dst = idx->dict_body[ch];
+            sj.src_len = static_cast<uint32_t>(dp.compressed);
+            sj.dst_len = static_cast<uint32_t>(dp.uncompressed);
+            sj.page = cd.dict_page;
+            plan->snappy_dict.push_back(sj);
+            dj.body = idx->dict_body[ch];
+          } else {
+            dj.body = stored;
+          }
+          dj.body_len = dp.uncompressed;
+          dj.n = dp.num_values;
+          dj.ptype = cd.ptype;
+          dj.width = cd.width;
+          dj.page = cd.dict_page;
+          dj.chunk = static_cast<int32_t>(ch);
+          dj.values = idx->dict_values[ch];
+          dj.str_pos = idx->dict_str_pos[ch];
+          dj.str_len = idx->dict_str_len[ch];
+          if (cd.ptype != pqi::T_BYTE_ARRAY)
+            plan->max_fixed_dict_bytes =
+                std::max<int>(plan->max_fixed_dict_bytes, dp.num_values * cd.width);
+          dict_job_of_chunk[ch] = static_cast<int32_t>(plan->dict_jobs.size());
+          plan->dict_jobs.push_back(dj);
+          plan->dict_chunks.push_back(static_cast<int32_t>(ch));
+          plan->read_bytes += static_cast<uint64_t>(dp.header_len) + static_cast<uint64_t>(dp.compressed);
+        }
+      }
+      for (uint32_t k = 0; k < cd.page_count; ++k) {
+        const uint32_t pid = cd.page_begin + k;
+        const auto& pg = idx->pages[pid];
+        if (pg.page_type == pqi::PAGE_DICT) continue;
+        const int64_t p0 = c0 + pg.first_row;
+        const int64_t p1 = p0 + pg.num_values;
+        if (p1 <= rb || p0 >= re || pg.num_values == 0) continue;
+        pqi::PlanPage pp{};
+        pp.page = pid;
+        pp.chunk = static_cast<uint32_t>(ch);
+        pp.col = static_cast<int32_t>(oc);
+        pp.row_lo = static_cast<int32_t>(std::max<int64_t>(rb - p0, 0));
+        pp.row_hi = static_cast<int32_t>(std::min<int64_t>(re - p0, pg.num_values));
+        pp.out_row = p0 - rb;
+        pp.dict = dict;
+        pp.body_len = pg.uncompressed;
+        pp.nonnull = -1;
+        const uint8_t* stored = cd.base + pg.offset + pg.header_len;
+        const bool v2_raw = pg.page_type == pqi::PAGE_DATA_V2 && !pg.v2_compressed;
+        if (cd.codec != pqi::CODEC_NONE && !v2_raw) {
+          pqi::SnappyJob sj{};
+          sj.src = stored;
+          sj.src_len = static_cast<uint32_t>(pg.compressed);
+          sj.dst_len = static_cast<uint32_t>(pg.uncompressed);
+          sj.prefix = pg.page_type == pqi::PAGE_DATA_V2 ? static_cast<uint32_t>(pg.def_len + pg.rep_len) : 0u;
+          sj.page = static_cast<int32_t>(pid);
+          data_job_off.push_back(static_cast<int64_t>(scratch));
+          plan->snappy_data.push_back(sj);
+          pp.body = reinterpret_cast<const uint8_t*>(static_cast<uintptr_t>(scratch));  // rebased below
+          pp.pad = 1;  // body is a scratch offset until rebased
+          scratch += (static_cast<uint64_t>(pg.uncompressed) + 32 + 15) & ~uint64_t(15);
+        } else {
+          if (pg.compressed != pg.uncompressed)
+            return fail(ctx, PQ_ERR_CORRUPT, "stored page size differs from its uncompressed size");
+          pp.body = stored;
+        }
+        plan->read_bytes += static_cast<uint64_t>(pg.header_len) + static_cast<uint64_t>(pg.compressed);
+        pp.item_begin = static_cast<uint32_t>(plan->items.size());
+        const int64_t span = pp.row_hi - pp.row_lo;
+        const int64_t per = plain ? span : item_rows_max;
+        uint32_t n_it = 0;
+        for (int64_t r = pp.row_lo; r < pp.row_hi; r += per) {
+          pqi::Item it{};
+          it.pp = static_cast<uint32_t>(plan->pps.size());
+          it.row0 = static_cast<int32_t>(r);
+          it.nrows = static_cast<int32_t>(std::min<int64_t>(per, pp.row_hi - r));
+          it.k0 = it.row0;
+          it.nn = it.nrows;
+          plan->items.push_back(it);
+          ++n_it;
+        }
+        pp.item_count = n_it;
+        plan->pps.push_back(pp);
+      }
+      const int32_t n_pp = static_cast<int32_t>(plan->pps.size()) - pp_first;
+      if (n_pp > 0) {
+        plan->chunk_pp.emplace_back(pp_first, n_pp);
+        plan->chunk_pp_chunk.push_back(static_cast<int32_t>(ch));
+      }
+    }
+    col.item_count = static_cast<uint32_t>(plan->items.size()) - col.item_begin;
+    sz.chars_bytes = chars;
+    if (cm.type == pqi::T_BYTE_ARRAY) plan->str_cols.push_back(static_cast<int32_t>(oc));
+    plan->decoded_bytes += sz.values_bytes + sz.validity_bytes + sz.chars_bytes;
+    plan->outcols.push_back(col);
+    plan->sizes.push_back(sz);
+  }
+  // device arrays
+  const size_t npp = plan->pps.size(), nit = plan->items.size();
+  plan->d_pps = plan_alloc(pqi::PlanPage, plan.get(), npp);
+  plan->d_items = plan_alloc(pqi::Item, plan.get(), nit);
+  plan->d_cols = plan_alloc(pqi::OutCol, plan.get(), plan->outcols.size());
+  plan->d_snappy = plan_alloc(pqi::SnappyJob, plan.get(), plan->snappy_data.size() + plan->snappy_dict.size());
+  plan->d_dict_jobs = plan_alloc(pqi::DictJob, plan.get(), plan->dict_jobs.size());
+  plan->d_str_cols = plan_alloc(int32_t, plan.get(), plan->str_cols.size());
+  plan->d_counter = plan_alloc(uint32_t, plan.get(), 4);
+  plan->d_status = plan_alloc(pqi::DevStatus, plan.get(), 1);
+  plan->d_scratch = scratch ? plan_alloc(uint8_t, plan.get(), scratch + 64) : nullptr;
+  const uint64_t str_rows = static_cast<uint64_t>(plan->n_rows) * plan->str_cols.size();
+  plan->d_str_scratch = str_rows ? plan_alloc(uint32_t, plan.get(), str_rows) : nullptr;
+  plan->d_str_items = plan->str_cols.empty() ? nullptr : plan_alloc(uint64_t, plan.get(), nit);
+  for (void* p : plan->owned)
+    if (!p) {
+      free_plan_device(plan.get());
+      return fail(ctx, PQ_ERR_OOM, "plan allocation");
+    }
+  if ((scratch && !plan->d_scratch) || (str_rows && !plan->d_str_scratch)) {
+    free_plan_device(plan.get());
+    return fail(ctx, PQ_ERR_OOM, "plan scratch");
+  }
+  plan->scratch_bytes = scratch + str_rows * 4 + (plan->d_str_items ? nit * 8 : 0);
+  // rebase scratch bodies, string scratch per column
+  size_t jd = 0;
+  for (auto& pp : plan->pps) {
+    if (pp.pad == 1) {
+      uint8_t* b = plan->d_scratch + reinterpret_cast<uintptr_t>(pp.body);
+      pp.body = b;
+      plan->snappy_data[jd].dst = b;
+      ++jd;
+      pp.pad = 0;
+    }
+  }
+  for (size_t i = 0; i < plan->str_cols.size(); ++i) {
+    auto& col = plan->outcols[plan->str_cols[i]];
+    col.str_scratch = plan->d_str_scratch + static_cast<uint64_t>(plan->n_rows) * i;
+    col.str_item_bytes = plan->d_str_items;
+  }
+  // upload
+  cudaStream_t s = nullptr;
+  std::vector<pqi::SnappyJob> alljobs(plan->snappy_data);
+  alljobs.insert(alljobs.end(), plan->snappy_dict.begin(), plan->snappy_dict.end());
+  if (npp) CK(cudaMemcpyAsync(plan->d_pps, plan->pps.data(), sizeof(pqi::PlanPage) * npp, cudaMemcpyHostToDevice, s));
+  if (nit) CK(cudaMemcpyAsync(plan->d_items, plan->items.data(), sizeof(pqi::Item) * nit, cudaMemcpyHostToDevice, s));
+  if (!alljobs.empty())
+    CK(cudaMemcpyAsync(plan->d_snappy, alljobs.data(), sizeof(pqi::SnappyJob) * alljobs.size(),
+                       cudaMemcpyHostToDevice, s));
+  if (!plan->dict_jobs.empty())
+    CK(cudaMemcpyAsync(plan->d_dict_jobs, plan->dict_jobs.data(), sizeof(pqi::DictJob) * plan->dict_jobs.size(),
+                       cudaMemcpyHostToDevice, s));
+  if (!plan->str_cols.empty())
+    CK(cudaMemcpyAsync(plan->d_str_cols, plan->str_cols.data(), sizeof(int32_t) * plan->str_cols.size(),
+                       cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaEventCreateWithFlags(&plan->done, cudaEventDisableTiming));
+  const int wbps = pqi::walk_blocks_per_sm(), ebps = pqi::expand_blocks_per_sm();
+  plan->walk_grid = static_cast<int>(std::min<size_t>(std::max<size_t>(npp, 1), size_t(ctx->n_sms) * wbps));
+  plan->expand_grid = static_cast<int>(std::min<size_t>(std::max<size_t>(nit, 1), size_t(ctx->n_sms) * ebps));
+  if (!plan->h_cols.reserve(sizeof(pqi::OutCol) * std::max<size_t>(plan->outcols.size(), 1)) ||
+      !plan->h_out.reserve(sizeof(pqi::DevStatus) + 8 * std::max<size_t>(plan->outcols.size(), 1))) {
+    free_plan_device(plan.get());
+    return fail(ctx, PQ_ERR_OOM, "pinned staging");
+  }
+  if (sizes)
+    for (size_t i = 0; i < plan->sizes.size(); ++i) sizes[i] = plan->sizes[i];
+  *out = plan.release();
+  return PQ_OK;
+}
+
+pq_status pq_plan_get_info(const pq_plan* plan, pq_plan_info* out) {
+  if (!plan || !out) return PQ_ERR_INVALID_ARG;
+  memset(out, 0, sizeof *out);
+  out->n_columns = static_cast<int32_t>(plan->cols.size());
+  out->n_pages = static_cast<int32_t>(plan->pps.size());
+  out->n_dict_pages = static_cast<int32_t>(plan->dict_jobs.size());
+  out->n_items = static_cast<int32_t>(plan->items.size());
+  out->read_bytes = plan->read_bytes;
+  out->decoded_bytes = plan->decoded_bytes;
+  out->scratch_bytes = plan->scratch_bytes;
+  return PQ_OK;
+}
+
+// ------------------------------------------------------------------ scan
+
+// Enqueues the kernels of one scan (no host synchronisation).
+static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts) {
+  pq_ctx* ctx = plan->ctx;
+  pqi::DecodeArgs a = decode_args(plan);
+  const int ncols = static_cast<int>(plan->outcols.size());
+  pqi::launch_prepare(a, ncols, ctx->n_sms * 4, s);
+  const int n_data_jobs = static_cast<int>(plan->snappy_data.size());
+  const int n_dict_jobs = static_cast<int>(plan->snappy_dict.size());
+  if (plan->flags & PQ_SCAN_PLAIN) {
+    // baseline: per chunk, one launch per stage; one page per thread block
+    if (with_dicts && n_dict_jobs) pqi::launch_snappy(plan->d_snappy + n_data_jobs, n_dict_jobs, ctx->n_sms, a.st, s);
+    if (with_dicts && !plan->dict_jobs.empty())
+      pqi::launch_dict(plan->d_dict_jobs, static_cast<int>(plan->dict_jobs.size()), plan->max_fixed_dict_bytes,
+                       plan->idx->d_dicts, ctx->n_sms, a.st, s);
+    size_t job = 0;
+    for (size_t k = 0; k < plan->chunk_pp.size(); ++k) {
+      const int first = plan->chunk_pp[k].first, n = plan->chunk_pp[k].second;
+      // this chunk's compressed pages are the next jobs in order
+      int nj = 0;
+      for (int p = first; p < first + n; ++p)
+        if (job + nj < plan->snappy_data.size() && plan->snappy_data[job + nj].page == static_cast<int32_t>(plan->pps[p].page))
+          ++nj;
+      if (nj) pqi::launch_snappy(plan->d_snappy + job, nj, ctx->n_sms, a.st, s);
+      job += nj;
+      pqi::launch_plain_pages(a, first, n, s);
+    }
+  } else {
+    if (n_data_jobs + (with_dicts ? n_dict_jobs : 0))
+      pqi::launch_snappy(plan->d_snappy, n_data_jobs + (with_dicts ? n_dict_jobs : 0), ctx->n_sms, a.st, s);
+    if (with_dicts && !plan->dict_jobs.empty())
+      pqi::launch_dict(plan->d_dict_jobs, static_cast<int>(plan->dict_jobs.size()), plan->max_fixed_dict_bytes,
+                       plan->idx->d_dicts, ctx->n_sms, a.st, s);
+    pqi::launch_walk(a, plan->walk_grid, s);
+    pqi::launch_expand(a, plan->expand_grid, s);
+  }
+  if (!plan->str_cols.empty())
+    pqi::launch_strings(a, plan->d_str_cols, static_cast<int>(plan->str_cols.size()), ncols,
+                        std::min<int>(static_cast<int>(plan->items.size()), ctx->n_sms * 8), s);
+  // status and string totals back to pinned host memory
+  cudaMemcpyAsync(plan->h_out.p, plan->d_status, sizeof(pqi::DevStatus), cudaMemcpyDeviceToHost, s);
+  for (size_t i = 0; i < plan->str_cols.size(); ++i) {
+    const auto& col = plan->outcols[plan->str_cols[i]];
+    cudaMemcpyAsync(plan->h_out.p + sizeof(pqi::DevStatus) + 8 * i,
+                    reinterpret_cast<int64_t*>(col.values) + plan->n_rows, 8, cudaMemcpyDeviceToHost, s);
+  }
+}
+
+pq_status pq_scan_columns(pq_ctx* ctx, pq_plan* plan, const pq_column* outs, void* stream) {
+  if (!ctx || !plan || (!outs && !plan->outcols.empty())) return fail(ctx, PQ_ERR_INVALID_ARG, "pq_scan_columns");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // output descriptors
+  bool changed = false;
+  for (size_t i = 0; i < plan->outcols.size(); ++i) {
+    auto& col = plan->outcols[i];
+    const auto& sz = plan->sizes[i];
+    if (!outs[i].values && sz.values_bytes) return fail(ctx, PQ_ERR_INVALID_ARG, "missing values buffer");
+    if (col.optional && !outs[i].validity && sz.n_rows)
+      return fail(ctx, PQ_ERR_INVALID_ARG, "missing validity buffer for an OPTIONAL column");
+    if (col.ptype == pqi::T_BYTE_ARRAY && outs[i].chars_capacity < sz.chars_bytes)
+      return fail(ctx, PQ_ERR_CAPACITY, "chars buffer smaller than the plan's chars_bytes");
+    if (col.ptype == pqi::T_BYTE_ARRAY && !outs[i].chars && sz.chars_bytes)
+      return fail(ctx, PQ_ERR_INVALID_ARG, "missing chars buffer");
+    uint8_t* v = static_cast<uint8_t*>(outs[i].values);
+    uint32_t* m = col.optional ? outs[i].validity : nullptr;
+    uint8_t* c = static_cast<uint8_t*>(outs[i].chars);
+    changed |= v != col.values || m != col.validity || c != col.chars || outs[i].chars_capacity != col.chars_cap;
+    col.values = v;
+    col.validity = m;
+    col.chars = c;
+    col.chars_cap = outs[i].chars_capacity;
+  }
+  if (plan->graph && changed && (plan->str_cols.size() > 0)) {
+    // the graph reads string totals through baked addresses: rebuild it
+    cudaGraphExecDestroy(plan->graph);
+    plan->graph = nullptr;
+  }
+  memcpy(plan->h_cols.p, plan->outcols.data(), sizeof(pqi::OutCol) * plan->outcols.size());
+  if (!plan->outcols.empty())
+    CK(cudaMemcpyAsync(plan->d_cols, plan->h_cols.p, sizeof(pqi::OutCol) * plan->outcols.size(),
+                       cudaMemcpyHostToDevice, s));
+  // resident dictionaries: decode once, then skip the dictionary stage
+  bool with_dicts = true;
+  if (plan->flags & PQ_SCAN_RESIDENT_DICT) {
+    bool all = true;
+    for (int32_t ch : plan->dict_chunks) all = all && plan->idx->dict_resident[ch];
+    with_dicts = !all;
+  }
+  if ((plan->flags & PQ_SCAN_GRAPH) && !(plan->flags & PQ_SCAN_PLAIN)) {
+    if (plan->graph && plan->dicts_in_graph != with_dicts) {
+      cudaGraphExecDestroy(plan->graph);
+      plan->graph = nullptr;
+    }
+    if (!plan->graph) {
+      cudaStream_t cs = s;
+      bool own = false;
+      if (!cs) {
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        own = true;
+      }
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      enqueue_scan(plan, cs, with_dicts);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(cs, &g);
+      if (own) {
+        cudaStreamSynchronize(cs);
+        cudaStreamDestroy(cs);
+      }
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
+      e = cudaGraphInstantiate(&plan->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+      plan->dicts_in_graph = with_dicts;
+    }
+    CK(cudaGraphLaunch(plan->graph, s));
+  } else {
+    enqueue_scan(plan, s, with_dicts);
+  }
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(plan->done, s));
+  if (plan->flags & PQ_SCAN_RESIDENT_DICT)
+    for (int32_t ch : plan->dict_chunks) plan->idx->dict_resident[ch] = 1;
+  return PQ_OK;
+}
+
+pq_status pq_scan_wait(pq_ctx* ctx, pq_plan* plan, void* stream, uint64_t* chars_bytes) {
+  if (!ctx || !plan) return fail(ctx, PQ_ERR_INVALID_ARG, "pq_scan_wait");
+  (void)stream;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaEventSynchronize(plan->done));
+  pqi::DevStatus st;
+  memcpy(&st, plan->h_out.p, sizeof st);
+  if (chars_bytes) {
+    size_t j = 0;
+    for (size_t i = 0; i < plan->outcols.size(); ++i) {
+      if (plan->outcols[i].ptype == pqi::T_BYTE_ARRAY) {
+        int64_t v;
+        memcpy(&v, plan->h_out.p + sizeof(pqi::DevStatus) + 8 * j, 8);
+        chars_bytes[i] = static_cast<uint64_t>(v);
+        ++j;
+      } else {
+        chars_bytes[i] = 0;
+      }
+    }
+  }
+  if (st.flags && (plan->flags & PQ_SCAN_RESIDENT_DICT))
+    for (int32_t ch : plan->dict_chunks) plan->idx->dict_resident[ch] = 0;
+  return status_from_device(ctx, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Internal host-side objects behind the C ABI handles.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/pq.h"
+#include "decode_job.h"
+#include "host_meta.h"
+#include "pq_internal.h"
+#include "snappy_job.h"
+
+namespace pqe {
+
+// Caching device allocator: freed blocks go to a free list keyed by size and
+// are reused by later requests of up to the same size (within 2x), so that a
+// repeated index/plan/scan cycle makes no cudaMalloc calls after warm-up.
+class DevPool {
+ public:
+  void* alloc(size_t n);
+  void free(void* p);
+  void trim();
+  ~DevPool();
+
+ private:
+  std::mutex mu_;
+  std::multimap<size_t, void*> free_;
+  std::unordered_map<void*, size_t> used_;
+};
+
+// Growable pinned host buffer.
+struct Pinned {
+  uint8_t* p = nullptr;
+  size_t cap = 0;
+  bool reserve(size_t n);
+  ~Pinned();
+};
+
+}  // namespace pqe
+
+struct pq_ctx {
+  int device = 0;
+  int n_sms = 0;
+  std::string last_error;
+  pqe::DevPool pool;
+  pqe::Pinned tail;     // footer staging
+  std::mutex mu;        // serialises use from the serving thread and the API
+};
+
+struct pq_index {
+  pq_ctx* ctx = nullptr;
+  std::vector<pq_file> files;
+  std::vector<pqh::FileMeta> metas;
+  std::vector<pqh::ColumnMeta> schema;
+  int n_columns = 0;
+  int n_row_groups = 0;
+  int64_t num_rows = 0;
+  // chunks: file-major, row group, column
+  std::vector<pqi::ChunkDev> chunks;
+  std::vector<int32_t> chunk_col;
+  std::vector<int64_t> chunk_first_row;   // global row of the chunk's first row
+  std::vector<int64_t> chunk_file_off;    // file offset of the chunk's first byte
+  std::vector<int64_t> chunk_ba_bytes;    // SizeStatistics chars total, -1 unknown
+  std::vector<pqi::PageDev> pages;
+  pqi::ChunkDev* d_chunks = nullptr;
+  pqi::PageDev* d_pages = nullptr;
+  pqi::DictDev* d_dicts = nullptr;
+  int64_t* d_chunk_file_off = nullptr;
+  pqi::DevStatus* d_status = nullptr;
+  // dictionary buffers (index-owned), per chunk
+  std::vector<uint8_t*> dict_values;
+  std::vector<uint32_t*> dict_str_pos;
+  std::vector<uint32_t*> dict_str_len;
+  std::vector<uint8_t*> dict_body;        // decompressed dictionary page (compressed chunks)
+  std::vector<uint8_t> dict_resident;     // 1 once decoded and kept
+  uint64_t stored_bytes = 0;
+  uint64_t uncompressed_bytes = 0;
+  int64_t n_data_pages = 0;
+  bool used_oi = false;
+};
+
+struct pq_plan {
+  pq_ctx* ctx = nullptr;
+  pq_index* idx = nullptr;
+  uint32_t flags = 0;
+  std::vector<int32_t> cols;
+  int64_t row_begin = 0, n_rows = 0;
+  std::vector<pq_out_size> sizes;
+  std::vector<pqi::PlanPage> pps;
+  std::vector<pqi::Item> items;
+  std::vector<pqi::OutCol> outcols;
+  std::vector<pqi::SnappyJob> snappy_data;   // data pages
+  std::vector<pqi::SnappyJob> snappy_dict;   // dictionary pages (into index buffers)
+  std::vector<pqi::DictJob> dict_jobs;
+  std::vector<int32_t> dict_chunks;          // chunk of each dict job
+  std::vector<int32_t> str_cols;             // output columns of type BYTE_ARRAY
+  // per chunk: range of plan pages (plain baseline launches per chunk)
+  std::vector<std::pair<int32_t, int32_t>> chunk_pp;  // (first pp, count)
+  std::vector<int32_t> chunk_pp_chunk;
+  int max_fixed_dict_bytes = 0;
+  uint64_t read_bytes = 0;
+  uint64_t decoded_bytes = 0;
+  uint64_t scratch_bytes = 0;
+  // device
+  pqi::PlanPage* d_pps = nullptr;
+  pqi::Item* d_items = nullptr;
+  pqi::OutCol* d_cols = nullptr;
+  pqi::SnappyJob* d_snappy = nullptr;        // data jobs then dict jobs
+  pqi::DictJob* d_dict_jobs = nullptr;
+  int32_t* d_str_cols = nullptr;
+  uint8_t* d_scratch = nullptr;
+  uint32_t* d_str_scratch = nullptr;
+  uint64_t* d_str_items = nullptr;
+  uint32_t* d_counter = nullptr;
+  pqi::DevStatus* d_status = nullptr;
+  std::vector<void*> owned;                  // pool blocks to release
+  // host staging (pinned): output descriptors in, status + string totals out
+  pqe::Pinned h_cols;
+  pqe::Pinned h_out;
+  cudaEvent_t done = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  bool dicts_in_graph = true;
+  int walk_grid = 0, expand_grid = 0;
+};
+
+namespace pqe {
+// Shared helpers (engine.cpp)
+pq_status fail(pq_ctx* ctx, pq_status s, const std::string& msg);
+pq_status cuda_fail(pq_ctx* ctx, cudaError_t e, const char* what);
+pqi::DecodeArgs decode_args(pq_plan* plan);
+}  // namespace pqe

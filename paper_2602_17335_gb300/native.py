@@ -1,0 +1,252 @@
+"""ctypes binding of the C ABI in ``include/pq.h`` — argument marshalling only.
+
+Every function keeps its C name; structs mirror the header field by field.
+Loading fails loudly (``RuntimeError``) when the built library is missing:
+there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpqscan.so")
+
+PQ_OK, PQ_ERR_INVALID_ARG, PQ_ERR_CORRUPT, PQ_ERR_UNSUPPORTED = 0, 1, 2, 3
+PQ_ERR_OOM, PQ_ERR_BUDGET, PQ_ERR_TIMEOUT, PQ_ERR_CUDA, PQ_ERR_CAPACITY = 4, 5, 6, 7, 8
+PQ_TYPE_INT32, PQ_TYPE_INT64, PQ_TYPE_FLOAT, PQ_TYPE_DOUBLE, PQ_TYPE_BYTE_ARRAY = 1, 2, 4, 5, 6
+PQ_SCAN_BATCHED, PQ_SCAN_PLAIN, PQ_SCAN_GRAPH, PQ_SCAN_RESIDENT_DICT = 0, 1, 2, 4
+
+STATUS_NAMES = {0: "PQ_OK", 1: "PQ_ERR_INVALID_ARG", 2: "PQ_ERR_CORRUPT", 3: "PQ_ERR_UNSUPPORTED",
+                4: "PQ_ERR_OOM", 5: "PQ_ERR_BUDGET", 6: "PQ_ERR_TIMEOUT", 7: "PQ_ERR_CUDA",
+                8: "PQ_ERR_CAPACITY"}
+
+
+class pq_file(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("size", C.c_uint64)]
+
+
+class pq_index_info(C.Structure):
+    _fields_ = [("n_files", C.c_int32), ("n_columns", C.c_int32), ("n_row_groups", C.c_int32),
+                ("n_chunks", C.c_int32), ("n_pages", C.c_int64), ("n_data_pages", C.c_int64),
+                ("num_rows", C.c_int64), ("stored_bytes", C.c_uint64), ("uncompressed_bytes", C.c_uint64),
+                ("used_offset_index", C.c_int32), ("reserved", C.c_int32)]
+
+
+class pq_column_info(C.Structure):
+    _fields_ = [("name", C.c_char * 64), ("type", C.c_int32), ("optional", C.c_int32),
+                ("type_length", C.c_int32), ("reserved", C.c_int32)]
+
+
+class pq_page_info(C.Structure):
+    _fields_ = [("header_offset", C.c_int64), ("file", C.c_int32), ("chunk", C.c_int32),
+                ("page_type", C.c_int32), ("encoding", C.c_int32), ("header_len", C.c_int32),
+                ("uncompressed_size", C.c_int32), ("compressed_size", C.c_int32), ("num_values", C.c_int32),
+                ("num_nulls", C.c_int32), ("def_len", C.c_int32), ("first_row", C.c_int64)]
+
+
+class pq_request(C.Structure):
+    _fields_ = [("columns", C.POINTER(C.c_int32)), ("n_columns", C.c_int32), ("flags", C.c_uint32),
+                ("row_begin", C.c_int64), ("row_count", C.c_int64)]
+
+
+class pq_out_size(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("type", C.c_int32), ("optional", C.c_int32),
+                ("values_bytes", C.c_uint64), ("validity_bytes", C.c_uint64), ("chars_bytes", C.c_uint64)]
+
+
+class pq_plan_info(C.Structure):
+    _fields_ = [("n_columns", C.c_int32), ("n_pages", C.c_int32), ("n_dict_pages", C.c_int32),
+                ("n_items", C.c_int32), ("read_bytes", C.c_uint64), ("decoded_bytes", C.c_uint64),
+                ("scratch_bytes", C.c_uint64)]
+
+
+class pq_column(C.Structure):
+    _fields_ = [("values", C.c_void_p), ("validity", C.c_void_p), ("chars", C.c_void_p),
+                ("chars_capacity", C.c_uint64)]
+
+
+class pq_serve_config(C.Structure):
+    _fields_ = [("budget_bytes", C.c_uint64), ("slots", C.c_int32), ("timeout_ms", C.c_int32)]
+
+
+class pq_serve_request(C.Structure):
+    _fields_ = [("columns", C.POINTER(C.c_int32)), ("n_columns", C.c_int32), ("reserved", C.c_int32),
+                ("row_begin", C.c_int64), ("row_count", C.c_int64)]
+
+
+class pq_serve_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("n_columns", C.c_int32), ("columns", C.POINTER(pq_column)),
+                ("sizes", C.POINTER(pq_out_size)), ("queue_ms", C.c_double), ("latency_ms", C.c_double),
+                ("decoded_bytes", C.c_uint64)]
+
+
+class pq_write_column(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("type", C.c_int32), ("encoding", C.c_int32), ("codec", C.c_int32),
+                ("page_version", C.c_int32), ("compress_threshold", C.c_double), ("values", C.c_void_p),
+                ("chars", C.c_void_p), ("valid", C.c_void_p)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "pq_version": (C.c_char_p, []),
+    "pq_status_string": (C.c_char_p, [C.c_int]),
+    "pq_ctx_create": (C.c_int, [C.c_int, C.POINTER(_P)]),
+    "pq_ctx_destroy": (None, [_P]),
+    "pq_last_error": (C.c_char_p, [_P]),
+    "pq_index_chunks": (C.c_int, [_P, C.POINTER(pq_file), C.c_int, _P, C.POINTER(_P)]),
+    "pq_index_get_info": (C.c_int, [_P, C.POINTER(pq_index_info)]),
+    "pq_index_get_column": (C.c_int, [_P, C.c_int, C.POINTER(pq_column_info)]),
+    "pq_index_copy_pages": (C.c_int, [_P, C.POINTER(pq_page_info), C.c_int64, C.POINTER(C.c_int64)]),
+    "pq_free_index": (None, [_P]),
+    "pq_plan_scan": (C.c_int, [_P, _P, C.POINTER(pq_request), C.POINTER(_P), C.POINTER(pq_out_size)]),
+    "pq_plan_get_info": (C.c_int, [_P, C.POINTER(pq_plan_info)]),
+    "pq_free_plan": (None, [_P]),
+    "pq_scan_columns": (C.c_int, [_P, _P, C.POINTER(pq_column), _P]),
+    "pq_scan_wait": (C.c_int, [_P, _P, _P, C.POINTER(C.c_uint64)]),
+    "pq_scan_host": (C.c_int, [_P, C.POINTER(pq_file), C.c_int, C.POINTER(pq_request), C.POINTER(pq_column),
+                               C.POINTER(pq_out_size)]),
+    "pq_serve_create": (C.c_int, [_P, _P, C.POINTER(pq_serve_config), C.POINTER(_P)]),
+    "pq_serve_submit": (C.c_int, [_P, C.POINTER(pq_serve_request), C.POINTER(C.c_uint64)]),
+    "pq_serve_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(pq_serve_result), C.POINTER(C.c_int)]),
+    "pq_serve_release": (C.c_int, [_P, C.c_uint64]),
+    "pq_serve_destroy": (None, [_P]),
+    "pq_write_table": (C.c_int, [C.POINTER(pq_write_column), C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_int,
+                                 C.c_int, C.POINTER(C.POINTER(C.c_uint8)), C.POINTER(C.c_uint64)]),
+    "pq_write_free": (None, [C.POINTER(C.c_uint8)]),
+}
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded engine library (raises when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"engine library not built: {LIB_PATH} (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            try:
+                fn = getattr(L, name)
+            except AttributeError:
+                continue  # reported by missing_symbols()
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def missing_symbols():
+    """Names declared in include/pq.h that the loaded library does not export."""
+    L = lib()
+    return [n for n in _SIGS if not hasattr(L, n)]
+
+
+class PqError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status, ctx=None):
+    if status != PQ_OK:
+        msg = lib().pq_last_error(ctx).decode() if ctx else ""
+        raise PqError(status, msg)
+    return status
+
+
+# Thin wrappers with the C names (marshalling only).
+def pq_version():
+    return lib().pq_version().decode()
+
+
+def pq_ctx_create(device=0):
+    h = C.c_void_p()
+    check(lib().pq_ctx_create(device, C.byref(h)))
+    return h
+
+
+def pq_ctx_destroy(ctx):
+    lib().pq_ctx_destroy(ctx)
+
+
+def pq_last_error(ctx):
+    return lib().pq_last_error(ctx).decode()
+
+
+def pq_index_chunks(ctx, files, stream=None):
+    """files: list of (device pointer, size)."""
+    arr = (pq_file * len(files))(*[pq_file(p, n) for p, n in files])
+    h = C.c_void_p()
+    check(lib().pq_index_chunks(ctx, arr, len(files), stream, C.byref(h)), ctx)
+    return h
+
+
+def pq_index_get_info(idx):
+    info = pq_index_info()
+    check(lib().pq_index_get_info(idx, C.byref(info)))
+    return info
+
+
+def pq_index_get_column(idx, column):
+    info = pq_column_info()
+    check(lib().pq_index_get_column(idx, column, C.byref(info)))
+    return info
+
+
+def pq_index_copy_pages(idx):
+    n = C.c_int64()
+    check(lib().pq_index_copy_pages(idx, None, 0, C.byref(n)))
+    arr = (pq_page_info * max(n.value, 1))()
+    check(lib().pq_index_copy_pages(idx, arr, n.value, C.byref(n)))
+    return arr[:n.value]
+
+
+def pq_free_index(idx):
+    lib().pq_free_index(idx)
+
+
+def pq_plan_scan(ctx, idx, columns=None, row_begin=0, row_count=-1, flags=PQ_SCAN_BATCHED):
+    """Returns (plan handle, list of pq_out_size)."""
+    req = pq_request()
+    ncols = pq_index_get_info(idx).n_columns if columns is None else len(columns)
+    keep = None
+    if columns is not None:
+        keep = (C.c_int32 * max(len(columns), 1))(*columns)
+        req.columns = C.cast(keep, C.POINTER(C.c_int32))
+        req.n_columns = len(columns)
+    req.flags = flags
+    req.row_begin = row_begin
+    req.row_count = row_count
+    sizes = (pq_out_size * max(ncols, 1))()
+    h = C.c_void_p()
+    check(lib().pq_plan_scan(ctx, idx, C.byref(req), C.byref(h), sizes), ctx)
+    return h, list(sizes[:ncols])
+
+
+def pq_plan_get_info(plan):
+    info = pq_plan_info()
+    check(lib().pq_plan_get_info(plan, C.byref(info)))
+    return info
+
+
+def pq_free_plan(plan):
+    lib().pq_free_plan(plan)
+
+
+def pq_scan_columns(ctx, plan, outs, stream=None):
+    """outs: list of pq_column (device pointers)."""
+    arr = (pq_column * max(len(outs), 1))(*outs)
+    return check(lib().pq_scan_columns(ctx, plan, arr, stream), ctx)
+
+
+def pq_scan_wait(ctx, plan, ncols, stream=None):
+    """Returns (status, chars bytes per column); does not raise."""
+    chars = (C.c_uint64 * max(ncols, 1))()
+    st = lib().pq_scan_wait(ctx, plan, stream, chars)
+    return st, list(chars[:ncols])

@@ -1,0 +1,192 @@
+"""GPU scan vs CPU oracle, bit for bit, through the C ABI.
+
+Inputs are files the oracle writer produced from seeded synthetic tables
+shaped like the scan workloads (eight-column table, single dictionary
+column); sizes span several 8192-row work items and 2048-row tiles with
+ragged tails.  Expected values always come from the oracle reader."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import reader as R
+from oracle import writer as W
+
+from gpu_util import assert_columns_equal, engine, slice_result, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SMALL = dict(string_pool_size=700, zipf_k=2000)
+
+
+@pytest.fixture(scope="module")
+def eng():
+    e = engine()
+    yield e
+    e.close()
+
+
+def _roundtrip(eng, data, **kw):
+    from paper_2602_17335_gb300 import native as N
+    expect = R.read_file(data)
+    outs = eng.read([to_dev(data)], **kw)
+    cols = kw.get("columns")
+    rb = kw.get("row_begin", 0)
+    rc = kw.get("row_count", -1)
+    rows = len(expect[0].values) if expect[0].values is not None else len(expect[0].offsets) - 1
+    hi = rows if rc < 0 else rb + rc
+    exp = [slice_result(expect[c], rb, hi) for c in (cols if cols is not None else range(len(expect)))]
+    assert_columns_equal(outs, exp)
+    return N
+
+
+@pytest.mark.parametrize("rg_rows,page_bytes", [(16384, 2048), (25000, 64 * 1024), (40000, 1 << 20),
+                                                (7000, 700)])
+@pytest.mark.parametrize("codec,version", [("UNCOMPRESSED", 1), ("UNCOMPRESSED", 2), ("SNAPPY", 1),
+                                           ("SNAPPY", 2)])
+def test_eight_column_table(eng, rg_rows, page_bytes, codec, version):
+    tab = synth.config2_table(40_000, rg_rows, **SMALL)
+    data = W.write_file(tab, synth.config2_spec(rg_rows, page_bytes, codec, version))
+    _roundtrip(eng, data)
+
+
+@pytest.mark.parametrize("policy", ["rle", "packed", "mixed"])
+def test_hybrid_writer_policies(eng, policy):
+    tab = synth.config2_table(30_000, 30_000, **SMALL)
+    spec = synth.config2_spec(30_000, 4096)
+    spec.seed = 5
+    for c in spec.columns:
+        c.hybrid_policy = policy
+    _roundtrip(eng, W.write_file(tab, spec))
+
+
+def test_single_dictionary_column(eng):
+    n = 1 << 18
+    tab = synth.config1_table(n)
+    _roundtrip(eng, W.write_file(tab, synth.config1_spec(1 << 20, n)))
+
+
+@pytest.mark.parametrize("rb,rc,cols", [(0, 1, None), (8191, 2, [0, 4, 5]), (12345, 20000, [1, 2, 3]),
+                                        (39999, 1, [4, 5, 6, 7]), (5000, 0, [0]), (0, -1, [7, 5]),
+                                        (16383, 8194, None)])
+def test_row_ranges_and_column_subsets(eng, rb, rc, cols):
+    tab = synth.config2_table(40_000, 16384, **SMALL)
+    data = W.write_file(tab, synth.config2_spec(16384, 8192, "SNAPPY", 1))
+    _roundtrip(eng, data, columns=cols, row_begin=rb, row_count=rc)
+
+
+@pytest.mark.parametrize("mode", ["plain", "graph", "resident"])
+def test_scan_modes(eng, mode):
+    from paper_2602_17335_gb300 import native as N
+    from paper_2602_17335_gb300.scan import alloc_outputs
+    tab = synth.config2_table(30_000, 12_000, **SMALL)
+    data = W.write_file(tab, synth.config2_spec(12_000, 16 * 1024, "SNAPPY", 2))
+    expect = R.read_file(data)
+    flags = {"plain": N.PQ_SCAN_PLAIN, "graph": N.PQ_SCAN_GRAPH,
+             "resident": N.PQ_SCAN_RESIDENT_DICT | N.PQ_SCAN_GRAPH}[mode]
+    dev = to_dev(data)
+    idx = eng.index([dev])
+    plan, sizes = eng.plan(idx, flags=flags)
+    for rep in range(3):  # replays reuse the plan (and the captured graph)
+        outs = alloc_outputs(sizes)
+        eng.scan(plan, outs)
+        st, chars = eng.wait(plan, len(outs))
+        assert st == N.PQ_OK, N.pq_last_error(eng.ctx)
+        for o, c in zip(outs, chars):
+            if o.chars is not None:
+                o.chars = o.chars[:c]
+        assert_columns_equal(outs, expect)
+    N.pq_free_plan(plan)
+    N.pq_free_index(idx)
+
+
+def test_page_table_matches_oracle_walk(eng):
+    from paper_2602_17335_gb300 import native as N
+    tab = synth.config2_table(20_000, 8000, **SMALL)
+    for oi in (True, False):
+        spec = synth.config2_spec(8000, 3000, "SNAPPY", 2, offset_index=oi)
+        data = W.write_file(tab, spec)
+        info = R.parse_footer(data)
+        idx = eng.index([to_dev(data)])
+        pages = N.pq_index_copy_pages(idx)
+        ii = N.pq_index_get_info(idx)
+        assert ii.used_offset_index == (1 if oi else 0)
+        exp = []
+        for ci, ch in enumerate(info.chunks):
+            row = 0
+            for p in R.chunk_pages(data, ch):
+                first = 0 if p.page_type == 2 else row
+                if p.page_type != 2:
+                    row += p.num_values
+                exp.append((p.offset, ci, p.page_type, p.encoding, p.header_len, p.uncompressed,
+                            p.compressed, p.num_values, p.num_nulls, p.def_len, first))
+        got = [(g.header_offset, g.chunk, g.page_type, g.encoding, g.header_len, g.uncompressed_size,
+                g.compressed_size, g.num_values, g.num_nulls, g.def_len, g.first_row) for g in pages]
+        assert got == exp
+        assert ii.num_rows == 20_000 and ii.n_chunks == len(info.chunks)
+        N.pq_free_index(idx)
+
+
+def test_multiple_files(eng):
+    from oracle.reader import ColumnResult
+    datas, expects = [], []
+    for f in range(3):
+        tab = synth.config2_table(9000 + 1000 * f, 4096, file=f, **SMALL)
+        d = W.write_file(tab, synth.config2_spec(4096, 4096, "SNAPPY" if f % 2 else "UNCOMPRESSED", 1 + f % 2))
+        datas.append(d)
+        expects.append(R.read_file(d))
+    outs = eng.read([to_dev(d) for d in datas])
+    merged = []
+    for c in range(8):
+        parts = [e[c] for e in expects]
+        valid = None if parts[0].valid is None else np.concatenate([p.valid for p in parts])
+        if parts[0].ptype == "BYTE_ARRAY":
+            offs = [parts[0].offsets]
+            base = parts[0].offsets[-1]
+            for p in parts[1:]:
+                offs.append(p.offsets[1:] + base)
+                base += p.offsets[-1]
+            merged.append(ColumnResult(parts[0].name, "BYTE_ARRAY", None, valid, np.concatenate(offs),
+                                       np.concatenate([p.chars for p in parts])))
+        else:
+            merged.append(ColumnResult(parts[0].name, parts[0].ptype, np.concatenate([p.values for p in parts]), valid))
+    assert_columns_equal(outs, merged)
+
+
+def test_edge_cases(eng):
+    """All-null and all-valid OPTIONAL pages, a one-entry dictionary (bit
+    width 0), DELTA with full-width random deltas and wrap-around extremes,
+    one-row and single-page chunks."""
+    n = 20_000
+    rng = np.random.default_rng(1)
+    i64 = np.iinfo(np.int64)
+    i32 = np.iinfo(np.int32)
+    cols = [
+        synth.ColumnData("allnull", "INT64", np.zeros(n, np.int64), np.zeros(n, bool)),
+        synth.ColumnData("allvalid", "INT32", rng.integers(-5, 5, n).astype(np.int32), np.ones(n, bool)),
+        synth.ColumnData("onedict", "INT64", np.full(n, 77, np.int64)),
+        synth.ColumnData("delta_rand64", "INT64", rng.integers(i64.min, i64.max, n, dtype=np.int64, endpoint=True)),
+        synth.ColumnData("delta_rand32", "INT32", rng.integers(i32.min, i32.max, n, dtype=np.int64).astype(np.int32)),
+        synth.ColumnData("delta_wrap", "INT64", np.tile(np.array([i64.min, i64.max, 0, -1], np.int64), n // 4)),
+        synth.ColumnData("opt_dict", "DOUBLE", np.where(rng.random(n) < 0.5, rng.integers(0, 3, n) * 1.5, 0.0),
+                         None),
+        synth.ColumnData("opt_delta", "INT32", np.cumsum(rng.integers(0, 3, n)).astype(np.int32),
+                         rng.random(n) > 0.3),
+    ]
+    cols[7].values[~cols[7].valid] = 0
+    encs = ["PLAIN", "RLE_DICTIONARY", "RLE_DICTIONARY", "DELTA_BINARY_PACKED", "DELTA_BINARY_PACKED",
+            "DELTA_BINARY_PACKED", "RLE_DICTIONARY", "DELTA_BINARY_PACKED"]
+    tab = synth.Table(cols)
+    for rg, page in ((n, 1 << 20), (5000, 1500), (1, 64)):
+        spec = synth.TableSpec(rg, page, [synth.ColumnSpec(e) for e in encs])
+        nt = synth.Table([synth.slice_column(c, 0, n if rg > 1 else 40) for c in cols])
+        _roundtrip(eng, W.write_file(nt if rg == 1 else tab, spec))
+
+
+def test_config4_style_mixed_chunks(eng):
+    draws = synth.config4_draws(n_files=3, chunks_per_file=4, rows_lo=500, rows_hi=40_000, page_lo=512,
+                                page_hi=64 * 1024)
+    for d in draws:
+        col, cspec = synth.config4_column(d)
+        data = W.write_file(synth.Table([col]), synth.TableSpec(rg_rows=15_000, page_bytes=d.page_bytes,
+                                                                columns=[cspec]))
+        _roundtrip(eng, data)
