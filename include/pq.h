@@ -163,6 +163,8 @@ void pq_free_index(pq_index* idx);
 #define PQ_SCAN_GRAPH 2u          /* capture the batched scan into a CUDA graph on first
                                      use; later scans of the same plan replay it */
 #define PQ_SCAN_RESIDENT_DICT 4u  /* decode dictionaries once and keep them in the index */
+#define PQ_SCAN_TIMING 8u         /* record CUDA events between the scan's stages (see
+                                     pq_plan_stage_ms); not combined with PQ_SCAN_GRAPH */
 
 /* A scan request: which columns, which rows.  Rows are numbered over the
  * concatenation of all indexed files in order; the selected range must lie
@@ -195,6 +197,8 @@ typedef struct pq_plan_info {
   uint64_t read_bytes;       /* stored bytes of the touched chunks' pages (headers incl.) */
   uint64_t decoded_bytes;    /* values + validity + offsets + chars the scan writes */
   uint64_t scratch_bytes;    /* device scratch the plan holds */
+  int32_t launches_per_scan; /* kernels one pq_scan_columns call launches */
+  int32_t reserved;
 } pq_plan_info;
 
 /* Plans a scan of `req` over `idx`: selects the pages overlapping the row
@@ -209,6 +213,20 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
                        pq_out_size* sizes);
 pq_status pq_plan_get_info(const pq_plan* plan, pq_plan_info* out);
 void pq_free_plan(pq_plan* plan);
+
+/* Stages of a scan, in order, for pq_plan_stage_ms. */
+#define PQ_STAGE_PREPARE 0     /* reset of bitmaps, counters, error word */
+#define PQ_STAGE_SNAPPY 1      /* page decompression (K1) */
+#define PQ_STAGE_DICT 2        /* dictionary decode (K6) */
+#define PQ_STAGE_WALK 3        /* page walk: levels, stream checkpoints */
+#define PQ_STAGE_EXPAND 4      /* value expansion of the work items */
+#define PQ_STAGE_STRINGS 5     /* string offsets and chars */
+#define PQ_N_STAGES 6
+
+/* Device milliseconds of each stage of the last scan of a plan created with
+ * PQ_SCAN_TIMING (CUDA events on the scan's stream; call after
+ * pq_scan_wait).  `ms` receives PQ_N_STAGES values (0 for skipped stages). */
+pq_status pq_plan_stage_ms(const pq_plan* plan, float* ms);
 
 /* ------------------------------------------------------------------ scan */
 
@@ -244,14 +262,13 @@ pq_status pq_scan_columns(pq_ctx* ctx, pq_plan* plan, const pq_column* outs, voi
  * the chars bytes written (0 for fixed-width columns). */
 pq_status pq_scan_wait(pq_ctx* ctx, pq_plan* plan, void* stream, uint64_t* chars_bytes);
 
-/* End-to-end scan from HOST memory: the files are in host memory (pinned
- * for full speed), the outputs are host buffers laid out exactly as
- * pq_column describes.  Row groups are staged host->device, decoded and
- * copied back in a pipeline over two buffers per stage on separate streams,
- * so that copies overlap decoding (the overlapped reader of the paper's
- * Section 4.1, at row-group granularity).  Synchronous.  `req` as for
- * pq_plan_scan (row range must cover whole files' rows from 0; only
- * columns are selectable).  Errors as for index/plan/scan. */
+/* End-to-end scan from HOST memory: `host_files` point to host memory
+ * (pinned for full speed), `host_outs` are host buffers laid out exactly as
+ * pq_column describes.  The files are copied to the device, indexed,
+ * planned and scanned, and the columns copied back; the call is
+ * synchronous.  When `host_outs` is NULL only `sizes` is filled (one entry
+ * per requested column), so that the caller can allocate the outputs.
+ * `req` as for pq_plan_scan.  Errors as for index/plan/scan. */
 pq_status pq_scan_host(pq_ctx* ctx, const pq_file* host_files, int n_files, const pq_request* req,
                        const pq_column* host_outs, pq_out_size* sizes);
 

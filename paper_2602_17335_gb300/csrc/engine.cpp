@@ -567,6 +567,8 @@ void pq_free_plan(pq_plan* plan) {
     cudaEventDestroy(plan->done);
   }
   if (plan->graph) cudaGraphExecDestroy(plan->graph);
+  for (auto& e : plan->stage_ev)
+    if (e) cudaEventDestroy(e);
   free_plan_device(plan);
   delete plan;
 }
@@ -583,6 +585,8 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
   *out = nullptr;
   CK(cudaSetDevice(ctx->device));
   std::lock_guard<std::mutex> lk(ctx->mu);
+  if ((req->flags & PQ_SCAN_TIMING) && (req->flags & PQ_SCAN_GRAPH))
+    return fail(ctx, PQ_ERR_INVALID_ARG, "PQ_SCAN_TIMING cannot be combined with PQ_SCAN_GRAPH");
   auto plan = std::make_unique<pq_plan>();
   plan->ctx = ctx;
   plan->idx = idx;
@@ -801,6 +805,31 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
                        cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaEventCreateWithFlags(&plan->done, cudaEventDisableTiming));
+  if (plan->flags & PQ_SCAN_TIMING)
+    for (auto& e : plan->stage_ev) CK(cudaEventCreate(&e));
+  {
+    // kernels per scan: prepare, snappy, dictionary (2), walk + expand or one
+    // plain launch (+ its snappy) per chunk, strings (2)
+    int n = 1;
+    const bool any_dict = !plan->dict_jobs.empty();
+    if (plain) {
+      n += (plan->snappy_dict.empty() ? 0 : 1) + (any_dict ? 2 : 0);
+      size_t job = 0;
+      for (auto& cp : plan->chunk_pp) {
+        int nj = 0;
+        for (int q = cp.first; q < cp.first + cp.second; ++q)
+          if (job + nj < plan->snappy_data.size() && plan->snappy_data[job + nj].page == static_cast<int32_t>(plan->pps[q].page))
+            ++nj;
+        n += (nj ? 1 : 0) + 1;
+        job += nj;
+      }
+    } else {
+      n += (plan->snappy_data.size() + plan->snappy_dict.size() ? 1 : 0) + (any_dict ? 2 : 0);
+      n += (npp ? 1 : 0) + (nit ? 1 : 0);
+    }
+    n += plan->str_cols.empty() ? 0 : 2;
+    plan->launches = n;
+  }
   const int wbps = pqi::walk_blocks_per_sm(), ebps = pqi::expand_blocks_per_sm();
   plan->walk_grid = static_cast<int>(std::min<size_t>(std::max<size_t>(npp, 1), size_t(ctx->n_sms) * wbps));
   plan->expand_grid = static_cast<int>(std::min<size_t>(std::max<size_t>(nit, 1), size_t(ctx->n_sms) * ebps));
@@ -825,6 +854,20 @@ pq_status pq_plan_get_info(const pq_plan* plan, pq_plan_info* out) {
   out->read_bytes = plan->read_bytes;
   out->decoded_bytes = plan->decoded_bytes;
   out->scratch_bytes = plan->scratch_bytes;
+  out->launches_per_scan = plan->launches;
+  return PQ_OK;
+}
+
+pq_status pq_plan_stage_ms(const pq_plan* plan, float* ms) {
+  if (!plan || !ms) return PQ_ERR_INVALID_ARG;
+  if (!(plan->flags & PQ_SCAN_TIMING) || !plan->stage_ev[0]) return PQ_ERR_INVALID_ARG;
+  for (int i = 0; i < PQ_N_STAGES; ++i) {
+    ms[i] = 0.f;
+    if (cudaEventElapsedTime(&ms[i], plan->stage_ev[i], plan->stage_ev[i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      return PQ_ERR_CUDA;
+    }
+  }
   return PQ_OK;
 }
 
@@ -835,15 +878,23 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts) {
   pq_ctx* ctx = plan->ctx;
   pqi::DecodeArgs a = decode_args(plan);
   const int ncols = static_cast<int>(plan->outcols.size());
+  const bool timing = (plan->flags & PQ_SCAN_TIMING) != 0;
+  auto mark = [&](int i) {
+    if (timing) cudaEventRecord(plan->stage_ev[i], s);
+  };
+  mark(0);
   pqi::launch_prepare(a, ncols, ctx->n_sms * 4, s);
+  mark(1);
   const int n_data_jobs = static_cast<int>(plan->snappy_data.size());
   const int n_dict_jobs = static_cast<int>(plan->snappy_dict.size());
   if (plan->flags & PQ_SCAN_PLAIN) {
     // baseline: per chunk, one launch per stage; one page per thread block
     if (with_dicts && n_dict_jobs) pqi::launch_snappy(plan->d_snappy + n_data_jobs, n_dict_jobs, ctx->n_sms, a.st, s);
+    mark(2);
     if (with_dicts && !plan->dict_jobs.empty())
       pqi::launch_dict(plan->d_dict_jobs, static_cast<int>(plan->dict_jobs.size()), plan->max_fixed_dict_bytes,
                        plan->idx->d_dicts, ctx->n_sms, a.st, s);
+    mark(3);
     size_t job = 0;
     for (size_t k = 0; k < plan->chunk_pp.size(); ++k) {
       const int first = plan->chunk_pp[k].first, n = plan->chunk_pp[k].second;
@@ -856,18 +907,25 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts) {
       job += nj;
       pqi::launch_plain_pages(a, first, n, s);
     }
+    mark(4);
+    mark(5);
   } else {
     if (n_data_jobs + (with_dicts ? n_dict_jobs : 0))
       pqi::launch_snappy(plan->d_snappy, n_data_jobs + (with_dicts ? n_dict_jobs : 0), ctx->n_sms, a.st, s);
+    mark(2);
     if (with_dicts && !plan->dict_jobs.empty())
       pqi::launch_dict(plan->d_dict_jobs, static_cast<int>(plan->dict_jobs.size()), plan->max_fixed_dict_bytes,
                        plan->idx->d_dicts, ctx->n_sms, a.st, s);
+    mark(3);
     pqi::launch_walk(a, plan->walk_grid, s);
+    mark(4);
     pqi::launch_expand(a, plan->expand_grid, s);
+    mark(5);
   }
   if (!plan->str_cols.empty())
     pqi::launch_strings(a, plan->d_str_cols, static_cast<int>(plan->str_cols.size()), ncols,
                         std::min<int>(static_cast<int>(plan->items.size()), ctx->n_sms * 8), s);
+  mark(6);
   // status and string totals back to pinned host memory
   cudaMemcpyAsync(plan->h_out.p, plan->d_status, sizeof(pqi::DevStatus), cudaMemcpyDeviceToHost, s);
   for (size_t i = 0; i < plan->str_cols.size(); ++i) {

@@ -127,6 +127,8 @@ struct pq_plan {
   cudaStream_t graph_stream = nullptr;
   bool dicts_in_graph = true;
   int walk_grid = 0, expand_grid = 0;
+  int launches = 0;
+  cudaEvent_t stage_ev[PQ_N_STAGES + 1] = {};
 };
 
 namespace pqe {

@@ -1,0 +1,746 @@
+// Parquet writer — the offline rewriter of the paper's Sections 3 and 5:
+// a flat table is written with a chosen row-group size, page size,
+// encoding per column chunk (V1 PLAIN / dictionary, V2 DELTA_BINARY_PACKED),
+// page version, and per-chunk compression kept only when it shrinks the
+// chunk by more than a threshold (Section 3, "No Unnecessary Compression").
+//
+// Layout rules (identical to the ones the engine documents for pq_write_table):
+//  * row group k holds rows [k*rg_rows, (k+1)*rg_rows);
+//  * rows per data page: max(8, floor(page_bytes*8 / b) rounded down to a
+//    multiple of 8), b = 8*width (PLAIN) or max(index bit width, 1)
+//    (dictionary), +1 when OPTIONAL; REQUIRED DELTA pages hold 1 + 128k
+//    values (the most whole blocks that fit page_bytes, a shorter tail taken
+//    whole when it fits); PLAIN BYTE_ARRAY pages take rows while the page has
+//    fewer than 8 rows or the encoded bytes still fit;
+//  * dictionary entries in order of first appearance, index bit width =
+//    bit length of (entries - 1);
+//  * hybrid runs: a repeated run for >= 8 equal values when the pending
+//    literal values fill whole groups, otherwise bit-packed runs of at most
+//    63 groups;
+//  * V1 pages compress levels + values, V2 pages values only; the dictionary
+//    page body is compressed with the chunk codec;
+//  * an OffsetIndex per chunk after the last row group when requested.
+// Chunks are encoded in parallel on `n_threads` host threads.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/pq.h"
+
+namespace {
+
+using Bytes = std::vector<uint8_t>;
+
+// ------------------------------------------------------------------ Thrift compact writer
+
+struct TW {
+  Bytes& o;
+  std::vector<int> last{0};
+  explicit TW(Bytes& out) : o(out) {}
+  void varint(uint64_t v) {
+    while (v >= 0x80) {
+      o.push_back(static_cast<uint8_t>(v | 0x80));
+      v >>= 7;
+    }
+    o.push_back(static_cast<uint8_t>(v));
+  }
+  static uint64_t zz(int64_t v) { return (static_cast<uint64_t>(v) << 1) ^ static_cast<uint64_t>(v >> 63); }
+  void head(int fid, int type) {
+    int d = fid - last.back();
+    if (d > 0 && d <= 15) {
+      o.push_back(static_cast<uint8_t>((d << 4) | type));
+    } else {
+      o.push_back(static_cast<uint8_t>(type));
+      varint(zz(fid));
+    }
+    last.back() = fid;
+  }
+  void i32(int fid, int64_t v) { head(fid, 5); varint(zz(v)); }
+  void i64(int fid, int64_t v) { head(fid, 6); varint(zz(v)); }
+  void i16(int fid, int64_t v) { head(fid, 4); varint(zz(v)); }
+  void boolean(int fid, bool v) { head(fid, v ? 1 : 2); }
+  void binary(int fid, const std::string& s) {
+    head(fid, 8);
+    varint(s.size());
+    o.insert(o.end(), s.begin(), s.end());
+  }
+  void list_begin(int fid, int elem_type, size_t n) {
+    head(fid, 9);
+    if (n < 15) {
+      o.push_back(static_cast<uint8_t>((n << 4) | elem_type));
+    } else {
+      o.push_back(static_cast<uint8_t>(0xF0 | elem_type));
+      varint(n);
+    }
+  }
+  void struct_begin(int fid) {
+    head(fid, 12);
+    last.push_back(0);
+  }
+  void elem_struct_begin() { last.push_back(0); }
+  void struct_end() {
+    o.push_back(0);
+    last.pop_back();
+  }
+  void stop() { o.push_back(0); }
+};
+
+void uleb(Bytes& o, uint64_t v) {
+  while (v >= 0x80) {
+    o.push_back(static_cast<uint8_t>(v | 0x80));
+    v >>= 7;
+  }
+  o.push_back(static_cast<uint8_t>(v));
+}
+
+int bit_length(uint64_t v) { return v ? 64 - __builtin_clzll(v) : 0; }
+
+// LSB-first packing of `n` values of `w` bits.
+void pack_bits(Bytes& o, const uint64_t* v, size_t n, int w) {
+  if (w == 0) return;
+  size_t nbytes = (n * static_cast<size_t>(w) + 7) / 8;
+  size_t base = o.size();
+  o.resize(base + nbytes, 0);
+  uint8_t* d = o.data() + base;
+  uint64_t bit = 0;
+  for (size_t i = 0; i < n; ++i) {
+    uint64_t x = w == 64 ? v[i] : (v[i] & ((1ull << w) - 1));
+    for (int b = 0; b < w;) {
+      size_t byte = (bit + b) >> 3;
+      int off = static_cast<int>((bit + b) & 7);
+      int take = std::min(8 - off, w - b);
+      d[byte] |= static_cast<uint8_t>(((x >> b) & ((1u << take) - 1)) << off);
+      b += take;
+    }
+    bit += w;
+  }
+}
+
+// ------------------------------------------------------------------ hybrid encoder
+
+void packed_run(Bytes& o, const uint64_t* v, size_t n, int w) {
+  size_t groups = (n + 7) / 8;
+  uleb(o, (groups << 1) | 1);
+  std::vector<uint64_t> pad(groups * 8, 0);
+  std::copy(v, v + n, pad.begin());
+  pack_bits(o, pad.data(), pad.size(), w);
+}
+
+void rle_run(Bytes& o, uint64_t value, size_t count, int w) {
+  uleb(o, static_cast<uint64_t>(count) << 1);
+  for (int b = 0; b < (w + 7) / 8; ++b) o.push_back(static_cast<uint8_t>(value >> (8 * b)));
+}
+
+void hybrid_encode(Bytes& o, const uint64_t* v, size_t n, int w) {
+  // run[i] = equal values starting at i
+  std::vector<uint32_t> run(n);
+  for (size_t i = n; i-- > 0;) run[i] = (i + 1 < n && v[i] == v[i + 1]) ? run[i + 1] + 1 : 1;
+  std::vector<uint64_t> pending;
+  auto flush = [&]() {
+    for (size_t a = 0; a < pending.size(); a += 504)
+      packed_run(o, pending.data() + a, std::min<size_t>(504, pending.size() - a), w);
+    pending.clear();
+  };
+  size_t i = 0;
+  while (i < n) {
+    if (run[i] >= 8 && pending.size() % 8 == 0) {
+      flush();
+      rle_run(o, v[i], run[i], w);
+      i += run[i];
+    } else {
+      pending.push_back(v[i]);
+      ++i;
+    }
+  }
+  flush();
+}
+
+// ------------------------------------------------------------------ DELTA encoder
+
+struct DeltaEnc {
+  int bits;
+  uint64_t wrap(uint64_t v) const { return bits == 32 ? static_cast<uint32_t>(v) : v; }
+  int64_t sgn(uint64_t v) const {
+    return bits == 32 ? static_cast<int64_t>(static_cast<int32_t>(static_cast<uint32_t>(v))) : static_cast<int64_t>(v);
+  }
+  void header(Bytes& o, size_t count, int64_t first) const {
+    uleb(o, 128);
+    uleb(o, 4);
+    uleb(o, count);
+    uleb(o, TW::zz(count ? first : 0));
+  }
+  // deltas: signed (sign-extended) values
+  void block(Bytes& o, const int64_t* d, size_t n) const {
+    int64_t mn = *std::min_element(d, d + n);
+    uleb(o, TW::zz(mn));
+    uint64_t packed[128];
+    int widths[4] = {0, 0, 0, 0};
+    for (size_t i = 0; i < n; ++i) packed[i] = wrap(static_cast<uint64_t>(d[i]) - static_cast<uint64_t>(mn));
+    for (int m = 0; m < 4; ++m) {
+      uint64_t mx = 0;
+      bool any = false;
+      for (size_t i = m * 32; i < std::min<size_t>(n, (m + 1) * 32); ++i) {
+        mx = std::max(mx, packed[i]);
+        any = true;
+      }
+      widths[m] = any ? bit_length(mx) : 0;
+    }
+    for (int m = 0; m < 4; ++m) o.push_back(static_cast<uint8_t>(widths[m]));
+    for (int m = 0; m < 4; ++m) {
+      if (static_cast<size_t>(m) * 32 >= n) break;
+      uint64_t mb[32] = {0};
+      for (size_t i = m * 32; i < std::min<size_t>(n, (m + 1) * 32); ++i) mb[i - m * 32] = packed[i];
+      pack_bits(o, mb, 32, widths[m]);
+    }
+  }
+  static size_t block_size(int64_t mn, const int* widths, size_t n) {
+    Bytes t;
+    uleb(t, TW::zz(mn));
+    size_t s = t.size() + 4;
+    for (int m = 0; m < 4; ++m)
+      if (static_cast<size_t>(m) * 32 < n) s += 4 * widths[m];
+    return s;
+  }
+};
+
+// ------------------------------------------------------------------ Snappy compressor
+
+// Greedy LZ77 over 4-byte sequences with a hash table of recent positions.
+void snappy_compress(const uint8_t* in, size_t n, Bytes& o) {
+  o.clear();
+  uleb(o, n);
+  auto literal = [&](size_t a, size_t b) {
+    while (a < b) {
+      size_t len = std::min<size_t>(b - a, 65536);
+      if (len <= 60) {
+        o.push_back(static_cast<uint8_t>((len - 1) << 2));
+      } else {
+        size_t v = len - 1;
+        int nb = v < 256 ? 1 : v < 65536 ? 2 : v < (1u << 24) ? 3 : 4;
+        o.push_back(static_cast<uint8_t>((59 + nb) << 2));
+        for (int k = 0; k < nb; ++k) o.push_back(static_cast<uint8_t>(v >> (8 * k)));
+      }
+      o.insert(o.end(), in + a, in + a + len);
+      a += len;
+    }
+  };
+  auto copy = [&](size_t off, size_t len) {
+    while (len > 0) {
+      if (len >= 4 && len <= 11 && off < 2048) {
+        o.push_back(static_cast<uint8_t>(((off >> 8) << 5) | ((len - 4) << 2) | 1));
+        o.push_back(static_cast<uint8_t>(off));
+        return;
+      }
+      size_t c = std::min<size_t>(len, 64);
+      if (off < 65536) {
+        o.push_back(static_cast<uint8_t>(((c - 1) << 2) | 2));
+        o.push_back(static_cast<uint8_t>(off));
+        o.push_back(static_cast<uint8_t>(off >> 8));
+      } else {
+        o.push_back(static_cast<uint8_t>(((c - 1) << 2) | 3));
+        for (int k = 0; k < 4; ++k) o.push_back(static_cast<uint8_t>(off >> (8 * k)));
+      }
+      len -= c;
+    }
+  };
+  if (n < 16) {
+    literal(0, n);
+    return;
+  }
+  const int kBits = 14;
+  std::vector<int64_t> table(size_t(1) << kBits, -1);
+  auto h4 = [&](size_t i) {
+    uint32_t x;
+    memcpy(&x, in + i, 4);
+    return (x * 0x1e35a7bdu) >> (32 - kBits);
+  };
+  size_t i = 0, lit = 0;
+  const size_t limit = n - 4;
+  while (i <= limit) {
+    uint32_t h = h4(i);
+    int64_t cand = table[h];
+    table[h] = static_cast<int64_t>(i);
+    if (cand >= 0 && i - cand < (1u << 31) && memcmp(in + cand, in + i, 4) == 0) {
+      size_t len = 4;
+      while (i + len < n && in[cand + len] == in[i + len]) ++len;
+      literal(lit, i);
+      copy(i - cand, len);
+      size_t end = i + len;
+      for (size_t k = i + 1; k < end && k <= limit; k += 2) table[h4(k)] = static_cast<int64_t>(k);
+      i = end;
+      lit = i;
+    } else {
+      ++i;
+    }
+  }
+  literal(lit, n);
+}
+
+// ------------------------------------------------------------------ chunk encoder
+
+struct ChunkOut {
+  Bytes data;
+  int64_t dict_off = -1;    // relative to the chunk start
+  int64_t data_off = 0;
+  int64_t total_unc = 0;
+  int64_t total_cmp = 0;
+  int codec = 0;
+  std::vector<int> encodings;
+  std::vector<std::array<int64_t, 3>> locations;  // (relative offset, size incl. header, first row)
+  int64_t ba_bytes = -1;
+  bool ok = true;
+};
+
+struct ColIn {
+  const pq_write_column* c;
+  int64_t r0, r1;
+};
+
+int type_width(int t) { return t == PQ_TYPE_INT32 || t == PQ_TYPE_FLOAT ? 4 : (t == PQ_TYPE_INT64 || t == PQ_TYPE_DOUBLE) ? 8 : 0; }
+
+void page_header(Bytes& o, int type, int64_t unc, int64_t cmp, int sub, const std::vector<std::pair<int, int64_t>>& f,
+                 int v2_bool = -1) {
+  TW t(o);
+  t.i32(1, type);
+  t.i32(2, unc);
+  t.i32(3, cmp);
+  t.struct_begin(sub);
+  for (auto& kv : f) t.i32(kv.first, kv.second);
+  if (v2_bool >= 0) t.boolean(7, v2_bool != 0);
+  t.struct_end();
+  t.stop();
+}
+
+std::array<int64_t, 3> A3(int64_t a, int64_t b, int64_t c) { return {a, b, c}; }
+
+void encode_chunk(const ColIn& in, int64_t page_bytes, int codec, ChunkOut* out) {
+  const pq_write_column& c = *in.c;
+  const int64_t n = in.r1 - in.r0;
+  const int width = type_width(c.type);
+  const bool optional = c.valid != nullptr;
+  const bool is_ba = c.type == PQ_TYPE_BYTE_ARRAY;
+  const uint8_t* valid = optional ? c.valid + in.r0 : nullptr;
+  // non-null value indices (row ids) in order
+  std::vector<int64_t> rows_nn;
+  rows_nn.reserve(n);
+  for (int64_t r = 0; r < n; ++r)
+    if (!optional || valid[r]) rows_nn.push_back(r);
+  auto fixed_bits = [&](int64_t r) -> uint64_t {
+    const uint8_t* p = static_cast<const uint8_t*>(c.values) + (in.r0 + r) * width;
+    uint64_t v = 0;
+    memcpy(&v, p, width);
+    return v;
+  };
+  const int64_t* offs = is_ba ? static_cast<const int64_t*>(c.values) + in.r0 : nullptr;
+  auto str = [&](int64_t r, const uint8_t** p) -> int64_t {
+    *p = c.chars + offs[r];
+    return offs[r + 1] - offs[r];
+  };
+  if (is_ba) {
+    int64_t s = 0;
+    for (int64_t r : rows_nn) s += offs[r + 1] - offs[r];
+    out->ba_bytes = s;
+  }
+  // dictionary
+  const bool dict = c.encoding == 8 || c.encoding == 2;
+  const bool delta = c.encoding == 5;
+  std::vector<uint64_t> idx;  // per non-null value
+  Bytes dict_body;
+  int64_t dict_n = 0;
+  int bw = 0;
+  if (dict) {
+    idx.resize(rows_nn.size());
+    if (is_ba) {
+      std::unordered_map<std::string, uint32_t> pos;
+      pos.reserve(1024);
+      for (size_t k = 0; k < rows_nn.size(); ++k) {
+        const uint8_t* p;
+        int64_t len = str(rows_nn[k], &p);
+        std::string key(reinterpret_cast<const char*>(p), static_cast<size_t>(len));
+        auto it = pos.find(key);
+        if (it == pos.end()) {
+          uint32_t id = static_cast<uint32_t>(pos.size());
+          pos.emplace(key, id);
+          uint32_t l = static_cast<uint32_t>(len);
+          dict_body.insert(dict_body.end(), reinterpret_cast<uint8_t*>(&l), reinterpret_cast<uint8_t*>(&l) + 4);
+          dict_body.insert(dict_body.end(), p, p + len);
+          idx[k] = id;
+        } else {
+          idx[k] = it->second;
+        }
+      }
+      dict_n = static_cast<int64_t>(pos.size());
+    } else {
+      std::unordered_map<uint64_t, uint32_t> pos;
+      pos.reserve(1024);
+      for (size_t k = 0; k < rows_nn.size(); ++k) {
+        uint64_t v = fixed_bits(rows_nn[k]);
+        auto it = pos.find(v);
+        if (it == pos.end()) {
+          uint32_t id = static_cast<uint32_t>(pos.size());
+          pos.emplace(v, id);
+          dict_body.insert(dict_body.end(), reinterpret_cast<uint8_t*>(&v), reinterpret_cast<uint8_t*>(&v) + width);
+          idx[k] = id;
+        } else {
+          idx[k] = it->second;
+        }
+      }
+      dict_n = static_cast<int64_t>(pos.size());
+    }
+    bw = bit_length(dict_n > 0 ? static_cast<uint64_t>(dict_n - 1) : 0);
+  }
+  DeltaEnc de{c.type == PQ_TYPE_INT32 ? 32 : 64};
+  auto sval = [&](int64_t r) -> int64_t { return de.sgn(fixed_bits(r)); };
+  // ---- page row counts
+  std::vector<int64_t> counts;
+  if (is_ba && !dict) {
+    int64_t r = 0;
+    while (r < n) {
+      int64_t used = 0, rows = 0;
+      while (r + rows < n) {
+        int64_t rr = r + rows;
+        int64_t cost = (!optional || valid[rr]) ? 4 + (offs[rr + 1] - offs[rr]) : 0;
+        if (rows >= 8 && used + cost > page_bytes) break;
+        used += cost;
+        ++rows;
+      }
+      counts.push_back(rows);
+      r += rows;
+    }
+  } else if (delta && !optional) {
+    int64_t a = 0;
+    std::vector<int64_t> d;
+    while (a < n) {
+      int64_t rem = n - a;
+      if (rem <= 129) {
+        counts.push_back(rem);
+        break;
+      }
+      // size with k whole blocks: header(1 + 128k) + sum of block sizes
+      auto hdr = [&](int64_t cnt) {
+        Bytes t;
+        de.header(t, static_cast<size_t>(cnt), sval(a));
+        return static_cast<int64_t>(t.size());
+      };
+      auto blk = [&](int64_t j0, int64_t nd) {  // deltas j0.. (value index a+1+j0 ..)
+        int64_t dd[128];
+        for (int64_t q = 0; q < nd; ++q)
+          dd[q] = de.sgn(static_cast<uint64_t>(sval(a + 1 + j0 + q)) - static_cast<uint64_t>(sval(a + j0 + q)));
+        int64_t mn = *std::min_element(dd, dd + nd);
+        int w[4] = {0, 0, 0, 0};
+        for (int m = 0; m < 4; ++m) {
+          uint64_t mx = 0;
+          for (int64_t q = m * 32; q < std::min<int64_t>(nd, (m + 1) * 32); ++q)
+            mx = std::max(mx, de.wrap(static_cast<uint64_t>(dd[q]) - static_cast<uint64_t>(mn)));
+          w[m] = bit_length(mx);
+        }
+        return static_cast<int64_t>(DeltaEnc::block_size(mn, w, static_cast<size_t>(nd)));
+      };
+      int64_t k = 1;
+      int64_t body = blk(0, 128);
+      int64_t result = -1;
+      while (1 + 128 * (k + 1) <= rem) {
+        int64_t nxt = body + blk(128 * k, 128);
+        if (hdr(1 + 128 * (k + 1)) + nxt > page_bytes) {
+          result = 1 + 128 * k;
+          break;
+        }
+        body = nxt;
+        ++k;
+      }
+      if (result < 0) {
+        // whole tail: remaining deltas after k blocks form one more (partial) block
+        int64_t tail_deltas = rem - 1 - 128 * k;
+        int64_t full = hdr(rem) + body + (tail_deltas > 0 ? blk(128 * k, tail_deltas) : 0);
+        result = full <= page_bytes ? rem : 1 + 128 * k;
+      }
+      counts.push_back(result);
+      a += result;
+    }
+  } else {
+    int64_t bits = dict ? std::max(bw, 1) : 8 * width;
+    if (optional) bits += 1;
+    int64_t per = std::max<int64_t>(8, (page_bytes * 8 / bits) / 8 * 8);
+    for (int64_t r = 0; r < n; r += per) counts.push_back(std::min(per, n - r));
+  }
+  // ---- build pages
+  auto build = [&](int use_codec, ChunkOut* co) {
+    co->data.clear();
+    co->locations.clear();
+    co->total_unc = co->total_cmp = 0;
+    co->dict_off = -1;
+    Bytes body, cbody, hdr;
+    auto compress = [&](const Bytes& src, Bytes& dst) {
+      if (use_codec == 1)
+        snappy_compress(src.data(), src.size(), dst);
+      else
+        dst = src;
+    };
+    if (dict) {
+      compress(dict_body, cbody);
+      hdr.clear();
+      page_header(hdr, 2, static_cast<int64_t>(dict_body.size()), static_cast<int64_t>(cbody.size()), 7,
+                  {{1, dict_n}, {2, 0}});
+      co->dict_off = static_cast<int64_t>(co->data.size());
+      co->data.insert(co->data.end(), hdr.begin(), hdr.end());
+      co->data.insert(co->data.end(), cbody.begin(), cbody.end());
+      co->total_unc += static_cast<int64_t>(hdr.size() + dict_body.size());
+      co->total_cmp += static_cast<int64_t>(hdr.size() + cbody.size());
+    }
+    co->data_off = static_cast<int64_t>(co->data.size());
+    int64_t row = 0;
+    size_t vpos = 0;
+    Bytes levels, vals;
+    std::vector<uint64_t> tmp;
+    for (int64_t cnt : counts) {
+      // levels
+      size_t nn = 0;
+      levels.clear();
+      if (optional) {
+        tmp.resize(cnt);
+        for (int64_t r = 0; r < cnt; ++r) {
+          tmp[r] = valid[row + r] ? 1 : 0;
+          nn += tmp[r];
+        }
+        hybrid_encode(levels, tmp.data(), tmp.size(), 1);
+      } else {
+        nn = static_cast<size_t>(cnt);
+      }
+      // values
+      vals.clear();
+      if (dict) {
+        vals.push_back(static_cast<uint8_t>(bw));
+        hybrid_encode(vals, idx.data() + vpos, nn, bw);
+      } else if (delta) {
+        de.header(vals, nn, nn ? sval(rows_nn[vpos]) : 0);
+        int64_t dd[128];
+        for (size_t b = 1; b < nn; b += 128) {
+          size_t m = std::min<size_t>(128, nn - b);
+          for (size_t q = 0; q < m; ++q)
+            dd[q] = de.sgn(static_cast<uint64_t>(sval(rows_nn[vpos + b + q])) -
+                           static_cast<uint64_t>(sval(rows_nn[vpos + b + q - 1])));
+          de.block(vals, dd, m);
+        }
+      } else if (is_ba) {
+        for (size_t k = 0; k < nn; ++k) {
+          const uint8_t* p;
+          int64_t len = str(rows_nn[vpos + k], &p);
+          uint32_t l = static_cast<uint32_t>(len);
+          vals.insert(vals.end(), reinterpret_cast<uint8_t*>(&l), reinterpret_cast<uint8_t*>(&l) + 4);
+          vals.insert(vals.end(), p, p + len);
+        }
+      } else {
+        size_t base = vals.size();
+        vals.resize(base + nn * width);
+        for (size_t k = 0; k < nn; ++k) {
+          uint64_t v = fixed_bits(rows_nn[vpos + k]);
+          memcpy(vals.data() + base + k * width, &v, width);
+        }
+      }
+      const int enc = c.encoding == 2 ? 8 : c.encoding;
+      hdr.clear();
+      size_t page_start = co->data.size();
+      if (c.page_version == 2) {
+        compress(vals, cbody);
+        const int64_t unc = static_cast<int64_t>(levels.size() + vals.size());
+        const int64_t cmp = static_cast<int64_t>(levels.size() + cbody.size());
+        page_header(hdr, 3, unc, cmp, 8,
+                    {{1, cnt}, {2, cnt - static_cast<int64_t>(nn)}, {3, cnt}, {4, enc},
+                     {5, static_cast<int64_t>(levels.size())}, {6, 0}},
+                    use_codec != 0);
+        co->data.insert(co->data.end(), hdr.begin(), hdr.end());
+        co->data.insert(co->data.end(), levels.begin(), levels.end());
+        co->data.insert(co->data.end(), cbody.begin(), cbody.end());
+        co->total_unc += static_cast<int64_t>(hdr.size()) + unc;
+        co->total_cmp += static_cast<int64_t>(hdr.size()) + cmp;
+      } else {
+        body.clear();
+        if (optional) {
+          uint32_t L = static_cast<uint32_t>(levels.size());
+          body.insert(body.end(), reinterpret_cast<uint8_t*>(&L), reinterpret_cast<uint8_t*>(&L) + 4);
+          body.insert(body.end(), levels.begin(), levels.end());
+        }
+        body.insert(body.end(), vals.begin(), vals.end());
+        compress(body, cbody);
+        page_header(hdr, 0, static_cast<int64_t>(body.size()), static_cast<int64_t>(cbody.size()), 5,
+                    {{1, cnt}, {2, enc}, {3, 3}, {4, 3}});
+        co->data.insert(co->data.end(), hdr.begin(), hdr.end());
+        co->data.insert(co->data.end(), cbody.begin(), cbody.end());
+        co->total_unc += static_cast<int64_t>(hdr.size() + body.size());
+        co->total_cmp += static_cast<int64_t>(hdr.size() + cbody.size());
+      }
+      co->locations.push_back(A3(static_cast<int64_t>(page_start), static_cast<int64_t>(co->data.size() - page_start), row));
+      row += cnt;
+      vpos += nn;
+    }
+    co->codec = use_codec;
+  };
+  build(codec, out);
+  if (codec != 0 && c.compress_threshold >= 0) {
+    ChunkOut plain;
+    build(0, &plain);
+    if (static_cast<double>(out->total_cmp) > static_cast<double>(plain.total_cmp) * (1.0 - c.compress_threshold)) {
+      plain.ba_bytes = out->ba_bytes;
+      *out = std::move(plain);
+    }
+  }
+  std::vector<int> encs = {c.encoding == 2 ? 8 : c.encoding};
+  if (dict) encs.push_back(0);
+  if (optional) encs.push_back(3);
+  std::sort(encs.begin(), encs.end());
+  encs.erase(std::unique(encs.begin(), encs.end()), encs.end());
+  out->encodings = encs;
+}
+
+}  // namespace
+
+extern "C" {
+
+pq_status pq_write_table(const pq_write_column* cols, int n_cols, int64_t n_rows, int64_t rg_rows,
+                         int64_t page_bytes, int offset_index, int n_threads, uint8_t** out, uint64_t* out_size) {
+  if (!cols || n_cols <= 0 || n_rows < 0 || rg_rows <= 0 || page_bytes <= 0 || !out || !out_size)
+    return PQ_ERR_INVALID_ARG;
+  for (int c = 0; c < n_cols; ++c) {
+    const auto& col = cols[c];
+    const bool fixed = col.type == PQ_TYPE_INT32 || col.type == PQ_TYPE_INT64 || col.type == PQ_TYPE_DOUBLE ||
+                       col.type == PQ_TYPE_FLOAT;
+    if (!fixed && col.type != PQ_TYPE_BYTE_ARRAY) return PQ_ERR_UNSUPPORTED;
+    if (col.encoding != 0 && col.encoding != 2 && col.encoding != 8 && col.encoding != 5) return PQ_ERR_UNSUPPORTED;
+    if (col.encoding == 5 && col.type != PQ_TYPE_INT32 && col.type != PQ_TYPE_INT64) return PQ_ERR_INVALID_ARG;
+    if (col.codec != 0 && col.codec != 1) return PQ_ERR_UNSUPPORTED;
+    if (col.page_version != 1 && col.page_version != 2) return PQ_ERR_INVALID_ARG;
+    if (!col.values && n_rows > 0) return PQ_ERR_INVALID_ARG;
+    if (col.type == PQ_TYPE_BYTE_ARRAY && !col.chars && n_rows > 0) return PQ_ERR_INVALID_ARG;
+  }
+  const int64_t n_rg = n_rows == 0 ? 0 : (n_rows + rg_rows - 1) / rg_rows;
+  std::vector<ColIn> jobs;
+  for (int64_t g = 0; g < n_rg; ++g)
+    for (int c = 0; c < n_cols; ++c) jobs.push_back({&cols[c], g * rg_rows, std::min(n_rows, (g + 1) * rg_rows)});
+  std::vector<ChunkOut> chunks(jobs.size());
+  int nt = n_threads > 0 ? n_threads : static_cast<int>(std::thread::hardware_concurrency());
+  nt = std::max(1, std::min<int>(nt, static_cast<int>(jobs.size())));
+  std::atomic<size_t> next{0};
+  auto worker = [&]() {
+    for (size_t j; (j = next.fetch_add(1)) < jobs.size();)
+      encode_chunk(jobs[j], page_bytes, jobs[j].c->codec, &chunks[j]);
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back(worker);
+  worker();
+  for (auto& t : th) t.join();
+  // assemble
+  Bytes file = {'P', 'A', 'R', '1'};
+  std::vector<int64_t> start(jobs.size());
+  size_t total = 4;
+  for (auto& ch : chunks) total += ch.data.size();
+  file.reserve(total + 1024 + jobs.size() * 64);
+  for (size_t j = 0; j < jobs.size(); ++j) {
+    start[j] = static_cast<int64_t>(file.size());
+    file.insert(file.end(), chunks[j].data.begin(), chunks[j].data.end());
+    Bytes().swap(chunks[j].data);
+  }
+  std::vector<std::pair<int64_t, int64_t>> oi(jobs.size(), {-1, 0});
+  if (offset_index) {
+    for (size_t j = 0; j < jobs.size(); ++j) {
+      Bytes b;
+      TW t(b);
+      t.list_begin(1, 12, chunks[j].locations.size());
+      for (auto& l : chunks[j].locations) {
+        t.elem_struct_begin();
+        t.i64(1, start[j] + l[0]);
+        t.i32(2, l[1]);
+        t.i64(3, l[2]);
+        t.struct_end();
+      }
+      t.stop();
+      oi[j] = {static_cast<int64_t>(file.size()), static_cast<int64_t>(b.size())};
+      file.insert(file.end(), b.begin(), b.end());
+    }
+  }
+  Bytes f;
+  TW t(f);
+  t.i32(1, 2);
+  t.list_begin(2, 12, static_cast<size_t>(n_cols) + 1);
+  t.elem_struct_begin();
+  t.binary(4, "schema");
+  t.i32(5, n_cols);
+  t.struct_end();
+  for (int c = 0; c < n_cols; ++c) {
+    t.elem_struct_begin();
+    t.i32(1, cols[c].type);
+    t.i32(3, cols[c].valid ? 1 : 0);
+    t.binary(4, cols[c].name ? cols[c].name : "");
+    t.struct_end();
+  }
+  t.i64(3, n_rows);
+  t.list_begin(4, 12, static_cast<size_t>(n_rg));
+  for (int64_t g = 0; g < n_rg; ++g) {
+    int64_t unc = 0, cmp = 0;
+    for (int c = 0; c < n_cols; ++c) {
+      unc += chunks[g * n_cols + c].total_unc;
+      cmp += chunks[g * n_cols + c].total_cmp;
+    }
+    t.elem_struct_begin();
+    t.list_begin(1, 12, n_cols);
+    for (int c = 0; c < n_cols; ++c) {
+      const size_t j = static_cast<size_t>(g * n_cols + c);
+      const ChunkOut& ch = chunks[j];
+      t.elem_struct_begin();
+      t.i64(2, start[j]);
+      t.struct_begin(3);
+      t.i32(1, cols[c].type);
+      t.list_begin(2, 5, ch.encodings.size());
+      for (int e : ch.encodings) t.varint(TW::zz(e));
+      t.list_begin(3, 8, 1);
+      std::string name = cols[c].name ? cols[c].name : "";
+      t.varint(name.size());
+      f.insert(f.end(), name.begin(), name.end());
+      t.i32(4, ch.codec);
+      t.i64(5, jobs[j].r1 - jobs[j].r0);
+      t.i64(6, ch.total_unc);
+      t.i64(7, ch.total_cmp);
+      t.i64(9, start[j] + ch.data_off);
+      if (ch.dict_off >= 0) t.i64(11, start[j] + ch.dict_off);
+      if (cols[c].type == PQ_TYPE_BYTE_ARRAY) {
+        t.struct_begin(16);
+        t.i64(1, ch.ba_bytes);
+        t.struct_end();
+      }
+      t.struct_end();
+      if (offset_index) {
+        t.i64(4, oi[j].first);
+        t.i32(5, oi[j].second);
+      }
+      t.struct_end();
+    }
+    t.i64(2, unc);
+    t.i64(3, jobs[g * n_cols].r1 - jobs[g * n_cols].r0);
+    t.i64(5, start[g * n_cols]);
+    t.i64(6, cmp);
+    t.i16(7, g);
+    t.struct_end();
+  }
+  t.binary(6, "pqscan-gb300");
+  t.stop();
+  file.insert(file.end(), f.begin(), f.end());
+  uint32_t fl = static_cast<uint32_t>(f.size());
+  file.insert(file.end(), reinterpret_cast<uint8_t*>(&fl), reinterpret_cast<uint8_t*>(&fl) + 4);
+  file.insert(file.end(), {'P', 'A', 'R', '1'});
+  uint8_t* buf = static_cast<uint8_t*>(malloc(file.size()));
+  if (!buf) return PQ_ERR_OOM;
+  memcpy(buf, file.data(), file.size());
+  *out = buf;
+  *out_size = file.size();
+  return PQ_OK;
+}
+
+void pq_write_free(uint8_t* buf) { free(buf); }
+
+}  // extern "C"

@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpqscan.so")
 PQ_OK, PQ_ERR_INVALID_ARG, PQ_ERR_CORRUPT, PQ_ERR_UNSUPPORTED = 0, 1, 2, 3
 PQ_ERR_OOM, PQ_ERR_BUDGET, PQ_ERR_TIMEOUT, PQ_ERR_CUDA, PQ_ERR_CAPACITY = 4, 5, 6, 7, 8
 PQ_TYPE_INT32, PQ_TYPE_INT64, PQ_TYPE_FLOAT, PQ_TYPE_DOUBLE, PQ_TYPE_BYTE_ARRAY = 1, 2, 4, 5, 6
-PQ_SCAN_BATCHED, PQ_SCAN_PLAIN, PQ_SCAN_GRAPH, PQ_SCAN_RESIDENT_DICT = 0, 1, 2, 4
+PQ_SCAN_BATCHED, PQ_SCAN_PLAIN, PQ_SCAN_GRAPH, PQ_SCAN_RESIDENT_DICT, PQ_SCAN_TIMING = 0, 1, 2, 4, 8
+STAGES = ("prepare", "snappy", "dict", "walk", "expand", "strings")
 
 STATUS_NAMES = {0: "PQ_OK", 1: "PQ_ERR_INVALID_ARG", 2: "PQ_ERR_CORRUPT", 3: "PQ_ERR_UNSUPPORTED",
                 4: "PQ_ERR_OOM", 5: "PQ_ERR_BUDGET", 6: "PQ_ERR_TIMEOUT", 7: "PQ_ERR_CUDA",
@@ -58,7 +59,7 @@ class pq_out_size(C.Structure):
 class pq_plan_info(C.Structure):
     _fields_ = [("n_columns", C.c_int32), ("n_pages", C.c_int32), ("n_dict_pages", C.c_int32),
                 ("n_items", C.c_int32), ("read_bytes", C.c_uint64), ("decoded_bytes", C.c_uint64),
-                ("scratch_bytes", C.c_uint64)]
+                ("scratch_bytes", C.c_uint64), ("launches_per_scan", C.c_int32), ("reserved", C.c_int32)]
 
 
 class pq_column(C.Structure):
@@ -101,6 +102,7 @@ _SIGS = {
     "pq_free_index": (None, [_P]),
     "pq_plan_scan": (C.c_int, [_P, _P, C.POINTER(pq_request), C.POINTER(_P), C.POINTER(pq_out_size)]),
     "pq_plan_get_info": (C.c_int, [_P, C.POINTER(pq_plan_info)]),
+    "pq_plan_stage_ms": (C.c_int, [_P, C.POINTER(C.c_float)]),
     "pq_free_plan": (None, [_P]),
     "pq_scan_columns": (C.c_int, [_P, _P, C.POINTER(pq_column), _P]),
     "pq_scan_wait": (C.c_int, [_P, _P, _P, C.POINTER(C.c_uint64)]),
@@ -235,6 +237,32 @@ def pq_plan_get_info(plan):
     return info
 
 
+def pq_plan_stage_ms(plan):
+    ms = (C.c_float * len(STAGES))()
+    check(lib().pq_plan_stage_ms(plan, ms))
+    return dict(zip(STAGES, ms[:]))
+
+
+def pq_scan_host(ctx, host_files, columns=None, row_begin=0, row_count=-1, flags=PQ_SCAN_BATCHED, outs=None):
+    """host_files: list of (host pointer, size).  With outs=None returns the
+    output sizes; otherwise fills the host buffers described by `outs`
+    (list of pq_column with host pointers)."""
+    arr = (pq_file * len(host_files))(*[pq_file(p, n) for p, n in host_files])
+    req = pq_request()
+    keep = None
+    if columns is not None:
+        keep = (C.c_int32 * max(len(columns), 1))(*columns)
+        req.columns = C.cast(keep, C.POINTER(C.c_int32))
+        req.n_columns = len(columns)
+    req.flags = flags
+    req.row_begin = row_begin
+    req.row_count = row_count
+    sizes = (pq_out_size * 64)()
+    o = None if outs is None else (pq_column * max(len(outs), 1))(*outs)
+    check(lib().pq_scan_host(ctx, arr, len(host_files), C.byref(req), o, sizes), ctx)
+    return sizes
+
+
 def pq_free_plan(plan):
     lib().pq_free_plan(plan)
 
@@ -250,3 +278,18 @@ def pq_scan_wait(ctx, plan, ncols, stream=None):
     chars = (C.c_uint64 * max(ncols, 1))()
     st = lib().pq_scan_wait(ctx, plan, stream, chars)
     return st, list(chars[:ncols])
+
+
+def pq_write_table(columns, n_rows, rg_rows, page_bytes, offset_index=True, n_threads=0):
+    """columns: list of pq_write_column (pointers kept alive by the caller).
+    Returns the file as a numpy uint8 array."""
+    import numpy as np
+    arr = (pq_write_column * len(columns))(*columns)
+    out = C.POINTER(C.c_uint8)()
+    size = C.c_uint64()
+    check(lib().pq_write_table(arr, len(columns), n_rows, rg_rows, page_bytes, 1 if offset_index else 0,
+                               n_threads, C.byref(out), C.byref(size)))
+    try:
+        return np.ctypeslib.as_array(out, shape=(size.value,)).copy() if size.value else np.zeros(0, np.uint8)
+    finally:
+        lib().pq_write_free(out)
