@@ -31,14 +31,21 @@ struct DecodeArgs {
   Item* items;
   const OutCol* cols;
   DevStatus* st;
-  uint32_t* item_counter;  // persistent expansion: next item to take
+  uint32_t* item_counter;   // [0] next work item (expansion), [1] next walk page
+  const uint32_t* walk_pps; // plan pages that need the walk, longest chains first
+  const uint32_t* delta_pps;// DELTA plan pages (block bases)
+  uint32_t* dpos;           // DELTA block positions (stream offsets)
+  int64_t* dbase;           // DELTA value preceding each block
   int n_pp;
   int n_items;
+  int n_walk;
+  int n_delta;
 };
 
 void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, DictDev* dicts, int n_sms,
                  DevStatus* st, cudaStream_t s);
 void launch_walk(const DecodeArgs& a, int grid, cudaStream_t s);
+void launch_delta_bases(const DecodeArgs& a, cudaStream_t s);
 void launch_expand(const DecodeArgs& a, int grid, cudaStream_t s);
 void launch_strings(const DecodeArgs& a, const int* str_cols, int n_str_cols, int n_cols_total, int grid,
                     cudaStream_t s);

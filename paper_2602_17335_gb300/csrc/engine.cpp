@@ -109,8 +109,14 @@ pqi::DecodeArgs decode_args(pq_plan* plan) {
   a.cols = plan->d_cols;
   a.st = plan->d_status;
   a.item_counter = plan->d_counter;
+  a.walk_pps = plan->d_walk_pps;
+  a.delta_pps = plan->d_delta_pps;
+  a.dpos = plan->d_dpos;
+  a.dbase = plan->d_dbase;
   a.n_pp = static_cast<int>(plan->pps.size());
   a.n_items = static_cast<int>(plan->items.size());
+  a.n_walk = static_cast<int>(plan->walk_pps.size());
+  a.n_delta = static_cast<int>(plan->delta_pps.size());
   return a;
 }
 
@@ -316,7 +322,8 @@ pq_status pq_index_chunks(pq_ctx* ctx, const pq_file* files, int n_files, void* 
         if (cm.codec != pqi::CODEC_NONE && cm.codec != pqi::CODEC_SNAPPY)
           return fail(ctx, PQ_ERR_UNSUPPORTED, "codec " + std::to_string(cm.codec) + " not supported");
         if (start < 4 || cm.total_compressed < 0 ||
-            static_cast<uint64_t>(start) + static_cast<uint64_t>(cm.total_compressed) + 8 + m.footer_len > fsize)
+            static_cast<uint64_t>(start) + static_cast<uint64_t>(cm.total_compressed) + 8 + m.footer_len > fsize ||
+            static_cast<uint64_t>(start) + static_cast<uint64_t>(cm.total_compressed) + 32 > fsize)
           return fail(ctx, PQ_ERR_CORRUPT, "chunk byte range outside the file");
         pqi::ChunkDev cd{};
         cd.base = static_cast<const uint8_t*>(files[f].data) + start;
@@ -611,6 +618,7 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
   const int64_t item_rows_max = pqi::ITEM_ROWS;
   uint64_t scratch = 0;
   std::vector<int64_t> data_job_off;  // scratch offset per data snappy job
+  std::vector<int64_t> walk_cost;     // estimated chain steps per walked page
   std::vector<int32_t> dict_job_of_chunk(idx->chunks.size(), -1);
   for (size_t oc = 0; oc < plan->cols.size(); ++oc) {
     const int c = plan->cols[oc];
@@ -719,8 +727,30 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
         }
         plan->read_bytes += static_cast<uint64_t>(pg.header_len) + static_cast<uint64_t>(pg.compressed);
         pp.item_begin = static_cast<uint32_t>(plan->items.size());
+        const bool plain_fixed = pg.encoding == pqi::ENC_PLAIN && cd.ptype != pqi::T_BYTE_ARRAY;
+        const bool needs_walk = cd.max_def || !plain_fixed;
+        if (!cd.max_def) {
+          // REQUIRED: the value stream starts after the (empty) levels
+          if (pg.page_type == pqi::PAGE_DATA_V2 && (pg.rep_len != 0 || pg.def_len != 0))
+            return fail(ctx, PQ_ERR_CORRUPT, "levels in a page of a REQUIRED column");
+          pp.values_off = 0;
+          pp.nonnull = pg.num_values;
+        }
+        if (pg.encoding == pqi::ENC_DELTA_BP) {
+          pp.dtab = static_cast<uint32_t>(plan->delta_blocks);
+          plan->delta_blocks += pg.num_values > 1 ? static_cast<uint64_t>(pg.num_values - 2) / 128 + 1 : 1;
+          plan->delta_pps.push_back(static_cast<uint32_t>(plan->pps.size()));
+        }
+        if (needs_walk && !plain) {
+          plan->walk_pps.push_back(static_cast<uint32_t>(plan->pps.size()));
+          walk_cost.push_back(pg.encoding == pqi::ENC_DELTA_BP ? pg.num_values / 128 + (cd.max_def ? pg.num_values / 8 : 0)
+                              : cd.max_def ? pg.num_values / 8
+                              : cd.ptype == pqi::T_BYTE_ARRAY && pg.encoding == pqi::ENC_PLAIN ? pg.num_values
+                                                                                                 : pg.num_values / 256);
+        }
         const int64_t span = pp.row_hi - pp.row_lo;
-        const int64_t per = plain ? span : item_rows_max;
+        const int64_t per = (cd.max_def && !plain_fixed) ? pqi::ITEM_ROWS_OPT : item_rows_max;
+        (void)span;
         uint32_t n_it = 0;
         for (int64_t r = pp.row_lo; r < pp.row_hi; r += per) {
           pqi::Item it{};
@@ -748,8 +778,21 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
     plan->outcols.push_back(col);
     plan->sizes.push_back(sz);
   }
+  // walk list: longest header chains first
+  {
+    std::vector<size_t> order(plan->walk_pps.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return walk_cost[x] > walk_cost[y]; });
+    std::vector<uint32_t> sorted(order.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = plan->walk_pps[order[i]];
+    plan->walk_pps.swap(sorted);
+  }
   // device arrays
   const size_t npp = plan->pps.size(), nit = plan->items.size();
+  plan->d_walk_pps = plan_alloc(uint32_t, plan.get(), plan->walk_pps.size());
+  plan->d_delta_pps = plan_alloc(uint32_t, plan.get(), plan->delta_pps.size());
+  plan->d_dpos = plan_alloc(uint32_t, plan.get(), plan->delta_blocks);
+  plan->d_dbase = plan_alloc(int64_t, plan.get(), plan->delta_blocks);
   plan->d_pps = plan_alloc(pqi::PlanPage, plan.get(), npp);
   plan->d_items = plan_alloc(pqi::Item, plan.get(), nit);
   plan->d_cols = plan_alloc(pqi::OutCol, plan.get(), plan->outcols.size());
@@ -771,7 +814,7 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
     free_plan_device(plan.get());
     return fail(ctx, PQ_ERR_OOM, "plan scratch");
   }
-  plan->scratch_bytes = scratch + str_rows * 4 + (plan->d_str_items ? nit * 8 : 0);
+  plan->scratch_bytes = scratch + str_rows * 4 + (plan->d_str_items ? nit * 8 : 0) + plan->delta_blocks * 12;
   // rebase scratch bodies, string scratch per column
   size_t jd = 0;
   for (auto& pp : plan->pps) {
@@ -803,6 +846,12 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
   if (!plan->str_cols.empty())
     CK(cudaMemcpyAsync(plan->d_str_cols, plan->str_cols.data(), sizeof(int32_t) * plan->str_cols.size(),
                        cudaMemcpyHostToDevice, s));
+  if (!plan->walk_pps.empty())
+    CK(cudaMemcpyAsync(plan->d_walk_pps, plan->walk_pps.data(), sizeof(uint32_t) * plan->walk_pps.size(),
+                       cudaMemcpyHostToDevice, s));
+  if (!plan->delta_pps.empty())
+    CK(cudaMemcpyAsync(plan->d_delta_pps, plan->delta_pps.data(), sizeof(uint32_t) * plan->delta_pps.size(),
+                       cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaEventCreateWithFlags(&plan->done, cudaEventDisableTiming));
   if (plan->flags & PQ_SCAN_TIMING)
@@ -825,14 +874,15 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
       }
     } else {
       n += (plan->snappy_data.size() + plan->snappy_dict.size() ? 1 : 0) + (any_dict ? 2 : 0);
-      n += (npp ? 1 : 0) + (nit ? 1 : 0);
+      n += (plan->walk_pps.empty() ? 0 : 1) + (plan->delta_pps.empty() ? 0 : 1) + (nit ? 1 : 0);
     }
     n += plan->str_cols.empty() ? 0 : 2;
     plan->launches = n;
   }
   const int wbps = pqi::walk_blocks_per_sm(), ebps = pqi::expand_blocks_per_sm();
-  plan->walk_grid = static_cast<int>(std::min<size_t>(std::max<size_t>(npp, 1), size_t(ctx->n_sms) * wbps));
-  plan->expand_grid = static_cast<int>(std::min<size_t>(std::max<size_t>(nit, 1), size_t(ctx->n_sms) * ebps));
+  plan->walk_grid =
+      static_cast<int>(std::min<size_t>(std::max<size_t>(plan->walk_pps.size(), 1), size_t(ctx->n_sms) * wbps));
+  plan->expand_grid = static_cast<int>(std::min<size_t>(std::max<size_t>((nit + 7) / 8, 1), size_t(ctx->n_sms) * ebps));
   if (!plan->h_cols.reserve(sizeof(pqi::OutCol) * std::max<size_t>(plan->outcols.size(), 1)) ||
       !plan->h_out.reserve(sizeof(pqi::DevStatus) + 8 * std::max<size_t>(plan->outcols.size(), 1))) {
     free_plan_device(plan.get());
@@ -918,6 +968,7 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts) {
                        plan->idx->d_dicts, ctx->n_sms, a.st, s);
     mark(3);
     pqi::launch_walk(a, plan->walk_grid, s);
+    pqi::launch_delta_bases(a, s);
     mark(4);
     pqi::launch_expand(a, plan->expand_grid, s);
     mark(5);

@@ -99,6 +99,9 @@ struct pq_plan {
   std::vector<pqi::DictJob> dict_jobs;
   std::vector<int32_t> dict_chunks;          // chunk of each dict job
   std::vector<int32_t> str_cols;             // output columns of type BYTE_ARRAY
+  std::vector<uint32_t> walk_pps;            // plan pages that need the walk, longest first
+  std::vector<uint32_t> delta_pps;           // DELTA plan pages
+  uint64_t delta_blocks = 0;                 // capacity of the DELTA block tables
   // per chunk: range of plan pages (plain baseline launches per chunk)
   std::vector<std::pair<int32_t, int32_t>> chunk_pp;  // (first pp, count)
   std::vector<int32_t> chunk_pp_chunk;
@@ -117,6 +120,10 @@ struct pq_plan {
   uint32_t* d_str_scratch = nullptr;
   uint64_t* d_str_items = nullptr;
   uint32_t* d_counter = nullptr;
+  uint32_t* d_walk_pps = nullptr;
+  uint32_t* d_delta_pps = nullptr;
+  uint32_t* d_dpos = nullptr;
+  int64_t* d_dbase = nullptr;
   pqi::DevStatus* d_status = nullptr;
   std::vector<void*> owned;                  // pool blocks to release
   // host staging (pinned): output descriptors in, status + string totals out

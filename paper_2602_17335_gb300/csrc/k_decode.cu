@@ -1,5 +1,5 @@
-// K2-K8 — dictionary decode, page walk, tiled expansion, string passes and
-// the plain one-page-per-block baseline.
+// K2-K8 — dictionary decode, page walk, warp-granular expansion, string
+// passes and the plain one-page-per-block baseline.
 //
 // What a page holds (paper Section 2; byte layouts from the Parquet format):
 //   V1 data page: [4-byte LE length + RLE/bit-packed def levels]? values
@@ -8,36 +8,62 @@
 //   indices (1-byte bit width + RLE/bit-packed hybrid), or
 //   DELTA_BINARY_PACKED (header, then blocks of miniblocks).
 //
-// The scan runs in two phases so that pages larger than a thread block's
-// share of the GPU still use the whole GPU (paper Section 3, Insight 1):
+// Run and block headers make every stream a chain: the next header's
+// position is only known after the current one is read.  The scan keeps
+// that chain as short as the format allows and moves everything else off it
+// (paper Section 3, Insight 1: a page must not be the unit of parallelism):
 //
-//  walk   (one block per page): reads each stream's run / block headers —
-//         serial by construction — through a shared-memory window filled by
-//         the bulk-copy engine, writes the validity bitmap, and records for
-//         every ITEM_ROWS-row work item the stream position it starts from
-//         (a checkpoint).  DELTA blocks are summed in parallel so that each
-//         checkpoint carries the value preceding its block.
-//  expand (persistent blocks, one work item at a time): starts from the
-//         checkpoint, decodes TILE_ROWS rows at a time into shared memory
-//         (dictionary gather, delta prefix sums via warp shuffles, PLAIN
-//         loads) and writes each output row once, nulls as zero.
-//
-// Strings add a pass: expand records per row the dictionary index (or the
-// PLAIN value offset) plus per-item chars totals; a scan turns those into
-// item bases, and the copy pass writes int64 offsets and the chars.
+//  walk   one thread block per page that needs it; thread 0 follows the
+//         header chain through two shared-memory windows it fills with the
+//         bulk-copy engine (the next window streams in while the current one
+//         is read), a handful of dependent instructions per run; the block's
+//         other threads turn each batch of runs into the validity bitmap and
+//         into checkpoints (stream position at the first value) for the
+//         work items.  DELTA pages record every block's position.
+//  bases  DELTA only: one warp per block sums its deltas, a block-wide scan
+//         gives every block the value that precedes it.
+//  expand one warp per work item (ITEM_ROWS rows), no block-wide barriers:
+//         from the checkpoint the warp decodes its runs 32 values per lane
+//         step, gathers issued back to back, and writes every output row
+//         once (nulls as zero).
+//  strings expand records per row the dictionary index (or PLAIN value
+//         offset) and per-item chars totals; a scan makes item bases; the
+//         copy pass writes int64 offsets and the chars.
 #include "decode_job.h"
 #include "dev_util.cuh"
 
 namespace pqi {
 
-constexpr int WALK_THREADS = 128;
+constexpr int WALK_THREADS = 256;
 constexpr int EXP_THREADS = 256;
-constexpr uint32_t WIN_BYTES = 16384;
-constexpr int LV_BATCH = 128;
-constexpr int BLK_BATCH = 128;
-constexpr int SEG_MAX = 256;
-constexpr int DB_MAX = 24;
+constexpr int EXP_WARPS = EXP_THREADS / 32;
+constexpr uint32_t CWIN = 16384;  // chain window (two per walking block)
+constexpr uint32_t COVL = 64;     // overlap of consecutive chain windows
+constexpr int RB = 1024;          // runs per walk batch
 constexpr uint32_t NULL_IDX = 0xffffffffu;
+
+// ------------------------------------------------------------------ global bit readers
+
+// Bits [b, b + w) (w <= 32) of the little-endian bit stream at `base`,
+// through aligned 32-bit loads (reads at most 8 bytes past the value).
+__device__ __forceinline__ uint32_t gbits32(const uint8_t* base, uint64_t b, int w) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(base) + (b >> 3);
+  const uint32_t* q = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
+  const uint32_t sh = static_cast<uint32_t>((a & 3) * 8 + (b & 7));
+  const uint64_t v = ((static_cast<uint64_t>(__ldg(q + 1)) << 32) | __ldg(q)) >> sh;
+  return w >= 32 ? static_cast<uint32_t>(v) : static_cast<uint32_t>(v) & ((1u << w) - 1u);
+}
+
+__device__ __forceinline__ uint64_t gbits64(const uint8_t* base, uint64_t b, int w) {
+  if (w <= 32) return gbits32(base, b, w);
+  const uintptr_t a = reinterpret_cast<uintptr_t>(base) + (b >> 3);
+  const uint32_t* q = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
+  const uint32_t sh = static_cast<uint32_t>((a & 3) * 8 + (b & 7));
+  const uint64_t lo = (static_cast<uint64_t>(__ldg(q + 1)) << 32) | __ldg(q);
+  const uint64_t hi = __ldg(q + 2);
+  const uint64_t v = sh ? ((lo >> sh) | (hi << (64 - sh))) : lo;
+  return w >= 64 ? v : (v & ((1ull << w) - 1));
+}
 
 // ------------------------------------------------------------------ K6 dictionaries
 
@@ -56,7 +82,7 @@ __global__ void k_dict_fixed(const DictJob* __restrict__ jobs, DictDev* dicts, D
   uint32_t* dst = reinterpret_cast<uint32_t*>(j.values);
   for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < words;
        i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-    uint32_t lo = __ldg(src + i);
+    const uint32_t lo = __ldg(src + i);
     dst[i] = sh ? __funnelshift_r(lo, __ldg(src + i + 1), sh) : lo;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -69,70 +95,223 @@ __global__ void k_dict_fixed(const DictJob* __restrict__ jobs, DictDev* dicts, D
   }
 }
 
-struct DictStrSmem {
-  uint64_t bar;
-  uint32_t ctl[4];
-  alignas(16) uint8_t win[WIN_BYTES + 16];
+// ------------------------------------------------------------------ the header chain
+
+// Two shared-memory windows owned by one thread: the current one (fields
+// *0) and the other one (*1), swapped when the chain moves on.  A window
+// holds stream bytes [w, w + n); consecutive windows overlap by COVL bytes
+// so that any read of up to COVL bytes fits in one of them.  Only the owning
+// thread issues copies into them and reads them.  All state is scalar so
+// that it stays in registers.
+struct Chain {
+  uint8_t* b0;
+  uint8_t* b1;
+  uint64_t* m0;
+  uint64_t* m1;
+  uint32_t p0, p1;   // mbarrier phase parities
+  int64_t w0, w1;    // stream offset of the window's first byte
+  uint32_t n0, n1;   // bytes held
+  uint32_t e0, e1;   // a copy is in flight
+  uint32_t swapped;  // 1 when b0 is the second physical buffer
+  const uint8_t* sb;
+  uint32_t slen;
 };
 
-// BYTE_ARRAY dictionary: the entries are (4-byte length, bytes) back to back;
-// the walk over them is serial, done by thread 0 in a staged window.
-__global__ void __launch_bounds__(128) k_dict_str(const DictJob* __restrict__ jobs, DictDev* dicts,
-                                                  DevStatus* st) {
-  __shared__ DictStrSmem sm;
+__device__ __forceinline__ void ch_swap(Chain& c) {
+  uint8_t* tb = c.b0; c.b0 = c.b1; c.b1 = tb;
+  uint64_t* tm = c.m0; c.m0 = c.m1; c.m1 = tm;
+  uint32_t t = c.p0; c.p0 = c.p1; c.p1 = t;
+  int64_t tw = c.w0; c.w0 = c.w1; c.w1 = tw;
+  t = c.n0; c.n0 = c.n1; c.n1 = t;
+  t = c.e0; c.e0 = c.e1; c.e1 = t;
+  c.swapped ^= 1u;
+}
+
+// Copies stream bytes from `from` (rounded down to 16) into a window: up to
+// CWIN bytes, at most 16 bytes past the stream end (readable padding).
+__device__ __forceinline__ void ch_issue(const Chain& c, uint8_t* buf, uint64_t* bar, int64_t from, int64_t* w,
+                                         uint32_t* n, uint32_t* e) {
+  const uint8_t* a = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(c.sb + from) & ~uintptr_t(15));
+  int64_t want = (static_cast<int64_t>((c.sb + c.slen) - a) + 16) & ~int64_t(15);
+  if (want < 16) want = 16;
+  const uint32_t bytes = static_cast<uint32_t>(want < CWIN ? want : CWIN);
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(bar, bytes);
+  bulk_g2s(buf, a, bytes, bar);
+  *w = a - c.sb;
+  *n = bytes;
+  *e = 1;
+}
+
+__device__ __forceinline__ bool ch_wait0(Chain& c) {
+  if (!c.e0) return true;
+  const bool ok = mbar_wait(c.m0, c.p0);
+  c.p0 ^= 1u;
+  c.e0 = 0;
+  return ok;
+}
+
+__device__ __forceinline__ bool ch_wait1(Chain& c) {
+  if (!c.e1) return true;
+  const bool ok = mbar_wait(c.m1, c.p1);
+  c.p1 ^= 1u;
+  c.e1 = 0;
+  return ok;
+}
+
+// Starts the copy of the window that follows the current one.
+__device__ __forceinline__ void ch_prefetch(Chain& c) {
+  const int64_t nxt = c.w0 + c.n0 - COVL;
+  if (nxt < static_cast<int64_t>(c.slen))
+    ch_issue(c, c.b1, c.m1, nxt, &c.w1, &c.n1, &c.e1);
+  else
+    c.n1 = 0;
+}
+
+__device__ __forceinline__ void ch_init(Chain& c, uint8_t* buf0, uint8_t* buf1, uint64_t* bar0, uint64_t* bar1,
+                                        uint32_t par0, uint32_t par1) {
+  c.b0 = buf0;
+  c.b1 = buf1;
+  c.m0 = bar0;
+  c.m1 = bar1;
+  c.p0 = par0;
+  c.p1 = par1;
+  c.w0 = c.w1 = 0;
+  c.n0 = c.n1 = 0;
+  c.e0 = c.e1 = 0;
+  c.swapped = 0;
+  c.sb = nullptr;
+  c.slen = 0;
+}
+
+// Physical-buffer parities (to carry them across uses of the windows).
+__device__ __forceinline__ uint32_t ch_par(const Chain& c, int phys) {
+  return (phys == 0) == (c.swapped == 0) ? c.p0 : c.p1;
+}
+
+__device__ __forceinline__ bool ch_start(Chain& c, const uint8_t* sb, uint32_t slen) {
+  c.sb = sb;
+  c.slen = slen;
+  c.n1 = 0;
+  ch_issue(c, c.b0, c.m0, 0, &c.w0, &c.n0, &c.e0);
+  if (!ch_wait0(c)) return false;
+  ch_prefetch(c);
+  return true;
+}
+
+// Makes stream bytes [pos, pos + need) readable in the current window.
+__device__ __forceinline__ bool ch_ensure(Chain& c, int64_t pos, uint32_t need) {
+  int64_t o = pos - c.w0;
+  if (o >= 0 && o + need <= c.n0) return true;
+  if (!ch_wait1(c)) return false;
+  o = pos - c.w1;
+  if (c.n1 && o >= 0 && o + need <= c.n1) {
+    ch_swap(c);
+    ch_prefetch(c);
+    return true;
+  }
+  // a jump past the prefetched window: load at pos, then prefetch after it
+  ch_issue(c, c.b0, c.m0, pos, &c.w0, &c.n0, &c.e0);
+  if (!ch_wait0(c)) return false;
+  ch_prefetch(c);
+  return true;
+}
+
+__device__ __forceinline__ bool ch_drain(Chain& c) {
+  const bool a = ch_wait0(c);
+  const bool b = ch_wait1(c);
+  return a && b;
+}
+
+__device__ __forceinline__ const uint8_t* ch_ptr(const Chain& c, int64_t pos) { return c.b0 + (pos - c.w0); }
+
+// 8 bytes at stream position pos as two little-endian words (aligned loads).
+__device__ __forceinline__ void ch_read8(const Chain& c, int64_t pos, uint32_t* lo, uint32_t* hi) {
+  const uint32_t o = static_cast<uint32_t>(pos - c.w0);
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(c.b0) + (o >> 2);
+  const uint32_t sh = (o & 3) * 8;
+  const uint32_t a = w[0], b = w[1], d = w[2];
+  *lo = sh ? __funnelshift_r(a, b, sh) : a;
+  *hi = sh ? __funnelshift_r(b, d, sh) : b;
+}
+
+// ULEB128 from a window pointer with 16 readable bytes.
+__device__ __forceinline__ int uleb_p(const uint8_t* q, uint64_t* v) {
+  uint64_t r = 0;
+#pragma unroll 1
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t b = q[i];
+    r |= static_cast<uint64_t>(b & 0x7f) << (7 * i);
+    if (!(b & 0x80)) {
+      *v = r;
+      return i + 1;
+    }
+  }
+  return 0;
+}
+
+// ------------------------------------------------------------------ string dictionaries
+
+struct DictStrSmem {
+  uint64_t bar[2];
+  alignas(16) uint8_t win[2][CWIN + 16];
+};
+
+// BYTE_ARRAY dictionary: entries are (4-byte length, bytes) back to back; the
+// chain over them is followed by one thread through the double window.
+__global__ void __launch_bounds__(32) k_dict_str(const DictJob* __restrict__ jobs, DictDev* dicts, DevStatus* st) {
+  extern __shared__ __align__(16) uint8_t smraw[];
+  DictStrSmem& sm = *reinterpret_cast<DictStrSmem*>(smraw);
   const DictJob j = jobs[blockIdx.x];
-  if (j.ptype != T_BYTE_ARRAY) return;
-  if (threadIdx.x == 0) {
-    mbar_init(&sm.bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  Win win{sm.win, nullptr, WIN_BYTES, 0, &sm.bar, 0};
-  const uint8_t* body = j.body;
+  if (j.ptype != T_BYTE_ARRAY || threadIdx.x != 0) return;
+  mbar_init(&sm.bar[0], 1);
+  mbar_init(&sm.bar[1], 1);
+  fence_mbar_init();
+  Chain c;
+  ch_init(c, sm.win[0], sm.win[1], &sm.bar[0], &sm.bar[1], 0, 0);
   const uint32_t blen = static_cast<uint32_t>(j.body_len);
-  uint32_t pos = 0, k = 0, maxlen = 0;
+  if (!ch_start(c, j.body, blen)) {
+    report(st, DERR_TIMEOUT, j.page, WHERE_DICT, 3);
+    ch_drain(c);
+    return;
+  }
+  uint32_t pos = 0, maxlen = 0;
   bool bad = false;
-  if (!win_load(win, body, body + blen, st, j.page, WHERE_DICT)) return;
-  for (uint32_t guard = 0; guard <= blen + 1; ++guard) {
-    if (threadIdx.x == 0) {
-      uint32_t reload = 0;
-      while (k < static_cast<uint32_t>(j.n)) {
-        uint32_t wrel = static_cast<uint32_t>((body + pos) - win.g0);
-        if (pos + 4 > blen) { bad = true; break; }
-        if (wrel + 4 > win.n) { reload = 1; break; }
-        const uint8_t* q = win.s + wrel;
-        uint32_t len = q[0] | (q[1] << 8) | (q[2] << 16) | (static_cast<uint32_t>(q[3]) << 24);
-        if (len > blen - pos - 4) { bad = true; break; }
-        j.str_pos[k] = pos + 4;
-        j.str_len[k] = len;
-        maxlen = len > maxlen ? len : maxlen;
-        pos += 4 + len;
-        ++k;
-      }
-      sm.ctl[0] = reload;
-      sm.ctl[1] = bad ? 1u : 0u;
-      sm.ctl[2] = pos;
-    }
-    __syncthreads();
-    uint32_t reload = sm.ctl[0];
-    if (sm.ctl[1]) break;
-    if (!reload) break;
-    if (!win_load(win, body + sm.ctl[2], body + blen, st, j.page, WHERE_DICT)) return;
+  for (int32_t k = 0; k < j.n;) {
+    if (pos + 4 > blen) { bad = true; break; }
+    if (!ch_ensure(c, pos, 16)) { bad = true; break; }
+    // steps inside the current window: the length word, then the next entry
+    uint32_t o = static_cast<uint32_t>(pos - c.w0);
+    const uint32_t lim = c.n0 - 16;
+    const uint32_t wb = static_cast<uint32_t>(c.w0);
+    const uint32_t* w32 = reinterpret_cast<const uint32_t*>(c.b0);
+    do {
+      const uint32_t i = o >> 2, sh = (o & 3u) << 3;
+      const uint32_t len = __funnelshift_r(w32[i], w32[i + 1], sh);
+      const uint32_t p = o + wb;
+      if (p + 4 > blen || len > blen - p - 4) { bad = true; break; }
+      j.str_pos[k] = p + 4;
+      j.str_len[k] = len;
+      maxlen = len > maxlen ? len : maxlen;
+      o += 4 + len;
+      ++k;
+    } while (k < j.n && o <= lim);
+    if (bad) break;
+    pos = o + wb;
   }
-  if (threadIdx.x == 0) {
-    if (bad || k != static_cast<uint32_t>(j.n)) {
-      report(st, DERR_CORRUPT, j.page, WHERE_DICT, 2);
-      return;
-    }
-    DictDev d{};
-    d.str_pos = j.str_pos;
-    d.str_len = j.str_len;
-    d.chars = body;
-    d.n = j.n;
-    d.max_len = static_cast<int32_t>(maxlen);
-    d.valid = 1;
-    dicts[j.chunk] = d;
+  ch_drain(c);
+  if (bad) {
+    report(st, DERR_CORRUPT, j.page, WHERE_DICT, 2);
+    return;
   }
+  DictDev d{};
+  d.str_pos = j.str_pos;
+  d.str_len = j.str_len;
+  d.chars = j.body;
+  d.n = j.n;
+  d.max_len = static_cast<int32_t>(maxlen);
+  d.valid = 1;
+  dicts[j.chunk] = d;
 }
 
 void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, DictDev* dicts, int n_sms, DevStatus* st,
@@ -142,58 +321,25 @@ void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, DictDev* 
   if (gx < 1) gx = 1;
   if (gx > 4 * n_sms) gx = 4 * n_sms;
   k_dict_fixed<<<dim3(gx, n_jobs), 256, 0, s>>>(jobs, dicts, st);
-  k_dict_str<<<n_jobs, 128, 0, s>>>(jobs, dicts, st);
+  k_dict_str<<<n_jobs, 32, sizeof(DictStrSmem), s>>>(jobs, dicts, st);
 }
 
-// ------------------------------------------------------------------ shared layouts
+// ------------------------------------------------------------------ walk
 
 struct WalkSmem {
-  uint64_t bar;
+  uint64_t bar[2];
   int32_t ctl[16];
   int64_t c64[8];
-  // level runs of one batch
-  int32_t lrow[LV_BATCH];
-  int32_t lcnt[LV_BATCH];
-  uint32_t lmeta[LV_BATCH];  // bit 31 set: bit-packed, low bits = window bit position; else value
-  int32_t lpre[LV_BATCH];
-  // delta blocks of one batch
-  uint32_t bstart[BLK_BATCH];  // stream offset of the block
-  uint32_t bdata[BLK_BATCH];   // window offset of the first miniblock
-  uint32_t bwid[BLK_BATCH];    // window offset of the width bytes
-  int32_t bcnt[BLK_BATCH];     // values in the block
-  int32_t bk[BLK_BATCH];       // dense index of the block's first value
-  int64_t bmin[BLK_BATCH];
-  uint64_t bsum[BLK_BATCH];
+  uint32_t rpos[RB];   // hybrid: run header offset; levels: run data offset
+  int32_t rk[RB];      // hybrid: dense index at run start; levels: row at run start
+  int32_t rcnt[RB];    // levels: rows of the run inside the page
+  uint32_t rmeta[RB];  // levels: 0x80000000 bit-packed, else the repeated value
+  int32_t rpre[RB];    // levels: valid rows before the run (page-relative)
   int32_t tmp32[32];
-  alignas(16) uint8_t win[WIN_BYTES + 16];
+  alignas(16) uint8_t win[2][CWIN + 16];
 };
 
-struct ExpSmem {
-  uint64_t bar;
-  int32_t ctl[16];
-  int64_t c64[8];
-  uint32_t wbits[TILE_ROWS / 32];
-  uint32_t wpre[TILE_ROWS / 32];
-  int32_t sdst[SEG_MAX];
-  int32_t scnt[SEG_MAX];
-  uint32_t smeta[SEG_MAX];
-  uint32_t sval[SEG_MAX];
-  uint32_t dstart[DB_MAX];
-  uint32_t ddata[DB_MAX];
-  uint32_t dwid[DB_MAX];
-  int32_t dk[DB_MAX];
-  int32_t dcnt[DB_MAX];
-  int32_t dnext[DB_MAX];
-  int64_t dmin[DB_MAX];
-  uint64_t dsum[DB_MAX];
-  uint64_t dbase[DB_MAX];
-  uint32_t tmp32[32];
-  uint64_t tmp64[32];
-  alignas(16) uint64_t vbuf[TILE_ROWS];
-  alignas(16) uint8_t win[WIN_BYTES + 16];
-};
-
-// Page layout resolved by the walk and reused by the expansion.
+// Page layout.
 struct PageCtx {
   const uint8_t* body;
   uint32_t blen;
@@ -207,529 +353,6 @@ struct PageCtx {
   int32_t max_def;
 };
 
-// ------------------------------------------------------------------ walk: levels
-
-// k at row R of this batch: valid rows before R (R inside run j).
-__device__ __forceinline__ int32_t level_k_at(const WalkSmem& sm, const uint32_t* w32, int nb, int32_t R) {
-  int lo = 0, hi = nb - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (sm.lrow[mid] <= R) lo = mid; else hi = mid - 1;
-  }
-  int32_t off = R - sm.lrow[lo];
-  int32_t part;
-  uint32_t meta = sm.lmeta[lo];
-  if (meta & 0x80000000u) {
-    uint32_t bp = meta & 0x7fffffffu;
-    part = 0;
-    for (int32_t x = 0; x < off; x += 32) {
-      int n = off - x < 32 ? off - x : 32;
-      part += __popc(bits32(w32, bp + x, n));
-    }
-  } else {
-    part = static_cast<int32_t>(meta) * off;
-  }
-  return sm.lpre[lo] + part;
-}
-
-// Walks the definition levels [lv0, lv1) of a page: writes the validity
-// bits of rows [row_lo, row_hi) and the dense start (k0) / count (nn) of
-// every item.  Returns the page's non-null count (-1 on error).
-__device__ int32_t walk_levels(WalkSmem& sm, Win& win, const PageCtx& pc, const PlanPage& pp, Item* items,
-                               const OutCol& col, DevStatus* st) {
-  const int tid = threadIdx.x;
-  const uint8_t* sb = pc.body + pc.lv0;
-  const uint32_t slen = pc.lv1 - pc.lv0;
-  if (!win_load(win, sb, sb + slen, st, pc.pgid, WHERE_WALK_LEVELS)) return -1;
-  if (tid == 0) {
-    sm.ctl[0] = 0;  // stream position
-    sm.ctl[1] = 0;  // rows consumed
-    sm.ctl[5] = 0;  // error
-    sm.c64[0] = 0;  // valid rows before the batch
-    sm.c64[1] = -1; // k at row_hi when found inside the walk
-  }
-  __syncthreads();
-  const uint32_t* w32 = reinterpret_cast<const uint32_t*>(win.s);
-  for (uint32_t guard = 0; guard <= slen + 2; ++guard) {
-    if (tid == 0) {
-      uint32_t hp = static_cast<uint32_t>(sm.ctl[0]);
-      int32_t row = sm.ctl[1];
-      int nb = 0, reload = 0, err = 0;
-      while (nb < LV_BATCH && row < pc.nrows) {
-        if (hp >= slen) { err = 1; break; }
-        uint32_t wrel = static_cast<uint32_t>((sb + hp) - win.g0);
-        uint32_t lim_w = win.n, lim_s = wrel + (slen - hp);
-        uint32_t lim = lim_w < lim_s ? lim_w : lim_s;
-        uint64_t h = 0;
-        int hl = uleb([&](uint32_t q) { return static_cast<uint32_t>(win.s[q]); }, wrel, lim, &h);
-        if (hl == 0) {
-          if (lim == lim_s) err = 1; else reload = 1;
-          break;
-        }
-        int32_t take;
-        if (h & 1) {
-          uint64_t g = h >> 1;
-          if (g > slen) { err = 1; break; }
-          uint32_t nbody = static_cast<uint32_t>(g);  // bit width 1: one byte per group
-          if (hp + hl + nbody > slen) { err = 1; break; }
-          if (wrel + hl + nbody > win.n) {
-            if (wrel == 0) err = 2; else reload = 1;
-            break;
-          }
-          uint64_t c = g * 8;
-          take = static_cast<int32_t>(c < static_cast<uint64_t>(pc.nrows - row) ? c : (pc.nrows - row));
-          sm.lrow[nb] = row;
-          sm.lcnt[nb] = take;
-          sm.lmeta[nb] = 0x80000000u | ((wrel + hl) * 8);
-          hp += hl + nbody;
-        } else {
-          if (wrel + hl + 1 > win.n) {
-            if (hp + hl + 1 > slen) err = 1; else reload = 1;
-            break;
-          }
-          if (hp + hl + 1 > slen) { err = 1; break; }
-          uint32_t v = win.s[wrel + hl];
-          if (v > 1) { err = 1; break; }
-          uint64_t c = h >> 1;
-          take = static_cast<int32_t>(c < static_cast<uint64_t>(pc.nrows - row) ? c : (pc.nrows - row));
-          sm.lrow[nb] = row;
-          sm.lcnt[nb] = take;
-          sm.lmeta[nb] = v;
-          hp += hl + 1;
-        }
-        if (take > 0) {
-          row += take;
-          ++nb;
-        }
-      }
-      sm.ctl[0] = static_cast<int32_t>(hp);
-      sm.ctl[2] = nb;
-      sm.ctl[3] = reload;
-      sm.ctl[4] = row;
-      sm.ctl[5] = err;
-    }
-    __syncthreads();
-    const int nb = sm.ctl[2];
-    const int err = sm.ctl[5];
-    if (err) {
-      if (tid == 0) report(st, err == 2 ? DERR_UNSUPPORTED : DERR_CORRUPT, pc.pgid, WHERE_WALK_LEVELS, err);
-      return -1;
-    }
-    const int32_t b0 = sm.ctl[1];
-    const int32_t b1 = sm.ctl[4];
-    // (1) valid count per run, prefix over the batch
-    int32_t cnt = 0;
-    if (tid < nb) {
-      uint32_t meta = sm.lmeta[tid];
-      if (meta & 0x80000000u) {
-        uint32_t bp = meta & 0x7fffffffu;
-        for (int32_t x = 0; x < sm.lcnt[tid]; x += 32) {
-          int n = sm.lcnt[tid] - x < 32 ? sm.lcnt[tid] - x : 32;
-          cnt += __popc(bits32(w32, bp + x, n));
-        }
-      } else {
-        cnt = static_cast<int32_t>(meta) * sm.lcnt[tid];
-      }
-    }
-    int32_t total;
-    int32_t pre = block_exclusive_sum(cnt, sm.tmp32, &total);
-    const int64_t vb = sm.c64[0];
-    if (tid < nb) sm.lpre[tid] = static_cast<int32_t>(vb) + pre;
-    __syncthreads();
-    // (2) bitmap words of rows [max(b0,row_lo), min(b1,row_hi))
-    if (nb > 0 && col.validity) {
-      int32_t r_lo = b0 > pp.row_lo ? b0 : pp.row_lo;
-      int32_t r_hi = b1 < pp.row_hi ? b1 : pp.row_hi;
-      if (r_lo < r_hi) {
-        int64_t o0 = pp.out_row + r_lo, o1 = pp.out_row + r_hi;
-        int64_t w0 = o0 >> 5, w1 = (o1 - 1) >> 5;
-        for (int64_t w = w0 + tid; w <= w1; w += blockDim.x) {
-          int64_t a = w * 32 > o0 ? w * 32 : o0;
-          int64_t e = w * 32 + 32 < o1 ? w * 32 + 32 : o1;
-          uint32_t word = 0;
-          int32_t r = static_cast<int32_t>(a - pp.out_row);
-          const int32_t rend = static_cast<int32_t>(e - pp.out_row);
-          // run containing r
-          int lo = 0, hi = nb - 1;
-          while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (sm.lrow[mid] <= r) lo = mid; else hi = mid - 1;
-          }
-          for (int j = lo; j < nb && r < rend; ++j) {
-            int32_t s0 = r, s1 = sm.lrow[j] + sm.lcnt[j];
-            if (s1 > rend) s1 = rend;
-            if (s1 <= s0) continue;
-            int n = s1 - s0;
-            uint32_t meta = sm.lmeta[j];
-            uint32_t bitsv;
-            if (meta & 0x80000000u)
-              bitsv = bits32(w32, (meta & 0x7fffffffu) + (s0 - sm.lrow[j]), n);
-            else
-              bitsv = meta ? (n == 32 ? 0xffffffffu : ((1u << n) - 1)) : 0u;
-            word |= bitsv << static_cast<uint32_t>((pp.out_row + s0) - w * 32);
-            r = s1;
-          }
-          if (a == w * 32 && e == w * 32 + 32)
-            col.validity[w] = word;
-          else if (word)
-            atomicOr(col.validity + w, word);
-        }
-      }
-    }
-    // (3) item starts inside this batch
-    for (uint32_t i = tid; i <= pp.item_count; i += blockDim.x) {
-      int32_t R = i < pp.item_count ? pp.row_lo + static_cast<int32_t>(i) * ITEM_ROWS : pp.row_hi;
-      if (nb > 0 && R >= b0 && R < b1) {
-        int32_t kR = level_k_at(sm, w32, nb, R);
-        if (i < pp.item_count)
-          items[pp.item_begin + i].k0 = kR;
-        else
-          sm.c64[1] = kR;
-      }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      sm.c64[0] = vb + total;
-      sm.ctl[1] = b1;
-    }
-    const int reload = sm.ctl[3];
-    const bool done = b1 >= pc.nrows;
-    __syncthreads();
-    if (done) break;
-    if (reload) {
-      if (!win_load(win, sb + sm.ctl[0], sb + slen, st, pc.pgid, WHERE_WALK_LEVELS)) return -1;
-    } else if (nb == 0) {
-      if (tid == 0) report(st, DERR_CORRUPT, pc.pgid, WHERE_WALK_LEVELS, 9);
-      return -1;
-    }
-  }
-  __syncthreads();
-  const int32_t nonnull = static_cast<int32_t>(sm.c64[0]);
-  const int64_t k_hi = sm.c64[1] >= 0 ? sm.c64[1] : nonnull;
-  __syncthreads();
-  // item counts: nn_i = k_{i+1} - k_i
-  for (uint32_t i = tid; i < pp.item_count; i += blockDim.x) {
-    int32_t ka = items[pp.item_begin + i].k0;
-    int32_t kb = i + 1 < pp.item_count ? items[pp.item_begin + i + 1].k0 : static_cast<int32_t>(k_hi);
-    items[pp.item_begin + i].nn = kb - ka;
-  }
-  __syncthreads();
-  return nonnull;
-}
-
-// ------------------------------------------------------------------ walk: value streams
-
-// Dictionary indices: records (run header offset, dense index at run start)
-// for each item start.
-__device__ bool walk_hybrid(WalkSmem& sm, Win& win, const uint8_t* sb, uint32_t slen, int bw, int32_t total,
-                            const PlanPage& pp, Item* items, int pgid, DevStatus* st) {
-  const int tid = threadIdx.x;
-  if (!win_load(win, sb, sb + slen, st, pgid, WHERE_WALK_VALUES)) return false;
-  if (tid == 0) {
-    sm.ctl[0] = 0;  // header position
-    sm.ctl[1] = 0;  // dense index at that header
-    sm.ctl[2] = 0;  // next item
-  }
-  __syncthreads();
-  const uint32_t vbytes = (bw + 7) / 8;
-  for (uint32_t guard = 0; guard <= slen + 2; ++guard) {
-    if (tid == 0) {
-      uint32_t hp = static_cast<uint32_t>(sm.ctl[0]);
-      int32_t kk = sm.ctl[1];
-      uint32_t ni = static_cast<uint32_t>(sm.ctl[2]);
-      int reload = 0, err = 0, done = 0;
-      for (;;) {
-        while (ni < pp.item_count && items[pp.item_begin + ni].nn == 0) ++ni;
-        if (ni >= pp.item_count) { done = 1; break; }
-        if (kk >= total || hp >= slen) { err = 1; break; }
-        uint32_t wrel = static_cast<uint32_t>((sb + hp) - win.g0);
-        uint32_t lim_w = win.n, lim_s = wrel + (slen - hp);
-        uint32_t lim = lim_w < lim_s ? lim_w : lim_s;
-        uint64_t h = 0;
-        int hl = uleb([&](uint32_t q) { return static_cast<uint32_t>(win.s[q]); }, wrel, lim, &h);
-        if (hl == 0) {
-          if (lim == lim_s) err = 1; else reload = 1;
-          break;
-        }
-        uint64_t c, body;
-        if (h & 1) {
-          c = (h >> 1) * 8;
-          body = (h >> 1) * static_cast<uint64_t>(bw);
-        } else {
-          c = h >> 1;
-          body = vbytes;
-        }
-        if (hp + hl + body > slen) { err = 1; break; }
-        int64_t end = static_cast<int64_t>(kk) + static_cast<int64_t>(c);
-        while (ni < pp.item_count) {
-          Item& it = items[pp.item_begin + ni];
-          if (it.nn == 0) { ++ni; continue; }
-          if (it.k0 < end) {
-            it.pos = static_cast<int32_t>(hp);
-            it.run_k0 = kk;
-            it.base = 0;
-            ++ni;
-          } else {
-            break;
-          }
-        }
-        hp += hl + static_cast<uint32_t>(body);
-        kk = end > total ? total : static_cast<int32_t>(end);
-      }
-      sm.ctl[0] = static_cast<int32_t>(hp);
-      sm.ctl[1] = kk;
-      sm.ctl[2] = static_cast<int32_t>(ni);
-      sm.ctl[3] = reload;
-      sm.ctl[4] = err;
-      sm.ctl[5] = done;
-    }
-    __syncthreads();
-    if (sm.ctl[4]) {
-      if (tid == 0) report(st, DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 1);
-      return false;
-    }
-    if (sm.ctl[5]) return true;
-    if (!win_load(win, sb + sm.ctl[0], sb + slen, st, pgid, WHERE_WALK_VALUES)) return false;
-  }
-  if (tid == 0) report(st, DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 2);
-  return false;
-}
-
-struct DeltaHdr {
-  int32_t block, mbc, vpm, total, hlen;
-  int64_t first;
-};
-
-// Parses the DELTA_BINARY_PACKED header from global memory.
-__device__ bool delta_header(const uint8_t* sb, uint32_t slen, DeltaHdr* d) {
-  auto get = [&](uint32_t q) { return static_cast<uint32_t>(__ldg(sb + q)); };
-  uint64_t a, b, c, f;
-  uint32_t p = 0;
-  int n;
-  if (!(n = uleb(get, p, slen, &a))) return false;
-  p += n;
-  if (!(n = uleb(get, p, slen, &b))) return false;
-  p += n;
-  if (!(n = uleb(get, p, slen, &c))) return false;
-  p += n;
-  if (!(n = uleb(get, p, slen, &f))) return false;
-  p += n;
-  if (a == 0 || a % 128 || a > 4096 || b == 0 || b > 64 || a % b || (a / b) % 32 || c > 0x7fffffff) return false;
-  d->block = static_cast<int32_t>(a);
-  d->mbc = static_cast<int32_t>(b);
-  d->vpm = static_cast<int32_t>(a / b);
-  d->total = static_cast<int32_t>(c);
-  d->first = unzigzag(f);
-  d->hlen = static_cast<int32_t>(p);
-  return true;
-}
-
-// Parses one block header at window offset `wrel`: fills min delta, width
-// offset and data offset; returns the block's byte size (header included)
-// or 0 when it does not fit in [wrel, lim) (*need_more set) or is malformed.
-__device__ __forceinline__ uint32_t delta_block(const Win& win, uint32_t wrel, uint32_t lim, const DeltaHdr& d,
-                                                int32_t nvals, int type_bits, int64_t* mn, uint32_t* wpos,
-                                                uint32_t* dpos, int* need_more, int* bad) {
-  uint64_t z = 0;
-  int hl = uleb([&](uint32_t q) { return static_cast<uint32_t>(win.s[q]); }, wrel, lim, &z);
-  if (hl == 0) {
-    *need_more = 1;
-    return 0;
-  }
-  if (wrel + hl + d.mbc > lim) {
-    *need_more = 1;
-    return 0;
-  }
-  *mn = unzigzag(z);
-  *wpos = wrel + hl;
-  uint64_t bits = 0;
-  const int used = (nvals + d.vpm - 1) / d.vpm;  // miniblocks holding values
-  for (int m = 0; m < used; ++m) {
-    uint32_t w = win.s[wrel + hl + m];
-    if (static_cast<int>(w) > type_bits) {
-      *bad = 1;
-      return 0;
-    }
-    bits += static_cast<uint64_t>(w) * d.vpm;
-  }
-  uint32_t size = static_cast<uint32_t>(hl + d.mbc + bits / 8);
-  *dpos = wrel + hl + d.mbc;
-  if (wrel + size > lim) {
-    *need_more = 1;
-    return 0;
-  }
-  return size;
-}
-
-// Value v of a DELTA block (packed delta, min not added).
-__device__ __forceinline__ uint64_t delta_packed(const Win& win, uint32_t wpos, uint32_t dpos, int vpm, int v) {
-  const uint32_t* w32 = reinterpret_cast<const uint32_t*>(win.s);
-  int m = v / vpm;
-  uint64_t bit = static_cast<uint64_t>(dpos) * 8;
-  for (int q = 0; q < m; ++q) bit += static_cast<uint64_t>(win.s[wpos + q]) * vpm;
-  int w = win.s[wpos + m];
-  return bits64(w32, bit + static_cast<uint64_t>(v - m * vpm) * w, w);
-}
-
-// DELTA: walks blocks, sums them in parallel, and records for each item the
-// block containing its first value plus the value preceding that block.
-__device__ bool walk_delta(WalkSmem& sm, Win& win, const uint8_t* sb, uint32_t slen, int type_bits,
-                           int32_t total, const PlanPage& pp, Item* items, int pgid, DevStatus* st) {
-  const int tid = threadIdx.x;
-  DeltaHdr d;
-  bool ok = delta_header(sb, slen, &d);
-  if (!ok || d.total != total) {
-    if (tid == 0) report(st, ok ? DERR_CORRUPT : DERR_UNSUPPORTED, pgid, WHERE_WALK_VALUES, 3);
-    return false;
-  }
-  if (total == 0) return true;
-  if (!win_load(win, sb + d.hlen, sb + slen, st, pgid, WHERE_WALK_VALUES)) return false;
-  if (tid == 0) {
-    sm.ctl[0] = d.hlen;  // block position
-    sm.ctl[1] = 1;       // dense index of the block's first value
-    sm.ctl[2] = 0;       // next item
-    sm.c64[0] = d.first; // value preceding the block
-    // items starting at the first value
-    uint32_t ni = 0;
-    while (ni < pp.item_count) {
-      Item& it = items[pp.item_begin + ni];
-      if (it.nn != 0 && it.k0 > 0) break;
-      if (it.nn != 0) {
-        it.pos = d.hlen;
-        it.run_k0 = 1;
-        it.base = d.first;
-      }
-      ++ni;
-    }
-    sm.ctl[2] = static_cast<int32_t>(ni);
-  }
-  __syncthreads();
-  for (uint32_t guard = 0; guard <= slen + 2; ++guard) {
-    if (tid == 0) {
-      uint32_t bp = static_cast<uint32_t>(sm.ctl[0]);
-      int32_t kk = sm.ctl[1];
-      int nb = 0, reload = 0, bad = 0;
-      while (nb < BLK_BATCH && kk < total) {
-        if (bp >= slen) { bad = 1; break; }
-        uint32_t wrel = static_cast<uint32_t>((sb + bp) - win.g0);
-        uint32_t lim_w = win.n, lim_s = wrel + (slen - bp);
-        uint32_t lim = lim_w < lim_s ? lim_w : lim_s;
-        int32_t nvals = total - kk < d.block ? total - kk : d.block;
-        int64_t mn;
-        uint32_t wpos, dpos;
-        int more = 0;
-        uint32_t size = delta_block(win, wrel, lim, d, nvals, type_bits, &mn, &wpos, &dpos, &more, &bad);
-        if (bad) break;
-        if (size == 0) {
-          if (lim == lim_s) bad = 1; else if (wrel == 0) bad = 2; else reload = 1;
-          break;
-        }
-        sm.bstart[nb] = bp;
-        sm.bdata[nb] = dpos;
-        sm.bwid[nb] = wpos;
-        sm.bcnt[nb] = nvals;
-        sm.bk[nb] = kk;
-        sm.bmin[nb] = mn;
-        ++nb;
-        bp += size;
-        kk += nvals;
-      }
-      sm.ctl[3] = nb;
-      sm.ctl[4] = reload;
-      sm.ctl[5] = bad;
-      sm.ctl[6] = static_cast<int32_t>(bp);
-      sm.ctl[7] = kk;
-    }
-    __syncthreads();
-    const int nb = sm.ctl[3];
-    if (sm.ctl[5]) {
-      if (tid == 0) report(st, sm.ctl[5] == 2 ? DERR_UNSUPPORTED : DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 4);
-      return false;
-    }
-    for (int b = tid; b < nb; b += blockDim.x) {
-      uint64_t s = 0;
-      for (int v = 0; v < sm.bcnt[b]; ++v) s += delta_packed(win, sm.bwid[b], sm.bdata[b], d.vpm, v);
-      sm.bsum[b] = s + static_cast<uint64_t>(sm.bmin[b]) * static_cast<uint64_t>(sm.bcnt[b]);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      uint64_t prev = static_cast<uint64_t>(sm.c64[0]);
-      uint32_t ni = static_cast<uint32_t>(sm.ctl[2]);
-      for (int b = 0; b < nb; ++b) {
-        const int32_t end = sm.bk[b] + sm.bcnt[b];
-        while (ni < pp.item_count) {
-          Item& it = items[pp.item_begin + ni];
-          if (it.nn == 0) { ++ni; continue; }
-          if (it.k0 < end) {
-            it.pos = static_cast<int32_t>(sm.bstart[b]);
-            it.run_k0 = sm.bk[b];
-            it.base = static_cast<int64_t>(prev);
-            ++ni;
-          } else {
-            break;
-          }
-        }
-        prev += sm.bsum[b];
-      }
-      sm.c64[0] = static_cast<int64_t>(prev);
-      sm.ctl[2] = static_cast<int32_t>(ni);
-      sm.ctl[0] = sm.ctl[6];
-      sm.ctl[1] = sm.ctl[7];
-    }
-    __syncthreads();
-    if (sm.ctl[1] >= total) return true;
-    if (sm.ctl[4]) {
-      if (!win_load(win, sb + sm.ctl[0], sb + slen, st, pgid, WHERE_WALK_VALUES)) return false;
-    } else if (nb == 0) {
-      if (tid == 0) report(st, DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 5);
-      return false;
-    }
-  }
-  if (tid == 0) report(st, DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 6);
-  return false;
-}
-
-// PLAIN BYTE_ARRAY: serial walk over (length, bytes) values; records the
-// offset of each item's first value and the chars before it.
-__device__ bool walk_plain_ba(const uint8_t* sb, uint32_t slen, int32_t total, const PlanPage& pp, Item* items,
-                              int pgid, DevStatus* st) {
-  if (threadIdx.x == 0) {
-    uint32_t pos = 0;
-    int64_t chars = 0;
-    uint32_t ni = 0;
-    for (int32_t k = 0; k <= total; ++k) {
-      while (ni < pp.item_count) {
-        Item& it = items[pp.item_begin + ni];
-        if (it.nn == 0) { ++ni; continue; }
-        if (it.k0 == k) {
-          it.pos = static_cast<int32_t>(pos);
-          it.run_k0 = k;
-          it.base = chars;
-          ++ni;
-        } else {
-          break;
-        }
-      }
-      if (k == total) break;
-      if (pos + 4 > slen) {
-        report(st, DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 7);
-        return false;
-      }
-      uint32_t len = ld_le32_g(sb + pos);
-      if (len > slen - pos - 4) {
-        report(st, DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 8);
-        return false;
-      }
-      pos += 4 + len;
-      chars += len;
-    }
-  }
-  __syncthreads();
-  return true;
-}
-
-// Resolves the page layout; returns false (error recorded) when the page is
-// outside the supported subset or malformed.
 __device__ bool page_ctx(const DecodeArgs& a, const PlanPage& pp, PageCtx* pc) {
   const PageDev pg = a.pages[pp.page];
   const ChunkDev ch = a.chunks[pp.chunk];
@@ -745,7 +368,7 @@ __device__ bool page_ctx(const DecodeArgs& a, const PlanPage& pp, PageCtx* pc) {
   if (pg.page_type == PAGE_DATA) {
     if (ch.max_def) {
       if (pc->blen < 4) return false;
-      uint32_t L = ld_le32_g(pc->body);
+      const uint32_t L = ld_le32_g(pc->body);
       if (L > pc->blen - 4) return false;
       pc->lv0 = 4;
       pc->lv1 = 4 + L;
@@ -755,15 +378,559 @@ __device__ bool page_ctx(const DecodeArgs& a, const PlanPage& pp, PageCtx* pc) {
     if (pg.rep_len != 0) return false;
     if (static_cast<uint32_t>(pg.def_len) > pc->blen) return false;
     if (!ch.max_def && pg.def_len != 0) return false;
-    pc->lv0 = 0;
     pc->lv1 = static_cast<uint32_t>(pg.def_len);
     pc->v0 = pc->lv1;
   }
   return true;
 }
 
+__device__ __forceinline__ Chain make_chain(WalkSmem& sm) {
+  Chain c;
+  ch_init(c, sm.win[0], sm.win[1], &sm.bar[0], &sm.bar[1], static_cast<uint32_t>(sm.ctl[14]),
+          static_cast<uint32_t>(sm.ctl[15]));
+  return c;
+}
+
+__device__ __forceinline__ void keep_parity(WalkSmem& sm, const Chain& c) {
+  sm.ctl[14] = static_cast<int32_t>(ch_par(c, 0));
+  sm.ctl[15] = static_cast<int32_t>(ch_par(c, 1));
+}
+
+// Valid rows among the first `n` rows of level run j (bits from global memory).
+__device__ __forceinline__ int32_t run_valid(const WalkSmem& sm, const uint8_t* lsb, int j, int32_t n) {
+  const uint32_t meta = sm.rmeta[j];
+  if (!(meta & 0x80000000u)) return static_cast<int32_t>(meta) * n;
+  int32_t c = 0;
+  const uint64_t b0 = static_cast<uint64_t>(sm.rpos[j]) * 8;
+  for (int32_t x = 0; x < n; x += 32) {
+    const int m = n - x < 32 ? n - x : 32;
+    c += __popc(gbits32(lsb, b0 + x, m));
+  }
+  return c;
+}
+
+__device__ __forceinline__ int find_run(const int32_t* key, int nb, int32_t v) {
+  int lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (key[mid] <= v) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Definition levels of one page: validity bits of rows [row_lo, row_hi) and
+// the dense start (k0) / count (nn) of every item.  Returns the page's
+// non-null count, -1 on error.
+__device__ int32_t walk_levels(WalkSmem& sm, const PageCtx& pc, const PlanPage& pp, Item* items, const OutCol& col,
+                               DevStatus* st) {
+  const int tid = threadIdx.x;
+  const uint8_t* lsb = pc.body + pc.lv0;
+  const uint32_t slen = pc.lv1 - pc.lv0;
+  Chain c = make_chain(sm);
+  if (tid == 0) {
+    sm.ctl[0] = 0;   // chain position
+    sm.ctl[1] = 0;   // rows consumed
+    sm.c64[0] = 0;   // valid rows before the batch
+    sm.c64[1] = -1;  // k at row_hi
+    sm.ctl[5] = pc.nrows > 0 && !ch_start(c, lsb, slen) ? 3 : 0;
+  }
+  __syncthreads();
+  for (uint32_t guard = 0; guard <= slen + 2 && !sm.ctl[5] && sm.ctl[1] < pc.nrows; ++guard) {
+    if (tid == 0) {
+      uint32_t pos = static_cast<uint32_t>(sm.ctl[0]);
+      int32_t row = sm.ctl[1];
+      int nb = 0, err = 0;
+      while (nb < RB && row < pc.nrows) {
+        if (pos >= slen) { err = 1; break; }
+        if (!ch_ensure(c, pos, 16)) { err = 3; break; }
+        {
+          // fast steps: one-byte run headers inside the current window
+          uint32_t o = static_cast<uint32_t>(pos - c.w0);
+          const uint32_t lim = c.n0 - 16;
+          const uint32_t wb = static_cast<uint32_t>(c.w0);
+          const uint8_t* b = c.b0;
+          // software-pipelined: the next header is loaded before this run's bookkeeping
+          uint32_t h = o <= lim ? b[o] : 0x80u, v1 = o <= lim ? b[o + 1] : 0u;
+          while (nb < RB && row < pc.nrows && !(h & 0x80u)) {
+            const uint32_t g = h >> 1;
+            const uint32_t packed = h & 1u;
+            const uint32_t on = o + (packed ? 1 + g : 2);
+            const uint32_t hn = on <= lim ? b[on] : 0x80u;
+            const uint32_t vn = on <= lim ? b[on + 1] : 0u;
+            const uint32_t meta = packed ? 0x80000000u : v1;
+            if (!packed && v1 > 1) { err = 1; break; }
+            const uint32_t cnt = packed ? g << 3 : g;
+            const int32_t take = static_cast<int32_t>(cnt) < pc.nrows - row ? static_cast<int32_t>(cnt) : pc.nrows - row;
+            if (take > 0) {
+              sm.rpos[nb] = o + 1 + wb;
+              sm.rk[nb] = row;
+              sm.rcnt[nb] = take;
+              sm.rmeta[nb] = meta;
+              ++nb;
+              row += take;
+            }
+            o = on;
+            h = hn;
+            v1 = vn;
+          }
+          pos = o + wb;
+          if (err) break;
+          if (nb >= RB || row >= pc.nrows) break;
+          if (pos > slen) { err = 1; break; }
+          if (pos >= slen) { err = 1; break; }
+          if (!ch_ensure(c, pos, 16)) { err = 3; break; }
+        }
+        const uint8_t* q = ch_ptr(c, pos);
+        uint64_t h;
+        int hl;
+        if (q[0] < 0x80) {
+          h = q[0];
+          hl = 1;
+        } else {
+          hl = uleb_p(q, &h);
+          if (!hl) { err = 1; break; }
+        }
+        int64_t cnt;
+        uint32_t meta, adv;
+        if (h & 1) {
+          const uint64_t g = h >> 1;
+          if (g > slen) { err = 1; break; }
+          cnt = static_cast<int64_t>(g) * 8;
+          adv = hl + static_cast<uint32_t>(g);
+          meta = 0x80000000u;
+        } else {
+          cnt = static_cast<int64_t>(h >> 1);
+          adv = hl + 1;
+          meta = q[hl];
+          if (meta > 1) { err = 1; break; }
+        }
+        if (static_cast<uint64_t>(pos) + adv > slen) { err = 1; break; }
+        const int32_t take = static_cast<int32_t>(cnt < pc.nrows - row ? cnt : pc.nrows - row);
+        if (take > 0) {
+          sm.rpos[nb] = pos + hl;
+          sm.rk[nb] = row;
+          sm.rcnt[nb] = take;
+          sm.rmeta[nb] = meta;
+          ++nb;
+          row += take;
+        }
+        pos += adv;
+      }
+      sm.ctl[0] = static_cast<int32_t>(pos);
+      sm.ctl[2] = nb;
+      sm.ctl[4] = row;
+      sm.ctl[5] = err;
+    }
+    __syncthreads();
+    if (sm.ctl[5]) break;
+    const int nb = sm.ctl[2];
+    const int32_t b0 = sm.ctl[1], b1 = sm.ctl[4];
+    // valid counts per run, prefix over the batch (4 consecutive runs per thread)
+    int32_t loc[4];
+    int32_t mine = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = tid * 4 + q;
+      loc[q] = j < nb ? run_valid(sm, lsb, j, sm.rcnt[j]) : 0;
+      mine += loc[q];
+    }
+    int32_t total;
+    const int32_t pre = block_exclusive_sum(mine, sm.tmp32, &total);
+    const int32_t vb = static_cast<int32_t>(sm.c64[0]);
+    {
+      int32_t run = vb + pre;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = tid * 4 + q;
+        if (j < nb) sm.rpre[j] = run;
+        run += loc[q];
+      }
+    }
+    __syncthreads();
+    // validity bits of rows [max(b0,row_lo), min(b1,row_hi))
+    if (nb > 0 && col.validity) {
+      const int32_t r_lo = b0 > pp.row_lo ? b0 : pp.row_lo;
+      const int32_t r_hi = b1 < pp.row_hi ? b1 : pp.row_hi;
+      if (r_lo < r_hi) {
+        const int64_t o0 = pp.out_row + r_lo, o1 = pp.out_row + r_hi;
+        const int64_t w0 = o0 >> 5, w1 = (o1 - 1) >> 5;
+        for (int64_t w = w0 + tid; w <= w1; w += blockDim.x) {
+          const int64_t a0 = w * 32 > o0 ? w * 32 : o0;
+          const int64_t e0 = w * 32 + 32 < o1 ? w * 32 + 32 : o1;
+          uint32_t word = 0;
+          int32_t r = static_cast<int32_t>(a0 - pp.out_row);
+          const int32_t rend = static_cast<int32_t>(e0 - pp.out_row);
+          for (int j = find_run(sm.rk, nb, r); j < nb && r < rend; ++j) {
+            int32_t s1 = sm.rk[j] + sm.rcnt[j];
+            if (s1 > rend) s1 = rend;
+            if (s1 <= r) continue;
+            const int n = s1 - r;
+            const uint32_t meta = sm.rmeta[j];
+            uint32_t bitsv;
+            if (meta & 0x80000000u)
+              bitsv = gbits32(lsb, static_cast<uint64_t>(sm.rpos[j]) * 8 + (r - sm.rk[j]), n);
+            else
+              bitsv = meta ? (n == 32 ? 0xffffffffu : ((1u << n) - 1u)) : 0u;
+            word |= bitsv << static_cast<uint32_t>((pp.out_row + r) - w * 32);
+            r = s1;
+          }
+          if (a0 == w * 32 && e0 == w * 32 + 32)
+            col.validity[w] = word;
+          else if (word)
+            atomicOr(col.validity + w, word);
+        }
+      }
+    }
+    // dense index at each item start (and at row_hi) inside the batch
+    for (uint32_t i = tid; i <= pp.item_count; i += blockDim.x) {
+      const int32_t R = i < pp.item_count ? items[pp.item_begin + i].row0 : pp.row_hi;
+      if (nb > 0 && R >= b0 && R < b1) {
+        const int j = find_run(sm.rk, nb, R);
+        const int32_t kR = sm.rpre[j] + run_valid(sm, lsb, j, R - sm.rk[j]);
+        if (i < pp.item_count)
+          items[pp.item_begin + i].k0 = kR;
+        else
+          sm.c64[1] = kR;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      sm.c64[0] = vb + total;
+      sm.ctl[1] = b1;
+      if (nb == 0 && b1 < pc.nrows) sm.ctl[5] = 1;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (!ch_drain(c) && !sm.ctl[5]) sm.ctl[5] = 3;
+    if (!sm.ctl[5] && sm.ctl[1] < pc.nrows) sm.ctl[5] = 1;
+    keep_parity(sm, c);
+  }
+  __syncthreads();
+  if (sm.ctl[5]) {
+    if (tid == 0) report(st, sm.ctl[5] == 3 ? DERR_TIMEOUT : DERR_CORRUPT, pc.pgid, WHERE_WALK_LEVELS, sm.ctl[5]);
+    return -1;
+  }
+  const int32_t nonnull = static_cast<int32_t>(sm.c64[0]);
+  const int32_t k_hi = sm.c64[1] >= 0 ? static_cast<int32_t>(sm.c64[1]) : nonnull;
+  for (uint32_t i = tid; i < pp.item_count; i += blockDim.x) {
+    const int32_t ka = items[pp.item_begin + i].k0;
+    const int32_t kb = i + 1 < pp.item_count ? items[pp.item_begin + i + 1].k0 : k_hi;
+    items[pp.item_begin + i].nn = kb - ka;
+  }
+  __syncthreads();
+  return nonnull;
+}
+
+// Dictionary indices: checkpoints (run header offset, dense index at run
+// start) for every item with values.
+__device__ bool walk_hybrid(WalkSmem& sm, const uint8_t* sb, uint32_t slen, int bw, int32_t total,
+                            const PlanPage& pp, Item* items, int pgid, DevStatus* st) {
+  const int tid = threadIdx.x;
+  const uint32_t vbytes = (bw + 7) / 8;
+  Chain c = make_chain(sm);
+  if (tid == 0) {
+    sm.ctl[0] = 0;  // position
+    sm.ctl[1] = 0;  // dense index
+    sm.ctl[5] = ch_start(c, sb, slen) ? 0 : 3;
+  }
+  __syncthreads();
+  for (uint32_t guard = 0; guard <= slen + 2 && !sm.ctl[5] && sm.ctl[1] < total; ++guard) {
+    if (tid == 0) {
+      uint32_t pos = static_cast<uint32_t>(sm.ctl[0]);
+      int64_t k = sm.ctl[1];
+      int nb = 0, err = 0;
+      while (nb < RB && k < total) {
+        if (pos >= slen) { err = 1; break; }
+        if (!ch_ensure(c, pos, 16)) { err = 3; break; }
+        {
+          // fast steps: one-byte run headers inside the current window
+          uint32_t o = static_cast<uint32_t>(pos - c.w0);
+          const uint32_t lim = c.n0 - 16;
+          const uint32_t wb = static_cast<uint32_t>(c.w0);
+          const uint8_t* b = c.b0;
+          int32_t kk = static_cast<int32_t>(k);
+          // software-pipelined: the next header is loaded before this run's bookkeeping
+          uint32_t h = o <= lim ? b[o] : 0x80u;
+          while (nb < RB && kk < total && !(h & 0x80u)) {
+            const uint32_t g = h >> 1;
+            const uint32_t packed = h & 1u;
+            const uint32_t on = o + 1 + (packed ? g * static_cast<uint32_t>(bw) : vbytes);
+            const uint32_t hn = on <= lim ? b[on] : 0x80u;
+            const uint32_t cnt = packed ? g << 3 : g;
+            sm.rpos[nb] = o + wb;
+            sm.rk[nb] = kk;
+            ++nb;
+            kk = static_cast<int32_t>(cnt) < total - kk ? kk + static_cast<int32_t>(cnt) : total;
+            o = on;
+            h = hn;
+          }
+          pos = o + wb;
+          k = kk;
+          if (nb >= RB || k >= total) {
+            if (pos > slen) err = 1;
+            break;
+          }
+          if (pos >= slen) { err = 1; break; }
+          if (!ch_ensure(c, pos, 16)) { err = 3; break; }
+        }
+        const uint8_t* q = ch_ptr(c, pos);
+        uint64_t h;
+        int hl;
+        if (q[0] < 0x80) {
+          h = q[0];
+          hl = 1;
+        } else {
+          hl = uleb_p(q, &h);
+          if (!hl) { err = 1; break; }
+        }
+        uint64_t cnt, adv;
+        if (h & 1) {
+          cnt = (h >> 1) << 3;
+          adv = hl + (h >> 1) * static_cast<uint64_t>(bw);
+        } else {
+          cnt = h >> 1;
+          adv = hl + vbytes;
+        }
+        if (static_cast<uint64_t>(pos) + adv > slen) { err = 1; break; }
+        sm.rpos[nb] = pos;
+        sm.rk[nb] = static_cast<int32_t>(k);
+        ++nb;
+        pos += static_cast<uint32_t>(adv);
+        k = k + static_cast<int64_t>(cnt) > total ? total : k + static_cast<int64_t>(cnt);
+      }
+      sm.ctl[0] = static_cast<int32_t>(pos);
+      sm.ctl[2] = nb;
+      sm.ctl[3] = static_cast<int32_t>(k);
+      sm.ctl[5] = err;
+    }
+    __syncthreads();
+    if (sm.ctl[5]) break;
+    const int nb = sm.ctl[2];
+    const int32_t kb0 = sm.ctl[1], kb1 = sm.ctl[3];
+    for (uint32_t i = tid; i < pp.item_count; i += blockDim.x) {
+      Item& it = items[pp.item_begin + i];
+      const int32_t ik = it.k0;
+      if (nb > 0 && it.nn > 0 && ik >= kb0 && ik < kb1) {
+        const int j = find_run(sm.rk, nb, ik);
+        it.pos = static_cast<int32_t>(sm.rpos[j]);
+        it.run_k0 = sm.rk[j];
+        it.base = 0;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      sm.ctl[1] = kb1;
+      if (nb == 0 && kb1 < total) sm.ctl[5] = 1;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (!ch_drain(c) && !sm.ctl[5]) sm.ctl[5] = 3;
+    if (!sm.ctl[5] && sm.ctl[1] < total) sm.ctl[5] = 1;
+    keep_parity(sm, c);
+  }
+  __syncthreads();
+  if (sm.ctl[5]) {
+    if (tid == 0) report(st, sm.ctl[5] == 3 ? DERR_TIMEOUT : DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 1);
+    return false;
+  }
+  return true;
+}
+
+struct DeltaHdr {
+  int32_t block, mbc, vpm, total, hlen;
+  int64_t first;
+};
+
+// DELTA_BINARY_PACKED header: block size (multiple of 128, <= 4096),
+// miniblocks per block (<= 32, values per miniblock a multiple of 32),
+// total values, first value.
+__device__ bool delta_header(const uint8_t* sb, uint32_t slen, DeltaHdr* d) {
+  auto get = [&](uint32_t q) { return static_cast<uint32_t>(__ldg(sb + q)); };
+  uint64_t a, b, c, f;
+  uint32_t p = 0;
+  int n;
+  if (!(n = uleb(get, p, slen, &a))) return false;
+  p += n;
+  if (!(n = uleb(get, p, slen, &b))) return false;
+  p += n;
+  if (!(n = uleb(get, p, slen, &c))) return false;
+  p += n;
+  if (!(n = uleb(get, p, slen, &f))) return false;
+  p += n;
+  if (a == 0 || a % 128 || a > 4096 || b == 0 || b > 32 || a % b || (a / b) % 32 || c > 0x7fffffff) return false;
+  d->block = static_cast<int32_t>(a);
+  d->mbc = static_cast<int32_t>(b);
+  d->vpm = static_cast<int32_t>(a / b);
+  d->total = static_cast<int32_t>(c);
+  d->first = unzigzag(f);
+  d->hlen = static_cast<int32_t>(p);
+  return true;
+}
+
+// DELTA: thread 0 follows the block chain and records every block's stream
+// offset.  The common layout (4 miniblocks of 32 values, one-byte min delta,
+// a full block) takes the fast step: size = 5 + 4 * (sum of the 4 widths).
+__device__ bool walk_delta(WalkSmem& sm, const uint8_t* sb, uint32_t slen, int type_bits, int32_t total,
+                           PlanPage* ppw, uint32_t* dpos, uint32_t dcap, int pgid, DevStatus* st) {
+  if (threadIdx.x == 0) {
+    int err = 0;
+    DeltaHdr d{};
+    if (!delta_header(sb, slen, &d)) err = 2;
+    else if (d.total != total) err = 1;
+    int32_t nblocks = 0;
+    Chain c = make_chain(sm);
+    if (!err && total > 1) {
+      if (!ch_start(c, sb, slen)) err = 3;
+      int64_t pos = d.hlen;
+      int64_t k = 1;
+      const bool fast_layout = d.mbc == 4 && d.vpm == 32;
+      const int64_t full_end = 1 + static_cast<int64_t>((total - 1) / d.block) * d.block;  // k after the full blocks
+      while (!err && k < total) {
+        if (pos >= slen || static_cast<uint32_t>(nblocks) >= dcap) { err = 1; break; }
+        if (!ch_ensure(c, pos, 48)) { err = 3; break; }
+        if (fast_layout && k < full_end) {
+          // fast steps: size = 5 + 4 * (sum of the 4 width bytes), all in registers
+          uint32_t o = static_cast<uint32_t>(pos - c.w0);
+          const uint32_t lim = c.n0 - 48;
+          const uint32_t wb = static_cast<uint32_t>(c.w0);
+          const uint32_t* w32 = reinterpret_cast<const uint32_t*>(c.b0);
+          uint32_t left = static_cast<uint32_t>((full_end - k) / d.block);
+          const uint32_t room = dcap - static_cast<uint32_t>(nblocks);
+          if (left > room) left = room;
+          uint32_t* out = dpos + nblocks;
+          uint32_t done = 0;
+          // software-pipelined: the next block's header words are loaded
+          // before this block's position is stored
+          uint32_t x0 = 0, x1 = 0, x2 = 0;
+          if (o <= lim) {
+            const uint32_t i = o >> 2;
+            x0 = w32[i];
+            x1 = w32[i + 1];
+            x2 = w32[i + 2];
+          }
+          while (done < left && o <= lim) {
+            const uint32_t sh = (o & 3u) << 3;
+            const uint32_t lo = __funnelshift_r(x0, x1, sh);
+            const uint32_t hi = __funnelshift_r(x1, x2, sh);
+            const uint32_t wid = __funnelshift_r(lo, hi, 8);
+            if ((lo | wid) & 0x80u || wid & 0x80808080u) break;
+            const uint32_t on = o + 5u + 4u * __dp4a(wid, 0x01010101u, 0u);
+            if (on <= lim) {
+              const uint32_t i = on >> 2;
+              x0 = w32[i];
+              x1 = w32[i + 1];
+              x2 = w32[i + 2];
+            }
+            out[done++] = o + wb;
+            o = on;
+          }
+          nblocks += static_cast<int32_t>(done);
+          k += static_cast<int64_t>(done) * d.block;
+          pos = o + wb;
+          if (k >= total) break;
+          if (pos >= slen || static_cast<uint32_t>(nblocks) >= dcap) { err = 1; break; }
+          if (!ch_ensure(c, pos, 48)) { err = 3; break; }
+        }
+        const int32_t nv = total - k < d.block ? static_cast<int32_t>(total - k) : d.block;
+        uint32_t size;
+        uint32_t lo, hi;
+        ch_read8(c, pos, &lo, &hi);
+        const uint32_t widths = (lo >> 8) | (hi << 24);
+        if (fast_layout && nv == d.block && !(lo & 0x80u) && !(widths & 0x80808080u)) {
+          size = 5u + 4u * __dp4a(widths, 0x01010101u, 0u);
+        } else {
+          if (!ch_ensure(c, pos, 48)) { err = 3; break; }
+          const uint8_t* q = ch_ptr(c, pos);
+          uint64_t z;
+          const int vl = uleb_p(q, &z);
+          if (!vl) { err = 1; break; }
+          const int used = (nv + d.vpm - 1) / d.vpm;
+          uint64_t bits = 0;
+          for (int m = 0; m < used; ++m) {
+            const uint32_t w = q[vl + m];
+            if (static_cast<int>(w) > type_bits) { err = 1; break; }
+            bits += static_cast<uint64_t>(w) * d.vpm;
+          }
+          if (err) break;
+          size = static_cast<uint32_t>(vl + d.mbc + bits / 8);
+        }
+        if (pos + size > slen) { err = 1; break; }
+        dpos[nblocks++] = static_cast<uint32_t>(pos);
+        pos += size;
+        k += nv;
+      }
+      if (!err && pos > slen) err = 1;
+      if (!ch_drain(c) && !err) err = 3;
+    }
+    keep_parity(sm, c);
+    if (err) {
+      report(st, err == 3 ? DERR_TIMEOUT : (err == 2 ? DERR_UNSUPPORTED : DERR_CORRUPT), pgid, WHERE_WALK_VALUES, 3);
+      ppw->dblocks = -1;
+    } else {
+      ppw->dblocks = nblocks;
+      ppw->dfirst = d.first;
+      ppw->dbs = d.block;
+      ppw->dvpm = d.vpm;
+      ppw->dmbc = d.mbc;
+    }
+    sm.ctl[5] = err;
+  }
+  __syncthreads();
+  return sm.ctl[5] == 0;
+}
+
+// PLAIN BYTE_ARRAY: thread 0 follows the (length, bytes) chain and records
+// for every item the offset of its first value and the chars before it.
+__device__ bool walk_plain_ba(WalkSmem& sm, const uint8_t* sb, uint32_t slen, int32_t total, const PlanPage& pp,
+                              Item* items, int pgid, DevStatus* st) {
+  if (threadIdx.x == 0) {
+    int err = 0;
+    Chain c = make_chain(sm);
+    uint32_t pos = 0;
+    int64_t chars = 0;
+    int32_t nk0 = 0;
+    auto next_item = [&](uint32_t from) -> uint32_t {
+      for (; from < pp.item_count; ++from) {
+        const Item& it = items[pp.item_begin + from];
+        if (it.nn > 0) {
+          nk0 = it.k0;
+          return from;
+        }
+      }
+      return from;
+    };
+    uint32_t ni = next_item(0);
+    if (total > 0 && !ch_start(c, sb, slen)) err = 3;
+    for (int32_t k = 0; !err && k <= total; ++k) {
+      while (ni < pp.item_count && nk0 == k) {
+        Item& it = items[pp.item_begin + ni];
+        it.pos = static_cast<int32_t>(pos);
+        it.run_k0 = k;
+        it.base = chars;
+        ni = next_item(ni + 1);
+      }
+      if (k == total) break;
+      if (pos + 4 > slen) { err = 1; break; }
+      if (!ch_ensure(c, pos, 16)) { err = 3; break; }
+      uint32_t len, hi;
+      ch_read8(c, pos, &len, &hi);
+      if (len > slen - pos - 4) { err = 1; break; }
+      pos += 4 + len;
+      chars += len;
+    }
+    if (total > 0 && !ch_drain(c) && !err) err = 3;
+    keep_parity(sm, c);
+    if (err) report(st, err == 3 ? DERR_TIMEOUT : DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 7);
+    sm.ctl[5] = err;
+  }
+  __syncthreads();
+  return sm.ctl[5] == 0;
+}
+
 // Walk of one page (block-collective).
-__device__ void walk_page(const DecodeArgs& a, int p, WalkSmem& sm, Win& win) {
+__device__ void walk_page(const DecodeArgs& a, int p, WalkSmem& sm) {
   const int tid = threadIdx.x;
   const PlanPage pp = a.pps[p];
   const PageDev pg = a.pages[pp.page];
@@ -780,57 +947,46 @@ __device__ void walk_page(const DecodeArgs& a, int p, WalkSmem& sm, Win& win) {
   }
   int32_t nonnull;
   if (pc.max_def) {
-    nonnull = walk_levels(sm, win, pc, pp, a.items, col, a.st);
+    nonnull = walk_levels(sm, pc, pp, a.items, col, a.st);
     if (nonnull < 0) return;
     if (pg.page_type == PAGE_DATA_V2 && pg.num_nulls != pc.nrows - nonnull) {
       if (tid == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_WALK_LEVELS, 12);
       return;
     }
   } else {
-    nonnull = pc.nrows;
-    for (uint32_t i = tid; i < pp.item_count; i += blockDim.x) {
-      Item& it = a.items[pp.item_begin + i];
-      it.k0 = it.row0;
-      it.nn = it.nrows;
-    }
-    __syncthreads();
+    nonnull = pc.nrows;  // items carry k0 = row0, nn = nrows from the planner
   }
   const uint8_t* sb = pc.body + pc.v0;
   const uint32_t slen = pc.blen - pc.v0;
   bool ok = true;
   if (pc.enc == ENC_PLAIN) {
     if (pc.ptype == T_BYTE_ARRAY) {
-      ok = walk_plain_ba(sb, slen, nonnull, pp, a.items, pgid, a.st);
+      ok = walk_plain_ba(sm, sb, slen, nonnull, pp, a.items, pgid, a.st);
     } else if (static_cast<uint64_t>(nonnull) * pc.width > slen) {
       if (tid == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 9);
       ok = false;
     }
   } else if (pc.enc == ENC_RLE_DICT || pc.enc == ENC_PLAIN_DICT) {
-    const DictDev dd = a.dicts[pp.dict >= 0 ? pp.dict : 0];
     if (pp.dict < 0) {
       if (tid == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 10);
       ok = false;
     } else if (nonnull > 0) {
-      if (slen < 1) {
-        if (tid == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 11);
+      const int bw = slen >= 1 ? __ldg(sb) : 255;
+      if (bw > 32) {
+        if (tid == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 12);
         ok = false;
       } else {
-        int bw = __ldg(sb);
-        if (bw > 32) {
-          if (tid == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 12);
-          ok = false;
-        } else {
-          ok = walk_hybrid(sm, win, sb + 1, slen - 1, bw, nonnull, pp, a.items, pgid, a.st);
-        }
+        ok = walk_hybrid(sm, sb + 1, slen - 1, bw, nonnull, pp, a.items, pgid, a.st);
       }
     }
-    (void)dd;
   } else if (pc.enc == ENC_DELTA_BP) {
     if (pc.ptype != T_INT32 && pc.ptype != T_INT64) {
       if (tid == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 13);
       ok = false;
     } else {
-      ok = walk_delta(sm, win, sb, slen, pc.ptype == T_INT32 ? 32 : 64, nonnull, pp, a.items, pgid, a.st);
+      const uint32_t cap = static_cast<uint32_t>(nonnull > 1 ? (nonnull - 2) / 128 + 1 : 0);
+      ok = walk_delta(sm, sb, slen, pc.ptype == T_INT32 ? 32 : 64, nonnull, a.pps + p, a.dpos + pp.dtab, cap, pgid,
+                      a.st);
     }
   } else {
     if (tid == 0) report(a.st, DERR_UNSUPPORTED, pgid, WHERE_WALK_VALUES, 14);
@@ -843,348 +999,174 @@ __device__ void walk_page(const DecodeArgs& a, int p, WalkSmem& sm, Win& win) {
   __syncthreads();
 }
 
+__device__ __forceinline__ void walk_init(WalkSmem& sm) {
+  if (threadIdx.x == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    fence_mbar_init();
+    sm.ctl[14] = sm.ctl[15] = 0;
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(WALK_THREADS) k_walk(DecodeArgs a) {
   extern __shared__ __align__(16) uint8_t smraw[];
   WalkSmem& sm = *reinterpret_cast<WalkSmem*>(smraw);
-  if (threadIdx.x == 0) {
-    mbar_init(&sm.bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  Win win{sm.win, nullptr, WIN_BYTES, 0, &sm.bar, 0};
-  for (int p = blockIdx.x; p < a.n_pp; p += gridDim.x) walk_page(a, p, sm, win);
-}
-
-// ------------------------------------------------------------------ expand
-
-// Validity of tile rows [orow, orow + nt): word bits and ranks in shared
-// memory; returns the number of valid rows.
-__device__ int32_t tile_validity(ExpSmem& sm, const OutCol& col, int64_t orow, int nt) {
-  const int nw = (nt + 31) >> 5;
-  uint32_t bits = 0;
-  if (threadIdx.x < nw) {
-    int64_t b = orow + threadIdx.x * 32;
-    int n = nt - static_cast<int>(threadIdx.x) * 32;
-    if (n > 32) n = 32;
-    int64_t wi = b >> 5;
-    uint32_t sh = static_cast<uint32_t>(b & 31);
-    uint32_t lo = col.validity[wi];
-    uint32_t hi = (sh && (b & 31) + n > 32) ? col.validity[wi + 1] : 0u;
-    bits = sh ? __funnelshift_r(lo, hi, sh) : lo;
-    if (n < 32) bits &= (1u << n) - 1;
-  }
-  uint32_t total;
-  uint32_t pre = block_exclusive_sum(static_cast<uint32_t>(__popc(bits)), sm.tmp32, &total);
-  if (threadIdx.x < nw) {
-    sm.wbits[threadIdx.x] = bits;
-    sm.wpre[threadIdx.x] = pre;
-  }
-  __syncthreads();
-  return static_cast<int32_t>(total);
-}
-
-__device__ __forceinline__ int32_t row_rank(const ExpSmem& sm, int r, bool* valid) {
-  uint32_t w = sm.wbits[r >> 5];
-  uint32_t b = static_cast<uint32_t>(r & 31);
-  *valid = (w >> b) & 1u;
-  return static_cast<int32_t>(sm.wpre[r >> 5] + __popc(w & ((1u << b) - 1u)));
-}
-
-// Hybrid (dictionary index) stream state, kept in ctl/c64 between tiles.
-//  ctl[0] hp      next run header (stream offset)
-//  ctl[1] kk      dense index of the next value
-//  ctl[2] left    values left in the current run
-//  ctl[3] rle     current run is repeated
-//  c64[0] cur     repeated value, or stream bit position of the next packed value
-__device__ bool hyb_tile(ExpSmem& sm, Win& win, const uint8_t* sb, uint32_t slen, int bw, int32_t total,
-                         int32_t kneed, int nvals, const DictDev& dd, int ptype, int pgid, DevStatus* st) {
-  const int tid = threadIdx.x;
-  const uint32_t* w32 = reinterpret_cast<const uint32_t*>(win.s);
-  const uint32_t vbytes = (bw + 7) / 8;
-  int produced = 0;
-  for (uint32_t guard = 0; guard < 4u * (slen + 64) && produced < nvals; ++guard) {
-    if (tid == 0) {
-      uint32_t hp = static_cast<uint32_t>(sm.ctl[0]);
-      int32_t kk = sm.ctl[1];
-      int32_t left = sm.ctl[2];
-      int rle = sm.ctl[3];
-      uint64_t cur = static_cast<uint64_t>(sm.c64[0]);
-      int nseg = 0, reload = 0, err = 0;
-      int prod = produced;
-      const int64_t wbit0 = (sb - win.g0) * 8;  // window bit of stream bit 0
-      while (prod < nvals && nseg < SEG_MAX) {
-        if (left == 0) {
-          if (kk >= total || hp >= slen) { err = 1; break; }
-          int64_t wrel_s = (sb + hp) - win.g0;
-          if (wrel_s < 0 || wrel_s >= win.n) { reload = 1; break; }
-          uint32_t wrel = static_cast<uint32_t>(wrel_s);
-          uint32_t lim_w = win.n, lim_s = wrel + (slen - hp);
-          uint32_t lim = lim_w < lim_s ? lim_w : lim_s;
-          uint64_t h = 0;
-          int hl = uleb([&](uint32_t q) { return static_cast<uint32_t>(win.s[q]); }, wrel, lim, &h);
-          if (hl == 0) {
-            if (lim == lim_s) err = 1; else reload = 1;
-            break;
-          }
-          uint64_t c;
-          if (h & 1) {
-            c = (h >> 1) * 8;
-            uint64_t body = (h >> 1) * static_cast<uint64_t>(bw);
-            if (hp + hl + body > slen) { err = 1; break; }
-            cur = static_cast<uint64_t>(hp + hl) * 8;
-            rle = 0;
-            hp += hl + static_cast<uint32_t>(body);
-          } else {
-            c = h >> 1;
-            if (hp + hl + vbytes > slen) { err = 1; break; }
-            if (wrel + hl + vbytes > win.n) { reload = 1; break; }
-            uint32_t v = 0;
-            for (uint32_t q = 0; q < vbytes; ++q) v |= static_cast<uint32_t>(win.s[wrel + hl + q]) << (8 * q);
-            cur = v;
-            rle = 1;
-            hp += hl + vbytes;
-          }
-          int64_t room = static_cast<int64_t>(total) - kk;
-          left = static_cast<int32_t>(static_cast<int64_t>(c) < room ? static_cast<int64_t>(c) : room);
-          continue;
-        }
-        if (kk < kneed) {  // skip values before the item's first
-          int32_t s = kneed - kk < left ? kneed - kk : left;
-          left -= s;
-          kk += s;
-          if (!rle) cur += static_cast<uint64_t>(s) * bw;
-          continue;
-        }
-        int32_t take = nvals - prod < left ? nvals - prod : left;
-        uint32_t meta = 0x80000000u;
-        if (!rle) {
-          int64_t wb = wbit0 + static_cast<int64_t>(cur);
-          if (wb < 0) { reload = 1; break; }
-          int64_t room = bw ? (static_cast<int64_t>(win.n) * 8 - wb) / bw : take;
-          if (room < take) {
-            take = static_cast<int32_t>(room > 0 ? room : 0);
-            reload = 1;
-          }
-          if (take == 0) break;
-          meta = static_cast<uint32_t>(wb);
-        }
-        sm.sdst[nseg] = prod;
-        sm.scnt[nseg] = take;
-        sm.smeta[nseg] = meta;
-        sm.sval[nseg] = rle ? static_cast<uint32_t>(cur) : 0u;
-        ++nseg;
-        prod += take;
-        left -= take;
-        kk += take;
-        if (!rle) cur += static_cast<uint64_t>(take) * bw;
-        if (reload) break;
-      }
-      sm.ctl[0] = static_cast<int32_t>(hp);
-      sm.ctl[1] = kk;
-      sm.ctl[2] = left;
-      sm.ctl[3] = rle;
-      sm.c64[0] = static_cast<int64_t>(cur);
-      sm.ctl[4] = nseg;
-      sm.ctl[5] = reload;
-      sm.ctl[6] = err;
-      sm.ctl[7] = prod;
-    }
+  walk_init(sm);
+  for (uint32_t guard = 0; guard <= static_cast<uint32_t>(a.n_walk); ++guard) {
+    if (threadIdx.x == 0) sm.ctl[13] = static_cast<int32_t>(atomicAdd(a.item_counter + 1, 1u));
     __syncthreads();
-    if (sm.ctl[6]) {
-      if (tid == 0) report(st, DERR_CORRUPT, pgid, WHERE_EXPAND, 1);
-      return false;
-    }
-    const int nseg = sm.ctl[4];
-    const int prod = sm.ctl[7];
-    // expand the segments into vbuf
-    for (int j = produced + tid; j < prod; j += blockDim.x) {
-      int lo = 0, hi = nseg - 1;
-      while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (sm.sdst[mid] <= j) lo = mid; else hi = mid - 1;
-      }
-      uint32_t meta = sm.smeta[lo];
-      uint32_t idx;
-      if (meta == 0x80000000u)
-        idx = sm.sval[lo];
-      else
-        idx = bits32(w32, static_cast<uint64_t>(meta) + static_cast<uint64_t>(j - sm.sdst[lo]) * bw, bw);
-      if (idx >= static_cast<uint32_t>(dd.n)) {
-        report(st, DERR_CORRUPT, pgid, WHERE_EXPAND, 2);
-        idx = 0;
-        if (dd.n == 0) {
-          sm.vbuf[j] = 0;
-          continue;
-        }
-      }
-      if (ptype == T_BYTE_ARRAY) {
-        sm.vbuf[j] = idx;
-      } else if (dd.width == 4) {
-        sm.vbuf[j] = reinterpret_cast<const uint32_t*>(dd.values)[idx];
-      } else {
-        sm.vbuf[j] = reinterpret_cast<const uint64_t*>(dd.values)[idx];
-      }
-    }
-    const int reload = sm.ctl[5];
-    produced = prod;
-    if (reload) {
-      int64_t from;
-      if (sm.ctl[2] > 0 && !sm.ctl[3])
-        from = static_cast<int64_t>(static_cast<uint64_t>(sm.c64[0]) >> 3);
-      else
-        from = sm.ctl[0];
-      if (!win_load(win, sb + from, sb + slen, st, pgid, WHERE_EXPAND)) return false;
-    } else {
-      __syncthreads();
-      if (nseg == 0 && produced < nvals) {
-        if (tid == 0) report(st, DERR_CORRUPT, pgid, WHERE_EXPAND, 3);
-        return false;
-      }
-    }
+    const int w = sm.ctl[13];
+    __syncthreads();
+    if (w >= a.n_walk) break;
+    walk_page(a, static_cast<int>(a.walk_pps[w]), sm);
   }
-  if (produced < nvals) {
-    if (tid == 0) report(st, DERR_CORRUPT, pgid, WHERE_EXPAND, 4);
-    return false;
-  }
-  return true;
 }
 
-// DELTA stream state, kept between tiles:
-//  ctl[8]  block position (stream offset) of the current block
-//  ctl[9]  dense index of its first value
-//  c64[1]  value preceding it
-__device__ bool delta_tile(ExpSmem& sm, Win& win, const uint8_t* sb, uint32_t slen, const DeltaHdr& d,
-                           int type_bits, int32_t kneed, int nvals, int pgid, DevStatus* st) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const int32_t kend = kneed + nvals;
-  // the first value of the page comes from the header
-  if (kneed == 0 && nvals > 0 && tid == 0) sm.vbuf[0] = static_cast<uint64_t>(d.first);
-  for (uint32_t guard = 0; guard < 4u * (slen + 64); ++guard) {
-    if (tid == 0) {
-      uint32_t bp = static_cast<uint32_t>(sm.ctl[8]);
-      int32_t kk = sm.ctl[9];
-      int nb = 0, reload = 0, bad = 0;
-      while (nb < DB_MAX && kk < kend && kk < d.total) {
-        if (bp >= slen) { bad = 1; break; }
-        int64_t wrel_s = (sb + bp) - win.g0;
-        if (wrel_s < 0 || wrel_s >= win.n) { reload = 1; break; }
-        uint32_t wrel = static_cast<uint32_t>(wrel_s);
-        uint32_t lim_w = win.n, lim_s = wrel + (slen - bp);
-        uint32_t lim = lim_w < lim_s ? lim_w : lim_s;
-        int32_t nv = d.total - kk < d.block ? d.total - kk : d.block;
-        int64_t mn;
-        uint32_t wpos, dpos;
-        int more = 0;
-        uint32_t size = delta_block(win, wrel, lim, d, nv, type_bits, &mn, &wpos, &dpos, &more, &bad);
-        if (bad) break;
-        if (size == 0) {
-          if (lim == lim_s) bad = 1; else if (wrel == 0) bad = 2; else reload = 1;
-          break;
-        }
-        sm.dstart[nb] = bp;
-        sm.ddata[nb] = dpos;
-        sm.dwid[nb] = wpos;
-        sm.dk[nb] = kk;
-        sm.dcnt[nb] = nv;
-        sm.dmin[nb] = mn;
-        sm.dnext[nb] = static_cast<int32_t>(bp + size);
-        ++nb;
-        bp += size;
-        kk += nv;
-      }
-      sm.ctl[10] = nb;
-      sm.ctl[11] = reload;
-      sm.ctl[12] = bad;
-    }
-    __syncthreads();
-    const int nb = sm.ctl[10];
-    if (sm.ctl[12]) {
-      if (tid == 0) report(st, sm.ctl[12] == 2 ? DERR_UNSUPPORTED : DERR_CORRUPT, pgid, WHERE_EXPAND, 5);
-      return false;
-    }
-    // each warp decodes whole blocks: local inclusive prefix of (min + packed)
-    for (int b = warp; b < nb; b += nwarps) {
-      const int32_t cnt = sm.dcnt[b];
-      const uint64_t mn = static_cast<uint64_t>(sm.dmin[b]);
-      uint64_t carry = 0;
-      for (int r0 = 0; r0 < cnt; r0 += 32) {
-        int v = r0 + lane;
-        uint64_t x = v < cnt ? mn + delta_packed(win, sm.dwid[b], sm.ddata[b], d.vpm, v) : 0;
+// ------------------------------------------------------------------ DELTA block bases
+
+// Per-lane miniblock layout of the block at `pos`: width of miniblock `lane`
+// and its exclusive bit offset.  Returns the header length (0: malformed).
+__device__ __forceinline__ int delta_block_layout(const uint8_t* sb, uint32_t pos, const PlanPage& pp, int32_t nv,
+                                                  int type_bits, int lane, int64_t* mn, uint32_t* wbyte,
+                                                  uint32_t* excl, bool* bad) {
+  uint64_t z = 0;
+  const int vl = uleb([&](uint32_t q) { return static_cast<uint32_t>(__ldg(sb + pos + q)); }, 0, 10, &z);
+  *mn = unzigzag(z);
+  const uint32_t wb = lane < pp.dmbc ? __ldg(sb + pos + vl + lane) : 0u;
+  const int used = (nv + pp.dvpm - 1) / pp.dvpm;
+  *bad = __any_sync(0xffffffffu, lane < used && static_cast<int>(wb) > type_bits) || !vl;
+  const uint32_t mbits = lane < used ? wb * static_cast<uint32_t>(pp.dvpm) : 0u;
+  uint32_t incl = mbits;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
-          if (lane >= o) x += y;
-        }
-        x += carry;
-        int32_t dense = sm.dk[b] + v;
-        if (v < cnt && dense >= kneed && dense < kend) sm.vbuf[dense - kneed] = x;
-        carry = __shfl_sync(0xffffffffu, x, 31);
-      }
-      if (lane == 0) sm.dsum[b] = carry;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      uint64_t prev = static_cast<uint64_t>(sm.c64[1]);
-      int adv = 1;
-      for (int b = 0; b < nb; ++b) {
-        sm.dbase[b] = prev;
-        prev += sm.dsum[b];
-        if (adv && sm.dk[b] + sm.dcnt[b] <= kend) {
-          sm.ctl[8] = sm.dnext[b];
-          sm.ctl[9] = sm.dk[b] + sm.dcnt[b];
-          sm.c64[1] = static_cast<int64_t>(prev);
-        } else {
-          adv = 0;
-        }
-      }
-    }
-    __syncthreads();
-    for (int b = warp; b < nb; b += nwarps) {
-      for (int v = lane; v < sm.dcnt[b]; v += 32) {
-        int32_t dense = sm.dk[b] + v;
-        if (dense >= kneed && dense < kend) sm.vbuf[dense - kneed] += sm.dbase[b];
-      }
-    }
-    __syncthreads();
-    const int reload = sm.ctl[11];
-    const bool finished = nb > 0 ? (sm.dk[nb - 1] + sm.dcnt[nb - 1] >= kend || sm.dk[nb - 1] + sm.dcnt[nb - 1] >= d.total)
-                                 : (kend <= 1);
-    __syncthreads();
-    if (finished) return true;
-    if (reload) {
-      if (!win_load(win, sb + sm.ctl[8], sb + slen, st, pgid, WHERE_EXPAND)) return false;
-    } else if (nb == 0) {
-      if (tid == 0) report(st, DERR_CORRUPT, pgid, WHERE_EXPAND, 6);
-      return false;
-    }
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
   }
-  if (tid == 0) report(st, DERR_CORRUPT, pgid, WHERE_EXPAND, 7);
-  return false;
+  *wbyte = wb;
+  *excl = incl - mbits;
+  return vl;
 }
 
-// PLAIN BYTE_ARRAY: thread 0 walks the values of the tile (serial).
-//  ctl[13] position of the next value's length prefix
-__device__ bool plain_ba_tile(ExpSmem& sm, const uint8_t* sb, uint32_t slen, int nvals, int pgid, DevStatus* st) {
-  if (threadIdx.x == 0) {
-    uint32_t pos = static_cast<uint32_t>(sm.ctl[13]);
-    int err = 0;
-    for (int j = 0; j < nvals; ++j) {
-      if (pos + 4 > slen) { err = 1; break; }
-      uint32_t len = ld_le32_g(sb + pos);
-      if (len > slen - pos - 4) { err = 1; break; }
-      sm.vbuf[j] = pos;
-      pos += 4 + len;
-    }
-    sm.ctl[13] = static_cast<int32_t>(pos);
-    sm.ctl[14] = err;
+// Delta sum of block b of a DELTA page (one warp): sum over its values of
+// (min delta + packed delta), wrapping mod 2^64.  Returns false when the
+// block is malformed.
+__device__ bool delta_block_sum(const uint8_t* sb, const PlanPage& pp, const uint32_t* dpos, int type_bits, int b,
+                                int lane, uint64_t* sum) {
+  const uint32_t pos = dpos[b];
+  const int64_t bk = 1 + static_cast<int64_t>(b) * pp.dbs;
+  const int32_t nv = static_cast<int32_t>(pp.nonnull - bk < pp.dbs ? pp.nonnull - bk : pp.dbs);
+  int64_t mn;
+  uint32_t wb, excl;
+  bool bad;
+  const int vl = delta_block_layout(sb, pos, pp, nv, type_bits, lane, &mn, &wb, &excl, &bad);
+  if (bad) return false;
+  const uint64_t dbit = static_cast<uint64_t>(pos + vl + pp.dmbc) * 8;
+  uint64_t x[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {  // up to 128 values per block with all loads issued together
+    const int v = u * 32 + lane;
+    const int m = (v < nv ? v : nv - 1) / pp.dvpm;
+    const int w = __shfl_sync(0xffffffffu, static_cast<int>(wb), m);
+    const uint32_t off = __shfl_sync(0xffffffffu, excl, m);
+    if (v < nv) x[u] = gbits64(sb, dbit + off + static_cast<uint64_t>(v - m * pp.dvpm) * w, w);
   }
-  __syncthreads();
-  if (sm.ctl[14]) {
-    if (threadIdx.x == 0) report(st, DERR_CORRUPT, pgid, WHERE_EXPAND, 8);
-    return false;
+  uint64_t s = 0;
+  for (int v = lane; v < nv; v += 32) s += static_cast<uint64_t>(mn);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) s += x[u];
+  for (int v = 128 + lane; v < nv; v += 32) {  // blocks larger than 128 values
+    const int m = v / pp.dvpm;
+    const int w = __shfl_sync(__activemask(), static_cast<int>(wb), m);
+    const uint32_t off = __shfl_sync(__activemask(), excl, m);
+    s += gbits64(sb, dbit + off + static_cast<uint64_t>(v - m * pp.dvpm) * w, w);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  *sum = s;
   return true;
 }
+
+// Block sums of every DELTA page, spread over the whole GPU: blockIdx.y is
+// the page, warps stride over its blocks.  The sums land in dbase.
+__global__ void __launch_bounds__(256) k_delta_sums(DecodeArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int p = static_cast<int>(a.delta_pps[blockIdx.y]);
+  const PlanPage pp = a.pps[p];
+  if (pp.dblocks <= 0 || pp.nonnull < 0) return;
+  const uint8_t* sb = pp.body + pp.values_off;
+  const uint32_t* dpos = a.dpos + pp.dtab;
+  int64_t* dsum = a.dbase + pp.dtab;
+  const int type_bits = a.chunks[pp.chunk].ptype == T_INT32 ? 32 : 64;
+  const int w0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int b = w0; b < pp.dblocks; b += nw) {
+    uint64_t sum = 0;
+    if (!delta_block_sum(sb, pp, dpos, type_bits, b, lane, &sum)) {
+      if (lane == 0) report(a.st, DERR_CORRUPT, static_cast<int>(pp.page), WHERE_WALK_VALUES, 20);
+      sum = 0;
+    }
+    if (lane == 0) dsum[b] = static_cast<int64_t>(sum);
+  }
+}
+
+// In-place exclusive scan of one page's block sums, from its first value.
+__device__ void delta_scan_page(const DecodeArgs& a, int p, uint64_t* tmp) {
+  const PlanPage pp = a.pps[p];
+  if (pp.dblocks <= 0 || pp.nonnull < 0) return;
+  int64_t* d = a.dbase + pp.dtab;
+  uint64_t carry = static_cast<uint64_t>(pp.dfirst);
+  for (int b0 = 0; b0 < pp.dblocks; b0 += blockDim.x * 4) {
+    uint64_t loc[4];
+    uint64_t mine = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = b0 + threadIdx.x * 4 + q;
+      loc[q] = j < pp.dblocks ? static_cast<uint64_t>(d[j]) : 0;
+      mine += loc[q];
+    }
+    uint64_t tot;
+    uint64_t run = carry + block_exclusive_sum(mine, tmp, &tot);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = b0 + threadIdx.x * 4 + q;
+      if (j < pp.dblocks) d[j] = static_cast<int64_t>(run);
+      run += loc[q];
+    }
+    carry += tot;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_delta_scan(DecodeArgs a) {
+  __shared__ uint64_t tmp[32];
+  delta_scan_page(a, static_cast<int>(a.delta_pps[blockIdx.x]), tmp);
+}
+
+// One DELTA page inside one thread block (plain baseline).
+__device__ void delta_bases_page(const DecodeArgs& a, int p, uint64_t* tmp) {
+  const PlanPage pp = a.pps[p];
+  if (pp.dblocks <= 0 || pp.nonnull < 0) return;
+  const int lane = threadIdx.x & 31;
+  const uint8_t* sb = pp.body + pp.values_off;
+  const int type_bits = a.chunks[pp.chunk].ptype == T_INT32 ? 32 : 64;
+  for (int b = threadIdx.x >> 5; b < pp.dblocks; b += blockDim.x >> 5) {
+    uint64_t sum = 0;
+    if (!delta_block_sum(sb, pp, a.dpos + pp.dtab, type_bits, b, lane, &sum)) {
+      if (lane == 0) report(a.st, DERR_CORRUPT, static_cast<int>(pp.page), WHERE_WALK_VALUES, 20);
+      sum = 0;
+    }
+    if (lane == 0) a.dbase[pp.dtab + b] = static_cast<int64_t>(sum);
+  }
+  __syncthreads();
+  delta_scan_page(a, p, tmp);
+}
+
+// ------------------------------------------------------------------ expand (one warp per item)
+
+struct WarpSmem {
+  uint64_t vbuf[ITEM_ROWS_OPT];  // dense values of an OPTIONAL item (non-PLAIN)
+};
 
 __device__ __forceinline__ void store_val(uint8_t* base, int64_t row, int width, uint64_t v) {
   if (width == 4)
@@ -1193,132 +1175,328 @@ __device__ __forceinline__ void store_val(uint8_t* base, int64_t row, int width,
     reinterpret_cast<uint64_t*>(base)[row] = v;
 }
 
-// Decodes one work item (block-collective).
-__device__ void expand_item(const DecodeArgs& a, int it_id, ExpSmem& sm, Win& win) {
-  const int tid = threadIdx.x;
+// Where dense values go: straight to the output rows (REQUIRED), to the
+// string scratch (REQUIRED BYTE_ARRAY), or to the warp's staging buffer
+// (OPTIONAL, scattered to rows afterwards).
+struct Sink {
+  uint8_t* out;
+  uint32_t* sidx;
+  uint64_t* vbuf;
+  int64_t orow0;
+  int width;
+  __device__ __forceinline__ void put(int32_t j, uint64_t v) const {
+    if (vbuf)
+      vbuf[j] = v;
+    else if (sidx)
+      sidx[orow0 + j] = static_cast<uint32_t>(v);
+    else
+      store_val(out, orow0 + j, width, v);
+  }
+};
+
+// Dictionary indices of dense values [k0, k1), from the checkpoint run;
+// up to 4 gathers per lane are issued before any result is used.
+__device__ bool warp_hybrid(const uint8_t* sb, uint32_t slen, int bw, int32_t total, uint32_t pos, int32_t rk,
+                            int32_t k0, int32_t k1, const DictDev& dd, bool idx_only, const Sink& sink,
+                            uint64_t* chars, int lane) {
+  const uint32_t vbytes = (bw + 7) / 8;
+  for (uint32_t guard = 0; rk < k1 && guard <= slen; ++guard) {
+    uint64_t h = 0;
+    int hl = 0;
+    uint32_t rle = 0;
+    if (lane == 0 && pos < slen) {
+      hl = uleb([&](uint32_t q) { return static_cast<uint32_t>(__ldg(sb + q)); }, pos, slen, &h);
+      if (hl && !(h & 1)) {
+        if (pos + hl + vbytes > slen)
+          hl = 0;
+        else
+          for (uint32_t q = 0; q < vbytes; ++q) rle |= static_cast<uint32_t>(__ldg(sb + pos + hl + q)) << (8 * q);
+      }
+    }
+    hl = __shfl_sync(0xffffffffu, hl, 0);
+    if (!hl) return false;
+    h = __shfl_sync(0xffffffffu, h, 0);
+    rle = __shfl_sync(0xffffffffu, rle, 0);
+    const bool packed = h & 1;
+    const uint64_t cnt = packed ? (h >> 1) << 3 : h >> 1;
+    const uint64_t adv = hl + (packed ? (h >> 1) * static_cast<uint64_t>(bw) : vbytes);
+    if (pos + adv > slen) return false;
+    const int64_t rend64 = static_cast<int64_t>(rk) + static_cast<int64_t>(cnt);
+    const int32_t s = rk > k0 ? rk : k0;
+    int64_t e64 = rend64 < k1 ? rend64 : k1;
+    if (e64 > total) e64 = total;
+    const int32_t e = static_cast<int32_t>(e64);
+    const uint64_t dbit = static_cast<uint64_t>(pos + hl) * 8;
+    bool bad = false;
+    for (int32_t j0 = s; j0 < e; j0 += 128) {
+      uint32_t idx[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int32_t j = j0 + u * 32 + lane;
+        uint32_t x = 0;
+        if (j < e) {
+          x = packed ? gbits32(sb, dbit + static_cast<uint64_t>(j - rk) * bw, bw) : rle;
+          if (x >= static_cast<uint32_t>(dd.n)) {
+            bad = true;
+            x = 0;
+          }
+        }
+        idx[u] = x;
+      }
+      if (dd.n == 0) {
+        bad = bad || j0 < e;
+        break;
+      }
+      if (idx_only) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int32_t j = j0 + u * 32 + lane;
+          if (j < e) {
+            sink.put(j - k0, idx[u]);
+            *chars += dd.str_len[idx[u]];
+          }
+        }
+      } else if (dd.width == 4) {
+        uint32_t v[4];
+        const uint32_t* dv = reinterpret_cast<const uint32_t*>(dd.values);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = __ldg(dv + idx[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int32_t j = j0 + u * 32 + lane;
+          if (j < e) sink.put(j - k0, v[u]);
+        }
+      } else {
+        uint64_t v[4];
+        const uint64_t* dv = reinterpret_cast<const uint64_t*>(dd.values);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = __ldg(dv + idx[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int32_t j = j0 + u * 32 + lane;
+          if (j < e) sink.put(j - k0, v[u]);
+        }
+      }
+    }
+    if (__any_sync(0xffffffffu, bad)) return false;
+    pos += static_cast<uint32_t>(adv);
+    rk = rend64 > total ? total : static_cast<int32_t>(rend64);
+  }
+  return rk >= k1;
+}
+
+// DELTA values [k0, k1) from the block tables.
+__device__ bool warp_delta(const uint8_t* sb, const PlanPage& pp, const uint32_t* dpos, const int64_t* dbase,
+                           int type_bits, int32_t k0, int32_t k1, const Sink& sink, int lane) {
+  const int32_t total = pp.nonnull;
+  if (k0 == 0 && k1 > 0 && lane == 0) sink.put(0, static_cast<uint64_t>(pp.dfirst));
+  const int32_t ka = k0 > 1 ? k0 : 1;
+  if (ka >= k1) return true;
+  const int bfirst = (ka - 1) / pp.dbs, blast = (k1 - 2) / pp.dbs;
+  if (blast >= pp.dblocks) return false;
+  for (int b = bfirst; b <= blast; ++b) {
+    const uint32_t pos = dpos[b];
+    const int64_t bk = 1 + static_cast<int64_t>(b) * pp.dbs;
+    const int32_t nv = static_cast<int32_t>(total - bk < pp.dbs ? total - bk : pp.dbs);
+    int64_t mn;
+    uint32_t wb, excl;
+    bool bad;
+    const int vl = delta_block_layout(sb, pos, pp, nv, type_bits, lane, &mn, &wb, &excl, &bad);
+    if (bad) return false;
+    const uint64_t dbit = static_cast<uint64_t>(pos + vl + pp.dmbc) * 8;
+    uint64_t carry = static_cast<uint64_t>(dbase[b]);
+    for (int r0 = 0; r0 < nv; r0 += 128) {
+      // 4 rounds of 32 values: all packed deltas loaded before the scans
+      uint64_t x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int v = r0 + u * 32 + lane;
+        const int m = (v < nv ? v : nv - 1) / pp.dvpm;
+        const int w = __shfl_sync(0xffffffffu, static_cast<int>(wb), m);
+        const uint32_t off = __shfl_sync(0xffffffffu, excl, m);
+        x[u] = v < nv ? static_cast<uint64_t>(mn) +
+                            gbits64(sb, dbit + off + static_cast<uint64_t>(v - m * pp.dvpm) * w, w)
+                      : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        uint64_t y = x[u];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint64_t t = __shfl_up_sync(0xffffffffu, y, o);
+          if (lane >= o) y += t;
+        }
+        const int v = r0 + u * 32 + lane;
+        const int64_t dense = bk + v;
+        if (v < nv && dense >= k0 && dense < k1) sink.put(static_cast<int32_t>(dense - k0), carry + y);
+        carry += __shfl_sync(0xffffffffu, y, 31);
+      }
+    }
+  }
+  return true;
+}
+
+// PLAIN BYTE_ARRAY: lane 0 follows the values from the checkpoint.
+__device__ bool warp_plain_ba(const uint8_t* sb, uint32_t slen, uint32_t pos, int32_t k0, int32_t k1,
+                              const Sink& sink, uint64_t* chars, int lane) {
+  int ok = 1;
+  if (lane == 0) {
+    for (int32_t k = k0; k < k1; ++k) {
+      if (pos + 4 > slen) { ok = 0; break; }
+      const uint32_t len = ld_le32_g(sb + pos);
+      if (len > slen - pos - 4) { ok = 0; break; }
+      sink.put(k - k0, pos);
+      *chars += len;
+      pos += 4 + len;
+    }
+  }
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// Bits of the validity bitmap for output rows [r, r + n), n <= 32.
+__device__ __forceinline__ uint32_t bitmap_bits(const uint32_t* v, int64_t r, int n) {
+  const int64_t wi = r >> 5;
+  const uint32_t sh = static_cast<uint32_t>(r & 31);
+  const uint32_t lo = v[wi];
+  const uint32_t hi = (sh && sh + n > 32) ? v[wi + 1] : 0u;
+  const uint32_t b = sh ? __funnelshift_r(lo, hi, sh) : lo;
+  return n < 32 ? b & ((1u << n) - 1u) : b;
+}
+
+__device__ void expand_item(const DecodeArgs& a, int it_id, WarpSmem& ws, int lane) {
   const Item it = a.items[it_id];
   if (it.nrows <= 0) return;
   const PlanPage pp = a.pps[it.pp];
+  if (pp.nonnull < 0) return;  // the walk of this page failed (error recorded)
   const PageDev pg = a.pages[pp.page];
   const OutCol col = a.cols[pp.col];
   const int pgid = static_cast<int>(pp.page);
-  if (pp.nonnull < 0) return;  // the walk of this page failed (error already recorded)
-  const uint8_t* body = pp.body;
-  const uint32_t v0 = static_cast<uint32_t>(pp.values_off);
-  const uint8_t* sb = body + v0;
-  uint32_t slen = static_cast<uint32_t>(pp.body_len) - v0;
-  const int32_t nonnull = pp.nonnull;
+  const uint8_t* sb = pp.body + pp.values_off;
+  const uint32_t slen = static_cast<uint32_t>(pp.body_len - pp.values_off);
   const int enc = pg.encoding;
   const bool isdict = enc == ENC_RLE_DICT || enc == ENC_PLAIN_DICT;
   const bool isdelta = enc == ENC_DELTA_BP;
   const bool isba = col.ptype == T_BYTE_ARRAY;
   const int width = col.width;
-  DictDev dd{};
-  int bw = 0;
-  DeltaHdr dh{};
-  const int type_bits = col.ptype == T_INT32 ? 32 : 64;
-  if (isdict && it.nn > 0) {
-    dd = a.dicts[pp.dict];
-    bw = __ldg(sb);
-    sb += 1;
-    slen -= 1;
-    if (tid == 0) {
-      sm.ctl[0] = it.pos;
-      sm.ctl[1] = it.run_k0;
-      sm.ctl[2] = 0;
-      sm.ctl[3] = 0;
-      sm.c64[0] = 0;
-    }
-    if (!win_load(win, sb + it.pos, sb + slen, a.st, pgid, WHERE_EXPAND)) return;
-  } else if (isdelta && it.nn > 0) {
-    if (!delta_header(sb, slen, &dh)) return;
-    if (tid == 0) {
-      sm.ctl[8] = it.pos;
-      sm.ctl[9] = it.run_k0;
-      sm.c64[1] = it.base;
-    }
-    if (!win_load(win, sb + it.pos, sb + slen, a.st, pgid, WHERE_EXPAND)) return;
-  } else if (isba && enc == ENC_PLAIN && it.nn > 0) {
-    if (tid == 0) sm.ctl[13] = it.pos;
-  }
-  __syncthreads();
-  int32_t k = it.k0;
-  uint64_t chars_sum = 0;
   const int64_t orow0 = pp.out_row + it.row0;
-  for (int t0 = 0; t0 < it.nrows; t0 += TILE_ROWS) {
-    const int nt = it.nrows - t0 < TILE_ROWS ? it.nrows - t0 : TILE_ROWS;
-    const int64_t orow = orow0 + t0;
-    int32_t nv = col.optional ? tile_validity(sm, col, orow, nt) : nt;
-    if (k + nv > nonnull) {
-      if (tid == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_EXPAND, 9);
+  const int32_t k0 = it.k0, nn = it.nn;
+  if (k0 < 0 || nn < 0 || static_cast<int64_t>(k0) + nn > pp.nonnull ||
+      (col.optional && !isba && enc != ENC_PLAIN && nn > ITEM_ROWS_OPT) ||
+      (col.optional && isba && nn > ITEM_ROWS_OPT)) {
+    if (lane == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_EXPAND, 9);
+    return;
+  }
+  uint64_t chars = 0;
+  bool ok = true;
+  if (enc == ENC_PLAIN && !isba) {
+    if (static_cast<uint64_t>(k0 + nn) * width > slen) {
+      if (lane == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_EXPAND, 10);
       return;
     }
-    bool ok = true;
-    if (nv > 0) {
-      if (isdict)
-        ok = hyb_tile(sm, win, sb, slen, bw, nonnull, k, nv, dd, col.ptype, pgid, a.st);
-      else if (isdelta)
-        ok = delta_tile(sm, win, sb, slen, dh, type_bits, k, nv, pgid, a.st);
-      else if (isba)
-        ok = plain_ba_tile(sm, sb, slen, nv, pgid, a.st);
-    }
-    __syncthreads();
-    if (!ok) return;
-    // emit rows
-    if (isba) {
-      for (int r = tid; r < nt; r += blockDim.x) {
-        bool valid = true;
-        int32_t rank = r;
-        if (col.optional) rank = row_rank(sm, r, &valid);
-        uint32_t s = valid ? static_cast<uint32_t>(sm.vbuf[rank]) : NULL_IDX;
-        col.str_scratch[orow + r] = s;
-        if (valid) chars_sum += isdict ? dd.str_len[s] : ld_le32_g(sb + s);
-      }
-    } else if (!isdict && !isdelta) {
-      // PLAIN fixed width: straight from the page
-      const uint8_t* src = sb + static_cast<int64_t>(k) * width;
-      for (int r = tid; r < nt; r += blockDim.x) {
-        bool valid = true;
-        int32_t rank = r;
-        if (col.optional) rank = row_rank(sm, r, &valid);
-        uint64_t v = valid ? ld_unaligned_g(src + static_cast<int64_t>(rank) * width, width) : 0;
-        store_val(col.values, orow + r, width, v);
+    const uint8_t* src = sb + static_cast<int64_t>(k0) * width;
+    if (!col.optional) {
+      for (int32_t r0 = 0; r0 < it.nrows; r0 += 256) {
+        uint64_t v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int32_t r = r0 + u * 32 + lane;
+          v[u] = r < it.nrows ? ld_unaligned_g(src + static_cast<int64_t>(r) * width, width) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int32_t r = r0 + u * 32 + lane;
+          if (r < it.nrows) store_val(col.values, orow0 + r, width, v[u]);
+        }
       }
     } else {
-      for (int r = tid; r < nt; r += blockDim.x) {
-        bool valid = true;
-        int32_t rank = r;
-        if (col.optional) rank = row_rank(sm, r, &valid);
-        store_val(col.values, orow + r, width, valid ? sm.vbuf[rank] : 0);
+      int32_t rank = 0;
+      for (int32_t r0 = 0; r0 < it.nrows; r0 += 256) {
+        uint32_t bits[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int32_t c0 = r0 + u * 32;
+          const int n = it.nrows - c0 < 32 ? it.nrows - c0 : 32;
+          bits[u] = n > 0 ? bitmap_bits(col.validity, orow0 + c0, n) : 0u;
+        }
+        uint64_t v[8];
+        int32_t rr[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          rr[u] = rank + __popc(bits[u] & ((1u << lane) - 1u));
+          rank += __popc(bits[u]);
+          v[u] = (bits[u] >> lane) & 1u ? ld_unaligned_g(src + static_cast<int64_t>(rr[u]) * width, width) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int32_t r = r0 + u * 32 + lane;
+          if (r < it.nrows) store_val(col.values, orow0 + r, width, v[u]);
+        }
       }
     }
-    k += nv;
-    __syncthreads();
+    return;
+  }
+  const int type_bits = col.ptype == T_INT32 ? 32 : 64;
+  Sink sink{nullptr, nullptr, nullptr, orow0, width};
+  if (col.optional)
+    sink.vbuf = ws.vbuf;
+  else if (isba)
+    sink.sidx = col.str_scratch;
+  else
+    sink.out = col.values;
+  if (nn > 0) {
+    if (isdict) {
+      const DictDev dd = a.dicts[pp.dict];
+      const int bw = __ldg(sb);
+      ok = bw <= 32 && warp_hybrid(sb + 1, slen - 1, bw, pp.nonnull, static_cast<uint32_t>(it.pos), it.run_k0, k0,
+                                   k0 + nn, dd, isba, sink, &chars, lane);
+    } else if (isdelta) {
+      ok = warp_delta(sb, pp, a.dpos + pp.dtab, a.dbase + pp.dtab, type_bits, k0, k0 + nn, sink, lane);
+    } else if (isba) {
+      ok = warp_plain_ba(sb, slen, static_cast<uint32_t>(it.pos), k0, k0 + nn, sink, &chars, lane);
+    } else {
+      ok = false;
+    }
+  }
+  if (!ok) {
+    if (lane == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_EXPAND, 1);
+    return;
+  }
+  __syncwarp();
+  if (col.optional) {
+    // scatter the staged dense values to rows, nulls as zero
+    int32_t rank = 0;
+    for (int32_t r0 = 0; r0 < it.nrows; r0 += 32) {
+      const int n = it.nrows - r0 < 32 ? it.nrows - r0 : 32;
+      const uint32_t bits = bitmap_bits(col.validity, orow0 + r0, n);
+      const bool valid = (bits >> lane) & 1u;
+      const int32_t rr = rank + __popc(bits & ((1u << lane) - 1u));
+      if (lane < n) {
+        if (isba)
+          col.str_scratch[orow0 + r0 + lane] = valid ? static_cast<uint32_t>(ws.vbuf[rr]) : NULL_IDX;
+        else
+          store_val(col.values, orow0 + r0 + lane, width, valid ? ws.vbuf[rr] : 0);
+      }
+      rank += __popc(bits);
+    }
+    __syncwarp();
   }
   if (isba) {
-    uint64_t tot;
-    (void)block_exclusive_sum(chars_sum, sm.tmp64, &tot);
-    if (tid == 0) col.str_item_bytes[it_id] = tot;
+    uint64_t t = chars;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) col.str_item_bytes[it_id] = t;
   }
 }
 
 __global__ void __launch_bounds__(EXP_THREADS) k_expand(DecodeArgs a) {
-  extern __shared__ __align__(16) uint8_t smraw[];
-  ExpSmem& sm = *reinterpret_cast<ExpSmem*>(smraw);
-  if (threadIdx.x == 0) {
-    mbar_init(&sm.bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  Win win{sm.win, nullptr, WIN_BYTES, 0, &sm.bar, 0};
+  __shared__ WarpSmem ws[EXP_WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t guard = 0; guard <= static_cast<uint32_t>(a.n_items); ++guard) {
-    if (threadIdx.x == 0) sm.ctl[15] = static_cast<int32_t>(atomicAdd(a.item_counter, 1u));
-    __syncthreads();
-    const int it = sm.ctl[15];
-    __syncthreads();
-    if (it >= a.n_items) break;
-    expand_item(a, it, sm, win);
-    __syncthreads();
+    uint32_t u = 0;
+    if (lane == 0) u = atomicAdd(a.item_counter, 1u);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= static_cast<uint32_t>(a.n_items)) break;
+    expand_item(a, static_cast<int>(u), ws[warp], lane);
   }
 }
 
@@ -1331,12 +1509,23 @@ __global__ void k_str_scan(DecodeArgs a, const int* __restrict__ str_cols) {
   __shared__ uint64_t carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  for (uint32_t b = 0; b < col.item_count; b += blockDim.x) {
-    uint32_t i = b + threadIdx.x;
-    uint64_t v = i < col.item_count ? col.str_item_bytes[col.item_begin + i] : 0;
+  for (uint32_t b = 0; b < col.item_count; b += blockDim.x * 4) {
+    uint64_t loc[4];
+    uint64_t mine = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t i = b + threadIdx.x * 4 + q;
+      loc[q] = i < col.item_count ? col.str_item_bytes[col.item_begin + i] : 0;
+      mine += loc[q];
+    }
     uint64_t tot;
-    uint64_t pre = block_exclusive_sum(v, tmp, &tot);
-    if (i < col.item_count) col.str_item_bytes[col.item_begin + i] = carry + pre;
+    uint64_t run = carry + block_exclusive_sum(mine, tmp, &tot);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t i = b + threadIdx.x * 4 + q;
+      if (i < col.item_count) col.str_item_bytes[col.item_begin + i] = run;
+      run += loc[q];
+    }
     __syncthreads();
     if (threadIdx.x == 0) carry += tot;
     __syncthreads();
@@ -1347,15 +1536,24 @@ __global__ void k_str_scan(DecodeArgs a, const int* __restrict__ str_cols) {
   }
 }
 
-// Per item of a string column: int64 offsets and the chars copy.
+// Per item of a string column, one warp: offsets by a warp scan of the
+// lengths; each 32-string chunk is assembled in shared memory (lanes copy
+// their own string) and written out with aligned 16-byte stores, bytes
+// only at the chunk's two ends.
+constexpr int STR_STAGE = 2048;
+
 __global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a) {
-  __shared__ uint64_t tmp[32];
-  for (int itx = blockIdx.x; itx < a.n_items; itx += gridDim.x) {
+  __shared__ __align__(16) uint8_t stage[8][STR_STAGE + 16];
+  const int lane = threadIdx.x & 31;
+  uint8_t* sbuf = stage[threadIdx.x >> 5];
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int itx = gw; itx < a.n_items; itx += nw) {
     const Item it = a.items[itx];
     if (it.nrows <= 0) continue;
     const PlanPage pp = a.pps[it.pp];
     const OutCol col = a.cols[pp.col];
-    if (col.ptype != T_BYTE_ARRAY) continue;
+    if (col.ptype != T_BYTE_ARRAY || pp.nonnull < 0) continue;
     const PageDev pg = a.pages[pp.page];
     const bool isdict = pg.encoding == ENC_RLE_DICT || pg.encoding == ENC_PLAIN_DICT;
     DictDev dd{};
@@ -1364,12 +1562,12 @@ __global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a) {
     uint64_t base = col.str_item_bytes[itx];
     const int64_t orow0 = pp.out_row + it.row0;
     int64_t* offs = reinterpret_cast<int64_t*>(col.values);
-    for (int r0 = 0; r0 < it.nrows; r0 += blockDim.x) {
-      int r = r0 + threadIdx.x;
+    for (int r0 = 0; r0 < it.nrows; r0 += 32) {
+      const int r = r0 + lane;
       uint32_t len = 0;
       const uint8_t* src = nullptr;
       if (r < it.nrows) {
-        uint32_t s = col.str_scratch[orow0 + r];
+        const uint32_t s = col.str_scratch[orow0 + r];
         if (s != NULL_IDX) {
           if (isdict) {
             len = dd.str_len[s];
@@ -1380,13 +1578,50 @@ __global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a) {
           }
         }
       }
-      uint64_t tot;
-      uint64_t pre = block_exclusive_sum(static_cast<uint64_t>(len), tmp, &tot);
-      if (r < it.nrows) {
-        uint64_t off = base + pre;
-        offs[orow0 + r] = static_cast<int64_t>(off);
-        if (off + len <= col.chars_cap)
-          for (uint32_t q = 0; q < len; ++q) col.chars[off + q] = __ldg(src + q);
+      uint64_t incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint64_t tot = __shfl_sync(0xffffffffu, incl, 31);
+      const uint64_t off = base + incl - len;
+      if (r < it.nrows) offs[orow0 + r] = static_cast<int64_t>(off);
+      if (base + tot <= col.chars_cap) {
+        const uint32_t a0 = static_cast<uint32_t>(base & 15);
+        if (a0 + tot <= STR_STAGE) {
+          // lanes place their strings, congruent to the output mod 16
+          uint8_t* d = sbuf + a0 + (off - base);
+          if (len) {
+            // aligned 4-byte loads of the source, bytes placed one by one
+            const uint32_t* sw = reinterpret_cast<const uint32_t*>(reinterpret_cast<uintptr_t>(src) & ~uintptr_t(3));
+            const uint32_t sh = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 3) * 8;
+            uint32_t cur = __ldg(sw);
+            for (uint32_t q = 0; q < len; q += 4) {
+              const uint32_t nxt = __ldg(sw + (q >> 2) + 1);
+              const uint32_t w = sh ? __funnelshift_r(cur, nxt, sh) : cur;
+              d[q] = static_cast<uint8_t>(w);
+              if (q + 1 < len) d[q + 1] = static_cast<uint8_t>(w >> 8);
+              if (q + 2 < len) d[q + 2] = static_cast<uint8_t>(w >> 16);
+              if (q + 3 < len) d[q + 3] = static_cast<uint8_t>(w >> 24);
+              cur = nxt;
+            }
+          }
+          __syncwarp();
+          uint8_t* g = col.chars + base;
+          const uint32_t head = a0 ? 16 - a0 : 0;
+          const uint32_t h = head < tot ? head : static_cast<uint32_t>(tot);
+          if (static_cast<uint32_t>(lane) < h) g[lane] = sbuf[a0 + lane];
+          const uint32_t nv = static_cast<uint32_t>((tot - h) >> 4);
+          const uint4* sv = reinterpret_cast<const uint4*>(sbuf + a0 + h);
+          uint4* gv = reinterpret_cast<uint4*>(g + h);
+          for (uint32_t q = lane; q < nv; q += 32) gv[q] = sv[q];
+          for (uint32_t q = h + (nv << 4) + lane; q < tot; q += 32) g[q] = sbuf[a0 + q];
+          __syncwarp();
+        } else if (r < it.nrows) {
+          uint8_t* d = col.chars + off;
+          for (uint32_t q = 0; q < len; ++q) d[q] = __ldg(src + q);
+        }
       }
       base += tot;
     }
@@ -1395,43 +1630,39 @@ __global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a) {
 
 // ------------------------------------------------------------------ plain baseline
 
-union PlainSmem {
-  WalkSmem w;
-  ExpSmem e;
-};
-
-// One page per thread block: walk then expand the page's single item.
-__global__ void __launch_bounds__(EXP_THREADS) k_plain_page(DecodeArgs a, int pp_begin) {
+// One page per thread block: the walk, DELTA bases, then the block's warps
+// decode the page's items.
+__global__ void __launch_bounds__(WALK_THREADS) k_plain_page(DecodeArgs a, int pp_begin) {
   extern __shared__ __align__(16) uint8_t smraw[];
-  PlainSmem& sm = *reinterpret_cast<PlainSmem*>(smraw);
+  WalkSmem& sm = *reinterpret_cast<WalkSmem*>(smraw);
   const int p = pp_begin + blockIdx.x;
-  if (threadIdx.x == 0) {
-    mbar_init(&sm.w.bar, 1);
-    fence_mbar_init();
-  }
+  walk_init(sm);
+  const PlanPage pp0 = a.pps[p];
+  const PageDev pg = a.pages[pp0.page];
+  const ChunkDev ch = a.chunks[pp0.chunk];
+  const bool needs_walk = ch.max_def || pg.encoding != ENC_PLAIN || ch.ptype == T_BYTE_ARRAY;
+  if (needs_walk) walk_page(a, p, sm);
   __syncthreads();
-  // both layouts start with the same barrier word; the expansion continues
-  // with the phase parity the walk left
-  Win ww{sm.w.win, nullptr, WIN_BYTES, 0, &sm.w.bar, 0};
-  walk_page(a, p, sm.w, ww);
-  __syncthreads();
-  Win we{sm.e.win, nullptr, WIN_BYTES, 0, &sm.e.bar, ww.parity};
-  const PlanPage pp = a.pps[p];
-  for (uint32_t i = 0; i < pp.item_count; ++i) {
-    expand_item(a, static_cast<int>(pp.item_begin + i), sm.e, we);
+  if (pg.encoding == ENC_DELTA_BP) {
+    delta_bases_page(a, p, reinterpret_cast<uint64_t*>(sm.win[1]));
     __syncthreads();
   }
+  const PlanPage pp = a.pps[p];
+  WarpSmem* ws = reinterpret_cast<WarpSmem*>(sm.win[0]);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint32_t i = warp; i < pp.item_count; i += nw) expand_item(a, static_cast<int>(pp.item_begin + i), ws[warp], lane);
 }
 
 // ------------------------------------------------------------------ per-scan reset
 
 // Zeroes the validity bitmaps (bits are OR-ed in by the walk), the string
-// item totals, the item counter and the error word.
+// item totals, the work counters and the error word.
 __global__ void k_prepare(DecodeArgs a, int n_cols) {
   const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
   const uint64_t nthr = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   if (tid == 0) {
-    *a.item_counter = 0;
+    a.item_counter[0] = 0;
+    a.item_counter[1] = 0;
     a.st->flags = 0;
     a.st->first_page = -1;
     a.st->where = 0;
@@ -1459,6 +1690,8 @@ static int g_walk_bps = 0, g_exp_bps = 0;
 int walk_blocks_per_sm() {
   if (!g_walk_bps) {
     cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(WalkSmem));
+    cudaFuncSetAttribute(k_plain_page, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(WalkSmem));
+    cudaFuncSetAttribute(k_dict_str, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(DictStrSmem));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_walk_bps, k_walk, WALK_THREADS, sizeof(WalkSmem));
     if (g_walk_bps < 1) g_walk_bps = 1;
   }
@@ -1467,23 +1700,26 @@ int walk_blocks_per_sm() {
 
 int expand_blocks_per_sm() {
   if (!g_exp_bps) {
-    cudaFuncSetAttribute(k_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(ExpSmem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_exp_bps, k_expand, EXP_THREADS, sizeof(ExpSmem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_exp_bps, k_expand, EXP_THREADS, 0);
     if (g_exp_bps < 1) g_exp_bps = 1;
   }
   return g_exp_bps;
 }
 
 void launch_walk(const DecodeArgs& a, int grid, cudaStream_t s) {
-  if (a.n_pp <= 0) return;
-  walk_blocks_per_sm();
+  if (a.n_walk <= 0) return;
   k_walk<<<grid, WALK_THREADS, sizeof(WalkSmem), s>>>(a);
+}
+
+void launch_delta_bases(const DecodeArgs& a, cudaStream_t s) {
+  if (a.n_delta <= 0) return;
+  k_delta_sums<<<dim3(32, a.n_delta), 256, 0, s>>>(a);
+  k_delta_scan<<<a.n_delta, 256, 0, s>>>(a);
 }
 
 void launch_expand(const DecodeArgs& a, int grid, cudaStream_t s) {
   if (a.n_items <= 0) return;
-  expand_blocks_per_sm();
-  k_expand<<<grid, EXP_THREADS, sizeof(ExpSmem), s>>>(a);
+  k_expand<<<grid, EXP_THREADS, 0, s>>>(a);
 }
 
 void launch_strings(const DecodeArgs& a, const int* str_cols, int n_str_cols, int n_cols_total, int grid,
@@ -1496,12 +1732,7 @@ void launch_strings(const DecodeArgs& a, const int* str_cols, int n_str_cols, in
 
 void launch_plain_pages(const DecodeArgs& a, int pp_begin, int n, cudaStream_t s) {
   if (n <= 0) return;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_plain_page, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(PlainSmem));
-    attr = true;
-  }
-  k_plain_page<<<n, EXP_THREADS, sizeof(PlainSmem), s>>>(a, pp_begin);
+  k_plain_page<<<n, WALK_THREADS, sizeof(WalkSmem), s>>>(a, pp_begin);
 }
 
 }  // namespace pqi

@@ -101,6 +101,7 @@ struct PlanPage {
   const uint8_t* body;     // page body (decompressed when the chunk is compressed)
   int64_t out_row;         // output row of the page's row 0 (may be < 0 when the
                            // request starts inside the page)
+  int64_t dfirst;          // DELTA: first value (from the stream header)   [walk]
   uint32_t page;           // page-table row
   uint32_t chunk;
   int32_t col;             // output column (request order)
@@ -110,8 +111,13 @@ struct PlanPage {
   uint32_t item_count;
   int32_t dict;            // chunk id of its dictionary (DictDev row), -1 none
   int32_t body_len;        // bytes of `body` (levels + values, uncompressed)
-  int32_t values_off;      // start of the value stream within `body` (set by the walk)
-  int32_t nonnull;         // non-null values on the page (set by the walk)
+  int32_t values_off;      // start of the value stream within `body`   [host or walk]
+  int32_t nonnull;         // non-null values on the page; -1 until known [host or walk]
+  uint32_t dtab;           // DELTA: first row of the page's block tables
+  int32_t dblocks;         // DELTA: blocks found by the walk                [walk]
+  int32_t dbs;             // DELTA: values per block                        [walk]
+  int32_t dvpm;            // DELTA: values per miniblock                    [walk]
+  int32_t dmbc;            // DELTA: miniblocks per block                    [walk]
   int32_t pad;
 };
 
@@ -151,9 +157,10 @@ PQ_HD inline int type_width(int32_t t) {
   return t == T_INT32 || t == T_FLOAT ? 4 : (t == T_INT64 || t == T_DOUBLE) ? 8 : 0;
 }
 
-// Rows per decode work item (a multiple of 32 and of the tile size).
-constexpr int ITEM_ROWS = 8192;
-// Rows per tile inside a work item (one pass of decode -> shared buffer -> emit).
-constexpr int TILE_ROWS = 2048;
+// Rows per decode work item (one warp decodes one item): REQUIRED columns
+// and OPTIONAL PLAIN fixed-width columns write straight to the output;
+// other OPTIONAL columns stage the item's dense values in shared memory.
+constexpr int ITEM_ROWS = 2048;
+constexpr int ITEM_ROWS_OPT = 512;
 
 }  // namespace pqi
