@@ -19,8 +19,7 @@ struct DictJob {
   int32_t page;         // page-table row
   int32_t chunk;        // DictDev row
   uint8_t* values;      // fixed width: n * width bytes (16-byte aligned)
-  uint32_t* str_pos;    // BYTE_ARRAY: n entries
-  uint32_t* str_len;    // BYTE_ARRAY: n entries
+  uint64_t* str_ent;    // BYTE_ARRAY: n entries, (chars offset << 32) | length
 };
 
 struct DecodeArgs {
@@ -36,6 +35,8 @@ struct DecodeArgs {
   const uint32_t* delta_pps;// DELTA plan pages (block bases)
   uint32_t* dpos;           // DELTA block positions (stream offsets)
   int64_t* dbase;           // DELTA value preceding each block
+  DeltaRegion* dregs;       // DELTA region summaries
+  uint32_t* dreg_lists;     // DELTA region block lists (DELTA_REGION_LIST per region)
   int n_pp;
   int n_items;
   int n_walk;
@@ -44,11 +45,11 @@ struct DecodeArgs {
 
 void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, DictDev* dicts, int n_sms,
                  DevStatus* st, cudaStream_t s);
-void launch_walk(const DecodeArgs& a, int grid, cudaStream_t s);
-void launch_delta_bases(const DecodeArgs& a, cudaStream_t s);
-void launch_expand(const DecodeArgs& a, int grid, cudaStream_t s);
-void launch_strings(const DecodeArgs& a, const int* str_cols, int n_str_cols, int n_cols_total, int grid,
-                    cudaStream_t s);
+// Launches over sub-ranges (one output column's share of the plan).
+void launch_walk(const DecodeArgs& a, int wbegin, int n, cudaStream_t s);
+void launch_delta_bases(const DecodeArgs& a, int dbegin, int n, int max_regions, cudaStream_t s);
+void launch_expand(const DecodeArgs& a, int ibegin, int n, cudaStream_t s);
+void launch_strings(const DecodeArgs& a, int col, int n_items, int n_sms, cudaStream_t s);
 // Plain baseline: pages [pp_begin, pp_begin + n) decoded one page per block.
 void launch_plain_pages(const DecodeArgs& a, int pp_begin, int n, cudaStream_t s);
 void launch_prepare(const DecodeArgs& a, int n_cols, int grid, cudaStream_t s);

@@ -113,6 +113,8 @@ pqi::DecodeArgs decode_args(pq_plan* plan) {
   a.delta_pps = plan->d_delta_pps;
   a.dpos = plan->d_dpos;
   a.dbase = plan->d_dbase;
+  a.dregs = plan->d_dregs;
+  a.dreg_lists = plan->d_dreg_lists;
   a.n_pp = static_cast<int>(plan->pps.size());
   a.n_items = static_cast<int>(plan->items.size());
   a.n_walk = static_cast<int>(plan->walk_pps.size());
@@ -191,6 +193,13 @@ pq_status pq_ctx_create(int device, pq_ctx** out) {
   ctx->device = device;
   cudaDeviceGetAttribute(&ctx->n_sms, cudaDevAttrMultiProcessorCount, device);
   if (ctx->n_sms <= 0) ctx->n_sms = 1;
+  for (auto& b : ctx->branch) {
+    if (cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      pq_ctx_destroy(ctx);
+      return PQ_ERR_CUDA;
+    }
+  }
   *out = ctx;
   return PQ_OK;
 }
@@ -199,6 +208,8 @@ void pq_ctx_destroy(pq_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  for (auto& b : ctx->branch)
+    if (b) cudaStreamDestroy(b);
   delete ctx;
 }
 
@@ -214,8 +225,7 @@ static void free_index_device(pq_index* idx) {
   pool.free(idx->d_chunk_file_off);
   pool.free(idx->d_status);
   for (auto p : idx->dict_values) pool.free(p);
-  for (auto p : idx->dict_str_pos) pool.free(p);
-  for (auto p : idx->dict_str_len) pool.free(p);
+  for (auto p : idx->dict_str_ent) pool.free(p);
   for (auto p : idx->dict_body) pool.free(p);
 }
 
@@ -451,8 +461,7 @@ pq_status pq_index_chunks(pq_ctx* ctx, const pq_file* files, int n_files, void* 
   }
   // 6. host checks, dictionary buffers
   idx->dict_values.assign(nch, nullptr);
-  idx->dict_str_pos.assign(nch, nullptr);
-  idx->dict_str_len.assign(nch, nullptr);
+  idx->dict_str_ent.assign(nch, nullptr);
   idx->dict_body.assign(nch, nullptr);
   idx->dict_resident.assign(nch, 0);
   for (int c = 0; c < nch; ++c) {
@@ -479,9 +488,8 @@ pq_status pq_index_chunks(pq_ctx* ctx, const pq_file* files, int n_files, void* 
       }
       const size_t n = static_cast<size_t>(dp.num_values);
       if (cd.ptype == pqi::T_BYTE_ARRAY) {
-        idx->dict_str_pos[c] = static_cast<uint32_t*>(pool.alloc(4 * n + 16));
-        idx->dict_str_len[c] = static_cast<uint32_t*>(pool.alloc(4 * n + 16));
-        if (!idx->dict_str_pos[c] || !idx->dict_str_len[c]) {
+        idx->dict_str_ent[c] = static_cast<uint64_t*>(pool.alloc(8 * n + 16));
+        if (!idx->dict_str_ent[c]) {
           free_index_device(idx.get());
           return fail(ctx, PQ_ERR_OOM, "dictionary");
         }
@@ -576,6 +584,9 @@ void pq_free_plan(pq_plan* plan) {
   if (plan->graph) cudaGraphExecDestroy(plan->graph);
   for (auto& e : plan->stage_ev)
     if (e) cudaEventDestroy(e);
+  if (plan->fork) cudaEventDestroy(plan->fork);
+  for (auto& e : plan->join)
+    if (e) cudaEventDestroy(e);
   free_plan_device(plan);
   delete plan;
 }
@@ -623,6 +634,14 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
   for (size_t oc = 0; oc < plan->cols.size(); ++oc) {
     const int c = plan->cols[oc];
     const auto& cm = idx->schema[c];
+    pq_plan::ColWork cw;
+    cw.snap_data_begin = static_cast<int>(plan->snappy_data.size());
+    cw.snap_dict_begin = static_cast<int>(plan->snappy_dict.size());
+    cw.dict_begin = static_cast<int>(plan->dict_jobs.size());
+    cw.walk_begin = static_cast<int>(plan->walk_pps.size());
+    cw.delta_begin = static_cast<int>(plan->delta_pps.size());
+    const int max_fixed_before = plan->max_fixed_dict_bytes;
+    plan->max_fixed_dict_bytes = 0;
     pqi::OutCol col{};
     col.n_rows = plan->n_rows;
     col.ptype = cm.type;
@@ -678,8 +697,7 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
           dj.page = cd.dict_page;
           dj.chunk = static_cast<int32_t>(ch);
           dj.values = idx->dict_values[ch];
-          dj.str_pos = idx->dict_str_pos[ch];
-          dj.str_len = idx->dict_str_len[ch];
+          dj.str_ent = idx->dict_str_ent[ch];
           if (cd.ptype != pqi::T_BYTE_ARRAY)
             plan->max_fixed_dict_bytes =
                 std::max<int>(plan->max_fixed_dict_bytes, dp.num_values * cd.width);
@@ -739,6 +757,10 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
         if (pg.encoding == pqi::ENC_DELTA_BP) {
           pp.dtab = static_cast<uint32_t>(plan->delta_blocks);
           plan->delta_blocks += pg.num_values > 1 ? static_cast<uint64_t>(pg.num_values - 2) / 128 + 1 : 1;
+          pp.dreg = static_cast<uint32_t>(plan->delta_regions);
+          pp.dreg_cap = static_cast<int32_t>(pg.uncompressed / pqi::DELTA_REGION + 2);
+          plan->delta_regions += static_cast<uint64_t>(pp.dreg_cap);
+          cw.max_regions = std::max(cw.max_regions, pp.dreg_cap);
           plan->delta_pps.push_back(static_cast<uint32_t>(plan->pps.size()));
         }
         if (needs_walk && !plain) {
@@ -772,20 +794,28 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
       }
     }
     col.item_count = static_cast<uint32_t>(plan->items.size()) - col.item_begin;
+    cw.snap_data_n = static_cast<int>(plan->snappy_data.size()) - cw.snap_data_begin;
+    cw.snap_dict_n = static_cast<int>(plan->snappy_dict.size()) - cw.snap_dict_begin;
+    cw.dict_n = static_cast<int>(plan->dict_jobs.size()) - cw.dict_begin;
+    cw.walk_n = static_cast<int>(plan->walk_pps.size()) - cw.walk_begin;
+    cw.delta_n = static_cast<int>(plan->delta_pps.size()) - cw.delta_begin;
+    cw.max_fixed_dict = plan->max_fixed_dict_bytes;
+    plan->max_fixed_dict_bytes = std::max(max_fixed_before, plan->max_fixed_dict_bytes);
+    plan->colwork.push_back(cw);
     sz.chars_bytes = chars;
     if (cm.type == pqi::T_BYTE_ARRAY) plan->str_cols.push_back(static_cast<int32_t>(oc));
     plan->decoded_bytes += sz.values_bytes + sz.validity_bytes + sz.chars_bytes;
     plan->outcols.push_back(col);
     plan->sizes.push_back(sz);
   }
-  // walk list: longest header chains first
-  {
-    std::vector<size_t> order(plan->walk_pps.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  // walk list: inside each column, longest header chains first
+  for (const auto& cw : plan->colwork) {
+    std::vector<size_t> order(cw.walk_n);
+    for (int i = 0; i < cw.walk_n; ++i) order[i] = cw.walk_begin + i;
     std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return walk_cost[x] > walk_cost[y]; });
     std::vector<uint32_t> sorted(order.size());
     for (size_t i = 0; i < order.size(); ++i) sorted[i] = plan->walk_pps[order[i]];
-    plan->walk_pps.swap(sorted);
+    std::copy(sorted.begin(), sorted.end(), plan->walk_pps.begin() + cw.walk_begin);
   }
   // device arrays
   const size_t npp = plan->pps.size(), nit = plan->items.size();
@@ -793,6 +823,8 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
   plan->d_delta_pps = plan_alloc(uint32_t, plan.get(), plan->delta_pps.size());
   plan->d_dpos = plan_alloc(uint32_t, plan.get(), plan->delta_blocks);
   plan->d_dbase = plan_alloc(int64_t, plan.get(), plan->delta_blocks);
+  plan->d_dregs = plan_alloc(pqi::DeltaRegion, plan.get(), plan->delta_regions);
+  plan->d_dreg_lists = plan_alloc(uint32_t, plan.get(), plan->delta_regions * pqi::DELTA_REGION_LIST);
   plan->d_pps = plan_alloc(pqi::PlanPage, plan.get(), npp);
   plan->d_items = plan_alloc(pqi::Item, plan.get(), nit);
   plan->d_cols = plan_alloc(pqi::OutCol, plan.get(), plan->outcols.size());
@@ -814,7 +846,8 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
     free_plan_device(plan.get());
     return fail(ctx, PQ_ERR_OOM, "plan scratch");
   }
-  plan->scratch_bytes = scratch + str_rows * 4 + (plan->d_str_items ? nit * 8 : 0) + plan->delta_blocks * 12;
+  plan->scratch_bytes = scratch + str_rows * 4 + (plan->d_str_items ? nit * 8 : 0) + plan->delta_blocks * 12 +
+                        plan->delta_regions * (sizeof(pqi::DeltaRegion) + 4ull * pqi::DELTA_REGION_LIST);
   // rebase scratch bodies, string scratch per column
   size_t jd = 0;
   for (auto& pp : plan->pps) {
@@ -856,6 +889,9 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
   CK(cudaEventCreateWithFlags(&plan->done, cudaEventDisableTiming));
   if (plan->flags & PQ_SCAN_TIMING)
     for (auto& e : plan->stage_ev) CK(cudaEventCreate(&e));
+  CK(cudaEventCreateWithFlags(&plan->fork, cudaEventDisableTiming));
+  plan->join.assign(plan->outcols.size(), nullptr);
+  for (auto& e : plan->join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   {
     // kernels per scan: prepare, snappy, dictionary (2), walk + expand or one
     // plain launch (+ its snappy) per chunk, strings (2)
@@ -873,10 +909,13 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
         job += nj;
       }
     } else {
-      n += (plan->snappy_data.size() + plan->snappy_dict.size() ? 1 : 0) + (any_dict ? 2 : 0);
-      n += (plan->walk_pps.empty() ? 0 : 1) + (plan->delta_pps.empty() ? 0 : 1) + (nit ? 1 : 0);
+      for (size_t oc = 0; oc < plan->colwork.size(); ++oc) {
+        const auto& cw = plan->colwork[oc];
+        n += (cw.snap_dict_n ? 1 : 0) + (cw.dict_n ? 2 : 0) + (cw.snap_data_n ? 1 : 0) + (cw.walk_n ? 1 : 0) +
+             (cw.delta_n ? 4 : 0) + (plan->outcols[oc].item_count ? 1 : 0);
+      }
     }
-    n += plan->str_cols.empty() ? 0 : 2;
+    for (int32_t sc : plan->str_cols) n += plan->outcols[sc].item_count ? 2 : 0;
     plan->launches = n;
   }
   const int wbps = pqi::walk_blocks_per_sm(), ebps = pqi::expand_blocks_per_sm();
@@ -923,7 +962,31 @@ pq_status pq_plan_stage_ms(const pq_plan* plan, float* ms) {
 
 // ------------------------------------------------------------------ scan
 
-// Enqueues the kernels of one scan (no host synchronisation).
+// Kernels of one output column, in order, on one stream.
+static void enqueue_column(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, bool with_dicts, cudaStream_t s) {
+  pq_ctx* ctx = plan->ctx;
+  const auto& cw = plan->colwork[oc];
+  const int n_data_total = static_cast<int>(plan->snappy_data.size());
+  if (with_dicts && cw.snap_dict_n)
+    pqi::launch_snappy(plan->d_snappy + n_data_total + cw.snap_dict_begin, cw.snap_dict_n, ctx->n_sms, a.st, s);
+  if (with_dicts && cw.dict_n)
+    pqi::launch_dict(plan->d_dict_jobs + cw.dict_begin, cw.dict_n, cw.max_fixed_dict, plan->idx->d_dicts, ctx->n_sms,
+                     a.st, s);
+  if (cw.snap_data_n) pqi::launch_snappy(plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, ctx->n_sms, a.st, s);
+  pqi::launch_walk(a, cw.walk_begin, cw.walk_n, s);
+  pqi::launch_delta_bases(a, cw.delta_begin, cw.delta_n, cw.max_regions, s);
+  const auto& col = plan->outcols[oc];
+  pqi::launch_expand(a, static_cast<int>(col.item_begin), static_cast<int>(col.item_count), s);
+  if (col.ptype == pqi::T_BYTE_ARRAY)
+    pqi::launch_strings(a, static_cast<int>(oc), static_cast<int>(col.item_count), ctx->n_sms, s);
+}
+
+// Enqueues the kernels of one scan (no host synchronisation).  Default:
+// every output column is an independent branch (fork/join through events on
+// the context's branch streams), so that the serial header chains of one
+// column overlap the bandwidth-bound expansion of the others.  With
+// PQ_SCAN_TIMING the stages run one after another over all columns, so that
+// each stage can be timed.  PQ_SCAN_PLAIN: per chunk, one launch per stage.
 static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts) {
   pq_ctx* ctx = plan->ctx;
   pqi::DecodeArgs a = decode_args(plan);
@@ -948,7 +1011,6 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts) {
     size_t job = 0;
     for (size_t k = 0; k < plan->chunk_pp.size(); ++k) {
       const int first = plan->chunk_pp[k].first, n = plan->chunk_pp[k].second;
-      // this chunk's compressed pages are the next jobs in order
       int nj = 0;
       for (int p = first; p < first + n; ++p)
         if (job + nj < plan->snappy_data.size() && plan->snappy_data[job + nj].page == static_cast<int32_t>(plan->pps[p].page))
@@ -959,23 +1021,45 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts) {
     }
     mark(4);
     mark(5);
-  } else {
-    if (n_data_jobs + (with_dicts ? n_dict_jobs : 0))
-      pqi::launch_snappy(plan->d_snappy, n_data_jobs + (with_dicts ? n_dict_jobs : 0), ctx->n_sms, a.st, s);
+    for (int32_t sc : plan->str_cols)
+      pqi::launch_strings(a, sc, static_cast<int>(plan->outcols[sc].item_count), ctx->n_sms, s);
+  } else if (timing) {
+    for (int oc = 0; oc < ncols; ++oc) {
+      const auto& cw = plan->colwork[oc];
+      if (with_dicts && cw.snap_dict_n)
+        pqi::launch_snappy(plan->d_snappy + n_data_jobs + cw.snap_dict_begin, cw.snap_dict_n, ctx->n_sms, a.st, s);
+      if (cw.snap_data_n) pqi::launch_snappy(plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, ctx->n_sms, a.st, s);
+    }
     mark(2);
-    if (with_dicts && !plan->dict_jobs.empty())
-      pqi::launch_dict(plan->d_dict_jobs, static_cast<int>(plan->dict_jobs.size()), plan->max_fixed_dict_bytes,
-                       plan->idx->d_dicts, ctx->n_sms, a.st, s);
+    for (int oc = 0; oc < ncols; ++oc) {
+      const auto& cw = plan->colwork[oc];
+      if (with_dicts && cw.dict_n)
+        pqi::launch_dict(plan->d_dict_jobs + cw.dict_begin, cw.dict_n, cw.max_fixed_dict, plan->idx->d_dicts,
+                         ctx->n_sms, a.st, s);
+    }
     mark(3);
-    pqi::launch_walk(a, plan->walk_grid, s);
-    pqi::launch_delta_bases(a, s);
+    for (int oc = 0; oc < ncols; ++oc) {
+      const auto& cw = plan->colwork[oc];
+      pqi::launch_walk(a, cw.walk_begin, cw.walk_n, s);
+      pqi::launch_delta_bases(a, cw.delta_begin, cw.delta_n, cw.max_regions, s);
+    }
     mark(4);
-    pqi::launch_expand(a, plan->expand_grid, s);
+    for (int oc = 0; oc < ncols; ++oc)
+      pqi::launch_expand(a, static_cast<int>(plan->outcols[oc].item_begin),
+                         static_cast<int>(plan->outcols[oc].item_count), s);
     mark(5);
+    for (int32_t sc : plan->str_cols)
+      pqi::launch_strings(a, sc, static_cast<int>(plan->outcols[sc].item_count), ctx->n_sms, s);
+  } else {
+    cudaEventRecord(plan->fork, s);
+    for (int oc = 0; oc < ncols; ++oc) {
+      cudaStream_t b = ctx->branch[oc % pq_ctx::kBranches];
+      cudaStreamWaitEvent(b, plan->fork, 0);
+      enqueue_column(plan, oc, a, with_dicts, b);
+      cudaEventRecord(plan->join[oc], b);
+    }
+    for (int oc = 0; oc < ncols; ++oc) cudaStreamWaitEvent(s, plan->join[oc], 0);
   }
-  if (!plan->str_cols.empty())
-    pqi::launch_strings(a, plan->d_str_cols, static_cast<int>(plan->str_cols.size()), ncols,
-                        std::min<int>(static_cast<int>(plan->items.size()), ctx->n_sms * 8), s);
   mark(6);
   // status and string totals back to pinned host memory
   cudaMemcpyAsync(plan->h_out.p, plan->d_status, sizeof(pqi::DevStatus), cudaMemcpyDeviceToHost, s);

@@ -46,6 +46,8 @@ struct Pinned {
 struct pq_ctx {
   int device = 0;
   int n_sms = 0;
+  static constexpr int kBranches = 8;
+  cudaStream_t branch[kBranches] = {};  // per-column branches of a scan
   std::string last_error;
   pqe::DevPool pool;
   pqe::Pinned tail;     // footer staging
@@ -74,8 +76,7 @@ struct pq_index {
   pqi::DevStatus* d_status = nullptr;
   // dictionary buffers (index-owned), per chunk
   std::vector<uint8_t*> dict_values;
-  std::vector<uint32_t*> dict_str_pos;
-  std::vector<uint32_t*> dict_str_len;
+  std::vector<uint64_t*> dict_str_ent;
   std::vector<uint8_t*> dict_body;        // decompressed dictionary page (compressed chunks)
   std::vector<uint8_t> dict_resident;     // 1 once decoded and kept
   uint64_t stored_bytes = 0;
@@ -102,6 +103,7 @@ struct pq_plan {
   std::vector<uint32_t> walk_pps;            // plan pages that need the walk, longest first
   std::vector<uint32_t> delta_pps;           // DELTA plan pages
   uint64_t delta_blocks = 0;                 // capacity of the DELTA block tables
+  uint64_t delta_regions = 0;                // capacity of the DELTA region tables
   // per chunk: range of plan pages (plain baseline launches per chunk)
   std::vector<std::pair<int32_t, int32_t>> chunk_pp;  // (first pp, count)
   std::vector<int32_t> chunk_pp_chunk;
@@ -124,6 +126,8 @@ struct pq_plan {
   uint32_t* d_delta_pps = nullptr;
   uint32_t* d_dpos = nullptr;
   int64_t* d_dbase = nullptr;
+  pqi::DeltaRegion* d_dregs = nullptr;
+  uint32_t* d_dreg_lists = nullptr;
   pqi::DevStatus* d_status = nullptr;
   std::vector<void*> owned;                  // pool blocks to release
   // host staging (pinned): output descriptors in, status + string totals out
@@ -135,6 +139,19 @@ struct pq_plan {
   bool dicts_in_graph = true;
   int walk_grid = 0, expand_grid = 0;
   int launches = 0;
+  // per output column: ranges into the job lists
+  struct ColWork {
+    int snap_data_begin = 0, snap_data_n = 0;  // into snappy_data
+    int snap_dict_begin = 0, snap_dict_n = 0;  // into snappy_dict
+    int dict_begin = 0, dict_n = 0;            // into dict_jobs
+    int max_fixed_dict = 0;
+    int walk_begin = 0, walk_n = 0;            // into walk_pps
+    int delta_begin = 0, delta_n = 0;          // into delta_pps
+    int max_regions = 0;                       // most DELTA regions of one page
+  };
+  std::vector<ColWork> colwork;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
   cudaEvent_t stage_ev[PQ_N_STAGES + 1] = {};
 };
 

@@ -285,15 +285,22 @@ __global__ void __launch_bounds__(32) k_dict_str(const DictJob* __restrict__ job
     const uint32_t lim = c.n0 - 16;
     const uint32_t wb = static_cast<uint32_t>(c.w0);
     const uint32_t* w32 = reinterpret_cast<const uint32_t*>(c.b0);
+    // software-pipelined: the next length word is loaded before this
+    // entry is checked and stored
+    uint32_t x0 = w32[o >> 2], x1 = w32[(o >> 2) + 1];
     do {
-      const uint32_t i = o >> 2, sh = (o & 3u) << 3;
-      const uint32_t len = __funnelshift_r(w32[i], w32[i + 1], sh);
+      const uint32_t sh = (o & 3u) << 3;
+      const uint32_t len = __funnelshift_r(x0, x1, sh);
+      const uint32_t on = o + 4 + len;
+      if (on <= lim) {
+        x0 = w32[on >> 2];
+        x1 = w32[(on >> 2) + 1];
+      }
       const uint32_t p = o + wb;
       if (p + 4 > blen || len > blen - p - 4) { bad = true; break; }
-      j.str_pos[k] = p + 4;
-      j.str_len[k] = len;
+      j.str_ent[k] = (static_cast<uint64_t>(p + 4) << 32) | len;
       maxlen = len > maxlen ? len : maxlen;
-      o += 4 + len;
+      o = on;
       ++k;
     } while (k < j.n && o <= lim);
     if (bad) break;
@@ -305,8 +312,7 @@ __global__ void __launch_bounds__(32) k_dict_str(const DictJob* __restrict__ job
     return;
   }
   DictDev d{};
-  d.str_pos = j.str_pos;
-  d.str_len = j.str_len;
+  d.str_ent = j.str_ent;
   d.chars = j.body;
   d.n = j.n;
   d.max_len = static_cast<int32_t>(maxlen);
@@ -773,7 +779,7 @@ __device__ bool delta_header(const uint8_t* sb, uint32_t slen, DeltaHdr* d) {
 // offset.  The common layout (4 miniblocks of 32 values, one-byte min delta,
 // a full block) takes the fast step: size = 5 + 4 * (sum of the 4 widths).
 __device__ bool walk_delta(WalkSmem& sm, const uint8_t* sb, uint32_t slen, int type_bits, int32_t total,
-                           PlanPage* ppw, uint32_t* dpos, uint32_t dcap, int pgid, DevStatus* st) {
+                           PlanPage* ppw, uint32_t* dpos, uint32_t dcap, bool serial, int pgid, DevStatus* st) {
   if (threadIdx.x == 0) {
     int err = 0;
     DeltaHdr d{};
@@ -781,6 +787,17 @@ __device__ bool walk_delta(WalkSmem& sm, const uint8_t* sb, uint32_t slen, int t
     else if (d.total != total) err = 1;
     int32_t nblocks = 0;
     Chain c = make_chain(sm);
+    if (!err && !serial) {
+      // batched scan: the block chain is found by the parallel region walk
+      ppw->dfirst = d.first;
+      ppw->dbs = d.block;
+      ppw->dvpm = d.vpm;
+      ppw->dmbc = d.mbc;
+      ppw->dhlen = d.hlen;
+      ppw->dblocks = total > 1 ? -2 : 0;
+      sm.ctl[5] = 0;
+      goto done;
+    }
     if (!err && total > 1) {
       if (!ch_start(c, sb, slen)) err = 3;
       int64_t pos = d.hlen;
@@ -874,9 +891,11 @@ __device__ bool walk_delta(WalkSmem& sm, const uint8_t* sb, uint32_t slen, int t
       ppw->dbs = d.block;
       ppw->dvpm = d.vpm;
       ppw->dmbc = d.mbc;
+      ppw->dhlen = d.hlen;
     }
     sm.ctl[5] = err;
   }
+done:
   __syncthreads();
   return sm.ctl[5] == 0;
 }
@@ -930,7 +949,7 @@ __device__ bool walk_plain_ba(WalkSmem& sm, const uint8_t* sb, uint32_t slen, in
 }
 
 // Walk of one page (block-collective).
-__device__ void walk_page(const DecodeArgs& a, int p, WalkSmem& sm) {
+__device__ void walk_page(const DecodeArgs& a, int p, WalkSmem& sm, bool serial_delta) {
   const int tid = threadIdx.x;
   const PlanPage pp = a.pps[p];
   const PageDev pg = a.pages[pp.page];
@@ -985,8 +1004,8 @@ __device__ void walk_page(const DecodeArgs& a, int p, WalkSmem& sm) {
       ok = false;
     } else {
       const uint32_t cap = static_cast<uint32_t>(nonnull > 1 ? (nonnull - 2) / 128 + 1 : 0);
-      ok = walk_delta(sm, sb, slen, pc.ptype == T_INT32 ? 32 : 64, nonnull, a.pps + p, a.dpos + pp.dtab, cap, pgid,
-                      a.st);
+      ok = walk_delta(sm, sb, slen, pc.ptype == T_INT32 ? 32 : 64, nonnull, a.pps + p, a.dpos + pp.dtab, cap,
+                      serial_delta, pgid, a.st);
     }
   } else {
     if (tid == 0) report(a.st, DERR_UNSUPPORTED, pgid, WHERE_WALK_VALUES, 14);
@@ -1009,17 +1028,304 @@ __device__ __forceinline__ void walk_init(WalkSmem& sm) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(WALK_THREADS) k_walk(DecodeArgs a) {
+// One thread block per page of walk list entries [wbegin, wbegin + gridDim.x).
+__global__ void __launch_bounds__(WALK_THREADS) k_walk(DecodeArgs a, int wbegin) {
   extern __shared__ __align__(16) uint8_t smraw[];
   WalkSmem& sm = *reinterpret_cast<WalkSmem*>(smraw);
   walk_init(sm);
-  for (uint32_t guard = 0; guard <= static_cast<uint32_t>(a.n_walk); ++guard) {
-    if (threadIdx.x == 0) sm.ctl[13] = static_cast<int32_t>(atomicAdd(a.item_counter + 1, 1u));
-    __syncthreads();
-    const int w = sm.ctl[13];
-    __syncthreads();
-    if (w >= a.n_walk) break;
-    walk_page(a, static_cast<int>(a.walk_pps[w]), sm);
+  walk_page(a, static_cast<int>(a.walk_pps[wbegin + blockIdx.x]), sm, false);
+}
+
+// ------------------------------------------------------------------ DELTA: parallel block chain
+
+constexpr int DREG_TAIL = 4096;      // bytes staged past a region for its last blocks
+constexpr int DREG_LEAD = 1024;      // lead-in searched before a region for a block start
+constexpr int DREG_SMEM = DREG_LEAD + DELTA_REGION + DREG_TAIL + 32;
+constexpr uint32_t DB_UNKNOWN = 0xffffffffu;
+
+// Size of the full block whose header starts at smem offset o (avail bytes
+// staged from there): 0 when implausible (varint too long, a width above the
+// type's bits), DB_UNKNOWN when the staged bytes do not decide.
+__device__ __forceinline__ uint32_t dblock_size_s(const uint8_t* sm, uint32_t o, uint32_t avail, int mbc, int vpm,
+                                                  int type_bits) {
+  if (avail < 10u + static_cast<uint32_t>(mbc)) return DB_UNKNOWN;
+  int vl = 0;
+  for (int i = 0; i < 10; ++i)
+    if (!(sm[o + i] & 0x80u)) {
+      vl = i + 1;
+      break;
+    }
+  if (!vl || (type_bits == 32 && vl > 5)) return 0;
+  uint32_t bits = 0;
+  for (int m = 0; m < mbc; ++m) {
+    const uint32_t w = sm[o + vl + m];
+    if (static_cast<int>(w) > type_bits) return 0;
+    bits += w * static_cast<uint32_t>(vpm);
+  }
+  return static_cast<uint32_t>(vl + mbc) + bits / 8;
+}
+
+// Same from global memory (slow path).
+__device__ uint32_t dblock_size_g(const uint8_t* sb, uint32_t pos, uint32_t slen, int mbc, int vpm, int type_bits) {
+  if (pos >= slen) return 0;
+  int vl = 0;
+  for (int i = 0; i < 10 && pos + i < slen; ++i)
+    if (!(__ldg(sb + pos + i) & 0x80u)) {
+      vl = i + 1;
+      break;
+    }
+  if (!vl || (type_bits == 32 && vl > 5) || pos + vl + mbc > slen) return 0;
+  uint32_t bits = 0;
+  for (int m = 0; m < mbc; ++m) {
+    const uint32_t w = __ldg(sb + pos + vl + m);
+    if (static_cast<int>(w) > type_bits) return 0;
+    bits += w * static_cast<uint32_t>(vpm);
+  }
+  return static_cast<uint32_t>(vl + mbc) + bits / 8;
+}
+
+// One warp per region of one DELTA page.  Region i covers stream bytes
+// [h + i*R, h + (i+1)*R) (h: stream header bytes).  Region 0 starts on the
+// first block; region i > 0 searches its lead-in, DREG_LEAD bytes before the
+// region, for the first offset where four consecutive block headers are
+// plausible, and follows the chain from there.  A chain that starts on a
+// look-alike usually joins the true chain within a block or two, so by the
+// region's first byte it is on the true chain; k_dfix checks that and
+// repairs the rare region where it is not.  Block starts inside the region
+// go to the region's list; the first start at or after its end is its exit.
+__global__ void __launch_bounds__(32) k_dreg(DecodeArgs a, int dbegin) {
+  extern __shared__ __align__(16) uint8_t smraw[];
+  __shared__ uint64_t bar;
+  const int lane = threadIdx.x;
+  const int p = static_cast<int>(a.delta_pps[dbegin + blockIdx.y]);
+  const PlanPage pp = a.pps[p];
+  if (pp.dblocks != -2 || pp.nonnull < 0 || static_cast<int>(blockIdx.x) >= pp.dreg_cap) return;
+  const int i = blockIdx.x;
+  const uint8_t* sb = pp.body + pp.values_off;
+  const uint32_t slen = static_cast<uint32_t>(pp.body_len - pp.values_off);
+  const int type_bits = a.chunks[pp.chunk].ptype == T_INT32 ? 32 : 64;
+  DeltaRegion* R = a.dregs + pp.dreg + i;
+  uint32_t* list = a.dreg_lists + static_cast<uint64_t>(pp.dreg + i) * DELTA_REGION_LIST;
+  const uint64_t start64 = static_cast<uint64_t>(pp.dhlen) + static_cast<uint64_t>(i) * DELTA_REGION;
+  if (start64 >= slen) {
+    if (lane == 0) *R = DeltaRegion{-1, -1, 0, 0};
+    return;
+  }
+  const uint32_t start = static_cast<uint32_t>(start64);
+  const uint32_t end = slen - start < static_cast<uint32_t>(DELTA_REGION) ? slen : start + DELTA_REGION;
+  const uint32_t sstart = i == 0 ? start : start - DREG_LEAD;  // region i > 0: start >= h + R > DREG_LEAD
+  // stage [sstart, end + tail), 16-byte aligned, at most 16 bytes past the stream
+  const uint8_t* g = sb + sstart;
+  const uint8_t* ga = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(g) & ~uintptr_t(15));
+  const uint32_t shift = static_cast<uint32_t>(g - ga);
+  const uint64_t lim_end = (end + DREG_TAIL < slen ? end + DREG_TAIL : slen);
+  uint32_t bytes = static_cast<uint32_t>(((sb + lim_end) - ga + 16) & ~int64_t(15));
+  if (bytes > static_cast<uint32_t>(DREG_SMEM)) bytes = DREG_SMEM;
+  if (lane == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bar, bytes);
+    bulk_g2s(smraw, ga, bytes, &bar);
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(&bar, 0);
+  if (!__all_sync(0xffffffffu, ok)) {
+    if (lane == 0) {
+      report(a.st, DERR_TIMEOUT, static_cast<int>(pp.page), WHERE_WALK_VALUES, 30);
+      mbar_wait(&bar, 0);
+      *R = DeltaRegion{-1, -1, 0, 0};
+    }
+    return;
+  }
+  // stream offset s is at smem offset s - sstart + shift; staged bytes end at known_end
+  const uint32_t known_end = sstart - shift + bytes > slen + 16 ? slen + 16 : sstart - shift + bytes;
+  auto avail = [&](uint32_t s) -> uint32_t { return s < known_end ? known_end - s : 0u; };
+  auto at = [&](uint32_t s) -> uint32_t { return s - sstart + shift; };
+  uint32_t q = 0xffffffffu;
+  if (i == 0) {
+    q = start;
+  } else {
+    for (uint32_t c0 = sstart; c0 < end && q == 0xffffffffu; c0 += 32) {
+      const uint32_t cand = c0 + lane;
+      bool good = cand < end;
+      uint32_t pos = cand;
+      for (int k = 0; good && k < 4 && pos < slen; ++k) {
+        const uint32_t sz = dblock_size_s(smraw, at(pos), avail(pos), pp.dmbc, pp.dvpm, type_bits);
+        if (sz == 0) good = false;
+        else if (sz == DB_UNKNOWN) break;
+        else pos += sz;
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, good);
+      if (m) q = c0 + __ffs(m) - 1;
+    }
+  }
+  if (lane == 0) {
+    int32_t first = -1, cnt = 0, x = -1;
+    if (q != 0xffffffffu) {
+      uint32_t pos = q;
+      while (true) {
+        if (pos >= end) {
+          x = static_cast<int32_t>(pos);
+          break;
+        }
+        if (pos >= start) {
+          if (cnt == DELTA_REGION_LIST) break;  // list full: k_dfix walks the rest
+          if (first < 0) first = static_cast<int32_t>(pos);
+          list[cnt++] = pos;
+        }
+        const uint32_t sz = dblock_size_s(smraw, at(pos), avail(pos), pp.dmbc, pp.dvpm, type_bits);
+        if (sz == 0 || sz == DB_UNKNOWN) break;  // the page's last block, or a false chain
+        pos += sz;
+      }
+    }
+    *R = DeltaRegion{first, first >= 0 ? x : -1, cnt, 0};
+  }
+}
+
+// Serial chain of one region from its true entry `pos`: block starts go
+// straight to `out` until the chain reaches `end`, `want` blocks, or one of
+// the region's recorded starts (list[j..cnt), from which the list is right).
+// Returns the blocks written; *pe gets the offset reached, *jm the list
+// index joined (-1 if none), *bad is set when a block other than the page's
+// last looks malformed.
+__device__ int32_t dwalk_join(const uint8_t* sb, uint32_t slen, uint32_t pos, uint32_t end, int32_t want,
+                              const uint32_t* list, int32_t cnt, bool list_exits, int mbc, int vpm,
+                              int type_bits, uint32_t* out, uint32_t* pe, int32_t* jm, bool* bad) {
+  int32_t j = 0;
+  if (cnt > 0) {  // first recorded start >= pos
+    int lo = 0, hi = cnt;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (list[mid] < pos) lo = mid + 1; else hi = mid;
+    }
+    j = lo;
+  }
+  int32_t c = 0;
+  *jm = -1;
+  while (pos < end && c < want) {
+    while (j < cnt && list[j] < pos) ++j;
+    if (j < cnt && list[j] == pos && (list_exits || cnt - j >= want - c)) {
+      *jm = j;
+      break;
+    }
+    out[c++] = pos;
+    const uint32_t sz = dblock_size_g(sb, pos, slen, mbc, vpm, type_bits);
+    if (sz == 0) {
+      if (c < want) *bad = true;
+      break;
+    }
+    pos += sz;
+  }
+  *pe = pos;
+  return c;
+}
+
+// Per DELTA page: stitch the regions.  The true chain enters region i at the
+// exit of region i-1; when that is the region's first recorded start the
+// list is taken whole, otherwise the region is walked serially from the
+// entry until it joins the list.  The lists are then copied to the page's
+// block table in parallel and the last block is checked against the
+// stream's end.
+__global__ void __launch_bounds__(256) k_dfix(DecodeArgs a, int dbegin) {
+  constexpr int MAXR = 1024;
+  __shared__ int32_t s_q[MAXR], s_x[MAXR], s_c[MAXR];
+  __shared__ int32_t s_skip[MAXR], s_cnt[MAXR], s_base[MAXR];
+  __shared__ int32_t s_nreg, s_ok;
+  const int p = static_cast<int>(a.delta_pps[dbegin + blockIdx.x]);
+  const PlanPage pp = a.pps[p];
+  if (pp.dblocks != -2 || pp.nonnull < 0) return;
+  const uint8_t* sb = pp.body + pp.values_off;
+  const uint32_t slen = static_cast<uint32_t>(pp.body_len - pp.values_off);
+  const int type_bits = a.chunks[pp.chunk].ptype == T_INT32 ? 32 : 64;
+  const int32_t B = (pp.nonnull - 1 + pp.dbs - 1) / pp.dbs;  // blocks of the page
+  uint32_t* dpos = a.dpos + pp.dtab;
+  const uint32_t h = static_cast<uint32_t>(pp.dhlen);
+  const int nreg = slen > h ? static_cast<int>((slen - h + DELTA_REGION - 1) / DELTA_REGION) : 0;
+  const bool regions = nreg <= pp.dreg_cap && nreg <= MAXR;
+  if (regions)
+    for (int i = threadIdx.x; i < nreg; i += blockDim.x) {
+      const DeltaRegion r = a.dregs[pp.dreg + i];
+      s_q[i] = r.q;
+      s_x[i] = r.x;
+      s_c[i] = r.cnt;
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool bad = false;
+    uint32_t e = h;
+    int32_t b = 0, jm;
+    if (!regions) {
+      b = dwalk_join(sb, slen, e, slen, B, nullptr, 0, false, pp.dmbc, pp.dvpm, type_bits, dpos, &e, &jm, &bad);
+      s_nreg = 0;
+    } else {
+      for (int i = 0; i < nreg; ++i) {
+        const uint32_t start = h + static_cast<uint32_t>(i) * DELTA_REGION;
+        const uint32_t end = slen - start < static_cast<uint32_t>(DELTA_REGION) ? slen : start + DELTA_REGION;
+        s_skip[i] = -1;
+        s_cnt[i] = 0;
+        if (b >= B || e >= end || bad) continue;
+        const int32_t cnt = s_q[i] >= 0 ? s_c[i] : 0;
+        const bool exits = s_x[i] >= 0;
+        int32_t j = -1;
+        if (cnt > 0 && static_cast<uint32_t>(s_q[i]) == e && (exits || cnt >= B - b)) {
+          j = 0;
+        } else {
+          const uint32_t* list = a.dreg_lists + static_cast<uint64_t>(pp.dreg + i) * DELTA_REGION_LIST;
+          b += dwalk_join(sb, slen, e, end, B - b, list, cnt, exits, pp.dmbc, pp.dvpm, type_bits, dpos + b, &e,
+                          &j, &bad);
+        }
+        if (j >= 0) {
+          const int32_t c = cnt - j < B - b ? cnt - j : B - b;
+          s_skip[i] = j;
+          s_cnt[i] = c;
+          s_base[i] = b;
+          b += c;
+          e = exits ? static_cast<uint32_t>(s_x[i]) : end;
+        }
+      }
+      s_nreg = nreg;
+    }
+    s_ok = !bad && b == B;
+  }
+  __syncthreads();
+  if (s_ok) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x >> 5; i < s_nreg; i += nw) {
+      if (s_skip[i] < 0) continue;
+      const uint32_t* list = a.dreg_lists + static_cast<uint64_t>(pp.dreg + i) * DELTA_REGION_LIST + s_skip[i];
+      for (int j = lane; j < s_cnt[i]; j += 32) dpos[s_base[i] + j] = list[j];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool ok = s_ok;
+    if (ok && B > 0) {
+      // the last block, partial or not: its used miniblocks lie inside the stream
+      const uint32_t pos = dpos[B - 1];
+      const int32_t nv = pp.nonnull - 1 - (B - 1) * pp.dbs;
+      const int used = (nv + pp.dvpm - 1) / pp.dvpm;
+      int vl = 0;
+      for (int k = 0; k < 10 && pos + k < slen; ++k)
+        if (!(__ldg(sb + pos + k) & 0x80u)) {
+          vl = k + 1;
+          break;
+        }
+      uint64_t bits = 0;
+      if (!vl || pos + vl + pp.dmbc > slen) ok = false;
+      for (int m = 0; ok && m < used; ++m) {
+        const uint32_t w = __ldg(sb + pos + vl + m);
+        if (static_cast<int>(w) > type_bits) ok = false;
+        bits += static_cast<uint64_t>(w) * pp.dvpm;
+      }
+      if (ok && pos + vl + pp.dmbc + bits / 8 > slen) ok = false;
+    }
+    if (!ok) {
+      report(a.st, DERR_CORRUPT, static_cast<int>(pp.page), WHERE_WALK_VALUES, 31);
+      a.pps[p].dblocks = -1;
+    } else {
+      a.pps[p].dblocks = B;
+    }
   }
 }
 
@@ -1089,9 +1395,9 @@ __device__ bool delta_block_sum(const uint8_t* sb, const PlanPage& pp, const uin
 
 // Block sums of every DELTA page, spread over the whole GPU: blockIdx.y is
 // the page, warps stride over its blocks.  The sums land in dbase.
-__global__ void __launch_bounds__(256) k_delta_sums(DecodeArgs a) {
+__global__ void __launch_bounds__(256) k_delta_sums(DecodeArgs a, int dbegin) {
   const int lane = threadIdx.x & 31;
-  const int p = static_cast<int>(a.delta_pps[blockIdx.y]);
+  const int p = static_cast<int>(a.delta_pps[dbegin + blockIdx.y]);
   const PlanPage pp = a.pps[p];
   if (pp.dblocks <= 0 || pp.nonnull < 0) return;
   const uint8_t* sb = pp.body + pp.values_off;
@@ -1138,9 +1444,9 @@ __device__ void delta_scan_page(const DecodeArgs& a, int p, uint64_t* tmp) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_delta_scan(DecodeArgs a) {
+__global__ void __launch_bounds__(256) k_delta_scan(DecodeArgs a, int dbegin) {
   __shared__ uint64_t tmp[32];
-  delta_scan_page(a, static_cast<int>(a.delta_pps[blockIdx.x]), tmp);
+  delta_scan_page(a, static_cast<int>(a.delta_pps[dbegin + blockIdx.x]), tmp);
 }
 
 // One DELTA page inside one thread block (plain baseline).
@@ -1253,7 +1559,7 @@ __device__ bool warp_hybrid(const uint8_t* sb, uint32_t slen, int bw, int32_t to
           const int32_t j = j0 + u * 32 + lane;
           if (j < e) {
             sink.put(j - k0, idx[u]);
-            *chars += dd.str_len[idx[u]];
+            *chars += static_cast<uint32_t>(dd.str_ent[idx[u]]);
           }
         }
       } else if (dd.width == 4) {
@@ -1488,23 +1794,25 @@ __device__ void expand_item(const DecodeArgs& a, int it_id, WarpSmem& ws, int la
   }
 }
 
-__global__ void __launch_bounds__(EXP_THREADS) k_expand(DecodeArgs a) {
+// Items [ibegin, ibegin + icount): each warp decodes EXP_IPW consecutive items.
+constexpr int EXP_IPW = 2;
+
+__global__ void __launch_bounds__(EXP_THREADS) k_expand(DecodeArgs a, int ibegin, int icount) {
   __shared__ WarpSmem ws[EXP_WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint32_t guard = 0; guard <= static_cast<uint32_t>(a.n_items); ++guard) {
-    uint32_t u = 0;
-    if (lane == 0) u = atomicAdd(a.item_counter, 1u);
-    u = __shfl_sync(0xffffffffu, u, 0);
-    if (u >= static_cast<uint32_t>(a.n_items)) break;
-    expand_item(a, static_cast<int>(u), ws[warp], lane);
+  const int first = (blockIdx.x * EXP_WARPS + warp) * EXP_IPW;
+  for (int j = 0; j < EXP_IPW; ++j) {
+    const int u = first + j;
+    if (u >= icount) break;
+    expand_item(a, ibegin + u, ws[warp], lane);
   }
 }
 
 // ------------------------------------------------------------------ strings
 
 // Per string column: exclusive prefix of item chars; writes the final offset.
-__global__ void k_str_scan(DecodeArgs a, const int* __restrict__ str_cols) {
-  const OutCol col = a.cols[str_cols[blockIdx.x]];
+__global__ void k_str_scan(DecodeArgs a, int c) {
+  const OutCol col = a.cols[c];
   __shared__ uint64_t tmp[32];
   __shared__ uint64_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -1542,13 +1850,15 @@ __global__ void k_str_scan(DecodeArgs a, const int* __restrict__ str_cols) {
 // only at the chunk's two ends.
 constexpr int STR_STAGE = 2048;
 
-__global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a) {
+__global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a, int c) {
   __shared__ __align__(16) uint8_t stage[8][STR_STAGE + 16];
   const int lane = threadIdx.x & 31;
   uint8_t* sbuf = stage[threadIdx.x >> 5];
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int itx = gw; itx < a.n_items; itx += nw) {
+  const int ib = static_cast<int>(a.cols[c].item_begin);
+  const int ie = ib + static_cast<int>(a.cols[c].item_count);
+  for (int itx = ib + gw; itx < ie; itx += nw) {
     const Item it = a.items[itx];
     if (it.nrows <= 0) continue;
     const PlanPage pp = a.pps[it.pp];
@@ -1562,68 +1872,79 @@ __global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a) {
     uint64_t base = col.str_item_bytes[itx];
     const int64_t orow0 = pp.out_row + it.row0;
     int64_t* offs = reinterpret_cast<int64_t*>(col.values);
-    for (int r0 = 0; r0 < it.nrows; r0 += 32) {
-      const int r = r0 + lane;
-      uint32_t len = 0;
-      const uint8_t* src = nullptr;
-      if (r < it.nrows) {
-        const uint32_t s = col.str_scratch[orow0 + r];
-        if (s != NULL_IDX) {
-          if (isdict) {
-            len = dd.str_len[s];
-            src = dd.chars + dd.str_pos[s];
-          } else {
-            len = ld_le32_g(sb + s);
-            src = sb + s + 4;
-          }
-        }
-      }
-      uint64_t incl = len;
+    for (int g0 = 0; g0 < it.nrows; g0 += 256) {
+      // metadata of 8 chunks of 32 strings, loads issued together
+      uint32_t sidx[8];
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
+      for (int u = 0; u < 8; ++u) {
+        const int r = g0 + u * 32 + lane;
+        sidx[u] = r < it.nrows ? col.str_scratch[orow0 + r] : NULL_IDX;
       }
-      const uint64_t tot = __shfl_sync(0xffffffffu, incl, 31);
-      const uint64_t off = base + incl - len;
-      if (r < it.nrows) offs[orow0 + r] = static_cast<int64_t>(off);
-      if (base + tot <= col.chars_cap) {
-        const uint32_t a0 = static_cast<uint32_t>(base & 15);
-        if (a0 + tot <= STR_STAGE) {
-          // lanes place their strings, congruent to the output mod 16
-          uint8_t* d = sbuf + a0 + (off - base);
-          if (len) {
-            // aligned 4-byte loads of the source, bytes placed one by one
-            const uint32_t* sw = reinterpret_cast<const uint32_t*>(reinterpret_cast<uintptr_t>(src) & ~uintptr_t(3));
-            const uint32_t sh = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 3) * 8;
-            uint32_t cur = __ldg(sw);
-            for (uint32_t q = 0; q < len; q += 4) {
-              const uint32_t nxt = __ldg(sw + (q >> 2) + 1);
-              const uint32_t w = sh ? __funnelshift_r(cur, nxt, sh) : cur;
-              d[q] = static_cast<uint8_t>(w);
-              if (q + 1 < len) d[q + 1] = static_cast<uint8_t>(w >> 8);
-              if (q + 2 < len) d[q + 2] = static_cast<uint8_t>(w >> 16);
-              if (q + 3 < len) d[q + 3] = static_cast<uint8_t>(w >> 24);
-              cur = nxt;
-            }
+      uint64_t ent[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        ent[u] = 0;
+        if (sidx[u] != NULL_IDX) {
+          if (isdict) {
+            ent[u] = __ldg(dd.str_ent + sidx[u]);
+          } else {
+            ent[u] = (static_cast<uint64_t>(sidx[u] + 4) << 32) | ld_le32_g(sb + sidx[u]);
           }
-          __syncwarp();
-          uint8_t* g = col.chars + base;
-          const uint32_t head = a0 ? 16 - a0 : 0;
-          const uint32_t h = head < tot ? head : static_cast<uint32_t>(tot);
-          if (static_cast<uint32_t>(lane) < h) g[lane] = sbuf[a0 + lane];
-          const uint32_t nv = static_cast<uint32_t>((tot - h) >> 4);
-          const uint4* sv = reinterpret_cast<const uint4*>(sbuf + a0 + h);
-          uint4* gv = reinterpret_cast<uint4*>(g + h);
-          for (uint32_t q = lane; q < nv; q += 32) gv[q] = sv[q];
-          for (uint32_t q = h + (nv << 4) + lane; q < tot; q += 32) g[q] = sbuf[a0 + q];
-          __syncwarp();
-        } else if (r < it.nrows) {
-          uint8_t* d = col.chars + off;
-          for (uint32_t q = 0; q < len; ++q) d[q] = __ldg(src + q);
         }
       }
-      base += tot;
+      const uint8_t* cbase = isdict ? dd.chars : sb;
+      for (int u = 0; u < 8; ++u) {
+        const int r0 = g0 + u * 32;
+        if (r0 >= it.nrows) break;
+        const int r = r0 + lane;
+        const uint32_t len = static_cast<uint32_t>(ent[u]);
+        const uint8_t* src = cbase + (ent[u] >> 32);
+        uint64_t incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const uint64_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        const uint64_t off = base + incl - len;
+        if (r < it.nrows) offs[orow0 + r] = static_cast<int64_t>(off);
+        if (base + tot <= col.chars_cap) {
+          const uint32_t a0 = static_cast<uint32_t>(base & 15);
+          if (a0 + tot <= STR_STAGE) {
+            // lanes place their strings, congruent to the output mod 16
+            uint8_t* d = sbuf + a0 + (off - base);
+            if (len) {
+              const uint32_t* sw = reinterpret_cast<const uint32_t*>(reinterpret_cast<uintptr_t>(src) & ~uintptr_t(3));
+              const uint32_t sh = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 3) * 8;
+              uint32_t cur = __ldg(sw);
+              for (uint32_t q = 0; q < len; q += 4) {
+                const uint32_t nxt = __ldg(sw + (q >> 2) + 1);
+                const uint32_t w = sh ? __funnelshift_r(cur, nxt, sh) : cur;
+                d[q] = static_cast<uint8_t>(w);
+                if (q + 1 < len) d[q + 1] = static_cast<uint8_t>(w >> 8);
+                if (q + 2 < len) d[q + 2] = static_cast<uint8_t>(w >> 16);
+                if (q + 3 < len) d[q + 3] = static_cast<uint8_t>(w >> 24);
+                cur = nxt;
+              }
+            }
+            __syncwarp();
+            uint8_t* g = col.chars + base;
+            const uint32_t head = a0 ? 16 - a0 : 0;
+            const uint32_t h = head < tot ? head : static_cast<uint32_t>(tot);
+            if (static_cast<uint32_t>(lane) < h) g[lane] = sbuf[a0 + lane];
+            const uint32_t nv = static_cast<uint32_t>((tot - h) >> 4);
+            const uint4* sv = reinterpret_cast<const uint4*>(sbuf + a0 + h);
+            uint4* gv = reinterpret_cast<uint4*>(g + h);
+            for (uint32_t q = lane; q < nv; q += 32) gv[q] = sv[q];
+            for (uint32_t q = h + (nv << 4) + lane; q < tot; q += 32) g[q] = sbuf[a0 + q];
+            __syncwarp();
+          } else if (r < it.nrows) {
+            uint8_t* d = col.chars + off;
+            for (uint32_t q = 0; q < len; ++q) d[q] = __ldg(src + q);
+          }
+        }
+        base += tot;
+      }
     }
   }
 }
@@ -1641,7 +1962,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_plain_page(DecodeArgs a, int p
   const PageDev pg = a.pages[pp0.page];
   const ChunkDev ch = a.chunks[pp0.chunk];
   const bool needs_walk = ch.max_def || pg.encoding != ENC_PLAIN || ch.ptype == T_BYTE_ARRAY;
-  if (needs_walk) walk_page(a, p, sm);
+  if (needs_walk) walk_page(a, p, sm, true);
   __syncthreads();
   if (pg.encoding == ENC_DELTA_BP) {
     delta_bases_page(a, p, reinterpret_cast<uint64_t*>(sm.win[1]));
@@ -1706,28 +2027,39 @@ int expand_blocks_per_sm() {
   return g_exp_bps;
 }
 
-void launch_walk(const DecodeArgs& a, int grid, cudaStream_t s) {
-  if (a.n_walk <= 0) return;
-  k_walk<<<grid, WALK_THREADS, sizeof(WalkSmem), s>>>(a);
+void launch_walk(const DecodeArgs& a, int wbegin, int n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_walk<<<n, WALK_THREADS, sizeof(WalkSmem), s>>>(a, wbegin);
 }
 
-void launch_delta_bases(const DecodeArgs& a, cudaStream_t s) {
-  if (a.n_delta <= 0) return;
-  k_delta_sums<<<dim3(32, a.n_delta), 256, 0, s>>>(a);
-  k_delta_scan<<<a.n_delta, 256, 0, s>>>(a);
+void launch_delta_bases(const DecodeArgs& a, int dbegin, int n, int max_regions, cudaStream_t s) {
+  if (n <= 0) return;
+  static bool attr = false;
+  constexpr int dreg_smem = DREG_SMEM;
+  if (!attr) {
+    cudaFuncSetAttribute(k_dreg, cudaFuncAttributeMaxDynamicSharedMemorySize, dreg_smem);
+    attr = true;
+  }
+  if (max_regions > 0) {
+    k_dreg<<<dim3(max_regions, n), 32, dreg_smem, s>>>(a, dbegin);
+    k_dfix<<<n, 256, 0, s>>>(a, dbegin);
+  }
+  k_delta_sums<<<dim3(32, n), 256, 0, s>>>(a, dbegin);
+  k_delta_scan<<<n, 256, 0, s>>>(a, dbegin);
 }
 
-void launch_expand(const DecodeArgs& a, int grid, cudaStream_t s) {
-  if (a.n_items <= 0) return;
-  k_expand<<<grid, EXP_THREADS, 0, s>>>(a);
+void launch_expand(const DecodeArgs& a, int ibegin, int n, cudaStream_t s) {
+  if (n <= 0) return;
+  const int per_block = EXP_WARPS * EXP_IPW;
+  k_expand<<<(n + per_block - 1) / per_block, EXP_THREADS, 0, s>>>(a, ibegin, n);
 }
 
-void launch_strings(const DecodeArgs& a, const int* str_cols, int n_str_cols, int n_cols_total, int grid,
-                    cudaStream_t s) {
-  (void)n_cols_total;
-  if (n_str_cols <= 0) return;
-  k_str_scan<<<n_str_cols, 256, 0, s>>>(a, str_cols);
-  k_str_copy<<<grid, 256, 0, s>>>(a);
+void launch_strings(const DecodeArgs& a, int col, int n_items, int n_sms, cudaStream_t s) {
+  if (n_items <= 0) return;
+  k_str_scan<<<1, 256, 0, s>>>(a, col);
+  int blocks = (n_items + 7) / 8;
+  if (blocks > n_sms * 8) blocks = n_sms * 8;
+  k_str_copy<<<blocks, 256, 0, s>>>(a, col);
 }
 
 void launch_plain_pages(const DecodeArgs& a, int pp_begin, int n, cudaStream_t s) {

@@ -86,9 +86,8 @@ struct PageDev {
 // Decoded dictionary of one chunk.
 struct DictDev {
   const uint8_t* values;   // fixed width: n * width bytes, 16-byte aligned copy
-  const uint32_t* str_pos; // BYTE_ARRAY: n+1 entries; entry i's chars start at str_pos[i]
-                           // relative to `chars`, its length at str_len[i]
-  const uint32_t* str_len;
+  const uint64_t* str_ent; // BYTE_ARRAY: n entries; entry i = (offset of its chars in
+                           // `chars` << 32) | its length
   const uint8_t* chars;    // BYTE_ARRAY: the (decompressed) dictionary page body
   int32_t n;
   int32_t width;
@@ -118,6 +117,20 @@ struct PlanPage {
   int32_t dbs;             // DELTA: values per block                        [walk]
   int32_t dvpm;            // DELTA: values per miniblock                    [walk]
   int32_t dmbc;            // DELTA: miniblocks per block                    [walk]
+  int32_t dhlen;           // DELTA: stream header bytes (first block offset) [walk]
+  uint32_t dreg;           // DELTA: first row of the page's region tables
+  int32_t dreg_cap;        // DELTA: region rows reserved for the page
+  int32_t pad;             // host: 1 while `body` is a scratch offset
+};
+
+// DELTA block-chain region (speculative parallel walk): regions of
+// DELTA_REGION stream bytes, each walked from its first plausible block start.
+constexpr int DELTA_REGION = 16384;
+constexpr int DELTA_REGION_LIST = DELTA_REGION / 5 + 2;  // blocks are >= 5 bytes
+struct DeltaRegion {
+  int32_t q;      // first block start found in the region (-1: none)
+  int32_t x;      // first chain position at or past the region end
+  int32_t cnt;    // block starts recorded in [q, region end)
   int32_t pad;
 };
 

@@ -190,3 +190,27 @@ def test_config4_style_mixed_chunks(eng):
         data = W.write_file(synth.Table([col]), synth.TableSpec(rg_rows=15_000, page_bytes=d.page_bytes,
                                                                 columns=[cspec]))
         _roundtrip(eng, data)
+
+
+def test_delta_block_chains_across_regions(eng):
+    """Single-page DELTA chunks long enough that the block chain spans many
+    16 KB regions: constant deltas (zero-width miniblocks, 5-byte blocks),
+    small random steps, runs that alternate between constant and noisy
+    deltas, and full-width random values (1 KB blocks, where a region's
+    lead-in holds about one block)."""
+    n = 1 << 20
+    rng = np.random.default_rng(3)
+    i64 = np.iinfo(np.int64)
+    cols = [
+        synth.ColumnData("const_step", "INT64", np.arange(n, dtype=np.int64) * 3),
+        synth.ColumnData("steps07", "INT64", np.cumsum(rng.integers(0, 8, n)).astype(np.int64)),
+        synth.ColumnData("mixed32", "INT32", np.cumsum(np.where((np.arange(n) // 4096) % 2 == 0, 1,
+                                                                rng.integers(-1000, 1000, n))).astype(np.int32)),
+    ]
+    spec = synth.TableSpec(n, 64 << 20, [synth.ColumnSpec("DELTA_BINARY_PACKED")] * 3)
+    _roundtrip(eng, W.write_file(synth.Table(cols), spec))
+    m = 1 << 16
+    wide = [synth.ColumnData("rand64", "INT64", rng.integers(i64.min, i64.max, m, dtype=np.int64, endpoint=True)),
+            synth.ColumnData("rand32", "INT32", rng.integers(-2**31, 2**31, m, dtype=np.int64).astype(np.int32))]
+    spec = synth.TableSpec(m, 64 << 20, [synth.ColumnSpec("DELTA_BINARY_PACKED")] * 2)
+    _roundtrip(eng, W.write_file(synth.Table(wide), spec))
