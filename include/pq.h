@@ -359,6 +359,40 @@ pq_status pq_write_table(const pq_write_column* cols, int n_cols, int64_t n_rows
                          uint64_t* out_size);
 void pq_write_free(uint8_t* buf);
 
+/* ---- Allocation-free DELTA stream decode (no counterpart in the paper) ----
+ *
+ * Decodes one DELTA_BINARY_PACKED value stream (the Parquet encoding the
+ * paper's Section 3 names for sorted integer columns) of `n_values` INT32 or
+ * INT64 values from device memory `d_stream` (`stream_len` bytes, followed
+ * by at least 32 readable bytes, which are not used as data) into device
+ * memory `d_values` (n_values * 4 or * 8 bytes, little-endian).  The stream
+ * is the value part of a REQUIRED data page: header (block size, miniblocks
+ * per block, value count, first value) then the blocks; its value count
+ * must equal `n_values`.  Same kernels and results as the DELTA path of
+ * pq_scan_columns.
+ *
+ * It allocates nothing: every piece of scratch sits in one fixed device
+ * array of about 1.3 MB in the library, so callers that cannot allocate
+ * device memory can use it — a host process whose device memory is all
+ * reserved by another framework's allocator, or code that must not stall on
+ * the device-wide synchronisation a cudaMalloc/cudaFree may cause.
+ * Limits: stream_len <= 1 MiB (1048576) and n_values <= 4194305; larger
+ * inputs are rejected with PQ_ERR_CAPACITY before anything runs.
+ * The first call on a device does the set-up (looks up the array's device
+ * address, which may load the library's device code); make that first call
+ * before any stream capture.  Every run starts by clearing the status word
+ * in the array; nothing else needs to start at zero.  The array is shared by
+ * all calls on a device: calls that overlap in time (from several host
+ * threads, or on several streams without ordering) race on it and give
+ * undefined results.  Synchronous: enqueues on `stream` (NULL = the legacy
+ * default stream), then waits for it to read the device status.
+ * Errors: PQ_ERR_INVALID_ARG (NULL ctx, pointers, other types),
+ * PQ_ERR_CAPACITY (over the limits), PQ_ERR_UNSUPPORTED (stream header
+ * outside Parquet's DELTA rules), PQ_ERR_CORRUPT (value count mismatch,
+ * malformed blocks), PQ_ERR_TIMEOUT, PQ_ERR_CUDA. */
+pq_status pq_delta_decode_static(pq_ctx* ctx, const void* d_stream, uint64_t stream_len, pq_type type,
+                                 int64_t n_values, void* d_values, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -61,4 +61,28 @@ void launch_index_walk(const ChunkDev* chunks, int n_chunks, PageDev* pages, uin
 void launch_index_oi(const ChunkDev* chunks, int n_chunks, const int64_t* chunk_file_off, PageDev* pages,
                      int n_pages, DevStatus* st, cudaStream_t s);
 
+// One DELTA_BINARY_PACKED stream decoded with every piece of scratch inside
+// one caller-provided block laid out as below (the allocation-free entry
+// point keeps it in a fixed device array).  Limits: a stream of at most
+// DS_MAX_STREAM bytes and at most DS_MAX_VALUES values.
+constexpr uint64_t ds_align(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+constexpr uint64_t DS_MAX_STREAM = 1u << 20;
+constexpr int32_t DS_MAX_BLOCKS = 32768;                      // blocks hold >= 128 values
+constexpr int64_t DS_MAX_VALUES = int64_t(DS_MAX_BLOCKS) * 128 + 1;
+constexpr int32_t DS_MAX_REGIONS = int32_t(DS_MAX_STREAM / DELTA_REGION) + 2;
+constexpr uint64_t DS_OFF_STATUS = 0;
+constexpr uint64_t DS_OFF_CHUNK = ds_align(DS_OFF_STATUS + sizeof(DevStatus));
+constexpr uint64_t DS_OFF_PAGE = ds_align(DS_OFF_CHUNK + sizeof(ChunkDev));
+constexpr uint64_t DS_OFF_PPS = ds_align(DS_OFF_PAGE + sizeof(PlanPage));
+constexpr uint64_t DS_OFF_REGIONS = ds_align(DS_OFF_PPS + sizeof(uint32_t));
+constexpr uint64_t DS_OFF_LISTS = ds_align(DS_OFF_REGIONS + sizeof(DeltaRegion) * DS_MAX_REGIONS);
+constexpr uint64_t DS_OFF_DPOS = ds_align(DS_OFF_LISTS + 4ull * DELTA_REGION_LIST * DS_MAX_REGIONS);
+constexpr uint64_t DS_OFF_DBASE = ds_align(DS_OFF_DPOS + 4ull * DS_MAX_BLOCKS);
+constexpr uint64_t DS_SCRATCH_BYTES = ds_align(DS_OFF_DBASE + 8ull * DS_MAX_BLOCKS);
+// Enqueues the decode of `n` values from `stream` (len bytes, 32 readable
+// bytes after them) into `out` (4- or 8-byte values per ptype); the status
+// lands at scratch + DS_OFF_STATUS.  Caller checks the limits first.
+void launch_delta_static(uint8_t* scratch, const uint8_t* stream, uint32_t len, int ptype, int32_t n, void* out,
+                         cudaStream_t s);
+
 }  // namespace pqi

@@ -2004,6 +2004,85 @@ void launch_prepare(const DecodeArgs& a, int n_cols, int grid, cudaStream_t s) {
   k_prepare<<<grid, 256, 0, s>>>(a, n_cols);
 }
 
+// ------------------------------------------------------------------ one DELTA stream, fixed scratch
+
+// Fills the one-page plan of a bare DELTA stream: status cleared, header
+// parsed and checked against the expected value count.
+__global__ void k_dstatic_init(DecodeArgs a, ChunkDev* chunk, uint32_t* delta_pps, const uint8_t* stream,
+                               uint32_t len, int ptype, int32_t n) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  *a.st = DevStatus{0u, -1, 0, 0};
+  ChunkDev ch{};
+  ch.ptype = ptype;
+  ch.width = ptype == T_INT32 ? 4 : 8;
+  *chunk = ch;
+  *delta_pps = 0;
+  PlanPage pp{};
+  pp.body = stream;
+  pp.body_len = static_cast<int32_t>(len);
+  pp.values_off = 0;
+  pp.nonnull = -1;
+  pp.dtab = 0;
+  pp.dreg = 0;
+  pp.dreg_cap = static_cast<int32_t>(len / DELTA_REGION + 2);
+  pp.dblocks = -1;
+  DeltaHdr d{};
+  if (!delta_header(stream, len, &d)) {
+    report(a.st, DERR_UNSUPPORTED, 0, WHERE_WALK_VALUES, 40);
+  } else if (d.total != n || (n > 1 && (n - 2) / d.block + 1 > DS_MAX_BLOCKS)) {
+    report(a.st, DERR_CORRUPT, 0, WHERE_WALK_VALUES, 41);
+  } else {
+    pp.nonnull = n;
+    pp.dfirst = d.first;
+    pp.dbs = d.block;
+    pp.dvpm = d.vpm;
+    pp.dmbc = d.mbc;
+    pp.dhlen = d.hlen;
+    pp.dblocks = n > 1 ? -2 : 0;
+  }
+  a.pps[0] = pp;
+}
+
+// One warp per DS_WARP_VALUES values, from the block tables.
+constexpr int DS_WARP_VALUES = 4096;
+__global__ void __launch_bounds__(256) k_dstatic_expand(DecodeArgs a, uint8_t* out, int32_t n) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t k0 = w * DS_WARP_VALUES;
+  if (k0 >= n) return;
+  const int32_t k1 = static_cast<int32_t>(k0 + DS_WARP_VALUES < n ? k0 + DS_WARP_VALUES : n);
+  const PlanPage pp = a.pps[0];
+  if (pp.nonnull < 0 || (n > 1 && pp.dblocks <= 0)) return;  // error already reported
+  const int ptype = a.chunks[0].ptype;
+  Sink sink{out, nullptr, nullptr, k0, ptype == T_INT32 ? 4 : 8};
+  if (!warp_delta(pp.body, pp, a.dpos, a.dbase, ptype == T_INT32 ? 32 : 64, static_cast<int32_t>(k0), k1, sink,
+                  lane) &&
+      lane == 0)
+    report(a.st, DERR_CORRUPT, 0, WHERE_EXPAND, 42);
+}
+
+void launch_delta_static(uint8_t* scratch, const uint8_t* stream, uint32_t len, int ptype, int32_t n, void* out,
+                         cudaStream_t s) {
+  DecodeArgs a{};
+  a.st = reinterpret_cast<DevStatus*>(scratch + DS_OFF_STATUS);
+  a.chunks = reinterpret_cast<ChunkDev*>(scratch + DS_OFF_CHUNK);
+  a.pps = reinterpret_cast<PlanPage*>(scratch + DS_OFF_PAGE);
+  a.delta_pps = reinterpret_cast<uint32_t*>(scratch + DS_OFF_PPS);
+  a.dregs = reinterpret_cast<DeltaRegion*>(scratch + DS_OFF_REGIONS);
+  a.dreg_lists = reinterpret_cast<uint32_t*>(scratch + DS_OFF_LISTS);
+  a.dpos = reinterpret_cast<uint32_t*>(scratch + DS_OFF_DPOS);
+  a.dbase = reinterpret_cast<int64_t*>(scratch + DS_OFF_DBASE);
+  a.n_pp = 1;
+  a.n_delta = 1;
+  k_dstatic_init<<<1, 32, 0, s>>>(a, reinterpret_cast<ChunkDev*>(scratch + DS_OFF_CHUNK),
+                                  reinterpret_cast<uint32_t*>(scratch + DS_OFF_PPS), stream, len, ptype, n);
+  launch_delta_bases(a, 0, 1, static_cast<int>(len / DELTA_REGION + 2), s);
+  if (n > 0) {
+    const int64_t warps = (static_cast<int64_t>(n) + DS_WARP_VALUES - 1) / DS_WARP_VALUES;
+    k_dstatic_expand<<<static_cast<unsigned>((warps + 7) / 8), 256, 0, s>>>(a, static_cast<uint8_t*>(out), n);
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 
 static int g_walk_bps = 0, g_exp_bps = 0;

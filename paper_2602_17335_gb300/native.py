@@ -116,6 +116,7 @@ _SIGS = {
     "pq_write_table": (C.c_int, [C.POINTER(pq_write_column), C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_int,
                                  C.c_int, C.POINTER(C.POINTER(C.c_uint8)), C.POINTER(C.c_uint64)]),
     "pq_write_free": (None, [C.POINTER(C.c_uint8)]),
+    "pq_delta_decode_static": (C.c_int, [_P, _P, C.c_uint64, C.c_int, C.c_int64, _P, _P]),
 }
 
 _lib = None
@@ -293,3 +294,9 @@ def pq_write_table(columns, n_rows, rg_rows, page_bytes, offset_index=True, n_th
         return np.ctypeslib.as_array(out, shape=(size.value,)).copy() if size.value else np.zeros(0, np.uint8)
     finally:
         lib().pq_write_free(out)
+
+
+def pq_delta_decode_static(ctx, d_stream, stream_len, ptype, n_values, d_values, stream=None):
+    """Allocation-free decode of one DELTA_BINARY_PACKED stream (device
+    pointers); returns the status without raising."""
+    return lib().pq_delta_decode_static(ctx, d_stream, stream_len, ptype, n_values, d_values, stream)
