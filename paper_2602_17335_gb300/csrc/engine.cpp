@@ -116,7 +116,7 @@ pqi::DecodeArgs decode_args(pq_plan* plan) {
   a.dregs = plan->d_dregs;
   a.dreg_lists = plan->d_dreg_lists;
   a.n_pp = static_cast<int>(plan->pps.size());
-  a.n_items = static_cast<int>(plan->items.size());
+  a.n_items = static_cast<int>(plan->n_items);
   a.n_walk = static_cast<int>(plan->walk_pps.size());
   a.n_delta = static_cast<int>(plan->delta_pps.size());
   return a;
@@ -377,19 +377,36 @@ pq_status pq_index_chunks(pq_ctx* ctx, const pq_file* files, int n_files, void* 
                      cudaMemcpyHostToDevice, s));
   int64_t n_pages = 0;
   if (all_oi && nch > 0) {
-    // 4a. OffsetIndex: page counts from the list headers, then one thread per page
-    std::vector<uint8_t> oi;
+    // 4a. OffsetIndex: page counts from the list headers (the first 16 bytes
+    // of every chunk's OffsetIndex, fetched in one round trip into the
+    // footer staging, which is free again), then one thread per page
+    if (!ctx->tail.reserve(16 * static_cast<size_t>(nch))) {
+      free_index_device(idx.get());
+      return fail(ctx, PQ_ERR_OOM, "pinned staging");
+    }
+    {
+      int ci = 0;
+      for (int f = 0; f < n_files; ++f) {
+        const uint8_t* base = static_cast<const uint8_t*>(files[f].data);
+        for (const auto& g : idx->metas[f].rgs)
+          for (int c = 0; c < idx->n_columns; ++c, ++ci) {
+            const auto& cm = g.chunks[c];
+            CK(cudaMemcpyAsync(ctx->tail.p + 16 * ci, base + cm.oi_offset, std::min<int32_t>(cm.oi_length, 16),
+                               cudaMemcpyDeviceToHost, s));
+          }
+      }
+      CK(cudaStreamSynchronize(s));
+    }
     int ci = 0;
     for (int f = 0; f < n_files; ++f) {
       for (const auto& g : idx->metas[f].rgs) {
         for (int c = 0; c < idx->n_columns; ++c, ++ci) {
           const auto& cm = g.chunks[c];
-          oi.resize(std::min<int32_t>(cm.oi_length, 16));
           const uint8_t* base = static_cast<const uint8_t*>(files[f].data);
-          CK(cudaMemcpyAsync(oi.data(), base + cm.oi_offset, oi.size(), cudaMemcpyDeviceToHost, s));
-          CK(cudaStreamSynchronize(s));
           int64_t np = 0;
-          if (pqh::offset_index_pages(oi.data(), oi.size(), &np) != pqh::META_OK || np < 0) {
+          if (pqh::offset_index_pages(ctx->tail.p + 16 * ci, std::min<int32_t>(cm.oi_length, 16), &np) !=
+                  pqh::META_OK ||
+              np < 0) {
             free_index_device(idx.get());
             return fail(ctx, PQ_ERR_CORRUPT, "malformed OffsetIndex");
           }
@@ -647,7 +664,7 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
     col.ptype = cm.type;
     col.width = pqi::type_width(cm.type);
     col.optional = cm.repetition == 1;
-    col.item_begin = static_cast<uint32_t>(plan->items.size());
+    col.item_begin = static_cast<uint32_t>(plan->n_items);
     pq_out_size sz{};
     sz.n_rows = plan->n_rows;
     sz.type = cm.type;
@@ -744,7 +761,7 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
           pp.body = stored;
         }
         plan->read_bytes += static_cast<uint64_t>(pg.header_len) + static_cast<uint64_t>(pg.compressed);
-        pp.item_begin = static_cast<uint32_t>(plan->items.size());
+        pp.item_begin = static_cast<uint32_t>(plan->n_items);
         const bool plain_fixed = pg.encoding == pqi::ENC_PLAIN && cd.ptype != pqi::T_BYTE_ARRAY;
         const bool needs_walk = cd.max_def || !plain_fixed;
         if (!cd.max_def) {
@@ -772,19 +789,10 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
         }
         const int64_t span = pp.row_hi - pp.row_lo;
         const int64_t per = (cd.max_def && !plain_fixed) ? pqi::ITEM_ROWS_OPT : item_rows_max;
-        (void)span;
-        uint32_t n_it = 0;
-        for (int64_t r = pp.row_lo; r < pp.row_hi; r += per) {
-          pqi::Item it{};
-          it.pp = static_cast<uint32_t>(plan->pps.size());
-          it.row0 = static_cast<int32_t>(r);
-          it.nrows = static_cast<int32_t>(std::min<int64_t>(per, pp.row_hi - r));
-          it.k0 = it.row0;
-          it.nn = it.nrows;
-          plan->items.push_back(it);
-          ++n_it;
-        }
+        const uint32_t n_it = static_cast<uint32_t>((span + per - 1) / per);
+        pp.item_rows = static_cast<int32_t>(per);
         pp.item_count = n_it;
+        plan->n_items += n_it;
         plan->pps.push_back(pp);
       }
       const int32_t n_pp = static_cast<int32_t>(plan->pps.size()) - pp_first;
@@ -793,7 +801,7 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
         plan->chunk_pp_chunk.push_back(static_cast<int32_t>(ch));
       }
     }
-    col.item_count = static_cast<uint32_t>(plan->items.size()) - col.item_begin;
+    col.item_count = static_cast<uint32_t>(plan->n_items) - col.item_begin;
     cw.snap_data_n = static_cast<int>(plan->snappy_data.size()) - cw.snap_data_begin;
     cw.snap_dict_n = static_cast<int>(plan->snappy_dict.size()) - cw.snap_dict_begin;
     cw.dict_n = static_cast<int>(plan->dict_jobs.size()) - cw.dict_begin;
@@ -818,7 +826,7 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
     std::copy(sorted.begin(), sorted.end(), plan->walk_pps.begin() + cw.walk_begin);
   }
   // device arrays
-  const size_t npp = plan->pps.size(), nit = plan->items.size();
+  const size_t npp = plan->pps.size(), nit = plan->n_items;
   plan->d_walk_pps = plan_alloc(uint32_t, plan.get(), plan->walk_pps.size());
   plan->d_delta_pps = plan_alloc(uint32_t, plan.get(), plan->delta_pps.size());
   plan->d_dpos = plan_alloc(uint32_t, plan.get(), plan->delta_blocks);
@@ -869,7 +877,7 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
   std::vector<pqi::SnappyJob> alljobs(plan->snappy_data);
   alljobs.insert(alljobs.end(), plan->snappy_dict.begin(), plan->snappy_dict.end());
   if (npp) CK(cudaMemcpyAsync(plan->d_pps, plan->pps.data(), sizeof(pqi::PlanPage) * npp, cudaMemcpyHostToDevice, s));
-  if (nit) CK(cudaMemcpyAsync(plan->d_items, plan->items.data(), sizeof(pqi::Item) * nit, cudaMemcpyHostToDevice, s));
+  if (nit) pqi::launch_make_items(decode_args(plan.get()), static_cast<int>(npp), s);
   if (!alljobs.empty())
     CK(cudaMemcpyAsync(plan->d_snappy, alljobs.data(), sizeof(pqi::SnappyJob) * alljobs.size(),
                        cudaMemcpyHostToDevice, s));
@@ -939,7 +947,7 @@ pq_status pq_plan_get_info(const pq_plan* plan, pq_plan_info* out) {
   out->n_columns = static_cast<int32_t>(plan->cols.size());
   out->n_pages = static_cast<int32_t>(plan->pps.size());
   out->n_dict_pages = static_cast<int32_t>(plan->dict_jobs.size());
-  out->n_items = static_cast<int32_t>(plan->items.size());
+  out->n_items = static_cast<int32_t>(plan->n_items);
   out->read_bytes = plan->read_bytes;
   out->decoded_bytes = plan->decoded_bytes;
   out->scratch_bytes = plan->scratch_bytes;

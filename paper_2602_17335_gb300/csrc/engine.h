@@ -93,7 +93,7 @@ struct pq_plan {
   int64_t row_begin = 0, n_rows = 0;
   std::vector<pq_out_size> sizes;
   std::vector<pqi::PlanPage> pps;
-  std::vector<pqi::Item> items;
+  uint64_t n_items = 0;                      // work items (built on the device)
   std::vector<pqi::OutCol> outcols;
   std::vector<pqi::SnappyJob> snappy_data;   // data pages
   std::vector<pqi::SnappyJob> snappy_dict;   // dictionary pages (into index buffers)

@@ -1844,16 +1844,103 @@ __global__ void k_str_scan(DecodeArgs a, int c) {
   }
 }
 
+// Copies `len` bytes from global `src` (any alignment) to shared `d` (any
+// alignment).  The source is read as aligned 16-byte words (about
+// (len + 15) / 16 + 1 sectors per string, instead of one per 4 bytes), the
+// destination is written as 4-byte words funnel-shifted from them, with byte
+// stores only for the partial words at the string's two ends.  The aligned
+// words may reach up to 16 bytes past `src + len`; callers guarantee those
+// bytes are readable.
+__device__ __forceinline__ void stage_string(uint8_t* d, const uint8_t* src, uint32_t len) {
+  const int p = static_cast<int>(reinterpret_cast<uintptr_t>(src) & 15);
+  const uint4* sv = reinterpret_cast<const uint4*>(reinterpret_cast<uintptr_t>(src) - p);
+  const int dd = static_cast<int>(reinterpret_cast<uintptr_t>(d) & 3);
+  uint32_t* dw = reinterpret_cast<uint32_t*>(d - dd);
+  const int nw = (dd + static_cast<int>(len) + 3) >> 2;  // destination words touched
+  const int q0 = p - dd;                                  // span byte of destination word 0 (>= -3)
+  const uint32_t sh = static_cast<uint32_t>(q0 & 3) * 8;
+  int wi = q0 >> 2;                                       // span word (-1 when q0 < 0)
+  auto pick = [](const uint4& x, int k) -> uint32_t {
+    return (k & 2) ? ((k & 1) ? x.w : x.z) : ((k & 1) ? x.y : x.x);
+  };
+  uint4 v = __ldg(sv + (wi < 0 ? 0 : (wi >> 2)));
+  uint32_t cur = wi < 0 ? 0u : pick(v, wi & 3);
+  const int end = dd + static_cast<int>(len);             // destination bytes [dd, end) relative to dw
+  for (int k = 0; k < nw; ++k) {
+    ++wi;
+    if ((wi & 3) == 0) v = __ldg(sv + (wi >> 2));
+    const uint32_t nxt = pick(v, wi & 3);
+    const uint32_t val = sh ? __funnelshift_r(cur, nxt, sh) : cur;
+    cur = nxt;
+    const int b0 = 4 * k;
+    if (b0 >= dd && b0 + 4 <= end) {
+      dw[k] = val;
+    } else {
+      uint8_t* db = reinterpret_cast<uint8_t*>(dw + k);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (b0 + j >= dd && b0 + j < end) db[j] = static_cast<uint8_t>(val >> (8 * j));
+    }
+  }
+}
+
+// Same copy from a shared-memory copy of the aligned source span (`raw`,
+// 16-byte aligned, holding span bytes [0, p + len) and readable for 16
+// bytes more).
+__device__ __forceinline__ void stage_from_raw(uint8_t* d, const uint8_t* raw, int p, uint32_t len) {
+  const uint32_t* rw = reinterpret_cast<const uint32_t*>(raw);
+  const int dd = static_cast<int>(reinterpret_cast<uintptr_t>(d) & 3);
+  uint32_t* dw = reinterpret_cast<uint32_t*>(d - dd);
+  const int nw = (dd + static_cast<int>(len) + 3) >> 2;
+  const int q0 = p - dd;
+  const uint32_t sh = static_cast<uint32_t>(q0 & 3) * 8;
+  int wi = q0 >> 2;
+  uint32_t cur = wi < 0 ? 0u : rw[wi];
+  const int end = dd + static_cast<int>(len);
+  for (int k = 0; k < nw; ++k) {
+    ++wi;
+    const uint32_t nxt = rw[wi];
+    const uint32_t val = sh ? __funnelshift_r(cur, nxt, sh) : cur;
+    cur = nxt;
+    const int b0 = 4 * k;
+    if (b0 >= dd && b0 + 4 <= end) {
+      dw[k] = val;
+    } else {
+      uint8_t* db = reinterpret_cast<uint8_t*>(dw + k);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (b0 + j >= dd && b0 + j < end) db[j] = static_cast<uint8_t>(val >> (8 * j));
+    }
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Per item of a string column, one warp: offsets by a warp scan of the
-// lengths; each 32-string chunk is assembled in shared memory (lanes copy
-// their own string) and written out with aligned 16-byte stores, bytes
-// only at the chunk's two ends.
+// lengths; strings are processed 64 at a time: each lane's source spans
+// (up to STR_RAW_BLK aligned 16-byte blocks) are fetched together with
+// asynchronous global-to-shared copies, then each 32-string chunk is
+// assembled in shared memory (lanes place their own string) and written out
+// with aligned 16-byte stores, bytes only at the chunk's two ends.  Longer
+// strings are read straight from global memory.
 constexpr int STR_STAGE = 2048;
+constexpr int STR_RAW_BLK = 4;  // strings up to 49 bytes go through the async copies
+struct StrWarpSmem {
+  uint8_t stage[STR_STAGE + 16];
+  uint4 raw[64 * STR_RAW_BLK + 1];  // +1: the last slot's read-ahead word
+};
+constexpr int STR_SMEM = 8 * sizeof(StrWarpSmem);
 
 __global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a, int c) {
-  __shared__ __align__(16) uint8_t stage[8][STR_STAGE + 16];
+  extern __shared__ __align__(16) uint8_t str_smem[];
+  StrWarpSmem& ws = reinterpret_cast<StrWarpSmem*>(str_smem)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
-  uint8_t* sbuf = stage[threadIdx.x >> 5];
+  uint8_t* sbuf = ws.stage;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const int ib = static_cast<int>(a.cols[c].item_begin);
@@ -1872,6 +1959,7 @@ __global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a, int c) {
     uint64_t base = col.str_item_bytes[itx];
     const int64_t orow0 = pp.out_row + it.row0;
     int64_t* offs = reinterpret_cast<int64_t*>(col.values);
+    const uint8_t* cbase = isdict ? dd.chars : sb;
     for (int g0 = 0; g0 < it.nrows; g0 += 256) {
       // metadata of 8 chunks of 32 strings, loads issued together
       uint32_t sidx[8];
@@ -1892,58 +1980,73 @@ __global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a, int c) {
           }
         }
       }
-      const uint8_t* cbase = isdict ? dd.chars : sb;
-      for (int u = 0; u < 8; ++u) {
-        const int r0 = g0 + u * 32;
-        if (r0 >= it.nrows) break;
-        const int r = r0 + lane;
-        const uint32_t len = static_cast<uint32_t>(ent[u]);
-        const uint8_t* src = cbase + (ent[u] >> 32);
-        uint64_t incl = len;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
-        }
-        const uint64_t tot = __shfl_sync(0xffffffffu, incl, 31);
-        const uint64_t off = base + incl - len;
-        if (r < it.nrows) offs[orow0 + r] = static_cast<int64_t>(off);
-        if (base + tot <= col.chars_cap) {
-          const uint32_t a0 = static_cast<uint32_t>(base & 15);
-          if (a0 + tot <= STR_STAGE) {
-            // lanes place their strings, congruent to the output mod 16
-            uint8_t* d = sbuf + a0 + (off - base);
-            if (len) {
-              const uint32_t* sw = reinterpret_cast<const uint32_t*>(reinterpret_cast<uintptr_t>(src) & ~uintptr_t(3));
-              const uint32_t sh = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 3) * 8;
-              uint32_t cur = __ldg(sw);
-              for (uint32_t q = 0; q < len; q += 4) {
-                const uint32_t nxt = __ldg(sw + (q >> 2) + 1);
-                const uint32_t w = sh ? __funnelshift_r(cur, nxt, sh) : cur;
-                d[q] = static_cast<uint8_t>(w);
-                if (q + 1 < len) d[q + 1] = static_cast<uint8_t>(w >> 8);
-                if (q + 2 < len) d[q + 2] = static_cast<uint8_t>(w >> 16);
-                if (q + 3 < len) d[q + 3] = static_cast<uint8_t>(w >> 24);
-                cur = nxt;
-              }
-            }
-            __syncwarp();
-            uint8_t* g = col.chars + base;
-            const uint32_t head = a0 ? 16 - a0 : 0;
-            const uint32_t h = head < tot ? head : static_cast<uint32_t>(tot);
-            if (static_cast<uint32_t>(lane) < h) g[lane] = sbuf[a0 + lane];
-            const uint32_t nv = static_cast<uint32_t>((tot - h) >> 4);
-            const uint4* sv = reinterpret_cast<const uint4*>(sbuf + a0 + h);
-            uint4* gv = reinterpret_cast<uint4*>(g + h);
-            for (uint32_t q = lane; q < nv; q += 32) gv[q] = sv[q];
-            for (uint32_t q = h + (nv << 4) + lane; q < tot; q += 32) g[q] = sbuf[a0 + q];
-            __syncwarp();
-          } else if (r < it.nrows) {
-            uint8_t* d = col.chars + off;
-            for (uint32_t q = 0; q < len; ++q) d[q] = __ldg(src + q);
+      for (int u2 = 0; u2 < 8; u2 += 2) {
+        if (g0 + u2 * 32 >= it.nrows) break;
+        // source spans of two chunks, fetched together
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t len = static_cast<uint32_t>(ent[u2 + h]);
+          const uint8_t* src = cbase + (ent[u2 + h] >> 32);
+          const uint32_t p = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 15);
+          const uint32_t nb = (p + len + 15) >> 4;
+          if (len && nb <= STR_RAW_BLK) {
+            const uint8_t* sa = src - p;
+            uint4* slot = ws.raw + (h * 32 + lane) * STR_RAW_BLK;
+            for (uint32_t b = 0; b < nb; ++b) cp_async16(slot + b, sa + 16 * b);
           }
         }
-        base += tot;
+        cp_async_wait_all();
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int u = u2 + h;
+          const int r0 = g0 + u * 32;
+          if (r0 >= it.nrows) break;
+          const int r = r0 + lane;
+          const uint32_t len = static_cast<uint32_t>(ent[u]);
+          const uint8_t* src = cbase + (ent[u] >> 32);
+          uint64_t incl = len;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+          }
+          const uint64_t tot = __shfl_sync(0xffffffffu, incl, 31);
+          const uint64_t off = base + incl - len;
+          if (r < it.nrows) offs[orow0 + r] = static_cast<int64_t>(off);
+          if (base + tot <= col.chars_cap) {
+            const uint32_t a0 = static_cast<uint32_t>(base & 15);
+            if (a0 + tot <= STR_STAGE) {
+              // lanes place their strings, congruent to the output mod 16
+              if (len) {
+                const int p = static_cast<int>(reinterpret_cast<uintptr_t>(src) & 15);
+                uint8_t* d = sbuf + a0 + (off - base);
+                if (((p + len + 15) >> 4) <= STR_RAW_BLK)
+                  stage_from_raw(d, reinterpret_cast<const uint8_t*>(ws.raw + (h * 32 + lane) * STR_RAW_BLK), p,
+                                 len);
+                else
+                  stage_string(d, src, len);
+              }
+              __syncwarp();
+              uint8_t* g = col.chars + base;
+              const uint32_t head = a0 ? 16 - a0 : 0;
+              const uint32_t hh = head < tot ? head : static_cast<uint32_t>(tot);
+              if (static_cast<uint32_t>(lane) < hh) g[lane] = sbuf[a0 + lane];
+              const uint32_t nv = static_cast<uint32_t>((tot - hh) >> 4);
+              const uint4* sv = reinterpret_cast<const uint4*>(sbuf + a0 + hh);
+              uint4* gv = reinterpret_cast<uint4*>(g + hh);
+              for (uint32_t q = lane; q < nv; q += 32) gv[q] = sv[q];
+              for (uint32_t q = hh + (nv << 4) + lane; q < tot; q += 32) g[q] = sbuf[a0 + q];
+              __syncwarp();
+            } else if (r < it.nrows) {
+              uint8_t* d = col.chars + off;
+              for (uint32_t q = 0; q < len; ++q) d[q] = __ldg(src + q);
+            }
+          }
+          base += tot;
+        }
+        __syncwarp();
       }
     }
   }
@@ -2004,6 +2107,28 @@ void launch_prepare(const DecodeArgs& a, int n_cols, int grid, cudaStream_t s) {
   k_prepare<<<grid, 256, 0, s>>>(a, n_cols);
 }
 
+// ------------------------------------------------------------------ work items
+
+// One warp per plan page: item j covers page rows [row_lo + j*R, ...) with R
+// the page's item rows; the dense range starts equal to the row range (the
+// walk rewrites it for pages with levels).
+__global__ void __launch_bounds__(256) k_make_items(DecodeArgs a, int n_pp) {
+  const int lane = threadIdx.x & 31;
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (p >= n_pp) return;
+  const PlanPage pp = a.pps[p];
+  for (uint32_t j = lane; j < pp.item_count; j += 32) {
+    Item it{};
+    it.pp = static_cast<uint32_t>(p);
+    it.row0 = pp.row_lo + static_cast<int32_t>(j) * pp.item_rows;
+    const int32_t left = pp.row_hi - it.row0;
+    it.nrows = left < pp.item_rows ? left : pp.item_rows;
+    it.k0 = it.row0;
+    it.nn = it.nrows;
+    a.items[pp.item_begin + j] = it;
+  }
+}
+
 // ------------------------------------------------------------------ one DELTA stream, fixed scratch
 
 // Fills the one-page plan of a bare DELTA stream: status cleared, header
@@ -2059,6 +2184,10 @@ __global__ void __launch_bounds__(256) k_dstatic_expand(DecodeArgs a, uint8_t* o
                   lane) &&
       lane == 0)
     report(a.st, DERR_CORRUPT, 0, WHERE_EXPAND, 42);
+}
+
+void launch_make_items(const DecodeArgs& a, int n_pp, cudaStream_t s) {
+  if (n_pp > 0) k_make_items<<<(n_pp + 7) / 8, 256, 0, s>>>(a, n_pp);
 }
 
 void launch_delta_static(uint8_t* scratch, const uint8_t* stream, uint32_t len, int ptype, int32_t n, void* out,
@@ -2138,7 +2267,12 @@ void launch_strings(const DecodeArgs& a, int col, int n_items, int n_sms, cudaSt
   k_str_scan<<<1, 256, 0, s>>>(a, col);
   int blocks = (n_items + 7) / 8;
   if (blocks > n_sms * 8) blocks = n_sms * 8;
-  k_str_copy<<<blocks, 256, 0, s>>>(a, col);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_str_copy, cudaFuncAttributeMaxDynamicSharedMemorySize, STR_SMEM);
+    attr = true;
+  }
+  k_str_copy<<<blocks, 256, STR_SMEM, s>>>(a, col);
 }
 
 void launch_plain_pages(const DecodeArgs& a, int pp_begin, int n, cudaStream_t s) {

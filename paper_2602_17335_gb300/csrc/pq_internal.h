@@ -121,6 +121,7 @@ struct PlanPage {
   uint32_t dreg;           // DELTA: first row of the page's region tables
   int32_t dreg_cap;        // DELTA: region rows reserved for the page
   int32_t pad;             // host: 1 while `body` is a scratch offset
+  int32_t item_rows;       // rows per work item of this page
 };
 
 // DELTA block-chain region (speculative parallel walk): regions of
