@@ -657,6 +657,7 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
     cw.dict_begin = static_cast<int>(plan->dict_jobs.size());
     cw.walk_begin = static_cast<int>(plan->walk_pps.size());
     cw.delta_begin = static_cast<int>(plan->delta_pps.size());
+    cw.copy_only = cm.repetition != 1 && cm.type != pqi::T_BYTE_ARRAY;
     const int max_fixed_before = plan->max_fixed_dict_bytes;
     plan->max_fixed_dict_bytes = 0;
     pqi::OutCol col{};
@@ -763,6 +764,7 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
         plan->read_bytes += static_cast<uint64_t>(pg.header_len) + static_cast<uint64_t>(pg.compressed);
         pp.item_begin = static_cast<uint32_t>(plan->n_items);
         const bool plain_fixed = pg.encoding == pqi::ENC_PLAIN && cd.ptype != pqi::T_BYTE_ARRAY;
+        if (!plain_fixed || cd.max_def) cw.copy_only = false;
         const bool needs_walk = cd.max_def || !plain_fixed;
         if (!cd.max_def) {
           // REQUIRED: the value stream starts after the (empty) levels
@@ -839,7 +841,7 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
   plan->d_snappy = plan_alloc(pqi::SnappyJob, plan.get(), plan->snappy_data.size() + plan->snappy_dict.size());
   plan->d_dict_jobs = plan_alloc(pqi::DictJob, plan.get(), plan->dict_jobs.size());
   plan->d_str_cols = plan_alloc(int32_t, plan.get(), plan->str_cols.size());
-  plan->d_counter = plan_alloc(uint32_t, plan.get(), 4);
+  plan->d_counter = plan_alloc(uint32_t, plan.get(), 4 + plan->outcols.size());
   plan->d_status = plan_alloc(pqi::DevStatus, plan.get(), 1);
   plan->d_scratch = scratch ? plan_alloc(uint8_t, plan.get(), scratch + 64) : nullptr;
   const uint64_t str_rows = static_cast<uint64_t>(plan->n_rows) * plan->str_cols.size();
@@ -984,7 +986,12 @@ static void enqueue_column(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, b
   pqi::launch_walk(a, cw.walk_begin, cw.walk_n, s);
   pqi::launch_delta_bases(a, cw.delta_begin, cw.delta_n, cw.max_regions, s);
   const auto& col = plan->outcols[oc];
-  pqi::launch_expand(a, static_cast<int>(col.item_begin), static_cast<int>(col.item_count), s);
+  if (cw.copy_only)
+    pqi::launch_copy_items(a, static_cast<int>(col.item_begin), static_cast<int>(col.item_count),
+                           static_cast<int>(oc), ctx->n_sms, s);
+  else
+    pqi::launch_expand(a, static_cast<int>(col.item_begin), static_cast<int>(col.item_count), static_cast<int>(oc),
+                       ctx->n_sms, s);
   if (col.ptype == pqi::T_BYTE_ARRAY)
     pqi::launch_strings(a, static_cast<int>(oc), static_cast<int>(col.item_count), ctx->n_sms, s);
 }
@@ -1052,9 +1059,15 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts) {
       pqi::launch_delta_bases(a, cw.delta_begin, cw.delta_n, cw.max_regions, s);
     }
     mark(4);
-    for (int oc = 0; oc < ncols; ++oc)
-      pqi::launch_expand(a, static_cast<int>(plan->outcols[oc].item_begin),
-                         static_cast<int>(plan->outcols[oc].item_count), s);
+    for (int oc = 0; oc < ncols; ++oc) {
+      const auto& oco = plan->outcols[oc];
+      if (plan->colwork[oc].copy_only)
+        pqi::launch_copy_items(a, static_cast<int>(oco.item_begin), static_cast<int>(oco.item_count), oc,
+                               ctx->n_sms, s);
+      else
+        pqi::launch_expand(a, static_cast<int>(oco.item_begin), static_cast<int>(oco.item_count), oc, ctx->n_sms,
+                           s);
+    }
     mark(5);
     for (int32_t sc : plan->str_cols)
       pqi::launch_strings(a, sc, static_cast<int>(plan->outcols[sc].item_count), ctx->n_sms, s);

@@ -148,6 +148,7 @@ struct pq_plan {
     int walk_begin = 0, walk_n = 0;            // into walk_pps
     int delta_begin = 0, delta_n = 0;          // into delta_pps
     int max_regions = 0;                       // most DELTA regions of one page
+    bool copy_only = false;                    // every page REQUIRED PLAIN fixed-width
   };
   std::vector<ColWork> colwork;
   cudaEvent_t fork = nullptr;

@@ -37,6 +37,7 @@ namespace pqi {
 constexpr int WALK_THREADS = 256;
 constexpr int EXP_THREADS = 256;
 constexpr int EXP_WARPS = EXP_THREADS / 32;
+constexpr int EXP_COUNTER0 = 4;  // item_counter[4 + c]: next item of output column c
 constexpr uint32_t CWIN = 16384;  // chain window (two per walking block)
 constexpr uint32_t COVL = 64;     // overlap of consecutive chain windows
 constexpr int RB = 1024;          // runs per walk batch
@@ -1669,6 +1670,97 @@ __device__ __forceinline__ uint32_t bitmap_bits(const uint32_t* v, int64_t r, in
   return n < 32 ? b & ((1u << n) - 1u) : b;
 }
 
+// 16 bytes starting at byte s (0..15) of the 32-byte pair (A, B); the word
+// offset s >> 2 is warp-uniform, so the switch does not diverge.
+__device__ __forceinline__ uint4 shift_pair(const uint4& A, const uint4& B, uint32_t s) {
+  const uint32_t bs = (s & 3) * 8;
+  uint32_t w0, w1, w2, w3, w4;
+  switch (s >> 2) {
+    case 0: w0 = A.x; w1 = A.y; w2 = A.z; w3 = A.w; w4 = B.x; break;
+    case 1: w0 = A.y; w1 = A.z; w2 = A.w; w3 = B.x; w4 = B.y; break;
+    case 2: w0 = A.z; w1 = A.w; w2 = B.x; w3 = B.y; w4 = B.z; break;
+    default: w0 = A.w; w1 = B.x; w2 = B.y; w3 = B.z; w4 = B.w; break;
+  }
+  return make_uint4(__funnelshift_r(w0, w1, bs), __funnelshift_r(w1, w2, bs), __funnelshift_r(w2, w3, bs),
+                    __funnelshift_r(w3, w4, bs));
+}
+
+// One warp copies `bytes` bytes from `src` (any alignment) to `dst` (aligned
+// to the value width): bytes up to dst's 16-byte boundary one by one, then
+// 16-byte stores built from aligned 16-byte loads (8 per lane in flight; the
+// next aligned word comes from the neighbouring lane by a shuffle), then the
+// tail.  Reads may reach 16 bytes past src + bytes.
+__device__ __forceinline__ uint4 shfl_u4(const uint4& v, int src_lane) {
+  return make_uint4(__shfl_sync(0xffffffffu, v.x, src_lane), __shfl_sync(0xffffffffu, v.y, src_lane),
+                    __shfl_sync(0xffffffffu, v.z, src_lane), __shfl_sync(0xffffffffu, v.w, src_lane));
+}
+__device__ __forceinline__ uint4 shfl_down_u4(const uint4& v) {
+  return make_uint4(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1),
+                    __shfl_down_sync(0xffffffffu, v.z, 1), __shfl_down_sync(0xffffffffu, v.w, 1));
+}
+
+__device__ __forceinline__ void warp_copy(uint8_t* dst, const uint8_t* src, uint64_t bytes, int lane) {
+  const uint32_t head0 = static_cast<uint32_t>((16 - (reinterpret_cast<uintptr_t>(dst) & 15)) & 15);
+  const uint32_t head = head0 < bytes ? head0 : static_cast<uint32_t>(bytes);
+  if (static_cast<uint32_t>(lane) < head) dst[lane] = __ldg(src + lane);
+  dst += head;
+  src += head;
+  bytes -= head;
+  const uint64_t nvec = bytes >> 4;
+  const uint32_t s = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 15);
+  const uint4* sa = reinterpret_cast<const uint4*>(src - s);
+  uint4* dv = reinterpret_cast<uint4*>(dst);
+  constexpr int U = 8;
+  for (uint64_t v0 = 0; v0 < nvec; v0 += 32 * U) {
+    uint4 A[U];
+    uint4 X = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t i = v0 + u * 32 + lane;
+      A[u] = i <= nvec ? __ldg(sa + i) : make_uint4(0, 0, 0, 0);
+    }
+    if (s && lane == 0 && v0 + 32 * U <= nvec) X = __ldg(sa + v0 + 32 * U);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t i = v0 + u * 32 + lane;
+      uint4 out = A[u];
+      if (s) {  // warp-uniform
+        const uint4 dn = shfl_down_u4(A[u]);
+        const uint4 nx = shfl_u4(u + 1 < U ? A[u + 1] : X, 0);
+        out = shift_pair(A[u], lane == 31 ? nx : dn, s);
+      }
+      if (i < nvec) dv[i] = out;
+    }
+  }
+  const uint32_t tail = static_cast<uint32_t>(bytes & 15);
+  if (static_cast<uint32_t>(lane) < tail) dst[(nvec << 4) + lane] = __ldg(src + (nvec << 4) + lane);
+}
+
+// Columns whose pages are all REQUIRED PLAIN fixed-width: every item is a
+// straight copy of nrows * width bytes, handed out through the column's
+// counter.
+__global__ void __launch_bounds__(256) k_copy_items(DecodeArgs a, int ibegin, int icount, int cidx) {
+  const int lane = threadIdx.x & 31;
+  uint32_t* ctr = a.item_counter + 4 + cidx;
+  for (;;) {
+    int u = 0;
+    if (lane == 0) u = static_cast<int>(atomicAdd(ctr, 1u));
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= icount) break;
+    const Item it = a.items[ibegin + u];
+    if (it.nrows <= 0) continue;
+    const PlanPage pp = a.pps[it.pp];
+    const OutCol col = a.cols[pp.col];
+    const int width = col.width;
+    if (static_cast<uint64_t>(it.k0 + it.nrows) * width > static_cast<uint64_t>(pp.body_len - pp.values_off)) {
+      if (lane == 0) report(a.st, DERR_CORRUPT, static_cast<int>(pp.page), WHERE_EXPAND, 10);
+      continue;
+    }
+    warp_copy(col.values + (pp.out_row + it.row0) * width, pp.body + pp.values_off + static_cast<int64_t>(it.k0) * width,
+              static_cast<uint64_t>(it.nrows) * width, lane);
+  }
+}
+
 __device__ void expand_item(const DecodeArgs& a, int it_id, WarpSmem& ws, int lane) {
   const Item it = a.items[it_id];
   if (it.nrows <= 0) return;
@@ -1794,15 +1886,17 @@ __device__ void expand_item(const DecodeArgs& a, int it_id, WarpSmem& ws, int la
   }
 }
 
-// Items [ibegin, ibegin + icount): each warp decodes EXP_IPW consecutive items.
-constexpr int EXP_IPW = 2;
-
-__global__ void __launch_bounds__(EXP_THREADS) k_expand(DecodeArgs a, int ibegin, int icount) {
+// Items [ibegin, ibegin + icount), handed out one at a time to warps through
+// the column's counter (items differ in cost), over a grid sized to the
+// resident capacity.
+__global__ void __launch_bounds__(EXP_THREADS, 3) k_expand(DecodeArgs a, int ibegin, int icount, int cidx) {
   __shared__ WarpSmem ws[EXP_WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int first = (blockIdx.x * EXP_WARPS + warp) * EXP_IPW;
-  for (int j = 0; j < EXP_IPW; ++j) {
-    const int u = first + j;
+  uint32_t* ctr = a.item_counter + EXP_COUNTER0 + cidx;
+  for (;;) {
+    int u = 0;
+    if (lane == 0) u = static_cast<int>(atomicAdd(ctr, 1u));
+    u = __shfl_sync(0xffffffffu, u, 0);
     if (u >= icount) break;
     expand_item(a, ibegin + u, ws[warp], lane);
   }
@@ -2084,9 +2178,8 @@ __global__ void __launch_bounds__(WALK_THREADS) k_plain_page(DecodeArgs a, int p
 __global__ void k_prepare(DecodeArgs a, int n_cols) {
   const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
   const uint64_t nthr = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  if (tid < static_cast<uint64_t>(EXP_COUNTER0 + n_cols)) a.item_counter[tid] = 0;
   if (tid == 0) {
-    a.item_counter[0] = 0;
-    a.item_counter[1] = 0;
     a.st->flags = 0;
     a.st->first_page = -1;
     a.st->where = 0;
@@ -2256,10 +2349,24 @@ void launch_delta_bases(const DecodeArgs& a, int dbegin, int n, int max_regions,
   k_delta_scan<<<n, 256, 0, s>>>(a, dbegin);
 }
 
-void launch_expand(const DecodeArgs& a, int ibegin, int n, cudaStream_t s) {
+void launch_copy_items(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, cudaStream_t s) {
   if (n <= 0) return;
-  const int per_block = EXP_WARPS * EXP_IPW;
-  k_expand<<<(n + per_block - 1) / per_block, EXP_THREADS, 0, s>>>(a, ibegin, n);
+  static int bps = 0;
+  if (!bps) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_copy_items, 256, 0);
+    if (bps < 1) bps = 1;
+  }
+  int blocks = (n + 7) / 8;
+  if (blocks > n_sms * bps) blocks = n_sms * bps;
+  k_copy_items<<<blocks, 256, 0, s>>>(a, ibegin, n, cidx);
+}
+
+void launch_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, cudaStream_t s) {
+  if (n <= 0) return;
+  int blocks = (n + EXP_WARPS - 1) / EXP_WARPS;
+  const int cap = n_sms * expand_blocks_per_sm();
+  if (blocks > cap) blocks = cap;
+  k_expand<<<blocks, EXP_THREADS, 0, s>>>(a, ibegin, n, cidx);
 }
 
 void launch_strings(const DecodeArgs& a, int col, int n_items, int n_sms, cudaStream_t s) {
