@@ -60,6 +60,14 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scan-reps", type=int, default=10, help="graph replays for the roofline")
     ap.add_argument("--json-out", default=None)
+    ap.add_argument("--workload", default="scan", choices=["scan", "serve"],
+                    help="scan: one table, index+plan+scan per step; serve: Poisson requests through pq_serve_*")
+    ap.add_argument("--serve-files", type=int, default=4, help="serve: tables in the catalog index")
+    ap.add_argument("--serve-requests", type=int, default=200, help="serve: requests per offered-load point")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="serve: mean arrivals per second at 1x")
+    ap.add_argument("--serve-loads", default="0.125,0.25,0.5,1", help="serve: offered-load multipliers")
+    ap.add_argument("--serve-budget-gib", type=float, default=64.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
     return ap.parse_args()
 
 
@@ -373,6 +381,115 @@ def run_ours(a, rank, world, local_rank):
                 json.dump(line, f, indent=1)
 
 
+# ----------------------------------------------------------------- serving (Poisson requests)
+
+def serve_catalog(a):
+    """Tables sharing the eight-column schema, one per layout: row groups of
+    2^23 rows with 64 KiB and 1 MiB pages, uncompressed and Snappy."""
+    from paper_2602_17335_gb300.tables import write_table
+    layouts = [(64 * 1024, "UNCOMPRESSED"), (MiB, "UNCOMPRESSED"), (64 * 1024, "SNAPPY"), (MiB, "SNAPPY")]
+    files = []
+    for f in range(a.serve_files):
+        pb, codec = layouts[f % len(layouts)]
+        tab = synth.config2_table(a.rows, a.rg_rows, file=f)
+        spec = synth.config2_spec(a.rg_rows, pb, codec, 1)
+        if codec == "SNAPPY":
+            for c in spec.columns:
+                c.compress_threshold = -1.0
+        files.append((write_table(tab, spec), f"{pb // 1024} KiB pages, {codec.lower()}"))
+    return files
+
+
+def request_stream(a, n, rate, seed, total_rows):
+    """Open-loop Poisson arrivals; columns log-uniform over 1..8 (a random
+    subset), rows log-uniform over [2^20, 2^28), start uniform (ranges wrap)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    out = []
+    for i in range(n):
+        k = int(np.clip(np.floor(np.exp(rng.uniform(0, np.log(9)))), 1, 8))
+        cols = sorted(rng.choice(8, k, replace=False).tolist())
+        rows = int(np.exp(rng.uniform(np.log(2 ** 20), np.log(2 ** 28))))
+        start = int(rng.integers(0, total_rows))
+        out.append((float(t[i]), cols, start, rows))
+    return out
+
+
+def run_serve(a):
+    import torch
+    from paper_2602_17335_gb300 import native as N
+    from paper_2602_17335_gb300.scan import Engine
+    t0 = time.time()
+    files = serve_catalog(a)
+    gen_s = time.time() - t0
+    dev_files = [torch.from_numpy(d).cuda() for d, _ in files]
+    eng = Engine(0)
+    idx = eng.index(dev_files)
+    info = N.pq_index_get_info(idx)
+    srv = N.pq_serve_create(eng.ctx, idx, int(a.serve_budget_gib * (1 << 30)), a.serve_slots)
+    points = []
+    with ClockSampler(0) as clk:
+        for li, mult in enumerate(float(x) for x in a.serve_loads.split(",")):
+            rate = a.serve_rate * mult
+            reqs = request_stream(a, a.serve_requests, rate, 1000 + li, info.num_rows)
+            pending, lat, qms, rejected, decoded = {}, [], [], 0, 0
+            start = time.perf_counter()
+            i = 0
+            while i < len(reqs) or pending:
+                now = time.perf_counter() - start
+                while i < len(reqs) and reqs[i][0] <= now:
+                    _, cols, rb, rc = reqs[i]
+                    st, tk = N.pq_serve_submit(srv, cols, rb, rc)
+                    if st == N.PQ_OK:
+                        pending[tk] = i
+                    else:
+                        rejected += 1
+                    i += 1
+                for tk in list(pending):
+                    res = N.pq_serve_poll(srv, tk)
+                    if res is None:
+                        continue
+                    if res.status == N.PQ_OK:
+                        lat.append(res.latency_ms)
+                        qms.append(res.queue_ms)
+                        decoded += res.decoded_bytes
+                    else:
+                        rejected += 1
+                    N.pq_serve_release(srv, tk)
+                    del pending[tk]
+                time.sleep(0.0002)
+            wall = time.perf_counter() - start
+            lat_sorted = sorted(lat)
+
+            def pct(p):
+                return lat_sorted[min(len(lat_sorted) - 1, int(np.ceil(p / 100 * len(lat_sorted))) - 1)] if lat_sorted else None
+            points.append({"offered_rps": rate, "achieved_rps": len(lat) / wall, "completed": len(lat),
+                           "refused_or_failed": rejected, "p50_ms": pct(50), "p99_ms": pct(99),
+                           "mean_queue_ms": float(np.mean(qms)) if qms else None, "decoded_gbs": decoded / wall / 1e9,
+                           "wall_s": wall})
+    N.pq_serve_destroy(srv)
+    N.pq_free_index(idx)
+    eng.close()
+    knee = max(points, key=lambda p: p["decoded_gbs"])
+    line = {"metric": "p50/p99 served scan latency", "value": knee["p99_ms"], "unit": "ms",
+            "n_gpus": 1, "steps": a.serve_requests * len(points), "warmup": 0, "ms_per_step": None,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": "serving: Poisson requests over %d eight-column tables of %d rows "
+                                   "(%s), budget %.0f GiB, %d slots" % (
+                                       len(files), a.rows, "; ".join(d for _, d in files), a.serve_budget_gib,
+                                       a.serve_slots),
+                       "rows_per_request": "log-uniform 2^20..2^28, wrapping", "columns_per_request": "1..8",
+                       "l2": "inputs larger than L2"},
+            "serving": points, "clocks": clk.summary(),
+            "detail": {"catalog_rows": info.num_rows, "write_seconds": gen_s,
+                       "value_is": "p99 latency at the offered load with the highest decoded GB/s"}}
+    print(json.dumps(line), flush=True)
+    if a.json_out:
+        with open(a.json_out, "w") as f:
+            json.dump(line, f, indent=1)
+
+
 def main():
     a = parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -389,6 +506,10 @@ def main():
             dist.init_process_group("nccl")
     if a.impl == "reference":
         run_reference(a, rank, world)
+        return
+    if a.workload == "serve":
+        if rank == 0:
+            run_serve(a)
         return
     run_ours(a, rank, world, local_rank)
     if world > 1:

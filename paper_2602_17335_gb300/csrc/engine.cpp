@@ -135,7 +135,7 @@ static const char* where_name(int w) {
   }
 }
 
-static pq_status status_from_device(pq_ctx* ctx, const pqi::DevStatus& st) {
+pq_status status_from_device(pq_ctx* ctx, const pqi::DevStatus& st) {
   if (!st.flags) return PQ_OK;
   char buf[256];
   snprintf(buf, sizeof buf, "%s: %s at page %d (code %d)", where_name(st.where),
@@ -615,34 +615,25 @@ static void* plan_alloc_bytes(pq_plan* plan, size_t bytes) {
 }
 #define plan_alloc(T, plan, count) static_cast<T*>(plan_alloc_bytes(plan, std::max<size_t>(count, 1) * sizeof(T)))
 
-pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_plan** out, pq_out_size* sizes) {
-  if (!ctx || !idx || !req || !out) return fail(ctx, PQ_ERR_INVALID_ARG, "pq_plan_scan: bad arguments");
-  *out = nullptr;
-  CK(cudaSetDevice(ctx->device));
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  if ((req->flags & PQ_SCAN_TIMING) && (req->flags & PQ_SCAN_GRAPH))
+}  // extern "C"
+
+namespace pqe {
+
+// Host half of planning: plan pages, work item counts, job lists and the
+// scratch layout for the rows of `segs` (each segment's rows go to output
+// rows starting at its out0), nothing on the device yet.
+pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& cols, const std::vector<RowSeg>& segs,
+                     int64_t n_rows, uint32_t flags, std::unique_ptr<pq_plan>* out) {
+  if ((flags & PQ_SCAN_TIMING) && (flags & PQ_SCAN_GRAPH))
     return fail(ctx, PQ_ERR_INVALID_ARG, "PQ_SCAN_TIMING cannot be combined with PQ_SCAN_GRAPH");
   auto plan = std::make_unique<pq_plan>();
   plan->ctx = ctx;
   plan->idx = idx;
-  plan->flags = req->flags;
-  if (req->columns) {
-    for (int i = 0; i < req->n_columns; ++i) {
-      if (req->columns[i] < 0 || req->columns[i] >= idx->n_columns)
-        return fail(ctx, PQ_ERR_INVALID_ARG, "column id out of range");
-      plan->cols.push_back(req->columns[i]);
-    }
-  } else {
-    for (int i = 0; i < idx->n_columns; ++i) plan->cols.push_back(i);
-  }
-  if (req->row_begin < 0 || req->row_begin > idx->num_rows)
-    return fail(ctx, PQ_ERR_INVALID_ARG, "row range outside the indexed rows");
-  const int64_t rb = req->row_begin;
-  const int64_t re = req->row_count < 0 ? idx->num_rows : rb + req->row_count;
-  if (re > idx->num_rows) return fail(ctx, PQ_ERR_INVALID_ARG, "row range outside the indexed rows");
-  plan->row_begin = rb;
-  plan->n_rows = re - rb;
-  const bool plain = (req->flags & PQ_SCAN_PLAIN) != 0;
+  plan->flags = flags;
+  plan->cols = cols;
+  plan->row_begin = segs.empty() ? 0 : segs[0].rb;
+  plan->n_rows = n_rows;
+  const bool plain = (flags & PQ_SCAN_PLAIN) != 0;
   const int64_t item_rows_max = pqi::ITEM_ROWS;
   uint64_t scratch = 0;
   std::vector<int64_t> data_job_off;  // scratch offset per data snappy job
@@ -674,7 +665,9 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
                                                    : static_cast<uint64_t>(plan->n_rows) * col.width;
     sz.validity_bytes = col.optional ? static_cast<uint64_t>((plan->n_rows + 31) / 32) * 4 : 0;
     uint64_t chars = 0;
+    for (const RowSeg& seg : segs)
     for (size_t ch = 0; ch < idx->chunks.size(); ++ch) {
+      const int64_t rb = seg.rb, re = seg.re;
       if (idx->chunk_col[ch] != c) continue;
       const auto& cd = idx->chunks[ch];
       const int64_t c0 = idx->chunk_first_row[ch];
@@ -738,7 +731,7 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
         pp.col = static_cast<int32_t>(oc);
         pp.row_lo = static_cast<int32_t>(std::max<int64_t>(rb - p0, 0));
         pp.row_hi = static_cast<int32_t>(std::min<int64_t>(re - p0, pg.num_values));
-        pp.out_row = p0 - rb;
+        pp.out_row = seg.out0 + p0 - rb;
         pp.dict = dict;
         pp.body_len = pg.uncompressed;
         pp.nonnull = -1;
@@ -827,33 +820,45 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
     for (size_t i = 0; i < order.size(); ++i) sorted[i] = plan->walk_pps[order[i]];
     std::copy(sorted.begin(), sorted.end(), plan->walk_pps.begin() + cw.walk_begin);
   }
+  plan->device_bytes = plan_device_bytes(plan.get(), scratch);
+  plan->host_scratch = scratch;
+  *out = std::move(plan);
+  return PQ_OK;
+}
+
+// Device half: allocations from the context's pool, uploads, work items,
+// events, pinned staging.
+pq_status plan_upload(pq_plan* plan) {
+  pq_ctx* ctx = plan->ctx;
+  const bool plain = (plan->flags & PQ_SCAN_PLAIN) != 0;
+  const uint64_t scratch = plan->host_scratch;
   // device arrays
   const size_t npp = plan->pps.size(), nit = plan->n_items;
-  plan->d_walk_pps = plan_alloc(uint32_t, plan.get(), plan->walk_pps.size());
-  plan->d_delta_pps = plan_alloc(uint32_t, plan.get(), plan->delta_pps.size());
-  plan->d_dpos = plan_alloc(uint32_t, plan.get(), plan->delta_blocks);
-  plan->d_dbase = plan_alloc(int64_t, plan.get(), plan->delta_blocks);
-  plan->d_dregs = plan_alloc(pqi::DeltaRegion, plan.get(), plan->delta_regions);
-  plan->d_dreg_lists = plan_alloc(uint32_t, plan.get(), plan->delta_regions * pqi::DELTA_REGION_LIST);
-  plan->d_pps = plan_alloc(pqi::PlanPage, plan.get(), npp);
-  plan->d_items = plan_alloc(pqi::Item, plan.get(), nit);
-  plan->d_cols = plan_alloc(pqi::OutCol, plan.get(), plan->outcols.size());
-  plan->d_snappy = plan_alloc(pqi::SnappyJob, plan.get(), plan->snappy_data.size() + plan->snappy_dict.size());
-  plan->d_dict_jobs = plan_alloc(pqi::DictJob, plan.get(), plan->dict_jobs.size());
-  plan->d_str_cols = plan_alloc(int32_t, plan.get(), plan->str_cols.size());
-  plan->d_counter = plan_alloc(uint32_t, plan.get(), 4 + plan->outcols.size());
-  plan->d_status = plan_alloc(pqi::DevStatus, plan.get(), 1);
-  plan->d_scratch = scratch ? plan_alloc(uint8_t, plan.get(), scratch + 64) : nullptr;
+  plan->d_walk_pps = plan_alloc(uint32_t, plan, plan->walk_pps.size());
+  plan->d_delta_pps = plan_alloc(uint32_t, plan, plan->delta_pps.size());
+  plan->d_dpos = plan_alloc(uint32_t, plan, plan->delta_blocks);
+  plan->d_dbase = plan_alloc(int64_t, plan, plan->delta_blocks);
+  plan->d_dregs = plan_alloc(pqi::DeltaRegion, plan, plan->delta_regions);
+  plan->d_dreg_lists = plan_alloc(uint32_t, plan, plan->delta_regions * pqi::DELTA_REGION_LIST);
+  plan->d_pps = plan_alloc(pqi::PlanPage, plan, npp);
+  plan->d_items = plan_alloc(pqi::Item, plan, nit);
+  plan->d_cols = plan_alloc(pqi::OutCol, plan, plan->outcols.size());
+  plan->d_snappy = plan_alloc(pqi::SnappyJob, plan, plan->snappy_data.size() + plan->snappy_dict.size());
+  plan->d_dict_jobs = plan_alloc(pqi::DictJob, plan, plan->dict_jobs.size());
+  plan->d_str_cols = plan_alloc(int32_t, plan, plan->str_cols.size());
+  plan->d_counter = plan_alloc(uint32_t, plan, 4 + plan->outcols.size());
+  plan->d_status = plan_alloc(pqi::DevStatus, plan, 1);
+  plan->d_scratch = scratch ? plan_alloc(uint8_t, plan, scratch + 64) : nullptr;
   const uint64_t str_rows = static_cast<uint64_t>(plan->n_rows) * plan->str_cols.size();
-  plan->d_str_scratch = str_rows ? plan_alloc(uint32_t, plan.get(), str_rows) : nullptr;
-  plan->d_str_items = plan->str_cols.empty() ? nullptr : plan_alloc(uint64_t, plan.get(), nit);
+  plan->d_str_scratch = str_rows ? plan_alloc(uint32_t, plan, str_rows) : nullptr;
+  plan->d_str_items = plan->str_cols.empty() ? nullptr : plan_alloc(uint64_t, plan, nit);
   for (void* p : plan->owned)
     if (!p) {
-      free_plan_device(plan.get());
+      free_plan_device(plan);
       return fail(ctx, PQ_ERR_OOM, "plan allocation");
     }
   if ((scratch && !plan->d_scratch) || (str_rows && !plan->d_str_scratch)) {
-    free_plan_device(plan.get());
+    free_plan_device(plan);
     return fail(ctx, PQ_ERR_OOM, "plan scratch");
   }
   plan->scratch_bytes = scratch + str_rows * 4 + (plan->d_str_items ? nit * 8 : 0) + plan->delta_blocks * 12 +
@@ -879,7 +884,7 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
   std::vector<pqi::SnappyJob> alljobs(plan->snappy_data);
   alljobs.insert(alljobs.end(), plan->snappy_dict.begin(), plan->snappy_dict.end());
   if (npp) CK(cudaMemcpyAsync(plan->d_pps, plan->pps.data(), sizeof(pqi::PlanPage) * npp, cudaMemcpyHostToDevice, s));
-  if (nit) pqi::launch_make_items(decode_args(plan.get()), static_cast<int>(npp), s);
+  if (nit) pqi::launch_make_items(decode_args(plan), static_cast<int>(npp), s);
   if (!alljobs.empty())
     CK(cudaMemcpyAsync(plan->d_snappy, alljobs.data(), sizeof(pqi::SnappyJob) * alljobs.size(),
                        cudaMemcpyHostToDevice, s));
@@ -934,9 +939,52 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
   plan->expand_grid = static_cast<int>(std::min<size_t>(std::max<size_t>((nit + 7) / 8, 1), size_t(ctx->n_sms) * ebps));
   if (!plan->h_cols.reserve(sizeof(pqi::OutCol) * std::max<size_t>(plan->outcols.size(), 1)) ||
       !plan->h_out.reserve(sizeof(pqi::DevStatus) + 8 * std::max<size_t>(plan->outcols.size(), 1))) {
-    free_plan_device(plan.get());
+    free_plan_device(plan);
     return fail(ctx, PQ_ERR_OOM, "pinned staging");
   }
+  return PQ_OK;
+}
+
+uint64_t plan_device_bytes(const pq_plan* plan, uint64_t scratch) {
+  const uint64_t npp = plan->pps.size(), nit = plan->n_items;
+  const uint64_t str_rows = static_cast<uint64_t>(plan->n_rows) * plan->str_cols.size();
+  return npp * sizeof(pqi::PlanPage) + nit * sizeof(pqi::Item) + plan->outcols.size() * sizeof(pqi::OutCol) +
+         (plan->snappy_data.size() + plan->snappy_dict.size()) * sizeof(pqi::SnappyJob) +
+         plan->dict_jobs.size() * sizeof(pqi::DictJob) + 4 * (plan->walk_pps.size() + plan->delta_pps.size()) +
+         plan->delta_blocks * 12 +
+         plan->delta_regions * (sizeof(pqi::DeltaRegion) + 4ull * pqi::DELTA_REGION_LIST) + scratch + 64 +
+         str_rows * 4 + (plan->str_cols.empty() ? 0 : nit * 8) + 4096;
+}
+
+}  // namespace pqe
+
+extern "C" {
+
+pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_plan** out, pq_out_size* sizes) {
+  if (!ctx || !idx || !req || !out) return fail(ctx, PQ_ERR_INVALID_ARG, "pq_plan_scan: bad arguments");
+  *out = nullptr;
+  CK(cudaSetDevice(ctx->device));
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  std::vector<int32_t> cols;
+  if (req->columns) {
+    for (int i = 0; i < req->n_columns; ++i) {
+      if (req->columns[i] < 0 || req->columns[i] >= idx->n_columns)
+        return fail(ctx, PQ_ERR_INVALID_ARG, "column id out of range");
+      cols.push_back(req->columns[i]);
+    }
+  } else {
+    for (int i = 0; i < idx->n_columns; ++i) cols.push_back(i);
+  }
+  if (req->row_begin < 0 || req->row_begin > idx->num_rows)
+    return fail(ctx, PQ_ERR_INVALID_ARG, "row range outside the indexed rows");
+  const int64_t rb = req->row_begin;
+  const int64_t re = req->row_count < 0 ? idx->num_rows : rb + req->row_count;
+  if (re > idx->num_rows) return fail(ctx, PQ_ERR_INVALID_ARG, "row range outside the indexed rows");
+  std::unique_ptr<pq_plan> plan;
+  pq_status st = plan_build(ctx, idx, cols, {RowSeg{rb, re, 0}}, re - rb, req->flags, &plan);
+  if (st != PQ_OK) return st;
+  st = plan_upload(plan.get());
+  if (st != PQ_OK) return st;
   if (sizes)
     for (size_t i = 0; i < plan->sizes.size(); ++i) sizes[i] = plan->sizes[i];
   *out = plan.release();
@@ -1002,7 +1050,8 @@ static void enqueue_column(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, b
 // column overlap the bandwidth-bound expansion of the others.  With
 // PQ_SCAN_TIMING the stages run one after another over all columns, so that
 // each stage can be timed.  PQ_SCAN_PLAIN: per chunk, one launch per stage.
-static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts) {
+static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const cudaStream_t* branches,
+                         int n_branches) {
   pq_ctx* ctx = plan->ctx;
   pqi::DecodeArgs a = decode_args(plan);
   const int ncols = static_cast<int>(plan->outcols.size());
@@ -1074,7 +1123,7 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts) {
   } else {
     cudaEventRecord(plan->fork, s);
     for (int oc = 0; oc < ncols; ++oc) {
-      cudaStream_t b = ctx->branch[oc % pq_ctx::kBranches];
+      cudaStream_t b = branches[oc % n_branches];
       cudaStreamWaitEvent(b, plan->fork, 0);
       enqueue_column(plan, oc, a, with_dicts, b);
       cudaEventRecord(plan->join[oc], b);
@@ -1091,10 +1140,13 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts) {
   }
 }
 
-pq_status pq_scan_columns(pq_ctx* ctx, pq_plan* plan, const pq_column* outs, void* stream) {
-  if (!ctx || !plan || (!outs && !plan->outcols.empty())) return fail(ctx, PQ_ERR_INVALID_ARG, "pq_scan_columns");
-  CK(cudaSetDevice(ctx->device));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace pqe {
+
+pq_status scan_enqueue(pq_plan* plan, const pq_column* outs, cudaStream_t s, const cudaStream_t* branches,
+                       int n_branches, bool allow_graph) {
+  pq_ctx* ctx = plan->ctx;
   // output descriptors
   bool changed = false;
   for (size_t i = 0; i < plan->outcols.size(); ++i) {
@@ -1132,7 +1184,7 @@ pq_status pq_scan_columns(pq_ctx* ctx, pq_plan* plan, const pq_column* outs, voi
     for (int32_t ch : plan->dict_chunks) all = all && plan->idx->dict_resident[ch];
     with_dicts = !all;
   }
-  if ((plan->flags & PQ_SCAN_GRAPH) && !(plan->flags & PQ_SCAN_PLAIN)) {
+  if (allow_graph && (plan->flags & PQ_SCAN_GRAPH) && !(plan->flags & PQ_SCAN_PLAIN)) {
     if (plan->graph && plan->dicts_in_graph != with_dicts) {
       cudaGraphExecDestroy(plan->graph);
       plan->graph = nullptr;
@@ -1145,7 +1197,7 @@ pq_status pq_scan_columns(pq_ctx* ctx, pq_plan* plan, const pq_column* outs, voi
         own = true;
       }
       CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-      enqueue_scan(plan, cs, with_dicts);
+      enqueue_scan(plan, cs, with_dicts, branches, n_branches);
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamEndCapture(cs, &g);
       if (own) {
@@ -1160,13 +1212,23 @@ pq_status pq_scan_columns(pq_ctx* ctx, pq_plan* plan, const pq_column* outs, voi
     }
     CK(cudaGraphLaunch(plan->graph, s));
   } else {
-    enqueue_scan(plan, s, with_dicts);
+    enqueue_scan(plan, s, with_dicts, branches, n_branches);
   }
   CK(cudaGetLastError());
   CK(cudaEventRecord(plan->done, s));
   if (plan->flags & PQ_SCAN_RESIDENT_DICT)
     for (int32_t ch : plan->dict_chunks) plan->idx->dict_resident[ch] = 1;
   return PQ_OK;
+}
+
+}  // namespace pqe
+
+extern "C" {
+
+pq_status pq_scan_columns(pq_ctx* ctx, pq_plan* plan, const pq_column* outs, void* stream) {
+  if (!ctx || !plan || (!outs && !plan->outcols.empty())) return fail(ctx, PQ_ERR_INVALID_ARG, "pq_scan_columns");
+  CK(cudaSetDevice(ctx->device));
+  return scan_enqueue(plan, outs, static_cast<cudaStream_t>(stream), ctx->branch, pq_ctx::kBranches, true);
 }
 
 pq_status pq_scan_wait(pq_ctx* ctx, pq_plan* plan, void* stream, uint64_t* chars_bytes) {

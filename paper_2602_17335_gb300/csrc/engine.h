@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -111,6 +112,8 @@ struct pq_plan {
   uint64_t read_bytes = 0;
   uint64_t decoded_bytes = 0;
   uint64_t scratch_bytes = 0;
+  uint64_t host_scratch = 0;                 // decompression scratch bytes (plan_build)
+  uint64_t device_bytes = 0;                 // device bytes plan_upload will take
   // device
   pqi::PlanPage* d_pps = nullptr;
   pqi::Item* d_items = nullptr;
@@ -157,8 +160,21 @@ struct pq_plan {
 };
 
 namespace pqe {
+// Rows [rb, re) of the index, written to output rows starting at out0.
+struct RowSeg {
+  int64_t rb, re, out0;
+};
 // Shared helpers (engine.cpp)
 pq_status fail(pq_ctx* ctx, pq_status s, const std::string& msg);
+pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& cols, const std::vector<RowSeg>& segs,
+                     int64_t n_rows, uint32_t flags, std::unique_ptr<pq_plan>* out);
+pq_status plan_upload(pq_plan* plan);
+uint64_t plan_device_bytes(const pq_plan* plan, uint64_t scratch);
+// Enqueues one scan of `plan` into `outs` on `s`, columns forked onto
+// `branches` (n_branches >= 1); no host synchronisation.
+pq_status scan_enqueue(pq_plan* plan, const pq_column* outs, cudaStream_t s, const cudaStream_t* branches,
+                       int n_branches, bool allow_graph);
+pq_status status_from_device(pq_ctx* ctx, const pqi::DevStatus& st);
 pq_status cuda_fail(pq_ctx* ctx, cudaError_t e, const char* what);
 pqi::DecodeArgs decode_args(pq_plan* plan);
 }  // namespace pqe

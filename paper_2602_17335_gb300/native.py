@@ -300,3 +300,37 @@ def pq_delta_decode_static(ctx, d_stream, stream_len, ptype, n_values, d_values,
     """Allocation-free decode of one DELTA_BINARY_PACKED stream (device
     pointers); returns the status without raising."""
     return lib().pq_delta_decode_static(ctx, d_stream, stream_len, ptype, n_values, d_values, stream)
+
+
+def pq_serve_create(ctx, idx, budget_bytes, slots=4, timeout_ms=0):
+    cfg = pq_serve_config(budget_bytes, slots, timeout_ms)
+    srv = C.c_void_p()
+    check(lib().pq_serve_create(ctx, idx, C.byref(cfg), C.byref(srv)), ctx)
+    return srv.value
+
+
+def pq_serve_submit(srv, columns, row_begin, row_count):
+    """Returns (status, ticket); does not raise (PQ_ERR_BUDGET is an answer)."""
+    arr = (C.c_int32 * len(columns))(*columns)
+    req = pq_serve_request(arr, len(columns), 0, row_begin, row_count)
+    t = C.c_uint64()
+    st = lib().pq_serve_submit(srv, C.byref(req), C.byref(t))
+    return st, t.value
+
+
+def pq_serve_poll(srv, ticket):
+    """Returns None while running, else the filled pq_serve_result."""
+    res = pq_serve_result()
+    done = C.c_int()
+    st = lib().pq_serve_poll(srv, ticket, C.byref(res), C.byref(done))
+    if st != PQ_OK:
+        raise PqError(st, "pq_serve_poll")
+    return res if done.value else None
+
+
+def pq_serve_release(srv, ticket):
+    return lib().pq_serve_release(srv, ticket)
+
+
+def pq_serve_destroy(srv):
+    lib().pq_serve_destroy(srv)

@@ -61,3 +61,38 @@ def assert_columns_equal(outs, expect, chars_sizes=None):
             words = bitmap_words(e.valid)
             got = o.validity.cpu().numpy().view(np.uint8)[:len(words)]
             assert np.array_equal(got, words), f"{e.name}: validity differs"
+
+
+def _cudart():
+    import ctypes
+    for name in ("libcudart.so.13", "libcudart.so"):
+        try:
+            lib = ctypes.CDLL(name)
+            lib.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+            lib.cudaMemcpy.restype = ctypes.c_int
+            return lib
+        except OSError:
+            continue
+    raise RuntimeError("CUDA runtime library not found")
+
+
+def server_result_outs(res):
+    """Copies a serving result's server-owned device columns into torch
+    tensors (ColumnOut objects), so they compare like scan outputs."""
+    import torch
+    from paper_2602_17335_gb300 import native as N
+    from paper_2602_17335_gb300.scan import alloc_outputs
+    rt = _cudart()
+    sizes = [res.sizes[i] for i in range(res.n_columns)]
+    outs = alloc_outputs(sizes)
+    for i, o in enumerate(outs):
+        c = res.columns[i]
+        s = sizes[i]
+        vb = (s.n_rows + 1) * 8 if s.type == N.PQ_TYPE_BYTE_ARRAY else s.values_bytes
+        assert rt.cudaMemcpy(o.values.data_ptr(), c.values, vb, 4) == 0
+        if o.validity is not None and s.validity_bytes:
+            assert rt.cudaMemcpy(o.validity.data_ptr(), c.validity, s.validity_bytes, 4) == 0
+        if o.chars is not None and s.chars_bytes:
+            assert rt.cudaMemcpy(o.chars.data_ptr(), c.chars, s.chars_bytes, 4) == 0
+    torch.cuda.synchronize()
+    return outs
