@@ -60,8 +60,15 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scan-reps", type=int, default=10, help="graph replays for the roofline")
     ap.add_argument("--json-out", default=None)
-    ap.add_argument("--workload", default="scan", choices=["scan", "serve"],
-                    help="scan: one table, index+plan+scan per step; serve: Poisson requests through pq_serve_*")
+    ap.add_argument("--workload", default="scan", choices=["scan", "serve", "batched", "single"],
+                    help="scan: one table, index+plan+scan per step; serve: Poisson requests through pq_serve_*; "
+                         "batched: many uneven single-column files in one graph launch vs plain launches; "
+                         "single: one dictionary INT32 column, plain one-page-per-block vs batched")
+    ap.add_argument("--c4-files", type=int, default=256)
+    ap.add_argument("--c4-chunks-per-file", type=int, default=4)
+    ap.add_argument("--c4-rows-lo", type=float, default=1e4)
+    ap.add_argument("--c4-rows-hi", type=float, default=1e6)
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-files", type=int, default=4, help="serve: tables in the catalog index")
     ap.add_argument("--serve-requests", type=int, default=200, help="serve: requests per offered-load point")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serve: mean arrivals per second at 1x")
@@ -490,6 +497,175 @@ def run_serve(a):
             json.dump(line, f, indent=1)
 
 
+# ----------------------------------------------------------------- batched (uneven chunks, one graph)
+
+def _pack_files(datas, torch):
+    """One device buffer holding every file at a 256-byte aligned offset."""
+    offs, tot = [], 0
+    for d in datas:
+        offs.append(tot)
+        tot += (d.nbytes + 255) // 256 * 256
+    host = np.zeros(tot, np.uint8)
+    for d, o in zip(datas, offs):
+        host[o:o + d.nbytes] = d
+    dev = torch.from_numpy(host).cuda()
+    return dev, [(dev.data_ptr() + o, d.nbytes) for d, o in zip(datas, offs)]
+
+
+def _time_batch(N, ctx, batch, stream, reps, torch):
+    for _ in range(3):
+        N.pq_batch_launch(ctx, batch, stream)
+    assert N.pq_batch_wait(batch) == N.PQ_OK, N.pq_last_error(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        N.pq_batch_launch(ctx, batch, stream)
+    e1.record()
+    torch.cuda.synchronize()
+    assert N.pq_batch_wait(batch) == N.PQ_OK, N.pq_last_error(ctx)
+    return e0.elapsed_time(e1) / reps
+
+
+def run_batched(a):
+    import torch
+    from paper_2602_17335_gb300 import native as N
+    from paper_2602_17335_gb300.autotune import autotune
+    from paper_2602_17335_gb300.scan import Engine, alloc_outputs, stream_handle
+    from paper_2602_17335_gb300.tables import write_table
+    t0 = time.time()
+    draws = synth.config4_draws(n_files=a.c4_files, chunks_per_file=a.c4_chunks_per_file, rows_lo=a.c4_rows_lo,
+                                rows_hi=a.c4_rows_hi)
+    groups = {}
+    for d in draws:
+        col, cspec = synth.config4_column(d)
+        data = write_table(synth.Table([col]), synth.TableSpec(rg_rows=d.n_rows, page_bytes=d.page_bytes,
+                                                               columns=[cspec]))
+        groups.setdefault(d.kind, []).append(data)
+    gen_s = time.time() - t0
+    eng = Engine(0)
+    sh = stream_handle(torch.cuda.current_stream())
+    keep, idxs = [], []
+    for kind, datas in groups.items():
+        dev, files = _pack_files(datas, torch)
+        keep.append(dev)
+        idxs.append(N.pq_index_chunks(eng.ctx, files, sh))
+    pages = sum(N.pq_index_get_info(ix).n_data_pages for ix in idxs)
+    stored = sum(d.nbytes for ds in groups.values() for d in ds)
+
+    def build(flags):
+        plans, outs, dec, rd = [], [], 0, 0
+        for ix in idxs:
+            pl, sizes = N.pq_plan_scan(eng.ctx, ix, None, 0, -1, flags)
+            info = N.pq_plan_get_info(pl)
+            dec += info.decoded_bytes
+            rd += info.read_bytes
+            plans.append(pl)
+            outs.append(alloc_outputs(sizes))
+        return plans, outs, dec, rd
+
+    def free(plans):
+        for pl in plans:
+            N.pq_free_plan(pl)
+
+    def time_mode(flags, graph, reps):
+        plans, outs, dec, rd = build(flags)
+        b = N.pq_batch_create(eng.ctx, plans, [[o.desc() for o in oo] for oo in outs],
+                              N.PQ_SCAN_GRAPH if graph else 0)
+        ms = _time_batch(N, eng.ctx, b, sh, reps, torch)
+        launches = sum(N.pq_plan_get_info(pl).launches_per_scan for pl in plans)
+        N.pq_batch_free(b)
+        free(plans)
+        del outs
+        return ms, dec, rd, launches
+
+    tuned, trials = None, []
+    if not a.no_autotune:
+        tuned, _, trials = autotune(eng.ctx, lambda t: time_mode(N.PQ_SCAN_BATCHED, True, 3)[0])
+    with ClockSampler(0) as clk:
+        ms_graph, dec, rd, launches = time_mode(N.PQ_SCAN_BATCHED, True, a.steps)
+    ms_stream, _, _, _ = time_mode(N.PQ_SCAN_BATCHED, False, a.steps)
+    ms_plain, _, _, plain_launches = time_mode(N.PQ_SCAN_PLAIN, False, max(2, a.steps // 2))
+    value = dec / (ms_graph * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    achieved = (rd + dec) / (ms_graph * 1e-3) / 1e9
+    line = {"metric": "decoded GB/s", "value": value, "unit": "GB/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": 3, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "batched: %d single-column files, rows log-uniform [%g, %g], pages log-uniform "
+                                   "4 KiB-2 MiB, kinds dict INT32 / dict string / PLAIN FP64 / DELTA INT64 / "
+                                   "OPTIONAL PLAIN INT64, half Snappy, V1/V2 half each" % (
+                                       len(draws), a.c4_rows_lo, a.c4_rows_hi),
+                       "step": "one batch launch (all chunks' kernels in one CUDA graph)",
+                       "l2": "inputs larger than L2 (%.2f GB stored, %.2f GB decoded)" % (stored / 1e9, dec / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "one batch graph launch"},
+            "compare": {"graph_ms": ms_graph, "streams_no_graph_ms": ms_stream, "plain_per_page_ms": ms_plain,
+                        "plain_vs_graph": ms_plain / ms_graph, "graph_launches_inside": launches,
+                        "plain_launches": plain_launches},
+            "autotune": {"chosen": tuned, "trials": [{"tuning": t, "ms": m} for t, m in trials]},
+            "gpu_launches": a.steps * launches, "clocks": clk.summary(),
+            "detail": {"chunks": len(draws), "data_pages": pages, "decoded_bytes": dec, "read_bytes": rd,
+                       "write_seconds": gen_s}}
+    for ix in idxs:
+        N.pq_free_index(ix)
+    eng.close()
+    print(json.dumps(line), flush=True)
+    if a.json_out:
+        with open(a.json_out, "w") as f:
+            json.dump(line, f, indent=1)
+
+
+def run_single(a):
+    """One REQUIRED INT32 column, 2^20 rows uniform in [0, 1024), dictionary
+    encoded (bit width 10), one row group, 1 MiB pages, uncompressed: the
+    plain one-page-per-block decode against the batched scan."""
+    import torch
+    from paper_2602_17335_gb300 import native as N
+    from paper_2602_17335_gb300.scan import Engine, alloc_outputs, stream_handle
+    from paper_2602_17335_gb300.tables import write_table
+    tab = synth.config1_table()
+    data = write_table(tab, synth.config1_spec())
+    dev = torch.from_numpy(data).cuda()
+    eng = Engine(0)
+    sh = stream_handle(torch.cuda.current_stream())
+    idx = eng.index([dev])
+    res = {}
+    with ClockSampler(0) as clk:
+        for name, flags in (("plain", N.PQ_SCAN_PLAIN), ("batched", N.PQ_SCAN_BATCHED | N.PQ_SCAN_GRAPH)):
+            pl, sizes = eng.plan(idx, flags=flags)
+            info = N.pq_plan_get_info(pl)
+            outs = alloc_outputs(sizes)
+            for _ in range(3):
+                eng.scan(pl, outs, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(a.steps):
+                eng.scan(pl, outs, torch.cuda.current_stream())
+            e1.record()
+            torch.cuda.synchronize()
+            st, _ = eng.wait(pl, len(outs))
+            assert st == N.PQ_OK, N.pq_last_error(eng.ctx)
+            ms = e0.elapsed_time(e1) / a.steps
+            res[name] = {"ms": ms, "decoded_gbs": info.decoded_bytes / (ms * 1e-3) / 1e9,
+                         "launches_per_scan": info.launches_per_scan, "pages": info.n_pages}
+            N.pq_free_plan(pl)
+    N.pq_free_index(idx)
+    eng.close()
+    line = {"metric": "decoded GB/s", "value": res["batched"]["decoded_gbs"], "unit": "GB/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": 3, "ms_per_step": res["batched"]["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "one dictionary INT32 column, 2^20 rows U[0,1024), bit width 10, one row group, "
+                                   "1 MiB pages, uncompressed", "step": "one scan launch",
+                       "l2": "inputs smaller than L2 (4 MiB out); scan replayed back to back"},
+            "compare": res, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    if a.json_out:
+        with open(a.json_out, "w") as f:
+            json.dump(line, f, indent=1)
+
+
 def main():
     a = parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -507,9 +683,9 @@ def main():
     if a.impl == "reference":
         run_reference(a, rank, world)
         return
-    if a.workload == "serve":
+    if a.workload in ("serve", "batched", "single"):
         if rank == 0:
-            run_serve(a)
+            {"serve": run_serve, "batched": run_batched, "single": run_single}[a.workload](a)
         return
     run_ours(a, rank, world, local_rank)
     if world > 1:

@@ -359,6 +359,50 @@ pq_status pq_write_table(const pq_write_column* cols, int n_cols, int64_t n_rows
                          uint64_t* out_size);
 void pq_write_free(uint8_t* buf);
 
+/* ------------------------------------------------------------ tuning */
+
+/* Knobs of the batched scan, per context; plans built afterwards use them
+ * (the autotuner in paper_2602_17335_gb300/autotune.py picks them by
+ * timing a sample of the workload).  They trade scheduling granularity
+ * against per-item overhead: the paper's Section 3 (Insight 1) ties
+ * parallelism to page count, this engine to work items of `item_rows`. */
+typedef struct pq_tuning {
+  int32_t item_rows;          /* rows per work item: REQUIRED pages and OPTIONAL PLAIN
+                                 pages; 256..65536, a multiple of 32 (default 2048) */
+  int32_t item_rows_opt;      /* rows per work item of OPTIONAL non-PLAIN pages;
+                                 32..512, a multiple of 32 (default 512) */
+  int32_t expand_ctas_per_sm; /* cap on resident CTAs per SM of the expansion and copy
+                                 kernels; 0 = the occupancy limit (default) */
+  int32_t branches;           /* streams the columns of one scan are forked onto, 1..8
+                                 (default 8) */
+} pq_tuning;
+
+/* Errors: PQ_ERR_INVALID_ARG (NULL, or a knob out of range). */
+pq_status pq_ctx_set_tuning(pq_ctx* ctx, const pq_tuning* t);
+pq_status pq_ctx_get_tuning(const pq_ctx* ctx, pq_tuning* t);
+
+/* ------------------------------------------------------------ batched scan */
+
+/* A batch groups several plans (typically one per schema of a heterogeneous
+ * set of files: the batched workload's thousands of uneven chunks) into one
+ * unit of work.  With PQ_SCAN_GRAPH in `flags` the scans of all plans are
+ * captured once into a single CUDA graph and each pq_batch_launch is one
+ * graph launch; otherwise each launch enqueues the kernels.  Plans run
+ * concurrently, each on its own stream, their columns in sequence.
+ * `outs[i]` is plan i's output array (as for pq_scan_columns), copied at
+ * creation; plans and output buffers must outlive the batch.
+ * Errors: PQ_ERR_INVALID_ARG, PQ_ERR_CAPACITY (as pq_scan_columns),
+ * PQ_ERR_CUDA. */
+typedef struct pq_batch pq_batch;
+pq_status pq_batch_create(pq_ctx* ctx, int n_plans, pq_plan* const* plans, const pq_column* const* outs,
+                          uint32_t flags, pq_batch** out);
+/* Enqueues one run of the batch on `stream` (NULL = legacy default stream). */
+pq_status pq_batch_launch(pq_batch* b, void* stream);
+/* Waits for the last launch; returns the first device error of any plan
+ * (per-plan string sizes: pq_scan_wait on the plan afterwards). */
+pq_status pq_batch_wait(pq_batch* b);
+void pq_batch_free(pq_batch* b);
+
 /* ---- Allocation-free DELTA stream decode (no counterpart in the paper) ----
  *
  * Decodes one DELTA_BINARY_PACKED value stream (the Parquet encoding the

@@ -1,0 +1,59 @@
+"""Autotuner for the batched scan's knobs (``pq_tuning`` in include/pq.h).
+
+The knobs set scheduling granularity:
+- rows per work item (REQUIRED and OPTIONAL-PLAIN pages, and OPTIONAL
+  non-PLAIN pages);
+- resident CTAs per SM of the expansion kernels;
+- how many streams one scan's columns are forked onto.
+
+The paper's Section 3 (Insight 1) ties a GPU reader's parallelism to its
+page count. Here parallelism comes from work items, so the best item size
+depends on the mix of pages, encodings and sizes. It is found by timing.
+
+The tuner does coordinate descent: each knob in turn over its candidate
+values, keeping the fastest setting. It times with a caller-supplied function
+that rebuilds the plans under the tuning it is given and returns milliseconds
+per run. The chosen tuning is left set on the context.
+"""
+from __future__ import annotations
+
+from typing import Callable, Dict, List, Tuple
+
+from . import native as N
+
+DEFAULT: Dict[str, int] = {"item_rows": 2048, "item_rows_opt": 512, "expand_ctas_per_sm": 0, "branches": 8}
+
+CANDIDATES: Dict[str, List[int]] = {
+    "item_rows": [1024, 2048, 4096, 8192],
+    "item_rows_opt": [256, 512],
+    "expand_ctas_per_sm": [0, 2],
+    "branches": [4, 8],
+}
+
+
+def autotune(ctx, time_ms: Callable[[Dict[str, int]], float], rounds: int = 1,
+             candidates: Dict[str, List[int]] = None) -> Tuple[Dict[str, int], float, List[Tuple[Dict[str, int], float]]]:
+    """Returns (best tuning, its ms, every trial).  `time_ms(tuning)` must
+    apply nothing itself: the tuner sets the tuning on `ctx` before each call."""
+    cands = candidates or CANDIDATES
+    trials: List[Tuple[Dict[str, int], float]] = []
+
+    def run(t: Dict[str, int]) -> float:
+        N.pq_ctx_set_tuning(ctx, **t)
+        ms = time_ms(t)
+        trials.append((dict(t), ms))
+        return ms
+
+    best = dict(DEFAULT)
+    best_ms = run(best)
+    for _ in range(rounds):
+        for knob, values in cands.items():
+            for v in values:
+                if v == best[knob]:
+                    continue
+                t = dict(best, **{knob: v})
+                ms = run(t)
+                if ms < best_ms:
+                    best, best_ms = t, ms
+    N.pq_ctx_set_tuning(ctx, **best)
+    return best, best_ms, trials

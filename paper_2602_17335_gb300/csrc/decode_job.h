@@ -48,9 +48,10 @@ void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, DictDev* 
 // Launches over sub-ranges (one output column's share of the plan).
 void launch_walk(const DecodeArgs& a, int wbegin, int n, cudaStream_t s);
 void launch_delta_bases(const DecodeArgs& a, int dbegin, int n, int max_regions, cudaStream_t s);
-void launch_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, cudaStream_t s);
+void launch_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, int ctas_per_sm, cudaStream_t s);
 // Items of a column whose pages are all REQUIRED PLAIN fixed-width: copies.
-void launch_copy_items(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, cudaStream_t s);
+void launch_copy_items(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, int ctas_per_sm,
+                       cudaStream_t s);
 void launch_strings(const DecodeArgs& a, int col, int n_items, int n_sms, cudaStream_t s);
 // Plain baseline: pages [pp_begin, pp_begin + n) decoded one page per block.
 void launch_plain_pages(const DecodeArgs& a, int pp_begin, int n, cudaStream_t s);

@@ -215,6 +215,22 @@ void pq_ctx_destroy(pq_ctx* ctx) {
 
 const char* pq_last_error(const pq_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
 
+pq_status pq_ctx_set_tuning(pq_ctx* ctx, const pq_tuning* t) {
+  if (!ctx || !t) return PQ_ERR_INVALID_ARG;
+  if (t->item_rows < 256 || t->item_rows > 65536 || t->item_rows % 32 || t->item_rows_opt < 32 ||
+      t->item_rows_opt > pqi::ITEM_ROWS_OPT || t->item_rows_opt % 32 || t->expand_ctas_per_sm < 0 ||
+      t->branches < 1 || t->branches > pq_ctx::kBranches)
+    return fail(ctx, PQ_ERR_INVALID_ARG, "pq_ctx_set_tuning: knob out of range");
+  ctx->tuning = *t;
+  return PQ_OK;
+}
+
+pq_status pq_ctx_get_tuning(const pq_ctx* ctx, pq_tuning* t) {
+  if (!ctx || !t) return PQ_ERR_INVALID_ARG;
+  *t = ctx->tuning;
+  return PQ_OK;
+}
+
 // ------------------------------------------------------------------ index
 
 static void free_index_device(pq_index* idx) {
@@ -634,7 +650,8 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
   plan->row_begin = segs.empty() ? 0 : segs[0].rb;
   plan->n_rows = n_rows;
   const bool plain = (flags & PQ_SCAN_PLAIN) != 0;
-  const int64_t item_rows_max = pqi::ITEM_ROWS;
+  plan->tuning = ctx->tuning;
+  const int64_t item_rows_max = plan->tuning.item_rows;
   uint64_t scratch = 0;
   std::vector<int64_t> data_job_off;  // scratch offset per data snappy job
   std::vector<int64_t> walk_cost;     // estimated chain steps per walked page
@@ -783,7 +800,7 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
                                                                                                  : pg.num_values / 256);
         }
         const int64_t span = pp.row_hi - pp.row_lo;
-        const int64_t per = (cd.max_def && !plain_fixed) ? pqi::ITEM_ROWS_OPT : item_rows_max;
+        const int64_t per = (cd.max_def && !plain_fixed) ? plan->tuning.item_rows_opt : item_rows_max;
         const uint32_t n_it = static_cast<uint32_t>((span + per - 1) / per);
         pp.item_rows = static_cast<int32_t>(per);
         pp.item_count = n_it;
@@ -1036,10 +1053,10 @@ static void enqueue_column(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, b
   const auto& col = plan->outcols[oc];
   if (cw.copy_only)
     pqi::launch_copy_items(a, static_cast<int>(col.item_begin), static_cast<int>(col.item_count),
-                           static_cast<int>(oc), ctx->n_sms, s);
+                           static_cast<int>(oc), ctx->n_sms, plan->tuning.expand_ctas_per_sm, s);
   else
     pqi::launch_expand(a, static_cast<int>(col.item_begin), static_cast<int>(col.item_count), static_cast<int>(oc),
-                       ctx->n_sms, s);
+                       ctx->n_sms, plan->tuning.expand_ctas_per_sm, s);
   if (col.ptype == pqi::T_BYTE_ARRAY)
     pqi::launch_strings(a, static_cast<int>(oc), static_cast<int>(col.item_count), ctx->n_sms, s);
 }
@@ -1112,10 +1129,10 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
       const auto& oco = plan->outcols[oc];
       if (plan->colwork[oc].copy_only)
         pqi::launch_copy_items(a, static_cast<int>(oco.item_begin), static_cast<int>(oco.item_count), oc,
-                               ctx->n_sms, s);
+                               ctx->n_sms, plan->tuning.expand_ctas_per_sm, s);
       else
         pqi::launch_expand(a, static_cast<int>(oco.item_begin), static_cast<int>(oco.item_count), oc, ctx->n_sms,
-                           s);
+                           plan->tuning.expand_ctas_per_sm, s);
     }
     mark(5);
     for (int32_t sc : plan->str_cols)
@@ -1228,7 +1245,8 @@ extern "C" {
 pq_status pq_scan_columns(pq_ctx* ctx, pq_plan* plan, const pq_column* outs, void* stream) {
   if (!ctx || !plan || (!outs && !plan->outcols.empty())) return fail(ctx, PQ_ERR_INVALID_ARG, "pq_scan_columns");
   CK(cudaSetDevice(ctx->device));
-  return scan_enqueue(plan, outs, static_cast<cudaStream_t>(stream), ctx->branch, pq_ctx::kBranches, true);
+  const int nb = std::min<int>(std::max<int>(plan->tuning.branches, 1), pq_ctx::kBranches);
+  return scan_enqueue(plan, outs, static_cast<cudaStream_t>(stream), ctx->branch, nb, true);
 }
 
 pq_status pq_scan_wait(pq_ctx* ctx, pq_plan* plan, void* stream, uint64_t* chars_bytes) {

@@ -50,6 +50,7 @@ struct pq_ctx {
   static constexpr int kBranches = 8;
   cudaStream_t branch[kBranches] = {};  // per-column branches of a scan
   std::string last_error;
+  pq_tuning tuning{pqi::ITEM_ROWS, pqi::ITEM_ROWS_OPT, 0, kBranches};
   pqe::DevPool pool;
   pqe::Pinned tail;     // footer staging
   std::mutex mu;        // serialises use from the serving thread and the API
@@ -114,6 +115,7 @@ struct pq_plan {
   uint64_t scratch_bytes = 0;
   uint64_t host_scratch = 0;                 // decompression scratch bytes (plan_build)
   uint64_t device_bytes = 0;                 // device bytes plan_upload will take
+  pq_tuning tuning{};                        // the context's knobs when the plan was built
   // device
   pqi::PlanPage* d_pps = nullptr;
   pqi::Item* d_items = nullptr;

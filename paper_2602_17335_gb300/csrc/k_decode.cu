@@ -2349,22 +2349,25 @@ void launch_delta_bases(const DecodeArgs& a, int dbegin, int n, int max_regions,
   k_delta_scan<<<n, 256, 0, s>>>(a, dbegin);
 }
 
-void launch_copy_items(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, cudaStream_t s) {
+void launch_copy_items(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, int ctas_per_sm,
+                       cudaStream_t s) {
   if (n <= 0) return;
   static int bps = 0;
   if (!bps) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_copy_items, 256, 0);
     if (bps < 1) bps = 1;
   }
+  const int per_sm = ctas_per_sm > 0 && ctas_per_sm < bps ? ctas_per_sm : bps;
   int blocks = (n + 7) / 8;
-  if (blocks > n_sms * bps) blocks = n_sms * bps;
+  if (blocks > n_sms * per_sm) blocks = n_sms * per_sm;
   k_copy_items<<<blocks, 256, 0, s>>>(a, ibegin, n, cidx);
 }
 
-void launch_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, cudaStream_t s) {
+void launch_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, int ctas_per_sm, cudaStream_t s) {
   if (n <= 0) return;
   int blocks = (n + EXP_WARPS - 1) / EXP_WARPS;
-  const int cap = n_sms * expand_blocks_per_sm();
+  const int bps = expand_blocks_per_sm();
+  const int cap = n_sms * (ctas_per_sm > 0 && ctas_per_sm < bps ? ctas_per_sm : bps);
   if (blocks > cap) blocks = cap;
   k_expand<<<blocks, EXP_THREADS, 0, s>>>(a, ibegin, n, cidx);
 }

@@ -88,6 +88,11 @@ class pq_write_column(C.Structure):
                 ("chars", C.c_void_p), ("valid", C.c_void_p)]
 
 
+class pq_tuning(C.Structure):
+    _fields_ = [("item_rows", C.c_int32), ("item_rows_opt", C.c_int32), ("expand_ctas_per_sm", C.c_int32),
+                ("branches", C.c_int32)]
+
+
 _P = C.c_void_p
 _SIGS = {
     "pq_version": (C.c_char_p, []),
@@ -117,6 +122,13 @@ _SIGS = {
                                  C.c_int, C.POINTER(C.POINTER(C.c_uint8)), C.POINTER(C.c_uint64)]),
     "pq_write_free": (None, [C.POINTER(C.c_uint8)]),
     "pq_delta_decode_static": (C.c_int, [_P, _P, C.c_uint64, C.c_int, C.c_int64, _P, _P]),
+    "pq_ctx_set_tuning": (C.c_int, [_P, C.POINTER(pq_tuning)]),
+    "pq_ctx_get_tuning": (C.c_int, [_P, C.POINTER(pq_tuning)]),
+    "pq_batch_create": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(C.POINTER(pq_column)), C.c_uint32,
+                                  C.POINTER(_P)]),
+    "pq_batch_launch": (C.c_int, [_P, _P]),
+    "pq_batch_wait": (C.c_int, [_P]),
+    "pq_batch_free": (None, [_P]),
 }
 
 _lib = None
@@ -334,3 +346,38 @@ def pq_serve_release(srv, ticket):
 
 def pq_serve_destroy(srv):
     lib().pq_serve_destroy(srv)
+
+
+def pq_ctx_set_tuning(ctx, item_rows=2048, item_rows_opt=512, expand_ctas_per_sm=0, branches=8):
+    t = pq_tuning(item_rows, item_rows_opt, expand_ctas_per_sm, branches)
+    check(lib().pq_ctx_set_tuning(ctx, C.byref(t)), ctx)
+
+
+def pq_ctx_get_tuning(ctx):
+    t = pq_tuning()
+    check(lib().pq_ctx_get_tuning(ctx, C.byref(t)), ctx)
+    return {"item_rows": t.item_rows, "item_rows_opt": t.item_rows_opt,
+            "expand_ctas_per_sm": t.expand_ctas_per_sm, "branches": t.branches}
+
+
+def pq_batch_create(ctx, plans, outs_per_plan, flags=0):
+    """plans: plan handles; outs_per_plan: list of lists of pq_column."""
+    n = len(plans)
+    parr = (C.c_void_p * n)(*plans)
+    keep = [(pq_column * max(len(o), 1))(*o) for o in outs_per_plan]
+    oarr = (C.POINTER(pq_column) * n)(*[C.cast(k, C.POINTER(pq_column)) for k in keep])
+    b = C.c_void_p()
+    check(lib().pq_batch_create(ctx, n, parr, oarr, flags, C.byref(b)), ctx)
+    return b.value
+
+
+def pq_batch_launch(ctx, batch, stream=None):
+    check(lib().pq_batch_launch(batch, stream), ctx)
+
+
+def pq_batch_wait(batch):
+    return lib().pq_batch_wait(batch)
+
+
+def pq_batch_free(batch):
+    lib().pq_batch_free(batch)

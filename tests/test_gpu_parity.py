@@ -214,3 +214,68 @@ def test_delta_block_chains_across_regions(eng):
             synth.ColumnData("rand32", "INT32", rng.integers(-2**31, 2**31, m, dtype=np.int64).astype(np.int32))]
     spec = synth.TableSpec(m, 64 << 20, [synth.ColumnSpec("DELTA_BINARY_PACKED")] * 2)
     _roundtrip(eng, W.write_file(synth.Table(wide), spec))
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_of_heterogeneous_chunks(eng, graph):
+    """Batched workload in miniature: single-column files of five kinds,
+    grouped by schema into one index and one plan each, all plans run as one
+    batch (one CUDA graph launch, or enqueued), launched twice; every column
+    equals the oracle's reading of its files; then again under a non-default
+    tuning (smaller work items, fewer branches, capped CTAs)."""
+    from paper_2602_17335_gb300 import native as N
+    from paper_2602_17335_gb300.scan import alloc_outputs
+    draws = synth.config4_draws(n_files=6, chunks_per_file=4, rows_lo=300, rows_hi=30_000, page_lo=512,
+                                page_hi=32 * 1024)
+    groups = {}
+    for d in draws:
+        col, cspec = synth.config4_column(d)
+        data = W.write_file(synth.Table([col]), synth.TableSpec(rg_rows=7_000, page_bytes=d.page_bytes,
+                                                                columns=[cspec]))
+        groups.setdefault(d.kind, []).append(data)
+    expected = {}
+    for kind, datas in groups.items():
+        parts = [R.read_file(d)[0] for d in datas]
+        from oracle.reader import ColumnResult
+        p0 = parts[0]
+        valid = None if p0.valid is None else np.concatenate([p.valid for p in parts])
+        if p0.ptype == "BYTE_ARRAY":
+            offs, base = [np.zeros(1, np.int64)], 0
+            for p in parts:
+                offs.append(p.offsets[1:] + base)
+                base += int(p.offsets[-1])
+            expected[kind] = ColumnResult(p0.name, p0.ptype, None, valid, np.concatenate(offs),
+                                          np.concatenate([p.chars for p in parts]))
+        else:
+            expected[kind] = ColumnResult(p0.name, p0.ptype, np.concatenate([p.values for p in parts]), valid)
+    devs = {k: [to_dev(d) for d in v] for k, v in groups.items()}
+    for tuning in (None, dict(item_rows=512, item_rows_opt=64, expand_ctas_per_sm=1, branches=2)):
+        if tuning:
+            N.pq_ctx_set_tuning(eng.ctx, **tuning)
+        try:
+            idxs, plans, outs, kinds = [], [], [], []
+            for kind, files in devs.items():
+                ix = eng.index(files)
+                pl, sizes = eng.plan(ix)
+                idxs.append(ix)
+                plans.append(pl)
+                outs.append(alloc_outputs(sizes))
+                kinds.append(kind)
+            b = N.pq_batch_create(eng.ctx, plans, [[o.desc() for o in oo] for oo in outs],
+                                  N.PQ_SCAN_GRAPH if graph else 0)
+            for _ in range(2):
+                N.pq_batch_launch(eng.ctx, b)
+                assert N.pq_batch_wait(b) == N.PQ_OK, N.pq_last_error(eng.ctx)
+                for pl, oo, kind in zip(plans, outs, kinds):
+                    st, chars = eng.wait(pl, len(oo))
+                    assert st == N.PQ_OK
+                    if oo[0].chars is not None:
+                        oo[0].chars = oo[0].chars[:chars[0]]
+                    assert_columns_equal(oo, [expected[kind]])
+            N.pq_batch_free(b)
+            for pl in plans:
+                N.pq_free_plan(pl)
+            for ix in idxs:
+                N.pq_free_index(ix)
+        finally:
+            N.pq_ctx_set_tuning(eng.ctx)
