@@ -1670,72 +1670,6 @@ __device__ __forceinline__ uint32_t bitmap_bits(const uint32_t* v, int64_t r, in
   return n < 32 ? b & ((1u << n) - 1u) : b;
 }
 
-// 16 bytes starting at byte s (0..15) of the 32-byte pair (A, B); the word
-// offset s >> 2 is warp-uniform, so the switch does not diverge.
-__device__ __forceinline__ uint4 shift_pair(const uint4& A, const uint4& B, uint32_t s) {
-  const uint32_t bs = (s & 3) * 8;
-  uint32_t w0, w1, w2, w3, w4;
-  switch (s >> 2) {
-    case 0: w0 = A.x; w1 = A.y; w2 = A.z; w3 = A.w; w4 = B.x; break;
-    case 1: w0 = A.y; w1 = A.z; w2 = A.w; w3 = B.x; w4 = B.y; break;
-    case 2: w0 = A.z; w1 = A.w; w2 = B.x; w3 = B.y; w4 = B.z; break;
-    default: w0 = A.w; w1 = B.x; w2 = B.y; w3 = B.z; w4 = B.w; break;
-  }
-  return make_uint4(__funnelshift_r(w0, w1, bs), __funnelshift_r(w1, w2, bs), __funnelshift_r(w2, w3, bs),
-                    __funnelshift_r(w3, w4, bs));
-}
-
-// One warp copies `bytes` bytes from `src` (any alignment) to `dst` (aligned
-// to the value width): bytes up to dst's 16-byte boundary one by one, then
-// 16-byte stores built from aligned 16-byte loads (8 per lane in flight; the
-// next aligned word comes from the neighbouring lane by a shuffle), then the
-// tail.  Reads may reach 16 bytes past src + bytes.
-__device__ __forceinline__ uint4 shfl_u4(const uint4& v, int src_lane) {
-  return make_uint4(__shfl_sync(0xffffffffu, v.x, src_lane), __shfl_sync(0xffffffffu, v.y, src_lane),
-                    __shfl_sync(0xffffffffu, v.z, src_lane), __shfl_sync(0xffffffffu, v.w, src_lane));
-}
-__device__ __forceinline__ uint4 shfl_down_u4(const uint4& v) {
-  return make_uint4(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1),
-                    __shfl_down_sync(0xffffffffu, v.z, 1), __shfl_down_sync(0xffffffffu, v.w, 1));
-}
-
-__device__ __forceinline__ void warp_copy(uint8_t* dst, const uint8_t* src, uint64_t bytes, int lane) {
-  const uint32_t head0 = static_cast<uint32_t>((16 - (reinterpret_cast<uintptr_t>(dst) & 15)) & 15);
-  const uint32_t head = head0 < bytes ? head0 : static_cast<uint32_t>(bytes);
-  if (static_cast<uint32_t>(lane) < head) dst[lane] = __ldg(src + lane);
-  dst += head;
-  src += head;
-  bytes -= head;
-  const uint64_t nvec = bytes >> 4;
-  const uint32_t s = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 15);
-  const uint4* sa = reinterpret_cast<const uint4*>(src - s);
-  uint4* dv = reinterpret_cast<uint4*>(dst);
-  constexpr int U = 8;
-  for (uint64_t v0 = 0; v0 < nvec; v0 += 32 * U) {
-    uint4 A[U];
-    uint4 X = make_uint4(0, 0, 0, 0);
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t i = v0 + u * 32 + lane;
-      A[u] = i <= nvec ? __ldg(sa + i) : make_uint4(0, 0, 0, 0);
-    }
-    if (s && lane == 0 && v0 + 32 * U <= nvec) X = __ldg(sa + v0 + 32 * U);
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t i = v0 + u * 32 + lane;
-      uint4 out = A[u];
-      if (s) {  // warp-uniform
-        const uint4 dn = shfl_down_u4(A[u]);
-        const uint4 nx = shfl_u4(u + 1 < U ? A[u + 1] : X, 0);
-        out = shift_pair(A[u], lane == 31 ? nx : dn, s);
-      }
-      if (i < nvec) dv[i] = out;
-    }
-  }
-  const uint32_t tail = static_cast<uint32_t>(bytes & 15);
-  if (static_cast<uint32_t>(lane) < tail) dst[(nvec << 4) + lane] = __ldg(src + (nvec << 4) + lane);
-}
-
 // Columns whose pages are all REQUIRED PLAIN fixed-width: every item is a
 // straight copy of nrows * width bytes, handed out through the column's
 // counter.

@@ -12,34 +12,22 @@
 // Lane 0 parses a batch of up to 32 element headers (the tag stream is
 // serial) into a per-warp shared-memory slot; then the warp executes the
 // batch in order, all 32 lanes copying the bytes of one element at a time.
-// Long literals and non-overlapping copies move 16-byte vectors when source
-// and destination share their 16-byte phase.
+// Long literals and non-overlapping copies move 16-byte vectors (aligned
+// loads funnel-shifted to the destination's alignment); copies out of the
+// output use coherent loads, since other lanes wrote those bytes.
 #include "dev_util.cuh"
 #include "snappy_job.h"
 
 namespace pqi {
 
-__device__ __forceinline__ void warp_copy_bytes(uint8_t* d, const uint8_t* s, uint32_t n, int lane) {
-  uintptr_t da = reinterpret_cast<uintptr_t>(d), sa = reinterpret_cast<uintptr_t>(s);
-  if (n >= 256 && ((da ^ sa) & 15) == 0) {
-    uint32_t head = static_cast<uint32_t>((16 - (da & 15)) & 15);
-    if (lane < static_cast<int>(head)) d[lane] = s[lane];
-    uint32_t nv = (n - head) >> 4;
-    const uint4* sv = reinterpret_cast<const uint4*>(s + head);
-    uint4* dv = reinterpret_cast<uint4*>(d + head);
-    for (uint32_t i = lane; i < nv; i += 32) dv[i] = sv[i];
-    for (uint32_t i = head + (nv << 4) + lane; i < n; i += 32) d[i] = s[i];
-    return;
-  }
-  for (uint32_t i = lane; i < n; i += 32) d[i] = s[i];
-}
-
 constexpr int kSnappyWarps = 4;  // warps per block
+constexpr uint32_t kRing = 8192;  // recent output kept in shared memory per warp (power of two)
 
 __global__ void __launch_bounds__(32 * kSnappyWarps) k_snappy(const SnappyJob* __restrict__ jobs, int n_jobs,
                                                               DevStatus* st) {
   __shared__ uint32_t s_kind_len[kSnappyWarps][32];
   __shared__ uint32_t s_arg[kSnappyWarps][32];
+  __shared__ uint8_t s_ring[kSnappyWarps][kRing];
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -50,13 +38,13 @@ __global__ void __launch_bounds__(32 * kSnappyWarps) k_snappy(const SnappyJob* _
       if (lane == 0) report(st, DERR_CORRUPT, jb.page, WHERE_SNAPPY, 1);
       continue;
     }
-    warp_copy_bytes(jb.dst, jb.src, jb.prefix, lane);  // V2 level bytes, never compressed
+    warp_copy<true>(jb.dst, jb.src, jb.prefix, lane);  // V2 level bytes, never compressed
     if (jb.raw) {
       if (jb.src_len != jb.dst_len) {
         if (lane == 0) report(st, DERR_CORRUPT, jb.page, WHERE_SNAPPY, 2);
         continue;
       }
-      warp_copy_bytes(jb.dst + jb.prefix, jb.src + jb.prefix, jb.src_len - jb.prefix, lane);
+      warp_copy<true>(jb.dst + jb.prefix, jb.src + jb.prefix, jb.src_len - jb.prefix, lane);
       __syncwarp();
       continue;
     }
@@ -125,19 +113,88 @@ __global__ void __launch_bounds__(32 * kSnappyWarps) k_snappy(const SnappyJob* _
       n_el = __shfl_sync(0xffffffffu, n_el, 0);
       bad = __shfl_sync(0xffffffffu, bad, 0);
       ip = __shfl_sync(0xffffffffu, ip, 0);
-      for (int e = 0; e < n_el; ++e) {
-        uint32_t kl = s_kind_len[w][e];
-        uint32_t kind = kl & 3, len = kl >> 2, arg = s_arg[w][e];
+      // Execute the batch.  Every output byte also goes to the warp's ring
+      // of recent output in shared memory, so that back-references into the
+      // last kRing bytes read shared memory instead of waiting on L2 for
+      // bytes the warp has just stored.  Pass 1, in parallel: literals and
+      // copies whose source lies wholly before the batch's first output
+      // byte; short ones one lane each, long literals by the whole warp.
+      // Pass 2, in order: copies that read output of this batch (or overlap
+      // themselves).
+      uint8_t* ring = s_ring[w];
+      constexpr uint32_t RM = kRing - 1;
+      uint32_t kl = 0, arg = 0;
+      if (lane < n_el) {
+        kl = s_kind_len[w][lane];
+        arg = s_arg[w][lane];
+      }
+      const uint32_t kind = kl & 3, len = kl >> 2;
+      uint32_t incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t o0 = op + incl - len;  // this lane's element output offset
+      const uint32_t bend = op + __shfl_sync(0xffffffffu, incl, 31);
+      // ring slots hold positions [ring_lo, bend) after this batch; writes of
+      // positions below ring_lo are skipped (each slot has one writer) and
+      // reads below it go to global memory
+      const uint32_t ring_lo = bend > kRing ? bend - kRing : 0u;
+      auto src_byte = [&](uint32_t pos, uint32_t first) -> uint8_t {
+        return first >= ring_lo ? ring[pos & RM] : ld_src<false>(out + pos);
+      };
+      const bool valid = lane < n_el;
+      const bool indep = valid && (kind == 0 || (arg >= len && o0 - arg + len <= op));
+      const bool small = kind != 0 || len <= 32;
+      if (indep && small) {
         if (kind == 0) {
-          warp_copy_bytes(out + op, in + arg, len, lane);
-        } else if (arg >= len) {
-          warp_copy_bytes(out + op, out + op - arg, len, lane);
+          for (uint32_t i = 0; i < len; ++i) {
+            const uint8_t b = __ldg(in + arg + i);
+            out[o0 + i] = b;
+            if (o0 + i >= ring_lo) ring[(o0 + i) & RM] = b;
+          }
         } else {
-          for (uint32_t i = lane; i < len; i += 32) out[op + i] = out[op - arg + (i % arg)];
+          const uint32_t first = o0 - arg;
+          for (uint32_t i = 0; i < len; ++i) {
+            const uint8_t b = src_byte(first + i, first);
+            out[o0 + i] = b;
+            if (o0 + i >= ring_lo) ring[(o0 + i) & RM] = b;
+          }
         }
-        op += len;
+      }
+      for (uint32_t m = __ballot_sync(0xffffffffu, indep && !small); m; m &= m - 1) {
+        const int e = __ffs(m) - 1;
+        const uint32_t el = __shfl_sync(0xffffffffu, len, e);
+        const uint32_t ea = __shfl_sync(0xffffffffu, arg, e), eo = __shfl_sync(0xffffffffu, o0, e);
+        if (el > 512) {
+          warp_copy<true>(out + eo, in + ea, el, lane);
+          for (uint32_t i = (eo >= ring_lo ? 0u : ring_lo - eo) + lane; i < el; i += 32)
+            ring[(eo + i) & RM] = __ldg(in + ea + i);
+        } else {
+          for (uint32_t i = lane; i < el; i += 32) {
+            const uint8_t b = __ldg(in + ea + i);
+            out[eo + i] = b;
+            if (eo + i >= ring_lo) ring[(eo + i) & RM] = b;
+          }
+        }
+      }
+      __syncwarp();
+      for (uint32_t m = __ballot_sync(0xffffffffu, valid && !indep); m; m &= m - 1) {
+        const int e = __ffs(m) - 1;
+        const uint32_t el = __shfl_sync(0xffffffffu, len, e);
+        const uint32_t ea = __shfl_sync(0xffffffffu, arg, e), eo = __shfl_sync(0xffffffffu, o0, e);
+        const uint32_t first = eo - ea;
+        for (uint32_t i = lane; i < el; i += 32) {
+          const uint32_t pos = ea >= el ? first + i : first + (i % ea);
+          const uint8_t b = src_byte(pos, first);
+          out[eo + i] = b;
+          if (eo + i >= ring_lo) ring[(eo + i) & RM] = b;
+        }
         __syncwarp();
       }
+      op += __shfl_sync(0xffffffffu, incl, 31);
+      __syncwarp();
     }
     if (lane == 0 && (bad || op != out_len || ip != in_len)) report(st, DERR_CORRUPT, jb.page, WHERE_SNAPPY, 4);
     __syncwarp();
