@@ -20,6 +20,17 @@ struct DictJob {
   int32_t chunk;        // DictDev row
   uint8_t* values;      // fixed width: n * width bytes (16-byte aligned)
   uint64_t* str_ent;    // BYTE_ARRAY: n entries, (chars offset << 32) | length
+  uint32_t sreg;        // BYTE_ARRAY: first row of the job's chain-region tables
+  int32_t sreg_cap;     // BYTE_ARRAY: region rows reserved (body_len / STR_REGION + 2)
+};
+
+// Chain regions of PLAIN BYTE_ARRAY dictionary pages: (4-byte length, bytes)
+// entries are found per STR_REGION bytes in parallel, then stitched.
+constexpr int STR_REGION = 16384;
+constexpr int STR_REGION_LIST = STR_REGION / 4 + 2;  // entries are >= 4 bytes
+struct DictScratch {
+  DeltaRegion* regs;    // one summary per region
+  uint32_t* lists;      // STR_REGION_LIST entry offsets per region
 };
 
 struct DecodeArgs {
@@ -43,8 +54,8 @@ struct DecodeArgs {
   int n_delta;
 };
 
-void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, DictDev* dicts, int n_sms,
-                 DevStatus* st, cudaStream_t s);
+void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, int max_str_regions, DictScratch ds,
+                 DictDev* dicts, int n_sms, DevStatus* st, cudaStream_t s);
 // Launches over sub-ranges (one output column's share of the plan).
 void launch_walk(const DecodeArgs& a, int wbegin, int n, cudaStream_t s);
 void launch_delta_bases(const DecodeArgs& a, int dbegin, int n, int max_regions, cudaStream_t s);

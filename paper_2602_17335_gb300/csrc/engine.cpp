@@ -726,6 +726,12 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
           dj.chunk = static_cast<int32_t>(ch);
           dj.values = idx->dict_values[ch];
           dj.str_ent = idx->dict_str_ent[ch];
+          if (cd.ptype == pqi::T_BYTE_ARRAY) {
+            dj.sreg = static_cast<uint32_t>(plan->dict_regions);
+            dj.sreg_cap = static_cast<int32_t>(dp.uncompressed / pqi::STR_REGION + 2);
+            plan->dict_regions += static_cast<uint64_t>(dj.sreg_cap);
+            cw.max_str_regions = std::max(cw.max_str_regions, dj.sreg_cap);
+          }
           if (cd.ptype != pqi::T_BYTE_ARRAY)
             plan->max_fixed_dict_bytes =
                 std::max<int>(plan->max_fixed_dict_bytes, dp.num_values * cd.width);
@@ -857,6 +863,8 @@ pq_status plan_upload(pq_plan* plan) {
   plan->d_dbase = plan_alloc(int64_t, plan, plan->delta_blocks);
   plan->d_dregs = plan_alloc(pqi::DeltaRegion, plan, plan->delta_regions);
   plan->d_dreg_lists = plan_alloc(uint32_t, plan, plan->delta_regions * pqi::DELTA_REGION_LIST);
+  plan->d_sregs = plan_alloc(pqi::DeltaRegion, plan, plan->dict_regions);
+  plan->d_slists = plan_alloc(uint32_t, plan, plan->dict_regions * pqi::STR_REGION_LIST);
   plan->d_pps = plan_alloc(pqi::PlanPage, plan, npp);
   plan->d_items = plan_alloc(pqi::Item, plan, nit);
   plan->d_cols = plan_alloc(pqi::OutCol, plan, plan->outcols.size());
@@ -969,7 +977,8 @@ uint64_t plan_device_bytes(const pq_plan* plan, uint64_t scratch) {
          (plan->snappy_data.size() + plan->snappy_dict.size()) * sizeof(pqi::SnappyJob) +
          plan->dict_jobs.size() * sizeof(pqi::DictJob) + 4 * (plan->walk_pps.size() + plan->delta_pps.size()) +
          plan->delta_blocks * 12 +
-         plan->delta_regions * (sizeof(pqi::DeltaRegion) + 4ull * pqi::DELTA_REGION_LIST) + scratch + 64 +
+         plan->delta_regions * (sizeof(pqi::DeltaRegion) + 4ull * pqi::DELTA_REGION_LIST) +
+         plan->dict_regions * (sizeof(pqi::DeltaRegion) + 4ull * pqi::STR_REGION_LIST) + scratch + 64 +
          str_rows * 4 + (plan->str_cols.empty() ? 0 : nit * 8) + 4096;
 }
 
@@ -1037,6 +1046,12 @@ pq_status pq_plan_stage_ms(const pq_plan* plan, float* ms) {
 
 // ------------------------------------------------------------------ scan
 
+static int max_str_regions_all(const pq_plan* plan) {
+  int m = 0;
+  for (const auto& cw : plan->colwork) m = std::max(m, cw.max_str_regions);
+  return m;
+}
+
 // Kernels of one output column, in order, on one stream.
 static void enqueue_column(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, bool with_dicts, cudaStream_t s) {
   pq_ctx* ctx = plan->ctx;
@@ -1045,8 +1060,8 @@ static void enqueue_column(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, b
   if (with_dicts && cw.snap_dict_n)
     pqi::launch_snappy(plan->d_snappy + n_data_total + cw.snap_dict_begin, cw.snap_dict_n, ctx->n_sms, a.st, s);
   if (with_dicts && cw.dict_n)
-    pqi::launch_dict(plan->d_dict_jobs + cw.dict_begin, cw.dict_n, cw.max_fixed_dict, plan->idx->d_dicts, ctx->n_sms,
-                     a.st, s);
+    pqi::launch_dict(plan->d_dict_jobs + cw.dict_begin, cw.dict_n, cw.max_fixed_dict, cw.max_str_regions,
+                     pqi::DictScratch{plan->d_sregs, plan->d_slists}, plan->idx->d_dicts, ctx->n_sms, a.st, s);
   if (cw.snap_data_n) pqi::launch_snappy(plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, ctx->n_sms, a.st, s);
   pqi::launch_walk(a, cw.walk_begin, cw.walk_n, s);
   pqi::launch_delta_bases(a, cw.delta_begin, cw.delta_n, cw.max_regions, s);
@@ -1087,7 +1102,8 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
     mark(2);
     if (with_dicts && !plan->dict_jobs.empty())
       pqi::launch_dict(plan->d_dict_jobs, static_cast<int>(plan->dict_jobs.size()), plan->max_fixed_dict_bytes,
-                       plan->idx->d_dicts, ctx->n_sms, a.st, s);
+                       max_str_regions_all(plan), pqi::DictScratch{plan->d_sregs, plan->d_slists}, plan->idx->d_dicts,
+                       ctx->n_sms, a.st, s);
     mark(3);
     size_t job = 0;
     for (size_t k = 0; k < plan->chunk_pp.size(); ++k) {
@@ -1115,8 +1131,8 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
     for (int oc = 0; oc < ncols; ++oc) {
       const auto& cw = plan->colwork[oc];
       if (with_dicts && cw.dict_n)
-        pqi::launch_dict(plan->d_dict_jobs + cw.dict_begin, cw.dict_n, cw.max_fixed_dict, plan->idx->d_dicts,
-                         ctx->n_sms, a.st, s);
+        pqi::launch_dict(plan->d_dict_jobs + cw.dict_begin, cw.dict_n, cw.max_fixed_dict, cw.max_str_regions,
+                         pqi::DictScratch{plan->d_sregs, plan->d_slists}, plan->idx->d_dicts, ctx->n_sms, a.st, s);
     }
     mark(3);
     for (int oc = 0; oc < ncols; ++oc) {

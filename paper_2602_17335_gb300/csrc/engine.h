@@ -106,6 +106,7 @@ struct pq_plan {
   std::vector<uint32_t> delta_pps;           // DELTA plan pages
   uint64_t delta_blocks = 0;                 // capacity of the DELTA block tables
   uint64_t delta_regions = 0;                // capacity of the DELTA region tables
+  uint64_t dict_regions = 0;                 // capacity of the string-dictionary region tables
   // per chunk: range of plan pages (plain baseline launches per chunk)
   std::vector<std::pair<int32_t, int32_t>> chunk_pp;  // (first pp, count)
   std::vector<int32_t> chunk_pp_chunk;
@@ -133,6 +134,8 @@ struct pq_plan {
   int64_t* d_dbase = nullptr;
   pqi::DeltaRegion* d_dregs = nullptr;
   uint32_t* d_dreg_lists = nullptr;
+  pqi::DeltaRegion* d_sregs = nullptr;
+  uint32_t* d_slists = nullptr;
   pqi::DevStatus* d_status = nullptr;
   std::vector<void*> owned;                  // pool blocks to release
   // host staging (pinned): output descriptors in, status + string totals out
@@ -153,6 +156,7 @@ struct pq_plan {
     int walk_begin = 0, walk_n = 0;            // into walk_pps
     int delta_begin = 0, delta_n = 0;          // into delta_pps
     int max_regions = 0;                       // most DELTA regions of one page
+    int max_str_regions = 0;                   // most chain regions of one string dictionary
     bool copy_only = false;                    // every page REQUIRED PLAIN fixed-width
   };
   std::vector<ColWork> colwork;

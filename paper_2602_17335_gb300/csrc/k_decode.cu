@@ -253,82 +253,243 @@ __device__ __forceinline__ int uleb_p(const uint8_t* q, uint64_t* v) {
 
 // ------------------------------------------------------------------ string dictionaries
 
-struct DictStrSmem {
-  uint64_t bar[2];
-  alignas(16) uint8_t win[2][CWIN + 16];
-};
+// BYTE_ARRAY dictionary pages: entries are (4-byte little-endian length,
+// bytes) back to back, so the entry starts form a chain.  The chain is found
+// per STR_REGION bytes in parallel: region i > 0 searches a lead-in before
+// its first byte for an offset where four consecutive entries are plausible
+// (a length that fits in the page), a look-alike start usually rejoins the
+// true chain within an entry or two, and k_sfix stitches the regions,
+// walking serially only where a region's start was wrong.
+constexpr int SREG_LEAD = 1024;
+constexpr int SREG_SMEM = SREG_LEAD + STR_REGION + 64;
 
-// BYTE_ARRAY dictionary: entries are (4-byte length, bytes) back to back; the
-// chain over them is followed by one thread through the double window.
-__global__ void __launch_bounds__(32) k_dict_str(const DictJob* __restrict__ jobs, DictDev* dicts, DevStatus* st) {
-  extern __shared__ __align__(16) uint8_t smraw[];
-  DictStrSmem& sm = *reinterpret_cast<DictStrSmem*>(smraw);
-  const DictJob j = jobs[blockIdx.x];
-  if (j.ptype != T_BYTE_ARRAY || threadIdx.x != 0) return;
-  mbar_init(&sm.bar[0], 1);
-  mbar_init(&sm.bar[1], 1);
-  fence_mbar_init();
-  Chain c;
-  ch_init(c, sm.win[0], sm.win[1], &sm.bar[0], &sm.bar[1], 0, 0);
-  const uint32_t blen = static_cast<uint32_t>(j.body_len);
-  if (!ch_start(c, j.body, blen)) {
-    report(st, DERR_TIMEOUT, j.page, WHERE_DICT, 3);
-    ch_drain(c);
-    return;
-  }
-  uint32_t pos = 0, maxlen = 0;
-  bool bad = false;
-  for (int32_t k = 0; k < j.n;) {
-    if (pos + 4 > blen) { bad = true; break; }
-    if (!ch_ensure(c, pos, 16)) { bad = true; break; }
-    // steps inside the current window: the length word, then the next entry
-    uint32_t o = static_cast<uint32_t>(pos - c.w0);
-    const uint32_t lim = c.n0 - 16;
-    const uint32_t wb = static_cast<uint32_t>(c.w0);
-    const uint32_t* w32 = reinterpret_cast<const uint32_t*>(c.b0);
-    // software-pipelined: the next length word is loaded before this
-    // entry is checked and stored
-    uint32_t x0 = w32[o >> 2], x1 = w32[(o >> 2) + 1];
-    do {
-      const uint32_t sh = (o & 3u) << 3;
-      const uint32_t len = __funnelshift_r(x0, x1, sh);
-      const uint32_t on = o + 4 + len;
-      if (on <= lim) {
-        x0 = w32[on >> 2];
-        x1 = w32[(on >> 2) + 1];
-      }
-      const uint32_t p = o + wb;
-      if (p + 4 > blen || len > blen - p - 4) { bad = true; break; }
-      j.str_ent[k] = (static_cast<uint64_t>(p + 4) << 32) | len;
-      maxlen = len > maxlen ? len : maxlen;
-      o = on;
-      ++k;
-    } while (k < j.n && o <= lim);
-    if (bad) break;
-    pos = o + wb;
-  }
-  ch_drain(c);
-  if (bad) {
-    report(st, DERR_CORRUPT, j.page, WHERE_DICT, 2);
-    return;
-  }
-  DictDev d{};
-  d.str_ent = j.str_ent;
-  d.chars = j.body;
-  d.n = j.n;
-  d.max_len = static_cast<int32_t>(maxlen);
-  d.valid = 1;
-  dicts[j.chunk] = d;
+__device__ __forceinline__ uint32_t sle32(const uint8_t* b, uint32_t o) {
+  return static_cast<uint32_t>(b[o]) | (static_cast<uint32_t>(b[o + 1]) << 8) |
+         (static_cast<uint32_t>(b[o + 2]) << 16) | (static_cast<uint32_t>(b[o + 3]) << 24);
 }
 
-void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, DictDev* dicts, int n_sms, DevStatus* st,
-                 cudaStream_t s) {
+__global__ void __launch_bounds__(32) k_sreg(const DictJob* __restrict__ jobs, DictScratch ds, DevStatus* st) {
+  extern __shared__ __align__(16) uint8_t smraw[];
+  __shared__ uint64_t bar;
+  const int lane = threadIdx.x;
+  const DictJob j = jobs[blockIdx.y];
+  if (j.ptype != T_BYTE_ARRAY || static_cast<int>(blockIdx.x) >= j.sreg_cap) return;
+  const int i = blockIdx.x;
+  const uint32_t blen = static_cast<uint32_t>(j.body_len);
+  DeltaRegion* R = ds.regs + j.sreg + i;
+  uint32_t* list = ds.lists + static_cast<uint64_t>(j.sreg + i) * STR_REGION_LIST;
+  const uint64_t start64 = static_cast<uint64_t>(i) * STR_REGION;
+  if (start64 >= blen) {
+    if (lane == 0) *R = DeltaRegion{-1, -1, 0, 0};
+    return;
+  }
+  const uint32_t start = static_cast<uint32_t>(start64);
+  const uint32_t end = blen - start < static_cast<uint32_t>(STR_REGION) ? blen : start + STR_REGION;
+  const uint32_t sstart = i == 0 ? 0u : start - SREG_LEAD;
+  // stage [sstart, end + 8), 16-byte aligned; at most 16 bytes past the body
+  const uint8_t* g = j.body + sstart;
+  const uint8_t* ga = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(g) & ~uintptr_t(15));
+  const uint32_t shift = static_cast<uint32_t>(g - ga);
+  const uint64_t lim_end = end + 8 < blen ? end + 8 : blen;
+  uint32_t bytes = static_cast<uint32_t>(((j.body + lim_end) - ga + 16) & ~int64_t(15));
+  if (bytes > static_cast<uint32_t>(SREG_SMEM)) bytes = SREG_SMEM;
+  if (lane == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bar, bytes);
+    bulk_g2s(smraw, ga, bytes, &bar);
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(&bar, 0);
+  if (!__all_sync(0xffffffffu, ok)) {
+    if (lane == 0) {
+      report(st, DERR_TIMEOUT, j.page, WHERE_DICT, 30);
+      mbar_wait(&bar, 0);
+      *R = DeltaRegion{-1, -1, 0, 0};
+    }
+    return;
+  }
+  const uint32_t known_end = sstart - shift + bytes > blen ? blen : sstart - shift + bytes;
+  auto at = [&](uint32_t s) -> uint32_t { return s - sstart + shift; };
+  // next entry start after the entry at p: 0 when implausible, 0xffffffff when not decidable
+  auto next = [&](uint32_t p) -> uint32_t {
+    if (p + 4 > known_end) return 0xffffffffu;
+    const uint32_t L = sle32(smraw, at(p));
+    if (L > blen - p - 4) return 0u;
+    return p + 4 + L;
+  };
+  uint32_t q = 0xffffffffu;
+  if (i == 0) {
+    q = 0;
+  } else {
+    for (uint32_t c0 = sstart; c0 < end && q == 0xffffffffu; c0 += 32) {
+      const uint32_t cand = c0 + lane;
+      bool good = cand < end;
+      uint32_t p = cand;
+      for (int k = 0; good && k < 4 && p < blen; ++k) {
+        const uint32_t nx = next(p);
+        if (nx == 0u) good = false;
+        else if (nx == 0xffffffffu) break;
+        else p = nx;
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, good);
+      if (m) q = c0 + __ffs(m) - 1;
+    }
+  }
+  if (lane == 0) {
+    int32_t first = -1, cnt = 0, x = -1;
+    if (q != 0xffffffffu) {
+      uint32_t p = q;
+      while (true) {
+        if (p >= end) {
+          x = static_cast<int32_t>(p);
+          break;
+        }
+        if (p >= start) {
+          if (cnt == STR_REGION_LIST) break;
+          if (first < 0) first = static_cast<int32_t>(p);
+          list[cnt++] = p;
+        }
+        const uint32_t nx = next(p);
+        if (nx == 0u || nx == 0xffffffffu) break;  // a look-alike chain
+        p = nx;
+      }
+    }
+    *R = DeltaRegion{first, first >= 0 ? x : -1, cnt, 0};
+  }
+}
+
+// Per BYTE_ARRAY dictionary page: stitch the regions (as k_dfix does for
+// DELTA blocks), then write every entry as (chars offset << 32) | length.
+// A region whose found start is not the true entry is walked again from the
+// true entry, in shared memory (the region is staged by one bulk copy), its
+// entries written directly.
+__global__ void __launch_bounds__(256) k_sfix(const DictJob* __restrict__ jobs, DictScratch ds, DictDev* dicts,
+                                              DevStatus* st) {
+  constexpr int MAXR = 512;
+  __shared__ int32_t s_q[MAXR], s_x[MAXR], s_c[MAXR];
+  __shared__ int32_t s_skip[MAXR], s_base[MAXR];
+  __shared__ int32_t s_nreg, s_ok;
+  __shared__ uint64_t s_bar;
+  __shared__ __align__(16) uint8_t s_stage[STR_REGION + 64];
+  const DictJob j = jobs[blockIdx.x];
+  if (j.ptype != T_BYTE_ARRAY) return;
+  const uint32_t blen = static_cast<uint32_t>(j.body_len);
+  const int32_t n = j.n;
+  const int nreg = static_cast<int>((static_cast<uint64_t>(blen) + STR_REGION - 1) / STR_REGION);
+  const bool regions = nreg <= j.sreg_cap && nreg <= MAXR;
+  if (regions)
+    for (int i = threadIdx.x; i < nreg; i += blockDim.x) {
+      const DeltaRegion r = ds.regs[j.sreg + i];
+      s_q[i] = r.q;
+      s_x[i] = r.x;
+      s_c[i] = r.cnt;
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    fence_mbar_init();
+    uint32_t parity = 0;
+    bool bad = false;
+    uint32_t e = 0;
+    int32_t b = 0;
+    if (!regions) {
+      // pages too large for the region tables: one serial walk in global memory
+      while (e < blen && b < n) {
+        if (e + 4 > blen) { bad = true; break; }
+        const uint32_t L = ld_le32_g(j.body + e);
+        if (L > blen - e - 4) { bad = true; break; }
+        j.str_ent[b++] = (static_cast<uint64_t>(e + 4) << 32) | L;
+        e += 4 + L;
+      }
+      s_nreg = 0;
+    } else {
+      for (int i = 0; i < nreg; ++i) {
+        const uint32_t start = static_cast<uint32_t>(i) * STR_REGION;
+        const uint32_t end = blen - start < static_cast<uint32_t>(STR_REGION) ? blen : start + STR_REGION;
+        s_skip[i] = -1;
+        if (b >= n || e >= end || bad) continue;
+        if (s_q[i] >= 0 && s_c[i] > 0 && s_x[i] >= 0 && static_cast<uint32_t>(s_q[i]) == e) {
+          const int32_t c = s_c[i] < n - b ? s_c[i] : n - b;
+          s_skip[i] = c;  // entries taken from the list
+          s_base[i] = b;
+          b += c;
+          e = static_cast<uint32_t>(s_x[i]);
+          continue;
+        }
+        // stage [e, end + 8) (at most STR_REGION + 24 bytes: e >= start)
+        const uint8_t* g = j.body + e;
+        const uint8_t* ga = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(g) & ~uintptr_t(15));
+        const uint32_t shift = static_cast<uint32_t>(g - ga);
+        const uint64_t lim = end + 8 < blen ? end + 8 : blen;
+        uint32_t bytes = static_cast<uint32_t>(((j.body + lim) - ga + 16) & ~int64_t(15));
+        if (bytes > sizeof(s_stage)) bytes = sizeof(s_stage);
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&s_bar, bytes);
+        bulk_g2s(s_stage, ga, bytes, &s_bar);
+        if (!mbar_wait(&s_bar, parity)) {
+          report(st, DERR_TIMEOUT, j.page, WHERE_DICT, 31);
+          mbar_wait(&s_bar, parity);
+          bad = true;
+          continue;
+        }
+        parity ^= 1u;
+        const uint32_t e0 = e;
+        const uint32_t known = e0 - shift + bytes > blen ? blen : e0 - shift + bytes;
+        while (e < end && b < n) {
+          if (e + 4 > known) { bad = true; break; }
+          const uint32_t L = sle32(s_stage, e - e0 + shift);
+          if (L > blen - e - 4) { bad = true; break; }
+          j.str_ent[b++] = (static_cast<uint64_t>(e + 4) << 32) | L;
+          e += 4 + L;
+        }
+      }
+      s_nreg = nreg;
+    }
+    s_ok = !bad && b == n && (n == 0 || e == blen);
+  }
+  __syncthreads();
+  if (!s_ok) {
+    if (threadIdx.x == 0) report(st, DERR_CORRUPT, j.page, WHERE_DICT, 2);
+    return;
+  }
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x >> 5; i < s_nreg; i += nw) {
+    if (s_skip[i] <= 0) continue;
+    const uint32_t* list = ds.lists + static_cast<uint64_t>(j.sreg + i) * STR_REGION_LIST;
+    for (int k = lane; k < s_skip[i]; k += 32) {
+      const uint32_t p = list[k];
+      j.str_ent[s_base[i] + k] = (static_cast<uint64_t>(p + 4) << 32) | ld_le32_g(j.body + p);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DictDev d{};
+    d.str_ent = j.str_ent;
+    d.chars = j.body;
+    d.n = n;
+    d.valid = 1;
+    dicts[j.chunk] = d;
+  }
+}
+
+void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, int max_str_regions, DictScratch ds,
+                 DictDev* dicts, int n_sms, DevStatus* st, cudaStream_t s) {
   if (n_jobs <= 0) return;
   int gx = (max_fixed_bytes / 4 + 256 * 16 - 1) / (256 * 16);
   if (gx < 1) gx = 1;
   if (gx > 4 * n_sms) gx = 4 * n_sms;
   k_dict_fixed<<<dim3(gx, n_jobs), 256, 0, s>>>(jobs, dicts, st);
-  k_dict_str<<<n_jobs, 32, sizeof(DictStrSmem), s>>>(jobs, dicts, st);
+  if (max_str_regions > 0) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_sreg, cudaFuncAttributeMaxDynamicSharedMemorySize, SREG_SMEM);
+      attr = true;
+    }
+    k_sreg<<<dim3(max_str_regions, n_jobs), 32, SREG_SMEM, s>>>(jobs, ds, st);
+    k_sfix<<<n_jobs, 256, 0, s>>>(jobs, ds, dicts, st);
+  }
 }
 
 // ------------------------------------------------------------------ walk
@@ -2247,7 +2408,6 @@ int walk_blocks_per_sm() {
   if (!g_walk_bps) {
     cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(WalkSmem));
     cudaFuncSetAttribute(k_plain_page, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(WalkSmem));
-    cudaFuncSetAttribute(k_dict_str, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(DictStrSmem));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_walk_bps, k_walk, WALK_THREADS, sizeof(WalkSmem));
     if (g_walk_bps < 1) g_walk_bps = 1;
   }
