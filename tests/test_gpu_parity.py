@@ -279,3 +279,33 @@ def test_batch_of_heterogeneous_chunks(eng, graph):
                 N.pq_free_index(ix)
         finally:
             N.pq_ctx_set_tuning(eng.ctx)
+
+
+def test_hybrid_run_chains_across_regions(eng):
+    """Level and dictionary-index streams long enough to span many 4 KB run
+    regions: nulls with probability 1/2 (short bit-packed runs), long null
+    and non-null stretches (long repeated runs), a nullable dictionary column,
+    indices of bit width 1 to 18, and a one-entry dictionary (bit width 0)."""
+    n = 1 << 20
+    rng = np.random.default_rng(7)
+    stretch = (np.arange(n) // 5000) % 3 != 0
+    coin = rng.random(n) < 0.5
+    cols = [
+        synth.ColumnData("opt_coin", "INT64", np.where(coin, rng.integers(-9, 9, n), 0).astype(np.int64), coin),
+        synth.ColumnData("opt_stretch", "INT32", np.where(stretch, np.arange(n) % 1000, 0).astype(np.int32), stretch),
+        synth.ColumnData("opt_dict", "INT32", np.where(coin, rng.integers(0, 300, n), 0).astype(np.int32), coin),
+        synth.ColumnData("dict_bw18", "INT32", rng.integers(0, 1 << 18, n).astype(np.int32)),
+        synth.ColumnData("dict_bw1", "INT64", rng.integers(0, 2, n).astype(np.int64)),
+        synth.ColumnData("dict_one", "INT32", np.full(n, 42, np.int32)),
+    ]
+    encs = ["PLAIN", "PLAIN", "RLE_DICTIONARY", "RLE_DICTIONARY", "RLE_DICTIONARY", "RLE_DICTIONARY"]
+    for policy in ("default", "mixed"):
+        cs = [synth.ColumnSpec(e) for e in encs]
+        for c in cs:
+            c.hybrid_policy = policy
+        spec = synth.TableSpec(n, 8 << 20, cs)
+        _roundtrip(eng, W.write_file(synth.Table(cols), spec))
+    # row ranges that start and end inside runs
+    spec = synth.TableSpec(n, 8 << 20, [synth.ColumnSpec(e) for e in encs])
+    data = W.write_file(synth.Table(cols), spec)
+    _roundtrip(eng, data, row_begin=12_345, row_count=700_001)

@@ -107,15 +107,34 @@ def test_serving_alone_and_in_mix(setup):
         N.pq_serve_destroy(srv)
 
 
+def _one_request_budget(N, e, idx, cols, rb, rc):
+    """The smallest power of two (bytes) that admits the request alone: at
+    least its device bytes and less than twice them."""
+    b = 1 << 16
+    while True:
+        srv = N.pq_serve_create(e.ctx, idx, budget_bytes=b, slots=1)
+        try:
+            st, t = N.pq_serve_submit(srv, cols, rb, rc)
+            if st == N.PQ_OK:
+                assert _wait(N, srv, t).status == N.PQ_OK
+                N.pq_serve_release(srv, t)
+                return b
+            assert st == N.PQ_ERR_BUDGET
+        finally:
+            N.pq_serve_destroy(srv)
+        b *= 2
+
+
 def test_serving_budget(setup):
     """A request larger than the whole budget is refused at submit; requests
-    that fit only one at a time still all finish (admission waits for
+    that fit about one at a time still all finish (admission waits for
     released outputs)."""
     from paper_2602_17335_gb300 import native as N
     e, idx, expect = setup
-    srv = N.pq_serve_create(e.ctx, idx, budget_bytes=400_000, slots=4)
+    one = _one_request_budget(N, e, idx, [2, 4], 0, 20_000)
+    srv = N.pq_serve_create(e.ctx, idx, budget_bytes=one + one // 4, slots=4)
     try:
-        st, _ = N.pq_serve_submit(srv, list(range(8)), 0, 10 * N_ROWS)
+        st, _ = N.pq_serve_submit(srv, list(range(8)), 0, 40 * N_ROWS)
         assert st == N.PQ_ERR_BUDGET
         tickets = []
         for k in range(6):
@@ -136,7 +155,8 @@ def test_serving_queue_timeout(setup):
     past its timeout and fails with PQ_ERR_TIMEOUT; the server keeps working."""
     from paper_2602_17335_gb300 import native as N
     e, idx, expect = setup
-    srv = N.pq_serve_create(e.ctx, idx, budget_bytes=250_000, slots=2, timeout_ms=50)
+    one = _one_request_budget(N, e, idx, [2], 0, 20_000)  # admits one such request, not two
+    srv = N.pq_serve_create(e.ctx, idx, budget_bytes=one, slots=2, timeout_ms=50)
     try:
         st, t1 = N.pq_serve_submit(srv, [2], 0, 20_000)
         assert st == N.PQ_OK
@@ -148,10 +168,10 @@ def test_serving_queue_timeout(setup):
         assert r2.status == N.PQ_ERR_TIMEOUT
         assert N.pq_serve_release(srv, t2) == N.PQ_OK
         assert N.pq_serve_release(srv, t1) == N.PQ_OK
-        st, t3 = N.pq_serve_submit(srv, [2], 5, 20_000)
+        st, t3 = N.pq_serve_submit(srv, [2], 0, 20_000)
         r3 = _wait(N, srv, t3)
         assert r3.status == N.PQ_OK
-        assert_columns_equal(server_result_outs(r3), _expected(expect, [2], 5, 20_000))
+        assert_columns_equal(server_result_outs(r3), _expected(expect, [2], 0, 20_000))
         N.pq_serve_release(srv, t3)
     finally:
         N.pq_serve_destroy(srv)
