@@ -253,6 +253,19 @@ void pq_free_index(pq_index* idx) {
   delete idx;
 }
 
+}  // extern "C"
+
+namespace pqe {
+// Frees an index whose device work has already completed (no device-wide sync).
+void index_release(pq_index* idx) {
+  if (!idx) return;
+  free_index_device(idx);
+  delete idx;
+}
+}  // namespace pqe
+
+extern "C" {
+
 static bool env_flag(const char* name) {
   const char* v = getenv(name);
   return v && *v && strcmp(v, "0") != 0;
@@ -315,6 +328,19 @@ pq_status pq_index_chunks(pq_ctx* ctx, const pq_file* files, int n_files, void* 
                   "file " + std::to_string(f) + ": " + err);
     idx->metas[f].footer_len = flen;
   }
+  return index_build(ctx, std::move(idx), !env_flag("PQ_NO_OFFSET_INDEX"), s, out);
+}
+
+}  // extern "C"
+
+namespace pqe {
+
+// Index from parsed footers: `idx` holds files (device base, size) and
+// metas; chunks at base + chunk offset.  allow_oi: page locations may be
+// read from OffsetIndex structures on the device.
+pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi, cudaStream_t s, pq_index** out) {
+  const int n_files = static_cast<int>(idx->files.size());
+  const pq_file* files = idx->files.data();
   // 2. schema
   idx->schema = idx->metas[0].columns;
   idx->n_columns = static_cast<int>(idx->schema.size());
@@ -333,7 +359,7 @@ pq_status pq_index_chunks(pq_ctx* ctx, const pq_file* files, int n_files, void* 
   }
   // 3. chunks
   int64_t row = 0;
-  bool all_oi = !env_flag("PQ_NO_OFFSET_INDEX");
+  bool all_oi = allow_oi;
   for (int f = 0; f < n_files; ++f) {
     const auto& m = idx->metas[f];
     const uint64_t fsize = files[f].size;
@@ -548,6 +574,10 @@ pq_status pq_index_chunks(pq_ctx* ctx, const pq_file* files, int n_files, void* 
   *out = idx.release();
   return PQ_OK;
 }
+
+}  // namespace pqe
+
+extern "C" {
 
 pq_status pq_index_get_info(const pq_index* idx, pq_index_info* out) {
   if (!idx || !out) return PQ_ERR_INVALID_ARG;

@@ -29,6 +29,8 @@
 //  strings expand records per row the dictionary index (or PLAIN value
 //         offset) and per-item chars totals; a scan makes item bases; the
 //         copy pass writes int64 offsets and the chars.
+#include <algorithm>
+
 #include "decode_job.h"
 #include "dev_util.cuh"
 
@@ -2289,6 +2291,18 @@ __global__ void k_prepare(DecodeArgs a, int n_cols) {
     if (col.str_item_bytes)
       for (uint64_t i = tid; i < col.item_count; i += nthr) col.str_item_bytes[col.item_begin + i] = 0;
   }
+}
+
+__global__ void k_add_offsets(int64_t* offs, int64_t n, int64_t base) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    offs[i] += base;
+}
+
+void launch_add_offsets(int64_t* offs, int64_t n, int64_t base, cudaStream_t s) {
+  if (n <= 0 || base == 0) return;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  k_add_offsets<<<static_cast<unsigned>(blocks), 256, 0, s>>>(offs, n, base);
 }
 
 void launch_prepare(const DecodeArgs& a, int n_cols, int grid, cudaStream_t s) {
