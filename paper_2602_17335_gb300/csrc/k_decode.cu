@@ -1558,7 +1558,12 @@ __device__ bool delta_block_sum(const uint8_t* sb, const PlanPage& pp, const uin
 }
 
 // Block sums of every DELTA page, spread over the whole GPU: blockIdx.y is
-// the page, warps stride over its blocks.  The sums land in dbase.
+// the page.  Blocks of the common layout (4 miniblocks) go four to a warp,
+// eight lanes per block and each lane 1/8 of the values, so that the loads
+// of four blocks are in flight together; other layouts take a warp per
+// block.  Every block is summed as a full block: only the page's last
+// block can be partial and the bases never use its sum.  The sums land in
+// dbase.
 __global__ void __launch_bounds__(256) k_delta_sums(DecodeArgs a, int dbegin) {
   const int lane = threadIdx.x & 31;
   const int p = static_cast<int>(a.delta_pps[dbegin + blockIdx.y]);
@@ -1570,13 +1575,51 @@ __global__ void __launch_bounds__(256) k_delta_sums(DecodeArgs a, int dbegin) {
   const int type_bits = a.chunks[pp.chunk].ptype == T_INT32 ? 32 : 64;
   const int w0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int nw = gridDim.x * (blockDim.x >> 5);
-  for (int b = w0; b < pp.dblocks; b += nw) {
-    uint64_t sum = 0;
-    if (!delta_block_sum(sb, pp, dpos, type_bits, b, lane, &sum)) {
-      if (lane == 0) report(a.st, DERR_CORRUPT, static_cast<int>(pp.page), WHERE_WALK_VALUES, 20);
-      sum = 0;
+  if (pp.dmbc != 4 || pp.dbs % 8) {
+    for (int b = w0; b < pp.dblocks; b += nw) {
+      uint64_t sum = 0;
+      if (!delta_block_sum(sb, pp, dpos, type_bits, b, lane, &sum)) {
+        if (lane == 0) report(a.st, DERR_CORRUPT, static_cast<int>(pp.page), WHERE_WALK_VALUES, 20);
+        sum = 0;
+      }
+      if (lane == 0) dsum[b] = static_cast<int64_t>(sum);
     }
-    if (lane == 0) dsum[b] = static_cast<int64_t>(sum);
+    return;
+  }
+  const int sub = lane >> 3, sl = lane & 7;
+  const int nv = pp.dbs, vpm = pp.dvpm;
+  for (int b0 = w0 * 4; b0 < pp.dblocks; b0 += nw * 4) {
+    const int b = b0 + sub;
+    const bool have = b < pp.dblocks;
+    uint64_t acc = 0;
+    bool bad = false;
+    // the last block's sum is never used (and its unused miniblock widths may be anything)
+    if (have && b + 1 < pp.dblocks) {
+      const uint32_t pos = dpos[b];
+      uint64_t z = 0;
+      const int vl = uleb([&](uint32_t q) { return static_cast<uint32_t>(__ldg(sb + pos + q)); }, 0, 10, &z);
+      const uint32_t wv[4] = {__ldg(sb + pos + vl), __ldg(sb + pos + vl + 1), __ldg(sb + pos + vl + 2),
+                              __ldg(sb + pos + vl + 3)};
+      bad = !vl || static_cast<int>(wv[0]) > type_bits || static_cast<int>(wv[1]) > type_bits ||
+            static_cast<int>(wv[2]) > type_bits || static_cast<int>(wv[3]) > type_bits;
+      if (!bad) {
+        const uint64_t dbit = static_cast<uint64_t>(pos + vl + 4) * 8;
+        const uint32_t o1 = wv[0] * vpm, o2 = o1 + wv[1] * vpm, o3 = o2 + wv[2] * vpm;
+        for (int v = sl; v < nv; v += 8) {
+          const int m = v / vpm;
+          const uint32_t w = m == 0 ? wv[0] : m == 1 ? wv[1] : m == 2 ? wv[2] : wv[3];
+          const uint32_t off = (m == 0 ? 0u : m == 1 ? o1 : m == 2 ? o2 : o3) + static_cast<uint32_t>(v - m * vpm) * w;
+          acc += gbits64(sb, dbit + off, static_cast<int>(w));
+        }
+        if (sl == 0) acc += static_cast<uint64_t>(unzigzag(z)) * static_cast<uint64_t>(nv);
+      }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (have && sl == 0) {
+      if (bad) report(a.st, DERR_CORRUPT, static_cast<int>(pp.page), WHERE_WALK_VALUES, 20);
+      dsum[b] = static_cast<int64_t>(bad ? 0 : acc);
+    }
   }
 }
 
@@ -2453,7 +2496,7 @@ void launch_delta_bases(const DecodeArgs& a, int dbegin, int n, int max_regions,
     k_dreg<<<dim3(max_regions, n), 32, dreg_smem, s>>>(a, dbegin);
     k_dfix<<<n, 256, 0, s>>>(a, dbegin);
   }
-  k_delta_sums<<<dim3(32, n), 256, 0, s>>>(a, dbegin);
+  k_delta_sums<<<dim3(64, n), 256, 0, s>>>(a, dbegin);
   k_delta_scan<<<n, 256, 0, s>>>(a, dbegin);
 }
 
