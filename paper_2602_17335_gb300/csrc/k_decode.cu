@@ -1713,17 +1713,38 @@ __device__ bool warp_hybrid(const uint8_t* sb, uint32_t slen, int bw, int32_t to
                             int32_t k0, int32_t k1, const DictDev& dd, bool idx_only, const Sink& sink,
                             uint64_t* chars, int lane) {
   const uint32_t vbytes = (bw + 7) / 8;
+  // lane 0 keeps the next run's first 8 bytes in flight: one-byte headers
+  // (and their repeated value) are decoded from them without a new load
+  uint64_t win = 0;
+  if (lane == 0 && pos < slen) win = ld_unaligned_g(sb + pos, 8);
   for (uint32_t guard = 0; rk < k1 && guard <= slen; ++guard) {
     uint64_t h = 0;
     int hl = 0;
     uint32_t rle = 0;
     if (lane == 0 && pos < slen) {
-      hl = uleb([&](uint32_t q) { return static_cast<uint32_t>(__ldg(sb + q)); }, pos, slen, &h);
-      if (hl && !(h & 1)) {
-        if (pos + hl + vbytes > slen)
-          hl = 0;
-        else
-          for (uint32_t q = 0; q < vbytes; ++q) rle |= static_cast<uint32_t>(__ldg(sb + pos + hl + q)) << (8 * q);
+      const uint32_t b0 = static_cast<uint32_t>(win & 0xffu);
+      if (!(b0 & 0x80u) && (b0 & 1u || 1 + vbytes <= 8)) {
+        h = b0;
+        hl = 1;
+        if (!(h & 1)) {
+          if (pos + 1 + vbytes > slen)
+            hl = 0;
+          else
+            rle = vbytes ? static_cast<uint32_t>((win >> 8) & (vbytes >= 4 ? 0xffffffffull : ((1ull << (8 * vbytes)) - 1)))
+                         : 0u;
+        }
+      } else {
+        hl = uleb([&](uint32_t q) { return static_cast<uint32_t>(__ldg(sb + q)); }, pos, slen, &h);
+        if (hl && !(h & 1)) {
+          if (pos + hl + vbytes > slen)
+            hl = 0;
+          else
+            for (uint32_t q = 0; q < vbytes; ++q) rle |= static_cast<uint32_t>(__ldg(sb + pos + hl + q)) << (8 * q);
+        }
+      }
+      if (hl) {
+        const uint64_t adv = hl + ((h & 1) ? (h >> 1) * static_cast<uint64_t>(bw) : vbytes);
+        if (pos + adv < slen) win = ld_unaligned_g(sb + pos + adv, 8);  // next run, loaded ahead
       }
     }
     hl = __shfl_sync(0xffffffffu, hl, 0);
@@ -1741,10 +1762,68 @@ __device__ bool warp_hybrid(const uint8_t* sb, uint32_t slen, int bw, int32_t to
     const int32_t e = static_cast<int32_t>(e64);
     const uint64_t dbit = static_cast<uint64_t>(pos + hl) * 8;
     bool bad = false;
-    for (int32_t j0 = s; j0 < e; j0 += 128) {
-      uint32_t idx[4];
+    if (dd.n == 0 && s < e) return false;
+    constexpr int U = 8;  // values per lane in flight
+    if (!idx_only && sink.out && !sink.vbuf && !sink.sidx && packed) {
+      // REQUIRED fixed-width output from a bit-packed run: word-aligned
+      // loads, a funnel shift, a gather, a store per value
+      const uintptr_t ab = reinterpret_cast<uintptr_t>(sb);
+      const uint32_t* wq = reinterpret_cast<const uint32_t*>(ab & ~uintptr_t(3));
+      const uint64_t b0 = (ab & 3) * 8 + dbit + static_cast<uint64_t>(s - rk) * bw;
+      const uint32_t mask = bw >= 32 ? 0xffffffffu : ((1u << bw) - 1u);
+      const uint32_t n = static_cast<uint32_t>(dd.n);
+      uint8_t* out = sink.out;
+      const int64_t orow = sink.orow0 + (s - k0);
+      for (int32_t j0 = 0; j0 < e - s; j0 += 32 * U) {
+        uint32_t x[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
+          const int32_t j = j0 + u * 32 + lane;
+          const uint64_t b = b0 + static_cast<uint64_t>(j) * bw;
+          const uint32_t* q = wq + (b >> 5);
+          x[u] = j < e - s ? __funnelshift_r(__ldg(q), __ldg(q + 1), static_cast<uint32_t>(b & 31)) & mask : 0u;
+          bad |= x[u] >= n;
+          x[u] = x[u] < n ? x[u] : 0u;
+        }
+        if (dd.width == 4) {
+          const uint32_t* dv = reinterpret_cast<const uint32_t*>(dd.values);
+          uint32_t v[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) v[u] = __ldg(dv + x[u]);
+          uint32_t* o32 = reinterpret_cast<uint32_t*>(out) + orow;
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (j0 + u * 32 + lane < e - s) o32[j0 + u * 32 + lane] = v[u];
+        } else {
+          const uint64_t* dv = reinterpret_cast<const uint64_t*>(dd.values);
+          uint64_t v[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) v[u] = __ldg(dv + x[u]);
+          uint64_t* o64 = reinterpret_cast<uint64_t*>(out) + orow;
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (j0 + u * 32 + lane < e - s) o64[j0 + u * 32 + lane] = v[u];
+        }
+      }
+    } else if (!idx_only && sink.out && !sink.vbuf && !sink.sidx && s < e) {
+      // REQUIRED fixed-width output from a repeated run: one gather, a fill
+      if (rle >= static_cast<uint32_t>(dd.n)) return false;
+      const int64_t orow = sink.orow0 + (s - k0);
+      const int32_t m = e - s;
+      if (dd.width == 4) {
+        const uint32_t v = __ldg(reinterpret_cast<const uint32_t*>(dd.values) + rle);
+        uint32_t* o32 = reinterpret_cast<uint32_t*>(sink.out) + orow;
+        for (int32_t j = lane; j < m; j += 32) o32[j] = v;
+      } else {
+        const uint64_t v = __ldg(reinterpret_cast<const uint64_t*>(dd.values) + rle);
+        uint64_t* o64 = reinterpret_cast<uint64_t*>(sink.out) + orow;
+        for (int32_t j = lane; j < m; j += 32) o64[j] = v;
+      }
+    } else
+    for (int32_t j0 = s; j0 < e; j0 += 32 * U) {
+      uint32_t idx[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
         const int32_t j = j0 + u * 32 + lane;
         uint32_t x = 0;
         if (j < e) {
@@ -1756,36 +1835,35 @@ __device__ bool warp_hybrid(const uint8_t* sb, uint32_t slen, int bw, int32_t to
         }
         idx[u] = x;
       }
-      if (dd.n == 0) {
-        bad = bad || j0 < e;
-        break;
-      }
       if (idx_only) {
+        uint64_t ent[U];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) ent[u] = j0 + u * 32 + lane < e ? __ldg(dd.str_ent + idx[u]) : 0ull;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
           const int32_t j = j0 + u * 32 + lane;
           if (j < e) {
             sink.put(j - k0, idx[u]);
-            *chars += static_cast<uint32_t>(dd.str_ent[idx[u]]);
+            *chars += static_cast<uint32_t>(ent[u]);
           }
         }
       } else if (dd.width == 4) {
-        uint32_t v[4];
+        uint32_t v[U];
         const uint32_t* dv = reinterpret_cast<const uint32_t*>(dd.values);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = __ldg(dv + idx[u]);
+        for (int u = 0; u < U; ++u) v[u] = __ldg(dv + idx[u]);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
           const int32_t j = j0 + u * 32 + lane;
           if (j < e) sink.put(j - k0, v[u]);
         }
       } else {
-        uint64_t v[4];
+        uint64_t v[U];
         const uint64_t* dv = reinterpret_cast<const uint64_t*>(dd.values);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = __ldg(dv + idx[u]);
+        for (int u = 0; u < U; ++u) v[u] = __ldg(dv + idx[u]);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
           const int32_t j = j0 + u * 32 + lane;
           if (j < e) sink.put(j - k0, v[u]);
         }
