@@ -602,10 +602,13 @@ __device__ int32_t walk_levels(WalkSmem& sm, const PageCtx& pc, const PlanPage& 
     sm.ctl[1] = 0;   // rows consumed
     sm.c64[0] = 0;   // valid rows before the batch
     sm.c64[1] = -1;  // k at row_hi
+    sm.ctl[6] = 0;   // a malformed header in a batch
     sm.ctl[5] = pc.nrows > 0 && !ch_start(c, lsb, slen) ? 3 : 0;
   }
   __syncthreads();
   for (uint32_t guard = 0; guard <= slen + 2 && !sm.ctl[5] && sm.ctl[1] < pc.nrows; ++guard) {
+    // thread 0 follows the chain and records only each run's header
+    // offset; the block decodes the headers of the batch afterwards
     if (tid == 0) {
       uint32_t pos = static_cast<uint32_t>(sm.ctl[0]);
       int32_t row = sm.ctl[1];
@@ -619,82 +622,97 @@ __device__ int32_t walk_levels(WalkSmem& sm, const PageCtx& pc, const PlanPage& 
           const uint32_t lim = c.n0 - 16;
           const uint32_t wb = static_cast<uint32_t>(c.w0);
           const uint8_t* b = c.b0;
-          // software-pipelined: the next header is loaded before this run's bookkeeping
-          uint32_t h = o <= lim ? b[o] : 0x80u, v1 = o <= lim ? b[o + 1] : 0u;
+          uint32_t h = o <= lim ? b[o] : 0x80u;
           while (nb < RB && row < pc.nrows && !(h & 0x80u)) {
             const uint32_t g = h >> 1;
-            const uint32_t packed = h & 1u;
-            const uint32_t on = o + (packed ? 1 + g : 2);
+            const uint32_t on = o + ((h & 1u) ? 1 + g : 2);
             const uint32_t hn = on <= lim ? b[on] : 0x80u;
-            const uint32_t vn = on <= lim ? b[on + 1] : 0u;
-            const uint32_t meta = packed ? 0x80000000u : v1;
-            if (!packed && v1 > 1) { err = 1; break; }
-            const uint32_t cnt = packed ? g << 3 : g;
-            const int32_t take = static_cast<int32_t>(cnt) < pc.nrows - row ? static_cast<int32_t>(cnt) : pc.nrows - row;
-            if (take > 0) {
-              sm.rpos[nb] = o + 1 + wb;
-              sm.rk[nb] = row;
-              sm.rcnt[nb] = take;
-              sm.rmeta[nb] = meta;
-              ++nb;
-              row += take;
-            }
+            sm.rpos[nb++] = o + wb;
+            row += static_cast<int32_t>((h & 1u) ? g << 3 : g);
             o = on;
             h = hn;
-            v1 = vn;
           }
           pos = o + wb;
-          if (err) break;
           if (nb >= RB || row >= pc.nrows) break;
-          if (pos > slen) { err = 1; break; }
           if (pos >= slen) { err = 1; break; }
           if (!ch_ensure(c, pos, 16)) { err = 3; break; }
         }
         const uint8_t* q = ch_ptr(c, pos);
         uint64_t h;
-        int hl;
-        if (q[0] < 0x80) {
-          h = q[0];
-          hl = 1;
-        } else {
-          hl = uleb_p(q, &h);
-          if (!hl) { err = 1; break; }
-        }
-        int64_t cnt;
-        uint32_t meta, adv;
-        if (h & 1) {
-          const uint64_t g = h >> 1;
-          if (g > slen) { err = 1; break; }
-          cnt = static_cast<int64_t>(g) * 8;
-          adv = hl + static_cast<uint32_t>(g);
-          meta = 0x80000000u;
-        } else {
-          cnt = static_cast<int64_t>(h >> 1);
-          adv = hl + 1;
-          meta = q[hl];
-          if (meta > 1) { err = 1; break; }
-        }
+        const int hl = uleb_p(q, &h);
+        if (!hl) { err = 1; break; }
+        const uint64_t cnt = (h & 1) ? (h >> 1) * 8 : h >> 1;
+        const uint64_t adv = hl + ((h & 1) ? (h >> 1) : 1);
         if (static_cast<uint64_t>(pos) + adv > slen) { err = 1; break; }
-        const int32_t take = static_cast<int32_t>(cnt < pc.nrows - row ? cnt : pc.nrows - row);
-        if (take > 0) {
-          sm.rpos[nb] = pos + hl;
-          sm.rk[nb] = row;
-          sm.rcnt[nb] = take;
-          sm.rmeta[nb] = meta;
-          ++nb;
-          row += take;
-        }
-        pos += adv;
+        sm.rpos[nb++] = pos;
+        row = cnt >= static_cast<uint64_t>(pc.nrows - row) ? pc.nrows : row + static_cast<int32_t>(cnt);
+        pos += static_cast<uint32_t>(adv);
       }
+      if (!err && pos > slen) err = 1;
       sm.ctl[0] = static_cast<int32_t>(pos);
       sm.ctl[2] = nb;
-      sm.ctl[4] = row;
       sm.ctl[5] = err;
     }
     __syncthreads();
     if (sm.ctl[5]) break;
     const int nb = sm.ctl[2];
-    const int32_t b0 = sm.ctl[1], b1 = sm.ctl[4];
+    const int32_t b0 = sm.ctl[1];
+    // decode the batch's headers: data offset, rows (clipped to the page),
+    // kind / repeated value; rows before each run by a block scan
+    {
+      int32_t cntv[4];
+      uint32_t dpos[4], meta[4];
+      int32_t mine = 0;
+      int bad = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = tid * 4 + q;
+        cntv[q] = 0;
+        dpos[q] = 0;
+        meta[q] = 0;
+        if (j < nb) {
+          const uint32_t hp = sm.rpos[j];
+          uint64_t h = 0;
+          const int hl = uleb([&](uint32_t x) { return static_cast<uint32_t>(__ldg(lsb + x)); }, hp, slen, &h);
+          if (!hl) bad = 1;
+          const bool packed = h & 1;
+          const uint64_t cnt = packed ? (h >> 1) * 8 : h >> 1;
+          dpos[q] = hp + hl;
+          if (!packed) {
+            meta[q] = hp + hl < slen ? __ldg(lsb + hp + hl) : 2u;
+            if (meta[q] > 1) bad = 1;
+          } else {
+            meta[q] = 0x80000000u;
+          }
+          cntv[q] = cnt > static_cast<uint64_t>(pc.nrows) ? pc.nrows : static_cast<int32_t>(cnt);
+          mine += cntv[q];
+        }
+      }
+      if (bad) sm.ctl[6] = 1;
+      int32_t total;
+      int32_t run = b0 + block_exclusive_sum(mine, sm.tmp32, &total);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = tid * 4 + q;
+        if (j < nb) {
+          const int32_t take = cntv[q] < pc.nrows - run ? cntv[q] : (pc.nrows - run > 0 ? pc.nrows - run : 0);
+          sm.rpos[j] = dpos[q];
+          sm.rk[j] = run;
+          sm.rcnt[j] = take;
+          sm.rmeta[j] = meta[q];
+          run += cntv[q];
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        int32_t e = b0 + total;
+        sm.ctl[4] = e < pc.nrows ? e : pc.nrows;
+        if (sm.ctl[6]) sm.ctl[5] = 1;
+      }
+      __syncthreads();
+      if (sm.ctl[5]) break;
+    }
+    const int32_t b1 = sm.ctl[4];
     // valid counts per run, prefix over the batch (4 consecutive runs per thread)
     int32_t loc[4];
     int32_t mine = 0;
