@@ -40,7 +40,8 @@ constexpr int WALK_THREADS = 256;
 constexpr int EXP_THREADS = 256;
 constexpr int EXP_WARPS = EXP_THREADS / 32;
 constexpr int EXP_COUNTER0 = 4;  // item_counter[4 + c]: next item of output column c
-constexpr uint32_t CWIN = 16384;  // chain window (two per walking block)
+constexpr uint32_t CWIN = 16384;      // chain window (two per walking block)
+constexpr uint32_t CWIN_MAX = 65536;  // window of walks over few pages
 constexpr uint32_t COVL = 64;     // overlap of consecutive chain windows
 constexpr int RB = 1024;          // runs per walk batch
 constexpr uint32_t NULL_IDX = 0xffffffffu;
@@ -118,6 +119,7 @@ struct Chain {
   uint32_t swapped;  // 1 when b0 is the second physical buffer
   const uint8_t* sb;
   uint32_t slen;
+  uint32_t cap;      // bytes per window
 };
 
 __device__ __forceinline__ void ch_swap(Chain& c) {
@@ -131,13 +133,13 @@ __device__ __forceinline__ void ch_swap(Chain& c) {
 }
 
 // Copies stream bytes from `from` (rounded down to 16) into a window: up to
-// CWIN bytes, at most 16 bytes past the stream end (readable padding).
+// the window capacity, at most 16 bytes past the stream end (readable padding).
 __device__ __forceinline__ void ch_issue(const Chain& c, uint8_t* buf, uint64_t* bar, int64_t from, int64_t* w,
                                          uint32_t* n, uint32_t* e) {
   const uint8_t* a = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(c.sb + from) & ~uintptr_t(15));
   int64_t want = (static_cast<int64_t>((c.sb + c.slen) - a) + 16) & ~int64_t(15);
   if (want < 16) want = 16;
-  const uint32_t bytes = static_cast<uint32_t>(want < CWIN ? want : CWIN);
+  const uint32_t bytes = static_cast<uint32_t>(want < c.cap ? want : c.cap);
   fence_proxy_async_smem();
   mbar_arrive_expect_tx(bar, bytes);
   bulk_g2s(buf, a, bytes, bar);
@@ -172,7 +174,8 @@ __device__ __forceinline__ void ch_prefetch(Chain& c) {
 }
 
 __device__ __forceinline__ void ch_init(Chain& c, uint8_t* buf0, uint8_t* buf1, uint64_t* bar0, uint64_t* bar1,
-                                        uint32_t par0, uint32_t par1) {
+                                        uint32_t par0, uint32_t par1, uint32_t cap = CWIN) {
+  c.cap = cap;
   c.b0 = buf0;
   c.b1 = buf1;
   c.m0 = bar0;
@@ -506,8 +509,11 @@ struct WalkSmem {
   uint32_t rmeta[RB];  // levels: 0x80000000 bit-packed, else the repeated value
   int32_t rpre[RB];    // levels: valid rows before the run (page-relative)
   int32_t tmp32[32];
-  alignas(16) uint8_t win[2][CWIN + 16];
+  // two chain windows of ctl[13] + 16 bytes each follow the struct
 };
+constexpr uint32_t walk_smem_bytes(uint32_t cap) {
+  return ((static_cast<uint32_t>(sizeof(WalkSmem)) + 15u) & ~15u) + 2u * (cap + 16u);
+}
 
 // Page layout.
 struct PageCtx {
@@ -556,8 +562,10 @@ __device__ bool page_ctx(const DecodeArgs& a, const PlanPage& pp, PageCtx* pc) {
 
 __device__ __forceinline__ Chain make_chain(WalkSmem& sm) {
   Chain c;
-  ch_init(c, sm.win[0], sm.win[1], &sm.bar[0], &sm.bar[1], static_cast<uint32_t>(sm.ctl[14]),
-          static_cast<uint32_t>(sm.ctl[15]));
+  const uint32_t cap = static_cast<uint32_t>(sm.ctl[13]);
+  uint8_t* w0 = reinterpret_cast<uint8_t*>(&sm) + ((sizeof(WalkSmem) + 15) & ~size_t(15));
+  ch_init(c, w0, w0 + cap + 16, &sm.bar[0], &sm.bar[1], static_cast<uint32_t>(sm.ctl[14]),
+          static_cast<uint32_t>(sm.ctl[15]), cap);
   return c;
 }
 
@@ -824,6 +832,8 @@ __device__ bool walk_hybrid(WalkSmem& sm, const uint8_t* sb, uint32_t slen, int 
   }
   __syncthreads();
   for (uint32_t guard = 0; guard <= slen + 2 && !sm.ctl[5] && sm.ctl[1] < total; ++guard) {
+    // thread 0 follows the chain and records each run's header offset; the
+    // block then decodes the batch's headers into dense indices
     if (tid == 0) {
       uint32_t pos = static_cast<uint32_t>(sm.ctl[0]);
       int64_t k = sm.ctl[1];
@@ -838,7 +848,6 @@ __device__ bool walk_hybrid(WalkSmem& sm, const uint8_t* sb, uint32_t slen, int 
           const uint32_t wb = static_cast<uint32_t>(c.w0);
           const uint8_t* b = c.b0;
           int32_t kk = static_cast<int32_t>(k);
-          // software-pipelined: the next header is loaded before this run's bookkeeping
           uint32_t h = o <= lim ? b[o] : 0x80u;
           while (nb < RB && kk < total && !(h & 0x80u)) {
             const uint32_t g = h >> 1;
@@ -846,9 +855,7 @@ __device__ bool walk_hybrid(WalkSmem& sm, const uint8_t* sb, uint32_t slen, int 
             const uint32_t on = o + 1 + (packed ? g * static_cast<uint32_t>(bw) : vbytes);
             const uint32_t hn = on <= lim ? b[on] : 0x80u;
             const uint32_t cnt = packed ? g << 3 : g;
-            sm.rpos[nb] = o + wb;
-            sm.rk[nb] = kk;
-            ++nb;
+            sm.rpos[nb++] = o + wb;
             kk = static_cast<int32_t>(cnt) < total - kk ? kk + static_cast<int32_t>(cnt) : total;
             o = on;
             h = hn;
@@ -881,9 +888,7 @@ __device__ bool walk_hybrid(WalkSmem& sm, const uint8_t* sb, uint32_t slen, int 
           adv = hl + vbytes;
         }
         if (static_cast<uint64_t>(pos) + adv > slen) { err = 1; break; }
-        sm.rpos[nb] = pos;
-        sm.rk[nb] = static_cast<int32_t>(k);
-        ++nb;
+        sm.rpos[nb++] = pos;
         pos += static_cast<uint32_t>(adv);
         k = k + static_cast<int64_t>(cnt) > total ? total : k + static_cast<int64_t>(cnt);
       }
@@ -894,6 +899,33 @@ __device__ bool walk_hybrid(WalkSmem& sm, const uint8_t* sb, uint32_t slen, int 
     }
     __syncthreads();
     if (sm.ctl[5]) break;
+    {
+      // dense index at each run start: headers decoded by the block, a scan
+      const int nbb = sm.ctl[2];
+      int32_t cntv[4];
+      int32_t mine = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = tid * 4 + q;
+        cntv[q] = 0;
+        if (j < nbb) {
+          uint64_t h = 0;
+          uleb([&](uint32_t x) { return static_cast<uint32_t>(__ldg(sb + x)); }, sm.rpos[j], slen, &h);
+          const uint64_t cnt = (h & 1) ? (h >> 1) << 3 : h >> 1;
+          cntv[q] = cnt > static_cast<uint64_t>(total) ? total : static_cast<int32_t>(cnt);
+          mine += cntv[q];
+        }
+      }
+      int32_t tot;
+      int32_t run = sm.ctl[1] + block_exclusive_sum(mine, sm.tmp32, &tot);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = tid * 4 + q;
+        if (j < nbb) sm.rk[j] = run < total ? run : total;
+        run += cntv[q];
+      }
+      __syncthreads();
+    }
     const int nb = sm.ctl[2];
     const int32_t kb0 = sm.ctl[1], kb1 = sm.ctl[3];
     for (uint32_t i = tid; i < pp.item_count; i += blockDim.x) {
@@ -1200,21 +1232,22 @@ __device__ void walk_page(const DecodeArgs& a, int p, WalkSmem& sm, bool serial_
   __syncthreads();
 }
 
-__device__ __forceinline__ void walk_init(WalkSmem& sm) {
+__device__ __forceinline__ void walk_init(WalkSmem& sm, uint32_t cap) {
   if (threadIdx.x == 0) {
     mbar_init(&sm.bar[0], 1);
     mbar_init(&sm.bar[1], 1);
     fence_mbar_init();
+    sm.ctl[13] = static_cast<int32_t>(cap);
     sm.ctl[14] = sm.ctl[15] = 0;
   }
   __syncthreads();
 }
 
 // One thread block per page of walk list entries [wbegin, wbegin + gridDim.x).
-__global__ void __launch_bounds__(WALK_THREADS) k_walk(DecodeArgs a, int wbegin) {
+__global__ void __launch_bounds__(WALK_THREADS) k_walk(DecodeArgs a, int wbegin, uint32_t cap) {
   extern __shared__ __align__(16) uint8_t smraw[];
   WalkSmem& sm = *reinterpret_cast<WalkSmem*>(smraw);
-  walk_init(sm);
+  walk_init(sm, cap);
   walk_page(a, static_cast<int>(a.walk_pps[wbegin + blockIdx.x]), sm, false);
 }
 
@@ -2390,19 +2423,22 @@ __global__ void __launch_bounds__(WALK_THREADS) k_plain_page(DecodeArgs a, int p
   extern __shared__ __align__(16) uint8_t smraw[];
   WalkSmem& sm = *reinterpret_cast<WalkSmem*>(smraw);
   const int p = pp_begin + blockIdx.x;
-  walk_init(sm);
+  walk_init(sm, CWIN);
   const PlanPage pp0 = a.pps[p];
   const PageDev pg = a.pages[pp0.page];
   const ChunkDev ch = a.chunks[pp0.chunk];
   const bool needs_walk = ch.max_def || pg.encoding != ENC_PLAIN || ch.ptype == T_BYTE_ARRAY;
   if (needs_walk) walk_page(a, p, sm, true);
   __syncthreads();
+  // the chain windows, free again: scan scratch, then the warps' staging
+  uint8_t* wins = smraw + ((sizeof(WalkSmem) + 15) & ~size_t(15));
   if (pg.encoding == ENC_DELTA_BP) {
-    delta_bases_page(a, p, reinterpret_cast<uint64_t*>(sm.win[1]));
+    delta_bases_page(a, p, reinterpret_cast<uint64_t*>(wins + CWIN + 16));
     __syncthreads();
   }
   const PlanPage pp = a.pps[p];
-  WarpSmem* ws = reinterpret_cast<WarpSmem*>(sm.win[0]);
+  static_assert(sizeof(WarpSmem) * (WALK_THREADS / 32) <= 2 * (CWIN + 16), "warp staging must fit the windows");
+  WarpSmem* ws = reinterpret_cast<WarpSmem*>(wins);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (uint32_t i = warp; i < pp.item_count; i += nw) expand_item(a, static_cast<int>(pp.item_begin + i), ws[warp], lane);
 }
@@ -2559,9 +2595,9 @@ static int g_walk_bps = 0, g_exp_bps = 0;
 
 int walk_blocks_per_sm() {
   if (!g_walk_bps) {
-    cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(WalkSmem));
-    cudaFuncSetAttribute(k_plain_page, cudaFuncAttributeMaxDynamicSharedMemorySize, sizeof(WalkSmem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_walk_bps, k_walk, WALK_THREADS, sizeof(WalkSmem));
+    cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, walk_smem_bytes(CWIN_MAX));
+    cudaFuncSetAttribute(k_plain_page, cudaFuncAttributeMaxDynamicSharedMemorySize, walk_smem_bytes(CWIN));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_walk_bps, k_walk, WALK_THREADS, walk_smem_bytes(CWIN));
     if (g_walk_bps < 1) g_walk_bps = 1;
   }
   return g_walk_bps;
@@ -2575,9 +2611,13 @@ int expand_blocks_per_sm() {
   return g_exp_bps;
 }
 
-void launch_walk(const DecodeArgs& a, int wbegin, int n, cudaStream_t s) {
+void launch_walk(const DecodeArgs& a, int wbegin, int n, int n_sms, cudaStream_t s) {
   if (n <= 0) return;
-  k_walk<<<n, WALK_THREADS, sizeof(WalkSmem), s>>>(a, wbegin);
+  walk_blocks_per_sm();  // sets the shared-memory attributes
+  // few pages (long chains each): larger windows, fewer refills on the
+  // chain's path; many pages: more resident walkers
+  const uint32_t cap = n <= n_sms ? CWIN_MAX : (n <= 2 * n_sms ? CWIN_MAX / 2 : CWIN);
+  k_walk<<<n, WALK_THREADS, walk_smem_bytes(cap), s>>>(a, wbegin, cap);
 }
 
 void launch_delta_bases(const DecodeArgs& a, int dbegin, int n, int max_regions, cudaStream_t s) {
@@ -2634,7 +2674,7 @@ void launch_strings(const DecodeArgs& a, int col, int n_items, int n_sms, cudaSt
 
 void launch_plain_pages(const DecodeArgs& a, int pp_begin, int n, cudaStream_t s) {
   if (n <= 0) return;
-  k_plain_page<<<n, WALK_THREADS, sizeof(WalkSmem), s>>>(a, pp_begin);
+  k_plain_page<<<n, WALK_THREADS, walk_smem_bytes(CWIN), s>>>(a, pp_begin);
 }
 
 }  // namespace pqi
