@@ -2208,10 +2208,11 @@ __global__ void k_str_scan(DecodeArgs a, int c) {
 }
 
 // Copies `len` bytes from global `src` (any alignment) to shared `d` (any
-// alignment).  The source is read as aligned 16-byte words (about
-// (len + 15) / 16 + 1 sectors per string, instead of one per 4 bytes), the
-// destination is written as 4-byte words funnel-shifted from them, with byte
-// stores only for the partial words at the string's two ends.  The aligned
+// alignment) whose words start at zero.  The source is read as aligned
+// 16-byte words (about (len + 15) / 16 + 1 sectors per string, instead of
+// one per 4 bytes), the destination is OR-ed in as 4-byte words
+// funnel-shifted from them, the partial words at the string's two ends
+// masked (neighbouring strings OR their own bytes into them).  The aligned
 // words may reach up to 16 bytes past `src + len`; callers guarantee those
 // bytes are readable.
 __device__ __forceinline__ void stage_string(uint8_t* d, const uint8_t* src, uint32_t len) {
@@ -2229,21 +2230,17 @@ __device__ __forceinline__ void stage_string(uint8_t* d, const uint8_t* src, uin
   uint4 v = __ldg(sv + (wi < 0 ? 0 : (wi >> 2)));
   uint32_t cur = wi < 0 ? 0u : pick(v, wi & 3);
   const int end = dd + static_cast<int>(len);             // destination bytes [dd, end) relative to dw
+  const uint32_t mfirst = 0xffffffffu << (8 * dd);
+  const uint32_t mlast = (end & 3) ? (0xffffffffu >> (8 * (4 - (end & 3)))) : 0xffffffffu;
   for (int k = 0; k < nw; ++k) {
     ++wi;
     if ((wi & 3) == 0) v = __ldg(sv + (wi >> 2));
     const uint32_t nxt = pick(v, wi & 3);
-    const uint32_t val = sh ? __funnelshift_r(cur, nxt, sh) : cur;
+    uint32_t val = __funnelshift_r(cur, nxt, sh);
     cur = nxt;
-    const int b0 = 4 * k;
-    if (b0 >= dd && b0 + 4 <= end) {
-      dw[k] = val;
-    } else {
-      uint8_t* db = reinterpret_cast<uint8_t*>(dw + k);
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (b0 + j >= dd && b0 + j < end) db[j] = static_cast<uint8_t>(val >> (8 * j));
-    }
+    if (k == 0) val &= mfirst;
+    if (k == nw - 1) val &= mlast;
+    atomicOr(dw + k, val);
   }
 }
 
@@ -2260,20 +2257,18 @@ __device__ __forceinline__ void stage_from_raw(uint8_t* d, const uint8_t* raw, i
   int wi = q0 >> 2;
   uint32_t cur = wi < 0 ? 0u : rw[wi];
   const int end = dd + static_cast<int>(len);
+  // the destination words start at zero and may be shared with neighbouring
+  // strings at the two ends: every word is OR-ed in, the end words masked
+  const uint32_t mfirst = 0xffffffffu << (8 * dd);
+  const uint32_t mlast = (end & 3) ? (0xffffffffu >> (8 * (4 - (end & 3)))) : 0xffffffffu;
   for (int k = 0; k < nw; ++k) {
     ++wi;
     const uint32_t nxt = rw[wi];
-    const uint32_t val = sh ? __funnelshift_r(cur, nxt, sh) : cur;
+    uint32_t val = __funnelshift_r(cur, nxt, sh);
     cur = nxt;
-    const int b0 = 4 * k;
-    if (b0 >= dd && b0 + 4 <= end) {
-      dw[k] = val;
-    } else {
-      uint8_t* db = reinterpret_cast<uint8_t*>(dw + k);
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (b0 + j >= dd && b0 + j < end) db[j] = static_cast<uint8_t>(val >> (8 * j));
-    }
+    if (k == 0) val &= mfirst;
+    if (k == nw - 1) val &= mlast;
+    atomicOr(dw + k, val);
   }
 }
 
@@ -2308,6 +2303,11 @@ __global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a, int c) {
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const int ib = static_cast<int>(a.cols[c].item_begin);
   const int ie = ib + static_cast<int>(a.cols[c].item_count);
+  {
+    uint4* zv = reinterpret_cast<uint4*>(sbuf);
+    for (int q = lane; q < (STR_STAGE + 16) / 16; q += 32) zv[q] = make_uint4(0, 0, 0, 0);
+    __syncwarp();
+  }
   for (int itx = ib + gw; itx < ie; itx += nw) {
     const Item it = a.items[itx];
     if (it.nrows <= 0) continue;
@@ -2401,6 +2401,10 @@ __global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a, int c) {
               uint4* gv = reinterpret_cast<uint4*>(g + hh);
               for (uint32_t q = lane; q < nv; q += 32) gv[q] = sv[q];
               for (uint32_t q = hh + (nv << 4) + lane; q < tot; q += 32) g[q] = sbuf[a0 + q];
+              __syncwarp();
+              // back to zero for the next chunk
+              uint4* zv = reinterpret_cast<uint4*>(sbuf);
+              for (uint32_t q = lane; q < (a0 + tot + 15) / 16; q += 32) zv[q] = make_uint4(0, 0, 0, 0);
               __syncwarp();
             } else if (r < it.nrows) {
               uint8_t* d = col.chars + off;
