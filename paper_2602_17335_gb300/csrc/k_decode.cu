@@ -2288,9 +2288,10 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // strings are read straight from global memory.
 constexpr int STR_STAGE = 2048;
 constexpr int STR_RAW_BLK = 4;  // strings up to 49 bytes go through the async copies
+constexpr int STR_SLOT = STR_RAW_BLK + 1;  // slot stride in 16-byte blocks (spreads lanes over banks)
 struct StrWarpSmem {
   uint8_t stage[STR_STAGE + 16];
-  uint4 raw[64 * STR_RAW_BLK + 1];  // +1: the last slot's read-ahead word
+  uint4 raw[64 * STR_SLOT + 1];  // +1: the last slot's read-ahead word
 };
 constexpr int STR_SMEM = 8 * sizeof(StrWarpSmem);
 
@@ -2324,11 +2325,12 @@ __global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a, int c) {
     int64_t* offs = reinterpret_cast<int64_t*>(col.values);
     const uint8_t* cbase = isdict ? dd.chars : sb;
     for (int g0 = 0; g0 < it.nrows; g0 += 256) {
-      // metadata of 8 chunks of 32 strings, loads issued together
+      // metadata of 4 chunks of 64 strings, loads issued together; lane l
+      // takes rows 2l and 2l+1 of each chunk (adjacent in the output)
       uint32_t sidx[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int r = g0 + u * 32 + lane;
+        const int r = g0 + (u >> 1) * 64 + 2 * lane + (u & 1);
         sidx[u] = r < it.nrows ? col.str_scratch[orow0 + r] : NULL_IDX;
       }
       uint64_t ent[8];
@@ -2344,75 +2346,79 @@ __global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a, int c) {
         }
       }
 #pragma unroll
-      for (int u2 = 0; u2 < 8; u2 += 2) {
-        if (g0 + u2 * 32 >= it.nrows) break;
-        // source spans of two chunks, fetched together
+      for (int cc = 0; cc < 4; ++cc) {
+        const int r0 = g0 + cc * 64;
+        if (r0 >= it.nrows) break;
+        // source spans of the lane's two strings, fetched together
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t len = static_cast<uint32_t>(ent[u2 + h]);
-          const uint8_t* src = cbase + (ent[u2 + h] >> 32);
+        for (int t = 0; t < 2; ++t) {
+          const uint32_t len = static_cast<uint32_t>(ent[2 * cc + t]);
+          const uint8_t* src = cbase + (ent[2 * cc + t] >> 32);
           const uint32_t p = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 15);
           const uint32_t nb = (p + len + 15) >> 4;
           if (len && nb <= STR_RAW_BLK) {
             const uint8_t* sa = src - p;
-            uint4* slot = ws.raw + (h * 32 + lane) * STR_RAW_BLK;
+            uint4* slot = ws.raw + (t * 32 + lane) * STR_SLOT;
             for (uint32_t b = 0; b < nb; ++b) cp_async16(slot + b, sa + 16 * b);
           }
         }
+        const uint32_t lena = static_cast<uint32_t>(ent[2 * cc]), lenb = static_cast<uint32_t>(ent[2 * cc + 1]);
+        const uint32_t mine = lena + lenb;
+        uint32_t incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t rel = incl - mine;  // chunk-relative offset of the lane's first string
+        const int ra = r0 + 2 * lane;
+        if (ra < it.nrows) offs[orow0 + ra] = static_cast<int64_t>(base + rel);
+        if (ra + 1 < it.nrows) offs[orow0 + ra + 1] = static_cast<int64_t>(base + rel + lena);
         cp_async_wait_all();
         __syncwarp();
+        if (base + tot <= col.chars_cap) {
+          const uint32_t a0 = static_cast<uint32_t>(base & 15);
+          if (a0 + tot <= STR_STAGE) {
+            // lanes place their strings, congruent to the output mod 16
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int u = u2 + h;
-          const int r0 = g0 + u * 32;
-          if (r0 >= it.nrows) break;
-          const int r = r0 + lane;
-          const uint32_t len = static_cast<uint32_t>(ent[u]);
-          const uint8_t* src = cbase + (ent[u] >> 32);
-          uint64_t incl = len;
+            for (int t = 0; t < 2; ++t) {
+              const uint32_t len = t ? lenb : lena;
+              if (!len) continue;
+              const uint8_t* src = cbase + (ent[2 * cc + t] >> 32);
+              const int p = static_cast<int>(reinterpret_cast<uintptr_t>(src) & 15);
+              uint8_t* d = sbuf + a0 + rel + (t ? lena : 0u);
+              if (((p + len + 15) >> 4) <= STR_RAW_BLK)
+                stage_from_raw(d, reinterpret_cast<const uint8_t*>(ws.raw + (t * 32 + lane) * STR_SLOT), p, len);
+              else
+                stage_string(d, src, len);
+            }
+            __syncwarp();
+            uint8_t* g = col.chars + base;
+            const uint32_t head = a0 ? 16 - a0 : 0;
+            const uint32_t hh = head < tot ? head : tot;
+            if (static_cast<uint32_t>(lane) < hh) g[lane] = sbuf[a0 + lane];
+            const uint32_t nv = (tot - hh) >> 4;
+            const uint4* sv = reinterpret_cast<const uint4*>(sbuf + a0 + hh);
+            uint4* gv = reinterpret_cast<uint4*>(g + hh);
+            for (uint32_t q = lane; q < nv; q += 32) gv[q] = sv[q];
+            for (uint32_t q = hh + (nv << 4) + lane; q < tot; q += 32) g[q] = sbuf[a0 + q];
+            __syncwarp();
+            // back to zero for the next chunk
+            uint4* zv = reinterpret_cast<uint4*>(sbuf);
+            for (uint32_t q = lane; q < (a0 + tot + 15) / 16; q += 32) zv[q] = make_uint4(0, 0, 0, 0);
+            __syncwarp();
+          } else {
 #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-          }
-          const uint64_t tot = __shfl_sync(0xffffffffu, incl, 31);
-          const uint64_t off = base + incl - len;
-          if (r < it.nrows) offs[orow0 + r] = static_cast<int64_t>(off);
-          if (base + tot <= col.chars_cap) {
-            const uint32_t a0 = static_cast<uint32_t>(base & 15);
-            if (a0 + tot <= STR_STAGE) {
-              // lanes place their strings, congruent to the output mod 16
-              if (len) {
-                const int p = static_cast<int>(reinterpret_cast<uintptr_t>(src) & 15);
-                uint8_t* d = sbuf + a0 + (off - base);
-                if (((p + len + 15) >> 4) <= STR_RAW_BLK)
-                  stage_from_raw(d, reinterpret_cast<const uint8_t*>(ws.raw + (h * 32 + lane) * STR_RAW_BLK), p,
-                                 len);
-                else
-                  stage_string(d, src, len);
-              }
-              __syncwarp();
-              uint8_t* g = col.chars + base;
-              const uint32_t head = a0 ? 16 - a0 : 0;
-              const uint32_t hh = head < tot ? head : static_cast<uint32_t>(tot);
-              if (static_cast<uint32_t>(lane) < hh) g[lane] = sbuf[a0 + lane];
-              const uint32_t nv = static_cast<uint32_t>((tot - hh) >> 4);
-              const uint4* sv = reinterpret_cast<const uint4*>(sbuf + a0 + hh);
-              uint4* gv = reinterpret_cast<uint4*>(g + hh);
-              for (uint32_t q = lane; q < nv; q += 32) gv[q] = sv[q];
-              for (uint32_t q = hh + (nv << 4) + lane; q < tot; q += 32) g[q] = sbuf[a0 + q];
-              __syncwarp();
-              // back to zero for the next chunk
-              uint4* zv = reinterpret_cast<uint4*>(sbuf);
-              for (uint32_t q = lane; q < (a0 + tot + 15) / 16; q += 32) zv[q] = make_uint4(0, 0, 0, 0);
-              __syncwarp();
-            } else if (r < it.nrows) {
-              uint8_t* d = col.chars + off;
+            for (int t = 0; t < 2; ++t) {
+              const uint32_t len = t ? lenb : lena;
+              const uint8_t* src = cbase + (ent[2 * cc + t] >> 32);
+              uint8_t* d = col.chars + base + rel + (t ? lena : 0u);
               for (uint32_t q = 0; q < len; ++q) d[q] = __ldg(src + q);
             }
           }
-          base += tot;
         }
+        base += tot;
         __syncwarp();
       }
     }
