@@ -172,6 +172,15 @@ __device__ __forceinline__ uint64_t bits64(const uint32_t* w, uint64_t b, int wi
 // Unaligned little-endian load of 4 or 8 bytes from global memory, using
 // aligned loads of the enclosing words (never reads outside the 8-byte
 // aligned words that contain the value).
+// Asks L2 to fetch the 128-byte lines of [p, end) (the warp's lanes take
+// every 32nd line).  A hint only: nothing waits for it.  `end` must not pass
+// the end of the buffer that holds p.
+__device__ __forceinline__ void prefetch_l2(const uint8_t* p, const uint8_t* end, int lane) {
+  const uintptr_t e = reinterpret_cast<uintptr_t>(end);
+  for (uintptr_t a = (reinterpret_cast<uintptr_t>(p) & ~uintptr_t(127)) + 128u * lane; a < e; a += 32u * 128u)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 __device__ __forceinline__ uint64_t ld_unaligned_g(const uint8_t* p, int width) {
   uintptr_t a = reinterpret_cast<uintptr_t>(p);
   const uint64_t* q = reinterpret_cast<const uint64_t*>(a & ~uintptr_t(7));

@@ -825,79 +825,130 @@ __device__ bool walk_hybrid(WalkSmem& sm, const uint8_t* sb, uint32_t slen, int 
   const int tid = threadIdx.x;
   const uint32_t vbytes = (bw + 7) / 8;
   Chain c = make_chain(sm);
+  // a bit-packed run of the most groups a one-byte header holds (63, header
+  // byte 127) spans `stride` bytes; streams of random indices are made of
+  // little else, so such stretches are checked by the whole block at once
+  constexpr uint32_t kMaxRun = 127;
+  constexpr int kSerialMax = 32;
+  const uint64_t stride = 1 + 63ull * static_cast<uint64_t>(bw);
   if (tid == 0) {
     sm.ctl[0] = 0;  // position
     sm.ctl[1] = 0;  // dense index
     sm.ctl[5] = ch_start(c, sb, slen) ? 0 : 3;
+    sm.ctl[7] = !sm.ctl[5] && slen > 0 && c.b0[0] == kMaxRun;  // next batch starts with a parallel check
   }
   __syncthreads();
   for (uint32_t guard = 0; guard <= slen + 2 && !sm.ctl[5] && sm.ctl[1] < total; ++guard) {
-    // thread 0 follows the chain and records each run's header offset; the
-    // block then decodes the batch's headers into dense indices
     if (tid == 0) {
-      uint32_t pos = static_cast<uint32_t>(sm.ctl[0]);
-      int64_t k = sm.ctl[1];
-      int nb = 0, err = 0;
-      while (nb < RB && k < total) {
-        if (pos >= slen) { err = 1; break; }
-        if (!ch_ensure(c, pos, 16)) { err = 3; break; }
-        {
-          // fast steps: one-byte run headers inside the current window
-          uint32_t o = static_cast<uint32_t>(pos - c.w0);
-          const uint32_t lim = c.n0 - 16;
-          const uint32_t wb = static_cast<uint32_t>(c.w0);
-          const uint8_t* b = c.b0;
-          int32_t kk = static_cast<int32_t>(k);
-          uint32_t h = o <= lim ? b[o] : 0x80u;
-          while (nb < RB && kk < total && !(h & 0x80u)) {
-            const uint32_t g = h >> 1;
-            const uint32_t packed = h & 1u;
-            const uint32_t on = o + 1 + (packed ? g * static_cast<uint32_t>(bw) : vbytes);
-            const uint32_t hn = on <= lim ? b[on] : 0x80u;
-            const uint32_t cnt = packed ? g << 3 : g;
-            sm.rpos[nb++] = o + wb;
-            kk = static_cast<int32_t>(cnt) < total - kk ? kk + static_cast<int32_t>(cnt) : total;
-            o = on;
-            h = hn;
-          }
-          pos = o + wb;
-          k = kk;
-          if (nb >= RB || k >= total) {
-            if (pos > slen) err = 1;
-            break;
-          }
-          if (pos >= slen) { err = 1; break; }
-          if (!ch_ensure(c, pos, 16)) { err = 3; break; }
-        }
-        const uint8_t* q = ch_ptr(c, pos);
-        uint64_t h;
-        int hl;
-        if (q[0] < 0x80) {
-          h = q[0];
-          hl = 1;
-        } else {
-          hl = uleb_p(q, &h);
-          if (!hl) { err = 1; break; }
-        }
-        uint64_t cnt, adv;
-        if (h & 1) {
-          cnt = (h >> 1) << 3;
-          adv = hl + (h >> 1) * static_cast<uint64_t>(bw);
-        } else {
-          cnt = h >> 1;
-          adv = hl + vbytes;
-        }
-        if (static_cast<uint64_t>(pos) + adv > slen) { err = 1; break; }
-        sm.rpos[nb++] = pos;
-        pos += static_cast<uint32_t>(adv);
-        k = k + static_cast<int64_t>(cnt) > total ? total : k + static_cast<int64_t>(cnt);
-      }
-      sm.ctl[0] = static_cast<int32_t>(pos);
-      sm.ctl[2] = nb;
-      sm.ctl[3] = static_cast<int32_t>(k);
-      sm.ctl[5] = err;
+      sm.ctl[9] = 0;             // runs recorded in the batch
+      sm.ctl[10] = sm.ctl[1];    // dense index reached
     }
     __syncthreads();
+    // a batch is gathered in segments: a parallel check of a stretch of
+    // maximal runs (when the next header says one starts there), then thread
+    // 0 stepping along the chain until kSerialMax maximal runs in a row
+    for (;;) {
+      if (sm.ctl[7]) {
+        // consecutive maximal runs at pos0 + i * stride, confirmed by reading
+        // their header bytes in parallel (the run at pos0 is known to be one)
+        const uint32_t pos0 = static_cast<uint32_t>(sm.ctl[0]);
+        const int32_t kb = sm.ctl[10];
+        const int nb0 = sm.ctl[9];
+        const int64_t need = (static_cast<int64_t>(total) - kb + 503) / 504;
+        const int imax = static_cast<int>(need < RB - nb0 ? need : RB - nb0);
+        __syncthreads();
+        if (tid == 0) sm.ctl[8] = imax;
+        __syncthreads();
+        for (int i = tid; i < imax; i += blockDim.x) {
+          const uint64_t p = pos0 + static_cast<uint64_t>(i) * stride;
+          if (p + stride > slen || __ldg(sb + p) != kMaxRun) {
+            atomicMin(&sm.ctl[8], i);
+            break;
+          }
+        }
+        __syncthreads();
+        const int m = sm.ctl[8];
+        for (int i = tid; i < m; i += blockDim.x) sm.rpos[nb0 + i] = pos0 + static_cast<uint32_t>(i * stride);
+        if (tid == 0) {
+          sm.ctl[9] = nb0 + m;
+          sm.ctl[0] = static_cast<int32_t>(pos0 + m * stride);
+          const int64_t ke = static_cast<int64_t>(kb) + 504ll * m;
+          sm.ctl[10] = static_cast<int32_t>(ke < total ? ke : total);
+        }
+      }
+      if (tid == 0) {
+        uint32_t pos = static_cast<uint32_t>(sm.ctl[0]);
+        int64_t k = sm.ctl[10];
+        int nb = sm.ctl[9], err = 0;
+        int maxrun = 0;  // consecutive maximal runs stepped through
+        while (nb < RB && k < total && maxrun < kSerialMax) {
+          if (pos >= slen) { err = 1; break; }
+          if (!ch_ensure(c, pos, 16)) { err = 3; break; }
+          {
+            // fast steps: one-byte run headers inside the current window
+            uint32_t o = static_cast<uint32_t>(pos - c.w0);
+            const uint32_t lim = c.n0 - 16;
+            const uint32_t wb = static_cast<uint32_t>(c.w0);
+            const uint8_t* b = c.b0;
+            int32_t kk = static_cast<int32_t>(k);
+            uint32_t h = o <= lim ? b[o] : 0x80u;
+            while (nb < RB && kk < total && !(h & 0x80u) && maxrun < kSerialMax) {
+              const uint32_t g = h >> 1;
+              const uint32_t packed = h & 1u;
+              const uint32_t on = o + 1 + (packed ? g * static_cast<uint32_t>(bw) : vbytes);
+              const uint32_t hn = on <= lim ? b[on] : 0x80u;
+              const uint32_t cnt = packed ? g << 3 : g;
+              sm.rpos[nb++] = o + wb;
+              kk = static_cast<int32_t>(cnt) < total - kk ? kk + static_cast<int32_t>(cnt) : total;
+              maxrun = h == kMaxRun ? maxrun + 1 : 0;
+              o = on;
+              h = hn;
+            }
+            pos = o + wb;
+            k = kk;
+            if (nb >= RB || k >= total || maxrun >= kSerialMax) {
+              if (pos > slen) err = 1;
+              break;
+            }
+            if (pos >= slen) { err = 1; break; }
+            if (!ch_ensure(c, pos, 16)) { err = 3; break; }
+          }
+          const uint8_t* q = ch_ptr(c, pos);
+          uint64_t h;
+          int hl;
+          if (q[0] < 0x80) {
+            h = q[0];
+            hl = 1;
+          } else {
+            hl = uleb_p(q, &h);
+            if (!hl) { err = 1; break; }
+          }
+          uint64_t cnt, adv;
+          if (h & 1) {
+            cnt = (h >> 1) << 3;
+            adv = hl + (h >> 1) * static_cast<uint64_t>(bw);
+          } else {
+            cnt = h >> 1;
+            adv = hl + vbytes;
+          }
+          if (static_cast<uint64_t>(pos) + adv > slen) { err = 1; break; }
+          sm.rpos[nb++] = pos;
+          pos += static_cast<uint32_t>(adv);
+          k = k + static_cast<int64_t>(cnt) > total ? total : k + static_cast<int64_t>(cnt);
+          maxrun = 0;
+        }
+        sm.ctl[0] = static_cast<int32_t>(pos);
+        sm.ctl[2] = nb;
+        sm.ctl[3] = static_cast<int32_t>(k);
+        sm.ctl[5] = err;
+        sm.ctl[7] = !err && k < total && pos < slen && __ldg(sb + pos) == kMaxRun;
+        sm.ctl[9] = nb;
+        sm.ctl[10] = static_cast<int32_t>(k);
+        sm.ctl[11] = sm.ctl[7] && nb < RB;  // the batch goes on with a parallel check
+      }
+      __syncthreads();
+      if (!sm.ctl[11]) break;
+    }
     if (sm.ctl[5]) break;
     {
       // dense index at each run start: headers decoded by the block, a scan
@@ -1764,6 +1815,13 @@ __device__ bool warp_hybrid(const uint8_t* sb, uint32_t slen, int bw, int32_t to
                             int32_t k0, int32_t k1, const DictDev& dd, bool idx_only, const Sink& sink,
                             uint64_t* chars, int lane) {
   const uint32_t vbytes = (bw + 7) / 8;
+  {
+    // the runs of [rk, k1) as if all were bit-packed: an upper bound of the
+    // item's bytes unless headers are long; lines fetched into L2 up front
+    const uint64_t span = 16 + (static_cast<uint64_t>(k1 - rk) * bw + 7) / 8;
+    const uint64_t end = pos + span < slen ? pos + span : slen;
+    if (pos < end) prefetch_l2(sb + pos, sb + end, lane);
+  }
   // lane 0 keeps the next run's first 8 bytes in flight: one-byte headers
   // (and their repeated value) are decoded from them without a new load
   uint64_t win = 0;
@@ -1936,6 +1994,12 @@ __device__ bool warp_delta(const uint8_t* sb, const PlanPage& pp, const uint32_t
   if (ka >= k1) return true;
   const int bfirst = (ka - 1) / pp.dbs, blast = (k1 - 2) / pp.dbs;
   if (blast >= pp.dblocks) return false;
+  {
+    const uint32_t slen = static_cast<uint32_t>(pp.body_len - pp.values_off);
+    const uint32_t p0 = dpos[bfirst];
+    const uint32_t p1 = blast + 1 < pp.dblocks ? dpos[blast + 1] : slen;
+    if (p0 < p1 && p1 <= slen) prefetch_l2(sb + p0, sb + p1, lane);
+  }
   for (int b = bfirst; b <= blast; ++b) {
     const uint32_t pos = dpos[b];
     const int64_t bk = 1 + static_cast<int64_t>(b) * pp.dbs;
@@ -2076,14 +2140,24 @@ __device__ void expand_item(const DecodeArgs& a, int it_id, WarpSmem& ws, int la
         }
       }
     } else {
+      if (nn > 0) prefetch_l2(src, src + static_cast<int64_t>(nn) * width, lane);
       int32_t rank = 0;
+      const uint32_t sh = static_cast<uint32_t>(orow0 & 31);
       for (int32_t r0 = 0; r0 < it.nrows; r0 += 256) {
+        // the bitmap words of these 256 rows (9 at most), one per lane,
+        // loaded together; each 32-row group's bits by two shuffles
+        const int64_t wbase = (orow0 + r0) >> 5;
+        const int64_t wend = (orow0 + it.nrows - 1) >> 5;
+        const uint32_t myw = lane < 9 && wbase + lane <= wend ? col.validity[wbase + lane] : 0u;
         uint32_t bits[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int32_t c0 = r0 + u * 32;
           const int n = it.nrows - c0 < 32 ? it.nrows - c0 : 32;
-          bits[u] = n > 0 ? bitmap_bits(col.validity, orow0 + c0, n) : 0u;
+          const uint32_t lo = __shfl_sync(0xffffffffu, myw, u);
+          const uint32_t hi = __shfl_sync(0xffffffffu, myw, u + 1);
+          const uint32_t b = sh ? __funnelshift_r(lo, hi, sh) : lo;
+          bits[u] = n <= 0 ? 0u : (n < 32 ? b & ((1u << n) - 1u) : b);
         }
         uint64_t v[8];
         int32_t rr[8];
@@ -2158,16 +2232,20 @@ __device__ void expand_item(const DecodeArgs& a, int it_id, WarpSmem& ws, int la
 // Items [ibegin, ibegin + icount), handed out one at a time to warps through
 // the column's counter (items differ in cost), over a grid sized to the
 // resident capacity.
-__global__ void __launch_bounds__(EXP_THREADS, 3) k_expand(DecodeArgs a, int ibegin, int icount, int cidx) {
+__global__ void __launch_bounds__(EXP_THREADS, 4) k_expand(DecodeArgs a, int ibegin, int icount, int cidx) {
   __shared__ WarpSmem ws[EXP_WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* ctr = a.item_counter + EXP_COUNTER0 + cidx;
-  for (;;) {
-    int u = 0;
-    if (lane == 0) u = static_cast<int>(atomicAdd(ctr, 1u));
-    u = __shfl_sync(0xffffffffu, u, 0);
-    if (u >= icount) break;
+  // each warp holds one claimed item in reserve: the next claim is issued
+  // before the current item is decoded, so its latency is hidden
+  int u = 0;
+  if (lane == 0) u = static_cast<int>(atomicAdd(ctr, 1u));
+  u = __shfl_sync(0xffffffffu, u, 0);
+  while (u < icount) {
+    int un = 0;
+    if (lane == 0) un = static_cast<int>(atomicAdd(ctr, 1u));
     expand_item(a, ibegin + u, ws[warp], lane);
+    u = __shfl_sync(0xffffffffu, un, 0);
   }
 }
 

@@ -281,6 +281,45 @@ def test_batch_of_heterogeneous_chunks(eng, graph):
             N.pq_ctx_set_tuning(eng.ctx)
 
 
+def test_maximal_run_stretches(eng):
+    """Dictionary-index streams made of stretches of maximal bit-packed runs
+    (63 groups, header byte 127) broken by repeated runs at irregular gaps:
+    a few runs apart, hundreds apart, and more than a walk batch (1024 runs)
+    apart; bit widths 4, 12 and 20; one 8 MiB page per chunk, so a page
+    holds thousands of runs; nullable and REQUIRED columns; the "mixed"
+    policy adds bit-packed runs shorter than the maximum."""
+    n = 1 << 21
+    rng = np.random.default_rng(2026)
+
+    def with_repeats(vals, mean_gap_runs):
+        out = vals.copy()
+        i = 0
+        while True:
+            i += int(rng.geometric(1.0 / (mean_gap_runs * 504))) // 8 * 8
+            if i >= n - 64:
+                break
+            L = int(rng.integers(8, 40))
+            out[i:i + L] = out[i]
+            i += L
+        return out
+
+    cols = [
+        synth.ColumnData("bw4_gap3", "INT32", with_repeats(rng.integers(0, 16, n).astype(np.int32), 3)),
+        synth.ColumnData("bw12_gap300", "INT32", with_repeats(rng.integers(0, 4096, n).astype(np.int32), 300)),
+        synth.ColumnData("bw20_gap5000", "INT64", with_repeats(rng.integers(0, 1 << 20, n).astype(np.int64), 5000)),
+        synth.ColumnData("bw12_none", "INT32", rng.integers(0, 4096, n).astype(np.int32)),
+    ]
+    valid = rng.random(n) < 0.999
+    cols.append(synth.ColumnData("opt_bw12", "INT32", np.where(valid, cols[1].values, 0).astype(np.int32), valid))
+    for policy in ("default", "mixed"):
+        cs = [synth.ColumnSpec("RLE_DICTIONARY") for _ in cols]
+        for c in cs:
+            c.hybrid_policy = policy
+        data = W.write_file(synth.Table(cols), synth.TableSpec(n, 8 << 20, cs))
+        _roundtrip(eng, data)
+        _roundtrip(eng, data, row_begin=300_001, row_count=1_500_007)
+
+
 def test_hybrid_run_chains_across_regions(eng):
     """Level and dictionary-index streams long enough to span many 4 KB run
     regions: nulls with probability 1/2 (short bit-packed runs), long null
