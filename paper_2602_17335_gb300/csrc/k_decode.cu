@@ -2458,18 +2458,89 @@ __global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a, int c) {
         if (base + tot <= col.chars_cap) {
           const uint32_t a0 = static_cast<uint32_t>(base & 15);
           if (a0 + tot <= STR_STAGE) {
-            // lanes place their strings, congruent to the output mod 16
+            // the chunk is assembled in shared memory congruent to the output
+            // mod 16.  Fast path: every lane with rows holds at least 4 bytes
+            // and both its strings sit in its source slots; each staging
+            // word is then written once, by the lane whose span holds the
+            // word's first byte, and the few bytes of a word that belong to
+            // the next lane's span come from that lane by a shuffle.
+            const int pa = static_cast<int>(reinterpret_cast<uintptr_t>(cbase + (ent[2 * cc] >> 32)) & 15);
+            const int pb = static_cast<int>(reinterpret_cast<uintptr_t>(cbase + (ent[2 * cc + 1] >> 32)) & 15);
+            const bool has = ra < it.nrows;
+            const bool good = !has || (lena + lenb >= 4 && ((pa + lena + 15) >> 4) <= STR_RAW_BLK &&
+                                       ((pb + lenb + 15) >> 4) <= STR_RAW_BLK);
+            if (__all_sync(0xffffffffu, good)) {
+              const uint32_t* rwa = reinterpret_cast<const uint32_t*>(ws.raw + lane * STR_SLOT);
+              const uint32_t* rwb = reinterpret_cast<const uint32_t*>(ws.raw + (32 + lane) * STR_SLOT);
+              const int sa = static_cast<int>(a0 + rel), ea = sa + static_cast<int>(lena),
+                        eb = ea + static_cast<int>(lenb);
+              // 4 bytes at byte `off` (>= -3) of a source slot
+              auto srcw = [](const uint32_t* rw, int off) -> uint32_t {
+                const int q = off >> 2;
+                return __funnelshift_r(rw[q], rw[q + 1], static_cast<uint32_t>(off & 3) * 8);
+              };
+              auto bmask = [](int n) -> uint32_t {
+                return n <= 0 ? 0u : (n >= 4 ? 0xffffffffu : ((1u << (8 * n)) - 1u));
+              };
+              // staging word w from the lane's two strings and `nxt` (bytes at
+              // and past eb, placed in the word)
+              auto mix = [&](int w, uint32_t nxt) -> uint32_t {
+                const int x = 4 * w;
+                const uint32_t ma = bmask(ea - x), mab = bmask(eb - x);
+                const uint32_t va = x < ea ? srcw(rwa, pa + x - sa) : 0u;
+                const uint32_t vb = (x + 4 > ea && x < eb) ? srcw(rwb, pb + x - ea) : 0u;
+                return (va & ma) | (vb & mab & ~ma) | (nxt & ~mab);
+              };
+              const uint32_t head = (has && (sa & 3)) ? (mix(sa >> 2, 0u) & ~bmask(sa & 3)) : 0u;
+              uint32_t nxt = __shfl_down_sync(0xffffffffu, head, 1);
+              if (lane == 31) nxt = 0;
+              if (has) {
+                uint32_t* sw = reinterpret_cast<uint32_t*>(sbuf);
+                int w = (lane == 0) ? (sa >> 2) : ((sa + 3) >> 2);
+                const int wa = ea >> 2, wb = eb >> 2;
+                if (w < wa) {  // words wholly inside the first string
+                  const int off = pa + 4 * w - sa;
+                  int q = off >> 2;
+                  const uint32_t sh = static_cast<uint32_t>(off & 3) * 8;
+                  uint32_t cur = rwa[q];
+                  for (; w < wa; ++w) {
+                    const uint32_t n2 = rwa[++q];
+                    sw[w] = __funnelshift_r(cur, n2, sh);
+                    cur = n2;
+                  }
+                }
+                if ((ea & 3) && w == wa) sw[w++] = mix(wa, nxt);  // end of the first string
+                if (w < wb) {  // words wholly inside the second string
+                  const int off = pb + 4 * w - ea;
+                  int q = off >> 2;
+                  const uint32_t sh = static_cast<uint32_t>(off & 3) * 8;
+                  uint32_t cur = rwb[q];
+                  for (; w < wb; ++w) {
+                    const uint32_t n2 = rwb[++q];
+                    sw[w] = __funnelshift_r(cur, n2, sh);
+                    cur = n2;
+                  }
+                }
+                if ((eb & 3) && w == wb) sw[w] = mix(wb, nxt);  // end of the span
+              }
+            } else {
+              // general path: the staging area starts at zero and lanes OR
+              // their strings in (end words are shared)
+              uint4* zv = reinterpret_cast<uint4*>(sbuf);
+              for (uint32_t q = lane; q < (a0 + tot + 15) / 16; q += 32) zv[q] = make_uint4(0, 0, 0, 0);
+              __syncwarp();
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-              const uint32_t len = t ? lenb : lena;
-              if (!len) continue;
-              const uint8_t* src = cbase + (ent[2 * cc + t] >> 32);
-              const int p = static_cast<int>(reinterpret_cast<uintptr_t>(src) & 15);
-              uint8_t* d = sbuf + a0 + rel + (t ? lena : 0u);
-              if (((p + len + 15) >> 4) <= STR_RAW_BLK)
-                stage_from_raw(d, reinterpret_cast<const uint8_t*>(ws.raw + (t * 32 + lane) * STR_SLOT), p, len);
-              else
-                stage_string(d, src, len);
+              for (int t = 0; t < 2; ++t) {
+                const uint32_t len = t ? lenb : lena;
+                if (!len) continue;
+                const uint8_t* src = cbase + (ent[2 * cc + t] >> 32);
+                const int p = static_cast<int>(reinterpret_cast<uintptr_t>(src) & 15);
+                uint8_t* d = sbuf + a0 + rel + (t ? lena : 0u);
+                if (((p + len + 15) >> 4) <= STR_RAW_BLK)
+                  stage_from_raw(d, reinterpret_cast<const uint8_t*>(ws.raw + (t * 32 + lane) * STR_SLOT), p, len);
+                else
+                  stage_string(d, src, len);
+              }
             }
             __syncwarp();
             uint8_t* g = col.chars + base;
@@ -2481,10 +2552,6 @@ __global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a, int c) {
             uint4* gv = reinterpret_cast<uint4*>(g + hh);
             for (uint32_t q = lane; q < nv; q += 32) gv[q] = sv[q];
             for (uint32_t q = hh + (nv << 4) + lane; q < tot; q += 32) g[q] = sbuf[a0 + q];
-            __syncwarp();
-            // back to zero for the next chunk
-            uint4* zv = reinterpret_cast<uint4*>(sbuf);
-            for (uint32_t q = lane; q < (a0 + tot + 15) / 16; q += 32) zv[q] = make_uint4(0, 0, 0, 0);
             __syncwarp();
           } else {
 #pragma unroll

@@ -182,6 +182,28 @@ def test_edge_cases(eng):
         _roundtrip(eng, W.write_file(nt if rg == 1 else tab, spec))
 
 
+@pytest.mark.parametrize("enc", ["RLE_DICTIONARY", "PLAIN"])
+def test_string_lengths_and_nulls(eng, enc):
+    """String columns whose rows cover every case of the chunk assembly:
+    lengths 0-3 (spans under a word), 4-12, up to 80 bytes (past the source
+    slots), nulls, and pools large and small; 64-row chunks end inside
+    items and pages."""
+    n = 50_003
+    rng = np.random.default_rng(99)
+    cols = []
+    for name, k, lo, hi, null in (("tiny", 50, 0, 3, 0.0), ("short", 400, 4, 12, 0.0), ("wide", 3000, 0, 80, 0.0),
+                                  ("opt_mid", 900, 5, 20, 0.3), ("opt_wide", 200, 1, 64, 0.05)):
+        sd = synth.strings_uniform(rng, n, k=k, min_len=lo, max_len=hi)
+        valid = None if null == 0.0 else rng.random(n) >= null
+        cols.append(synth.ColumnData(name, "BYTE_ARRAY", sd, valid))
+    tab = synth.Table(cols)
+    for page in (1 << 20, 3000):
+        spec = synth.TableSpec(20_000, page, [synth.ColumnSpec(enc) for _ in cols])
+        _roundtrip(eng, W.write_file(tab, spec))
+    spec = synth.TableSpec(n, 1 << 16, [synth.ColumnSpec(enc) for _ in cols])
+    _roundtrip(eng, W.write_file(tab, spec), row_begin=777, row_count=40_001)
+
+
 def test_config4_style_mixed_chunks(eng):
     draws = synth.config4_draws(n_files=3, chunks_per_file=4, rows_lo=500, rows_hi=40_000, page_lo=512,
                                 page_hi=64 * 1024)
