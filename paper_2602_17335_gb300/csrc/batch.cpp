@@ -85,6 +85,12 @@ pq_status pq_batch_launch(pq_batch* b, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (b->flags & PQ_SCAN_GRAPH) {
     if (!b->graph) {
+      // the plans' uploads are done before the capture (see scan_enqueue)
+      for (pq_plan* p : b->plans)
+        if (p->ready) {
+          const cudaError_t e = cudaEventSynchronize(p->ready);
+          if (e != cudaSuccess) return cuda_fail(ctx, e, "plan ready");
+        }
       cudaStream_t cs = nullptr;
       cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "capture stream");

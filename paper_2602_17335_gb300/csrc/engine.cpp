@@ -422,22 +422,37 @@ pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi,
     // 4a. OffsetIndex: page counts from the list headers (the first 16 bytes
     // of every chunk's OffsetIndex, fetched in one round trip into the
     // footer staging, which is free again), then one thread per page
-    if (!ctx->tail.reserve(16 * static_cast<size_t>(nch))) {
+    // staging: [0, 16 n) the list headers, [16 n, 24 n) their addresses,
+    // [24 n, 28 n) the OffsetIndex lengths; one gather launch between one
+    // upload and one download
+    const size_t n16 = 16 * static_cast<size_t>(nch);
+    if (!ctx->tail.reserve(28 * static_cast<size_t>(nch))) {
       free_index_device(idx.get());
       return fail(ctx, PQ_ERR_OOM, "pinned staging");
     }
     {
+      const uint8_t** hp = reinterpret_cast<const uint8_t**>(ctx->tail.p + n16);
+      int32_t* hl = reinterpret_cast<int32_t*>(ctx->tail.p + 24 * static_cast<size_t>(nch));
       int ci = 0;
       for (int f = 0; f < n_files; ++f) {
         const uint8_t* base = static_cast<const uint8_t*>(files[f].data);
         for (const auto& g : idx->metas[f].rgs)
           for (int c = 0; c < idx->n_columns; ++c, ++ci) {
-            const auto& cm = g.chunks[c];
-            CK(cudaMemcpyAsync(ctx->tail.p + 16 * ci, base + cm.oi_offset, std::min<int32_t>(cm.oi_length, 16),
-                               cudaMemcpyDeviceToHost, s));
+            hp[ci] = base + g.chunks[c].oi_offset;
+            hl[ci] = g.chunks[c].oi_length;
           }
       }
+      uint8_t* d_g = static_cast<uint8_t*>(pool.alloc(28 * static_cast<size_t>(nch)));
+      if (!d_g) {
+        free_index_device(idx.get());
+        return fail(ctx, PQ_ERR_OOM, "index staging");
+      }
+      CK(cudaMemcpyAsync(d_g + n16, ctx->tail.p + n16, 12 * static_cast<size_t>(nch), cudaMemcpyHostToDevice, s));
+      pqi::launch_gather16(reinterpret_cast<const uint8_t* const*>(d_g + n16),
+                           reinterpret_cast<const int32_t*>(d_g + 24 * static_cast<size_t>(nch)), nch, d_g, s);
+      CK(cudaMemcpyAsync(ctx->tail.p, d_g, n16, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
+      pool.free(d_g);
     }
     int ci = 0;
     for (int f = 0; f < n_files; ++f) {
@@ -643,6 +658,10 @@ void pq_free_plan(pq_plan* plan) {
   if (plan->done) {
     cudaEventSynchronize(plan->done);
     cudaEventDestroy(plan->done);
+  }
+  if (plan->ready) {
+    cudaEventSynchronize(plan->ready);
+    cudaEventDestroy(plan->ready);
   }
   if (plan->graph) cudaGraphExecDestroy(plan->graph);
   for (auto& e : plan->stage_ev)
@@ -955,7 +974,10 @@ pq_status plan_upload(pq_plan* plan) {
   if (!plan->delta_pps.empty())
     CK(cudaMemcpyAsync(plan->d_delta_pps, plan->delta_pps.data(), sizeof(uint32_t) * plan->delta_pps.size(),
                        cudaMemcpyHostToDevice, s));
-  CK(cudaStreamSynchronize(s));
+  // no host wait: a scan's stream waits on this event (the host arrays are
+  // plan members, alive until the plan is freed)
+  CK(cudaEventCreateWithFlags(&plan->ready, cudaEventDisableTiming));
+  CK(cudaEventRecord(plan->ready, s));
   CK(cudaEventCreateWithFlags(&plan->done, cudaEventDisableTiming));
   if (plan->flags & PQ_SCAN_TIMING)
     for (auto& e : plan->stage_ev) CK(cudaEventCreate(&e));
@@ -1235,6 +1257,14 @@ pq_status scan_enqueue(pq_plan* plan, const pq_column* outs, cudaStream_t s, con
     // the graph reads string totals through baked addresses: rebuild it
     cudaGraphExecDestroy(plan->graph);
     plan->graph = nullptr;
+  }
+  // the plan's uploads (legacy stream) come before anything of the scan.  A
+  // captured stream may not wait on an event recorded outside the capture:
+  // callers that capture wait for `ready` before the capture begins.
+  if (plan->ready) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cap));
+    if (cap == cudaStreamCaptureStatusNone) CK(cudaStreamWaitEvent(s, plan->ready, 0));
   }
   memcpy(plan->h_cols.p, plan->outcols.data(), sizeof(pqi::OutCol) * plan->outcols.size());
   if (!plan->outcols.empty())

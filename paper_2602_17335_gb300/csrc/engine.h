@@ -142,6 +142,7 @@ struct pq_plan {
   pqe::Pinned h_cols;
   pqe::Pinned h_out;
   cudaEvent_t done = nullptr;
+  cudaEvent_t ready = nullptr;  // the plan's uploads and item table are in place
   cudaGraphExec_t graph = nullptr;
   cudaStream_t graph_stream = nullptr;
   bool dicts_in_graph = true;

@@ -80,26 +80,21 @@ __global__ void k_index_walk(const ChunkDev* __restrict__ chunks, int n_chunks, 
   if (mode == 0) counts[c] = np;
 }
 
-// OffsetIndex path, step 1 (one thread per chunk): read the page locations
+// OffsetIndex path, step 1 (one warp per chunk): read the page locations
 // list {1: offset i64, 2: compressed_page_size i32, 3: first_row_index i64}
 // into the page table's offset field (file offset, rebased to the chunk).
 // Slot 0 of a dictionary chunk is reserved for its dictionary page, which
-// starts at the chunk start.
-__global__ void k_index_oi_locations(const ChunkDev* __restrict__ chunks, int n_chunks,
-                                     const int64_t* __restrict__ chunk_file_off, PageDev* pages,
-                                     DevStatus* st) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_chunks) return;
-  const ChunkDev ch = chunks[c];
-  TRd r{ch.oi_base, ch.oi_base + ch.oi_len, false};
+// starts at the chunk start.  The warp first copies the chunk's serialized
+// OffsetIndex into shared memory (when it fits), so that the serial parse by
+// lane 0 reads shared rather than global memory.
+constexpr int OI_WARPS = 4;
+constexpr uint32_t OI_SMEM = 8192;  // bytes staged per warp
+
+template <bool kGlobal>
+__device__ void oi_locations(TRdT<kGlobal> r, int c, const ChunkDev& ch, int64_t file_off, PageDev* pages,
+                             DevStatus* st) {
   int last = 0, fid = 0, type = 0;
-  uint32_t slot = ch.dict_page >= 0 ? 1u : 0u;
-  if (slot) {
-    PageDev d{};
-    d.offset = 0;
-    d.chunk = static_cast<uint32_t>(c);
-    pages[ch.page_begin] = d;
-  }
+  const uint32_t slot = ch.dict_page >= 0 ? 1u : 0u;
   bool got = false;
   for (int g = 0; g < 16 && r.field(&last, &fid, &type); ++g) {
     if (fid == 1 && type == 9) {
@@ -120,7 +115,7 @@ __global__ void k_index_oi_locations(const ChunkDev* __restrict__ chunks, int n_
           else
             r.skip(t2, 1);
         }
-        int64_t rel = off - chunk_file_off[c];
+        const int64_t rel = off - file_off;
         if (r.err || rel < 0 || static_cast<uint64_t>(rel) >= ch.size) {
           report(st, DERR_CORRUPT, -1 - c, WHERE_INDEX, 11);
           return;
@@ -137,6 +132,30 @@ __global__ void k_index_oi_locations(const ChunkDev* __restrict__ chunks, int n_
     if (r.err) break;
   }
   if (r.err || !got) report(st, DERR_CORRUPT, -1 - c, WHERE_INDEX, 12);
+}
+
+__global__ void __launch_bounds__(32 * OI_WARPS) k_index_oi_locations(const ChunkDev* __restrict__ chunks,
+                                                                      int n_chunks,
+                                                                      const int64_t* __restrict__ chunk_file_off,
+                                                                      PageDev* pages, DevStatus* st) {
+  __shared__ __align__(16) uint8_t buf[OI_WARPS][OI_SMEM];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c = blockIdx.x * OI_WARPS + w;
+  if (c >= n_chunks) return;
+  const ChunkDev ch = chunks[c];
+  if (lane == 0 && ch.dict_page >= 0) {
+    PageDev d{};
+    d.offset = 0;
+    d.chunk = static_cast<uint32_t>(c);
+    pages[ch.page_begin] = d;
+  }
+  if (ch.oi_len <= OI_SMEM) {
+    for (uint32_t i = lane; i < ch.oi_len; i += 32) buf[w][i] = __ldg(ch.oi_base + i);
+    __syncwarp();
+    if (lane == 0) oi_locations(TRdT<false>{buf[w], buf[w] + ch.oi_len, false}, c, ch, chunk_file_off[c], pages, st);
+  } else if (lane == 0) {
+    oi_locations(TRd{ch.oi_base, ch.oi_base + ch.oi_len, false}, c, ch, chunk_file_off[c], pages, st);
+  }
 }
 
 // OffsetIndex path, step 2: one thread per page parses its header.
@@ -167,29 +186,60 @@ __global__ void k_index_oi_headers(const ChunkDev* __restrict__ chunks, PageDev*
   pages[i] = h;
 }
 
-// OffsetIndex path, step 3: one thread per chunk sets first_row (prefix of
-// num_values) and checks that the pages are contiguous and cover the chunk's
-// values.
-__global__ void k_index_oi_rows(const ChunkDev* __restrict__ chunks, int n_chunks, PageDev* pages,
-                                DevStatus* st) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+// OffsetIndex path, step 3 (one warp per chunk): first_row of every data
+// page (an exclusive scan of num_values over the chunk's pages), a check
+// that each page starts where the previous one ends, and that the pages
+// cover the chunk's values.
+__global__ void __launch_bounds__(32 * OI_WARPS) k_index_oi_rows(const ChunkDev* __restrict__ chunks, int n_chunks,
+                                                                 PageDev* pages, DevStatus* st) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * OI_WARPS + (threadIdx.x >> 5);
   if (c >= n_chunks) return;
   const ChunkDev ch = chunks[c];
   int64_t row = 0;
-  uint64_t expect = 0;
-  for (uint32_t k = 0; k < ch.page_count; ++k) {
-    PageDev& pg = pages[ch.page_begin + k];
-    if (pg.offset != expect) {
-      report(st, DERR_CORRUPT, static_cast<int>(ch.page_begin + k), WHERE_INDEX, 15);
-      return;
+  uint64_t prev_end = 0;  // end of the page before this group of 32
+  bool bad = false;
+  for (uint32_t k0 = 0; k0 < ch.page_count; k0 += 32) {
+    const uint32_t k = k0 + lane;
+    const bool have = k < ch.page_count;
+    PageDev* pg = pages + ch.page_begin + k;
+    uint64_t off = 0, end = 0;
+    int64_t nv = 0;
+    if (have) {
+      off = pg->offset;
+      end = off + static_cast<uint64_t>(pg->header_len) + static_cast<uint64_t>(pg->compressed);
+      nv = pg->page_type != PAGE_DICT ? pg->num_values : 0;
     }
-    expect = pg.offset + pg.header_len + static_cast<uint64_t>(pg.compressed);
-    if (pg.page_type != PAGE_DICT) {
-      pg.first_row = row;
-      row += pg.num_values;
+    uint64_t before = __shfl_up_sync(0xffffffffu, end, 1);
+    if (lane == 0) before = prev_end;
+    bad |= have && off != before;
+    int64_t incl = nv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
+    if (have && pg->page_type != PAGE_DICT) pg->first_row = row + incl - nv;
+    row += __shfl_sync(0xffffffffu, incl, 31);
+    prev_end = __shfl_sync(0xffffffffu, end, 31);
   }
-  if (row != ch.num_values) report(st, DERR_CORRUPT, -1 - c, WHERE_INDEX, 16);
+  const unsigned badm = __ballot_sync(0xffffffffu, bad);
+  if (badm && lane == __ffs(badm) - 1) {
+    // the first page (in this lane's last group) found out of place
+    report(st, DERR_CORRUPT, -1 - c, WHERE_INDEX, 15);
+  }
+  if (lane == 0 && !badm && row != ch.num_values) report(st, DERR_CORRUPT, -1 - c, WHERE_INDEX, 16);
+}
+
+// The first min(len[i], 16) bytes at ptr[i] into out[16 i ..] (the rest
+// zero), one thread per pointer: many small reads in one launch.
+__global__ void k_gather16(const uint8_t* const* __restrict__ ptr, const int32_t* __restrict__ len, int n,
+                           uint8_t* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint8_t* p = ptr[i];
+  const int m = len[i] < 16 ? len[i] : 16;
+  for (int k = 0; k < 16; ++k) out[16 * i + k] = k < m ? __ldg(p + k) : 0;
 }
 
 }  // namespace pqi
@@ -205,9 +255,13 @@ void launch_index_walk(const ChunkDev* chunks, int n_chunks, PageDev* pages, uin
 void launch_index_oi(const ChunkDev* chunks, int n_chunks, const int64_t* chunk_file_off, PageDev* pages,
                      int n_pages, DevStatus* st, cudaStream_t s) {
   if (n_chunks <= 0) return;
-  int bs = 64;
-  k_index_oi_locations<<<(n_chunks + bs - 1) / bs, bs, 0, s>>>(chunks, n_chunks, chunk_file_off, pages, st);
+  const int blocks = (n_chunks + OI_WARPS - 1) / OI_WARPS;
+  k_index_oi_locations<<<blocks, 32 * OI_WARPS, 0, s>>>(chunks, n_chunks, chunk_file_off, pages, st);
   if (n_pages > 0) k_index_oi_headers<<<(n_pages + 127) / 128, 128, 0, s>>>(chunks, pages, n_pages, st);
-  k_index_oi_rows<<<(n_chunks + bs - 1) / bs, bs, 0, s>>>(chunks, n_chunks, pages, st);
+  k_index_oi_rows<<<blocks, 32 * OI_WARPS, 0, s>>>(chunks, n_chunks, pages, st);
+}
+void launch_gather16(const uint8_t* const* ptr, const int32_t* len, int n, uint8_t* out, cudaStream_t s) {
+  if (n <= 0) return;
+  k_gather16<<<(n + 127) / 128, 128, 0, s>>>(ptr, len, n, out);
 }
 }  // namespace pqi

@@ -14,7 +14,10 @@
 
 namespace pqi {
 
-struct TRd {
+// kGlobal: the bytes are in global memory (read-only loads); otherwise in
+// shared memory.
+template <bool kGlobal>
+struct TRdT {
   const uint8_t* p;
   const uint8_t* end;
   bool err;
@@ -24,7 +27,10 @@ struct TRd {
       err = true;
       return 0;
     }
-    return __ldg(p++);
+    if constexpr (kGlobal)
+      return __ldg(p++);
+    else
+      return *p++;
   }
   __device__ __forceinline__ uint64_t varint() {
     uint64_t v = 0;
@@ -145,6 +151,7 @@ struct TRd {
     return static_cast<int32_t>(v);
   }
 };
+using TRd = TRdT<true>;
 
 // Parses one PageHeader at [p, end).  On success fills `pg` (except offset,
 // first_row and chunk) and returns the header length; returns -1 on a
