@@ -69,6 +69,42 @@ __device__ __forceinline__ uint64_t gbits64(const uint8_t* base, uint64_t b, int
   return w >= 64 ? v : (v & ((1ull << w) - 1));
 }
 
+// DELTA_BINARY_PACKED block header with 4 miniblocks: min delta (zigzag
+// ULEB128, 1-10 bytes) then 4 bit-width bytes, parsed from the 16 bytes at
+// p held in registers (5 aligned 32-bit loads; reads at most 19 bytes past
+// p).  Returns the varint length (0 when longer than 10 bytes); *z the
+// varint, *w4 the widths (byte m = miniblock m).
+template <bool kShared>
+__device__ __forceinline__ int delta_header16(const uint8_t* p, uint64_t* z, uint32_t* w4) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uint32_t* q = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
+  const uint32_t sh = static_cast<uint32_t>(a & 3) * 8;
+  uint32_t r[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    if constexpr (kShared)
+      r[k] = q[k];
+    else
+      r[k] = __ldg(q + k);
+  }
+  const uint64_t lo = (static_cast<uint64_t>(__funnelshift_r(r[1], r[2], sh)) << 32) | __funnelshift_r(r[0], r[1], sh);
+  const uint64_t hi = (static_cast<uint64_t>(__funnelshift_r(r[3], r[4], sh)) << 32) | __funnelshift_r(r[2], r[3], sh);
+  // first byte with its high bit clear ends the varint
+  const uint64_t mlo = ~lo & 0x8080808080808080ull;
+  const uint64_t mhi = ~hi & 0x8080ull;
+  const int vl = mlo ? (__ffsll(static_cast<long long>(mlo)) >> 3) : (mhi ? 8 + (__ffsll(static_cast<long long>(mhi)) >> 3) : 0);
+  if (!vl) return 0;
+  uint64_t v = 0;
+  for (int i = 0; i < vl; ++i) {
+    const uint64_t byte = i < 8 ? (lo >> (8 * i)) & 0x7f : (hi >> (8 * (i - 8))) & 0x7f;
+    v |= byte << (7 * i);
+  }
+  *z = v;
+  *w4 = vl < 8 ? static_cast<uint32_t>((lo >> (8 * vl)) | (vl ? hi << (64 - 8 * vl) : 0ull))
+               : static_cast<uint32_t>(hi >> (8 * (vl - 8)));
+  return vl;
+}
+
 // ------------------------------------------------------------------ K6 dictionaries
 
 // Fixed-width dictionary: an aligned copy of the PLAIN page body.
@@ -1314,6 +1350,16 @@ constexpr uint32_t DB_UNKNOWN = 0xffffffffu;
 // type's bits), DB_UNKNOWN when the staged bytes do not decide.
 __device__ __forceinline__ uint32_t dblock_size_s(const uint8_t* sm, uint32_t o, uint32_t avail, int mbc, int vpm,
                                                   int type_bits) {
+  if (mbc == 4 && avail >= 20u) {  // the common layout: the header from registers
+    uint64_t z;
+    uint32_t w4;
+    const int vl = delta_header16<true>(sm + o, &z, &w4);
+    if (!vl || (type_bits == 32 && vl > 5)) return 0;
+    const uint32_t w0 = w4 & 0xffu, w1 = (w4 >> 8) & 0xffu, w2 = (w4 >> 16) & 0xffu, w3 = w4 >> 24;
+    const uint32_t tb = static_cast<uint32_t>(type_bits);
+    if (w0 > tb || w1 > tb || w2 > tb || w3 > tb) return 0;
+    return static_cast<uint32_t>(vl + 4) + (w0 + w1 + w2 + w3) * static_cast<uint32_t>(vpm) / 8;
+  }
   if (avail < 10u + static_cast<uint32_t>(mbc)) return DB_UNKNOWN;
   int vl = 0;
   for (int i = 0; i < 10; ++i)
@@ -1699,9 +1745,9 @@ __global__ void __launch_bounds__(256) k_delta_sums(DecodeArgs a, int dbegin) {
     if (have && b + 1 < pp.dblocks) {
       const uint32_t pos = dpos[b];
       uint64_t z = 0;
-      const int vl = uleb([&](uint32_t q) { return static_cast<uint32_t>(__ldg(sb + pos + q)); }, 0, 10, &z);
-      const uint32_t wv[4] = {__ldg(sb + pos + vl), __ldg(sb + pos + vl + 1), __ldg(sb + pos + vl + 2),
-                              __ldg(sb + pos + vl + 3)};
+      uint32_t w4 = 0;
+      const int vl = delta_header16<false>(sb + pos, &z, &w4);
+      const uint32_t wv[4] = {w4 & 0xffu, (w4 >> 8) & 0xffu, (w4 >> 16) & 0xffu, w4 >> 24};
       bad = !vl || static_cast<int>(wv[0]) > type_bits || static_cast<int>(wv[1]) > type_bits ||
             static_cast<int>(wv[2]) > type_bits || static_cast<int>(wv[3]) > type_bits;
       if (!bad) {
@@ -1999,6 +2045,81 @@ __device__ bool warp_delta(const uint8_t* sb, const PlanPage& pp, const uint32_t
     const uint32_t p0 = dpos[bfirst];
     const uint32_t p1 = blast + 1 < pp.dblocks ? dpos[blast + 1] : slen;
     if (p0 < p1 && p1 <= slen) prefetch_l2(sb + p0, sb + p1, lane);
+  }
+  if (pp.dbs == 128 && pp.dmbc == 4 && pp.dvpm == 32) {
+    // the common layout: lane j parses the header of block jb + j, then the
+    // blocks are decoded two at a time from the parsed headers (each block
+    // starts from its base, so blocks do not wait on one another)
+    for (int jb = bfirst; jb <= blast; jb += 32) {
+      const int b = jb + lane;
+      const bool have = b <= blast;
+      uint32_t hpos = 0, hw = 0;
+      int hvl = 0;
+      int64_t hmn = 0, hbase = 0;
+      bool badl = false;
+      if (have) {
+        hpos = dpos[b];
+        hbase = dbase[b];
+        uint64_t z = 0;
+        hvl = delta_header16<false>(sb + hpos, &z, &hw);
+        hmn = unzigzag(z);
+        const int64_t bk = 1 + static_cast<int64_t>(b) * 128;
+        const int nvb = static_cast<int>(total - bk < 128 ? total - bk : 128);
+        const int used = (nvb + 31) >> 5;
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          if (m < used && static_cast<int>((hw >> (8 * m)) & 0xffu) > type_bits) badl = true;
+        badl |= !hvl;
+      }
+      if (__any_sync(0xffffffffu, badl)) return false;
+      const int nb = blast - jb + 1 < 32 ? blast - jb + 1 : 32;
+      for (int t0 = 0; t0 < nb; t0 += 2) {
+        uint64_t x[2][4];
+        int64_t bkk[2];
+        int32_t nvv[2];
+        uint64_t carry[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int t = t0 + h < nb ? t0 + h : t0;  // a lone last block is read twice, used once
+          const uint32_t pos = __shfl_sync(0xffffffffu, hpos, t);
+          const int vl = __shfl_sync(0xffffffffu, hvl, t);
+          const uint32_t w4 = __shfl_sync(0xffffffffu, hw, t);
+          const int64_t mn = __shfl_sync(0xffffffffu, hmn, t);
+          carry[h] = static_cast<uint64_t>(__shfl_sync(0xffffffffu, hbase, t));
+          bkk[h] = 1 + static_cast<int64_t>(jb + t) * 128;
+          nvv[h] = static_cast<int32_t>(total - bkk[h] < 128 ? total - bkk[h] : 128);
+          const uint64_t dbit = static_cast<uint64_t>(pos + vl + 4) * 8;
+          uint32_t offm = 0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int w = static_cast<int>((w4 >> (8 * u)) & 0xffu);
+            const int v = u * 32 + lane;
+            x[h][u] = v < nvv[h] ? static_cast<uint64_t>(mn) +
+                                       gbits64(sb, dbit + offm + static_cast<uint64_t>(lane) * w, w)
+                                 : 0;
+            offm += static_cast<uint32_t>(w) * 32u;
+          }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (t0 + h >= nb) break;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            uint64_t y = x[h][u];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const uint64_t tt = __shfl_up_sync(0xffffffffu, y, o);
+              if (lane >= o) y += tt;
+            }
+            const int v = u * 32 + lane;
+            const int64_t dense = bkk[h] + v;
+            if (v < nvv[h] && dense >= k0 && dense < k1) sink.put(static_cast<int32_t>(dense - k0), carry[h] + y);
+            carry[h] += __shfl_sync(0xffffffffu, y, 31);
+          }
+        }
+      }
+    }
+    return true;
   }
   for (int b = bfirst; b <= blast; ++b) {
     const uint32_t pos = dpos[b];
