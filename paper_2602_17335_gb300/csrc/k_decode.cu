@@ -69,6 +69,16 @@ __device__ __forceinline__ uint64_t gbits64(const uint8_t* base, uint64_t b, int
   return w >= 64 ? v : (v & ((1ull << w) - 1));
 }
 
+// Bits [b, b + 64) of the little-endian bit stream at `base` (three
+// aligned 32-bit loads; reads at most 12 bytes past bit b + 64).
+__device__ __forceinline__ uint64_t gwin64(const uint8_t* base, uint64_t b) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(base) + (b >> 3);
+  const uint32_t* q = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
+  const uint32_t sh = static_cast<uint32_t>((a & 3) * 8 + (b & 7));  // 0..31
+  const uint32_t r0 = __ldg(q), r1 = __ldg(q + 1), r2 = __ldg(q + 2);
+  return (static_cast<uint64_t>(__funnelshift_r(r1, r2, sh)) << 32) | __funnelshift_r(r0, r1, sh);
+}
+
 // DELTA_BINARY_PACKED block header with 4 miniblocks: min delta (zigzag
 // ULEB128, 1-10 bytes) then 4 bit-width bytes, parsed from the 16 bytes at
 // p held in registers (5 aligned 32-bit loads; reads at most 19 bytes past
@@ -1340,7 +1350,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(DecodeArgs a, int wbegin,
 
 // ------------------------------------------------------------------ DELTA: parallel block chain
 
-constexpr int DREG_TAIL = 4096;      // bytes staged past a region for its last blocks
+constexpr int DREG_TAIL = 256;       // bytes staged past a region (the header of its last block)
 constexpr int DREG_LEAD = 1024;      // lead-in searched before a region for a block start
 constexpr int DREG_SMEM = DREG_LEAD + DELTA_REGION + DREG_TAIL + 32;
 constexpr uint32_t DB_UNKNOWN = 0xffffffffu;
@@ -1750,7 +1760,25 @@ __global__ void __launch_bounds__(256) k_delta_sums(DecodeArgs a, int dbegin) {
       const uint32_t wv[4] = {w4 & 0xffu, (w4 >> 8) & 0xffu, (w4 >> 16) & 0xffu, w4 >> 24};
       bad = !vl || static_cast<int>(wv[0]) > type_bits || static_cast<int>(wv[1]) > type_bits ||
             static_cast<int>(wv[2]) > type_bits || static_cast<int>(wv[3]) > type_bits;
-      if (!bad) {
+      if (!bad && vpm == 32) {
+        // lane sl sums values [16 sl, 16 sl + 16): half of miniblock sl / 2,
+        // four values per 64-bit window when the width is at most 16 bits
+        const int m = sl >> 1;
+        const uint32_t w = wv[m];
+        const uint32_t offm = 32u * (m == 0 ? 0u : m == 1 ? wv[0] : m == 2 ? wv[0] + wv[1] : wv[0] + wv[1] + wv[2]);
+        const uint64_t b0 = static_cast<uint64_t>(pos + vl + 4) * 8 + offm + static_cast<uint64_t>(sl & 1) * 16 * w;
+        if (w <= 16) {
+          const uint64_t mask = (1ull << w) - 1;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint64_t win = gwin64(sb, b0 + static_cast<uint64_t>(k) * 4 * w);
+            acc += (win & mask) + ((win >> w) & mask) + ((win >> (2 * w)) & mask) + ((win >> (3 * w)) & mask);
+          }
+        } else {
+          for (int i = 0; i < 16; ++i) acc += gbits64(sb, b0 + static_cast<uint64_t>(i) * w, static_cast<int>(w));
+        }
+        if (sl == 0) acc += static_cast<uint64_t>(unzigzag(z)) * static_cast<uint64_t>(nv);
+      } else if (!bad) {
         const uint64_t dbit = static_cast<uint64_t>(pos + vl + 4) * 8;
         const uint32_t o1 = wv[0] * vpm, o2 = o1 + wv[1] * vpm, o3 = o2 + wv[2] * vpm;
         for (int v = sl; v < nv; v += 8) {
@@ -2073,49 +2101,55 @@ __device__ bool warp_delta(const uint8_t* sb, const PlanPage& pp, const uint32_t
       }
       if (__any_sync(0xffffffffu, badl)) return false;
       const int nb = blast - jb + 1 < 32 ? blast - jb + 1 : 32;
-      for (int t0 = 0; t0 < nb; t0 += 2) {
-        uint64_t x[2][4];
-        int64_t bkk[2];
-        int32_t nvv[2];
-        uint64_t carry[2];
+      for (int t = 0; t < nb; ++t) {
+        // lane l takes values [4l, 4l + 4) of the block (miniblock l / 8):
+        // one 64-bit window when the width is at most 16 bits, a local
+        // prefix, then one warp scan of the lane totals
+        const uint32_t pos = __shfl_sync(0xffffffffu, hpos, t);
+        const int vl = __shfl_sync(0xffffffffu, hvl, t);
+        const uint32_t w4 = __shfl_sync(0xffffffffu, hw, t);
+        const uint64_t mn = static_cast<uint64_t>(__shfl_sync(0xffffffffu, hmn, t));
+        const uint64_t base = static_cast<uint64_t>(__shfl_sync(0xffffffffu, hbase, t));
+        const int64_t bk = 1 + static_cast<int64_t>(jb + t) * 128;
+        const int32_t nv = static_cast<int32_t>(total - bk < 128 ? total - bk : 128);
+        const int m = lane >> 3;
+        const uint32_t w0 = w4 & 0xffu, w1 = (w4 >> 8) & 0xffu, w2 = (w4 >> 16) & 0xffu;
+        const uint32_t w = (w4 >> (8 * m)) & 0xffu;
+        const uint32_t offm = 32u * (m == 0 ? 0u : m == 1 ? w0 : m == 2 ? w0 + w1 : w0 + w1 + w2);
+        const uint64_t b0 = static_cast<uint64_t>(pos + vl + 4) * 8 + offm + static_cast<uint64_t>(lane & 7) * 4 * w;
+        const int v0 = 4 * lane;
+        uint64_t x[4];
+        if (v0 < nv) {
+          if (w <= 16) {
+            const uint64_t win = gwin64(sb, b0);
+            const uint64_t mask = (1ull << w) - 1;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int t = t0 + h < nb ? t0 + h : t0;  // a lone last block is read twice, used once
-          const uint32_t pos = __shfl_sync(0xffffffffu, hpos, t);
-          const int vl = __shfl_sync(0xffffffffu, hvl, t);
-          const uint32_t w4 = __shfl_sync(0xffffffffu, hw, t);
-          const int64_t mn = __shfl_sync(0xffffffffu, hmn, t);
-          carry[h] = static_cast<uint64_t>(__shfl_sync(0xffffffffu, hbase, t));
-          bkk[h] = 1 + static_cast<int64_t>(jb + t) * 128;
-          nvv[h] = static_cast<int32_t>(total - bkk[h] < 128 ? total - bkk[h] : 128);
-          const uint64_t dbit = static_cast<uint64_t>(pos + vl + 4) * 8;
-          uint32_t offm = 0;
+            for (int i = 0; i < 4; ++i) x[i] = (win >> (i * w)) & mask;
+          } else {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int w = static_cast<int>((w4 >> (8 * u)) & 0xffu);
-            const int v = u * 32 + lane;
-            x[h][u] = v < nvv[h] ? static_cast<uint64_t>(mn) +
-                                       gbits64(sb, dbit + offm + static_cast<uint64_t>(lane) * w, w)
-                                 : 0;
-            offm += static_cast<uint32_t>(w) * 32u;
+            for (int i = 0; i < 4; ++i) x[i] = v0 + i < nv ? gbits64(sb, b0 + static_cast<uint64_t>(i) * w, w) : 0;
           }
+        } else {
+          x[0] = x[1] = x[2] = x[3] = 0;
         }
+        uint64_t loc[4];
+        uint64_t run = 0;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (t0 + h >= nb) break;
+        for (int i = 0; i < 4; ++i) {
+          run += v0 + i < nv ? mn + x[i] : 0;
+          loc[i] = run;
+        }
+        uint64_t incl = run;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            uint64_t y = x[h][u];
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const uint64_t before = base + (incl - run);
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const uint64_t tt = __shfl_up_sync(0xffffffffu, y, o);
-              if (lane >= o) y += tt;
-            }
-            const int v = u * 32 + lane;
-            const int64_t dense = bkk[h] + v;
-            if (v < nvv[h] && dense >= k0 && dense < k1) sink.put(static_cast<int32_t>(dense - k0), carry[h] + y);
-            carry[h] += __shfl_sync(0xffffffffu, y, 31);
-          }
+        for (int i = 0; i < 4; ++i) {
+          const int64_t dense = bk + v0 + i;
+          if (v0 + i < nv && dense >= k0 && dense < k1) sink.put(static_cast<int32_t>(dense - k0), before + loc[i]);
         }
       }
     }

@@ -126,7 +126,7 @@ struct PlanPage {
 
 // DELTA block-chain region (speculative parallel walk): regions of
 // DELTA_REGION stream bytes, each walked from its first plausible block start.
-constexpr int DELTA_REGION = 16384;
+constexpr int DELTA_REGION = 8192;
 constexpr int DELTA_REGION_LIST = DELTA_REGION / 5 + 2;  // blocks are >= 5 bytes
 struct DeltaRegion {
   int32_t q;      // first block start found in the region (-1: none)
