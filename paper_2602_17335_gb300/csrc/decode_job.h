@@ -57,7 +57,8 @@ struct DecodeArgs {
 void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, int max_str_regions, DictScratch ds,
                  DictDev* dicts, int n_sms, DevStatus* st, cudaStream_t s);
 // Launches over sub-ranges (one output column's share of the plan).
-void launch_walk(const DecodeArgs& a, int wbegin, int n, int n_sms, cudaStream_t s);
+// levels: the pages have definition levels (their walks use jump tables)
+void launch_walk(const DecodeArgs& a, int wbegin, int n, int n_sms, bool levels, cudaStream_t s);
 void launch_delta_bases(const DecodeArgs& a, int dbegin, int n, int max_regions, cudaStream_t s);
 void launch_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, int ctas_per_sm, cudaStream_t s);
 // Items of a column whose pages are all REQUIRED PLAIN fixed-width: copies.

@@ -1115,9 +1115,9 @@ static void enqueue_column(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, b
     pqi::launch_dict(plan->d_dict_jobs + cw.dict_begin, cw.dict_n, cw.max_fixed_dict, cw.max_str_regions,
                      pqi::DictScratch{plan->d_sregs, plan->d_slists}, plan->idx->d_dicts, ctx->n_sms, a.st, s);
   if (cw.snap_data_n) pqi::launch_snappy(plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, ctx->n_sms, a.st, s);
-  pqi::launch_walk(a, cw.walk_begin, cw.walk_n, ctx->n_sms, s);
-  pqi::launch_delta_bases(a, cw.delta_begin, cw.delta_n, cw.max_regions, s);
   const auto& col = plan->outcols[oc];
+  pqi::launch_walk(a, cw.walk_begin, cw.walk_n, ctx->n_sms, col.optional != 0, s);
+  pqi::launch_delta_bases(a, cw.delta_begin, cw.delta_n, cw.max_regions, s);
   if (cw.copy_only)
     pqi::launch_copy_items(a, static_cast<int>(col.item_begin), static_cast<int>(col.item_count),
                            static_cast<int>(oc), ctx->n_sms, plan->tuning.expand_ctas_per_sm, s);
@@ -1189,7 +1189,7 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
     mark(3);
     for (int oc = 0; oc < ncols; ++oc) {
       const auto& cw = plan->colwork[oc];
-      pqi::launch_walk(a, cw.walk_begin, cw.walk_n, ctx->n_sms, s);
+      pqi::launch_walk(a, cw.walk_begin, cw.walk_n, ctx->n_sms, plan->outcols[oc].optional != 0, s);
       pqi::launch_delta_bases(a, cw.delta_begin, cw.delta_n, cw.max_regions, s);
     }
     mark(4);

@@ -547,7 +547,7 @@ void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, int max_s
 
 struct WalkSmem {
   uint64_t bar[2];
-  int32_t ctl[16];
+  int32_t ctl[24];
   int64_t c64[8];
   uint32_t rpos[RB];   // hybrid: run header offset; levels: run data offset
   int32_t rk[RB];      // hybrid: dense index at run start; levels: row at run start
@@ -555,10 +555,14 @@ struct WalkSmem {
   uint32_t rmeta[RB];  // levels: 0x80000000 bit-packed, else the repeated value
   int32_t rpre[RB];    // levels: valid rows before the run (page-relative)
   int32_t tmp32[32];
-  // two chain windows of ctl[13] + 16 bytes each follow the struct
+  uint32_t hop[RB / 32];  // levels: table offsets of chain positions 32 runs apart
+  // two chain windows of ctl[13] + 16 bytes each follow the struct, then
+  // (level walks) three jump tables of ctl[16] 16-bit entries
 };
-constexpr uint32_t walk_smem_bytes(uint32_t cap) {
-  return ((static_cast<uint32_t>(sizeof(WalkSmem)) + 15u) & ~15u) + 2u * (cap + 16u);
+constexpr uint32_t JW = 2048;  // level-stream bytes covered by one set of jump tables
+constexpr uint16_t JSENT = 0xffffu;
+__host__ __device__ constexpr uint32_t walk_smem_bytes(uint32_t cap, uint32_t jw = 0) {
+  return ((static_cast<uint32_t>(sizeof(WalkSmem)) + 15u) & ~15u) + 2u * (cap + 16u) + 3u * 2u * jw;
 }
 
 // Page layout.
@@ -621,14 +625,25 @@ __device__ __forceinline__ void keep_parity(WalkSmem& sm, const Chain& c) {
 }
 
 // Valid rows among the first `n` rows of level run j (bits from global memory).
-__device__ __forceinline__ int32_t run_valid(const WalkSmem& sm, const uint8_t* lsb, int j, int32_t n) {
+// Bits [b, b + w) (w <= 32) at `base`, shared or global memory (plain loads).
+__device__ __forceinline__ uint32_t lbits32(const uint8_t* base, uint64_t b, int w) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(base) + (b >> 3);
+  const uint32_t* q = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
+  const uint32_t sh = static_cast<uint32_t>((a & 3) * 8 + (b & 7));
+  const uint64_t v = ((static_cast<uint64_t>(q[1]) << 32) | q[0]) >> sh;
+  return w >= 32 ? static_cast<uint32_t>(v) : static_cast<uint32_t>(v) & ((1u << w) - 1u);
+}
+
+// Valid rows among the first `n` rows of level run j.  Stream byte p is at
+// lb[p - lp0] (the staged window, or the page in global memory).
+__device__ __forceinline__ int32_t run_valid(const WalkSmem& sm, const uint8_t* lb, uint32_t lp0, int j, int32_t n) {
   const uint32_t meta = sm.rmeta[j];
   if (!(meta & 0x80000000u)) return static_cast<int32_t>(meta) * n;
   int32_t c = 0;
-  const uint64_t b0 = static_cast<uint64_t>(sm.rpos[j]) * 8;
+  const uint64_t b0 = static_cast<uint64_t>(sm.rpos[j] - lp0) * 8;
   for (int32_t x = 0; x < n; x += 32) {
     const int m = n - x < 32 ? n - x : 32;
-    c += __popc(gbits32(lsb, b0 + x, m));
+    c += __popc(lbits32(lb, b0 + x, m));
   }
   return c;
 }
@@ -660,10 +675,117 @@ __device__ int32_t walk_levels(WalkSmem& sm, const PageCtx& pc, const PlanPage& 
     sm.ctl[5] = pc.nrows > 0 && !ch_start(c, lsb, slen) ? 3 : 0;
   }
   __syncthreads();
+  const uint32_t jw = static_cast<uint32_t>(sm.ctl[16]);
   for (uint32_t guard = 0; guard <= slen + 2 && !sm.ctl[5] && sm.ctl[1] < pc.nrows; ++guard) {
+    // With jump tables: for every byte of the next jw stream bytes, the
+    // block computes where a run starting there would end (were that byte a
+    // one-byte header), then doubles the map five times; thread 0 steps 32
+    // runs at a time through it and the block fills in the runs between the
+    // steps.  Such a batch ends where the tables end; when it would hold no
+    // run (a longer header, the stream's or the window's end) the batch is
+    // gathered by the serial walk instead.
+    bool jumped = false;
+    const uint8_t* lb = lsb;  // where the batch's level bytes are read: stream byte p at lb[p - lp0]
+    uint32_t lp0 = 0;
+    if (jw) {
+      uint16_t* j1 = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(&sm) +
+                                                 walk_smem_bytes(static_cast<uint32_t>(sm.ctl[13])));
+      uint16_t* ja = j1 + jw;
+      uint16_t* jb = ja + jw;
+      if (tid == 0) {
+        const uint32_t pos = static_cast<uint32_t>(sm.ctl[0]);
+        int err = 0;
+        // the window must hold the tables' bytes and 16 more
+        const uint32_t need = (slen - pos < jw ? slen - pos : jw) + 16;
+        if (pos >= slen)
+          err = 1;
+        else if (!ch_ensure(c, pos, need))
+          err = 3;
+        sm.ctl[5] = err;
+        if (!err) {
+          const uint32_t o0 = static_cast<uint32_t>(pos - c.w0);
+          const uint32_t room = c.n0 - 16 > o0 ? c.n0 - 16 - o0 : 0u;
+          uint32_t L = room < jw ? room : jw;
+          L = L < slen - pos ? L : slen - pos;
+          sm.ctl[17] = static_cast<int32_t>(c.b0 - reinterpret_cast<uint8_t*>(&sm)) + static_cast<int32_t>(o0);
+          sm.ctl[18] = static_cast<int32_t>(L);
+        }
+      }
+      __syncthreads();
+      if (sm.ctl[5]) break;
+      const uint8_t* wb = reinterpret_cast<const uint8_t*>(&sm) + sm.ctl[17];
+      const uint32_t L = static_cast<uint32_t>(sm.ctl[18]);
+      const uint32_t pos0 = static_cast<uint32_t>(sm.ctl[0]);
+      // bit width 1: a bit-packed run spans its header and a byte per group,
+      // a repeated run its header and one value byte (headers of 1-5 bytes;
+      // the window holds 16 bytes past the tables)
+      for (uint32_t q = tid; q < L; q += blockDim.x) {
+        uint32_t h = wb[q], hl = 1;
+        if (h & 0x80u) {
+          h &= 0x7fu;
+          for (uint32_t k = 1; k < 5; ++k) {
+            const uint32_t bk = wb[q + k];
+            h |= (bk & 0x7fu) << (7 * k);
+            ++hl;
+            if (!(bk & 0x80u)) break;
+            if (k == 4) hl = 0;  // longer than five bytes: left to the serial walk
+          }
+        }
+        const uint64_t nx = static_cast<uint64_t>(q) + hl + ((h & 1u) ? (h >> 1) : 1u);
+        const uint16_t v = !hl || nx >= L ? JSENT : static_cast<uint16_t>(nx);
+        j1[q] = v;
+        ja[q] = v;
+      }
+      __syncthreads();
+      uint16_t* src = ja;
+      uint16_t* dst = jb;
+#pragma unroll 1
+      for (int r = 0; r < 5; ++r) {  // 2, 4, 8, 16, 32 runs
+        for (uint32_t q = tid; q < L; q += blockDim.x) {
+          const uint16_t m = src[q];
+          dst[q] = m == JSENT ? JSENT : src[m];
+        }
+        __syncthreads();
+        uint16_t* t = src;
+        src = dst;
+        dst = t;
+      }
+      if (tid == 0) {
+        int nb = 0, nh = 0;
+        uint32_t q = 0;
+        while (L > 0 && nb + 32 <= RB && src[q] != JSENT) {
+          sm.hop[nh++] = q;
+          nb += 32;
+          q = src[q];
+        }
+        while (L > 0 && nb < RB && j1[q] != JSENT) {
+          sm.rpos[nb++] = pos0 + q;
+          q = j1[q];
+        }
+        sm.ctl[19] = nh;
+        sm.ctl[2] = nb;
+        if (nb) sm.ctl[0] = static_cast<int32_t>(pos0 + q);
+      }
+      __syncthreads();
+      const int nh = sm.ctl[19];
+      for (int h = tid; h < nh; h += blockDim.x) {
+        uint32_t q = sm.hop[h];
+#pragma unroll 4
+        for (int k = 0; k < 32; ++k) {
+          sm.rpos[32 * h + k] = pos0 + q;
+          q = j1[q];
+        }
+      }
+      jumped = sm.ctl[2] > 0;
+      if (jumped) {
+        lb = wb;
+        lp0 = pos0;
+      }
+      __syncthreads();
+    }
     // thread 0 follows the chain and records only each run's header
     // offset; the block decodes the headers of the batch afterwards
-    if (tid == 0) {
+    if (!jumped && tid == 0) {
       uint32_t pos = static_cast<uint32_t>(sm.ctl[0]);
       int32_t row = sm.ctl[1];
       int nb = 0, err = 0;
@@ -727,13 +849,13 @@ __device__ int32_t walk_levels(WalkSmem& sm, const PageCtx& pc, const PlanPage& 
         if (j < nb) {
           const uint32_t hp = sm.rpos[j];
           uint64_t h = 0;
-          const int hl = uleb([&](uint32_t x) { return static_cast<uint32_t>(__ldg(lsb + x)); }, hp, slen, &h);
+          const int hl = uleb([&](uint32_t x) { return static_cast<uint32_t>(lb[x - lp0]); }, hp, slen, &h);
           if (!hl) bad = 1;
           const bool packed = h & 1;
           const uint64_t cnt = packed ? (h >> 1) * 8 : h >> 1;
           dpos[q] = hp + hl;
           if (!packed) {
-            meta[q] = hp + hl < slen ? __ldg(lsb + hp + hl) : 2u;
+            meta[q] = hp + hl < slen ? static_cast<uint32_t>(lb[hp + hl - lp0]) : 2u;
             if (meta[q] > 1) bad = 1;
           } else {
             meta[q] = 0x80000000u;
@@ -773,7 +895,7 @@ __device__ int32_t walk_levels(WalkSmem& sm, const PageCtx& pc, const PlanPage& 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = tid * 4 + q;
-      loc[q] = j < nb ? run_valid(sm, lsb, j, sm.rcnt[j]) : 0;
+      loc[q] = j < nb ? run_valid(sm, lb, lp0, j, sm.rcnt[j]) : 0;
       mine += loc[q];
     }
     int32_t total;
@@ -810,7 +932,7 @@ __device__ int32_t walk_levels(WalkSmem& sm, const PageCtx& pc, const PlanPage& 
             const uint32_t meta = sm.rmeta[j];
             uint32_t bitsv;
             if (meta & 0x80000000u)
-              bitsv = gbits32(lsb, static_cast<uint64_t>(sm.rpos[j]) * 8 + (r - sm.rk[j]), n);
+              bitsv = lbits32(lb, static_cast<uint64_t>(sm.rpos[j] - lp0) * 8 + (r - sm.rk[j]), n);
             else
               bitsv = meta ? (n == 32 ? 0xffffffffu : ((1u << n) - 1u)) : 0u;
             word |= bitsv << static_cast<uint32_t>((pp.out_row + r) - w * 32);
@@ -828,7 +950,7 @@ __device__ int32_t walk_levels(WalkSmem& sm, const PageCtx& pc, const PlanPage& 
       const int32_t R = i < pp.item_count ? items[pp.item_begin + i].row0 : pp.row_hi;
       if (nb > 0 && R >= b0 && R < b1) {
         const int j = find_run(sm.rk, nb, R);
-        const int32_t kR = sm.rpre[j] + run_valid(sm, lsb, j, R - sm.rk[j]);
+        const int32_t kR = sm.rpre[j] + run_valid(sm, lb, lp0, j, R - sm.rk[j]);
         if (i < pp.item_count)
           items[pp.item_begin + i].k0 = kR;
         else
@@ -1329,22 +1451,23 @@ __device__ void walk_page(const DecodeArgs& a, int p, WalkSmem& sm, bool serial_
   __syncthreads();
 }
 
-__device__ __forceinline__ void walk_init(WalkSmem& sm, uint32_t cap) {
+__device__ __forceinline__ void walk_init(WalkSmem& sm, uint32_t cap, uint32_t jw = 0) {
   if (threadIdx.x == 0) {
     mbar_init(&sm.bar[0], 1);
     mbar_init(&sm.bar[1], 1);
     fence_mbar_init();
     sm.ctl[13] = static_cast<int32_t>(cap);
     sm.ctl[14] = sm.ctl[15] = 0;
+    sm.ctl[16] = static_cast<int32_t>(jw);
   }
   __syncthreads();
 }
 
 // One thread block per page of walk list entries [wbegin, wbegin + gridDim.x).
-__global__ void __launch_bounds__(WALK_THREADS) k_walk(DecodeArgs a, int wbegin, uint32_t cap) {
+__global__ void __launch_bounds__(WALK_THREADS, 4) k_walk(DecodeArgs a, int wbegin, uint32_t cap, uint32_t jw) {
   extern __shared__ __align__(16) uint8_t smraw[];
   WalkSmem& sm = *reinterpret_cast<WalkSmem*>(smraw);
-  walk_init(sm, cap);
+  walk_init(sm, cap, jw);
   walk_page(a, static_cast<int>(a.walk_pps[wbegin + blockIdx.x]), sm, false);
 }
 
@@ -2905,7 +3028,7 @@ static int g_walk_bps = 0, g_exp_bps = 0;
 
 int walk_blocks_per_sm() {
   if (!g_walk_bps) {
-    cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, walk_smem_bytes(CWIN_MAX));
+    cudaFuncSetAttribute(k_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, walk_smem_bytes(CWIN_MAX, JW));
     cudaFuncSetAttribute(k_plain_page, cudaFuncAttributeMaxDynamicSharedMemorySize, walk_smem_bytes(CWIN));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_walk_bps, k_walk, WALK_THREADS, walk_smem_bytes(CWIN));
     if (g_walk_bps < 1) g_walk_bps = 1;
@@ -2921,13 +3044,17 @@ int expand_blocks_per_sm() {
   return g_exp_bps;
 }
 
-void launch_walk(const DecodeArgs& a, int wbegin, int n, int n_sms, cudaStream_t s) {
+void launch_walk(const DecodeArgs& a, int wbegin, int n, int n_sms, bool levels, cudaStream_t s) {
   if (n <= 0) return;
   walk_blocks_per_sm();  // sets the shared-memory attributes
   // few pages (long chains each): larger windows, fewer refills on the
   // chain's path; many pages: more resident walkers
   const uint32_t cap = n <= n_sms ? CWIN_MAX : (n <= 2 * n_sms ? CWIN_MAX / 2 : CWIN);
-  k_walk<<<n, WALK_THREADS, walk_smem_bytes(cap), s>>>(a, wbegin, cap);
+  // level walks: smaller chain windows, so that the jump tables leave room
+  // for as many resident walkers
+  const uint32_t jw = levels ? JW : 0u;
+  const uint32_t wcap = levels && cap > CWIN / 2 ? CWIN / 2 : cap;
+  k_walk<<<n, WALK_THREADS, walk_smem_bytes(wcap, jw), s>>>(a, wbegin, wcap, jw);
 }
 
 void launch_delta_bases(const DecodeArgs& a, int dbegin, int n, int max_regions, cudaStream_t s) {
