@@ -924,7 +924,7 @@ pq_status plan_upload(pq_plan* plan) {
   plan->d_status = plan_alloc(pqi::DevStatus, plan, 1);
   plan->d_scratch = scratch ? plan_alloc(uint8_t, plan, scratch + 64) : nullptr;
   const uint64_t str_rows = static_cast<uint64_t>(plan->n_rows) * plan->str_cols.size();
-  plan->d_str_scratch = str_rows ? plan_alloc(uint32_t, plan, str_rows) : nullptr;
+  plan->d_str_scratch = str_rows ? plan_alloc(uint64_t, plan, str_rows) : nullptr;
   plan->d_str_items = plan->str_cols.empty() ? nullptr : plan_alloc(uint64_t, plan, nit);
   for (void* p : plan->owned)
     if (!p) {
@@ -935,7 +935,7 @@ pq_status plan_upload(pq_plan* plan) {
     free_plan_device(plan);
     return fail(ctx, PQ_ERR_OOM, "plan scratch");
   }
-  plan->scratch_bytes = scratch + str_rows * 4 + (plan->d_str_items ? nit * 8 : 0) + plan->delta_blocks * 12 +
+  plan->scratch_bytes = scratch + str_rows * 8 + (plan->d_str_items ? nit * 8 : 0) + plan->delta_blocks * 12 +
                         plan->delta_regions * (sizeof(pqi::DeltaRegion) + 4ull * pqi::DELTA_REGION_LIST);
   // rebase scratch bodies, string scratch per column
   size_t jd = 0;
@@ -1031,7 +1031,7 @@ uint64_t plan_device_bytes(const pq_plan* plan, uint64_t scratch) {
          plan->delta_blocks * 12 +
          plan->delta_regions * (sizeof(pqi::DeltaRegion) + 4ull * pqi::DELTA_REGION_LIST) +
          plan->dict_regions * (sizeof(pqi::DeltaRegion) + 4ull * pqi::STR_REGION_LIST) + scratch + 64 +
-         str_rows * 4 + (plan->str_cols.empty() ? 0 : nit * 8) + 4096;
+         str_rows * 8 + (plan->str_cols.empty() ? 0 : nit * 8) + 4096;
 }
 
 }  // namespace pqe

@@ -125,7 +125,7 @@ struct pq_plan {
   pqi::DictJob* d_dict_jobs = nullptr;
   int32_t* d_str_cols = nullptr;
   uint8_t* d_scratch = nullptr;
-  uint32_t* d_str_scratch = nullptr;
+  uint64_t* d_str_scratch = nullptr;
   uint64_t* d_str_items = nullptr;
   uint32_t* d_counter = nullptr;
   uint32_t* d_walk_pps = nullptr;

@@ -44,7 +44,6 @@ constexpr uint32_t CWIN = 16384;      // chain window (two per walking block)
 constexpr uint32_t CWIN_MAX = 65536;  // window of walks over few pages
 constexpr uint32_t COVL = 64;     // overlap of consecutive chain windows
 constexpr int RB = 1024;          // runs per walk batch
-constexpr uint32_t NULL_IDX = 0xffffffffu;
 
 // ------------------------------------------------------------------ global bit readers
 
@@ -1992,7 +1991,7 @@ __device__ __forceinline__ void store_val(uint8_t* base, int64_t row, int width,
 // (OPTIONAL, scattered to rows afterwards).
 struct Sink {
   uint8_t* out;
-  uint32_t* sidx;
+  uint64_t* sidx;
   uint64_t* vbuf;
   int64_t orow0;
   int width;
@@ -2000,7 +1999,7 @@ struct Sink {
     if (vbuf)
       vbuf[j] = v;
     else if (sidx)
-      sidx[orow0 + j] = static_cast<uint32_t>(v);
+      sidx[orow0 + j] = v;
     else
       store_val(out, orow0 + j, width, v);
   }
@@ -2149,7 +2148,7 @@ __device__ bool warp_hybrid(const uint8_t* sb, uint32_t slen, int bw, int32_t to
         for (int u = 0; u < U; ++u) {
           const int32_t j = j0 + u * 32 + lane;
           if (j < e) {
-            sink.put(j - k0, idx[u]);
+            sink.put(j - k0, ent[u]);
             *chars += static_cast<uint32_t>(ent[u]);
           }
         }
@@ -2329,7 +2328,7 @@ __device__ bool warp_plain_ba(const uint8_t* sb, uint32_t slen, uint32_t pos, in
       if (pos + 4 > slen) { ok = 0; break; }
       const uint32_t len = ld_le32_g(sb + pos);
       if (len > slen - pos - 4) { ok = 0; break; }
-      sink.put(k - k0, pos);
+      sink.put(k - k0, (static_cast<uint64_t>(pos + 4) << 32) | len);
       *chars += len;
       pos += 4 + len;
     }
@@ -2491,7 +2490,7 @@ __device__ void expand_item(const DecodeArgs& a, int it_id, WarpSmem& ws, int la
       const int32_t rr = rank + __popc(bits & ((1u << lane) - 1u));
       if (lane < n) {
         if (isba)
-          col.str_scratch[orow0 + r0 + lane] = valid ? static_cast<uint32_t>(ws.vbuf[rr]) : NULL_IDX;
+          col.str_scratch[orow0 + r0 + lane] = valid ? ws.vbuf[rr] : 0ull;
         else
           store_val(col.values, orow0 + r0 + lane, width, valid ? ws.vbuf[rr] : 0);
       }
@@ -2642,7 +2641,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // assembled in shared memory (lanes place their own string) and written out
 // with aligned 16-byte stores, bytes only at the chunk's two ends.  Longer
 // strings are read straight from global memory.
-constexpr int STR_STAGE = 2048;
+constexpr int STR_STAGE = 2016;
 constexpr int STR_RAW_BLK = 4;  // strings up to 49 bytes go through the async copies
 constexpr int STR_SLOT = STR_RAW_BLK + 1;  // slot stride in 16-byte blocks (spreads lanes over banks)
 struct StrWarpSmem {
@@ -2651,7 +2650,7 @@ struct StrWarpSmem {
 };
 constexpr int STR_SMEM = 8 * sizeof(StrWarpSmem);
 
-__global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a, int c) {
+__global__ void __launch_bounds__(256, 4) k_str_copy(DecodeArgs a, int c) {
   extern __shared__ __align__(16) uint8_t str_smem[];
   StrWarpSmem& ws = reinterpret_cast<StrWarpSmem*>(str_smem)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
@@ -2683,23 +2682,11 @@ __global__ void __launch_bounds__(256) k_str_copy(DecodeArgs a, int c) {
     for (int g0 = 0; g0 < it.nrows; g0 += 256) {
       // metadata of 4 chunks of 64 strings, loads issued together; lane l
       // takes rows 2l and 2l+1 of each chunk (adjacent in the output)
-      uint32_t sidx[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int r = g0 + (u >> 1) * 64 + 2 * lane + (u & 1);
-        sidx[u] = r < it.nrows ? col.str_scratch[orow0 + r] : NULL_IDX;
-      }
       uint64_t ent[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        ent[u] = 0;
-        if (sidx[u] != NULL_IDX) {
-          if (isdict) {
-            ent[u] = __ldg(dd.str_ent + sidx[u]);
-          } else {
-            ent[u] = (static_cast<uint64_t>(sidx[u] + 4) << 32) | ld_le32_g(sb + sidx[u]);
-          }
-        }
+        const int r = g0 + (u >> 1) * 64 + 2 * lane + (u & 1);
+        ent[u] = r < it.nrows ? col.str_scratch[orow0 + r] : 0ull;
       }
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {

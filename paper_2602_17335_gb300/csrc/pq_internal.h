@@ -161,7 +161,9 @@ struct OutCol {
   int32_t width;
   int32_t optional;
   int32_t pad;
-  uint32_t* str_scratch; // BYTE_ARRAY: per-row dictionary index / value offset
+  uint64_t* str_scratch; // BYTE_ARRAY: per row (offset of its chars << 32) | its length, the
+                         // offset into the dictionary page (dictionary pages) or the page's
+                         // values (PLAIN pages); 0 for a null
   uint64_t* str_item_bytes; // BYTE_ARRAY: chars bytes per item, then exclusive prefix
   uint32_t item_begin;   // items of this column are contiguous in item order
   uint32_t item_count;
