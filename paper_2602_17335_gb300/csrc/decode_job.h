@@ -26,11 +26,11 @@ struct DictJob {
 
 // Chain regions of PLAIN BYTE_ARRAY dictionary pages: (4-byte length, bytes)
 // entries are found per STR_REGION bytes in parallel, then stitched.
-constexpr int STR_REGION = 16384;
+constexpr int STR_REGION = 4096;
 constexpr int STR_REGION_LIST = STR_REGION / 4 + 2;  // entries are >= 4 bytes
 struct DictScratch {
   DeltaRegion* regs;    // one summary per region
-  uint32_t* lists;      // STR_REGION_LIST entry offsets per region
+  uint64_t* lists;      // STR_REGION_LIST entries per region, (chars offset << 32) | length
 };
 
 struct DecodeArgs {

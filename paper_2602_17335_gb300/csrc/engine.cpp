@@ -913,7 +913,7 @@ pq_status plan_upload(pq_plan* plan) {
   plan->d_dregs = plan_alloc(pqi::DeltaRegion, plan, plan->delta_regions);
   plan->d_dreg_lists = plan_alloc(uint32_t, plan, plan->delta_regions * pqi::DELTA_REGION_LIST);
   plan->d_sregs = plan_alloc(pqi::DeltaRegion, plan, plan->dict_regions);
-  plan->d_slists = plan_alloc(uint32_t, plan, plan->dict_regions * pqi::STR_REGION_LIST);
+  plan->d_slists = plan_alloc(uint64_t, plan, plan->dict_regions * pqi::STR_REGION_LIST);
   plan->d_pps = plan_alloc(pqi::PlanPage, plan, npp);
   plan->d_items = plan_alloc(pqi::Item, plan, nit);
   plan->d_cols = plan_alloc(pqi::OutCol, plan, plan->outcols.size());
@@ -1030,7 +1030,7 @@ uint64_t plan_device_bytes(const pq_plan* plan, uint64_t scratch) {
          plan->dict_jobs.size() * sizeof(pqi::DictJob) + 4 * (plan->walk_pps.size() + plan->delta_pps.size()) +
          plan->delta_blocks * 12 +
          plan->delta_regions * (sizeof(pqi::DeltaRegion) + 4ull * pqi::DELTA_REGION_LIST) +
-         plan->dict_regions * (sizeof(pqi::DeltaRegion) + 4ull * pqi::STR_REGION_LIST) + scratch + 64 +
+         plan->dict_regions * (sizeof(pqi::DeltaRegion) + 8ull * pqi::STR_REGION_LIST) + scratch + 64 +
          str_rows * 8 + (plan->str_cols.empty() ? 0 : nit * 8) + 4096;
 }
 

@@ -135,7 +135,7 @@ struct pq_plan {
   pqi::DeltaRegion* d_dregs = nullptr;
   uint32_t* d_dreg_lists = nullptr;
   pqi::DeltaRegion* d_sregs = nullptr;
-  uint32_t* d_slists = nullptr;
+  uint64_t* d_slists = nullptr;
   pqi::DevStatus* d_status = nullptr;
   std::vector<void*> owned;                  // pool blocks to release
   // host staging (pinned): output descriptors in, status + string totals out

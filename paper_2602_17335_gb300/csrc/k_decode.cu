@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(32) k_sreg(const DictJob* __restrict__ jobs, D
   const int i = blockIdx.x;
   const uint32_t blen = static_cast<uint32_t>(j.body_len);
   DeltaRegion* R = ds.regs + j.sreg + i;
-  uint32_t* list = ds.lists + static_cast<uint64_t>(j.sreg + i) * STR_REGION_LIST;
+  uint64_t* list = ds.lists + static_cast<uint64_t>(j.sreg + i) * STR_REGION_LIST;
   const uint64_t start64 = static_cast<uint64_t>(i) * STR_REGION;
   if (start64 >= blen) {
     if (lane == 0) *R = DeltaRegion{-1, -1, 0, 0};
@@ -377,10 +377,11 @@ __global__ void __launch_bounds__(32) k_sreg(const DictJob* __restrict__ jobs, D
       const uint32_t cand = c0 + lane;
       bool good = cand < end;
       uint32_t p = cand;
+      // four entries in a row, each decided from the staged bytes (a
+      // look-alike length can jump past them: undecided is not plausible)
       for (int k = 0; good && k < 4 && p < blen; ++k) {
         const uint32_t nx = next(p);
-        if (nx == 0u) good = false;
-        else if (nx == 0xffffffffu) break;
+        if (nx == 0u || nx == 0xffffffffu) good = false;
         else p = nx;
       }
       const uint32_t m = __ballot_sync(0xffffffffu, good);
@@ -396,12 +397,14 @@ __global__ void __launch_bounds__(32) k_sreg(const DictJob* __restrict__ jobs, D
           x = static_cast<int32_t>(p);
           break;
         }
+        const uint32_t nx = next(p);
         if (p >= start) {
           if (cnt == STR_REGION_LIST) break;
           if (first < 0) first = static_cast<int32_t>(p);
-          list[cnt++] = p;
+          // the entry as the dictionary holds it, when its length is known
+          list[cnt++] = nx == 0u || nx == 0xffffffffu ? (static_cast<uint64_t>(p + 4) << 32) | 0xffffffffu
+                                                      : (static_cast<uint64_t>(p + 4) << 32) | (nx - p - 4);
         }
-        const uint32_t nx = next(p);
         if (nx == 0u || nx == 0xffffffffu) break;  // a look-alike chain
         p = nx;
       }
@@ -417,7 +420,7 @@ __global__ void __launch_bounds__(32) k_sreg(const DictJob* __restrict__ jobs, D
 // entries written directly.
 __global__ void __launch_bounds__(256) k_sfix(const DictJob* __restrict__ jobs, DictScratch ds, DictDev* dicts,
                                               DevStatus* st) {
-  constexpr int MAXR = 512;
+  constexpr int MAXR = 2048;
   __shared__ int32_t s_q[MAXR], s_x[MAXR], s_c[MAXR];
   __shared__ int32_t s_skip[MAXR], s_base[MAXR];
   __shared__ int32_t s_nreg, s_ok;
@@ -507,11 +510,8 @@ __global__ void __launch_bounds__(256) k_sfix(const DictJob* __restrict__ jobs, 
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = threadIdx.x >> 5; i < s_nreg; i += nw) {
     if (s_skip[i] <= 0) continue;
-    const uint32_t* list = ds.lists + static_cast<uint64_t>(j.sreg + i) * STR_REGION_LIST;
-    for (int k = lane; k < s_skip[i]; k += 32) {
-      const uint32_t p = list[k];
-      j.str_ent[s_base[i] + k] = (static_cast<uint64_t>(p + 4) << 32) | ld_le32_g(j.body + p);
-    }
+    const uint64_t* list = ds.lists + static_cast<uint64_t>(j.sreg + i) * STR_REGION_LIST;
+    for (int k = lane; k < s_skip[i]; k += 32) j.str_ent[s_base[i] + k] = list[k];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
