@@ -46,7 +46,7 @@ MiB = 1 << 20
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rows", type=int, default=1 << 26)
@@ -155,6 +155,11 @@ class ClockSampler:
             self.lines = []
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # the timed region starts once the sampler delivers samples
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.lines.clear()
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -247,13 +252,16 @@ def run_reference(a, rank, world):
     """The CPU oracle on the same workload (bounded sample per step)."""
     if rank != 0:
         return
-    data = make_files(a, 0)
+    data = bytes(make_files(a, 0))
+    # each step a bounded sample, sized so that the whole run stays within a
+    # few minutes
+    per_step = max(0.5, min(20.0, 150.0 / max(1, a.steps + a.warmup)))
     for _ in range(a.warmup):
-        oracle_sample(data, max_seconds=5.0)
+        oracle_sample(data, max_seconds=per_step)
     tot_b, tot_s = 0.0, 0.0
     desc = ""
     for _ in range(a.steps):
-        b, s, desc = oracle_sample(data, max_seconds=20.0)
+        b, s, desc = oracle_sample(data, max_seconds=per_step)
         tot_b += b
         tot_s += s
     value = tot_b / tot_s / 1e9
@@ -406,7 +414,7 @@ def run_ours(a, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        b, s, desc = oracle_sample(data, max_seconds=25.0)
+        b, s, desc = oracle_sample(bytes(data), max_seconds=25.0)
         cpu = {"value": b / s / 1e9, "unit": "GB/s", "cores": cpu_count_used(), "kind": "oracle", "sample": desc,
                "seconds": s}
 

@@ -204,6 +204,40 @@ def test_string_lengths_and_nulls(eng, enc):
     _roundtrip(eng, W.write_file(tab, spec), row_begin=777, row_count=40_001)
 
 
+def test_string_dictionary_chains(eng):
+    """Dictionary pages whose (length, bytes) chain is found per region in
+    parallel: binary strings (bytes that read as small plausible lengths),
+    strings longer than a region, many empty strings, and pools whose
+    dictionary page spans dozens of regions; uncompressed and Snappy."""
+    rng = np.random.default_rng(4242)
+    n = 30_000
+
+    def pool(lens, binary):
+        offs = np.zeros(len(lens) + 1, np.int64)
+        np.cumsum(lens, out=offs[1:])
+        if binary:
+            chars = rng.integers(0, 8, int(offs[-1])).astype(np.uint8)  # mostly bytes 0-7
+        else:
+            chars = rng.integers(65, 91, int(offs[-1])).astype(np.uint8)
+        return offs, chars
+
+    cols = []
+    for name, lens, binary in (
+            ("binary", rng.integers(0, 40, 6000), True),
+            ("long", rng.integers(2000, 9000, 60), False),
+            ("empties", np.where(rng.random(5000) < 0.5, 0, rng.integers(1, 12, 5000)), True),
+            ("mixed", np.where(rng.random(8000) < 0.02, rng.integers(3000, 6000, 8000), rng.integers(0, 20, 8000)),
+             True)):
+        offs, chars = pool(np.asarray(lens, np.int64), binary)
+        k = len(lens)
+        idx = rng.integers(0, k, n).astype(np.int32)
+        cols.append(synth.ColumnData(name, "BYTE_ARRAY", synth.StringData(offs, chars, idx)))
+    tab = synth.Table(cols)
+    for codec in ("UNCOMPRESSED", "SNAPPY"):
+        spec = synth.TableSpec(n, 1 << 20, [synth.ColumnSpec("RLE_DICTIONARY", codec=codec) for _ in cols])
+        _roundtrip(eng, W.write_file(tab, spec))
+
+
 def test_config4_style_mixed_chunks(eng):
     draws = synth.config4_draws(n_files=3, chunks_per_file=4, rows_lo=500, rows_hi=40_000, page_lo=512,
                                 page_hi=64 * 1024)
