@@ -233,6 +233,20 @@ pq_status pq_ctx_get_tuning(const pq_ctx* ctx, pq_tuning* t) {
 
 // ------------------------------------------------------------------ index
 
+// Small device-to-host reads (status words, page counts, the page table)
+// go by a copy kernel into pinned host memory rather than by the copy
+// engine, where they would wait behind bulk transfers of other streams.
+static cudaError_t d2h_small(void* pinned_dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (!bytes) return cudaSuccess;
+  void* dv = nullptr;
+  if (bytes >= (1u << 31) || cudaHostGetDevicePointer(&dv, pinned_dst, 0) != cudaSuccess || !dv) {
+    cudaGetLastError();
+    return cudaMemcpyAsync(pinned_dst, src, bytes, cudaMemcpyDeviceToHost, s);
+  }
+  pqi::launch_copy_small(dv, src, static_cast<uint32_t>(bytes), s);
+  return cudaGetLastError();
+}
+
 static void free_index_device(pq_index* idx) {
   DevPool& pool = idx->ctx->pool;
   pool.free(idx->d_chunks);
@@ -498,9 +512,15 @@ pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi,
     pqi::launch_index_walk(idx->d_chunks, nch, nullptr, d_counts, 0, idx->d_status, s);
     std::vector<uint32_t> counts(nch);
     pqi::DevStatus st{};
-    CK(cudaMemcpyAsync(counts.data(), d_counts, sizeof(uint32_t) * nch, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&st, idx->d_status, sizeof st, cudaMemcpyDeviceToHost, s));
+    if (!ctx->tail.reserve(sizeof st + sizeof(uint32_t) * nch)) {
+      free_index_device(idx.get());
+      return fail(ctx, PQ_ERR_OOM, "pinned staging");
+    }
+    CK(d2h_small(ctx->tail.p, idx->d_status, sizeof st, s));
+    CK(d2h_small(ctx->tail.p + sizeof st, d_counts, sizeof(uint32_t) * nch, s));
     CK(cudaStreamSynchronize(s));
+    memcpy(&st, ctx->tail.p, sizeof st);
+    memcpy(counts.data(), ctx->tail.p + sizeof st, sizeof(uint32_t) * nch);
     pool.free(d_counts);
     if (st.flags) {
       pq_status r = status_from_device(ctx, st);
@@ -523,11 +543,16 @@ pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi,
   // 5. page table back to the host
   idx->pages.resize(n_pages);
   pqi::DevStatus st{};
-  if (n_pages)
-    CK(cudaMemcpyAsync(idx->pages.data(), idx->d_pages, sizeof(pqi::PageDev) * n_pages, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&st, idx->d_status, sizeof st, cudaMemcpyDeviceToHost, s));
+  if (!ctx->tail.reserve(sizeof st + sizeof(pqi::PageDev) * n_pages)) {
+    free_index_device(idx.get());
+    return fail(ctx, PQ_ERR_OOM, "pinned staging");
+  }
+  CK(d2h_small(ctx->tail.p, idx->d_status, sizeof st, s));
+  CK(d2h_small(ctx->tail.p + sizeof st, idx->d_pages, sizeof(pqi::PageDev) * n_pages, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
+  memcpy(&st, ctx->tail.p, sizeof st);
+  if (n_pages) memcpy(idx->pages.data(), ctx->tail.p + sizeof st, sizeof(pqi::PageDev) * n_pages);
   if (st.flags) {
     pq_status r = status_from_device(ctx, st);
     free_index_device(idx.get());
@@ -1217,11 +1242,11 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
   }
   mark(6);
   // status and string totals back to pinned host memory
-  cudaMemcpyAsync(plan->h_out.p, plan->d_status, sizeof(pqi::DevStatus), cudaMemcpyDeviceToHost, s);
+  d2h_small(plan->h_out.p, plan->d_status, sizeof(pqi::DevStatus), s);
   for (size_t i = 0; i < plan->str_cols.size(); ++i) {
     const auto& col = plan->outcols[plan->str_cols[i]];
-    cudaMemcpyAsync(plan->h_out.p + sizeof(pqi::DevStatus) + 8 * i,
-                    reinterpret_cast<int64_t*>(col.values) + plan->n_rows, 8, cudaMemcpyDeviceToHost, s);
+    d2h_small(plan->h_out.p + sizeof(pqi::DevStatus) + 8 * i, reinterpret_cast<int64_t*>(col.values) + plan->n_rows,
+              8, s);
   }
 }
 

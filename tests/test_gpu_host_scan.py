@@ -31,7 +31,16 @@ def ctx():
     N.pq_ctx_destroy(c)
 
 
-def _host_scan(N, ctx, datas, columns, rb, rc):
+def _zeros(n, pinned):
+    """n zero bytes: a numpy array, or a numpy view of pinned host memory
+    (which the scan writes back by a copy kernel rather than by copies)."""
+    if not pinned:
+        return np.zeros(n, np.uint8)
+    import torch
+    return torch.zeros(max(n, 1), dtype=torch.uint8).pin_memory().numpy()[:n]
+
+
+def _host_scan(N, ctx, datas, columns, rb, rc, pinned=False):
     import ctypes as C
     bufs = [np.frombuffer(bytes(d), dtype=np.uint8).copy() for d in datas]
     files = [(b.ctypes.data, b.nbytes) for b in bufs]
@@ -41,17 +50,17 @@ def _host_scan(N, ctx, datas, columns, rb, rc):
     for i in range(n):
         s = sizes[i]
         c = N.pq_column()
-        v = np.zeros(int(s.values_bytes), np.uint8)
+        v = _zeros(int(s.values_bytes), pinned)
         keep.append(v)
         c.values = v.ctypes.data
         m = None
         if s.validity_bytes:
-            m = np.zeros(int(s.validity_bytes), np.uint8)
+            m = _zeros(int(s.validity_bytes), pinned)
             keep.append(m)
             c.validity = m.ctypes.data
         ch = None
         if s.chars_bytes:
-            ch = np.zeros(int(s.chars_bytes), np.uint8)
+            ch = _zeros(int(s.chars_bytes), pinned)
             keep.append(ch)
             c.chars = ch.ctypes.data
             c.chars_capacity = int(s.chars_bytes)
@@ -87,8 +96,8 @@ def _check(sizes, keep, expect_cols, columns):
 
 
 @pytest.mark.parametrize("rb,rc", [(0, -1), (8192, 24576), (100, 30_001)])
-@pytest.mark.parametrize("pipeline", [True, False])
-def test_host_scan_matches_oracle(ctx, rb, rc, pipeline, monkeypatch):
+@pytest.mark.parametrize("pipeline,pinned", [(True, False), (False, False), (True, True)])
+def test_host_scan_matches_oracle(ctx, rb, rc, pipeline, pinned, monkeypatch):
     from paper_2602_17335_gb300 import native as N
     if not pipeline:
         monkeypatch.setenv("PQ_HOST_NO_PIPELINE", "1")
@@ -96,6 +105,6 @@ def test_host_scan_matches_oracle(ctx, rb, rc, pipeline, monkeypatch):
     data = W.write_file(tab, synth.config2_spec(8192, 16 * 1024, "SNAPPY", 2))
     expect = R.read_file(data)
     columns = list(range(8))
-    sizes, keep, _ = _host_scan(N, ctx, [data], columns, rb, rc)
+    sizes, keep, _ = _host_scan(N, ctx, [data], columns, rb, rc, pinned)
     hi = 40_000 if rc < 0 else rb + rc
     _check(sizes, keep, [slice_result(expect[c], rb, hi) for c in columns], columns)
