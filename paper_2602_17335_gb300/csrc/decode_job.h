@@ -20,6 +20,7 @@ struct DictJob {
   int32_t chunk;        // DictDev row
   uint8_t* values;      // fixed width: n * width bytes (16-byte aligned)
   uint64_t* str_ent;    // BYTE_ARRAY: n entries, (chars offset << 32) | length
+  uint8_t* pad;         // BYTE_ARRAY: PAD_STRIDE_MAX * n + 64 bytes for the padded copy
   uint32_t sreg;        // BYTE_ARRAY: first row of the job's chain-region tables
   int32_t sreg_cap;     // BYTE_ARRAY: region rows reserved (body_len / STR_REGION + 2)
 };
@@ -27,6 +28,10 @@ struct DictJob {
 // Chain regions of PLAIN BYTE_ARRAY dictionary pages: (4-byte length, bytes)
 // entries are found per STR_REGION bytes in parallel, then stitched.
 constexpr int STR_REGION = 4096;
+// A string dictionary whose longest entry has at most PAD_STRIDE_MAX bytes is
+// also laid out with entry i at i * stride (stride: the longest entry rounded
+// up to 16 bytes), every entry 16-byte aligned; the entries then point there.
+constexpr int PAD_STRIDE_MAX = 48;
 constexpr int STR_REGION_LIST = STR_REGION / 4 + 2;  // entries are >= 4 bytes
 struct DictScratch {
   DeltaRegion* regs;    // one summary per region

@@ -257,6 +257,7 @@ static void free_index_device(pq_index* idx) {
   for (auto p : idx->dict_values) pool.free(p);
   for (auto p : idx->dict_str_ent) pool.free(p);
   for (auto p : idx->dict_body) pool.free(p);
+  for (auto p : idx->dict_pad) pool.free(p);
 }
 
 void pq_free_index(pq_index* idx) {
@@ -562,6 +563,7 @@ pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi,
   idx->dict_values.assign(nch, nullptr);
   idx->dict_str_ent.assign(nch, nullptr);
   idx->dict_body.assign(nch, nullptr);
+  idx->dict_pad.assign(nch, nullptr);
   idx->dict_resident.assign(nch, 0);
   for (int c = 0; c < nch; ++c) {
     auto& cd = idx->chunks[c];
@@ -588,7 +590,8 @@ pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi,
       const size_t n = static_cast<size_t>(dp.num_values);
       if (cd.ptype == pqi::T_BYTE_ARRAY) {
         idx->dict_str_ent[c] = static_cast<uint64_t*>(pool.alloc(8 * n + 16));
-        if (!idx->dict_str_ent[c]) {
+        idx->dict_pad[c] = static_cast<uint8_t*>(pool.alloc(static_cast<size_t>(pqi::PAD_STRIDE_MAX) * n + 64));
+        if (!idx->dict_str_ent[c] || !idx->dict_pad[c]) {
           free_index_device(idx.get());
           return fail(ctx, PQ_ERR_OOM, "dictionary");
         }
@@ -800,6 +803,7 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
           dj.chunk = static_cast<int32_t>(ch);
           dj.values = idx->dict_values[ch];
           dj.str_ent = idx->dict_str_ent[ch];
+          dj.pad = idx->dict_pad[ch];
           if (cd.ptype == pqi::T_BYTE_ARRAY) {
             dj.sreg = static_cast<uint32_t>(plan->dict_regions);
             dj.sreg_cap = static_cast<int32_t>(dp.uncompressed / pqi::STR_REGION + 2);

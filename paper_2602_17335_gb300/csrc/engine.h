@@ -80,6 +80,7 @@ struct pq_index {
   std::vector<uint8_t*> dict_values;
   std::vector<uint64_t*> dict_str_ent;
   std::vector<uint8_t*> dict_body;        // decompressed dictionary page (compressed chunks)
+  std::vector<uint8_t*> dict_pad;         // BYTE_ARRAY: the dictionary's 16-byte aligned copy
   std::vector<uint8_t> dict_resident;     // 1 once decoded and kept
   uint64_t stored_bytes = 0;
   uint64_t uncompressed_bytes = 0;

@@ -514,13 +514,53 @@ __global__ void __launch_bounds__(256) k_sfix(const DictJob* __restrict__ jobs, 
     for (int k = lane; k < s_skip[i]; k += 32) j.str_ent[s_base[i] + k] = list[k];
   }
   __syncthreads();
+  // longest entry: picks the padded layout (copied by k_dict_pad)
+  __shared__ int32_t s_max;
+  if (threadIdx.x == 0) s_max = 0;
+  __syncthreads();
+  int32_t mx = 0;
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int32_t L = static_cast<int32_t>(static_cast<uint32_t>(j.str_ent[i]));
+    mx = L > mx ? L : mx;
+  }
+  atomicMax(&s_max, mx);
+  __syncthreads();
   if (threadIdx.x == 0) {
     DictDev d{};
     d.str_ent = j.str_ent;
-    d.chars = j.body;
     d.n = n;
+    d.max_len = s_max;
+    d.chars = j.pad && n > 0 && s_max <= PAD_STRIDE_MAX ? j.pad : j.body;
     d.valid = 1;
     dicts[j.chunk] = d;
+  }
+}
+
+// Padded copy of the string dictionaries k_sfix marked for it: thread i
+// copies entry i (aligned words, the last one masked) to pad + i * stride
+// and points the entry there.  The bytes after an entry up to the next
+// stride are left as they are (never read as data).
+__global__ void __launch_bounds__(256) k_dict_pad(const DictJob* __restrict__ jobs, const DictDev* dicts) {
+  const DictJob j = jobs[blockIdx.y];
+  if (j.ptype != T_BYTE_ARRAY || !j.pad) return;
+  const DictDev d = dicts[j.chunk];
+  if (!d.valid || d.chars != j.pad) return;
+  const uint32_t stride = (static_cast<uint32_t>(d.max_len) + 15u) & ~15u;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < j.n; i += gridDim.x * blockDim.x) {
+    const uint64_t e = j.str_ent[i];
+    const uint32_t len = static_cast<uint32_t>(e);
+    const uint8_t* src = j.body + (e >> 32);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(j.pad + static_cast<uint64_t>(i) * stride);
+    const uint32_t* q = reinterpret_cast<const uint32_t*>(reinterpret_cast<uintptr_t>(src) & ~uintptr_t(3));
+    const uint32_t sh = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 3) * 8;
+    const uint32_t nw = (len + 3) >> 2;
+    uint32_t cur = nw ? q[0] : 0u;
+    for (uint32_t k = 0; k < nw; ++k) {
+      const uint32_t nx = q[k + 1];
+      dst[k] = __funnelshift_r(cur, nx, sh);
+      cur = nx;
+    }
+    j.str_ent[i] = (static_cast<uint64_t>(static_cast<uint64_t>(i) * stride) << 32) | len;
   }
 }
 
@@ -539,6 +579,7 @@ void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, int max_s
     }
     k_sreg<<<dim3(max_str_regions, n_jobs), 32, SREG_SMEM, s>>>(jobs, ds, st);
     k_sfix<<<n_jobs, 256, 0, s>>>(jobs, ds, dicts, st);
+    k_dict_pad<<<dim3(32, n_jobs), 256, 0, s>>>(jobs, dicts);
   }
 }
 
