@@ -75,9 +75,8 @@ void launch_plain_pages(const DecodeArgs& a, int pp_begin, int n, cudaStream_t s
 void launch_prepare(const DecodeArgs& a, int n_cols, int grid, cudaStream_t s);
 // offs[0..n) += base (string offsets of a slice placed after earlier slices).
 void launch_add_offsets(int64_t* offs, int64_t n, int64_t base, cudaStream_t s);
-// device memory -> memory the device reaches by stores (pinned host memory)
-void launch_copy_out(void* dst, const void* src, uint64_t bytes, cudaStream_t s);
-// the same for small transfers, reading exactly `bytes` bytes
+// device memory -> pinned host memory for small control transfers (by
+// stores rather than the copy engine), reading exactly `bytes` bytes
 void launch_copy_small(void* dst, const void* src, uint32_t bytes, cudaStream_t s);
 // Fills the work items of plan pages [0, n_pp) from their item ranges.
 void launch_make_items(const DecodeArgs& a, int n_pp, cudaStream_t s);

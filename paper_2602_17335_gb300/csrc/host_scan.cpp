@@ -165,48 +165,18 @@ pq_status scan_pipelined(pq_ctx* ctx, const pq_file* host_files, int n_files, co
       const auto& cm = metas[0].columns[cols[c]];
       const bool ba = cm.type == PQ_TYPE_BYTE_ARRAY;
       const int w = ba ? 8 : pqi::type_width(cm.type);
-      // +32: the copy-out kernel reads up to 16 bytes past what it copies
-      sl.outs[c].values = g.alloc(static_cast<size_t>(max_rows + 1) * w + 32);
-      if (cm.repetition == 1) sl.outs[c].validity = static_cast<uint32_t*>(g.alloc((max_rows + 31) / 32 * 4 + 32));
+      sl.outs[c].values = g.alloc(static_cast<size_t>(max_rows + 1) * w);
+      if (cm.repetition == 1) sl.outs[c].validity = static_cast<uint32_t*>(g.alloc((max_rows + 31) / 32 * 4));
       if (ba) {
-        sl.outs[c].chars = static_cast<uint8_t*>(g.alloc(static_cast<size_t>(max_chars[c]) + 48));
+        sl.outs[c].chars = static_cast<uint8_t*>(g.alloc(static_cast<size_t>(max_chars[c]) + 16));
         sl.outs[c].chars_capacity = static_cast<uint64_t>(max_chars[c]) + 16;
       }
       if (!sl.outs[c].values || (cm.repetition == 1 && !sl.outs[c].validity) || (ba && !sl.outs[c].chars))
         return fail(ctx, PQ_ERR_OOM, "slot outputs");
     }
   }
-  // Columns go back by a copy kernel when the host buffer is pinned memory
-  // the device can store to (device address of its first byte, else null),
-  // so that the copy engine stays free for the small transfers of indexing
-  // and planning; other buffers by copies.
-  auto device_view = [&](const void* p) -> uint8_t* {
-    if (!p) return nullptr;
-    cudaPointerAttributes at{};
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    return at.type == cudaMemoryTypeHost ? static_cast<uint8_t*>(at.devicePointer) : nullptr;
-  };
-  std::vector<uint8_t*> dv_values(cols.size()), dv_valid(cols.size()), dv_chars(cols.size());
-  for (size_t c = 0; c < cols.size(); ++c) {
-    dv_values[c] = device_view(host_outs[c].values);
-    dv_valid[c] = device_view(host_outs[c].validity);
-    dv_chars[c] = device_view(host_outs[c].chars);
-  }
-  // The copy kernels go in slices of 16 MB: the scan kernels of the next row
-  // group fill the GPU, and a copy kernel holding SMs for milliseconds would
-  // keep their last blocks from starting.
-  auto copy_out = [&](uint8_t* dview, void* host, const void* src, size_t bytes) -> cudaError_t {
-    if (!bytes) return cudaSuccess;
-    if (dview) {
-      constexpr size_t kSlice = size_t(16) << 20;
-      for (size_t o = 0; o < bytes; o += kSlice)
-        pqi::launch_copy_out(dview + o, static_cast<const uint8_t*>(src) + o, std::min(kSlice, bytes - o), g.sd);
-      return cudaGetLastError();
-    }
-    return cudaMemcpyAsync(host, src, bytes, cudaMemcpyDeviceToHost, g.sd);
+  auto copy_out = [&](void* host, const void* src, size_t bytes) -> cudaError_t {
+    return bytes ? cudaMemcpyAsync(host, src, bytes, cudaMemcpyDeviceToHost, g.sd) : cudaSuccess;
   };
   // copy-in of unit k into its slot, once the slot's previous copy-out is done
   auto copy_in = [&](size_t k) -> pq_status {
@@ -274,17 +244,14 @@ pq_status scan_pipelined(pq_ctx* ctx, const pq_file* host_files, int n_files, co
       uint8_t* hv = static_cast<uint8_t*>(host_outs[c].values);
       const bool ba = z.type == PQ_TYPE_BYTE_ARRAY;
       const int64_t w = ba ? 8 : pqi::type_width(z.type);
-      cudaError_t e = copy_out(dv_values[c] ? dv_values[c] + u.out0 * w : nullptr, hv + u.out0 * w, sl.outs[c].values,
-                               static_cast<size_t>((n + (ba ? 1 : 0)) * w));
+      cudaError_t e = copy_out(hv + u.out0 * w, sl.outs[c].values, static_cast<size_t>((n + (ba ? 1 : 0)) * w));
       if (e == cudaSuccess && z.optional)
-        e = copy_out(dv_valid[c] ? dv_valid[c] + u.out0 / 8 : nullptr,
-                     reinterpret_cast<uint8_t*>(host_outs[c].validity) + u.out0 / 8, sl.outs[c].validity,
+        e = copy_out(reinterpret_cast<uint8_t*>(host_outs[c].validity) + u.out0 / 8, sl.outs[c].validity,
                      static_cast<size_t>((n + 31) / 32 * 4));
       if (e == cudaSuccess && ba && chars[c]) {
         if (static_cast<uint64_t>(chars_base[c]) + chars[c] > host_outs[c].chars_capacity)
           return fail(ctx, PQ_ERR_CAPACITY, "host chars buffer smaller than the scanned chars");
-        e = copy_out(dv_chars[c] ? dv_chars[c] + chars_base[c] : nullptr, host_outs[c].chars + chars_base[c],
-                     sl.outs[c].chars, chars[c]);
+        e = copy_out(host_outs[c].chars + chars_base[c], sl.outs[c].chars, chars[c]);
       }
       if (e != cudaSuccess) return fail(ctx, PQ_ERR_CUDA, "device-to-host copy");
       chars_base[c] += static_cast<int64_t>(chars[c]);

@@ -2935,20 +2935,6 @@ __global__ void k_add_offsets(int64_t* offs, int64_t n, int64_t base) {
     offs[i] += base;
 }
 
-// Copies `bytes` bytes from device memory to memory the device reaches by
-// stores (pinned host memory): warps take 64 KB slices, each a warp_copy
-// (aligned 16-byte stores after a byte-wise head).
-__global__ void __launch_bounds__(128) k_copy_out(uint8_t* dst, const uint8_t* src, uint64_t bytes) {
-  constexpr uint64_t kSlice = 65536;
-  const int lane = threadIdx.x & 31;
-  const uint64_t w0 = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5;
-  const uint64_t nw = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
-  for (uint64_t s0 = w0 * kSlice; s0 < bytes; s0 += nw * kSlice) {
-    const uint64_t n = bytes - s0 < kSlice ? bytes - s0 : kSlice;
-    warp_copy<true>(dst + s0, src + s0, n, lane);
-  }
-}
-
 // Exactly `bytes` bytes (no read past them), 4-byte words when both ends
 // allow: small control transfers into pinned host memory.
 __global__ void k_copy_small(uint8_t* dst, const uint8_t* src, uint32_t bytes) {
@@ -2967,13 +2953,6 @@ void launch_copy_small(void* dst, const void* src, uint32_t bytes, cudaStream_t 
   if (!bytes) return;
   const uint32_t blocks = std::min<uint32_t>((bytes / 4 + 255) / 256 + 1, 32);
   k_copy_small<<<blocks, 256, 0, s>>>(static_cast<uint8_t*>(dst), static_cast<const uint8_t*>(src), bytes);
-}
-
-void launch_copy_out(void* dst, const void* src, uint64_t bytes, cudaStream_t s) {
-  if (!bytes) return;
-  const uint64_t slices = (bytes + 65535) / 65536;
-  const unsigned blocks = static_cast<unsigned>(std::min<uint64_t>((slices + 3) / 4, 128));
-  k_copy_out<<<blocks, 128, 0, s>>>(static_cast<uint8_t*>(dst), static_cast<const uint8_t*>(src), bytes);
 }
 
 void launch_add_offsets(int64_t* offs, int64_t n, int64_t base, cudaStream_t s) {
