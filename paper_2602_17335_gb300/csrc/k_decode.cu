@@ -1990,7 +1990,7 @@ __device__ void delta_scan_page(const DecodeArgs& a, int p, uint64_t* tmp) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) k_delta_scan(DecodeArgs a, int dbegin) {
+__global__ void __launch_bounds__(1024) k_delta_scan(DecodeArgs a, int dbegin) {
   __shared__ uint64_t tmp[32];
   delta_scan_page(a, static_cast<int>(a.delta_pps[dbegin + blockIdx.x]), tmp);
 }
@@ -2570,7 +2570,7 @@ __global__ void __launch_bounds__(EXP_THREADS, 4) k_expand(DecodeArgs a, int ibe
 // ------------------------------------------------------------------ strings
 
 // Per string column: exclusive prefix of item chars; writes the final offset.
-__global__ void k_str_scan(DecodeArgs a, int c) {
+__global__ void __launch_bounds__(1024) k_str_scan(DecodeArgs a, int c) {
   const OutCol col = a.cols[c];
   __shared__ uint64_t tmp[32];
   __shared__ uint64_t carry;
@@ -3118,7 +3118,7 @@ void launch_delta_bases(const DecodeArgs& a, int dbegin, int n, int max_regions,
     k_dfix<<<n, 256, 0, s>>>(a, dbegin);
   }
   k_delta_sums<<<dim3(64, n), 256, 0, s>>>(a, dbegin);
-  k_delta_scan<<<n, 256, 0, s>>>(a, dbegin);
+  k_delta_scan<<<n, 1024, 0, s>>>(a, dbegin);
 }
 
 void launch_copy_items(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, int ctas_per_sm,
@@ -3146,7 +3146,7 @@ void launch_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, 
 
 void launch_strings(const DecodeArgs& a, int col, int n_items, int n_sms, cudaStream_t s) {
   if (n_items <= 0) return;
-  k_str_scan<<<1, 256, 0, s>>>(a, col);
+  k_str_scan<<<1, 1024, 0, s>>>(a, col);
   int blocks = (n_items + 7) / 8;
   if (blocks > n_sms * 8) blocks = n_sms * 8;
   static bool attr = false;
