@@ -258,7 +258,7 @@ def run_reference(a, rank, world):
     data = bytes(make_files(a, 0))
     # each step a bounded sample, sized so that the whole run stays within a
     # few minutes
-    per_step = max(0.5, min(20.0, 150.0 / max(1, a.steps + a.warmup)))
+    per_step = max(0.3, min(20.0, 90.0 / max(1, a.steps + a.warmup)))
     for _ in range(a.warmup):
         oracle_sample(data, max_seconds=per_step)
     tot_b, tot_s = 0.0, 0.0
