@@ -258,7 +258,7 @@ class ClockSampler:
 # bench reports null.
 TRAFFIC_CAPTURES = {
     # profiles/traffic_eight_column_2p24_1MiB.md
-    "8388608/1048576/UNCOMPRESSED/V1/batched/oi1": {"rows": 16777216, "bytes": 1400624384, "sources": "733e240f792c9fd4"},
+    "8388608/1048576/UNCOMPRESSED/V1/batched/oi1": {"rows": 16777216, "bytes": 1400757504, "sources": "63e062155ec912be"},
 }
 
 KERNEL_SOURCES = ("k_decode.cu", "k_index.cu", "k_snappy.cu", "dev_util.cuh", "thrift_dev.cuh", "decode_job.h",

@@ -134,6 +134,48 @@ __device__ void oi_locations(TRdT<kGlobal> r, int c, const ChunkDev& ch, int64_t
   if (r.err || !got) report(st, DERR_CORRUPT, -1 - c, WHERE_INDEX, 12);
 }
 
+// The usual serialization of the OffsetIndex: field 1, a list of n structs,
+// each {1: i64 offset, 2: i32 compressed_page_size, 3: i64
+// first_row_index} with one-byte field headers (0x16, 0x15, 0x16) and a stop
+// byte.  Read straight through; false (nothing assumed written) when the
+// bytes take any other form, which the general parser then handles.
+__device__ bool oi_locations_fast(const uint8_t* p, const uint8_t* end, int c, const ChunkDev& ch, int64_t file_off,
+                                  PageDev* pages) {
+  auto varint = [&](uint64_t* v) -> bool {
+    uint64_t x = 0;
+    for (int i = 0; i < 10 && p < end; ++i) {
+      const uint32_t b = *p++;
+      x |= static_cast<uint64_t>(b & 0x7f) << (7 * i);
+      if (!(b & 0x80)) {
+        *v = x;
+        return true;
+      }
+    }
+    return false;
+  };
+  if (end - p < 2 || p[0] != 0x19 || (p[1] & 15) != 12) return false;
+  uint64_t n = p[1] >> 4;
+  p += 2;
+  if (n == 15 && !varint(&n)) return false;
+  if (n != ch.oi_pages) return false;
+  const uint32_t slot = ch.dict_page >= 0 ? 1u : 0u;
+  for (uint64_t i = 0; i < n; ++i) {
+    uint64_t off, skip;
+    if (p >= end || *p++ != 0x16 || !varint(&off)) return false;
+    if (p >= end || *p++ != 0x15 || !varint(&skip)) return false;
+    if (p >= end || *p++ != 0x16 || !varint(&skip)) return false;
+    if (p >= end || *p++ != 0x00) return false;
+    const int64_t rel = static_cast<int64_t>(off >> 1) ^ -static_cast<int64_t>(off & 1);
+    const int64_t r = rel - file_off;
+    if (r < 0 || static_cast<uint64_t>(r) >= ch.size) return false;
+    PageDev d{};
+    d.offset = static_cast<uint64_t>(r);
+    d.chunk = static_cast<uint32_t>(c);
+    pages[ch.page_begin + slot + i] = d;
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(32 * OI_WARPS) k_index_oi_locations(const ChunkDev* __restrict__ chunks,
                                                                       int n_chunks,
                                                                       const int64_t* __restrict__ chunk_file_off,
@@ -152,7 +194,8 @@ __global__ void __launch_bounds__(32 * OI_WARPS) k_index_oi_locations(const Chun
   if (ch.oi_len <= OI_SMEM) {
     for (uint32_t i = lane; i < ch.oi_len; i += 32) buf[w][i] = __ldg(ch.oi_base + i);
     __syncwarp();
-    if (lane == 0) oi_locations(TRdT<false>{buf[w], buf[w] + ch.oi_len, false}, c, ch, chunk_file_off[c], pages, st);
+    if (lane == 0 && !oi_locations_fast(buf[w], buf[w] + ch.oi_len, c, ch, chunk_file_off[c], pages))
+      oi_locations(TRdT<false>{buf[w], buf[w] + ch.oi_len, false}, c, ch, chunk_file_off[c], pages, st);
   } else if (lane == 0) {
     oi_locations(TRd{ch.oi_base, ch.oi_base + ch.oi_len, false}, c, ch, chunk_file_off[c], pages, st);
   }
