@@ -884,7 +884,9 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
                                                                                                  : pg.num_values / 256);
         }
         const int64_t span = pp.row_hi - pp.row_lo;
-        const int64_t per = (cd.max_def && !plain_fixed) ? plan->tuning.item_rows_opt : item_rows_max;
+        // pages with definition levels take the short items (their walks and
+        // expands carry a bitmap per item; measured faster for PLAIN too)
+        const int64_t per = cd.max_def ? plan->tuning.item_rows_opt : item_rows_max;
         const uint32_t n_it = static_cast<uint32_t>((span + per - 1) / per);
         pp.item_rows = static_cast<int32_t>(per);
         pp.item_count = n_it;

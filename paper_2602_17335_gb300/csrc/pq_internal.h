@@ -173,9 +173,10 @@ PQ_HD inline int type_width(int32_t t) {
   return t == T_INT32 || t == T_FLOAT ? 4 : (t == T_INT64 || t == T_DOUBLE) ? 8 : 0;
 }
 
-// Rows per decode work item (one warp decodes one item): REQUIRED columns
-// and OPTIONAL PLAIN fixed-width columns write straight to the output;
-// other OPTIONAL columns stage the item's dense values in shared memory.
+// Rows per decode work item (one warp decodes one item): ITEM_ROWS for pages
+// without definition levels, ITEM_ROWS_OPT for pages with them (OPTIONAL
+// columns other than PLAIN fixed-width stage an item's dense values in
+// shared memory; OPTIONAL PLAIN fixed-width write straight to the output).
 constexpr int ITEM_ROWS = 2048;
 constexpr int ITEM_ROWS_OPT = 512;
 
