@@ -367,10 +367,12 @@ void pq_write_free(uint8_t* buf);
  * against per-item overhead: the paper's Section 3 (Insight 1) ties
  * parallelism to page count, this engine to work items of `item_rows`. */
 typedef struct pq_tuning {
-  int32_t item_rows;          /* rows per work item: REQUIRED pages and OPTIONAL PLAIN
-                                 pages; 256..65536, a multiple of 32 (default 2048) */
-  int32_t item_rows_opt;      /* rows per work item of OPTIONAL non-PLAIN pages;
-                                 32..512, a multiple of 32 (default 512) */
+  int32_t item_rows;          /* rows per work item of pages without definition levels
+                                 (REQUIRED columns); 256..65536, a multiple of 32
+                                 (default 2048) */
+  int32_t item_rows_opt;      /* rows per work item of pages with definition levels
+                                 (OPTIONAL columns); 32..512, a multiple of 32
+                                 (default 512) */
   int32_t expand_ctas_per_sm; /* cap on resident CTAs per SM of the expansion and copy
                                  kernels; 0 = the occupancy limit (default) */
   int32_t branches;           /* streams the columns of one scan are forked onto, 1..8

@@ -1,8 +1,8 @@
 """Autotuner for the batched scan's knobs (``pq_tuning`` in include/pq.h).
 
 The knobs set scheduling granularity:
-- rows per work item (REQUIRED and OPTIONAL-PLAIN pages, and OPTIONAL
-  non-PLAIN pages);
+- rows per work item (pages without definition levels, and pages with
+  them);
 - resident CTAs per SM of the expansion kernels;
 - how many streams one scan's columns are forked onto.
 
