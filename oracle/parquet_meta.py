@@ -12,7 +12,9 @@ TYPE_NAME = {v: k for k, v in TYPE_ID.items()}
 PLAIN, PLAIN_DICTIONARY, RLE, BIT_PACKED, DELTA_BINARY_PACKED = 0, 2, 3, 4, 5
 DELTA_LENGTH_BYTE_ARRAY, DELTA_BYTE_ARRAY, RLE_DICTIONARY, BYTE_STREAM_SPLIT = 6, 7, 8, 9
 ENCODING_ID = {"PLAIN": PLAIN, "RLE_DICTIONARY": RLE_DICTIONARY,
-               "DELTA_BINARY_PACKED": DELTA_BINARY_PACKED}
+               "DELTA_BINARY_PACKED": DELTA_BINARY_PACKED,
+               "DELTA_LENGTH_BYTE_ARRAY": DELTA_LENGTH_BYTE_ARRAY,
+               "DELTA_BYTE_ARRAY": DELTA_BYTE_ARRAY, "BYTE_STREAM_SPLIT": BYTE_STREAM_SPLIT}
 
 # Codecs
 UNCOMPRESSED, SNAPPY = 0, 1

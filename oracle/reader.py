@@ -14,7 +14,9 @@ column chunks -> pages; decompression then decoding):
   width 1); V2 data page: rep/def levels (lengths from the header) are never
   compressed, values are compressed when is_compressed (default true);
 * values: PLAIN, RLE_DICTIONARY / PLAIN_DICTIONARY (1-byte bit width + hybrid
-  indices into the chunk's dictionary), DELTA_BINARY_PACKED;
+  indices into the chunk's dictionary), DELTA_BINARY_PACKED, and the other
+  V2 encodings of Section 3's Insight 3: BYTE_STREAM_SPLIT (fixed width),
+  DELTA_LENGTH_BYTE_ARRAY and DELTA_BYTE_ARRAY (BYTE_ARRAY);
 * row r of a page is null when its definition level is below the maximum
   (1); null slots of fixed-width outputs are 0; BYTE_ARRAY outputs are int64
   offsets (n + 1) plus chars.
@@ -29,14 +31,16 @@ from typing import List, Optional
 
 import numpy as np
 
+from . import byte_stream_split as _bss
 from . import delta as _delta
+from . import delta_strings as _dstr
 from . import hybrid as _hybrid
 from . import plain as _plain
 from . import snappy as _snappy
 from . import thrift as T
-from .parquet_meta import (DATA_PAGE, DATA_PAGE_V2, DELTA_BINARY_PACKED, DICTIONARY_PAGE, OPTIONAL,
-                           PLAIN, PLAIN_DICTIONARY, REPEATED, RLE_DICTIONARY, SNAPPY, TYPE_NAME,
-                           UNCOMPRESSED)
+from .parquet_meta import (BYTE_STREAM_SPLIT, DATA_PAGE, DATA_PAGE_V2, DELTA_BINARY_PACKED,
+                           DELTA_BYTE_ARRAY, DELTA_LENGTH_BYTE_ARRAY, DICTIONARY_PAGE, OPTIONAL, PLAIN,
+                           PLAIN_DICTIONARY, REPEATED, RLE_DICTIONARY, SNAPPY, TYPE_NAME, UNCOMPRESSED)
 
 
 class ParquetError(ValueError):
@@ -279,6 +283,15 @@ def decode_data_page(data, p: PageInfo, ch: ChunkInfo, dictionary):
         if len(vals) != nn:
             raise ParquetError("DELTA value count differs from the page")
         dense = np.array(vals, dtype=np.int32 if bits == 32 else np.int64)
+    elif enc == BYTE_STREAM_SPLIT:
+        if ch.ptype == "BYTE_ARRAY":
+            raise ParquetError("BYTE_STREAM_SPLIT on a BYTE_ARRAY column")
+        dense = _bss.decode(vals_buf, vpos, end, ch.ptype, nn)
+    elif enc in (DELTA_LENGTH_BYTE_ARRAY, DELTA_BYTE_ARRAY):
+        if ch.ptype != "BYTE_ARRAY":
+            raise ParquetError("delta string encoding on a fixed-width column")
+        dec = _dstr.decode_length_byte_array if enc == DELTA_LENGTH_BYTE_ARRAY else _dstr.decode_byte_array
+        dense, _ = dec(vals_buf, vpos, end, nn)
     else:
         raise Unsupported(f"encoding {enc}")
     # assemble rows

@@ -3,7 +3,9 @@
 Writes a flat table into a Parquet file following the paper's Section 2
 hierarchy (file -> row groups -> one column chunk per column -> pages) with
 the knobs its Section 3 varies: page size, row-group size, encoding per
-chunk (V1 PLAIN / dictionary, V2 DELTA_BINARY_PACKED, V1 or V2 data pages)
+chunk (V1 PLAIN / dictionary, the V2 set DELTA_BINARY_PACKED,
+DELTA_LENGTH_BYTE_ARRAY, DELTA_BYTE_ARRAY and BYTE_STREAM_SPLIT, V1 or V2
+data pages)
 and per-chunk compression, optionally kept only when it shrinks the chunk by
 more than a threshold ("No Unnecessary Compression", 10% in the paper).
 
@@ -20,8 +22,10 @@ them byte for byte on uncompressed data):
   - REQUIRED DELTA_BINARY_PACKED: 1 + 128 k values, k >= 1 the largest count
     of whole 128-value blocks whose encoded stream still fits page_bytes;
     OPTIONAL DELTA uses the fixed-width rule;
-  - PLAIN BYTE_ARRAY: rows are added while the page has < 8 rows or the
-    encoded bytes (4 + length per non-null value) still fit;
+  - BYTE_STREAM_SPLIT: as fixed-width PLAIN;
+  - BYTE_ARRAY (PLAIN, DELTA_LENGTH_BYTE_ARRAY, DELTA_BYTE_ARRAY): rows are
+    added while the page has < 8 rows or the PLAIN-encoded bytes (4 + length
+    per non-null value) still fit;
   the last page of a chunk takes the remaining rows;
 * hybrid runs follow the chosen policy (``default`` unless the spec says
   otherwise); V1 definition levels carry a 4-byte length prefix;
@@ -36,7 +40,9 @@ import numpy as np
 
 from synth import FIXED_WIDTH, ColumnSpec, StringData, Table, TableSpec, slice_column
 
+from . import byte_stream_split as _bss
 from . import delta as _delta
+from . import delta_strings as _dstr
 from . import hybrid as _hybrid
 from . import plain as _plain
 from . import snappy as _snappy
@@ -119,7 +125,7 @@ def _delta_page_values(vals, a, bits, page_bytes):
 def _page_row_counts(ptype, encoding, n_rows, valid, vals_all, page_bytes, bw):
     optional = valid is not None
     counts = []
-    if ptype == "BYTE_ARRAY" and encoding == "PLAIN":
+    if ptype == "BYTE_ARRAY" and encoding in ("PLAIN", "DELTA_LENGTH_BYTE_ARRAY", "DELTA_BYTE_ARRAY"):
         # vals_all holds the row values with None for nulls
         r = 0
         while r < n_rows:
@@ -197,6 +203,10 @@ def write_chunk(col, cspec: ColumnSpec, page_bytes: int, base: int, rng=None):
         bw = _hybrid.bit_width_for(max(len(dict_entries) - 1, 0))
     elif enc_name == "DELTA_BINARY_PACKED" and ptype not in ("INT32", "INT64"):
         raise ValueError("DELTA_BINARY_PACKED needs an INT32 or INT64 column")
+    elif enc_name == "BYTE_STREAM_SPLIT" and ptype == "BYTE_ARRAY":
+        raise ValueError("BYTE_STREAM_SPLIT needs a fixed-width column")
+    elif enc_name in ("DELTA_LENGTH_BYTE_ARRAY", "DELTA_BYTE_ARRAY") and ptype != "BYTE_ARRAY":
+        raise ValueError(f"{enc_name} needs a BYTE_ARRAY column")
 
     counts = _page_row_counts(ptype, enc_name, n_rows, valid,
                               rows_view if ptype == "BYTE_ARRAY" or enc_name != "DELTA_BINARY_PACKED"
@@ -232,6 +242,12 @@ def write_chunk(col, cspec: ColumnSpec, page_bytes: int, base: int, rng=None):
             elif enc_name == "DELTA_BINARY_PACKED":
                 bits = 32 if ptype == "INT32" else 64
                 vbytes = _delta.encode([int(v) for v in nonnull[vpos:vpos + nn]], bits)
+            elif enc_name == "BYTE_STREAM_SPLIT":
+                vbytes = _bss.encode(nonnull[vpos:vpos + nn], ptype)
+            elif enc_name == "DELTA_LENGTH_BYTE_ARRAY":
+                vbytes = _dstr.encode_length_byte_array(nonnull[vpos:vpos + nn])
+            elif enc_name == "DELTA_BYTE_ARRAY":
+                vbytes = _dstr.encode_byte_array(nonnull[vpos:vpos + nn])
             elif ptype == "BYTE_ARRAY":
                 vbytes = _plain.encode_byte_array(nonnull[vpos:vpos + nn])
             else:

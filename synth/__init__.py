@@ -36,6 +36,8 @@ FIXED_WIDTH = {INT32: 4, INT64: 8, DOUBLE: 8}
 
 # Writer-side knobs (names of encodings/codecs; no arithmetic here).
 PLAIN, RLE_DICTIONARY, DELTA_BINARY_PACKED = "PLAIN", "RLE_DICTIONARY", "DELTA_BINARY_PACKED"
+DELTA_LENGTH_BYTE_ARRAY, DELTA_BYTE_ARRAY = "DELTA_LENGTH_BYTE_ARRAY", "DELTA_BYTE_ARRAY"
+BYTE_STREAM_SPLIT = "BYTE_STREAM_SPLIT"
 UNCOMPRESSED, SNAPPY = "UNCOMPRESSED", "SNAPPY"
 
 KiB = 1 << 10
@@ -153,6 +155,26 @@ def strings_uniform(rng, n, k=10_000, min_len=8, max_len=32):
     return StringData(off, ch, idx)
 
 
+def strings_sorted(rng, n, rg_rows, k=4096, stems=64):
+    """Rows sorted inside each row group over a pool of ``k`` strings that
+    share prefixes: each is one of ``stems`` random stems (length U[4,12])
+    plus a random tail (length U[0,20]), all over [A-Za-z0-9]."""
+    alphabet = np.frombuffer(b"ABCDEFGHIJKLMNOPQRSTUVWXYZabcdefghijklmnopqrstuvwxyz0123456789", dtype=np.uint8)
+    stem_len = rng.integers(4, 13, size=stems)
+    stem = [bytes(alphabet[rng.integers(0, alphabet.shape[0], size=int(m))]) for m in stem_len]
+    pool = sorted(set(stem[int(rng.integers(0, stems))]
+                      + bytes(alphabet[rng.integers(0, alphabet.shape[0], size=int(rng.integers(0, 21)))])
+                      for _ in range(k)))
+    lens = np.array([len(x) for x in pool], dtype=np.int64)
+    offsets = np.zeros(len(pool) + 1, dtype=np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    chars = np.frombuffer(b"".join(pool), dtype=np.uint8).copy()
+    idx = rng.integers(0, len(pool), size=n, dtype=np.int64).astype(np.int32)
+    for a in range(0, n, rg_rows):
+        idx[a:a + rg_rows].sort()
+    return StringData(offsets, chars, idx)
+
+
 def lowcard_int32(rng, n, card=16):
     pool = rng.choice(1 << 20, size=card, replace=False).astype(np.int32)
     return pool[rng.integers(0, card, size=n)]
@@ -172,7 +194,9 @@ def sorted_lowcard_int32(rng, n, card, rg_rows):
 
 @dataclass
 class ColumnSpec:
-    encoding: str = PLAIN            # PLAIN | RLE_DICTIONARY | DELTA_BINARY_PACKED
+    # PLAIN | RLE_DICTIONARY | DELTA_BINARY_PACKED | BYTE_STREAM_SPLIT |
+    # DELTA_LENGTH_BYTE_ARRAY | DELTA_BYTE_ARRAY
+    encoding: str = PLAIN
     codec: str = UNCOMPRESSED        # UNCOMPRESSED | SNAPPY
     page_version: int = 1            # 1 = DATA_PAGE, 2 = DATA_PAGE_V2
     # hybrid run policy for the writer: "default", "rle", "packed", "mixed"
@@ -239,6 +263,42 @@ def config2_spec(rg_rows: int, page_bytes: int, codec: str = UNCOMPRESSED,
             RLE_DICTIONARY, RLE_DICTIONARY, RLE_DICTIONARY]
     return TableSpec(rg_rows=rg_rows, page_bytes=page_bytes,
                      columns=[ColumnSpec(e, codec, page_version) for e in encs],
+                     offset_index=offset_index)
+
+
+def v2_encodings_table(n_rows: int, rg_rows: int, seed: int = MASTER_SEED, file: int = 0) -> Table:
+    """Six columns for the other V2 encodings of the paper's Insight 3:
+
+      e1  DOUBLE standard normal                          -> BYTE_STREAM_SPLIT
+      e2  INT32 Zipf(1.1) over 10^4 distinct values       -> BYTE_STREAM_SPLIT
+      e3  OPTIONAL INT64 uniform over int64, 10% nulls    -> BYTE_STREAM_SPLIT
+      e4  BYTE_ARRAY, 10^4 random strings, rows uniform   -> DELTA_LENGTH_BYTE_ARRAY
+      e5  BYTE_ARRAY sorted in each row group, shared stems -> DELTA_BYTE_ARRAY
+      e6  OPTIONAL BYTE_ARRAY as e4, 10% nulls            -> DELTA_BYTE_ARRAY
+    """
+    r = lambda col: rng_for(6, col, file, seed)
+    e3_valid = bernoulli_valid(r(30), n_rows, 0.1)
+    e3 = uniform_int64_full(r(3), n_rows)
+    e3[~e3_valid] = 0
+    return Table([
+        ColumnData("e1_bss_f64", DOUBLE, normal_f64(r(1), n_rows)),
+        ColumnData("e2_bss_i32", INT32, zipf_int32(r(2), n_rows, 1.1, 10_000)),
+        ColumnData("e3_bss_opt_i64", INT64, e3, e3_valid),
+        ColumnData("e4_dlba_str", BYTE_ARRAY, strings_uniform(r(4), n_rows, 10_000)),
+        ColumnData("e5_dba_sorted_str", BYTE_ARRAY, strings_sorted(r(5), n_rows, rg_rows)),
+        ColumnData("e6_dba_opt_str", BYTE_ARRAY, strings_uniform(r(6), n_rows, 10_000),
+                   bernoulli_valid(r(60), n_rows, 0.1)),
+    ])
+
+
+V2_ENCODINGS = (BYTE_STREAM_SPLIT, BYTE_STREAM_SPLIT, BYTE_STREAM_SPLIT, DELTA_LENGTH_BYTE_ARRAY,
+                DELTA_BYTE_ARRAY, DELTA_BYTE_ARRAY)
+
+
+def v2_encodings_spec(rg_rows: int, page_bytes: int, codec: str = UNCOMPRESSED,
+                      page_version: int = 2, offset_index: bool = True) -> TableSpec:
+    return TableSpec(rg_rows=rg_rows, page_bytes=page_bytes,
+                     columns=[ColumnSpec(e, codec, page_version) for e in V2_ENCODINGS],
                      offset_index=offset_index)
 
 

@@ -39,6 +39,24 @@ def assert_matches(table, results):
 SMALL = dict(string_pool_size=200, zipf_k=300)
 
 
+def string_rows(col):
+    """Row values of a BYTE_ARRAY column, b'' for a null row."""
+    off, ch = col.values.materialize()
+    rows = [bytes(ch[off[j]:off[j + 1]]) for j in range(len(off) - 1)]
+    return rows if col.valid is None else [x if v else b"" for x, v in zip(rows, col.valid)]
+
+
+def assert_rows_match(table, results):
+    for col, r in zip(table.columns, results):
+        if col.ptype == "BYTE_ARRAY":
+            got = [bytes(r.chars[r.offsets[j]:r.offsets[j + 1]]) for j in range(len(r.offsets) - 1)]
+            assert got == string_rows(col), col.name
+        else:
+            v = np.asarray(col.values)
+            assert np.array_equal(v.view(np.uint8), r.values.view(np.uint8)), col.name
+        assert (r.valid is None) if col.valid is None else np.array_equal(col.valid, r.valid)
+
+
 @pytest.mark.parametrize("rg_rows,page_bytes", [(4096, 512), (1500, 2048), (10_000, 64 * 1024), (777, 8)])
 @pytest.mark.parametrize("codec,version", [("UNCOMPRESSED", 1), ("SNAPPY", 1), ("UNCOMPRESSED", 2), ("SNAPPY", 2)])
 def test_roundtrip_eight_column_table(rg_rows, page_bytes, codec, version):
@@ -172,3 +190,60 @@ def test_oracle_reads_pyarrow_files(version, compression, dict_, delta):
     assert np.array_equal(res[3].valid, valid) and np.array_equal(res[3].values[valid], i64[valid])
     assert np.all(res[3].values[~valid] == 0)
     assert [bytes(res[4].chars[res[4].offsets[j]:res[4].offsets[j + 1]]) for j in range(n)] == strs
+
+
+# ------------------------------------------------------------- V2 encodings (Insight 3)
+
+@pytest.mark.parametrize("rg_rows,page_bytes", [(2500, 700), (6000, 64 * 1024), (999, 8)])
+@pytest.mark.parametrize("codec,version", [("UNCOMPRESSED", 1), ("SNAPPY", 1), ("UNCOMPRESSED", 2), ("SNAPPY", 2)])
+def test_roundtrip_v2_encodings(rg_rows, page_bytes, codec, version):
+    tab = synth.v2_encodings_table(6000, rg_rows)
+    data = W.write_file(tab, synth.v2_encodings_spec(rg_rows, page_bytes, codec, version))
+    info = R.parse_footer(data)
+    encs = {p.encoding for ch in info.chunks for p in R.chunk_pages(data, ch)}
+    assert encs == {6, 7, 9}
+    assert_rows_match(tab, R.read_file(data))
+
+
+def test_pyarrow_reads_oracle_v2_encodings():
+    pq = pytest.importorskip("pyarrow.parquet")
+    tab = synth.v2_encodings_table(3000, 1100)
+    for codec, version in (("UNCOMPRESSED", 1), ("SNAPPY", 2)):
+        data = W.write_file(tab, synth.v2_encodings_spec(1100, 900, codec, version))
+        t = pq.read_table(io.BytesIO(data))
+        for i, col in enumerate(tab.columns):
+            got = t.column(i).to_pylist()
+            if col.ptype == "BYTE_ARRAY":
+                rows = string_rows(col)
+                exp = rows if col.valid is None else [x if v else None for x, v in zip(rows, col.valid)]
+            else:
+                v = np.asarray(col.values).tolist()
+                exp = v if col.valid is None else [x if m else None for x, m in zip(v, col.valid)]
+            assert got == exp, col.name
+
+
+@pytest.mark.parametrize("page_version", ["1.0", "2.0"])
+def test_oracle_reads_pyarrow_v2_encodings(page_version):
+    pa = pytest.importorskip("pyarrow")
+    pq = pytest.importorskip("pyarrow.parquet")
+    rng = np.random.default_rng(5)
+    n = 5000
+    f64 = rng.standard_normal(n)
+    i32 = rng.integers(-1000, 1000, size=n).astype(np.int32)
+    i64 = rng.integers(-2**62, 2**62, size=n)
+    valid = rng.random(n) > 0.1
+    strs = [b"key%06d" % x for x in np.sort(rng.integers(0, 10**6, size=n))]
+    t = pa.table({"a": pa.array(f64), "b": pa.array(i32), "c": pa.array(i64, mask=~valid),
+                  "d": pa.array(strs, pa.binary()), "e": pa.array(strs, pa.binary(), mask=~valid)})
+    buf = io.BytesIO()
+    pq.write_table(t, buf, use_dictionary=False, data_page_size=2048, row_group_size=2100,
+                   data_page_version=page_version,
+                   column_encoding={"a": "BYTE_STREAM_SPLIT", "b": "BYTE_STREAM_SPLIT", "c": "BYTE_STREAM_SPLIT",
+                                    "d": "DELTA_LENGTH_BYTE_ARRAY", "e": "DELTA_BYTE_ARRAY"})
+    res = R.read_file(buf.getvalue())
+    assert np.array_equal(res[0].values.view(np.int64), f64.view(np.int64))
+    assert np.array_equal(res[1].values, i32)
+    assert np.array_equal(res[2].valid, valid) and np.array_equal(res[2].values[valid], i64[valid])
+    assert [bytes(res[3].chars[res[3].offsets[j]:res[3].offsets[j + 1]]) for j in range(n)] == strs
+    assert [bytes(res[4].chars[res[4].offsets[j]:res[4].offsets[j + 1]]) for j in range(n)] == \
+        [x if v else b"" for x, v in zip(strs, valid)]

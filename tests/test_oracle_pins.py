@@ -8,7 +8,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle import delta, hybrid, snappy, thrift
+from oracle import byte_stream_split, delta, delta_strings, hybrid, snappy, thrift
 from oracle import reader as R
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_vectors.json")))
@@ -221,3 +221,106 @@ def test_snappy_errors():
         snappy.decompress(hx("05 0C 61 62 63 64"))    # shorter than declared
     with pytest.raises(snappy.SnappyError):
         snappy.decompress(hx("02 0C 61 62 63 64"))    # longer than declared
+
+
+# ------------------------------------------------------------------ byte stream split
+
+def test_byte_stream_split_hand_vectors():
+    for key in ("bss_double", "bss_int32"):
+        g = GOLD[key]
+        b = hx(g["hex"])
+        got = byte_stream_split.decode(b, 0, len(b), g["ptype"], len(g["values"]))
+        assert got.tolist() == g["values"]
+        assert byte_stream_split.encode(g["values"], g["ptype"]) == b
+
+
+@pytest.mark.parametrize("ptype,dtype", [("INT32", "<i4"), ("INT64", "<i8"), ("DOUBLE", "<f8")])
+def test_byte_stream_split_is_a_byte_transpose(ptype, dtype):
+    # special case reducing to a library routine: the streams are the K x N
+    # transpose of the N x K little-endian byte matrix of the values
+    rng = np.random.default_rng(17)
+    for n in (0, 1, 7, 33, 1000):
+        raw = rng.integers(0, 256, size=n * np.dtype(dtype).itemsize, dtype=np.uint8)
+        vals = raw.view(dtype)
+        k = np.dtype(dtype).itemsize
+        streams = raw.reshape(n, k).T.copy().tobytes()
+        assert byte_stream_split.encode(vals, ptype) == streams
+        got = byte_stream_split.decode(streams, 0, len(streams), ptype, n)
+        assert got.view(np.uint8).tobytes() == raw.tobytes()
+
+
+def test_byte_stream_split_nulls_and_errors():
+    b = hx(GOLD["bss_int32"]["hex"])
+    # an OPTIONAL page reads the first values of full-length streams
+    assert byte_stream_split.decode(b, 0, len(b), "INT32", 2).tolist() == GOLD["bss_int32"]["values"][:2]
+    with pytest.raises(byte_stream_split.ByteStreamSplitError):
+        byte_stream_split.decode(b, 0, len(b) - 1, "INT32", 2)   # not a whole number of values
+    with pytest.raises(byte_stream_split.ByteStreamSplitError):
+        byte_stream_split.decode(b, 0, len(b), "INT32", 4)       # more values than the streams hold
+
+
+# ------------------------------------------------------------------ delta strings
+
+def test_delta_length_byte_array_hand_vector():
+    g = GOLD["delta_length_byte_array"]
+    b = hx(g["hex"])
+    vals, end = delta_strings.decode_length_byte_array(b, 0, len(b), len(g["strings"]))
+    assert vals == [x.encode() for x in g["strings"]] and end == len(b)
+    assert delta_strings.encode_length_byte_array([x.encode() for x in g["strings"]]) == b
+
+
+def test_delta_byte_array_hand_vector():
+    g = GOLD["delta_byte_array"]
+    b = hx(g["hex"])
+    vals, end = delta_strings.decode_byte_array(b, 0, len(b), len(g["strings"]))
+    assert vals == [x.encode() for x in g["strings"]] and end == len(b)
+    assert delta_strings.encode_byte_array([x.encode() for x in g["strings"]]) == b
+
+
+def test_delta_strings_brute_force_small():
+    # every sequence of up to 4 strings over {'', a, b, aa, ab, ba, aab}
+    words = [b"", b"a", b"b", b"aa", b"ab", b"ba", b"aab"]
+    for n in range(0, 5):
+        for seq in itertools.product(words, repeat=n):
+            seq = list(seq)
+            e1 = delta_strings.encode_length_byte_array(seq)
+            assert delta_strings.decode_length_byte_array(e1, 0, len(e1), n) == (seq, len(e1))
+            e2 = delta_strings.encode_byte_array(seq)
+            assert delta_strings.decode_byte_array(e2, 0, len(e2), n) == (seq, len(e2))
+
+
+def test_delta_byte_array_without_shared_prefixes_is_length_encoding():
+    # strings with distinct first bytes share no prefix: the stream is a
+    # zero prefix stream followed by the DELTA_LENGTH_BYTE_ARRAY of the values
+    seq = [b"x1", b"y22", b"z", b"w4444"]
+    zeros = delta.encode([0, 0, 0, 0], 32)
+    assert delta_strings.encode_byte_array(seq) == zeros + delta_strings.encode_length_byte_array(seq)
+    assert zeros == hx("80 01 04 04 00") + hx("00 00 00 00 00")
+
+
+def test_delta_strings_long_shared_prefixes():
+    rng = np.random.default_rng(23)
+    stem = bytes(rng.integers(97, 123, size=300, dtype=np.uint8))
+    seq = sorted(stem[:int(rng.integers(0, 301))] + bytes(rng.integers(97, 123, size=int(rng.integers(0, 5)),
+                                                                       dtype=np.uint8)) for _ in range(700))
+    e = delta_strings.encode_byte_array(seq)
+    assert delta_strings.decode_byte_array(e, 0, len(e), len(seq))[0] == seq
+    assert len(e) < sum(len(x) for x in seq) // 4   # front coding pays on sorted keys
+
+
+def test_delta_strings_errors():
+    ok = delta_strings.encode_byte_array([b"ab", b"ac"])
+    with pytest.raises(delta_strings.DeltaStringError):     # count differs from the page
+        delta_strings.decode_byte_array(ok, 0, len(ok), 3)
+    bad_prefix = delta.encode([0, 3], 32) + delta_strings.encode_length_byte_array([b"ab", b"c"])
+    with pytest.raises(delta_strings.DeltaStringError):     # prefix 3 > len('ab')
+        delta_strings.decode_byte_array(bad_prefix, 0, len(bad_prefix), 2)
+    first_prefix = delta.encode([1, 0], 32) + delta_strings.encode_length_byte_array([b"ab", b"c"])
+    with pytest.raises(delta_strings.DeltaStringError):     # first value has no predecessor
+        delta_strings.decode_byte_array(first_prefix, 0, len(first_prefix), 2)
+    neg = delta.encode([2, -1], 32) + b"ab"
+    with pytest.raises(delta_strings.DeltaStringError):     # negative length
+        delta_strings.decode_length_byte_array(neg, 0, len(neg), 2)
+    short = delta_strings.encode_length_byte_array([b"abc", b"defg"])
+    with pytest.raises(delta_strings.DeltaStringError):     # bytes past the end
+        delta_strings.decode_length_byte_array(short, 0, len(short) - 1, 2)
