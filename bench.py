@@ -258,11 +258,11 @@ class ClockSampler:
 # bench reports null.
 TRAFFIC_CAPTURES = {
     # profiles/traffic_eight_column_2p24_1MiB.md
-    "8388608/1048576/UNCOMPRESSED/V1/batched/oi1": {"rows": 16777216, "bytes": 1363964928, "sources": "88978e5d28d5fd14"},
+    "8388608/1048576/UNCOMPRESSED/V1/batched/oi1": {"rows": 16777216, "bytes": 1364678400, "sources": "e763436e4f145bc0"},
 }
 
-KERNEL_SOURCES = ("k_decode.cu", "k_index.cu", "k_snappy.cu", "dev_util.cuh", "thrift_dev.cuh", "decode_job.h",
-                  "pq_internal.h", "snappy_job.h", "engine.cpp")
+KERNEL_SOURCES = ("k_decode.cu", "k_index.cu", "k_snappy.cu", "k_transcode.cu", "dev_util.cuh", "thrift_dev.cuh",
+                  "decode_job.h", "pq_internal.h", "snappy_job.h", "engine.cpp")
 
 
 def kernel_sources_digest():

@@ -15,7 +15,10 @@
  * Supported subset: flat schemas (REQUIRED or OPTIONAL leaf columns, no
  * repetition), physical types INT32, INT64, DOUBLE and BYTE_ARRAY, data
  * pages V1 and V2, encodings PLAIN, PLAIN_DICTIONARY / RLE_DICTIONARY (with
- * an RLE/bit-packed hybrid index stream) and DELTA_BINARY_PACKED, definition
+ * an RLE/bit-packed hybrid index stream), DELTA_BINARY_PACKED, and the other
+ * V2 encodings of the paper's Section 3 (Insight 3): BYTE_STREAM_SPLIT
+ * (fixed-width columns), DELTA_LENGTH_BYTE_ARRAY and DELTA_BYTE_ARRAY
+ * (BYTE_ARRAY columns; DELTA blocks of at most 2048 values), definition
  * levels with the RLE/bit-packed hybrid, codecs UNCOMPRESSED and SNAPPY.
  * Anything else is rejected with PQ_ERR_UNSUPPORTED, never mis-decoded.
  *

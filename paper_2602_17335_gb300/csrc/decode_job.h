@@ -38,6 +38,28 @@ struct DictScratch {
   uint64_t* lists;      // STR_REGION_LIST entries per region, (chars offset << 32) | length
 };
 
+// A BYTE_STREAM_SPLIT, DELTA_LENGTH_BYTE_ARRAY or DELTA_BYTE_ARRAY data page
+// rewritten into a PLAIN body (level bytes kept in front) before the walk.
+struct TranscodeJob {
+  const uint8_t* src;   // page body (decompressed): level bytes + encoded values
+  uint8_t* dst;         // BYTE_STREAM_SPLIT, DELTA_LENGTH_BYTE_ARRAY: dst_cap bytes for the PLAIN
+                        // body; DELTA_BYTE_ARRAY: null (a piece of the plan's pool)
+  uint32_t src_len;
+  uint32_t dst_cap;     // src_len (BYTE_STREAM_SPLIT), src_len + 4 * num_values (DELTA_LENGTH_BYTE_ARRAY)
+  uint32_t pp;          // plan page whose body and body_len the kernel sets
+  int32_t page;         // page-table row (errors)
+  int32_t enc;          // ENC_BSS, ENC_DELTA_LBA or ENC_DELTA_BA
+  int32_t width;        // BYTE_STREAM_SPLIT value bytes
+  int32_t levels;       // level bytes in front of the values: V2 def_len + rep_len;
+                        // -1: V1 with levels (4-byte length + levels); 0: none
+  int32_t num_values;   // page rows
+  int32_t required;     // 1: REQUIRED column (value count = rows)
+  int32_t pad;
+};
+// item_counter[TC_POOL_COUNTER .. +1]: bytes of the DELTA_BYTE_ARRAY pool
+// handed out in this scan (a 64-bit counter, zeroed by the per-scan reset).
+constexpr int TC_POOL_COUNTER = 2;
+
 struct DecodeArgs {
   const ChunkDev* chunks;
   const PageDev* pages;
@@ -46,7 +68,7 @@ struct DecodeArgs {
   Item* items;
   const OutCol* cols;
   DevStatus* st;
-  uint32_t* item_counter;   // [1] next walk page, [4 + c] next work item of output column c
+  uint32_t* item_counter;   // [2..3] transcode pool bytes, [4 + c] next work item of output column c
   const uint32_t* walk_pps; // plan pages that need the walk, longest chains first
   const uint32_t* delta_pps;// DELTA plan pages (block bases)
   uint32_t* dpos;           // DELTA block positions (stream offsets)
@@ -59,6 +81,10 @@ struct DecodeArgs {
   int n_delta;
 };
 
+// One block per job; `counters` is the plan's item_counter array (its pool
+// word); `pool` holds `pool_cap` bytes for DELTA_BYTE_ARRAY bodies.
+void launch_transcode(const TranscodeJob* jobs, int n, PlanPage* pps, uint8_t* pool, uint64_t pool_cap,
+                      uint32_t* counters, DevStatus* st, cudaStream_t s);
 void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, int max_str_regions, DictScratch ds,
                  DictDev* dicts, int n_sms, DevStatus* st, cudaStream_t s);
 // Launches over sub-ranges (one output column's share of the plan).

@@ -730,6 +730,7 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
   plan->tuning = ctx->tuning;
   const int64_t item_rows_max = plan->tuning.item_rows;
   uint64_t scratch = 0;
+  uint64_t tc_pool = 0;               // DELTA_BYTE_ARRAY pool bytes
   std::vector<int64_t> data_job_off;  // scratch offset per data snappy job
   std::vector<int64_t> walk_cost;     // estimated chain steps per walked page
   std::vector<int32_t> dict_job_of_chunk(idx->chunks.size(), -1);
@@ -742,6 +743,7 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
     cw.dict_begin = static_cast<int>(plan->dict_jobs.size());
     cw.walk_begin = static_cast<int>(plan->walk_pps.size());
     cw.delta_begin = static_cast<int>(plan->delta_pps.size());
+    cw.tc_begin = static_cast<int>(plan->tc_jobs.size());
     cw.copy_only = cm.repetition != 1 && cm.type != pqi::T_BYTE_ARRAY;
     const int max_fixed_before = plan->max_fixed_dict_bytes;
     plan->max_fixed_dict_bytes = 0;
@@ -775,6 +777,7 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
         chars += static_cast<uint64_t>(idx->chunk_ba_bytes[ch]);
       }
       const int32_t pp_first = static_cast<int32_t>(plan->pps.size());
+      bool tc_chunk_counted = false;  // this visit's chars are in the pool size
       // dictionary of this chunk
       int32_t dict = -1;
       if (cd.dict_page >= 0) {
@@ -826,7 +829,16 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
         const int64_t p0 = c0 + pg.first_row;
         const int64_t p1 = p0 + pg.num_values;
         if (p1 <= rb || p0 >= re || pg.num_values == 0) continue;
+        // BYTE_STREAM_SPLIT and the delta string encodings are rewritten into
+        // PLAIN bodies first; the decode kernels then read them as PLAIN
+        const int32_t enc = pg.encoding;
+        const bool tc = enc == pqi::ENC_BSS || enc == pqi::ENC_DELTA_LBA || enc == pqi::ENC_DELTA_BA;
+        if (tc && (enc == pqi::ENC_BSS) == (cd.ptype == pqi::T_BYTE_ARRAY))
+          return fail(ctx, PQ_ERR_CORRUPT, enc == pqi::ENC_BSS ? "BYTE_STREAM_SPLIT on a BYTE_ARRAY column"
+                                                                : "delta string encoding on a fixed-width column");
+        const int32_t eff = tc ? static_cast<int32_t>(pqi::ENC_PLAIN) : enc;
         pqi::PlanPage pp{};
+        pp.enc = eff;
         pp.page = pid;
         pp.chunk = static_cast<uint32_t>(ch);
         pp.col = static_cast<int32_t>(oc);
@@ -856,8 +868,41 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
           pp.body = stored;
         }
         plan->read_bytes += static_cast<uint64_t>(pg.header_len) + static_cast<uint64_t>(pg.compressed);
+        if (tc) {
+          pqi::TranscodeJob j{};
+          j.src = pp.pad == 1 ? nullptr : stored;  // a decompressed body is rebased at upload
+          j.src_len = static_cast<uint32_t>(pg.uncompressed);
+          j.pp = static_cast<uint32_t>(plan->pps.size());
+          j.page = static_cast<int32_t>(pid);
+          j.enc = enc;
+          j.width = cd.width;
+          j.levels = pg.page_type == pqi::PAGE_DATA_V2 ? pg.def_len + pg.rep_len : (cd.max_def ? -1 : 0);
+          j.num_values = pg.num_values;
+          j.required = cd.max_def ? 0 : 1;
+          plan->tc_src_off.push_back(pp.pad == 1 ? static_cast<int64_t>(reinterpret_cast<uintptr_t>(pp.body)) : -1);
+          if (enc == pqi::ENC_DELTA_BA) {
+            // the PLAIN size is known only on the device: the page takes a piece
+            // of a pool that holds its levels, length words and padding, plus
+            // (once per chunk) the chunk's value bytes
+            plan->tc_dst_off.push_back(-1);
+            tc_pool += (static_cast<uint64_t>(pg.uncompressed) + 4ull * static_cast<uint64_t>(pg.num_values) + 63) &
+                       ~uint64_t(15);
+            if (!tc_chunk_counted) {
+              tc_pool += (static_cast<uint64_t>(idx->chunk_ba_bytes[ch]) + 15) & ~uint64_t(15);
+              tc_chunk_counted = true;
+            }
+          } else {
+            const uint64_t cap = static_cast<uint64_t>(pg.uncompressed) +
+                                 (enc == pqi::ENC_DELTA_LBA ? 4ull * static_cast<uint64_t>(pg.num_values) : 0);
+            if (cap > 0x7fffffffull) return fail(ctx, PQ_ERR_UNSUPPORTED, "transcoded page above 2 GiB");
+            j.dst_cap = static_cast<uint32_t>(cap);
+            plan->tc_dst_off.push_back(static_cast<int64_t>(scratch));
+            scratch += (cap + 32 + 15) & ~uint64_t(15);
+          }
+          plan->tc_jobs.push_back(j);
+        }
         pp.item_begin = static_cast<uint32_t>(plan->n_items);
-        const bool plain_fixed = pg.encoding == pqi::ENC_PLAIN && cd.ptype != pqi::T_BYTE_ARRAY;
+        const bool plain_fixed = eff == pqi::ENC_PLAIN && cd.ptype != pqi::T_BYTE_ARRAY;
         if (!plain_fixed || cd.max_def) cw.copy_only = false;
         const bool needs_walk = cd.max_def || !plain_fixed;
         if (!cd.max_def) {
@@ -867,7 +912,7 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
           pp.values_off = 0;
           pp.nonnull = pg.num_values;
         }
-        if (pg.encoding == pqi::ENC_DELTA_BP) {
+        if (eff == pqi::ENC_DELTA_BP) {
           pp.dtab = static_cast<uint32_t>(plan->delta_blocks);
           plan->delta_blocks += pg.num_values > 1 ? static_cast<uint64_t>(pg.num_values - 2) / 128 + 1 : 1;
           pp.dreg = static_cast<uint32_t>(plan->delta_regions);
@@ -878,9 +923,9 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
         }
         if (needs_walk && !plain) {
           plan->walk_pps.push_back(static_cast<uint32_t>(plan->pps.size()));
-          walk_cost.push_back(pg.encoding == pqi::ENC_DELTA_BP ? pg.num_values / 128 + (cd.max_def ? pg.num_values / 8 : 0)
+          walk_cost.push_back(eff == pqi::ENC_DELTA_BP ? pg.num_values / 128 + (cd.max_def ? pg.num_values / 8 : 0)
                               : cd.max_def ? pg.num_values / 8
-                              : cd.ptype == pqi::T_BYTE_ARRAY && pg.encoding == pqi::ENC_PLAIN ? pg.num_values
+                              : cd.ptype == pqi::T_BYTE_ARRAY && eff == pqi::ENC_PLAIN ? pg.num_values
                                                                                                  : pg.num_values / 256);
         }
         const int64_t span = pp.row_hi - pp.row_lo;
@@ -905,6 +950,7 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
     cw.dict_n = static_cast<int>(plan->dict_jobs.size()) - cw.dict_begin;
     cw.walk_n = static_cast<int>(plan->walk_pps.size()) - cw.walk_begin;
     cw.delta_n = static_cast<int>(plan->delta_pps.size()) - cw.delta_begin;
+    cw.tc_n = static_cast<int>(plan->tc_jobs.size()) - cw.tc_begin;
     cw.max_fixed_dict = plan->max_fixed_dict_bytes;
     plan->max_fixed_dict_bytes = std::max(max_fixed_before, plan->max_fixed_dict_bytes);
     plan->colwork.push_back(cw);
@@ -923,6 +969,9 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
     for (size_t i = 0; i < order.size(); ++i) sorted[i] = plan->walk_pps[order[i]];
     std::copy(sorted.begin(), sorted.end(), plan->walk_pps.begin() + cw.walk_begin);
   }
+  plan->tc_pool_off = scratch;
+  plan->tc_pool_bytes = tc_pool;
+  scratch += tc_pool;
   plan->device_bytes = plan_device_bytes(plan.get(), scratch);
   plan->host_scratch = scratch;
   *out = std::move(plan);
@@ -950,6 +999,7 @@ pq_status plan_upload(pq_plan* plan) {
   plan->d_cols = plan_alloc(pqi::OutCol, plan, plan->outcols.size());
   plan->d_snappy = plan_alloc(pqi::SnappyJob, plan, plan->snappy_data.size() + plan->snappy_dict.size());
   plan->d_dict_jobs = plan_alloc(pqi::DictJob, plan, plan->dict_jobs.size());
+  plan->d_tc_jobs = plan_alloc(pqi::TranscodeJob, plan, plan->tc_jobs.size());
   plan->d_str_cols = plan_alloc(int32_t, plan, plan->str_cols.size());
   plan->d_counter = plan_alloc(uint32_t, plan, 4 + plan->outcols.size());
   plan->d_status = plan_alloc(pqi::DevStatus, plan, 1);
@@ -979,6 +1029,15 @@ pq_status plan_upload(pq_plan* plan) {
       pp.pad = 0;
     }
   }
+  // transcode jobs: sources and destinations in the scratch; the plan page
+  // reads the PLAIN body (DELTA_BYTE_ARRAY: its source until the kernel
+  // points it at its piece of the pool)
+  for (size_t i = 0; i < plan->tc_jobs.size(); ++i) {
+    auto& j = plan->tc_jobs[i];
+    if (plan->tc_src_off[i] >= 0) j.src = plan->d_scratch + plan->tc_src_off[i];
+    j.dst = plan->tc_dst_off[i] >= 0 ? plan->d_scratch + plan->tc_dst_off[i] : nullptr;
+    plan->pps[j.pp].body = j.dst ? j.dst : j.src;
+  }
   for (size_t i = 0; i < plan->str_cols.size(); ++i) {
     auto& col = plan->outcols[plan->str_cols[i]];
     col.str_scratch = plan->d_str_scratch + static_cast<uint64_t>(plan->n_rows) * i;
@@ -995,6 +1054,9 @@ pq_status plan_upload(pq_plan* plan) {
                        cudaMemcpyHostToDevice, s));
   if (!plan->dict_jobs.empty())
     CK(cudaMemcpyAsync(plan->d_dict_jobs, plan->dict_jobs.data(), sizeof(pqi::DictJob) * plan->dict_jobs.size(),
+                       cudaMemcpyHostToDevice, s));
+  if (!plan->tc_jobs.empty())
+    CK(cudaMemcpyAsync(plan->d_tc_jobs, plan->tc_jobs.data(), sizeof(pqi::TranscodeJob) * plan->tc_jobs.size(),
                        cudaMemcpyHostToDevice, s));
   if (!plan->str_cols.empty())
     CK(cudaMemcpyAsync(plan->d_str_cols, plan->str_cols.data(), sizeof(int32_t) * plan->str_cols.size(),
@@ -1031,11 +1093,20 @@ pq_status plan_upload(pq_plan* plan) {
         n += (nj ? 1 : 0) + 1;
         job += nj;
       }
+      size_t tcj = 0;
+      for (auto& cp : plan->chunk_pp) {
+        int ntc = 0;
+        while (tcj + ntc < plan->tc_jobs.size() &&
+               plan->tc_jobs[tcj + ntc].pp < static_cast<uint32_t>(cp.first + cp.second))
+          ++ntc;
+        n += ntc ? 1 : 0;
+        tcj += ntc;
+      }
     } else {
       for (size_t oc = 0; oc < plan->colwork.size(); ++oc) {
         const auto& cw = plan->colwork[oc];
         n += (cw.snap_dict_n ? 1 : 0) + (cw.dict_n ? 2 : 0) + (cw.snap_data_n ? 1 : 0) + (cw.walk_n ? 1 : 0) +
-             (cw.delta_n ? 4 : 0) + (plan->outcols[oc].item_count ? 1 : 0);
+             (cw.delta_n ? 4 : 0) + (cw.tc_n ? 1 : 0) + (plan->outcols[oc].item_count ? 1 : 0);
       }
     }
     for (int32_t sc : plan->str_cols) n += plan->outcols[sc].item_count ? 2 : 0;
@@ -1058,7 +1129,8 @@ uint64_t plan_device_bytes(const pq_plan* plan, uint64_t scratch) {
   const uint64_t str_rows = static_cast<uint64_t>(plan->n_rows) * plan->str_cols.size();
   return npp * sizeof(pqi::PlanPage) + nit * sizeof(pqi::Item) + plan->outcols.size() * sizeof(pqi::OutCol) +
          (plan->snappy_data.size() + plan->snappy_dict.size()) * sizeof(pqi::SnappyJob) +
-         plan->dict_jobs.size() * sizeof(pqi::DictJob) + 4 * (plan->walk_pps.size() + plan->delta_pps.size()) +
+         plan->dict_jobs.size() * sizeof(pqi::DictJob) + plan->tc_jobs.size() * sizeof(pqi::TranscodeJob) +
+         4 * (plan->walk_pps.size() + plan->delta_pps.size()) +
          plan->delta_blocks * 12 +
          plan->delta_regions * (sizeof(pqi::DeltaRegion) + 4ull * pqi::DELTA_REGION_LIST) +
          plan->dict_regions * (sizeof(pqi::DeltaRegion) + 8ull * pqi::STR_REGION_LIST) + scratch + 64 +
@@ -1135,6 +1207,12 @@ static int max_str_regions_all(const pq_plan* plan) {
   return m;
 }
 
+static void enqueue_transcode(pq_plan* plan, int begin, int n, const pqi::DecodeArgs& a, cudaStream_t s) {
+  if (n <= 0) return;
+  pqi::launch_transcode(plan->d_tc_jobs + begin, n, plan->d_pps, plan->d_scratch + plan->tc_pool_off,
+                        plan->tc_pool_bytes, plan->d_counter, a.st, s);
+}
+
 // Kernels of one output column, in order, on one stream.
 static void enqueue_column(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, bool with_dicts, cudaStream_t s) {
   pq_ctx* ctx = plan->ctx;
@@ -1146,6 +1224,7 @@ static void enqueue_column(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, b
     pqi::launch_dict(plan->d_dict_jobs + cw.dict_begin, cw.dict_n, cw.max_fixed_dict, cw.max_str_regions,
                      pqi::DictScratch{plan->d_sregs, plan->d_slists}, plan->idx->d_dicts, ctx->n_sms, a.st, s);
   if (cw.snap_data_n) pqi::launch_snappy(plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, ctx->n_sms, a.st, s);
+  enqueue_transcode(plan, cw.tc_begin, cw.tc_n, a, s);
   const auto& col = plan->outcols[oc];
   pqi::launch_walk(a, cw.walk_begin, cw.walk_n, ctx->n_sms, col.optional != 0, s);
   pqi::launch_delta_bases(a, cw.delta_begin, cw.delta_n, cw.max_regions, s);
@@ -1188,7 +1267,7 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
                        max_str_regions_all(plan), pqi::DictScratch{plan->d_sregs, plan->d_slists}, plan->idx->d_dicts,
                        ctx->n_sms, a.st, s);
     mark(3);
-    size_t job = 0;
+    size_t job = 0, tcj = 0;
     for (size_t k = 0; k < plan->chunk_pp.size(); ++k) {
       const int first = plan->chunk_pp[k].first, n = plan->chunk_pp[k].second;
       int nj = 0;
@@ -1197,6 +1276,10 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
           ++nj;
       if (nj) pqi::launch_snappy(plan->d_snappy + job, nj, ctx->n_sms, a.st, s);
       job += nj;
+      int ntc = 0;
+      while (tcj + ntc < plan->tc_jobs.size() && plan->tc_jobs[tcj + ntc].pp < static_cast<uint32_t>(first + n)) ++ntc;
+      enqueue_transcode(plan, static_cast<int>(tcj), ntc, a, s);
+      tcj += ntc;
       pqi::launch_plain_pages(a, first, n, s);
     }
     mark(4);
@@ -1209,6 +1292,7 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
       if (with_dicts && cw.snap_dict_n)
         pqi::launch_snappy(plan->d_snappy + n_data_jobs + cw.snap_dict_begin, cw.snap_dict_n, ctx->n_sms, a.st, s);
       if (cw.snap_data_n) pqi::launch_snappy(plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, ctx->n_sms, a.st, s);
+      enqueue_transcode(plan, cw.tc_begin, cw.tc_n, a, s);
     }
     mark(2);
     for (int oc = 0; oc < ncols; ++oc) {

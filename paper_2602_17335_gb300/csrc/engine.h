@@ -105,6 +105,12 @@ struct pq_plan {
   std::vector<int32_t> str_cols;             // output columns of type BYTE_ARRAY
   std::vector<uint32_t> walk_pps;            // plan pages that need the walk, longest first
   std::vector<uint32_t> delta_pps;           // DELTA plan pages
+  // V2 pages rewritten into PLAIN bodies (plan page order); host side: where
+  // each job's source and destination lie (scratch offset, or -1: `src` is
+  // the stored page / the destination is the pool)
+  std::vector<pqi::TranscodeJob> tc_jobs;
+  std::vector<int64_t> tc_src_off, tc_dst_off;
+  uint64_t tc_pool_off = 0, tc_pool_bytes = 0;  // DELTA_BYTE_ARRAY pool within the scratch
   uint64_t delta_blocks = 0;                 // capacity of the DELTA block tables
   uint64_t delta_regions = 0;                // capacity of the DELTA region tables
   uint64_t dict_regions = 0;                 // capacity of the string-dictionary region tables
@@ -124,6 +130,7 @@ struct pq_plan {
   pqi::OutCol* d_cols = nullptr;
   pqi::SnappyJob* d_snappy = nullptr;        // data jobs then dict jobs
   pqi::DictJob* d_dict_jobs = nullptr;
+  pqi::TranscodeJob* d_tc_jobs = nullptr;
   int32_t* d_str_cols = nullptr;
   uint8_t* d_scratch = nullptr;
   uint64_t* d_str_scratch = nullptr;
@@ -157,6 +164,7 @@ struct pq_plan {
     int max_fixed_dict = 0;
     int walk_begin = 0, walk_n = 0;            // into walk_pps
     int delta_begin = 0, delta_n = 0;          // into delta_pps
+    int tc_begin = 0, tc_n = 0;                // into tc_jobs
     int max_regions = 0;                       // most DELTA regions of one page
     int max_str_regions = 0;                   // most chain regions of one string dictionary
     bool copy_only = false;                    // every page REQUIRED PLAIN fixed-width

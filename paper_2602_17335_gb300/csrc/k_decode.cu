@@ -626,7 +626,7 @@ __device__ bool page_ctx(const DecodeArgs& a, const PlanPage& pp, PageCtx* pc) {
   pc->blen = static_cast<uint32_t>(pp.body_len);
   pc->nrows = pg.num_values;
   pc->pgid = static_cast<int32_t>(pp.page);
-  pc->enc = pg.encoding;
+  pc->enc = pp.enc;
   pc->ptype = ch.ptype;
   pc->width = ch.width;
   pc->max_def = ch.max_def;
@@ -2417,12 +2417,11 @@ __device__ void expand_item(const DecodeArgs& a, int it_id, WarpSmem& ws, int la
   if (it.nrows <= 0) return;
   const PlanPage pp = a.pps[it.pp];
   if (pp.nonnull < 0) return;  // the walk of this page failed (error recorded)
-  const PageDev pg = a.pages[pp.page];
   const OutCol col = a.cols[pp.col];
   const int pgid = static_cast<int>(pp.page);
   const uint8_t* sb = pp.body + pp.values_off;
   const uint32_t slen = static_cast<uint32_t>(pp.body_len - pp.values_off);
-  const int enc = pg.encoding;
+  const int enc = pp.enc;
   const bool isdict = enc == ENC_RLE_DICT || enc == ENC_PLAIN_DICT;
   const bool isdelta = enc == ENC_DELTA_BP;
   const bool isba = col.ptype == T_BYTE_ARRAY;
@@ -2711,6 +2710,7 @@ __global__ void __launch_bounds__(256, 4) k_str_copy(DecodeArgs a, int c) {
     const PlanPage pp = a.pps[it.pp];
     const OutCol col = a.cols[pp.col];
     if (col.ptype != T_BYTE_ARRAY || pp.nonnull < 0) continue;
+    // (a transcoded page is never a dictionary page: its own encoding decides)
     const PageDev pg = a.pages[pp.page];
     const bool isdict = pg.encoding == ENC_RLE_DICT || pg.encoding == ENC_PLAIN_DICT;
     DictDev dd{};
@@ -2886,14 +2886,13 @@ __global__ void __launch_bounds__(WALK_THREADS) k_plain_page(DecodeArgs a, int p
   const int p = pp_begin + blockIdx.x;
   walk_init(sm, CWIN);
   const PlanPage pp0 = a.pps[p];
-  const PageDev pg = a.pages[pp0.page];
   const ChunkDev ch = a.chunks[pp0.chunk];
-  const bool needs_walk = ch.max_def || pg.encoding != ENC_PLAIN || ch.ptype == T_BYTE_ARRAY;
+  const bool needs_walk = ch.max_def || pp0.enc != ENC_PLAIN || ch.ptype == T_BYTE_ARRAY;
   if (needs_walk) walk_page(a, p, sm, true);
   __syncthreads();
   // the chain windows, free again: scan scratch, then the warps' staging
   uint8_t* wins = smraw + ((sizeof(WalkSmem) + 15) & ~size_t(15));
-  if (pg.encoding == ENC_DELTA_BP) {
+  if (pp0.enc == ENC_DELTA_BP) {
     delta_bases_page(a, p, reinterpret_cast<uint64_t*>(wins + CWIN + 16));
     __syncthreads();
   }

@@ -38,7 +38,7 @@ enum : uint32_t {
 // Where in the engine an error was raised (stored with the first error).
 enum : int32_t {
   WHERE_INDEX = 1, WHERE_SNAPPY = 2, WHERE_DICT = 3, WHERE_WALK_LEVELS = 4, WHERE_WALK_VALUES = 5,
-  WHERE_EXPAND = 6, WHERE_STRINGS = 7, WHERE_PLAIN = 8
+  WHERE_EXPAND = 6, WHERE_STRINGS = 7, WHERE_PLAIN = 8, WHERE_TRANSCODE = 9
 };
 
 struct DevStatus {
@@ -122,6 +122,8 @@ struct PlanPage {
   int32_t dreg_cap;        // DELTA: region rows reserved for the page
   int32_t pad;             // host: 1 while `body` is a scratch offset
   int32_t item_rows;       // rows per work item of this page
+  int32_t enc;             // encoding the kernels decode: the page's own, or PLAIN once a
+                           // BYTE_STREAM_SPLIT / DELTA_(LENGTH_)BYTE_ARRAY page is transcoded
 };
 
 // DELTA block-chain region (speculative parallel walk): regions of
