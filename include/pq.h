@@ -331,7 +331,13 @@ typedef struct pq_write_column {
   const char* name;
   int32_t type;              /* PQ_TYPE_INT32 / INT64 / DOUBLE / BYTE_ARRAY */
   int32_t encoding;          /* Parquet Encoding: 0 PLAIN, 8 RLE_DICTIONARY,
-                                5 DELTA_BINARY_PACKED */
+                                5 DELTA_BINARY_PACKED (INT32/INT64), 9 BYTE_STREAM_SPLIT
+                                (fixed width), 6 DELTA_LENGTH_BYTE_ARRAY and 7
+                                DELTA_BYTE_ARRAY (BYTE_ARRAY); -1: per chunk, every valid
+                                encoding of the type is tried and the one with the smallest
+                                uncompressed chunk is kept, ties to the earlier of
+                                0, 8, 5, 9 (integers), 0, 8, 9 (DOUBLE), 0, 8, 6, 7
+                                (BYTE_ARRAY) (paper Section 3, "Encoding Flexibility") */
   int32_t codec;             /* 0 UNCOMPRESSED, 1 SNAPPY */
   int32_t page_version;      /* 1 DATA_PAGE, 2 DATA_PAGE_V2 */
   double compress_threshold; /* < 0: keep the codec's output; else keep it only when the
@@ -351,12 +357,16 @@ typedef struct pq_write_column {
  * being the bits per row (8*width for PLAIN, the index bit width for
  * dictionary indices, +1 for a definition level when OPTIONAL); a REQUIRED
  * DELTA_BINARY_PACKED page holds 1 + 128k values, the most whole 128-value
- * blocks that fit page_bytes; PLAIN BYTE_ARRAY pages take rows while they
- * fit; dictionary entries in order of first appearance; hybrid runs: a
+ * blocks that fit page_bytes; BYTE_ARRAY pages that are not dictionary
+ * encoded take rows while their PLAIN encoding fits; BYTE_STREAM_SPLIT pages
+ * as PLAIN; dictionary entries in order of first appearance; hybrid runs: a
  * repeated run for >= 8 equal values, else bit-packed runs of <= 63 groups;
  * an OffsetIndex per chunk when `offset_index` is nonzero.
  * `*out` is allocated with malloc (free with pq_write_free); `n_threads`
- * threads encode chunks in parallel (<= 0: hardware threads). */
+ * threads encode chunks in parallel (<= 0: hardware threads).  Host code
+ * only: needs no GPU.  Errors: PQ_ERR_INVALID_ARG (NULL pointers, sizes,
+ * an encoding not valid for the column's type), PQ_ERR_UNSUPPORTED (other
+ * types, encodings or codecs), PQ_ERR_OOM. */
 pq_status pq_write_table(const pq_write_column* cols, int n_cols, int64_t n_rows, int64_t rg_rows,
                          int64_t page_bytes, int offset_index, int n_threads, uint8_t** out,
                          uint64_t* out_size);

@@ -31,10 +31,15 @@ them byte for byte on uncompressed data):
   otherwise); V1 definition levels carry a 4-byte length prefix;
 * V1 pages compress levels and values together, V2 pages compress values
   only; the dictionary page body is compressed with the chunk's codec;
+* encoding "AUTO": each chunk is written with the valid encoding of its type
+  whose uncompressed chunk is smallest (``CANDIDATES`` order breaks ties);
 * an OffsetIndex per chunk (data pages only, first_row_index relative to the
   row group) is written after the last row group when requested.
 """
 from __future__ import annotations
+
+import copy
+from dataclasses import replace
 
 import numpy as np
 
@@ -180,9 +185,34 @@ def _compress(codec, data):
     return _snappy.compress(data) if codec == SNAPPY else bytes(data)
 
 
+# Valid encodings per physical type, in the order a tie is broken (the
+# paper's Section 3, "Encoding Flexibility": every valid encoding of the
+# type is tried per chunk and the smallest one is kept).
+CANDIDATES = {"INT32": ("PLAIN", "RLE_DICTIONARY", "DELTA_BINARY_PACKED", "BYTE_STREAM_SPLIT"),
+              "INT64": ("PLAIN", "RLE_DICTIONARY", "DELTA_BINARY_PACKED", "BYTE_STREAM_SPLIT"),
+              "DOUBLE": ("PLAIN", "RLE_DICTIONARY", "BYTE_STREAM_SPLIT"),
+              "BYTE_ARRAY": ("PLAIN", "RLE_DICTIONARY", "DELTA_LENGTH_BYTE_ARRAY", "DELTA_BYTE_ARRAY")}
+
+
+def choose_encoding(col, cspec: ColumnSpec, page_bytes: int, rng=None):
+    """The candidate whose uncompressed chunk (headers + page bodies) is
+    smallest; ties go to the earlier candidate."""
+    best, best_size = None, None
+    for enc in CANDIDATES[col.ptype]:
+        trial = replace(cspec, encoding=enc, codec="UNCOMPRESSED", compress_threshold=None)
+        _, meta, _, _ = write_chunk(col, trial, page_bytes, 0, copy.deepcopy(rng))
+        size = dict((f, v) for f, _, v in meta)[6]
+        if best is None or size < best_size:
+            best, best_size = enc, size
+    return best
+
+
 def write_chunk(col, cspec: ColumnSpec, page_bytes: int, base: int, rng=None):
     """Encodes one column chunk.  Returns (bytes, ColumnMetaData fields list,
-    page locations, codec actually used)."""
+    page locations, codec actually used).  Encoding "AUTO" writes the chunk
+    with ``choose_encoding``'s pick."""
+    if cspec.encoding == "AUTO":
+        cspec = replace(cspec, encoding=choose_encoding(col, cspec, page_bytes, rng))
     ptype = col.ptype
     enc_name = cspec.encoding
     codec = CODEC_ID[cspec.codec]

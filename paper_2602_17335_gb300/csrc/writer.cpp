@@ -1,17 +1,22 @@
 // Parquet writer — the offline rewriter of the paper's Sections 3 and 5:
 // a flat table is written with a chosen row-group size, page size,
-// encoding per column chunk (V1 PLAIN / dictionary, V2 DELTA_BINARY_PACKED),
-// page version, and per-chunk compression kept only when it shrinks the
-// chunk by more than a threshold (Section 3, "No Unnecessary Compression").
+// encoding per column chunk (V1 PLAIN / dictionary, the V2 set
+// DELTA_BINARY_PACKED, DELTA_LENGTH_BYTE_ARRAY, DELTA_BYTE_ARRAY and
+// BYTE_STREAM_SPLIT), page version, and per-chunk compression kept only when
+// it shrinks the chunk by more than a threshold (Section 3, "No Unnecessary
+// Compression").  With encoding -1 every chunk tries each valid encoding of
+// its type and keeps the one with the smallest encoded (uncompressed) chunk
+// (Section 3, "Encoding Flexibility").
 //
 // Layout rules (identical to the ones the engine documents for pq_write_table):
 //  * row group k holds rows [k*rg_rows, (k+1)*rg_rows);
 //  * rows per data page: max(8, floor(page_bytes*8 / b) rounded down to a
 //    multiple of 8), b = 8*width (PLAIN) or max(index bit width, 1)
-//    (dictionary), +1 when OPTIONAL; REQUIRED DELTA pages hold 1 + 128k
-//    values (the most whole blocks that fit page_bytes, a shorter tail taken
-//    whole when it fits); PLAIN BYTE_ARRAY pages take rows while the page has
-//    fewer than 8 rows or the encoded bytes still fit;
+//    (dictionary), +1 when OPTIONAL (BYTE_STREAM_SPLIT as PLAIN); REQUIRED
+//    DELTA pages hold 1 + 128k values (the most whole blocks that fit
+//    page_bytes, a shorter tail taken whole when it fits); BYTE_ARRAY pages
+//    that are not dictionary encoded take rows while the page has fewer than
+//    8 rows or the PLAIN-encoded bytes still fit;
 //  * dictionary entries in order of first appearance, index bit width =
 //    bit length of (entries - 1);
 //  * hybrid runs: a repeated run for >= 8 equal values when the pending
@@ -209,6 +214,21 @@ struct DeltaEnc {
     return s;
   }
 };
+
+// One DELTA_BINARY_PACKED INT32 stream (the length streams of the delta
+// string encodings).
+void delta_stream32(Bytes& o, const std::vector<int64_t>& v) {
+  const DeltaEnc de{32};
+  const size_t n = v.size();
+  de.header(o, n, n ? v[0] : 0);
+  int64_t dd[128];
+  for (size_t b = 1; b < n; b += 128) {
+    const size_t m = std::min<size_t>(128, n - b);
+    for (size_t q = 0; q < m; ++q)
+      dd[q] = de.sgn(static_cast<uint64_t>(v[b + q]) - static_cast<uint64_t>(v[b + q - 1]));
+    de.block(o, dd, m);
+  }
+}
 
 // ------------------------------------------------------------------ Snappy compressor
 
@@ -528,6 +548,39 @@ void encode_chunk(const ColIn& in, int64_t page_bytes, int codec, ChunkOut* out)
                            static_cast<uint64_t>(sval(rows_nn[vpos + b + q - 1])));
           de.block(vals, dd, m);
         }
+      } else if (c.encoding == 9) {
+        // BYTE_STREAM_SPLIT: stream b holds byte b of every value
+        size_t base = vals.size();
+        vals.resize(base + nn * width);
+        for (size_t k = 0; k < nn; ++k) {
+          const uint64_t v = fixed_bits(rows_nn[vpos + k]);
+          for (int b = 0; b < width; ++b) vals[base + b * nn + k] = static_cast<uint8_t>(v >> (8 * b));
+        }
+      } else if (c.encoding == 6 || c.encoding == 7) {
+        // DELTA_LENGTH_BYTE_ARRAY: lengths, then bytes; DELTA_BYTE_ARRAY:
+        // prefix lengths against the previous value of the page, then the
+        // suffixes as DELTA_LENGTH_BYTE_ARRAY
+        std::vector<int64_t> pre(nn, 0), suf(nn);
+        const uint8_t* prev = nullptr;
+        int64_t prev_len = 0;
+        for (size_t k = 0; k < nn; ++k) {
+          const uint8_t* p;
+          const int64_t len = str(rows_nn[vpos + k], &p);
+          int64_t cp = 0;
+          if (c.encoding == 7)
+            while (cp < len && cp < prev_len && p[cp] == prev[cp]) ++cp;
+          pre[k] = cp;
+          suf[k] = len - cp;
+          prev = p;
+          prev_len = len;
+        }
+        if (c.encoding == 7) delta_stream32(vals, pre);
+        delta_stream32(vals, suf);
+        for (size_t k = 0; k < nn; ++k) {
+          const uint8_t* p;
+          str(rows_nn[vpos + k], &p);
+          vals.insert(vals.end(), p + pre[k], p + pre[k] + suf[k]);
+        }
       } else if (is_ba) {
         for (size_t k = 0; k < nn; ++k) {
           const uint8_t* p;
@@ -612,8 +665,11 @@ pq_status pq_write_table(const pq_write_column* cols, int n_cols, int64_t n_rows
     const bool fixed = col.type == PQ_TYPE_INT32 || col.type == PQ_TYPE_INT64 || col.type == PQ_TYPE_DOUBLE ||
                        col.type == PQ_TYPE_FLOAT;
     if (!fixed && col.type != PQ_TYPE_BYTE_ARRAY) return PQ_ERR_UNSUPPORTED;
-    if (col.encoding != 0 && col.encoding != 2 && col.encoding != 8 && col.encoding != 5) return PQ_ERR_UNSUPPORTED;
-    if (col.encoding == 5 && col.type != PQ_TYPE_INT32 && col.type != PQ_TYPE_INT64) return PQ_ERR_INVALID_ARG;
+    const int e = col.encoding;
+    if (e != -1 && e != 0 && e != 2 && e != 8 && e != 5 && e != 6 && e != 7 && e != 9) return PQ_ERR_UNSUPPORTED;
+    if (e == 5 && col.type != PQ_TYPE_INT32 && col.type != PQ_TYPE_INT64) return PQ_ERR_INVALID_ARG;
+    if ((e == 6 || e == 7) && col.type != PQ_TYPE_BYTE_ARRAY) return PQ_ERR_INVALID_ARG;
+    if (e == 9 && !fixed) return PQ_ERR_INVALID_ARG;
     if (col.codec != 0 && col.codec != 1) return PQ_ERR_UNSUPPORTED;
     if (col.page_version != 1 && col.page_version != 2) return PQ_ERR_INVALID_ARG;
     if (!col.values && n_rows > 0) return PQ_ERR_INVALID_ARG;
@@ -627,9 +683,35 @@ pq_status pq_write_table(const pq_write_column* cols, int n_cols, int64_t n_rows
   int nt = n_threads > 0 ? n_threads : static_cast<int>(std::thread::hardware_concurrency());
   nt = std::max(1, std::min<int>(nt, static_cast<int>(jobs.size())));
   std::atomic<size_t> next{0};
+  // encoding -1: the chunk keeps the valid encoding of its type with the
+  // smallest encoded (uncompressed) size; ties go to the earlier candidate
+  std::vector<pq_write_column> chosen(jobs.size());
   auto worker = [&]() {
-    for (size_t j; (j = next.fetch_add(1)) < jobs.size();)
-      encode_chunk(jobs[j], page_bytes, jobs[j].c->codec, &chunks[j]);
+    for (size_t j; (j = next.fetch_add(1)) < jobs.size();) {
+      if (jobs[j].c->encoding != -1) {
+        encode_chunk(jobs[j], page_bytes, jobs[j].c->codec, &chunks[j]);
+        continue;
+      }
+      static const int kInt[] = {0, 8, 5, 9}, kFloat[] = {0, 8, 9}, kStr[] = {0, 8, 6, 7};
+      const int t = jobs[j].c->type;
+      const int* cand = t == PQ_TYPE_BYTE_ARRAY ? kStr : (t == PQ_TYPE_INT32 || t == PQ_TYPE_INT64) ? kInt : kFloat;
+      const int n_cand = t == PQ_TYPE_DOUBLE || t == PQ_TYPE_FLOAT ? 3 : 4;
+      int best = -1;
+      int64_t best_size = 0;
+      for (int k = 0; k < n_cand; ++k) {
+        pq_write_column trial = *jobs[j].c;
+        trial.encoding = cand[k];
+        ChunkOut co;
+        encode_chunk(ColIn{&trial, jobs[j].r0, jobs[j].r1}, page_bytes, 0, &co);
+        if (best < 0 || co.total_unc < best_size) {
+          best = cand[k];
+          best_size = co.total_unc;
+        }
+      }
+      chosen[j] = *jobs[j].c;
+      chosen[j].encoding = best;
+      encode_chunk(ColIn{&chosen[j], jobs[j].r0, jobs[j].r1}, page_bytes, chosen[j].codec, &chunks[j]);
+    }
   };
   std::vector<std::thread> th;
   for (int t = 1; t < nt; ++t) th.emplace_back(worker);

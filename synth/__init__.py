@@ -195,7 +195,8 @@ def sorted_lowcard_int32(rng, n, card, rg_rows):
 @dataclass
 class ColumnSpec:
     # PLAIN | RLE_DICTIONARY | DELTA_BINARY_PACKED | BYTE_STREAM_SPLIT |
-    # DELTA_LENGTH_BYTE_ARRAY | DELTA_BYTE_ARRAY
+    # DELTA_LENGTH_BYTE_ARRAY | DELTA_BYTE_ARRAY | AUTO (per chunk, the
+    # smallest valid encoding of the column's type)
     encoding: str = PLAIN
     codec: str = UNCOMPRESSED        # UNCOMPRESSED | SNAPPY
     page_version: int = 1            # 1 = DATA_PAGE, 2 = DATA_PAGE_V2

@@ -1,0 +1,165 @@
+"""The engine's native writer (`pq_write_table`, the rewriter of the paper's
+Sections 3 and 5) against the oracle writer, on the CPU (no GPU needed).
+
+Both follow the same deterministic layout rules, so on uncompressed data
+they must write the same bytes (only the footer's created_by differs);
+with Snappy the compressors differ, so the file must read back to the table
+and keep the same page structure.  The per-chunk encoding choice ("AUTO",
+Section 3's "Encoding Flexibility") is pinned to the smallest explicit
+encoding of each chunk and to the obvious winners of shaped data."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import reader as R
+from oracle import thrift as T
+from oracle import writer as W
+
+
+def _native():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2602_17335_gb300 import native as N
+    from paper_2602_17335_gb300.tables import write_table
+    return N, write_table
+
+
+def _split(data):
+    """(bytes before the footer, footer fields without created_by)."""
+    flen = int.from_bytes(data[-8:-4], "little")
+    fs = len(data) - 8 - flen
+    meta, _ = T.decode_struct(data, fs, len(data) - 8)
+    meta.pop(6, None)
+    return data[:fs], meta
+
+
+def _tables():
+    return {"eight_column": (synth.config2_table(12_000, 5000, string_pool_size=300, zipf_k=500),
+                             lambda v: synth.config2_spec(5000, 3000, "UNCOMPRESSED", v)),
+            "v2_encodings": (synth.v2_encodings_table(12_000, 5000),
+                             lambda v: synth.v2_encodings_spec(5000, 3000, "UNCOMPRESSED", v))}
+
+
+def _string_rows(col):
+    off, ch = col.values.materialize()
+    rows = [bytes(ch[off[j]:off[j + 1]]) for j in range(len(off) - 1)]
+    return rows if col.valid is None else [x if v else b"" for x, v in zip(rows, col.valid)]
+
+
+@pytest.mark.parametrize("table", ["eight_column", "v2_encodings"])
+@pytest.mark.parametrize("version", [1, 2])
+@pytest.mark.parametrize("auto", [False, True])
+def test_native_writer_matches_oracle_bytes(table, version, auto):
+    _, write_table = _native()
+    tab, spec_of = _tables()[table]
+    spec = spec_of(version)
+    if auto:
+        for c in spec.columns:
+            c.encoding = "AUTO"
+    native = bytes(write_table(tab, spec))
+    oracle = W.write_file(tab, spec)
+    assert _split(native) == _split(oracle)
+
+
+@pytest.mark.parametrize("version", [1, 2])
+def test_native_writer_snappy_reads_back(version):
+    _, write_table = _native()
+    tab = synth.v2_encodings_table(9000, 4000)
+    spec = synth.v2_encodings_spec(4000, 2048, "SNAPPY", version)
+    native = bytes(write_table(tab, spec))
+    res = R.read_file(native)
+    for col, r in zip(tab.columns, res):
+        if col.ptype == "BYTE_ARRAY":
+            got = [bytes(r.chars[r.offsets[j]:r.offsets[j + 1]]) for j in range(len(r.offsets) - 1)]
+            assert got == _string_rows(col), col.name
+        else:
+            assert np.array_equal(np.asarray(col.values).view(np.uint8), r.values.view(np.uint8)), col.name
+    # same pages (row counts, encodings) as the oracle writer's file
+    oracle = W.write_file(tab, spec)
+
+    def pages(data):
+        info = R.parse_footer(data)
+        return [[(p.page_type, p.num_values, p.encoding) for p in R.chunk_pages(data, ch)] for ch in info.chunks]
+
+    assert pages(native) == pages(oracle)
+
+
+def test_selective_compression_decisions():
+    """Insight 4's threshold: incompressible doubles drop Snappy, sorted
+    low-cardinality values keep it, in both writers."""
+    _, write_table = _native()
+    rng = np.random.default_rng(4)
+    n = 20_000
+    cols = [synth.ColumnData("noise", "DOUBLE", rng.standard_normal(n)),
+            synth.ColumnData("sorted", "INT32", np.sort(rng.integers(0, 40, n)).astype(np.int32))]
+    tab = synth.Table(cols)
+    spec = synth.TableSpec(n, 1 << 16, [synth.ColumnSpec("PLAIN", "SNAPPY", 1, compress_threshold=0.10)
+                                        for _ in cols])
+    for data in (bytes(write_table(tab, spec)), W.write_file(tab, spec)):
+        codecs = [ch.codec for ch in R.parse_footer(data).chunks]
+        assert codecs == [0, 1]
+
+
+def test_auto_is_the_smallest_candidate():
+    """AUTO's chunk equals the smallest explicit candidate of its type."""
+    tab = synth.v2_encodings_table(6000, 6000)
+    tab2 = synth.config2_table(6000, 6000, string_pool_size=300, zipf_k=500)
+    for col in tab.columns + tab2.columns:
+        sizes = {}
+        for enc in W.CANDIDATES[col.ptype]:
+            _, meta, _, _ = W.write_chunk(col, synth.ColumnSpec(enc), 4096, 0)
+            sizes[enc] = dict((f, v) for f, _, v in meta)[6]
+        _, meta, _, _ = W.write_chunk(col, synth.ColumnSpec("AUTO"), 4096, 0)
+        assert dict((f, v) for f, _, v in meta)[6] == min(sizes.values()), col.name
+        assert W.choose_encoding(col, synth.ColumnSpec("AUTO"), 4096) == min(sizes, key=lambda e: (
+            sizes[e], W.CANDIDATES[col.ptype].index(e)))
+
+
+def test_auto_obvious_winners():
+    """Shaped data whose best encoding follows from the definitions:
+    sorted keys with small steps -> DELTA_BINARY_PACKED (about 3 bits per
+    value); 16 distinct values -> RLE_DICTIONARY (4-bit indices); sorted
+    strings with long shared stems -> DELTA_BYTE_ARRAY; distinct random
+    strings -> DELTA_LENGTH_BYTE_ARRAY (packed lengths beat 4-byte ones);
+    random doubles -> PLAIN (BYTE_STREAM_SPLIT has the same size; the tie
+    goes to PLAIN)."""
+    rng = np.random.default_rng(12)
+    n = 8000
+    cases = [
+        (synth.ColumnData("keys", "INT64", synth.sorted_keys_int64(rng, n)), "DELTA_BINARY_PACKED"),
+        (synth.ColumnData("card16", "INT32", synth.lowcard_int32(rng, n, 16)), "RLE_DICTIONARY"),
+        (synth.ColumnData("stems", "BYTE_ARRAY", synth.strings_sorted(rng, n, n)), "DELTA_BYTE_ARRAY"),
+        (synth.ColumnData("distinct", "BYTE_ARRAY", synth.strings_uniform(rng, n, k=10 * n)), "DELTA_LENGTH_BYTE_ARRAY"),
+        (synth.ColumnData("noise", "DOUBLE", rng.standard_normal(n)), "PLAIN"),
+    ]
+    for col, want in cases:
+        assert W.choose_encoding(col, synth.ColumnSpec("AUTO"), 1 << 16) == want, col.name
+
+
+def test_native_writer_rejects_invalid_encodings():
+    N, _ = _native()
+    v = np.arange(16, dtype=np.int32)
+    for enc, status in ((6, N.PQ_ERR_INVALID_ARG), (7, N.PQ_ERR_INVALID_ARG), (3, N.PQ_ERR_UNSUPPORTED)):
+        w = N.pq_write_column()
+        w.name = b"x"
+        w.type = N.PQ_TYPE_INT32
+        w.encoding = enc
+        w.page_version = 1
+        w.compress_threshold = -1.0
+        w.values = v.ctypes.data
+        with pytest.raises(N.PqError) as ei:
+            N.pq_write_table([w], 16, 16, 1024)
+        assert ei.value.status == status
+    off = np.array([0, 1, 2], dtype=np.int64)
+    chars = np.frombuffer(b"ab", dtype=np.uint8).copy()
+    w = N.pq_write_column()
+    w.name = b"s"
+    w.type = N.PQ_TYPE_BYTE_ARRAY
+    w.encoding = 9
+    w.page_version = 1
+    w.compress_threshold = -1.0
+    w.values = off.ctypes.data
+    w.chars = chars.ctypes.data
+    with pytest.raises(N.PqError) as ei:
+        N.pq_write_table([w], 2, 2, 1024)
+    assert ei.value.status == N.PQ_ERR_INVALID_ARG
