@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rows", type=int, default=1 << 26)
+    ap.add_argument("--table", default="eight", choices=["eight", "v2"],
+                    help="scan: the eight-column table, or the six-column table of the other V2 encodings "
+                         "(BYTE_STREAM_SPLIT, DELTA_LENGTH_BYTE_ARRAY, DELTA_BYTE_ARRAY)")
     ap.add_argument("--rg-rows", type=int, default=1 << 23)
     ap.add_argument("--page-bytes", type=int, default=MiB)
     ap.add_argument("--codec", default="UNCOMPRESSED", choices=["UNCOMPRESSED", "SNAPPY"])
@@ -79,15 +82,22 @@ def parse_args():
 
 
 def workload_name(a):
-    return (f"eight-column table, {a.rows} rows, row groups of {a.rg_rows} rows, "
+    table = "six-column V2-encoding table" if getattr(a, "table", "eight") == "v2" else "eight-column table"
+    return (f"{table}, {a.rows} rows, row groups of {a.rg_rows} rows, "
             f"{a.page_bytes // 1024} KiB pages, {a.codec.lower()}, V{a.page_version} pages")
 
 
 def make_files(a, rank):
     """The table of this rank, written by the engine's native writer."""
     from paper_2602_17335_gb300.tables import write_table
-    tab = synth.config2_table(a.rows, a.rg_rows, file=rank)
-    spec = synth.config2_spec(a.rg_rows, a.page_bytes, a.codec, a.page_version, offset_index=not a.no_offset_index)
+    if getattr(a, "table", "eight") == "v2":
+        tab = synth.v2_encodings_table(a.rows, a.rg_rows, file=rank)
+        spec = synth.v2_encodings_spec(a.rg_rows, a.page_bytes, a.codec, a.page_version,
+                                       offset_index=not a.no_offset_index)
+    else:
+        tab = synth.config2_table(a.rows, a.rg_rows, file=rank)
+        spec = synth.config2_spec(a.rg_rows, a.page_bytes, a.codec, a.page_version,
+                                  offset_index=not a.no_offset_index)
     data = write_table(tab, spec)
     return data
 
@@ -275,7 +285,8 @@ def kernel_sources_digest():
 
 
 def traffic_key(a):
-    return f"{a.rg_rows}/{a.page_bytes}/{a.codec}/V{a.page_version}/{a.mode}/oi{int(not a.no_offset_index)}"
+    table = "v2/" if getattr(a, "table", "eight") == "v2" else ""
+    return f"{table}{a.rg_rows}/{a.page_bytes}/{a.codec}/V{a.page_version}/{a.mode}/oi{int(not a.no_offset_index)}"
 
 
 def stored_traffic(a):

@@ -443,6 +443,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_transcode(const TranscodeJob* jo
                                                          DevStatus* st) {
   __shared__ TcSmem sm;
   const TranscodeJob j = jobs[blockIdx.x];
+  {
+    // the page's bytes into L2 first (a hint): the stream headers are then
+    // followed by one thread at L2 rather than DRAM latency
+    const uintptr_t e = reinterpret_cast<uintptr_t>(j.src) + j.src_len;
+    for (uintptr_t q = (reinterpret_cast<uintptr_t>(j.src) & ~uintptr_t(127)) + 128u * threadIdx.x; q < e;
+         q += 128u * blockDim.x)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+  }
   if (threadIdx.x == 0) {
     sm.err = 0;
     sm.flag = 0;

@@ -163,3 +163,17 @@ def test_v2_encodings_corrupt_pages(eng, case, monkeypatch):
     with pytest.raises(N.PqError) as ei:
         eng.read([to_dev(data)])
     assert ei.value.status == N.PQ_ERR_CORRUPT
+
+
+@pytest.mark.parametrize("writer", ["oracle", "native"])
+def test_files_with_chosen_encodings(eng, writer):
+    """Files whose every chunk carries the smallest valid encoding of its type
+    (Section 3, "Encoding Flexibility"): encodings differ from chunk to chunk
+    of one column, V1 and V2 pages, with and without Snappy."""
+    from paper_2602_17335_gb300.tables import write_table
+    for tab, rg in ((synth.config2_table(20_000, 6000, string_pool_size=700, zipf_k=2000), 6000),
+                    (synth.v2_encodings_table(20_000, 7000), 7000)):
+        for codec, version in (("UNCOMPRESSED", 1), ("SNAPPY", 2)):
+            spec = synth.TableSpec(rg, 4096, [synth.ColumnSpec("AUTO", codec, version) for _ in tab.columns])
+            data = W.write_file(tab, spec) if writer == "oracle" else bytes(write_table(tab, spec))
+            _roundtrip(eng, data)
