@@ -268,7 +268,7 @@ class ClockSampler:
 # bench reports null.
 TRAFFIC_CAPTURES = {
     # profiles/traffic_eight_column_2p24_1MiB.md
-    "8388608/1048576/UNCOMPRESSED/V1/batched/oi1": {"rows": 16777216, "bytes": 1364678400, "sources": "e763436e4f145bc0"},
+    "8388608/1048576/UNCOMPRESSED/V1/batched/oi1": {"rows": 16777216, "bytes": 1365573120, "sources": "078ed2351ab25957"},
 }
 
 KERNEL_SOURCES = ("k_decode.cu", "k_index.cu", "k_snappy.cu", "k_transcode.cu", "dev_util.cuh", "thrift_dev.cuh",
