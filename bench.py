@@ -335,6 +335,38 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x, world):
+    """The largest x over the ranks: a multi-GPU step is as slow as its
+    slowest rank.  NCCL groups reduce on the rank's GPU, gloo on the host."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    """The sum of x over the ranks (bytes every rank decoded)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_gbs(bytes_all_ranks, seconds):
+    """Weak scaling: every rank scans its own table of the same shape (the
+    ranks' data differ by seed only); the job's rate is the bytes all ranks
+    decoded over the slowest rank's time."""
+    return bytes_all_ranks / seconds / 1e9
+
+
 def run_ours(a, rank, world, local_rank):
     import torch
     from paper_2602_17335_gb300 import native as N
@@ -386,14 +418,11 @@ def run_ours(a, rank, world, local_rank):
             step()
         end.record(stream)
         torch.cuda.synchronize(dev)
-    step_ms = start.elapsed_time(end) / a.steps
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(start.elapsed_time(end) / a.steps, world)
     decoded = float(pinfo.decoded_bytes)
     read = float(pinfo.read_bytes)
-    value = world * decoded / (step_ms * 1e-3) / 1e9
+    decoded_all = sum_over_ranks(decoded, world)
+    value = whole_job_gbs(decoded_all, step_ms * 1e-3)
 
     # roofline: one scan launch = all stages of pq_scan_columns, replayed from a graph
     idx = eng.index(files)
@@ -464,10 +493,10 @@ def run_ours(a, rank, world, local_rank):
         t0 = time.perf_counter()
         for _ in range(reps):
             N.pq_scan_host(eng.ctx, hfiles, outs=houts)
-        e2e_s = (time.perf_counter() - t0) / reps
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / reps, world)
         d2h = int(sum(s.values_bytes + s.validity_bytes for s in sizes) + sum(
             int(s.chars_bytes) for s in sizes))
-        e2e = {"value": world * decoded / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(data.nbytes),
+        e2e = {"value": whole_job_gbs(decoded_all, e2e_s), "unit": "GB/s", "h2d_bytes_per_step": int(data.nbytes),
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
         del keep
 
