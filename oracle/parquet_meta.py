@@ -17,8 +17,8 @@ ENCODING_ID = {"PLAIN": PLAIN, "RLE_DICTIONARY": RLE_DICTIONARY,
                "DELTA_BYTE_ARRAY": DELTA_BYTE_ARRAY, "BYTE_STREAM_SPLIT": BYTE_STREAM_SPLIT}
 
 # Codecs
-UNCOMPRESSED, SNAPPY = 0, 1
-CODEC_ID = {"UNCOMPRESSED": UNCOMPRESSED, "SNAPPY": SNAPPY}
+UNCOMPRESSED, SNAPPY, ZSTD = 0, 1, 6
+CODEC_ID = {"UNCOMPRESSED": UNCOMPRESSED, "SNAPPY": SNAPPY, "ZSTD": ZSTD}
 
 # Page types
 DATA_PAGE, INDEX_PAGE, DICTIONARY_PAGE, DATA_PAGE_V2 = 0, 1, 2, 3

@@ -9,7 +9,8 @@ column chunks -> pages; decompression then decoding):
   the next page header follows the previous header end plus its
   compressed_page_size; the walk stops once the data pages' num_values add up
   to the chunk's num_values;
-* V1 data page: whole body decompressed with the chunk codec; OPTIONAL
+* V1 data page: whole body decompressed with the chunk codec (Snappy or
+  Zstandard, the codecs of Section 2); OPTIONAL
   columns first carry a 4-byte LE length + RLE/bit-packed def levels (bit
   width 1); V2 data page: rep/def levels (lengths from the header) are never
   compressed, values are compressed when is_compressed (default true);
@@ -38,9 +39,10 @@ from . import hybrid as _hybrid
 from . import plain as _plain
 from . import snappy as _snappy
 from . import thrift as T
+from . import zstd as _zstd
 from .parquet_meta import (BYTE_STREAM_SPLIT, DATA_PAGE, DATA_PAGE_V2, DELTA_BINARY_PACKED,
                            DELTA_BYTE_ARRAY, DELTA_LENGTH_BYTE_ARRAY, DICTIONARY_PAGE, OPTIONAL, PLAIN,
-                           PLAIN_DICTIONARY, REPEATED, RLE_DICTIONARY, SNAPPY, TYPE_NAME, UNCOMPRESSED)
+                           PLAIN_DICTIONARY, REPEATED, RLE_DICTIONARY, SNAPPY, TYPE_NAME, UNCOMPRESSED, ZSTD)
 
 
 class ParquetError(ValueError):
@@ -191,6 +193,8 @@ def _decompress(codec, body, expect):
         out = bytes(body)
     elif codec == SNAPPY:
         out = _snappy.decompress(body)
+    elif codec == ZSTD:
+        out = _zstd.decompress(body)
     else:
         raise Unsupported(f"codec {codec}")
     if len(out) != expect:

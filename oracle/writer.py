@@ -52,8 +52,9 @@ from . import hybrid as _hybrid
 from . import plain as _plain
 from . import snappy as _snappy
 from . import thrift as T
+from . import zstd as _zstd
 from .parquet_meta import (CODEC_ID, DATA_PAGE, DATA_PAGE_V2, DICTIONARY_PAGE, ENCODING_ID,
-                           OPTIONAL, PLAIN, REQUIRED, RLE, SNAPPY, TYPE_ID, UNCOMPRESSED)
+                           OPTIONAL, PLAIN, REQUIRED, RLE, SNAPPY, TYPE_ID, UNCOMPRESSED, ZSTD)
 
 CREATED_BY = "pq-oracle"
 
@@ -182,7 +183,11 @@ def _page_header(ptype_page, uncompressed, compressed, sub_fid, sub_fields):
 
 
 def _compress(codec, data):
-    return _snappy.compress(data) if codec == SNAPPY else bytes(data)
+    if codec == SNAPPY:
+        return _snappy.compress(data)
+    if codec == ZSTD:
+        return _zstd.compress_stored(data)
+    return bytes(data)
 
 
 # Valid encodings per physical type, in the order a tie is broken (the

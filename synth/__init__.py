@@ -38,7 +38,7 @@ FIXED_WIDTH = {INT32: 4, INT64: 8, DOUBLE: 8}
 PLAIN, RLE_DICTIONARY, DELTA_BINARY_PACKED = "PLAIN", "RLE_DICTIONARY", "DELTA_BINARY_PACKED"
 DELTA_LENGTH_BYTE_ARRAY, DELTA_BYTE_ARRAY = "DELTA_LENGTH_BYTE_ARRAY", "DELTA_BYTE_ARRAY"
 BYTE_STREAM_SPLIT = "BYTE_STREAM_SPLIT"
-UNCOMPRESSED, SNAPPY = "UNCOMPRESSED", "SNAPPY"
+UNCOMPRESSED, SNAPPY, ZSTD = "UNCOMPRESSED", "SNAPPY", "ZSTD"
 
 KiB = 1 << 10
 MiB = 1 << 20
@@ -198,7 +198,7 @@ class ColumnSpec:
     # DELTA_LENGTH_BYTE_ARRAY | DELTA_BYTE_ARRAY | AUTO (per chunk, the
     # smallest valid encoding of the column's type)
     encoding: str = PLAIN
-    codec: str = UNCOMPRESSED        # UNCOMPRESSED | SNAPPY
+    codec: str = UNCOMPRESSED        # UNCOMPRESSED | SNAPPY | ZSTD (oracle writer: stored frames)
     page_version: int = 1            # 1 = DATA_PAGE, 2 = DATA_PAGE_V2
     # hybrid run policy for the writer: "default", "rle", "packed", "mixed"
     hybrid_policy: str = "default"

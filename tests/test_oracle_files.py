@@ -247,3 +247,51 @@ def test_oracle_reads_pyarrow_v2_encodings(page_version):
     assert [bytes(res[3].chars[res[3].offsets[j]:res[3].offsets[j + 1]]) for j in range(n)] == strs
     assert [bytes(res[4].chars[res[4].offsets[j]:res[4].offsets[j + 1]]) for j in range(n)] == \
         [x if v else b"" for x, v in zip(strs, valid)]
+
+
+# ------------------------------------------------------------- Zstandard (Section 2's codecs)
+
+@pytest.mark.parametrize("page_version", ["1.0", "2.0"])
+@pytest.mark.parametrize("level", [1, 9])
+def test_oracle_reads_pyarrow_zstd_files(page_version, level):
+    pa = pytest.importorskip("pyarrow")
+    pq = pytest.importorskip("pyarrow.parquet")
+    rng = np.random.default_rng(21)
+    n = 6000
+    i64 = np.cumsum(rng.integers(0, 5, size=n)).astype(np.int64)
+    f64 = rng.standard_normal(n)
+    valid = rng.random(n) > 0.1
+    strs = [b"s%d" % (x % 97) for x in rng.integers(0, 1000, size=n)]
+    t = pa.table({"a": pa.array(i64), "b": pa.array(f64), "c": pa.array(i64, mask=~valid),
+                  "d": pa.array(strs, pa.binary()), "e": pa.array(strs, pa.binary(), mask=~valid)})
+    buf = io.BytesIO()
+    pq.write_table(t, buf, compression="zstd", compression_level=level, data_page_size=4096, row_group_size=2500,
+                   data_page_version=page_version, use_dictionary=["d", "e"],
+                   column_encoding={"a": "DELTA_BINARY_PACKED", "b": "BYTE_STREAM_SPLIT"})
+    data = buf.getvalue()
+    assert {ch.codec for ch in R.parse_footer(data).chunks} == {6}
+    res = R.read_file(data)
+    assert np.array_equal(res[0].values, i64)
+    assert np.array_equal(res[1].values.view(np.int64), f64.view(np.int64))
+    assert np.array_equal(res[2].valid, valid) and np.array_equal(res[2].values[valid], i64[valid])
+    assert [bytes(res[3].chars[res[3].offsets[j]:res[3].offsets[j + 1]]) for j in range(n)] == strs
+    assert [bytes(res[4].chars[res[4].offsets[j]:res[4].offsets[j + 1]]) for j in range(n)] == \
+        [x if v else b"" for x, v in zip(strs, valid)]
+
+
+def test_oracle_zstd_files_round_trip_and_pyarrow_reads_them():
+    tab = synth.config2_table(4000, 1500, **SMALL)
+    for version in (1, 2):
+        spec = synth.config2_spec(1500, 2048, "ZSTD", version)
+        data = W.write_file(tab, spec)
+        assert {ch.codec for ch in R.parse_footer(data).chunks} == {6}
+        assert_rows_match(tab, R.read_file(data))
+    pq = pytest.importorskip("pyarrow.parquet")
+    t = pq.read_table(io.BytesIO(data))
+    for i, col in enumerate(tab.columns):
+        got = t.column(i).to_pylist()
+        if col.ptype == "BYTE_ARRAY":
+            assert got == string_rows(col)
+        else:
+            v = np.asarray(col.values).tolist()
+            assert got == (v if col.valid is None else [x if m else None for x, m in zip(v, col.valid)])

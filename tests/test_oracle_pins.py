@@ -8,7 +8,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle import byte_stream_split, delta, delta_strings, hybrid, snappy, thrift
+from oracle import byte_stream_split, delta, delta_strings, hybrid, snappy, thrift, zstd
 from oracle import reader as R
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_vectors.json")))
@@ -324,3 +324,92 @@ def test_delta_strings_errors():
     short = delta_strings.encode_length_byte_array([b"abc", b"defg"])
     with pytest.raises(delta_strings.DeltaStringError):     # bytes past the end
         delta_strings.decode_length_byte_array(short, 0, len(short) - 1, 2)
+
+
+# ------------------------------------------------------------------ zstandard
+
+def test_zstd_hand_vectors():
+    for key in ("zstd_raw_block", "zstd_rle_literals_no_sequences", "zstd_one_sequence_rle_tables"):
+        g = GOLD[key]
+        assert zstd.decompress(hx(g["hex"])) == g["text"].encode(), key
+    g = GOLD["zstd_rle_block"]
+    ch, n = g["text_repeat"]
+    assert zstd.decompress(hx(g["hex"])) == ch.encode() * n
+
+
+def _zstd_inputs(rng):
+    """Byte strings of many shapes: random, small alphabets, word soup,
+    long runs, integer columns, skewed bytes in blocks of 128 KB (Huffman
+    literal sections with 18-bit sizes), several blocks per frame."""
+    out = [b"", b"a", bytes(range(256)) * 40]
+    for trial in range(120):
+        kind = trial % 6
+        n = int(rng.integers(0, 300_000 if trial % 13 == 0 else 5000))
+        if kind == 0:
+            x = rng.integers(0, 256, n, dtype=np.uint8).tobytes()
+        elif kind == 1:
+            x = rng.integers(0, int(rng.integers(1, 6)), n, dtype=np.uint8).tobytes()
+        elif kind == 2:
+            words = [rng.integers(97, 123, int(rng.integers(1, 12)), dtype=np.uint8).tobytes()
+                     for _ in range(int(rng.integers(1, 50)))]
+            x = b"".join(words[int(i)] for i in rng.integers(0, len(words), max(1, n // 6)))
+        elif kind == 3:
+            x = np.repeat(rng.integers(0, 256, max(1, n // 50), dtype=np.uint8), 50).tobytes()
+        elif kind == 4:
+            x = np.cumsum(rng.integers(-3, 4, max(1, n // 4))).astype(np.int32).tobytes()
+        else:
+            x = np.minimum(rng.geometric(0.08, 200_000), 255).astype(np.uint8).tobytes()
+        out.append(x)
+    return out
+
+
+def test_zstd_against_libzstd():
+    """Frames written by libzstd (through pyarrow) at levels -5 .. 22 decode
+    to their input: every literal and sequence coding mode of the format
+    occurs among them (raw, RLE, Huffman 1 and 4 streams, new and repeated
+    tables; predefined, RLE, transmitted and repeated FSE tables; all three
+    repeat offsets)."""
+    pa = pytest.importorskip("pyarrow")
+    rng = np.random.default_rng(1)
+    levels = [-5, -1, 1, 2, 3, 5, 9, 15, 19, 22]
+    for i, x in enumerate(_zstd_inputs(rng)):
+        lvl = levels[i % len(levels)]
+        comp = pa.Codec("zstd", compression_level=lvl).compress(x, asbytes=True)
+        assert zstd.decompress(comp) == x, (i, lvl, len(x))
+
+
+def test_zstd_stored_frames_round_trip_and_libzstd_reads_them():
+    rng = np.random.default_rng(2)
+    cases = [b"", b"z", b"q" * 300_000, rng.integers(0, 256, 300_000, dtype=np.uint8).tobytes()]
+    cases += [bytes(t) for n in range(0, 4) for t in itertools.product(b"ab", repeat=n)]
+    for x in cases:
+        enc = zstd.compress_stored(x)
+        assert zstd.decompress(enc) == x
+    pa = pytest.importorskip("pyarrow")
+    for x in cases[:4]:
+        enc = zstd.compress_stored(x)
+        assert pa.Codec("zstd").decompress(enc, decompressed_size=len(x), asbytes=True) == x
+
+
+def test_zstd_frames_concatenate_and_skip():
+    a, b = zstd.compress_stored(b"first"), zstd.compress_stored(b"second")
+    skip = (0x184D2A53).to_bytes(4, "little") + (3).to_bytes(4, "little") + b"xyz"
+    assert zstd.decompress(a + skip + b) == b"firstsecond"
+
+
+def test_zstd_errors():
+    # good: magic | 20 | 0C | 55 00 00 | 18 'abc' | 01 54 03 02 06 | 06
+    good = hx(GOLD["zstd_one_sequence_rle_tables"]["hex"])
+    bad = [
+        b"\x00" + good[1:],                                   # not the magic number
+        good[:4] + bytes([good[4] | 8]) + good[5:],           # reserved descriptor bit
+        good[:-1],                                            # block runs past the input
+        good[:5] + bytes([13]) + good[6:],                    # content size 13, 12 bytes decoded
+        good[:6] + bytes([good[6] | 6]) + good[7:],           # reserved block type 3
+        good[:18] + b"\x0e",                                  # 3 data bits, 2 read: not consumed exactly
+        good[:16] + hx("03 06 08"),                           # offset code 3 + 0: offset 5 > 3 bytes out
+        hx("28 B5 2F FD 21 01 03 19 00 00 61 62 63"),         # dictionary id 1
+    ]
+    for b in bad:
+        with pytest.raises(zstd.ZstdError):
+            zstd.decompress(b)
