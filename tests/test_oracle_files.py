@@ -295,3 +295,21 @@ def test_oracle_zstd_files_round_trip_and_pyarrow_reads_them():
         else:
             v = np.asarray(col.values).tolist()
             assert got == (v if col.valid is None else [x if m else None for x, m in zip(v, col.valid)])
+
+
+@pytest.mark.parametrize("name", ["zstd_eight_column_v1.parquet", "zstd_eight_column_v2.parquet"])
+def test_zstd_fixtures_decode_to_their_table(name):
+    """The committed Zstandard fixtures (libzstd pages, written by
+    tests/golden/make_zstd_fixtures.py) decode, with the oracle, to the
+    seeded table they were made from."""
+    import importlib.util
+    import os
+    golden = os.path.join(os.path.dirname(__file__), "golden")
+    spec = importlib.util.spec_from_file_location("make_zstd_fixtures", os.path.join(golden, "make_zstd_fixtures.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    rows, rg, _, _, _ = mod.FIXTURES[name]
+    data = open(os.path.join(golden, name), "rb").read()
+    assert {ch.codec for ch in R.parse_footer(data).chunks} == {6}
+    tab = synth.config2_table(rows, rg, string_pool_size=700, zipf_k=2000)
+    assert_rows_match(tab, R.read_file(data))
