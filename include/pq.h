@@ -219,7 +219,9 @@ void pq_free_plan(pq_plan* plan);
 
 /* Stages of a scan, in order, for pq_plan_stage_ms. */
 #define PQ_STAGE_PREPARE 0     /* reset of bitmaps, counters, error word */
-#define PQ_STAGE_SNAPPY 1      /* page decompression (K1) */
+#define PQ_STAGE_SNAPPY 1      /* page decompression (K1), then the rewrite of
+                                  BYTE_STREAM_SPLIT / DELTA_(LENGTH_)BYTE_ARRAY
+                                  pages into PLAIN bodies */
 #define PQ_STAGE_DICT 2        /* dictionary decode (K6) */
 #define PQ_STAGE_WALK 3        /* page walk: levels, stream checkpoints */
 #define PQ_STAGE_EXPAND 4      /* value expansion of the work items */
