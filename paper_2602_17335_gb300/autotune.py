@@ -11,9 +11,10 @@ page count. Here parallelism comes from work items, so the best item size
 depends on the mix of pages, encodings and sizes. It is found by timing.
 
 The tuner does coordinate descent: each knob in turn over its candidate
-values, keeping the fastest setting. It times with a caller-supplied function
-that rebuilds the plans under the tuning it is given and returns milliseconds
-per run. The chosen tuning is left set on the context.
+values, keeping the fastest setting; a setting is timed once. It times with
+a caller-supplied function that rebuilds the plans under the tuning it is
+given and returns milliseconds per run. The chosen tuning is left set on the
+context.
 """
 from __future__ import annotations
 
@@ -37,11 +38,16 @@ def autotune(ctx, time_ms: Callable[[Dict[str, int]], float], rounds: int = 1,
     apply nothing itself: the tuner sets the tuning on `ctx` before each call."""
     cands = candidates or CANDIDATES
     trials: List[Tuple[Dict[str, int], float]] = []
+    timed: Dict[Tuple, float] = {}
 
     def run(t: Dict[str, int]) -> float:
+        key = tuple(sorted(t.items()))
+        if key in timed:  # a setting is timed once, even when the descent comes back to it
+            return timed[key]
         N.pq_ctx_set_tuning(ctx, **t)
         ms = time_ms(t)
         trials.append((dict(t), ms))
+        timed[key] = ms
         return ms
 
     best = dict(DEFAULT)
