@@ -2,9 +2,9 @@
 // a flat table is written with a chosen row-group size, page size,
 // encoding per column chunk (V1 PLAIN / dictionary, the V2 set
 // DELTA_BINARY_PACKED, DELTA_LENGTH_BYTE_ARRAY, DELTA_BYTE_ARRAY and
-// BYTE_STREAM_SPLIT), page version, and per-chunk compression kept only when
-// it shrinks the chunk by more than a threshold (Section 3, "No Unnecessary
-// Compression").  With encoding -1 every chunk tries each valid encoding of
+// BYTE_STREAM_SPLIT), page version, and per-chunk compression (Snappy or
+// Zstandard) kept only when it shrinks the chunk by more than a threshold
+// (Section 3, "No Unnecessary Compression").  With encoding -1 every chunk tries each valid encoding of
 // its type and keeps the one with the smallest encoded (uncompressed) chunk
 // (Section 3, "Encoding Flexibility").
 //
@@ -303,6 +303,276 @@ void snappy_compress(const uint8_t* in, size_t n, Bytes& o) {
   literal(lit, n);
 }
 
+// ------------------------------------------------------------------ Zstandard compressor
+
+// One Zstandard frame per page (single segment, content size in the
+// header, no checksum).  Each block of up to 128 KB of input is coded with
+// greedy LZ77 matches (4-byte hash over the whole frame so far) as
+// sequences whose codes use the format's predefined FSE tables, and its
+// literals stored raw; a block without matches, or one that would not
+// shrink, is stored as a raw (or RLE) block.  Every Zstandard decoder reads
+// the result.
+
+struct ZBitW {  // little-endian bit writer
+  Bytes& o;
+  uint64_t acc = 0;
+  int n = 0;
+  explicit ZBitW(Bytes& out) : o(out) {}
+  void put(uint64_t v, int nb) {  // nb <= 32
+    if (nb == 0) return;
+    acc |= (v & ((1ull << nb) - 1)) << n;
+    n += nb;
+    while (n >= 8) {
+      o.push_back(static_cast<uint8_t>(acc));
+      acc >>= 8;
+      n -= 8;
+    }
+  }
+  void finish() {  // end marker, then the last partial byte
+    put(1, 1);
+    if (n) o.push_back(static_cast<uint8_t>(acc));
+    acc = 0;
+    n = 0;
+  }
+};
+
+// FSE encoding of one predefined distribution: the decoder's table (symbols
+// spread over the states, each state's bit count and next-state base), and
+// for every symbol and every next state the state that leads there.
+struct ZFseEnc {
+  int al = 0, size = 0;
+  std::vector<uint8_t> sym, nb;
+  std::vector<uint16_t> base;
+  std::vector<std::vector<uint16_t>> from;  // [symbol][next state] -> state
+  ZFseEnc(const int8_t* norm, int nsym, int a) : al(a), size(1 << a), sym(size), nb(size), base(size), from(nsym) {
+    int high = size - 1;
+    std::vector<uint32_t> next(nsym);
+    for (int s = 0; s < nsym; ++s) {
+      if (norm[s] == -1) {
+        sym[high--] = static_cast<uint8_t>(s);
+        next[s] = 1;
+      } else {
+        next[s] = static_cast<uint32_t>(norm[s]);
+      }
+    }
+    const int step = (size >> 1) + (size >> 3) + 3, mask = size - 1;
+    int pos = 0;
+    for (int s = 0; s < nsym; ++s)
+      for (int i = 0; i < norm[s]; ++i) {
+        sym[pos] = static_cast<uint8_t>(s);
+        do pos = (pos + step) & mask; while (pos > high);
+      }
+    for (int s = 0; s < nsym; ++s) from[s].assign(size, 0);
+    for (int st = 0; st < size; ++st) {
+      const uint32_t x = next[sym[st]]++;
+      nb[st] = static_cast<uint8_t>(al - (bit_length(x) - 1));
+      base[st] = static_cast<uint16_t>((x << nb[st]) - size);
+      for (int y = base[st]; y < base[st] + (1 << nb[st]); ++y) from[sym[st]][y] = static_cast<uint16_t>(st);
+    }
+  }
+  int any_state(int s) const {
+    for (int st = 0; st < size; ++st)
+      if (sym[st] == s) return st;
+    return 0;
+  }
+};
+
+const ZFseEnc& zenc_table(int which) {  // 0 literal lengths, 1 offsets, 2 match lengths
+  static const int8_t LL[36] = {4, 3, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 1, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 2, 3, 2, 1,
+                                1, 1, 1, 1, -1, -1, -1, -1};
+  static const int8_t OF[29] = {1, 1, 1, 1, 1, 1, 2, 2, 2, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, -1, -1, -1,
+                                -1, -1};
+  static const int8_t ML[53] = {1, 4, 3, 2, 2, 2, 2, 2, 2, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1,
+                                1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, -1, -1, -1, -1, -1, -1, -1};
+  static const ZFseEnc t_ll(LL, 36, 6), t_of(OF, 29, 5), t_ml(ML, 53, 6);
+  return which == 0 ? t_ll : which == 1 ? t_of : t_ml;
+}
+
+// (code, extra-bit count, extra bits) of a literal length / match length
+void zll_code(uint32_t ll, int* code, int* nb, uint32_t* extra) {
+  static const uint32_t B[20] = {16, 18, 20, 22, 24, 28, 32, 40, 48, 64, 128, 256, 512, 1024, 2048, 4096, 8192,
+                                 16384, 32768, 65536};
+  static const int N[20] = {1, 1, 1, 1, 2, 2, 3, 3, 4, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16};
+  if (ll < 16) {
+    *code = static_cast<int>(ll);
+    *nb = 0;
+    *extra = 0;
+    return;
+  }
+  int k = 19;
+  while (ll < B[k]) --k;
+  *code = 16 + k;
+  *nb = N[k];
+  *extra = ll - B[k];
+}
+
+void zml_code(uint32_t ml, int* code, int* nb, uint32_t* extra) {
+  static const uint32_t B[21] = {35, 37, 39, 41, 43, 47, 51, 59, 67, 83, 99, 131, 259, 515, 1027, 2051, 4099, 8195,
+                                 16387, 32771, 65539};
+  static const int N[21] = {1, 1, 1, 1, 2, 2, 3, 3, 4, 4, 5, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16};
+  if (ml - 3 < 32) {
+    *code = static_cast<int>(ml - 3);
+    *nb = 0;
+    *extra = 0;
+    return;
+  }
+  int k = 20;
+  while (ml < B[k]) --k;
+  *code = 32 + k;
+  *nb = N[k];
+  *extra = ml - B[k];
+}
+
+struct ZSeq {
+  uint32_t ll, off, ml;
+};
+
+// Compressed-block body for `seqs` and `lits`; false when it would not be
+// smaller than `raw` bytes.
+bool zstd_block_body(const std::vector<ZSeq>& seqs, const Bytes& lits, size_t raw, Bytes& body) {
+  body.clear();
+  const size_t n = lits.size();
+  if (n <= 31) {
+    body.push_back(static_cast<uint8_t>(n << 3));
+  } else if (n <= 4095) {
+    body.push_back(static_cast<uint8_t>(((n & 15) << 4) | (1 << 2)));
+    body.push_back(static_cast<uint8_t>(n >> 4));
+  } else {
+    body.push_back(static_cast<uint8_t>(((n & 15) << 4) | (3 << 2)));
+    body.push_back(static_cast<uint8_t>(n >> 4));
+    body.push_back(static_cast<uint8_t>(n >> 12));
+  }
+  body.insert(body.end(), lits.begin(), lits.end());
+  const size_t ns = seqs.size();
+  if (ns < 128) {
+    body.push_back(static_cast<uint8_t>(ns));
+  } else if (ns < 0x7F00) {
+    body.push_back(static_cast<uint8_t>((ns >> 8) + 128));
+    body.push_back(static_cast<uint8_t>(ns));
+  } else {
+    body.push_back(255);
+    body.push_back(static_cast<uint8_t>(ns - 0x7F00));
+    body.push_back(static_cast<uint8_t>((ns - 0x7F00) >> 8));
+  }
+  body.push_back(0);  // all three codes use the predefined tables
+  const ZFseEnc& tl = zenc_table(0);
+  const ZFseEnc& to = zenc_table(1);
+  const ZFseEnc& tm = zenc_table(2);
+  // the decoder reads, per sequence: offset, match-length and literal-length
+  // extra bits, then (but after the last) the literal-length, match-length
+  // and offset state bits; and first of all the three initial states.  The
+  // stream is read from its end, so it is written in exactly the reverse
+  // order, last sequence first.
+  ZBitW w(body);
+  int sl = 0, so = 0, sm = 0;
+  for (size_t k = ns; k-- > 0;) {
+    const ZSeq& q = seqs[k];
+    int lc, lnb, mc, mnb;
+    uint32_t lx, mx;
+    zll_code(q.ll, &lc, &lnb, &lx);
+    zml_code(q.ml, &mc, &mnb, &mx);
+    const uint32_t ov = q.off + 3;
+    const int oc = bit_length(ov) - 1;
+    if (oc > 28) return false;  // beyond the predefined offset codes
+    const uint32_t ox = ov - (1u << oc);
+    if (k + 1 == ns) {
+      sl = tl.any_state(lc);
+      sm = tm.any_state(mc);
+      so = to.any_state(oc);
+    } else {
+      const int pl = tl.from[lc][sl], pm = tm.from[mc][sm], po = to.from[oc][so];
+      w.put(so - to.base[po], to.nb[po]);
+      w.put(sm - tm.base[pm], tm.nb[pm]);
+      w.put(sl - tl.base[pl], tl.nb[pl]);
+      sl = pl;
+      sm = pm;
+      so = po;
+    }
+    w.put(lx, lnb);
+    w.put(mx, mnb);
+    w.put(ox, oc);
+  }
+  w.put(sm, tm.al);
+  w.put(so, to.al);
+  w.put(sl, tl.al);
+  w.finish();
+  return body.size() < raw;
+}
+
+void zstd_compress(const uint8_t* in, size_t n, Bytes& o) {
+  o.clear();
+  const uint32_t magic = 0xFD2FB528u;
+  o.insert(o.end(), reinterpret_cast<const uint8_t*>(&magic), reinterpret_cast<const uint8_t*>(&magic) + 4);
+  if (n < 256) {
+    o.push_back(0x20);
+    o.push_back(static_cast<uint8_t>(n));
+  } else if (n < 65536 + 256) {
+    o.push_back(0x60);
+    o.push_back(static_cast<uint8_t>(n - 256));
+    o.push_back(static_cast<uint8_t>((n - 256) >> 8));
+  } else {
+    o.push_back(0xA0);
+    for (int k = 0; k < 4; ++k) o.push_back(static_cast<uint8_t>(n >> (8 * k)));
+  }
+  auto block_header = [&](size_t size, int type, bool last) {
+    const uint32_t h = static_cast<uint32_t>((size << 3) | (type << 1) | (last ? 1 : 0));
+    o.push_back(static_cast<uint8_t>(h));
+    o.push_back(static_cast<uint8_t>(h >> 8));
+    o.push_back(static_cast<uint8_t>(h >> 16));
+  };
+  if (n == 0) {
+    block_header(0, 0, true);
+    return;
+  }
+  const int kBits = 16;
+  std::vector<int64_t> table(size_t(1) << kBits, -1);
+  auto h4 = [&](size_t i) {
+    uint32_t x;
+    memcpy(&x, in + i, 4);
+    return (x * 0x9E3779B1u) >> (32 - kBits);
+  };
+  std::vector<ZSeq> seqs;
+  Bytes lits, body;
+  const size_t kBlock = 128 * 1024;
+  for (size_t b0 = 0; b0 < n; b0 += kBlock) {
+    const size_t b1 = std::min(n, b0 + kBlock);
+    const bool last = b1 == n;
+    seqs.clear();
+    lits.clear();
+    size_t i = b0, lit = b0;
+    while (i + 4 <= b1) {
+      const uint32_t h = h4(i);
+      const int64_t cand = table[h];
+      table[h] = static_cast<int64_t>(i);
+      if (cand >= 0 && memcmp(in + cand, in + i, 4) == 0) {
+        size_t len = 4;
+        while (i + len < b1 && in[cand + len] == in[i + len]) ++len;
+        seqs.push_back({static_cast<uint32_t>(i - lit), static_cast<uint32_t>(i - cand), static_cast<uint32_t>(len)});
+        lits.insert(lits.end(), in + lit, in + i);
+        for (size_t k = i + 1; k < i + len && k + 4 <= b1; k += 3) table[h4(k)] = static_cast<int64_t>(k);
+        i += len;
+        lit = i;
+      } else {
+        ++i;
+      }
+    }
+    lits.insert(lits.end(), in + lit, in + b1);
+    const size_t raw = b1 - b0;
+    bool same = true;
+    for (size_t k = b0 + 1; k < b1 && same; ++k) same = in[k] == in[b0];
+    if (same && raw > 1) {
+      block_header(raw, 1, last);
+      o.push_back(in[b0]);
+    } else if (!seqs.empty() && zstd_block_body(seqs, lits, raw, body)) {
+      block_header(body.size(), 2, last);
+      o.insert(o.end(), body.begin(), body.end());
+    } else {
+      block_header(raw, 0, last);
+      o.insert(o.end(), in + b0, in + b1);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ chunk encoder
 
 struct ChunkOut {
@@ -500,6 +770,8 @@ void encode_chunk(const ColIn& in, int64_t page_bytes, int codec, ChunkOut* out)
     auto compress = [&](const Bytes& src, Bytes& dst) {
       if (use_codec == 1)
         snappy_compress(src.data(), src.size(), dst);
+      else if (use_codec == 6)
+        zstd_compress(src.data(), src.size(), dst);
       else
         dst = src;
     };
@@ -670,7 +942,7 @@ pq_status pq_write_table(const pq_write_column* cols, int n_cols, int64_t n_rows
     if (e == 5 && col.type != PQ_TYPE_INT32 && col.type != PQ_TYPE_INT64) return PQ_ERR_INVALID_ARG;
     if ((e == 6 || e == 7) && col.type != PQ_TYPE_BYTE_ARRAY) return PQ_ERR_INVALID_ARG;
     if (e == 9 && !fixed) return PQ_ERR_INVALID_ARG;
-    if (col.codec != 0 && col.codec != 1) return PQ_ERR_UNSUPPORTED;
+    if (col.codec != 0 && col.codec != 1 && col.codec != 6) return PQ_ERR_UNSUPPORTED;
     if (col.page_version != 1 && col.page_version != 2) return PQ_ERR_INVALID_ARG;
     if (!col.values && n_rows > 0) return PQ_ERR_INVALID_ARG;
     if (col.type == PQ_TYPE_BYTE_ARRAY && !col.chars && n_rows > 0) return PQ_ERR_INVALID_ARG;

@@ -14,7 +14,7 @@ _TYPE = {"INT32": N.PQ_TYPE_INT32, "INT64": N.PQ_TYPE_INT64, "DOUBLE": N.PQ_TYPE
          "BYTE_ARRAY": N.PQ_TYPE_BYTE_ARRAY}
 _ENC = {"PLAIN": 0, "RLE_DICTIONARY": 8, "DELTA_BINARY_PACKED": 5, "DELTA_LENGTH_BYTE_ARRAY": 6,
         "DELTA_BYTE_ARRAY": 7, "BYTE_STREAM_SPLIT": 9, "AUTO": -1}
-_CODEC = {"UNCOMPRESSED": 0, "SNAPPY": 1}
+_CODEC = {"UNCOMPRESSED": 0, "SNAPPY": 1, "ZSTD": 6}
 
 
 def write_table(table: synth.Table, spec: synth.TableSpec, n_threads: int = 0) -> np.ndarray:

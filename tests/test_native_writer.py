@@ -4,9 +4,13 @@ Sections 3 and 5) against the oracle writer, on the CPU (no GPU needed).
 Both follow the same deterministic layout rules, so on uncompressed data
 they must write the same bytes (only the footer's created_by differs);
 with Snappy the compressors differ, so the file must read back to the table
-and keep the same page structure.  The per-chunk encoding choice ("AUTO",
-Section 3's "Encoding Flexibility") is pinned to the smallest explicit
-encoding of each chunk and to the obvious winners of shaped data."""
+and keep the same page structure; its Zstandard pages (LZ77 sequences under
+the predefined FSE tables) read back through the oracle and libzstd.  The
+per-chunk encoding choice ("AUTO", Section 3's "Encoding Flexibility") is
+pinned to the smallest explicit encoding of each chunk and to the obvious
+winners of shaped data."""
+import io
+
 import numpy as np
 import pytest
 
@@ -14,6 +18,7 @@ import synth
 from oracle import reader as R
 from oracle import thrift as T
 from oracle import writer as W
+from oracle import zstd as Z
 
 
 def _native():
@@ -163,3 +168,87 @@ def test_native_writer_rejects_invalid_encodings():
     with pytest.raises(N.PqError) as ei:
         N.pq_write_table([w], 2, 2, 1024)
     assert ei.value.status == N.PQ_ERR_INVALID_ARG
+
+
+def _frame_block_types(frame):
+    """Block types of one Zstandard frame (0 raw, 1 RLE, 2 compressed)."""
+    pos = 4
+    fhd = frame[pos]
+    pos += 1
+    single, fcs = (fhd >> 5) & 1, fhd >> 6
+    pos += 0 if single else 1
+    pos += single if fcs == 0 else {1: 2, 2: 4, 3: 8}[fcs]
+    out = []
+    while True:
+        h = int.from_bytes(frame[pos:pos + 3], "little")
+        pos += 3
+        t = (h >> 1) & 3
+        out.append(t)
+        pos += 1 if t == 1 else h >> 3
+        if h & 1:
+            return out
+
+
+def zstd_pages(data):
+    """(column, frame, uncompressed bytes) of every compressed page."""
+    for ch in R.parse_footer(data).chunks:
+        for p in R.chunk_pages(data, ch):
+            body = data[p.offset + p.header_len:p.offset + p.header_len + p.compressed]
+            if p.page_type == 3:
+                if not p.is_compressed:
+                    continue
+                yield ch.column, body[p.def_len + p.rep_len:], p.uncompressed - p.def_len - p.rep_len
+            else:
+                yield ch.column, body, p.uncompressed
+
+
+@pytest.mark.parametrize("version", [1, 2])
+def test_native_writer_zstd_pages(version):
+    """Zstandard pages of the native writer: the oracle reads them back to
+    the table, compressible columns get compressed blocks (LZ77 sequences
+    under the predefined FSE tables), incompressible ones raw blocks, and
+    libzstd (through pyarrow) reads the same file."""
+    _, write_table = _native()
+    rng = np.random.default_rng(3)
+    n = 30_000
+    cols = [synth.ColumnData("sorted", "INT64", np.cumsum(rng.integers(0, 3, n)).astype(np.int64)),
+            synth.ColumnData("strs", "BYTE_ARRAY", synth.strings_uniform(rng, n, k=200)),
+            synth.ColumnData("lowcard", "INT32", rng.integers(0, 5, n).astype(np.int32), rng.random(n) > 0.2),
+            synth.ColumnData("noise", "DOUBLE", rng.standard_normal(n))]
+    cols[2].values[~cols[2].valid] = 0
+    tab = synth.Table(cols)
+    spec = synth.TableSpec(12_000, 1 << 16, [synth.ColumnSpec("PLAIN", "ZSTD", version) for _ in cols])
+    data = bytes(write_table(tab, spec))
+    res = R.read_file(data)
+    for col, r in zip(tab.columns, res):
+        if col.ptype == "BYTE_ARRAY":
+            off, ch = col.values.materialize()
+            assert np.array_equal(off, r.offsets) and np.array_equal(ch, r.chars)
+        else:
+            assert np.array_equal(np.asarray(col.values).view(np.uint8), r.values.view(np.uint8))
+    kinds = {}
+    for c, frame, _ in zstd_pages(data):
+        kinds.setdefault(c, set()).update(_frame_block_types(frame))
+    assert 2 in kinds[0] and 2 in kinds[1] and 2 in kinds[2]
+    assert kinds[3] == {0}
+    pq = pytest.importorskip("pyarrow.parquet")
+    t = pq.read_table(io.BytesIO(data))
+    assert t.column(0).to_pylist() == cols[0].values.tolist()
+    assert t.column(3).to_pylist() == cols[3].values.tolist()
+    assert t.column(2).to_pylist() == [int(v) if m else None for v, m in zip(cols[2].values, cols[2].valid)]
+
+
+def test_native_zstd_frames_decode_with_libzstd():
+    """Every page frame the native writer makes decodes with libzstd to the
+    oracle's bytes (frames with up to several 128 KB blocks)."""
+    pa = pytest.importorskip("pyarrow")
+    _, write_table = _native()
+    tab = synth.config2_table(200_000, 200_000, string_pool_size=300, zipf_k=500)
+    data = bytes(write_table(tab, synth.config2_spec(200_000, 1 << 20, "ZSTD", 1)))
+    n = 0
+    for _, frame, size in zstd_pages(data):
+        want = Z.decompress(frame)
+        assert len(want) == size
+        assert pa.Codec("zstd").decompress(frame, decompressed_size=size, asbytes=True) == want
+        n += 1
+    assert n > 10

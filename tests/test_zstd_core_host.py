@@ -75,6 +75,23 @@ def test_fixture_pages(core, name):
     assert n > 20
 
 
+def test_native_writer_frames(core):
+    """Frames of the engine's own writer (sequences under the predefined
+    tables, raw and RLE blocks, several blocks per page)."""
+    import synth
+    from paper_2602_17335_gb300.tables import write_table
+    from test_native_writer import _native, zstd_pages
+    _native()
+    tab = synth.config2_table(200_000, 200_000, string_pool_size=300, zipf_k=500)
+    data = bytes(write_table(tab, synth.config2_spec(200_000, 1 << 20, "ZSTD", 2)))
+    n = 0
+    for _, frame, size in zstd_pages(data):
+        want = Z.decompress(frame)
+        assert len(want) == size and core(frame, size) == (0, want)
+        n += 1
+    assert n > 10
+
+
 def test_malformed_frames_return_errors(core):
     import json
     gold = json.load(open(os.path.join(HERE, "golden", "hand_vectors.json")))
