@@ -308,10 +308,11 @@ void snappy_compress(const uint8_t* in, size_t n, Bytes& o) {
 // One Zstandard frame per page (single segment, content size in the
 // header, no checksum).  Each block of up to 128 KB of input is coded with
 // greedy LZ77 matches (4-byte hash over the whole frame so far) as
-// sequences whose codes use the format's predefined FSE tables, and its
-// literals stored raw; a block without matches, or one that would not
-// shrink, is stored as a raw (or RLE) block.  Every Zstandard decoder reads
-// the result.
+// sequences whose codes use the format's predefined FSE tables; its
+// literals are Huffman-coded (1 or 4 streams) when they are all below 128
+// and that pays, else stored raw; a block without matches, or one that
+// would not shrink, is stored as a raw (or RLE) block.  Every Zstandard
+// decoder reads the result.
 
 struct ZBitW {  // little-endian bit writer
   Bytes& o;
@@ -427,12 +428,169 @@ struct ZSeq {
   uint32_t ll, off, ml;
 };
 
+// Huffman code lengths for byte counts, limited to kHufMaxBits: plain
+// Huffman merging, then, if the longest code is too long, lengths above the
+// limit are cut to it and the Kraft sum is repaid by lengthening the longest
+// codes still below the limit (least frequent first).
+constexpr int kHufMaxBits = 11;
+
+bool huf_lengths(const uint32_t* cnt, int nsym, int* len) {
+  struct Node {
+    uint64_t w;
+    int l, r;
+  };
+  std::vector<Node> nodes;
+  std::vector<std::pair<uint64_t, int>> heap;  // (weight, node) min-heap
+  for (int s = 0; s < nsym; ++s) {
+    len[s] = 0;
+    if (cnt[s]) {
+      nodes.push_back({cnt[s], -1 - s, -1});
+      heap.push_back({cnt[s], static_cast<int>(nodes.size()) - 1});
+    }
+  }
+  if (heap.size() < 2) return false;  // one symbol: RLE literals instead
+  auto cmp = [](const std::pair<uint64_t, int>& a, const std::pair<uint64_t, int>& b) { return a > b; };
+  std::make_heap(heap.begin(), heap.end(), cmp);
+  while (heap.size() > 1) {
+    std::pop_heap(heap.begin(), heap.end(), cmp);
+    const auto a = heap.back();
+    heap.pop_back();
+    std::pop_heap(heap.begin(), heap.end(), cmp);
+    const auto b = heap.back();
+    heap.pop_back();
+    nodes.push_back({a.first + b.first, a.second, b.second});
+    heap.push_back({a.first + b.first, static_cast<int>(nodes.size()) - 1});
+    std::push_heap(heap.begin(), heap.end(), cmp);
+  }
+  // depths by an explicit stack walk from the root
+  std::vector<std::pair<int, int>> st = {{heap[0].second, 0}};
+  while (!st.empty()) {
+    const auto [n, d] = st.back();
+    st.pop_back();
+    if (nodes[n].l < 0) {
+      len[-1 - nodes[n].l] = std::max(d, 1);
+    } else {
+      st.push_back({nodes[n].l, d + 1});
+      st.push_back({nodes[n].r, d + 1});
+    }
+  }
+  // limit: Kraft sum in units of 2^-kHufMaxBits must stay <= 2^kHufMaxBits
+  int64_t kraft = 0;
+  for (int s = 0; s < nsym; ++s)
+    if (len[s]) {
+      if (len[s] > kHufMaxBits) len[s] = kHufMaxBits;
+      kraft += int64_t(1) << (kHufMaxBits - len[s]);
+    }
+  const int64_t cap = int64_t(1) << kHufMaxBits;
+  if (kraft > cap) {
+    std::vector<int> order;
+    for (int s = 0; s < nsym; ++s)
+      if (len[s]) order.push_back(s);
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return cnt[a] < cnt[b] || (cnt[a] == cnt[b] && a < b); });
+    while (kraft > cap) {
+      bool moved = false;
+      for (int s : order)
+        if (len[s] < kHufMaxBits) {
+          kraft -= int64_t(1) << (kHufMaxBits - len[s] - 1);
+          ++len[s];
+          moved = true;
+          if (kraft <= cap) break;
+        }
+      if (!moved) return false;
+    }
+    // then spend what is left of the Kraft sum on the most frequent codes,
+    // so that the code stays complete
+    for (auto it = order.rbegin(); it != order.rend(); ++it)
+      while (len[*it] > 1 && kraft + (int64_t(1) << (kHufMaxBits - len[*it])) <= cap) {
+        kraft += int64_t(1) << (kHufMaxBits - len[*it]);
+        --len[*it];
+      }
+  }
+  return true;
+}
+
+// Huffman-coded literals section (tree description with direct 4-bit
+// weights, so literal bytes below 128 only; 1 stream up to 1023 literals,
+// else 4 streams).  False when it does not apply or would not shrink.
+bool huf_literals(const Bytes& lits, Bytes& out) {
+  const size_t n = lits.size();
+  if (n < 64 || n > 262143) return false;
+  uint32_t cnt[256] = {0};
+  for (uint8_t c : lits) ++cnt[c];
+  int top = 255;
+  while (top > 0 && cnt[top] == 0) --top;
+  if (top >= 128) return false;  // direct weights describe symbols 0..128 at most
+  int len[256];
+  if (!huf_lengths(cnt, top + 1, len)) return false;
+  int mb = 0;
+  for (int s = 0; s <= top; ++s) mb = std::max(mb, len[s]);
+  // weights: nbits = mb + 1 - weight; the Kraft sum must be exactly full
+  int64_t kraft = 0;
+  for (int s = 0; s <= top; ++s)
+    if (len[s]) kraft += int64_t(1) << (mb - len[s]);
+  if (kraft != (int64_t(1) << mb)) return false;
+  int w[256];
+  for (int s = 0; s <= top; ++s) w[s] = len[s] ? mb + 1 - len[s] : 0;
+  // canonical codes in the format's order: weight 1 first, symbols ascending
+  uint32_t code[256] = {0};
+  uint32_t start = 0;
+  for (int wt = 1; wt <= mb; ++wt)
+    for (int s = 0; s <= top; ++s)
+      if (w[s] == wt) {
+        code[s] = start >> (wt - 1);
+        start += 1u << (wt - 1);
+      }
+  // tree description: the last symbol's weight is implied
+  Bytes tree;
+  const int nw = top;  // weights of symbols 0 .. top-1 are written
+  tree.push_back(static_cast<uint8_t>(127 + nw));
+  for (int i = 0; i < nw; i += 2)
+    tree.push_back(static_cast<uint8_t>((w[i] << 4) | (i + 1 < nw ? w[i + 1] : 0)));
+  auto stream = [&](size_t a, size_t b, Bytes& o) {
+    ZBitW bw(o);
+    for (size_t k = b; k-- > a;) bw.put(code[lits[k]], len[lits[k]]);
+    bw.finish();
+  };
+  Bytes body = tree;
+  int sf;
+  if (n <= 1023) {
+    sf = 0;
+    Bytes s1;
+    stream(0, n, s1);
+    body.insert(body.end(), s1.begin(), s1.end());
+  } else {
+    const size_t per = (n + 3) / 4;
+    Bytes s[4];
+    for (int k = 0; k < 4; ++k) stream(std::min(n, k * per), std::min(n, (k + 1) * per), s[k]);
+    for (int k = 0; k < 3; ++k) {
+      if (s[k].size() > 65535) return false;
+      body.push_back(static_cast<uint8_t>(s[k].size()));
+      body.push_back(static_cast<uint8_t>(s[k].size() >> 8));
+    }
+    for (int k = 0; k < 4; ++k) body.insert(body.end(), s[k].begin(), s[k].end());
+    sf = n <= 1023 ? 1 : n <= 16383 ? 2 : 3;
+  }
+  const size_t csize = body.size();
+  const int bits = sf < 2 ? 10 : sf == 2 ? 14 : 18;
+  if (csize >= (size_t(1) << bits) || csize >= n) return false;
+  const int hlen = sf < 2 ? 3 : sf == 2 ? 4 : 5;
+  const uint64_t h = 2u | (static_cast<uint64_t>(sf) << 2) | (static_cast<uint64_t>(n) << 4) |
+                     (static_cast<uint64_t>(csize) << (4 + bits));
+  out.clear();
+  for (int k = 0; k < hlen; ++k) out.push_back(static_cast<uint8_t>(h >> (8 * k)));
+  out.insert(out.end(), body.begin(), body.end());
+  return true;
+}
+
 // Compressed-block body for `seqs` and `lits`; false when it would not be
 // smaller than `raw` bytes.
 bool zstd_block_body(const std::vector<ZSeq>& seqs, const Bytes& lits, size_t raw, Bytes& body) {
   body.clear();
   const size_t n = lits.size();
-  if (n <= 31) {
+  Bytes hl;
+  if (huf_literals(lits, hl)) {
+    body = hl;
+  } else if (n <= 31) {
     body.push_back(static_cast<uint8_t>(n << 3));
   } else if (n <= 4095) {
     body.push_back(static_cast<uint8_t>(((n & 15) << 4) | (1 << 2)));
@@ -442,7 +600,7 @@ bool zstd_block_body(const std::vector<ZSeq>& seqs, const Bytes& lits, size_t ra
     body.push_back(static_cast<uint8_t>(n >> 4));
     body.push_back(static_cast<uint8_t>(n >> 12));
   }
-  body.insert(body.end(), lits.begin(), lits.end());
+  if (hl.empty()) body.insert(body.end(), lits.begin(), lits.end());
   const size_t ns = seqs.size();
   if (ns < 128) {
     body.push_back(static_cast<uint8_t>(ns));
