@@ -38,6 +38,7 @@
 #include <vector>
 
 #include "../../include/pq.h"
+#include "huf_lengths.h"
 
 namespace {
 
@@ -428,87 +429,6 @@ struct ZSeq {
   uint32_t ll, off, ml;
 };
 
-// Huffman code lengths for byte counts, limited to kHufMaxBits: plain
-// Huffman merging, then, if the longest code is too long, lengths above the
-// limit are cut to it and the Kraft sum is repaid by lengthening the longest
-// codes still below the limit (least frequent first).
-constexpr int kHufMaxBits = 11;
-
-bool huf_lengths(const uint32_t* cnt, int nsym, int* len) {
-  struct Node {
-    uint64_t w;
-    int l, r;
-  };
-  std::vector<Node> nodes;
-  std::vector<std::pair<uint64_t, int>> heap;  // (weight, node) min-heap
-  for (int s = 0; s < nsym; ++s) {
-    len[s] = 0;
-    if (cnt[s]) {
-      nodes.push_back({cnt[s], -1 - s, -1});
-      heap.push_back({cnt[s], static_cast<int>(nodes.size()) - 1});
-    }
-  }
-  if (heap.size() < 2) return false;  // one symbol: RLE literals instead
-  auto cmp = [](const std::pair<uint64_t, int>& a, const std::pair<uint64_t, int>& b) { return a > b; };
-  std::make_heap(heap.begin(), heap.end(), cmp);
-  while (heap.size() > 1) {
-    std::pop_heap(heap.begin(), heap.end(), cmp);
-    const auto a = heap.back();
-    heap.pop_back();
-    std::pop_heap(heap.begin(), heap.end(), cmp);
-    const auto b = heap.back();
-    heap.pop_back();
-    nodes.push_back({a.first + b.first, a.second, b.second});
-    heap.push_back({a.first + b.first, static_cast<int>(nodes.size()) - 1});
-    std::push_heap(heap.begin(), heap.end(), cmp);
-  }
-  // depths by an explicit stack walk from the root
-  std::vector<std::pair<int, int>> st = {{heap[0].second, 0}};
-  while (!st.empty()) {
-    const auto [n, d] = st.back();
-    st.pop_back();
-    if (nodes[n].l < 0) {
-      len[-1 - nodes[n].l] = std::max(d, 1);
-    } else {
-      st.push_back({nodes[n].l, d + 1});
-      st.push_back({nodes[n].r, d + 1});
-    }
-  }
-  // limit: Kraft sum in units of 2^-kHufMaxBits must stay <= 2^kHufMaxBits
-  int64_t kraft = 0;
-  for (int s = 0; s < nsym; ++s)
-    if (len[s]) {
-      if (len[s] > kHufMaxBits) len[s] = kHufMaxBits;
-      kraft += int64_t(1) << (kHufMaxBits - len[s]);
-    }
-  const int64_t cap = int64_t(1) << kHufMaxBits;
-  if (kraft > cap) {
-    std::vector<int> order;
-    for (int s = 0; s < nsym; ++s)
-      if (len[s]) order.push_back(s);
-    std::sort(order.begin(), order.end(), [&](int a, int b) { return cnt[a] < cnt[b] || (cnt[a] == cnt[b] && a < b); });
-    while (kraft > cap) {
-      bool moved = false;
-      for (int s : order)
-        if (len[s] < kHufMaxBits) {
-          kraft -= int64_t(1) << (kHufMaxBits - len[s] - 1);
-          ++len[s];
-          moved = true;
-          if (kraft <= cap) break;
-        }
-      if (!moved) return false;
-    }
-    // then spend what is left of the Kraft sum on the most frequent codes,
-    // so that the code stays complete
-    for (auto it = order.rbegin(); it != order.rend(); ++it)
-      while (len[*it] > 1 && kraft + (int64_t(1) << (kHufMaxBits - len[*it])) <= cap) {
-        kraft += int64_t(1) << (kHufMaxBits - len[*it]);
-        --len[*it];
-      }
-  }
-  return true;
-}
-
 // Huffman-coded literals section (tree description with direct 4-bit
 // weights, so literal bytes below 128 only; 1 stream up to 1023 literals,
 // else 4 streams).  False when it does not apply or would not shrink.
@@ -521,7 +441,7 @@ bool huf_literals(const Bytes& lits, Bytes& out) {
   while (top > 0 && cnt[top] == 0) --top;
   if (top >= 128) return false;  // direct weights describe symbols 0..128 at most
   int len[256];
-  if (!huf_lengths(cnt, top + 1, len)) return false;
+  if (!pqw::huf_lengths(cnt, top + 1, len)) return false;
   int mb = 0;
   for (int s = 0; s <= top; ++s) mb = std::max(mb, len[s]);
   // weights: nbits = mb + 1 - weight; the Kraft sum must be exactly full

@@ -252,3 +252,70 @@ def test_native_zstd_frames_decode_with_libzstd():
         assert pa.Codec("zstd").decompress(frame, decompressed_size=size, asbytes=True) == want
         n += 1
     assert n > 10
+
+
+def test_native_zstd_huffman_literals(monkeypatch):
+    """Literal bytes below 128 come out Huffman-coded in 1- and 4-stream
+    sections, and libzstd reads them."""
+    pa = pytest.importorskip("pyarrow")
+    _, write_table = _native()
+    rng = np.random.default_rng(8)
+    rows = [(65 + np.minimum(rng.geometric(0.5, 100 if k % 2 else 1100) - 1, 60)).astype(np.uint8).tobytes()
+            for k in range(400)]   # lengths 100 and 1100: their bytes are below 128 too
+    lens = np.array([len(r) for r in rows], dtype=np.int64)
+    off = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum(lens, out=off[1:])
+    col = synth.ColumnData("geo", "BYTE_ARRAY", synth.StringData(off, np.frombuffer(b"".join(rows), np.uint8).copy(),
+                                                                 np.arange(len(rows), dtype=np.int32)))
+    data = bytes(write_table(synth.Table([col]), synth.TableSpec(len(rows), 1 << 20,
+                                                                 [synth.ColumnSpec("PLAIN", "ZSTD", 1)])))
+    kinds = set()
+    orig = Z.decode_literals
+
+    def spy(buf, pos, end, st):
+        kinds.add((buf[pos] & 3, (buf[pos] >> 2) & 3))
+        return orig(buf, pos, end, st)
+    monkeypatch.setattr(Z, "decode_literals", spy)
+    r = R.read_file(data)[0]
+    assert [bytes(r.chars[r.offsets[j]:r.offsets[j + 1]]) for j in range(len(rows))] == rows
+    assert (2, 0) in kinds and ((2, 2) in kinds or (2, 3) in kinds)
+    for _, frame, size in zstd_pages(data):
+        assert pa.Codec("zstd").decompress(frame, decompressed_size=size, asbytes=True) == Z.decompress(frame)
+
+
+def test_huffman_length_limit():
+    """The writer's code lengths: at most 11 bits, a complete prefix code
+    (Kraft sum exactly 1), never shorter for a rarer symbol; Fibonacci counts
+    (19 bits deep unrestricted) force the limit."""
+    import ctypes
+    import os
+    import shutil
+    import subprocess
+    import tempfile
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    so = os.path.join(tempfile.mkdtemp(), "huf.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I",
+                    os.path.join(root, "paper_2602_17335_gb300", "csrc"),
+                    os.path.join(root, "tests", "huf_lengths_harness.cpp"), "-o", so], check=True)
+    lib = ctypes.CDLL(so)
+    fib = [1, 1]
+    while len(fib) < 20:
+        fib.append(fib[-1] + fib[-2])
+    rng = np.random.default_rng(2)
+    cases = [fib, fib[::-1], [1] * 128, [5] + [0] * 50 + [7], list(rng.integers(0, 1000, 128)),
+             list((2.0 ** -np.arange(40) * 2 ** 30).astype(np.int64) + 1)]
+    for counts in cases:
+        cnt = np.array(counts, dtype=np.uint32)
+        ln = np.zeros(len(cnt), dtype=np.int32)
+        ok = lib.huf_lengths_host(cnt.ctypes.data, len(cnt), ln.ctypes.data)
+        assert ok
+        used = ln[cnt > 0]
+        assert np.all(ln[cnt == 0] == 0) and used.min() >= 1 and used.max() <= 11
+        assert sum(2.0 ** -int(l) for l in used) == 1.0
+        order = np.argsort(-cnt[cnt > 0], kind="stable")
+        assert np.all(np.diff(used[order]) >= 0) or len(used) < 2
+    ln = np.zeros(20, dtype=np.int32)
+    lib.huf_lengths_host(np.array(fib, np.uint32).ctypes.data, 20, ln.ctypes.data)
+    assert ln.max() == 11
