@@ -39,6 +39,7 @@
 
 #include "../../include/pq.h"
 #include "huf_lengths.h"
+#include "zstd_dec.cuh"
 
 namespace {
 
@@ -310,8 +311,8 @@ void snappy_compress(const uint8_t* in, size_t n, Bytes& o) {
 // header, no checksum).  Each block of up to 128 KB of input is coded with
 // greedy LZ77 matches (4-byte hash over the whole frame so far) as
 // sequences whose codes use the format's predefined FSE tables; its
-// literals are Huffman-coded (1 or 4 streams) when they are all below 128
-// and that pays, else stored raw; a block without matches, or one that
+// literals are Huffman-coded (1 or 4 streams) when that pays, else stored
+// raw; a block without matches, or one that
 // would not shrink, is stored as a raw (or RLE) block.  Every Zstandard
 // decoder reads the result.
 
@@ -429,9 +430,109 @@ struct ZSeq {
   uint32_t ll, off, ml;
 };
 
+// FSE-compressed Huffman weights (the tree description form for literal
+// bytes of 128 and above): normalized counts at accuracy log 6, the table
+// description, then the weights in two interleaved states.  The result is
+// checked by decoding it with the engine's own decoding core; any case the
+// simple scheme cannot express returns false (the literals then go raw).
+bool fse_weights(const int* w, int nw, int mb, Bytes& out) {
+  if (nw < 2) return false;
+  const int al = 6, L = 1 << al;
+  int cnt[16] = {0}, top = 0;
+  for (int i = 0; i < nw; ++i) {
+    ++cnt[w[i]];
+    top = std::max(top, w[i]);
+  }
+  int distinct = 0;
+  for (int s = 0; s <= top; ++s) distinct += cnt[s] > 0;
+  if (distinct < 2) return false;
+  int8_t norm[16] = {0};
+  int sum = 0, big = 0;
+  for (int s = 0; s <= top; ++s) {
+    if (!cnt[s]) continue;
+    norm[s] = static_cast<int8_t>(std::max(1, cnt[s] * L / nw));
+    sum += norm[s];
+    if (norm[s] > norm[big] || !cnt[big]) big = s;
+  }
+  norm[big] = static_cast<int8_t>(norm[big] + (L - sum));
+  if (norm[big] < 1) return false;
+  // table description: accuracy log, then probability + 1 per symbol with
+  // one bit less for the small values, 2-bit repeat flags after a zero
+  Bytes desc;
+  {
+    ZBitW bw(desc);
+    bw.put(al - 5, 4);
+    int remaining = L;
+    for (int s = 0; s <= top && remaining > 0; ++s) {
+      const uint32_t v = static_cast<uint32_t>(norm[s]) + 1;
+      const uint32_t nv = static_cast<uint32_t>(remaining) + 2;
+      const int nbits = bit_length(nv - 1);
+      const uint32_t spare = (1u << nbits) - nv;
+      if (v < spare)
+        bw.put(v, nbits - 1);
+      else if (v < (1u << (nbits - 1)))
+        bw.put(v, nbits);
+      else
+        bw.put(v + spare, nbits);
+      remaining -= norm[s];
+      if (norm[s] == 0) {
+        int run = 0;
+        while (s + 1 + run <= top && norm[s + 1 + run] == 0) ++run;
+        s += run;
+        for (;;) {
+          const int r = std::min(run, 3);
+          bw.put(r, 2);
+          run -= r;
+          if (r < 3) break;
+        }
+      }
+    }
+    if (remaining != 0) return false;
+    if (bw.n) desc.push_back(static_cast<uint8_t>(bw.acc));
+  }
+  const ZFseEnc t(norm, top + 1, al);
+  // decoder: states A (even weights) and B (odd) start from the last two
+  // fields written; after each weight but the last two its state reads its
+  // update; the update after weight nw-2 runs past the stream's start
+  std::vector<int> st(nw);
+  st[nw - 1] = t.any_state(w[nw - 1]);
+  st[nw - 2] = -1;
+  for (int k = 0; k < L; ++k)
+    if (t.sym[k] == w[nw - 2] && t.nb[k] > 0) {
+      st[nw - 2] = k;
+      break;
+    }
+  if (st[nw - 2] < 0) return false;
+  for (int i = nw - 3; i >= 0; --i) st[i] = t.from[w[i]][st[i + 2]];
+  Bytes bits;
+  {
+    ZBitW bw(bits);
+    for (int i = nw - 3; i >= 0; --i) bw.put(st[i + 2] - t.base[st[i]], t.nb[st[i]]);
+    bw.put(st[1], al);
+    bw.put(st[0], al);
+    bw.finish();
+  }
+  const size_t size = desc.size() + bits.size();
+  if (size >= 128) return false;
+  out.clear();
+  out.push_back(static_cast<uint8_t>(size));
+  out.insert(out.end(), desc.begin(), desc.end());
+  out.insert(out.end(), bits.begin(), bits.end());
+  // check with the decoding core
+  static thread_local pqi::ZState z;
+  uint32_t used = 0;
+  if (pqi::z_read_huf(out.data(), static_cast<uint32_t>(out.size()), &z, &used) || used != out.size() ||
+      z.huf_bits != mb)
+    return false;
+  for (int i = 0; i < nw; ++i)
+    if (z.weights[i] != w[i]) return false;
+  return true;
+}
+
 // Huffman-coded literals section (tree description with direct 4-bit
-// weights, so literal bytes below 128 only; 1 stream up to 1023 literals,
-// else 4 streams).  False when it does not apply or would not shrink.
+// weights for literal bytes below 128, else FSE-compressed weights; 1
+// stream up to 1023 literals, else 4 streams).  False when it does not
+// apply or would not shrink.
 bool huf_literals(const Bytes& lits, Bytes& out) {
   const size_t n = lits.size();
   if (n < 64 || n > 262143) return false;
@@ -439,7 +540,6 @@ bool huf_literals(const Bytes& lits, Bytes& out) {
   for (uint8_t c : lits) ++cnt[c];
   int top = 255;
   while (top > 0 && cnt[top] == 0) --top;
-  if (top >= 128) return false;  // direct weights describe symbols 0..128 at most
   int len[256];
   if (!pqw::huf_lengths(cnt, top + 1, len)) return false;
   int mb = 0;
@@ -463,9 +563,13 @@ bool huf_literals(const Bytes& lits, Bytes& out) {
   // tree description: the last symbol's weight is implied
   Bytes tree;
   const int nw = top;  // weights of symbols 0 .. top-1 are written
-  tree.push_back(static_cast<uint8_t>(127 + nw));
-  for (int i = 0; i < nw; i += 2)
-    tree.push_back(static_cast<uint8_t>((w[i] << 4) | (i + 1 < nw ? w[i + 1] : 0)));
+  if (nw <= 128) {
+    tree.push_back(static_cast<uint8_t>(127 + nw));
+    for (int i = 0; i < nw; i += 2)
+      tree.push_back(static_cast<uint8_t>((w[i] << 4) | (i + 1 < nw ? w[i + 1] : 0)));
+  } else if (!fse_weights(w, nw, mb, tree)) {
+    return false;
+  }
   auto stream = [&](size_t a, size_t b, Bytes& o) {
     ZBitW bw(o);
     for (size_t k = b; k-- > a;) bw.put(code[lits[k]], len[lits[k]]);

@@ -319,3 +319,30 @@ def test_huffman_length_limit():
     ln = np.zeros(20, dtype=np.int32)
     lib.huf_lengths_host(np.array(fib, np.uint32).ctypes.data, 20, ln.ctypes.data)
     assert ln.max() == 11
+
+
+def test_native_zstd_fse_compressed_weights(monkeypatch):
+    """Binary pages (literal bytes of 128 and above) get Huffman literals
+    whose weights are FSE-compressed (normalized counts, table description,
+    two interleaved states); libzstd reads every frame."""
+    pa = pytest.importorskip("pyarrow")
+    _, write_table = _native()
+    rng = np.random.default_rng(3)
+    n = 40_000
+    cols = [synth.ColumnData("sorted", "INT64", np.cumsum(rng.integers(0, 1000, n)).astype(np.int64)),
+            synth.ColumnData("rounded", "DOUBLE", np.round(rng.standard_normal(n), 2))]
+    data = bytes(write_table(synth.Table(cols), synth.TableSpec(n, 1 << 20, [synth.ColumnSpec("PLAIN", "ZSTD", 1)
+                                                                            for _ in cols])))
+    forms = []
+    orig = Z.read_huffman_description
+
+    def spy(buf, pos, end):
+        forms.append("direct" if buf[pos] >= 128 else "fse")
+        return orig(buf, pos, end)
+    monkeypatch.setattr(Z, "read_huffman_description", spy)
+    res = R.read_file(data)
+    for c, r in zip(cols, res):
+        assert np.array_equal(np.asarray(c.values).view(np.uint8), r.values.view(np.uint8))
+    assert "fse" in forms
+    for _, frame, size in zstd_pages(data):
+        assert pa.Codec("zstd").decompress(frame, decompressed_size=size, asbytes=True) == Z.decompress(frame)
