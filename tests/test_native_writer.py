@@ -206,15 +206,15 @@ def zstd_pages(data):
 def test_native_writer_zstd_pages(version):
     """Zstandard pages of the native writer: the oracle reads them back to
     the table, compressible columns get compressed blocks (LZ77 sequences
-    under the predefined FSE tables), incompressible ones raw blocks, and
-    libzstd (through pyarrow) reads the same file."""
+    under the predefined FSE tables), uniformly random bytes raw blocks,
+    and libzstd (through pyarrow) reads the same file."""
     _, write_table = _native()
     rng = np.random.default_rng(3)
     n = 30_000
     cols = [synth.ColumnData("sorted", "INT64", np.cumsum(rng.integers(0, 3, n)).astype(np.int64)),
             synth.ColumnData("strs", "BYTE_ARRAY", synth.strings_uniform(rng, n, k=200)),
             synth.ColumnData("lowcard", "INT32", rng.integers(0, 5, n).astype(np.int32), rng.random(n) > 0.2),
-            synth.ColumnData("noise", "DOUBLE", rng.standard_normal(n))]
+            synth.ColumnData("noise", "INT64", rng.integers(-2**63, 2**63 - 1, n, dtype=np.int64))]
     cols[2].values[~cols[2].valid] = 0
     tab = synth.Table(cols)
     spec = synth.TableSpec(12_000, 1 << 16, [synth.ColumnSpec("PLAIN", "ZSTD", version) for _ in cols])
