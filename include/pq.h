@@ -341,7 +341,7 @@ typedef struct pq_write_column {
                                 0, 8, 5, 9 (integers), 0, 8, 9 (DOUBLE), 0, 8, 6, 7
                                 (BYTE_ARRAY) (paper Section 3, "Encoding Flexibility") */
   int32_t codec;             /* 0 UNCOMPRESSED, 1 SNAPPY, 6 ZSTD (frames of LZ77 sequences
-                                coded with the predefined FSE tables, Huffman or raw
+                                under FSE tables fitted per block, Huffman or raw
                                 literals; the scan itself reads only UNCOMPRESSED and
                                 SNAPPY chunks) */
   int32_t page_version;      /* 1 DATA_PAGE, 2 DATA_PAGE_V2 */

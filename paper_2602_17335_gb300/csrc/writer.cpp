@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <array>
 #include <atomic>
+#include <memory>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -310,9 +311,9 @@ void snappy_compress(const uint8_t* in, size_t n, Bytes& o) {
 // One Zstandard frame per page (single segment, content size in the
 // header, no checksum).  Each block of up to 128 KB of input is coded with
 // greedy LZ77 matches (4-byte hash over the whole frame so far) as
-// sequences whose codes use the format's predefined FSE tables; its
-// literals are Huffman-coded (1 or 4 streams) when that pays, else stored
-// raw; a block without matches, or one that
+// sequences whose codes use FSE tables fitted to the block (or an RLE
+// table, or the predefined ones, whichever is smaller); its literals are
+// Huffman-coded (1 or 4 streams) when that pays, else stored raw; a block without matches, or one that
 // would not shrink, is stored as a raw (or RLE) block.  Every Zstandard
 // decoder reads the result.
 
@@ -347,7 +348,7 @@ struct ZFseEnc {
   std::vector<uint8_t> sym, nb;
   std::vector<uint16_t> base;
   std::vector<std::vector<uint16_t>> from;  // [symbol][next state] -> state
-  ZFseEnc(const int8_t* norm, int nsym, int a) : al(a), size(1 << a), sym(size), nb(size), base(size), from(nsym) {
+  ZFseEnc(const int16_t* norm, int nsym, int a) : al(a), size(1 << a), sym(size), nb(size), base(size), from(nsym) {
     int high = size - 1;
     std::vector<uint32_t> next(nsym);
     for (int s = 0; s < nsym; ++s) {
@@ -381,11 +382,11 @@ struct ZFseEnc {
 };
 
 const ZFseEnc& zenc_table(int which) {  // 0 literal lengths, 1 offsets, 2 match lengths
-  static const int8_t LL[36] = {4, 3, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 1, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 2, 3, 2, 1,
+  static const int16_t LL[36] = {4, 3, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 1, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 2, 3, 2, 1,
                                 1, 1, 1, 1, -1, -1, -1, -1};
-  static const int8_t OF[29] = {1, 1, 1, 1, 1, 1, 2, 2, 2, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, -1, -1, -1,
+  static const int16_t OF[29] = {1, 1, 1, 1, 1, 1, 2, 2, 2, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, -1, -1, -1,
                                 -1, -1};
-  static const int8_t ML[53] = {1, 4, 3, 2, 2, 2, 2, 2, 2, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1,
+  static const int16_t ML[53] = {1, 4, 3, 2, 2, 2, 2, 2, 2, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1,
                                 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, -1, -1, -1, -1, -1, -1, -1};
   static const ZFseEnc t_ll(LL, 36, 6), t_of(OF, 29, 5), t_ml(ML, 53, 6);
   return which == 0 ? t_ll : which == 1 ? t_of : t_ml;
@@ -430,6 +431,63 @@ struct ZSeq {
   uint32_t ll, off, ml;
 };
 
+// Normalized counts of cnt[0, nsym) to 2^al: every present symbol at least
+// 1, the rounding remainder on the most frequent one.  False if impossible.
+bool fse_normalize(const uint32_t* cnt, int nsym, int al, int16_t* norm) {
+  uint64_t total = 0;
+  for (int s = 0; s < nsym; ++s) total += cnt[s];
+  if (total == 0) return false;
+  const int64_t L = int64_t(1) << al;
+  int64_t sum = 0;
+  int big = -1;
+  for (int s = 0; s < nsym; ++s) {
+    norm[s] = 0;
+    if (!cnt[s]) continue;
+    norm[s] = static_cast<int16_t>(std::max<int64_t>(1, static_cast<int64_t>(cnt[s]) * L / static_cast<int64_t>(total)));
+    sum += norm[s];
+    if (big < 0 || norm[s] > norm[big]) big = s;
+  }
+  const int64_t fixed = norm[big] + (L - sum);
+  if (fixed < 1) return false;
+  norm[big] = static_cast<int16_t>(fixed);
+  return true;
+}
+
+// FSE table description of norm[0, nsym): accuracy log, then probability
+// + 1 per symbol (the small values one bit shorter), 2-bit repeat flags
+// after a zero probability, up to the last symbol.  Appends whole bytes.
+bool fse_describe(const int16_t* norm, int nsym, int al, Bytes& out) {
+  ZBitW bw(out);
+  bw.put(al - 5, 4);
+  int remaining = 1 << al;
+  for (int s = 0; s < nsym && remaining > 0; ++s) {
+    const uint32_t v = static_cast<uint32_t>(norm[s]) + 1;
+    const uint32_t nv = static_cast<uint32_t>(remaining) + 2;
+    const int nbits = bit_length(nv - 1);
+    const uint32_t spare = (1u << nbits) - nv;
+    if (v < spare)
+      bw.put(v, nbits - 1);
+    else if (v < (1u << (nbits - 1)))
+      bw.put(v, nbits);
+    else
+      bw.put(v + spare, nbits);
+    remaining -= norm[s];
+    if (norm[s] == 0) {
+      int run = 0;
+      while (s + 1 + run < nsym && norm[s + 1 + run] == 0) ++run;
+      s += run;
+      for (;;) {
+        const int r = std::min(run, 3);
+        bw.put(r, 2);
+        run -= r;
+        if (r < 3) break;
+      }
+    }
+  }
+  if (bw.n) out.push_back(static_cast<uint8_t>(bw.acc));
+  return remaining == 0;
+}
+
 // FSE-compressed Huffman weights (the tree description form for literal
 // bytes of 128 and above): normalized counts at accuracy log 6, the table
 // description, then the weights in two interleaved states.  The result is
@@ -446,50 +504,12 @@ bool fse_weights(const int* w, int nw, int mb, Bytes& out) {
   int distinct = 0;
   for (int s = 0; s <= top; ++s) distinct += cnt[s] > 0;
   if (distinct < 2) return false;
-  int8_t norm[16] = {0};
-  int sum = 0, big = 0;
-  for (int s = 0; s <= top; ++s) {
-    if (!cnt[s]) continue;
-    norm[s] = static_cast<int8_t>(std::max(1, cnt[s] * L / nw));
-    sum += norm[s];
-    if (norm[s] > norm[big] || !cnt[big]) big = s;
-  }
-  norm[big] = static_cast<int8_t>(norm[big] + (L - sum));
-  if (norm[big] < 1) return false;
-  // table description: accuracy log, then probability + 1 per symbol with
-  // one bit less for the small values, 2-bit repeat flags after a zero
+  uint32_t ucnt[16];
+  for (int s = 0; s <= top; ++s) ucnt[s] = static_cast<uint32_t>(cnt[s]);
+  int16_t norm[16] = {0};
+  if (!fse_normalize(ucnt, top + 1, al, norm)) return false;
   Bytes desc;
-  {
-    ZBitW bw(desc);
-    bw.put(al - 5, 4);
-    int remaining = L;
-    for (int s = 0; s <= top && remaining > 0; ++s) {
-      const uint32_t v = static_cast<uint32_t>(norm[s]) + 1;
-      const uint32_t nv = static_cast<uint32_t>(remaining) + 2;
-      const int nbits = bit_length(nv - 1);
-      const uint32_t spare = (1u << nbits) - nv;
-      if (v < spare)
-        bw.put(v, nbits - 1);
-      else if (v < (1u << (nbits - 1)))
-        bw.put(v, nbits);
-      else
-        bw.put(v + spare, nbits);
-      remaining -= norm[s];
-      if (norm[s] == 0) {
-        int run = 0;
-        while (s + 1 + run <= top && norm[s + 1 + run] == 0) ++run;
-        s += run;
-        for (;;) {
-          const int r = std::min(run, 3);
-          bw.put(r, 2);
-          run -= r;
-          if (r < 3) break;
-        }
-      }
-    }
-    if (remaining != 0) return false;
-    if (bw.n) desc.push_back(static_cast<uint8_t>(bw.acc));
-  }
+  if (!fse_describe(norm, top + 1, al, desc)) return false;
   const ZFseEnc t(norm, top + 1, al);
   // decoder: states A (even weights) and B (odd) start from the last two
   // fields written; after each weight but the last two its state reads its
@@ -625,59 +645,115 @@ bool zstd_block_body(const std::vector<ZSeq>& seqs, const Bytes& lits, size_t ra
     body.push_back(static_cast<uint8_t>(n >> 12));
   }
   if (hl.empty()) body.insert(body.end(), lits.begin(), lits.end());
+  // sequences: with the predefined tables, and with tables fitted to this
+  // block (an RLE table for a single code); the smaller section is kept
   const size_t ns = seqs.size();
-  if (ns < 128) {
-    body.push_back(static_cast<uint8_t>(ns));
-  } else if (ns < 0x7F00) {
-    body.push_back(static_cast<uint8_t>((ns >> 8) + 128));
-    body.push_back(static_cast<uint8_t>(ns));
-  } else {
-    body.push_back(255);
-    body.push_back(static_cast<uint8_t>(ns - 0x7F00));
-    body.push_back(static_cast<uint8_t>((ns - 0x7F00) >> 8));
+  std::vector<int> code[3], nbx[3];
+  std::vector<uint32_t> extra[3];
+  for (int k = 0; k < 3; ++k) {
+    code[k].resize(ns);
+    nbx[k].resize(ns);
+    extra[k].resize(ns);
   }
-  body.push_back(0);  // all three codes use the predefined tables
-  const ZFseEnc& tl = zenc_table(0);
-  const ZFseEnc& to = zenc_table(1);
-  const ZFseEnc& tm = zenc_table(2);
-  // the decoder reads, per sequence: offset, match-length and literal-length
-  // extra bits, then (but after the last) the literal-length, match-length
-  // and offset state bits; and first of all the three initial states.  The
-  // stream is read from its end, so it is written in exactly the reverse
-  // order, last sequence first.
-  ZBitW w(body);
-  int sl = 0, so = 0, sm = 0;
-  for (size_t k = ns; k-- > 0;) {
-    const ZSeq& q = seqs[k];
-    int lc, lnb, mc, mnb;
-    uint32_t lx, mx;
-    zll_code(q.ll, &lc, &lnb, &lx);
-    zml_code(q.ml, &mc, &mnb, &mx);
-    const uint32_t ov = q.off + 3;
-    const int oc = bit_length(ov) - 1;
-    if (oc > 28) return false;  // beyond the predefined offset codes
-    const uint32_t ox = ov - (1u << oc);
-    if (k + 1 == ns) {
-      sl = tl.any_state(lc);
-      sm = tm.any_state(mc);
-      so = to.any_state(oc);
-    } else {
-      const int pl = tl.from[lc][sl], pm = tm.from[mc][sm], po = to.from[oc][so];
-      w.put(so - to.base[po], to.nb[po]);
-      w.put(sm - tm.base[pm], tm.nb[pm]);
-      w.put(sl - tl.base[pl], tl.nb[pl]);
-      sl = pl;
-      sm = pm;
-      so = po;
+  for (size_t i = 0; i < ns; ++i) {
+    zll_code(seqs[i].ll, &code[0][i], &nbx[0][i], &extra[0][i]);
+    const uint32_t ov = seqs[i].off + 3;
+    code[1][i] = bit_length(ov) - 1;
+    nbx[1][i] = code[1][i];
+    extra[1][i] = ov - (1u << code[1][i]);
+    zml_code(seqs[i].ml, &code[2][i], &nbx[2][i], &extra[2][i]);
+  }
+  Bytes best, trial;
+  bool have = false;
+  for (int variant = 0; variant < 2; ++variant) {
+    const ZFseEnc* t[3];
+    std::unique_ptr<ZFseEnc> own[3];
+    int mode[3];
+    Bytes desc[3];
+    bool ok = true;
+    for (int k = 0; k < 3 && ok; ++k) {
+      const int nsym = k == 0 ? 36 : k == 1 ? 32 : 53;
+      if (variant == 0) {
+        t[k] = &zenc_table(k);
+        mode[k] = 0;
+        if (k == 1)
+          for (size_t i = 0; i < ns && ok; ++i) ok = code[1][i] <= 28;  // the predefined offset codes
+        continue;
+      }
+      uint32_t cnt[53] = {0};
+      int distinct = 0, last = 0;
+      for (size_t i = 0; i < ns; ++i) distinct += cnt[code[k][i]]++ == 0;
+      for (int s2 = 0; s2 < nsym; ++s2)
+        if (cnt[s2]) last = s2;
+      int16_t norm[53] = {0};
+      if (distinct == 1) {
+        norm[last] = 1;
+        own[k].reset(new ZFseEnc(norm, last + 1, 0));
+        mode[k] = 1;
+        desc[k].push_back(static_cast<uint8_t>(last));
+      } else {
+        const int max_al = k == 1 ? 8 : 9;
+        const int al = std::min(max_al, std::max(6, bit_length(ns)));
+        ok = fse_normalize(cnt, last + 1, al, norm) && fse_describe(norm, last + 1, al, desc[k]);
+        if (ok) own[k].reset(new ZFseEnc(norm, last + 1, al));
+        mode[k] = 2;
+      }
+      t[k] = own[k].get();
     }
-    w.put(lx, lnb);
-    w.put(mx, mnb);
-    w.put(ox, oc);
+    if (!ok) continue;
+    trial.clear();
+    if (ns < 128) {
+      trial.push_back(static_cast<uint8_t>(ns));
+    } else if (ns < 0x7F00) {
+      trial.push_back(static_cast<uint8_t>((ns >> 8) + 128));
+      trial.push_back(static_cast<uint8_t>(ns));
+    } else {
+      trial.push_back(255);
+      trial.push_back(static_cast<uint8_t>(ns - 0x7F00));
+      trial.push_back(static_cast<uint8_t>((ns - 0x7F00) >> 8));
+    }
+    trial.push_back(static_cast<uint8_t>((mode[0] << 6) | (mode[1] << 4) | (mode[2] << 2)));
+    for (int k = 0; k < 3; ++k) trial.insert(trial.end(), desc[k].begin(), desc[k].end());
+    // the decoder reads, per sequence: offset, match-length and
+    // literal-length extra bits, then (but after the last) the
+    // literal-length, match-length and offset state bits; and first of all
+    // the three initial states.  The stream is read from its end, so it is
+    // written in exactly the reverse order, last sequence first.
+    const ZFseEnc& tl = *t[0];
+    const ZFseEnc& to = *t[1];
+    const ZFseEnc& tm = *t[2];
+    ZBitW w(trial);
+    int sl = 0, so = 0, sm = 0;
+    for (size_t i = ns; i-- > 0;) {
+      const int lc = code[0][i], oc = code[1][i], mc = code[2][i];
+      if (i + 1 == ns) {
+        sl = tl.any_state(lc);
+        sm = tm.any_state(mc);
+        so = to.any_state(oc);
+      } else {
+        const int pl = tl.from[lc][sl], pm = tm.from[mc][sm], po = to.from[oc][so];
+        w.put(so - to.base[po], to.nb[po]);
+        w.put(sm - tm.base[pm], tm.nb[pm]);
+        w.put(sl - tl.base[pl], tl.nb[pl]);
+        sl = pl;
+        sm = pm;
+        so = po;
+      }
+      w.put(extra[0][i], nbx[0][i]);
+      w.put(extra[2][i], nbx[2][i]);
+      w.put(extra[1][i], nbx[1][i]);
+    }
+    w.put(sm, tm.al);
+    w.put(so, to.al);
+    w.put(sl, tl.al);
+    w.finish();
+    if (!have || trial.size() < best.size()) {
+      best.swap(trial);
+      have = true;
+    }
   }
-  w.put(sm, tm.al);
-  w.put(so, to.al);
-  w.put(sl, tl.al);
-  w.finish();
+  if (!have) return false;
+  body.insert(body.end(), best.begin(), best.end());
   return body.size() < raw;
 }
 

@@ -5,7 +5,7 @@ Both follow the same deterministic layout rules, so on uncompressed data
 they must write the same bytes (only the footer's created_by differs);
 with Snappy the compressors differ, so the file must read back to the table
 and keep the same page structure; its Zstandard pages (LZ77 sequences under
-the predefined FSE tables) read back through the oracle and libzstd.  The
+fitted or predefined FSE tables) read back through the oracle and libzstd.  The
 per-chunk encoding choice ("AUTO", Section 3's "Encoding Flexibility") is
 pinned to the smallest explicit encoding of each chunk and to the obvious
 winners of shaped data."""
@@ -206,7 +206,7 @@ def zstd_pages(data):
 def test_native_writer_zstd_pages(version):
     """Zstandard pages of the native writer: the oracle reads them back to
     the table, compressible columns get compressed blocks (LZ77 sequences
-    under the predefined FSE tables), uniformly random bytes raw blocks,
+    under FSE tables), uniformly random bytes raw blocks,
     and libzstd (through pyarrow) reads the same file."""
     _, write_table = _native()
     rng = np.random.default_rng(3)
@@ -344,5 +344,31 @@ def test_native_zstd_fse_compressed_weights(monkeypatch):
     for c, r in zip(cols, res):
         assert np.array_equal(np.asarray(c.values).view(np.uint8), r.values.view(np.uint8))
     assert "fse" in forms
+    for _, frame, size in zstd_pages(data):
+        assert pa.Codec("zstd").decompress(frame, decompressed_size=size, asbytes=True) == Z.decompress(frame)
+
+
+def test_native_zstd_fitted_sequence_tables(monkeypatch):
+    """Blocks whose sequence codes pay for their own FSE tables carry them
+    (transmitted tables; an RLE table where one code is used), and libzstd
+    reads every frame."""
+    pa = pytest.importorskip("pyarrow")
+    _, write_table = _native()
+    rng = np.random.default_rng(5)
+    n = 60_000
+    cols = [synth.ColumnData("sorted", "INT64", np.cumsum(rng.integers(0, 1000, n)).astype(np.int64)),
+            synth.ColumnData("lowcard", "INT32", rng.integers(0, 3, n).astype(np.int32))]
+    data = bytes(write_table(synth.Table(cols), synth.TableSpec(n, 1 << 20, [synth.ColumnSpec("PLAIN", "ZSTD", 2)
+                                                                            for _ in cols])))
+    modes = set()
+    orig = Z._table
+
+    def spy(buf, pos, end, mode, name, st):
+        modes.add(mode)
+        return orig(buf, pos, end, mode, name, st)
+    monkeypatch.setattr(Z, "_table", spy)
+    for c, r in zip(cols, R.read_file(data)):
+        assert np.array_equal(np.asarray(c.values).view(np.uint8), r.values.view(np.uint8))
+    assert {1, 2} <= modes
     for _, frame, size in zstd_pages(data):
         assert pa.Codec("zstd").decompress(frame, decompressed_size=size, asbytes=True) == Z.decompress(frame)
