@@ -198,8 +198,8 @@ class ClockSampler:
 
     def __enter__(self):
         try:
-            self.out = open(os.path.join(ROOT, "gpurun_out", "clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                            else os.devnull, "w")
+            # the raw samples go to $PQ_CLOCKS_CSV when set (the summary is in the JSON line)
+            self.out = open(os.environ.get("PQ_CLOCKS_CSV") or os.devnull, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index),
                  "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"

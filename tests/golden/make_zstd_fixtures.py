@@ -1,5 +1,6 @@
 """Writes the Zstandard Parquet fixtures of tests/golden (run it where
-pyarrow is installed; the GPU machine has no Zstandard library).
+pyarrow is installed: the fixtures carry libzstd-made pages to machines that
+have no Zstandard library).
 
 Inputs only: seeded synthetic tables from `synth`, compressed by libzstd
 through pyarrow at two levels, V1 and V2 pages.  Expected values never come
