@@ -162,6 +162,25 @@ def _oracle_unit(args):
     return decoded
 
 
+def pyarrow_context(data, decoded_bytes, reps=2):
+    """Context point, not the oracle: pyarrow's multithreaded reader on the
+    same file bytes in host memory, as decoded GB/s (best of `reps`)."""
+    try:
+        import pyarrow as pa
+        import pyarrow.parquet as pq
+    except ImportError:
+        return {"unavailable": "pyarrow is not installed on this host"}
+    buf = pa.py_buffer(bytes(data))
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        pq.read_table(pa.BufferReader(buf), use_threads=True)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return {"value": decoded_bytes / best / 1e9, "unit": "GB/s", "cores": os.cpu_count(),
+            "kind": "pyarrow read_table, all threads (context, not the oracle)", "seconds": best}
+
+
 def oracle_sample_all_cores(data):
     """The oracle_sample workload with the chunks as independent units over a
     process pool (spawn), one worker per unit up to the host's cores; each
@@ -500,8 +519,9 @@ def run_ours(a, rank, world, local_rank):
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
         del keep
 
-    cpu = cpu_all = None
+    cpu = cpu_all = ctx_pa = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        ctx_pa = pyarrow_context(data, decoded)
         b, s, desc = oracle_sample(bytes(data), max_seconds=25.0)
         cpu = {"value": b / s / 1e9, "unit": "GB/s", "cores": cpu_count_used(), "kind": "oracle", "sample": desc,
                "seconds": s}
@@ -521,7 +541,8 @@ def run_ours(a, rank, world, local_rank):
                        "l2": "inputs larger than L2 (files %.2f GB, outputs %.2f GB per step)" % (
                            data.nbytes / 1e9, decoded / 1e9),
                        "step": "index + plan + scan + wait"},
-            "roofline": roofline, "stages_ms": stages, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
+            "roofline": roofline, "stages_ms": stages, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
+            "cpu_context_pyarrow": ctx_pa, "e2e": e2e,
             "gpu_launches": a.steps * (index_launches + pinfo.launches_per_scan),
             "clocks": clk.summary(),
             "detail": {"decoded_bytes": decoded, "read_bytes": read, "pages": pinfo.n_pages,
