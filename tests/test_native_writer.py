@@ -372,3 +372,89 @@ def test_native_zstd_fitted_sequence_tables(monkeypatch):
     assert {1, 2} <= modes
     for _, frame, size in zstd_pages(data):
         assert pa.Codec("zstd").decompress(frame, decompressed_size=size, asbytes=True) == Z.decompress(frame)
+
+
+_WRITER_FUZZ = r'''
+import ctypes, pickle, sys
+sys.path.insert(0, sys.argv[3])
+from paper_2602_17335_gb300 import native as N
+lib = ctypes.CDLL(sys.argv[1])
+lib.pq_write_table.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                               ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+lib.pq_write_free.argtypes = [ctypes.c_void_p]
+out = []
+for blob, page, kind in pickle.load(open(sys.argv[2], "rb")):
+    if kind == "bytes":
+        offs = (ctypes.c_int64 * 2)(0, len(blob))
+        chars = ctypes.create_string_buffer(blob, max(len(blob), 1))
+        col = N.pq_write_column(b"b", N.PQ_TYPE_BYTE_ARRAY, 0, 6, 1, -1.0, ctypes.cast(offs, ctypes.c_void_p),
+                                ctypes.cast(chars, ctypes.c_void_p), None)
+        n_rows = 1
+    else:
+        vals = ctypes.create_string_buffer(blob, max(len(blob), 8))
+        col = N.pq_write_column(b"i", N.PQ_TYPE_INT64, 0, 6, 2, -1.0, ctypes.cast(vals, ctypes.c_void_p), None, None)
+        n_rows = len(blob) // 8
+    arr = (N.pq_write_column * 1)(col)
+    p = ctypes.c_void_p()
+    size = ctypes.c_uint64()
+    rc = lib.pq_write_table(ctypes.cast(arr, ctypes.c_void_p), 1, n_rows, max(n_rows, 1), page, 1, 1,
+                            ctypes.byref(p), ctypes.byref(size))
+    assert rc == 0, rc
+    out.append(ctypes.string_at(p, size.value))
+    lib.pq_write_free(p)
+pickle.dump(out, open(sys.argv[2] + ".out", "wb"))
+'''
+
+
+def test_native_zstd_writer_under_asan(tmp_path):
+    """The writer (its Zstandard encoder: matching, Huffman literals with
+    both weight forms, fitted and predefined FSE tables) compiled with
+    AddressSanitizer/UBSan on inputs of many shapes and sizes: no invalid
+    access, and every page decodes with libzstd and the oracle."""
+    import os
+    import pickle
+    import shutil
+    import subprocess
+    import sys
+    pa = pytest.importorskip("pyarrow")
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    asan = subprocess.run(["g++", "-print-file-name=libasan.so"], capture_output=True, text=True).stdout.strip()
+    ubsan = subprocess.run(["g++", "-print-file-name=libubsan.so"], capture_output=True, text=True).stdout.strip()
+    if not (os.path.isabs(asan) and os.path.exists(asan) and os.path.isabs(ubsan) and os.path.exists(ubsan)):
+        pytest.skip("no sanitizer runtime")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    so = str(tmp_path / "writer_asan.so")
+    subprocess.run(["g++", "-O1", "-g", "-std=c++17", "-shared", "-fPIC", "-fsanitize=address,undefined",
+                    "-fno-omit-frame-pointer", "-I", os.path.join(root, "include"), "-I",
+                    os.path.join(root, "paper_2602_17335_gb300", "csrc"),
+                    os.path.join(root, "paper_2602_17335_gb300", "csrc", "writer.cpp"), "-o", so, "-lpthread"],
+                   check=True)
+    rng = np.random.default_rng(6)
+    from test_oracle_pins import _zstd_inputs
+    cases = []
+    for i, x in enumerate(_zstd_inputs(np.random.default_rng(4))[:60]):
+        page = [700, 1 << 16, 1 << 20][i % 3]
+        if i % 2:
+            cases.append((x, page, "bytes"))
+        else:
+            cases.append((x[:len(x) // 8 * 8] or bytes(8), page, "int64"))
+    cases.append((bytes(rng.integers(0, 2, 400_000, dtype=np.uint8)), 1 << 20, "bytes"))
+    pk = str(tmp_path / "cases.pkl")
+    pickle.dump(cases, open(pk, "wb"))
+    env = dict(os.environ, LD_PRELOAD=asan + ":" + ubsan, ASAN_OPTIONS="detect_leaks=0",
+               UBSAN_OPTIONS="halt_on_error=1:print_stacktrace=1")
+    r = subprocess.run([sys.executable, "-c", _WRITER_FUZZ, so, pk, root], capture_output=True, text=True, env=env,
+                       timeout=900)
+    assert r.returncode == 0, r.stderr[-3000:]
+    assert "Sanitizer" not in r.stderr and "runtime error" not in r.stderr, r.stderr[-3000:]
+    files = pickle.load(open(pk + ".out", "rb"))
+    assert len(files) == len(cases)
+    for (blob, _, kind), data in zip(cases, files):
+        res = R.read_file(data)[0]
+        if kind == "bytes":
+            assert res.chars.tobytes() == blob
+        else:
+            assert res.values.tobytes() == (blob[:len(blob) // 8 * 8])
+        for _, frame, size in zstd_pages(data):
+            assert pa.Codec("zstd").decompress(frame, decompressed_size=size, asbytes=True) == Z.decompress(frame)
