@@ -310,8 +310,9 @@ void snappy_compress(const uint8_t* in, size_t n, Bytes& o) {
 
 // One Zstandard frame per page (single segment, content size in the
 // header, no checksum).  Each block of up to 128 KB of input is coded with
-// greedy LZ77 matches (4-byte hash over the whole frame so far) as
-// sequences whose codes use FSE tables fitted to the block (or an RLE
+// greedy LZ77 matches (the previous match's offset tried first, then a
+// 4-byte hash over the whole frame so far) as sequences, offsets coded as
+// repeat offsets where the history allows, whose codes use FSE tables fitted to the block (or an RLE
 // table, or the predefined ones, whichever is smaller); its literals are
 // Huffman-coded (1 or 4 streams) when that pays, else stored raw; a block without matches, or one that
 // would not shrink, is stored as a raw (or RLE) block.  Every Zstandard
@@ -626,9 +627,40 @@ bool huf_literals(const Bytes& lits, Bytes& out) {
   return true;
 }
 
+// Offset value of a match under the format's three repeat offsets (the
+// decoder's history, updated the way the decoder updates it).
+uint32_t zoffset_value(uint32_t ll, uint32_t off, uint32_t* r) {
+  uint32_t ov;
+  if (ll > 0 && off == r[0]) return 1;
+  if (off == r[1]) {
+    ov = ll > 0 ? 2 : 1;
+    std::swap(r[0], r[1]);
+    return ov;
+  }
+  if (off == r[2]) {
+    ov = ll > 0 ? 3 : 2;
+    const uint32_t t = r[2];
+    r[2] = r[1];
+    r[1] = r[0];
+    r[0] = t;
+    return ov;
+  }
+  if (ll == 0 && r[0] > 1 && off == r[0] - 1) {
+    r[2] = r[1];
+    r[1] = r[0];
+    r[0] = off;
+    return 3;
+  }
+  r[2] = r[1];
+  r[1] = r[0];
+  r[0] = off;
+  return off + 3;
+}
+
 // Compressed-block body for `seqs` and `lits`; false when it would not be
-// smaller than `raw` bytes.
-bool zstd_block_body(const std::vector<ZSeq>& seqs, const Bytes& lits, size_t raw, Bytes& body) {
+// smaller than `raw` bytes.  `rep` is the frame's repeat-offset history,
+// advanced only when the block is kept.
+bool zstd_block_body(const std::vector<ZSeq>& seqs, const Bytes& lits, size_t raw, Bytes& body, uint32_t* rep) {
   body.clear();
   const size_t n = lits.size();
   Bytes hl;
@@ -655,9 +687,10 @@ bool zstd_block_body(const std::vector<ZSeq>& seqs, const Bytes& lits, size_t ra
     nbx[k].resize(ns);
     extra[k].resize(ns);
   }
+  uint32_t r[3] = {rep[0], rep[1], rep[2]};
   for (size_t i = 0; i < ns; ++i) {
     zll_code(seqs[i].ll, &code[0][i], &nbx[0][i], &extra[0][i]);
-    const uint32_t ov = seqs[i].off + 3;
+    const uint32_t ov = zoffset_value(seqs[i].ll, seqs[i].off, r);
     code[1][i] = bit_length(ov) - 1;
     nbx[1][i] = code[1][i];
     extra[1][i] = ov - (1u << code[1][i]);
@@ -754,7 +787,11 @@ bool zstd_block_body(const std::vector<ZSeq>& seqs, const Bytes& lits, size_t ra
   }
   if (!have) return false;
   body.insert(body.end(), best.begin(), best.end());
-  return body.size() < raw;
+  if (body.size() >= raw) return false;
+  rep[0] = r[0];
+  rep[1] = r[1];
+  rep[2] = r[2];
+  return true;
 }
 
 void zstd_compress(const uint8_t* in, size_t n, Bytes& o) {
@@ -791,6 +828,8 @@ void zstd_compress(const uint8_t* in, size_t n, Bytes& o) {
   };
   std::vector<ZSeq> seqs;
   Bytes lits, body;
+  uint32_t rep[3] = {1, 4, 8};
+  size_t last_off = 0;
   const size_t kBlock = 128 * 1024;
   for (size_t b0 = 0; b0 < n; b0 += kBlock) {
     const size_t b1 = std::min(n, b0 + kBlock);
@@ -800,9 +839,13 @@ void zstd_compress(const uint8_t* in, size_t n, Bytes& o) {
     size_t i = b0, lit = b0;
     while (i + 4 <= b1) {
       const uint32_t h = h4(i);
-      const int64_t cand = table[h];
+      int64_t cand = table[h];
       table[h] = static_cast<int64_t>(i);
+      // the previous match's offset first: repeat offsets code cheaply
+      if (last_off && i >= last_off && memcmp(in + i - last_off, in + i, 4) == 0)
+        cand = static_cast<int64_t>(i - last_off);
       if (cand >= 0 && memcmp(in + cand, in + i, 4) == 0) {
+        last_off = i - static_cast<size_t>(cand);
         size_t len = 4;
         while (i + len < b1 && in[cand + len] == in[i + len]) ++len;
         seqs.push_back({static_cast<uint32_t>(i - lit), static_cast<uint32_t>(i - cand), static_cast<uint32_t>(len)});
@@ -821,7 +864,7 @@ void zstd_compress(const uint8_t* in, size_t n, Bytes& o) {
     if (same && raw > 1) {
       block_header(raw, 1, last);
       o.push_back(in[b0]);
-    } else if (!seqs.empty() && zstd_block_body(seqs, lits, raw, body)) {
+    } else if (!seqs.empty() && zstd_block_body(seqs, lits, raw, body, rep)) {
       block_header(body.size(), 2, last);
       o.insert(o.end(), body.begin(), body.end());
     } else {
