@@ -309,14 +309,15 @@ void snappy_compress(const uint8_t* in, size_t n, Bytes& o) {
 // ------------------------------------------------------------------ Zstandard compressor
 
 // One Zstandard frame per page (single segment, content size in the
-// header, no checksum).  Each block of up to 128 KB of input is coded with
-// greedy LZ77 matches (the previous match's offset tried first, then a
-// 4-byte hash over the whole frame so far) as sequences, offsets coded as
-// repeat offsets where the history allows, whose codes use FSE tables fitted to the block (or an RLE
-// table, or the predefined ones, whichever is smaller); its literals are
-// Huffman-coded (1 or 4 streams) when that pays, else stored raw; a block without matches, or one that
-// would not shrink, is stored as a raw (or RLE) block.  Every Zstandard
-// decoder reads the result.
+// header, no checksum).  Each block of up to 128 KB of input is coded as
+// sequences from greedy LZ77 matches: the previous match's offset is tried
+// first, then a 4-byte hash over the whole frame so far; offsets are coded
+// as repeat offsets where the history allows.  The sequence codes use FSE
+// tables fitted to the block (an RLE table for a single code, or the
+// predefined tables, whichever is smaller).  Literals are Huffman-coded (1
+// or 4 streams) when that pays, else stored raw.  A block without matches,
+// or one that would not shrink, is stored as a raw (or RLE) block.  Every
+// Zstandard decoder reads the result.
 
 struct ZBitW {  // little-endian bit writer
   Bytes& o;
