@@ -458,3 +458,27 @@ def test_native_zstd_writer_under_asan(tmp_path):
             assert res.values.tobytes() == (blob[:len(blob) // 8 * 8])
         for _, frame, size in zstd_pages(data):
             assert pa.Codec("zstd").decompress(frame, decompressed_size=size, asbytes=True) == Z.decompress(frame)
+
+
+@pytest.mark.parametrize("writer", ["oracle", "native"])
+def test_pyarrow_reads_chosen_encodings_with_codecs(writer):
+    """Files whose chunks carry their chosen encodings (every valid encoding
+    of each type can win) under each codec, V1 and V2 pages: pyarrow reads
+    the same values."""
+    pq = pytest.importorskip("pyarrow.parquet")
+    _, write_table = _native()
+    tabs = [synth.config2_table(6000, 2500, string_pool_size=300, zipf_k=500), synth.v2_encodings_table(6000, 2500)]
+    for tab in tabs:
+        for codec, version in (("UNCOMPRESSED", 2), ("SNAPPY", 1), ("ZSTD", 2)):
+            spec = synth.TableSpec(2500, 2048, [synth.ColumnSpec("AUTO", codec, version) for _ in tab.columns])
+            data = W.write_file(tab, spec) if writer == "oracle" else bytes(write_table(tab, spec))
+            t = pq.read_table(io.BytesIO(data))
+            for i, col in enumerate(tab.columns):
+                got = t.column(i).to_pylist()
+                if col.ptype == "BYTE_ARRAY":
+                    rows = _string_rows(col)
+                    exp = rows if col.valid is None else [x if v else None for x, v in zip(rows, col.valid)]
+                else:
+                    v = np.asarray(col.values).tolist()
+                    exp = v if col.valid is None else [x if m else None for x, m in zip(v, col.valid)]
+                assert got == exp, (writer, codec, version, col.name)
