@@ -438,99 +438,137 @@ PQ_HD inline void z_ml(uint32_t code, uint32_t* base, int* bits) {
   *bits = N[code - 32];
 }
 
+// Sequence decoding in steps, so that a caller can decode a batch of
+// sequences and execute them separately: z_seq_begin parses the section
+// header and tables and reads the initial states; z_seq_next decodes one
+// sequence (its literal length, offset and match length, the offset resolved
+// through the repeat-offset history); z_exec copies one sequence's literals
+// and match into the output.
+struct ZSeqState {
+  ZBack b;
+  uint32_t sl, so, sm;
+  uint32_t nseq, done;
+};
+
+PQ_HD inline int z_seq_begin(const uint8_t* p, uint32_t len, ZState* z, ZSeqState* s) {
+  if (len == 0) return ZE_SEQ;
+  uint32_t q;
+  const uint32_t b0 = p[0];
+  s->done = 0;
+  if (b0 == 0) {
+    if (len != 1) return ZE_SEQ;
+    s->nseq = 0;
+    return ZE_OK;
+  } else if (b0 < 128) {
+    s->nseq = b0;
+    q = 1;
+  } else if (b0 < 255) {
+    if (len < 2) return ZE_SEQ;
+    s->nseq = ((b0 - 128) << 8) + p[1];
+    q = 2;
+  } else {
+    if (len < 3) return ZE_SEQ;
+    s->nseq = p[1] + (static_cast<uint32_t>(p[2]) << 8) + 0x7F00;
+    q = 3;
+  }
+  if (q >= len) return ZE_SEQ;
+  const uint32_t modes = p[q++];
+  if (modes & 3) return ZE_SEQ;
+  const int ms[3] = {static_cast<int>(modes >> 6), static_cast<int>((modes >> 4) & 3),
+                     static_cast<int>((modes >> 2) & 3)};
+  for (int which = 0; which < 3; ++which) {
+    uint32_t u;
+    const int e = z_table(p + q, len - q, ms[which], which, z, &u);
+    if (e) return e;
+    q += u;
+  }
+  if (!zb_init(s->b, p + q, len - q)) return ZE_SEQ;
+  s->sl = zb_read(s->b, z->ll_al);
+  s->so = zb_read(s->b, z->of_al);
+  s->sm = zb_read(s->b, z->ml_al);
+  return ZE_OK;
+}
+
+PQ_HD inline int z_seq_next(ZState* z, ZSeqState* s, uint32_t* ll_out, uint32_t* off_out, uint32_t* ml_out) {
+  const uint32_t of_code = z->of[s->so].sym, ml_code = z->ml[s->sm].sym, ll_code = z->ll[s->sl].sym;
+  if (of_code > 31 || ll_code > 35 || ml_code > 52) return ZE_SEQ;
+  const uint32_t ov = (1u << of_code) + zb_read(s->b, static_cast<int>(of_code));
+  uint32_t mbase, lbase;
+  int mbits, lbits;
+  z_ml(ml_code, &mbase, &mbits);
+  z_ll(ll_code, &lbase, &lbits);
+  const uint32_t ml = mbase + zb_read(s->b, mbits);
+  const uint32_t ll = lbase + zb_read(s->b, lbits);
+  if (++s->done < s->nseq) {
+    s->sl = z->ll[s->sl].base + zb_read(s->b, z->ll[s->sl].nbits);
+    s->sm = z->ml[s->sm].base + zb_read(s->b, z->ml[s->sm].nbits);
+    s->so = z->of[s->so].base + zb_read(s->b, z->of[s->so].nbits);
+  }
+  uint32_t off;
+  if (ov > 3) {
+    off = ov - 3;
+    z->rep[2] = z->rep[1];
+    z->rep[1] = z->rep[0];
+    z->rep[0] = off;
+  } else {
+    const uint32_t idx = ll > 0 ? ov - 1 : ov;  // with no literals the repeat index shifts by one
+    if (idx == 0) {
+      off = z->rep[0];
+    } else if (idx == 1) {
+      off = z->rep[1];
+      z->rep[1] = z->rep[0];
+      z->rep[0] = off;
+    } else if (idx == 2) {
+      off = z->rep[2];
+      z->rep[2] = z->rep[1];
+      z->rep[1] = z->rep[0];
+      z->rep[0] = off;
+    } else {
+      off = z->rep[0] - 1;
+      z->rep[2] = z->rep[1];
+      z->rep[1] = z->rep[0];
+      z->rep[0] = off;
+    }
+  }
+  *ll_out = ll;
+  *off_out = off;
+  *ml_out = ml;
+  return ZE_OK;
+}
+
+// One sequence into dst: ll literals from the block's literals at *r (which
+// end at lit_end), then ml bytes from `off` back (byte by byte: a match may
+// overlap its own output).  The frame's output starts at out0.
+PQ_HD inline int z_exec(uint8_t* dst, uint64_t* w, uint64_t* r, uint64_t lit_end, uint64_t out0, uint32_t ll,
+                        uint32_t off, uint32_t ml) {
+  if (*r + ll > lit_end) return ZE_SEQ;
+  for (uint32_t k = 0; k < ll; ++k) dst[*w + k] = dst[*r + k];
+  *w += ll;
+  *r += ll;
+  if (off == 0 || off > *w - out0) return ZE_OFFSET;
+  if (*w + ml > *r) return ZE_SIZE;  // the output would run into unread literals: the page is too small
+  for (uint32_t k = 0; k < ml; ++k) dst[*w + k] = dst[*w - off + k];
+  *w += ml;
+  return ZE_OK;
+}
+
 // Sequences section at p[0, len), executed into dst (output so far ends at
 // *out_pos; the block's literals at dst[lit0, lit0 + nlit)).
 PQ_HD inline int z_sequences(const uint8_t* p, uint32_t len, ZState* z, uint8_t* dst, uint64_t* out_pos,
                              uint64_t out0, uint64_t lit0, uint32_t nlit) {
-  if (len == 0) return ZE_SEQ;
-  uint32_t nseq, q;
-  const uint32_t b0 = p[0];
-  if (b0 == 0) {
-    if (len != 1) return ZE_SEQ;
-    nseq = 0;
-    q = 1;
-  } else if (b0 < 128) {
-    nseq = b0;
-    q = 1;
-  } else if (b0 < 255) {
-    if (len < 2) return ZE_SEQ;
-    nseq = ((b0 - 128) << 8) + p[1];
-    q = 2;
-  } else {
-    if (len < 3) return ZE_SEQ;
-    nseq = p[1] + (static_cast<uint32_t>(p[2]) << 8) + 0x7F00;
-    q = 3;
-  }
+  ZSeqState s;
+  int e = z_seq_begin(p, len, z, &s);
+  if (e) return e;
   uint64_t w = *out_pos, r = lit0;
   const uint64_t lit_end = lit0 + nlit;
-  if (nseq) {
-    if (q >= len) return ZE_SEQ;
-    const uint32_t modes = p[q++];
-    if (modes & 3) return ZE_SEQ;
-    const int ms[3] = {static_cast<int>(modes >> 6), static_cast<int>((modes >> 4) & 3),
-                       static_cast<int>((modes >> 2) & 3)};
-    for (int which = 0; which < 3; ++which) {
-      uint32_t u;
-      const int e = z_table(p + q, len - q, ms[which], which, z, &u);
-      if (e) return e;
-      q += u;
-    }
-    ZBack b;
-    if (!zb_init(b, p + q, len - q)) return ZE_SEQ;
-    uint32_t sl = zb_read(b, z->ll_al), so = zb_read(b, z->of_al), sm = zb_read(b, z->ml_al);
-    for (uint32_t i = 0; i < nseq; ++i) {
-      const uint32_t of_code = z->of[so].sym, ml_code = z->ml[sm].sym, ll_code = z->ll[sl].sym;
-      if (of_code > 31 || ll_code > 35 || ml_code > 52) return ZE_SEQ;
-      const uint32_t ov = (1u << of_code) + zb_read(b, static_cast<int>(of_code));
-      uint32_t mbase, lbase;
-      int mbits, lbits;
-      z_ml(ml_code, &mbase, &mbits);
-      z_ll(ll_code, &lbase, &lbits);
-      const uint32_t ml = mbase + zb_read(b, mbits);
-      const uint32_t ll = lbase + zb_read(b, lbits);
-      if (i + 1 < nseq) {
-        sl = z->ll[sl].base + zb_read(b, z->ll[sl].nbits);
-        sm = z->ml[sm].base + zb_read(b, z->ml[sm].nbits);
-        so = z->of[so].base + zb_read(b, z->of[so].nbits);
-      }
-      // literals, then the match
-      if (r + ll > lit_end) return ZE_SEQ;
-      for (uint32_t k = 0; k < ll; ++k) dst[w + k] = dst[r + k];
-      w += ll;
-      r += ll;
-      uint32_t off;
-      if (ov > 3) {
-        off = ov - 3;
-        z->rep[2] = z->rep[1];
-        z->rep[1] = z->rep[0];
-        z->rep[0] = off;
-      } else {
-        const uint32_t idx = ll > 0 ? ov - 1 : ov;
-        if (idx == 0) {
-          off = z->rep[0];
-        } else if (idx == 1) {
-          off = z->rep[1];
-          z->rep[1] = z->rep[0];
-          z->rep[0] = off;
-        } else if (idx == 2) {
-          off = z->rep[2];
-          z->rep[2] = z->rep[1];
-          z->rep[1] = z->rep[0];
-          z->rep[0] = off;
-        } else {
-          off = z->rep[0] - 1;
-          z->rep[2] = z->rep[1];
-          z->rep[1] = z->rep[0];
-          z->rep[0] = off;
-        }
-      }
-      if (off == 0 || off > w - out0) return ZE_OFFSET;
-      if (w + ml > r) return ZE_SIZE;  // the output would run into unread literals: the page is too small
-      for (uint32_t k = 0; k < ml; ++k) dst[w + k] = dst[w - off + k];
-      w += ml;
-    }
-    if (b.pos != 0) return ZE_STREAM;
+  for (uint32_t i = 0; i < s.nseq; ++i) {
+    uint32_t ll, off, ml;
+    e = z_seq_next(z, &s, &ll, &off, &ml);
+    if (e) return e;
+    e = z_exec(dst, &w, &r, lit_end, out0, ll, off, ml);
+    if (e) return e;
   }
+  if (s.nseq && s.b.pos != 0) return ZE_STREAM;
   for (; r < lit_end; ++r, ++w) dst[w] = dst[r];
   *out_pos = w;
   return ZE_OK;
