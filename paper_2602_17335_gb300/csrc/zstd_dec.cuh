@@ -303,6 +303,44 @@ PQ_HD inline uint32_t z_le(const uint8_t* p, int n) {
 // Literals of a compressed block at p[0, len), decoded to dst[lit0, lit0 +
 // *nlit) (lit0 chosen here: the tail of the output).  Returns 0 or an error;
 // *used = section bytes.
+// The Huffman streams of a literals section: 1 stream, or 4 after a jump
+// table of three 2-byte sizes, each stream decoding (n + 3) / 4 literals
+// (the last one the rest).  Independent of one another: one decoder each.
+struct ZHufStreams {
+  const uint8_t* p[4];
+  uint32_t len[4];
+  uint32_t cnt[4];
+  uint32_t out[4];  // offset of the stream's literals within the section's
+  int n;
+};
+
+PQ_HD inline int z_huf_split(const uint8_t* q, uint32_t qlen, uint32_t regen, int streams, ZHufStreams* hs) {
+  if (streams == 1) {
+    hs->n = 1;
+    hs->p[0] = q;
+    hs->len[0] = qlen;
+    hs->cnt[0] = regen;
+    hs->out[0] = 0;
+    return ZE_OK;
+  }
+  if (qlen < 6) return ZE_LIT;
+  const uint32_t s1 = z_le(q, 2), s2 = z_le(q + 2, 2), s3 = z_le(q + 4, 2);
+  if (6ull + s1 + s2 + s3 > qlen) return ZE_LIT;
+  const uint32_t per = (regen + 3) / 4;
+  if (3 * per > regen) return ZE_LIT;
+  const uint32_t lens[4] = {s1, s2, s3, qlen - 6 - s1 - s2 - s3};
+  const uint8_t* sp = q + 6;
+  hs->n = 4;
+  for (int k = 0; k < 4; ++k) {
+    hs->p[k] = sp;
+    hs->len[k] = lens[k];
+    hs->cnt[k] = k < 3 ? per : regen - 3 * per;
+    hs->out[k] = static_cast<uint32_t>(k) * per;
+    sp += lens[k];
+  }
+  return ZE_OK;
+}
+
 PQ_HD inline int z_literals(const uint8_t* p, uint32_t len, ZState* z, uint8_t* dst, uint64_t out_pos,
                             uint64_t dst_len, uint64_t* lit0, uint32_t* nlit, uint32_t* used) {
   if (len == 0) return ZE_LIT;
@@ -358,26 +396,12 @@ PQ_HD inline int z_literals(const uint8_t* p, uint32_t len, ZState* z, uint8_t* 
   }
   *lit0 = dst_len - regen;
   *nlit = regen;
-  uint8_t* o = dst + *lit0;
-  if (streams == 1) {
-    const int e = z_huf_stream(q, qlen, regen, z, o);
-    if (e) return e;
-  } else {
-    if (qlen < 6) return ZE_LIT;
-    const uint32_t s1 = z_le(q, 2), s2 = z_le(q + 2, 2), s3 = z_le(q + 4, 2);
-    if (6ull + s1 + s2 + s3 > qlen) return ZE_LIT;
-    const uint32_t per = (regen + 3) / 4;
-    if (3 * per > regen) return ZE_LIT;
-    const uint32_t lens[4] = {s1, s2, s3, qlen - 6 - s1 - s2 - s3};
-    const uint32_t cnt[4] = {per, per, per, regen - 3 * per};
-    const uint8_t* sp = q + 6;
-    uint32_t done = 0;
-    for (int k = 0; k < 4; ++k) {
-      const int e = z_huf_stream(sp, lens[k], cnt[k], z, o + done);
-      if (e) return e;
-      sp += lens[k];
-      done += cnt[k];
-    }
+  ZHufStreams hs;
+  const int e = z_huf_split(q, qlen, regen, streams, &hs);
+  if (e) return e;
+  for (int k = 0; k < hs.n; ++k) {
+    const int e2 = z_huf_stream(hs.p[k], hs.len[k], hs.cnt[k], z, dst + *lit0 + hs.out[k]);
+    if (e2) return e2;
   }
   *used = hlen + csize;
   return ZE_OK;
