@@ -87,9 +87,7 @@ def workload_name(a):
             f"{a.page_bytes // 1024} KiB pages, {a.codec.lower()}, V{a.page_version} pages")
 
 
-def make_files(a, rank):
-    """The table of this rank, written by the engine's native writer."""
-    from paper_2602_17335_gb300.tables import write_table
+def table_and_spec(a, rank):
     if getattr(a, "table", "eight") == "v2":
         tab = synth.v2_encodings_table(a.rows, a.rg_rows, file=rank)
         spec = synth.v2_encodings_spec(a.rg_rows, a.page_bytes, a.codec, a.page_version,
@@ -98,8 +96,25 @@ def make_files(a, rank):
         tab = synth.config2_table(a.rows, a.rg_rows, file=rank)
         spec = synth.config2_spec(a.rg_rows, a.page_bytes, a.codec, a.page_version,
                                   offset_index=not a.no_offset_index)
-    data = write_table(tab, spec)
-    return data
+    return tab, spec
+
+
+def make_files(a, rank):
+    """The table of this rank, written by the engine's native writer."""
+    from paper_2602_17335_gb300.tables import write_table
+    tab, spec = table_and_spec(a, rank)
+    return write_table(tab, spec)
+
+
+def make_first_row_group_with_oracle(a):
+    """Row group 0 of rank 0's table (the part the CPU sample decodes),
+    written by the CPU oracle's writer: the same chunk bytes as in the full
+    file, and the reference arm never loads the engine library."""
+    from oracle import writer as W
+    tab, spec = table_and_spec(a, 0)
+    hi = min(a.rg_rows, tab.n_rows)
+    first = synth.Table([synth.slice_column(c, 0, hi) for c in tab.columns])
+    return W.write_file(first, spec)
 
 
 # ----------------------------------------------------------------- CPU oracle sample
@@ -210,6 +225,14 @@ def oracle_sample_all_cores(data):
 # ----------------------------------------------------------------- clocks
 
 class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region, plus the
+    sample delivered just before it starts and one taken synchronously as
+    soon as it ends, so a region shorter than the sampling period still has
+    a record."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
     def __init__(self, index):
         self.index = index
         self.proc = None
@@ -221,22 +244,29 @@ class ClockSampler:
             self.out = open(os.environ.get("PQ_CLOCKS_CSV") or os.devnull, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index),
-                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--query-gpu=" + self.QUERY,
                  "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
                 text=True)
             self.lines = []
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
-            # the timed region starts once the sampler delivers samples
+            # the timed region starts once the sampler has delivered a sample
+            # (taken just after the warm-up, so the clocks are those under load)
             t0 = time.time()
             while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
                 time.sleep(0.01)
-            self.lines.clear()
+            self.n_before = len(self.lines)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
+
+    def _one_sample(self):
+        try:
+            r = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
+            return [ln.strip() for ln in r.stdout.splitlines() if ln.strip()]
+        except (OSError, subprocess.TimeoutExpired):
+            return []
 
     def _read(self):
         for line in self.proc.stdout:
@@ -246,6 +276,10 @@ class ClockSampler:
 
     def __exit__(self, *exc):
         if self.proc:
+            self.n_during = len(self.lines) - getattr(self, "n_before", 0)
+            after = self._one_sample()
+            self.lines.extend(after)
+            self.n_after = len(after)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -273,7 +307,9 @@ class ClockSampler:
                 if v.lower() in ("active", "1"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "samples_before_during_after": [getattr(self, "n_before", 0),
+                                                                    getattr(self, "n_during", 0),
+                                                                    getattr(self, "n_after", 0)]}
 
 
 # ----------------------------------------------------------------- arms
@@ -330,7 +366,7 @@ def run_reference(a, rank, world):
     """The CPU oracle on the same workload (bounded sample per step)."""
     if rank != 0:
         return
-    data = bytes(make_files(a, 0))
+    data = bytes(make_first_row_group_with_oracle(a))
     # each step a bounded sample, sized so that the whole run stays within a
     # few minutes
     per_step = max(0.3, min(20.0, 90.0 / max(1, a.steps + a.warmup)))

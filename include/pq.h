@@ -425,8 +425,7 @@ void pq_batch_free(pq_batch* b);
 
 /* ---- Allocation-free DELTA stream decode (no counterpart in the paper) ----
  *
- * Decodes one DELTA_BINARY_PACKED value stream (the Parquet encoding the
- * paper's Section 3 names for sorted integer columns) of `n_values` INT32 or
+ * Decodes one DELTA_BINARY_PACKED value stream of `n_values` INT32 or
  * INT64 values from device memory `d_stream` (`stream_len` bytes, followed
  * by at least 32 readable bytes, which are not used as data) into device
  * memory `d_values` (n_values * 4 or * 8 bytes, little-endian).  The stream

@@ -300,9 +300,6 @@ PQ_HD inline uint32_t z_le(const uint8_t* p, int n) {
   return v;
 }
 
-// Literals of a compressed block at p[0, len), decoded to dst[lit0, lit0 +
-// *nlit) (lit0 chosen here: the tail of the output).  Returns 0 or an error;
-// *used = section bytes.
 // The Huffman streams of a literals section: 1 stream, or 4 after a jump
 // table of three 2-byte sizes, each stream decoding (n + 3) / 4 literals
 // (the last one the rest).  Independent of one another: one decoder each.
@@ -341,6 +338,9 @@ PQ_HD inline int z_huf_split(const uint8_t* q, uint32_t qlen, uint32_t regen, in
   return ZE_OK;
 }
 
+// Literals of a compressed block at p[0, len), decoded to dst[lit0, lit0 +
+// *nlit) (lit0 chosen here: the tail of the output).  Returns 0 or an error;
+// *used = section bytes.
 PQ_HD inline int z_literals(const uint8_t* p, uint32_t len, ZState* z, uint8_t* dst, uint64_t out_pos,
                             uint64_t dst_len, uint64_t* lit0, uint32_t* nlit, uint32_t* used) {
   if (len == 0) return ZE_LIT;

@@ -1,13 +1,16 @@
-"""pq_delta_decode_static (allocation-free DELTA stream decode) against the
-DELTA path of pq_scan_columns, through the C ABI, bit for bit.
+"""pq_delta_decode_static (allocation-free DELTA stream decode) through the
+C ABI, bit for bit against the CPU oracle's decoding of the same stream
+bytes (oracle.delta.decode) and against the DELTA path of pq_scan_columns.
 
 The file is named to be collected last: it must pass alone in a fresh
 process and after every other GPU test.  Each stream is decoded twice in a
-row into two buffers; both must equal the scan's column."""
+row into two buffers; both must equal the oracle's values and the scan's
+column."""
 import numpy as np
 import pytest
 
 import synth
+from oracle import delta as D
 from oracle import reader as R
 from oracle import writer as W
 
@@ -63,12 +66,17 @@ def _decode_twice_and_compare(eng, cols):
         for g in got:
             st = N.pq_delta_decode_static(eng.ctx, s.data_ptr(), len(stream), ptype, nv, g.data_ptr())
             assert st == N.PQ_OK, N.pq_last_error(eng.ctx)
+        bits = 32 if ptype == N.PQ_TYPE_INT32 else 64
+        vals, end = D.decode(stream, 0, len(stream), bits)
+        assert len(vals) == nv and end <= len(stream)
+        expect = np.array(vals, dtype=np.int32 if bits == 32 else np.int64)
         for g in got:
+            assert np.array_equal(g.cpu().numpy(), expect), f"column {col}: static decode differs from the oracle"
             assert torch.equal(g, ref), f"column {col}: static decode differs from the scan"
 
 
 def test_static_decode_matches_scan_many_regions(eng):
-    """Long streams: the block chain spans many 16 KB regions."""
+    """Long streams: the block chain spans many 8 KB regions."""
     rng = np.random.default_rng(11)
     n = 1_000_001
     i64 = np.iinfo(np.int64)
