@@ -450,19 +450,31 @@ def run_ours(a, rank, world, local_rank):
     N.pq_free_index(idx)
     index_launches = 3 if iinfo.used_offset_index else 2
 
+    host_s = [0.0] * 6  # index, plan, scan enqueue, wait, free plan, free index (host seconds)
+
     def step():
-        ix = N.pq_index_chunks(eng.ctx, [(t.data_ptr(), t.numel()) for t in files], sh)
+        tp = [time.perf_counter()]
+        ix = N.pq_index_chunks(eng.ctx, [(f.data_ptr(), f.numel()) for f in files], sh)
+        tp.append(time.perf_counter())
         pl, _ = N.pq_plan_scan(eng.ctx, ix, None, 0, -1, base_flags)
+        tp.append(time.perf_counter())
         N.pq_scan_columns(eng.ctx, pl, [o.desc() for o in outs], sh)
+        tp.append(time.perf_counter())
         st, _ = N.pq_scan_wait(eng.ctx, pl, len(outs), sh)
+        tp.append(time.perf_counter())
         N.pq_free_plan(pl)
+        tp.append(time.perf_counter())
         N.pq_free_index(ix)
+        tp.append(time.perf_counter())
+        for i in range(6):
+            host_s[i] += tp[i + 1] - tp[i]
         if st != N.PQ_OK:
             raise N.PqError(st, N.pq_last_error(eng.ctx))
 
     for _ in range(max(a.warmup, 1)):
         step()
     torch.cuda.synchronize(dev)
+    host_s[:] = [0.0] * 6
     if world > 1:
         torch.distributed.barrier()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -577,7 +589,9 @@ def run_ours(a, rank, world, local_rank):
                        "l2": "inputs larger than L2 (files %.2f GB, outputs %.2f GB per step)" % (
                            data.nbytes / 1e9, decoded / 1e9),
                        "step": "index + plan + scan + wait"},
-            "roofline": roofline, "stages_ms": stages, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
+            "roofline": roofline, "stages_ms": stages,
+            "step_host_ms": dict(zip(("index", "plan", "scan_enqueue", "wait", "free_plan", "free_index"),
+                                     (1e3 * x / a.steps for x in host_s))), "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
             "cpu_context_pyarrow": ctx_pa, "e2e": e2e,
             "gpu_launches": a.steps * (index_launches + pinfo.launches_per_scan),
             "clocks": clk.summary(),

@@ -1283,7 +1283,10 @@ __device__ bool walk_delta(WalkSmem& sm, const uint8_t* sb, uint32_t slen, int t
         if (fast_layout && k < full_end) {
           // fast steps: size = 5 + 4 * (sum of the 4 width bytes), all in registers
           uint32_t o = static_cast<uint32_t>(pos - c.w0);
-          const uint32_t lim = c.n0 - 48;
+          // near the stream's end the window may hold fewer than 48 bytes:
+          // then no fast step (lim would wrap around)
+          const bool roomy = c.n0 >= 48u;
+          const uint32_t lim = roomy ? c.n0 - 48 : 0u;
           const uint32_t wb = static_cast<uint32_t>(c.w0);
           const uint32_t* w32 = reinterpret_cast<const uint32_t*>(c.b0);
           uint32_t left = static_cast<uint32_t>((full_end - k) / d.block);
@@ -1294,13 +1297,13 @@ __device__ bool walk_delta(WalkSmem& sm, const uint8_t* sb, uint32_t slen, int t
           // software-pipelined: the next block's header words are loaded
           // before this block's position is stored
           uint32_t x0 = 0, x1 = 0, x2 = 0;
-          if (o <= lim) {
+          if (roomy && o <= lim) {
             const uint32_t i = o >> 2;
             x0 = w32[i];
             x1 = w32[i + 1];
             x2 = w32[i + 2];
           }
-          while (done < left && o <= lim) {
+          while (done < left && roomy && o <= lim) {
             const uint32_t sh = (o & 3u) << 3;
             const uint32_t lo = __funnelshift_r(x0, x1, sh);
             const uint32_t hi = __funnelshift_r(x1, x2, sh);
