@@ -728,6 +728,7 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
   plan->n_rows = n_rows;
   const bool plain = (flags & PQ_SCAN_PLAIN) != 0;
   plan->tuning = ctx->tuning;
+  plan->staged_expand = !env_flag("PQ_NO_STAGED_EXPAND");
   const int64_t item_rows_max = plan->tuning.item_rows;
   uint64_t scratch = 0;
   uint64_t tc_pool = 0;               // DELTA_BYTE_ARRAY pool bytes
@@ -822,6 +823,11 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
           plan->read_bytes += static_cast<uint64_t>(dp.header_len) + static_cast<uint64_t>(dp.compressed);
         }
       }
+      if (dict >= 0) {
+        const int64_t dn = idx->pages[cd.dict_page].num_values;
+        cw.max_dict_n = std::max(cw.max_dict_n, dn);
+        if (cd.ptype != pqi::T_BYTE_ARRAY) cw.max_dict_bytes = std::max<int64_t>(cw.max_dict_bytes, dn * cd.width);
+      }
       for (uint32_t k = 0; k < cd.page_count; ++k) {
         const uint32_t pid = cd.page_begin + k;
         const auto& pg = idx->pages[pid];
@@ -902,6 +908,7 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
           plan->tc_jobs.push_back(j);
         }
         pp.item_begin = static_cast<uint32_t>(plan->n_items);
+        if (eff == pqi::ENC_RLE_DICT || eff == pqi::ENC_PLAIN_DICT) cw.dict_pages++;
         const bool plain_fixed = eff == pqi::ENC_PLAIN && cd.ptype != pqi::T_BYTE_ARRAY;
         if (!plain_fixed || cd.max_def) cw.copy_only = false;
         const bool needs_walk = cd.max_def || !plain_fixed;
@@ -1213,6 +1220,32 @@ static void enqueue_transcode(pq_plan* plan, int begin, int n, const pqi::Decode
                         plan->tc_pool_bytes, plan->d_counter, a.st, s);
 }
 
+// Expansion of one output column: copies (REQUIRED PLAIN fixed width), the
+// staged dictionary expand (REQUIRED fixed width with dictionary pages), or
+// the general warp decode.
+static void launch_column_expand(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, cudaStream_t s) {
+  pq_ctx* ctx = plan->ctx;
+  const auto& cw = plan->colwork[oc];
+  const auto& col = plan->outcols[oc];
+  const int ib = static_cast<int>(col.item_begin), n = static_cast<int>(col.item_count);
+  if (cw.copy_only) {
+    pqi::launch_copy_items(a, ib, n, static_cast<int>(oc), ctx->n_sms, plan->tuning.expand_ctas_per_sm, s);
+    return;
+  }
+  if (plan->staged_expand && !col.optional && col.ptype != pqi::T_BYTE_ARRAY && cw.dict_pages > 0) {
+    int bw = 0;
+    while (bw < 32 && (int64_t(1) << bw) < cw.max_dict_n) ++bw;
+    const uint32_t stage = pqi::dict_expand_stage_bytes(plan->tuning.item_rows, bw);
+    uint32_t dict_cap = static_cast<uint32_t>((cw.max_dict_bytes + 15) & ~int64_t(15));
+    if (cw.max_dict_bytes > (int64_t(1) << 30) || !pqi::dict_expand_fits(stage, dict_cap)) dict_cap = 0;
+    if (pqi::dict_expand_fits(stage, dict_cap)) {
+      pqi::launch_dict_expand(a, ib, n, static_cast<int>(oc), ctx->n_sms, stage, dict_cap, s);
+      return;
+    }
+  }
+  pqi::launch_expand(a, ib, n, static_cast<int>(oc), ctx->n_sms, plan->tuning.expand_ctas_per_sm, s);
+}
+
 // Kernels of one output column, in order, on one stream.
 static void enqueue_column(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, bool with_dicts, cudaStream_t s) {
   pq_ctx* ctx = plan->ctx;
@@ -1228,12 +1261,7 @@ static void enqueue_column(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, b
   const auto& col = plan->outcols[oc];
   pqi::launch_walk(a, cw.walk_begin, cw.walk_n, ctx->n_sms, col.optional != 0, s);
   pqi::launch_delta_bases(a, cw.delta_begin, cw.delta_n, cw.max_regions, s);
-  if (cw.copy_only)
-    pqi::launch_copy_items(a, static_cast<int>(col.item_begin), static_cast<int>(col.item_count),
-                           static_cast<int>(oc), ctx->n_sms, plan->tuning.expand_ctas_per_sm, s);
-  else
-    pqi::launch_expand(a, static_cast<int>(col.item_begin), static_cast<int>(col.item_count), static_cast<int>(oc),
-                       ctx->n_sms, plan->tuning.expand_ctas_per_sm, s);
+  launch_column_expand(plan, oc, a, s);
   if (col.ptype == pqi::T_BYTE_ARRAY)
     pqi::launch_strings(a, static_cast<int>(oc), static_cast<int>(col.item_count), ctx->n_sms, s);
 }
@@ -1308,15 +1336,7 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
       pqi::launch_delta_bases(a, cw.delta_begin, cw.delta_n, cw.max_regions, s);
     }
     mark(4);
-    for (int oc = 0; oc < ncols; ++oc) {
-      const auto& oco = plan->outcols[oc];
-      if (plan->colwork[oc].copy_only)
-        pqi::launch_copy_items(a, static_cast<int>(oco.item_begin), static_cast<int>(oco.item_count), oc,
-                               ctx->n_sms, plan->tuning.expand_ctas_per_sm, s);
-      else
-        pqi::launch_expand(a, static_cast<int>(oco.item_begin), static_cast<int>(oco.item_count), oc, ctx->n_sms,
-                           plan->tuning.expand_ctas_per_sm, s);
-    }
+    for (int oc = 0; oc < ncols; ++oc) launch_column_expand(plan, oc, a, s);
     mark(5);
     for (int32_t sc : plan->str_cols)
       pqi::launch_strings(a, sc, static_cast<int>(plan->outcols[sc].item_count), ctx->n_sms, s);

@@ -154,6 +154,7 @@ struct pq_plan {
   cudaGraphExec_t graph = nullptr;
   cudaStream_t graph_stream = nullptr;
   bool dicts_in_graph = true;
+  bool staged_expand = true;  // the staged dictionary expand (PQ_NO_STAGED_EXPAND=1: the warp decode)
   int walk_grid = 0, expand_grid = 0;
   int launches = 0;
   // per output column: ranges into the job lists
@@ -168,6 +169,9 @@ struct pq_plan {
     int max_regions = 0;                       // most DELTA regions of one page
     int max_str_regions = 0;                   // most chain regions of one string dictionary
     bool copy_only = false;                    // every page REQUIRED PLAIN fixed-width
+    int dict_pages = 0;                        // data pages with dictionary indices
+    int64_t max_dict_n = 0;                    // most entries of one of its dictionaries
+    int64_t max_dict_bytes = 0;                // largest fixed-width dictionary (bytes)
   };
   std::vector<ColWork> colwork;
   cudaEvent_t fork = nullptr;
