@@ -97,8 +97,8 @@ void launch_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, 
 // up to `dict_cap` bytes gathered from shared memory (0: from global memory).
 uint32_t dict_expand_stage_bytes(int item_rows, int bw_est);
 bool dict_expand_fits(uint32_t stage, uint32_t dict_cap);
-void launch_dict_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, uint32_t stage, uint32_t dict_cap,
-                        cudaStream_t s);
+void launch_dict_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, int width, uint32_t stage,
+                        uint32_t dict_cap, cudaStream_t s);
 // Items of a column whose pages are all REQUIRED PLAIN fixed-width: copies.
 void launch_copy_items(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, int ctas_per_sm,
                        cudaStream_t s);

@@ -1232,14 +1232,15 @@ static void launch_column_expand(pq_plan* plan, size_t oc, const pqi::DecodeArgs
     pqi::launch_copy_items(a, ib, n, static_cast<int>(oc), ctx->n_sms, plan->tuning.expand_ctas_per_sm, s);
     return;
   }
-  if (plan->staged_expand && !col.optional && col.ptype != pqi::T_BYTE_ARRAY && cw.dict_pages > 0) {
+  if (plan->staged_expand && !col.optional && (col.width == 4 || col.width == 8) && col.ptype != pqi::T_BYTE_ARRAY &&
+      cw.dict_pages > 0) {
     int bw = 0;
     while (bw < 32 && (int64_t(1) << bw) < cw.max_dict_n) ++bw;
     const uint32_t stage = pqi::dict_expand_stage_bytes(plan->tuning.item_rows, bw);
     uint32_t dict_cap = static_cast<uint32_t>((cw.max_dict_bytes + 15) & ~int64_t(15));
     if (cw.max_dict_bytes > (int64_t(1) << 30) || !pqi::dict_expand_fits(stage, dict_cap)) dict_cap = 0;
     if (pqi::dict_expand_fits(stage, dict_cap)) {
-      pqi::launch_dict_expand(a, ib, n, static_cast<int>(oc), ctx->n_sms, stage, dict_cap, s);
+      pqi::launch_dict_expand(a, ib, n, static_cast<int>(oc), ctx->n_sms, col.width, stage, dict_cap, s);
       return;
     }
   }

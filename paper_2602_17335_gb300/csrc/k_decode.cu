@@ -30,6 +30,7 @@
 //         offset) and per-item chars totals; a scan makes item bases; the
 //         copy pass writes int64 offsets and the chars.
 #include <algorithm>
+#include <type_traits>
 
 #include "decode_job.h"
 #include "dev_util.cuh"
@@ -2571,75 +2572,126 @@ __global__ void __launch_bounds__(EXP_THREADS, 4) k_expand(DecodeArgs a, int ibe
 
 // ------------------------------------------------------------------ staged dictionary expand
 
-// REQUIRED fixed-width columns with dictionary pages.  One producer warp and
-// SX_WARPS decoding warps per thread block.  The producer claims groups of
-// SX_WARPS consecutive work items (one per decoding warp) and, for each,
-// stages the item's index bytes (from the checkpoint run header on) into
-// that warp's next free buffer with one bulk copy; each decoding warp has
-// SX_SLOTS buffers, so the copies of its next items stream in while it
-// decodes (full / empty mbarriers per buffer).  A decoding warp: lane 0
-// lists the item's runs from the staged bytes, then every lane decodes 16
-// output bytes (4 INT32 / 2 INT64 values) per step -- the index from the
-// staged bits, the value from the dictionary -- and writes them with one
-// 16-byte store.  Dictionaries of at most SX_DICT_MAX bytes are gathered from
-// a copy in shared memory: when a group belongs to another chunk, the
-// producer waits until the decoding warps have released every buffer, then
-// loads that chunk's dictionary.  Larger dictionaries are gathered from
-// global memory (L2).  Items whose runs do not fit the staged bytes or the
-// run table, and items of pages that are not dictionary encoded, take the
-// general warp decode.
+// REQUIRED fixed-width columns with dictionary pages.  A thread block claims
+// spans of SX_SPAN consecutive work items; its SX_WARPS warps take every
+// SX_WARPS-th item of the span.  Each warp stages an item's index bytes
+// (from the checkpoint run header on) into shared memory with one bulk copy,
+// issued one item ahead into the warp's other buffer, so that the next
+// item's bytes stream in while the current one is decoded; the item and
+// page fields it needs are loaded two items ahead.  Lane 0 lists the item's
+// runs from the staged bytes; every lane then decodes 16 output bytes (4
+// INT32 / 2 INT64 values) per step from one 64-bit window of the staged bits
+// and writes them with one 16-byte store.  Dictionaries of at most
+// SX_DICT_MAX bytes are gathered from a copy in shared memory, loaded once per
+// span when the span's chunk changes; larger ones from global memory (L2).
+// Items whose runs do not fit the staged bytes or the run table, and items
+// of pages that are not dictionary encoded, take the general warp decode.
 constexpr int SX_WARPS = 8;
-constexpr int SX_SLOTS = 2;
-constexpr int SX_THREADS = 32 * (SX_WARPS + 1);
+constexpr int SX_THREADS = 32 * SX_WARPS;
+constexpr int SX_SPAN = 64;
 constexpr int SX_MAXRUNS = 96;
 constexpr uint32_t SX_DICT_MAX = 48 * 1024;
 
-struct SxMeta {
-  int32_t item;    // absolute item id; -1 nothing to do; -2 end of work
-  int32_t mode;    // 1 staged, 2 general decode
-  int32_t s0;      // stream offset (after the bit-width byte) of staged byte 0
-  uint32_t bytes;  // staged bytes
-  int32_t dchunk;  // chunk whose dictionary is in shared memory while this item is decoded (-1 none)
-  int32_t pad;
-};
 struct SxWarp {
-  uint64_t full[SX_SLOTS];
-  uint64_t empty[SX_SLOTS];
-  SxMeta meta[SX_SLOTS];
+  uint64_t full[2];
   int32_t rk[SX_MAXRUNS + 1];  // dense index (page) at each run start; rk[nr] = end
   int32_t rb[SX_MAXRUNS];      // bit-packed: bit offset of the run's data in the buffer; -1: repeated
   uint32_t rv[SX_MAXRUNS];     // repeated: the value
 };
 struct SxBlock {
   uint64_t dbar;
+  int32_t span;    // the span claimed for the next round
+  int32_t dchunk;  // chunk whose dictionary is in shared memory (-1 none)
   SxWarp w[SX_WARPS];
 };
 __host__ __device__ constexpr uint32_t sx_smem_bytes(uint32_t stage, uint32_t dict_cap) {
-  return ((static_cast<uint32_t>(sizeof(SxBlock)) + 15u) & ~15u) + SX_WARPS * SX_SLOTS * (stage + 16u) + dict_cap;
+  return ((static_cast<uint32_t>(sizeof(SxBlock)) + 15u) & ~15u) + SX_WARPS * 2u * (stage + 16u) + dict_cap;
+}
+
+// What a warp knows about one of its items (lane-uniform).
+struct SxItem {
+  int32_t item;     // absolute id, -1 none
+  int32_t nrows, nn, k0, pos, run_k0, row0, pp;
+};
+struct SxPage {
+  int32_t pp;       // plan page these fields belong to (-1 none)
+  const uint8_t* sb;  // value stream (bit-width byte first)
+  uint32_t slen;
+  int32_t staged;   // dictionary indices the staged decode can take
+  int32_t dict, nonnull, page, bw, dn;
+  int64_t out_row;
+  const uint8_t* dvals;
+};
+
+__device__ __forceinline__ SxItem sx_item(const DecodeArgs& a, int item, int iend) {
+  SxItem r{-1, 0, 0, 0, 0, 0, 0, 0};
+  if (item >= 0 && item < iend) {
+    const Item& it = a.items[item];
+    r = SxItem{item, it.nrows, it.nn, it.k0, it.pos, it.run_k0, it.row0, static_cast<int32_t>(it.pp)};
+  }
+  return r;
+}
+
+__device__ __forceinline__ void sx_page(const DecodeArgs& a, int32_t ppi, SxPage* g) {
+  if (ppi == g->pp) return;
+  const PlanPage& pp = a.pps[ppi];
+  g->pp = ppi;
+  g->sb = pp.body + pp.values_off;
+  g->slen = static_cast<uint32_t>(pp.body_len - pp.values_off);
+  g->dict = pp.dict;
+  g->nonnull = pp.nonnull;
+  g->page = static_cast<int32_t>(pp.page);
+  g->out_row = pp.out_row;
+  g->staged = (pp.enc == ENC_RLE_DICT || pp.enc == ENC_PLAIN_DICT) && pp.dict >= 0 && g->slen >= 1 &&
+              pp.nonnull >= 0;
+  g->dvals = nullptr;
+  g->dn = 0;
+  g->bw = 0;
+  if (g->staged) {
+    const DictDev& dd = a.dicts[pp.dict];
+    g->dvals = dd.values;
+    g->dn = dd.n;
+    g->bw = __ldg(g->sb);
+  }
+}
+
+// Lane 0 issues the bulk copy of an item's index bytes; returns (in every
+// lane) the staged bytes, 0 when the item does not take the staged decode.
+__device__ __forceinline__ uint32_t sx_issue(const SxItem& t, const SxPage& g, uint8_t* buf, uint32_t stage,
+                                             uint64_t* bar, int32_t* s0, int lane) {
+  if (t.item < 0 || !g.staged || t.nrows <= 0 || t.nn <= 0 || static_cast<uint32_t>(t.pos) >= g.slen - 1) return 0;
+  const uint8_t* from = g.sb + 1 + t.pos;
+  const uint8_t* al = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(from) & ~uintptr_t(15));
+  // readable: the stream and the 16 bytes after it (chunk slack / scratch padding)
+  const uint64_t lim = static_cast<uint64_t>((g.sb + g.slen + 16) - al) & ~uint64_t(15);
+  const uint32_t tx = static_cast<uint32_t>(lim < stage ? lim : stage);
+  *s0 = static_cast<int32_t>(al - (g.sb + 1));
+  if (lane == 0) {
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, tx);
+    bulk_g2s(buf, al, tx, bar);
+  }
+  return tx;
 }
 
 // Decodes a staged item; false: the general decode must take it (runs past
 // the staged bytes or the run table) -- nothing has been written then.
-__device__ bool sx_decode(const DecodeArgs& a, const SxMeta& q, const uint8_t* buf, SxWarp& w, const uint8_t* sdict,
-                          int lane) {
-  const Item it = a.items[q.item];
-  const PlanPage pp = a.pps[it.pp];
-  const OutCol col = a.cols[pp.col];
-  const DictDev dd = a.dicts[pp.dict];
-  const uint8_t* sb = pp.body + pp.values_off;
-  const int pgid = static_cast<int>(pp.page);
-  const int bw = __ldg(sb);
-  const int32_t k0 = it.k0, k1 = it.k0 + it.nn;
+template <int kWidth>
+__device__ bool sx_decode(const DecodeArgs& a, const SxItem& t, const SxPage& g, int32_t s0, uint32_t bytes,
+                          const uint8_t* buf, SxWarp& w, const uint8_t* sdict, int32_t sdict_chunk,
+                          uint8_t* col_values, int lane) {
+  const int bw = g.bw;
+  const int32_t k0 = t.k0, nn = t.nn, k1 = t.k0 + t.nn;
   int nr = 0, status = 0;  // 0 ok, 1 fall back, 2 corrupt
   if (lane == 0) {
-    if (bw > 32 || dd.n <= 0 || dd.width != col.width || it.run_k0 > k0) {
+    if (bw > 32 || g.dn <= 0 || t.run_k0 > k0) {
       status = 2;
     } else {
       const uint32_t vbytes = (static_cast<uint32_t>(bw) + 7) / 8;
-      int64_t o = static_cast<int64_t>(it.pos) - q.s0;  // buffer offset of the run header
-      int32_t rk = it.run_k0;
+      int64_t o = static_cast<int64_t>(t.pos) - s0;  // buffer offset of the run header
+      int32_t rk = t.run_k0;
       while (rk < k1) {
-        if (nr == SX_MAXRUNS || o < 0 || o + 16 > q.bytes) { status = 1; break; }
+        if (nr == SX_MAXRUNS || o < 0 || o + 16 > bytes) { status = 1; break; }
         uint64_t h = 0;
         const int hl = uleb_p(buf + o, &h);
         if (!hl) { status = 2; break; }
@@ -2648,9 +2700,9 @@ __device__ bool sx_decode(const DecodeArgs& a, const SxMeta& q, const uint8_t* b
         w.rk[nr] = rk;
         if (h & 1) {
           const int64_t data = o + hl;
-          // bits of the values this item needs, plus 8 bytes of read-ahead
+          // bits of the values this item needs, plus 16 bytes of read-ahead
           const int64_t upto = (rk + static_cast<int64_t>(cnt) < k1 ? static_cast<int64_t>(cnt) : k1 - rk);
-          if (data + (upto * bw + 7) / 8 + 8 > q.bytes) { status = 1; break; }
+          if (data + (upto * bw + 7) / 8 + 16 > bytes) { status = 1; break; }
           w.rb[nr] = static_cast<int32_t>(data * 8);
           o = data + static_cast<int64_t>(h >> 1) * bw;
         } else {
@@ -2662,7 +2714,7 @@ __device__ bool sx_decode(const DecodeArgs& a, const SxMeta& q, const uint8_t* b
         }
         ++nr;
         const int64_t re = static_cast<int64_t>(rk) + static_cast<int64_t>(cnt);
-        rk = re > pp.nonnull ? pp.nonnull : static_cast<int32_t>(re);
+        rk = re > g.nonnull ? g.nonnull : static_cast<int32_t>(re);
       }
       if (status == 0 && nr == 0) status = 2;
       w.rk[nr] = k1 > rk ? k1 : rk;
@@ -2670,255 +2722,222 @@ __device__ bool sx_decode(const DecodeArgs& a, const SxMeta& q, const uint8_t* b
   }
   status = __shfl_sync(0xffffffffu, status, 0);
   if (status == 2) {
-    if (lane == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_EXPAND, 40);
+    if (lane == 0) report(a.st, DERR_CORRUPT, g.page, WHERE_EXPAND, 40);
     return true;
   }
   if (status == 1) return false;
   nr = __shfl_sync(0xffffffffu, nr, 0);
   __syncwarp();
+  using T = typename std::conditional<kWidth == 4, uint32_t, unsigned long long>::type;
+  constexpr int VPL = 16 / kWidth;  // values per lane per 16-byte store
   const uint32_t* bw32 = reinterpret_cast<const uint32_t*>(buf);
-  const uint32_t n = static_cast<uint32_t>(dd.n);
+  const uint32_t nmax = static_cast<uint32_t>(g.dn) - 1u;
   const uint32_t mask = bw >= 32 ? 0xffffffffu : ((1u << bw) - 1u);
-  const bool use_s = sdict != nullptr && q.dchunk == pp.dict;
-  const int width = col.width;
-  const int vpl = 16 / width;  // values per lane per 16-byte store
-  uint8_t* out = col.values + (pp.out_row + it.row0) * width;
-  const int32_t head = static_cast<int32_t>((reinterpret_cast<uintptr_t>(out) & 15) / width);
-  uint8_t* outa = out - head * width;  // 16-byte aligned
-  const int32_t npos = head + it.nn;
-  // the lane's current run (positions only grow): bit base relative to k0
+  const T* dsrc = reinterpret_cast<const T*>(sdict != nullptr && sdict_chunk == g.dict ? sdict : g.dvals);
+  const bool use_s = sdict != nullptr && sdict_chunk == g.dict;
+  uint8_t* out = col_values + (g.out_row + t.row0) * kWidth;
+  const int32_t head = static_cast<int32_t>((reinterpret_cast<uintptr_t>(out) & 15) / kWidth);
+  T* outa = reinterpret_cast<T*>(out) - head;  // 16-byte aligned
+  const int32_t npos = head + nn;
+  // the lane's current run (positions only grow)
   int r = 0;
-  int32_t nxt = 0, bbase = 0;
+  int32_t rend = w.rk[1], bbase = 0;  // bbase: bit of value k0 as if the run started there
   uint32_t rval = 0;
   bool rep = false;
   auto set_run = [&](int rr) {
     r = rr;
-    nxt = w.rk[rr + 1];
+    rend = w.rk[rr + 1];
     const int32_t b = w.rb[rr];
     rep = b < 0;
     rval = w.rv[rr];
     bbase = b - (w.rk[rr] - k0) * bw;
   };
   set_run(0);
-  bool bad = false;
-  for (int32_t p0 = lane * vpl; p0 < npos; p0 += 32 * vpl) {
-    uint32_t x[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      x[u] = 0;
-      const int32_t j = p0 + u - head;  // value within the item
-      if (u < vpl && j >= 0 && j < it.nn) {
-        const int32_t k = k0 + j;
-        if (k >= nxt) {
-          int rr = r + 1;
-          while (rr + 1 < nr && w.rk[rr + 1] <= k) ++rr;
-          set_run(rr);
-        }
-        uint32_t v = rval;
-        if (!rep) v = bits32(bw32, static_cast<uint64_t>(bbase + j * bw), 32) & mask;
-        bad |= v >= n;
-        x[u] = v < n ? v : 0u;
-      }
+  uint32_t over = 0;  // largest index seen (checked against the dictionary once)
+  auto one = [&](int32_t j) -> uint32_t {  // the index of value j, any run
+    const int32_t k = k0 + j;
+    if (k >= rend) {
+      int rr = r + 1;
+      while (rr + 1 < nr && w.rk[rr + 1] <= k) ++rr;
+      set_run(rr);
     }
-    const bool full = p0 >= head && p0 + vpl <= npos;
-    if (width == 4) {
-      uint32_t v[4];
-      if (use_s) {
+    uint32_t v = rval;
+    if (!rep) {
+      const uint32_t bp = static_cast<uint32_t>(bbase + j * bw);
+      v = __funnelshift_r(bw32[bp >> 5], bw32[(bp >> 5) + 1], bp & 31u) & mask;
+    }
+    return v;
+  };
+  for (int32_t p0 = lane * VPL; p0 < npos; p0 += 32 * VPL) {
+    const int32_t j0 = p0 - head;  // first value of the lane's 16 bytes
+    uint32_t x[VPL];
+    if (j0 >= 0 && j0 + VPL <= nn && k0 + j0 >= w.rk[r] && k0 + j0 + VPL <= rend) {
+      // all values in the current run
+      if (rep) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = reinterpret_cast<const uint32_t*>(sdict)[x[u]];
+        for (int u = 0; u < VPL; ++u) x[u] = rval;
       } else {
+        const uint32_t bp = static_cast<uint32_t>(bbase + j0 * bw);
+        const uint32_t* wp = bw32 + (bp >> 5);
+        const uint32_t sh = bp & 31u;
+        if (bw <= 8) {  // every value of the lane in one 32-bit window
+          const uint32_t win = __funnelshift_r(wp[0], wp[1], sh);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const uint32_t*>(dd.values) + x[u]);
-      }
-      uint32_t* o32 = reinterpret_cast<uint32_t*>(outa) + p0;
-      if (full) {
-        *reinterpret_cast<uint4*>(o32) = make_uint4(v[0], v[1], v[2], v[3]);
-      } else {
+          for (int u = 0; u < VPL; ++u) x[u] = (win >> (u * bw)) & mask;
+        } else {
+          // 64-bit windows of VPL / 2 values each (2 * bw <= 64)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int32_t j = p0 + u - head;
-          if (j >= 0 && j < it.nn) o32[u] = v[u];
+          for (int h = 0; h < VPL; h += 2) {
+            const uint32_t bq = sh + static_cast<uint32_t>(h * bw);
+            const uint32_t* wq = wp + (bq >> 5);
+            const uint32_t s2 = bq & 31u;
+            const uint32_t lo = __funnelshift_r(wq[0], wq[1], s2), hi = __funnelshift_r(wq[1], wq[2], s2);
+            x[h] = lo & mask;
+            x[h + 1] = __funnelshift_rc(lo, hi, static_cast<uint32_t>(bw)) & mask;  // (clamped: bw may be 32)
+          }
         }
       }
     } else {
-      uint64_t v[2];
-      if (use_s) {
 #pragma unroll
-        for (int u = 0; u < 2; ++u) v[u] = reinterpret_cast<const uint64_t*>(sdict)[x[u]];
-      } else {
-#pragma unroll
-        for (int u = 0; u < 2; ++u) v[u] = __ldg(reinterpret_cast<const uint64_t*>(dd.values) + x[u]);
-      }
-      uint64_t* o64 = reinterpret_cast<uint64_t*>(outa) + p0;
-      if (full) {
-        *reinterpret_cast<uint4*>(o64) = make_uint4(static_cast<uint32_t>(v[0]), static_cast<uint32_t>(v[0] >> 32),
-                                                    static_cast<uint32_t>(v[1]), static_cast<uint32_t>(v[1] >> 32));
-      } else {
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int32_t j = p0 + u - head;
-          if (j >= 0 && j < it.nn) o64[u] = v[u];
-        }
+      for (int u = 0; u < VPL; ++u) {
+        const int32_t j = j0 + u;
+        x[u] = (j >= 0 && j < nn) ? one(j) : 0u;
       }
     }
+    T v[VPL];
+#pragma unroll
+    for (int u = 0; u < VPL; ++u) {
+      over = max(over, x[u]);
+      const uint32_t xi = min(x[u], nmax);
+      v[u] = use_s ? dsrc[xi] : __ldg(dsrc + xi);
+    }
+    if (j0 >= 0 && j0 + VPL <= nn) {
+      if constexpr (kWidth == 4)
+        *reinterpret_cast<uint4*>(outa + p0) = make_uint4(v[0], v[1], v[2], v[3]);
+      else
+        *reinterpret_cast<uint4*>(outa + p0) = make_uint4(static_cast<uint32_t>(v[0]), static_cast<uint32_t>(v[0] >> 32),
+                                                          static_cast<uint32_t>(v[1]), static_cast<uint32_t>(v[1] >> 32));
+    } else {
+#pragma unroll
+      for (int u = 0; u < VPL; ++u)
+        if (j0 + u >= 0 && j0 + u < nn) outa[p0 + u] = v[u];
+    }
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_EXPAND, 41);
+  if (__any_sync(0xffffffffu, over > nmax) && lane == 0) report(a.st, DERR_CORRUPT, g.page, WHERE_EXPAND, 41);
   return true;
 }
 
-// Producer side: stage item `item` for decoding warp `c` in slot `sl`
-// (lane c of the producer warp).  Returns the chunk of its dictionary (-1
-// when it is not staged).
-__device__ __forceinline__ int sx_stage(const DecodeArgs& a, int item, int iend, SxWarp& w, int sl, uint8_t* buf,
-                                        uint32_t stage, int32_t dchunk) {
-  SxMeta m{-1, 0, 0, 0, dchunk, 0};
-  uint32_t tx = 0;
-  int chunk = -1;
-  if (item < iend) {
-    const Item it = a.items[item];
-    const PlanPage pp = a.pps[it.pp];
-    m.item = item;
-    m.mode = 2;
-    if (it.nrows <= 0 || pp.nonnull < 0) {
-      m.item = -1;
-      m.mode = 0;
-    } else if ((pp.enc == ENC_RLE_DICT || pp.enc == ENC_PLAIN_DICT) && pp.dict >= 0 && it.nn > 0) {
-      const uint8_t* sb = pp.body + pp.values_off;
-      const uint32_t slen = static_cast<uint32_t>(pp.body_len - pp.values_off);
-      const uint32_t pos = static_cast<uint32_t>(it.pos);
-      if (slen >= 1 && pos < slen - 1) {
-        const uint8_t* from = sb + 1 + pos;
-        const uint8_t* al = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(from) & ~uintptr_t(15));
-        // readable: the stream and the 16 bytes after it (chunk slack / scratch padding)
-        const uint64_t lim = static_cast<uint64_t>((sb + slen + 16) - al) & ~uint64_t(15);
-        tx = static_cast<uint32_t>(lim < stage ? lim : stage);
-        m.s0 = static_cast<int32_t>(al - (sb + 1));
-        m.bytes = tx;
-        m.mode = 1;
-        chunk = pp.dict;
-        w.meta[sl] = m;
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&w.full[sl], tx);
-        bulk_g2s(buf, al, tx, &w.full[sl]);
-        return chunk;
-      }
-    }
-  }
-  w.meta[sl] = m;
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&w.full[sl])) : "memory");
-  return chunk;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
+template <int kWidth>
 __global__ void __launch_bounds__(SX_THREADS) k_dict_expand(DecodeArgs a, int ibegin, int icount, int cidx,
                                                             uint32_t stage, uint32_t dict_cap) {
   extern __shared__ __align__(16) uint8_t sxraw[];
   SxBlock& sm = *reinterpret_cast<SxBlock*>(sxraw);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  SxWarp& w = sm.w[wid];
   uint8_t* bufs = sxraw + ((sizeof(SxBlock) + 15) & ~size_t(15));
-  auto bufp = [&](int c, int sl) { return bufs + (c * SX_SLOTS + sl) * (stage + 16); };
-  uint8_t* sdict = dict_cap ? bufs + SX_WARPS * SX_SLOTS * (stage + 16) : nullptr;
-  const int ngroups = (icount + SX_WARPS - 1) / SX_WARPS;
+  uint8_t* const buf0 = bufs + (2 * wid) * (stage + 16);
+  uint8_t* const buf1 = buf0 + (stage + 16);
+  uint8_t* sdict = dict_cap ? bufs + SX_WARPS * 2u * (stage + 16) : nullptr;
+  uint32_t* ctr = a.item_counter + EXP_COUNTER0 + cidx;
+  uint8_t* const col_values = a.cols[cidx].values;
+  const int nspans = (icount + SX_SPAN - 1) / SX_SPAN;
   const int iend = ibegin + icount;
-  if (threadIdx.x == 0) mbar_init(&sm.dbar, 1);
-  if (wid < SX_WARPS && lane < SX_SLOTS) {
-    mbar_init(&sm.w[wid].full[lane], 1);
-    mbar_init(&sm.w[wid].empty[lane], 1);
+  if (threadIdx.x == 0) {
+    mbar_init(&sm.dbar, 1);
+    sm.span = static_cast<int>(atomicAdd(ctr, 1u));
+    sm.dchunk = -1;
+  }
+  if (lane == 0) {
+    mbar_init(&w.full[0], 1);
+    mbar_init(&w.full[1], 1);
   }
   fence_mbar_init();
   __syncthreads();
-  if (wid == SX_WARPS) {
-    // producer
-    uint32_t* ctr = a.item_counter + EXP_COUNTER0 + cidx;
-    int32_t dchunk = -1;
-    uint32_t dpar = 0;
-    bool lost = false;
-    for (uint32_t n = 0;; ++n) {
-      int g = 0;
-      if (lane == 0) g = static_cast<int>(atomicAdd(ctr, 1u));
-      g = __shfl_sync(0xffffffffu, g, 0);
-      const int sl = static_cast<int>(n % SX_SLOTS);
-      const uint32_t use = n / SX_SLOTS;
-      // the buffers of this slot are free once the decoding warps released their previous use
-      if (lane < SX_WARPS && use > 0 && !lost) lost = !mbar_wait(&sm.w[lane].empty[sl], (use - 1) & 1u);
-      lost = __any_sync(0xffffffffu, lost);
-      const int item = g < ngroups ? ibegin + g * SX_WARPS + lane : iend;
-      if (sdict && g < ngroups && !lost) {
-        // the group's dictionary (its first item's chunk)
-        int want = -1;
-        if (lane == 0 && item < iend) {
-          const Item it = a.items[item];
-          const PlanPage pp = a.pps[it.pp];
-          if (it.nrows > 0 && (pp.enc == ENC_RLE_DICT || pp.enc == ENC_PLAIN_DICT)) want = pp.dict;
-        }
-        want = __shfl_sync(0xffffffffu, want, 0);
-        if (want >= 0 && want != dchunk) {
-          // every earlier item released (the other slots too), then load
-          if (lane < SX_WARPS && n > 0)
-            for (uint32_t m = n > SX_SLOTS ? n - SX_SLOTS : 0; m < n && !lost; ++m)
-              if (m % SX_SLOTS != static_cast<uint32_t>(sl) || m + SX_SLOTS <= n)
-                lost = !mbar_wait(&sm.w[lane].empty[m % SX_SLOTS], (m / SX_SLOTS) & 1u);
-          lost = __any_sync(0xffffffffu, lost);
-          const DictDev dd = a.dicts[want];
+  uint32_t par0 = 0, par1 = 0, dpar = 0;
+  SxPage pg;
+  pg.pp = -1;
+  for (;;) {
+    const int span = sm.span;
+    if (span >= nspans) break;
+    __syncthreads();  // every thread has read sm.span
+    const int first = ibegin + span * SX_SPAN;
+    const int last = first + SX_SPAN < iend ? first + SX_SPAN : iend;
+    if (threadIdx.x == 0) sm.span = static_cast<int>(atomicAdd(ctr, 1u));
+    if (sdict) {
+      // the span's dictionary: that of its first item
+      if (threadIdx.x == 0) {
+        const Item& it = a.items[first];
+        const PlanPage& pp = a.pps[it.pp];
+        const bool dict = (pp.enc == ENC_RLE_DICT || pp.enc == ENC_PLAIN_DICT) && pp.dict >= 0;
+        int want = dict ? pp.dict : -1;
+        if (want >= 0 && want != sm.dchunk) {
+          const DictDev& dd = a.dicts[want];
           const uint64_t db = ((static_cast<uint64_t>(dd.n) * dd.width) + 15) & ~uint64_t(15);
-          dchunk = -1;
-          if (!lost && db > 0 && db <= dict_cap && dd.values) {
-            if (lane == 0) {
-              fence_proxy_async_smem();
-              mbar_arrive_expect_tx(&sm.dbar, static_cast<uint32_t>(db));
-              bulk_g2s(sdict, dd.values, static_cast<uint32_t>(db), &sm.dbar);
-            }
-            const bool ok = mbar_wait(&sm.dbar, dpar);
-            dpar ^= 1u;
-            if (ok) {
-              dchunk = want;
-            } else {
-              if (lane == 0) report(a.st, DERR_TIMEOUT, -1, WHERE_EXPAND, 42);
-              mbar_wait(&sm.dbar, dpar ^ 1u);
-              lost = true;
-            }
+          if (db > 0 && db <= dict_cap && dd.values) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&sm.dbar, static_cast<uint32_t>(db));
+            bulk_g2s(sdict, dd.values, static_cast<uint32_t>(db), &sm.dbar);
+          } else {
+            want = -1;
           }
+          sm.dchunk = want >= 0 ? -2 - want : -1;  // -2 - chunk: loading
         }
       }
-      lost = __any_sync(0xffffffffu, lost);
-      if (lane < SX_WARPS) {
-        if (g >= ngroups || lost) {
-          SxMeta m{-2, 0, 0, 0, -1, 0};
-          sm.w[lane].meta[sl] = m;
-          mbar_arrive(&sm.w[lane].full[sl]);
+      __syncthreads();
+      if (sm.dchunk <= -2) {
+        const bool ok = mbar_wait(&sm.dbar, dpar);
+        dpar ^= 1u;
+        if (!ok) {
+          if (threadIdx.x == 0) report(a.st, DERR_TIMEOUT, -1, WHERE_EXPAND, 42);
+          mbar_wait(&sm.dbar, dpar ^ 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) sm.dchunk = ok ? -2 - sm.dchunk : -1;
+        __syncthreads();
+      }
+    }
+    const int32_t dchunk = sm.dchunk;
+    // this warp's items of the span: first + wid, first + wid + SX_WARPS, ...
+    int it_c = first + wid;
+    SxItem tc = sx_item(a, it_c, last);
+    SxItem tn = sx_item(a, it_c + SX_WARPS, last);
+    int32_t s0c = 0;
+    sx_page(a, tc.item >= 0 ? tc.pp : pg.pp, &pg);
+    uint32_t bc = sx_issue(tc, pg, buf0, stage, &w.full[0], &s0c, lane);
+    bool cur1 = false;  // the current item sits in buf1
+    while (tc.item >= 0) {
+      // the next item's copy, and the item after it, while this one is decoded
+      SxItem tnn = sx_item(a, it_c + 2 * SX_WARPS, last);
+      SxPage pn = pg;
+      if (tn.item >= 0) sx_page(a, tn.pp, &pn);
+      int32_t s0n = 0;
+      const uint32_t bn = sx_issue(tn, pn, cur1 ? buf0 : buf1, stage, cur1 ? &w.full[0] : &w.full[1], &s0n, lane);
+      bool done = false;
+      if (bc) {
+        uint32_t& par = cur1 ? par1 : par0;
+        const bool ok = mbar_wait(cur1 ? &w.full[1] : &w.full[0], par);
+        par ^= 1u;
+        if (!ok) {
+          if (lane == 0) report(a.st, DERR_TIMEOUT, pg.page, WHERE_EXPAND, 43);
+          mbar_wait(cur1 ? &w.full[1] : &w.full[0], par ^ 1u);
+          done = true;
         } else {
-          sx_stage(a, item, iend, sm.w[lane], sl, bufp(lane, sl), stage, dchunk);
+          done = sx_decode<kWidth>(a, tc, pg, s0c, bc, cur1 ? buf1 : buf0, w, sdict, dchunk, col_values, lane);
         }
       }
-      if (g >= ngroups || lost) break;
-    }
-    if (lost && lane == 0) report(a.st, DERR_TIMEOUT, -1, WHERE_EXPAND, 44);
-    return;
-  }
-  // decoding warps
-  SxWarp& w = sm.w[wid];
-  for (uint32_t n = 0;; ++n) {
-    const int sl = static_cast<int>(n % SX_SLOTS);
-    if (!mbar_wait(&w.full[sl], (n / SX_SLOTS) & 1u)) {
-      if (lane == 0) report(a.st, DERR_TIMEOUT, -1, WHERE_EXPAND, 43);
-      return;
-    }
-    const SxMeta m = w.meta[sl];
-    if (m.item == -2) break;
-    // (the general decode gets the buffer as its staging area, which only
-    // OPTIONAL columns use: this kernel serves REQUIRED ones)
-    uint8_t* buf = bufp(wid, sl);
-    if (m.mode == 1 && !sx_decode(a, m, buf, w, sdict, lane)) {
+      // (the general decode gets the buffer as its staging area, which only
+      // OPTIONAL columns use: this kernel serves REQUIRED ones)
+      if (!done) expand_item(a, tc.item, *reinterpret_cast<WarpSmem*>(cur1 ? buf1 : buf0), lane);
       __syncwarp();
-      expand_item(a, m.item, *reinterpret_cast<WarpSmem*>(buf), lane);
-    } else if (m.mode == 2) {
-      expand_item(a, m.item, *reinterpret_cast<WarpSmem*>(buf), lane);
+      tc = tn;
+      tn = tnn;
+      pg = pn;
+      s0c = s0n;
+      bc = bn;
+      cur1 = !cur1;
+      it_c += SX_WARPS;
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&w.empty[sl]);
+    __syncthreads();  // the span is done: the dictionary may be replaced
   }
 }
 
@@ -3501,22 +3520,29 @@ bool dict_expand_fits(uint32_t stage, uint32_t dict_cap) {
   return sx_smem_bytes(stage, dict_cap) <= 227u * 1024u && dict_cap <= SX_DICT_MAX;
 }
 
-void launch_dict_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, uint32_t stage, uint32_t dict_cap,
-                        cudaStream_t s) {
+void launch_dict_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, int width, uint32_t stage,
+                        uint32_t dict_cap, cudaStream_t s) {
   if (n <= 0) return;
   const uint32_t smem = sx_smem_bytes(stage, dict_cap);
-  static uint32_t attr = 0;
-  if (smem > attr) {
-    cudaFuncSetAttribute(k_dict_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    attr = 227 * 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_dict_expand<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_dict_expand<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
   }
   int bps = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_dict_expand, SX_THREADS, smem);
+  if (width == 4)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_dict_expand<4>, SX_THREADS, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_dict_expand<8>, SX_THREADS, smem);
   if (bps < 1) bps = 1;
-  const int groups = (n + SX_WARPS - 1) / SX_WARPS;
+  const int spans = (n + SX_SPAN - 1) / SX_SPAN;
   int blocks = n_sms * bps;
-  if (blocks > (groups + 1) / 2) blocks = (groups + 1) / 2 > 0 ? (groups + 1) / 2 : 1;
-  k_dict_expand<<<blocks, SX_THREADS, smem, s>>>(a, ibegin, n, cidx, stage, dict_cap);
+  if (blocks > spans) blocks = spans;
+  if (width == 4)
+    k_dict_expand<4><<<blocks, SX_THREADS, smem, s>>>(a, ibegin, n, cidx, stage, dict_cap);
+  else
+    k_dict_expand<8><<<blocks, SX_THREADS, smem, s>>>(a, ibegin, n, cidx, stage, dict_cap);
 }
 
 void launch_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, int ctas_per_sm, cudaStream_t s) {
