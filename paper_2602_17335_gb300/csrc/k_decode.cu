@@ -2691,10 +2691,12 @@ __device__ bool sx_decode(const DecodeArgs& a, const SxItem& t, const SxPage& g,
       int64_t o = static_cast<int64_t>(t.pos) - s0;  // buffer offset of the run header
       int32_t rk = t.run_k0;
       while (rk < k1) {
-        if (nr == SX_MAXRUNS || o < 0 || o + 16 > bytes) { status = 1; break; }
+        // (the buffer holds 16 bytes past `bytes`: a header read may look there)
+        if (nr == SX_MAXRUNS || o < 0 || o >= bytes) { status = 1; break; }
         uint64_t h = 0;
         const int hl = uleb_p(buf + o, &h);
         if (!hl) { status = 2; break; }
+        if (o + hl + ((h & 1) ? 0u : vbytes) > bytes) { status = 1; break; }
         const uint64_t cnt = (h & 1) ? (h >> 1) << 3 : h >> 1;
         if (cnt == 0) { status = 2; break; }
         w.rk[nr] = rk;
