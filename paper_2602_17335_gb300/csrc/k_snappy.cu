@@ -38,70 +38,79 @@ struct SnWarp {
   uint8_t ring[kRing];
 };
 
-// Input windows: window b holds input bytes [w[b], w[b] + n[b]).
+// Lane 0's input windows, all scalars (they stay in registers): the current
+// window (*0) and the other one (*1), swapped when the parse moves on.
+// Window offsets are input offsets modulo 2^32 (a window may start up to 15
+// bytes before the input).
 struct SnIn {
   const uint8_t* in;
   uint32_t in_len;
-  uint32_t w[2], n[2];
-  uint32_t par[2];
-  int cur;        // window being parsed
-  int pending;    // the other window has a copy in flight
+  uint8_t* b0;
+  uint8_t* b1;
+  uint64_t* m0;
+  uint64_t* m1;
+  uint32_t w0, w1, n0, n1, p0, p1;
+  uint32_t e1;  // a copy into window 1 is in flight
 };
 
-// Lane 0: start the copy of input [from, from + kWin) (16-byte aligned
-// start, at most 16 bytes past the input) into window b.
-__device__ __forceinline__ void sn_issue(SnIn& s, SnWarp& sw, int b, uint32_t from) {
+__device__ __forceinline__ void sn_swap(SnIn& s) {
+  uint8_t* tb = s.b0; s.b0 = s.b1; s.b1 = tb;
+  uint64_t* tm = s.m0; s.m0 = s.m1; s.m1 = tm;
+  uint32_t t = s.w0; s.w0 = s.w1; s.w1 = t;
+  t = s.n0; s.n0 = s.n1; s.n1 = t;
+  t = s.p0; s.p0 = s.p1; s.p1 = t;
+}
+
+// Copy of input [from, from + kWin) (16-byte aligned start, at most 16 bytes
+// past the input) into buffer `buf`.
+__device__ __forceinline__ void sn_issue(const SnIn& s, uint8_t* buf, uint64_t* bar, uint32_t from, uint32_t* w,
+                                         uint32_t* n) {
   const uintptr_t base = reinterpret_cast<uintptr_t>(s.in);
   const uintptr_t a = (base + from) & ~uintptr_t(15);
   const uintptr_t lim = (base + s.in_len + 16) & ~uintptr_t(15);
   uint32_t bytes = static_cast<uint32_t>(lim > a ? lim - a : 16);
   if (bytes > kWin) bytes = kWin;
   if (bytes < 16) bytes = 16;
-  s.w[b] = static_cast<uint32_t>(a - base);  // may wrap below 0 by up to 15: unsigned arithmetic below
-  s.n[b] = bytes;
+  *w = static_cast<uint32_t>(a - base);
+  *n = bytes;
   fence_proxy_async_smem();
-  mbar_arrive_expect_tx(&sw.bar[b], bytes);
-  bulk_g2s(sw.win[b], reinterpret_cast<const void*>(a), bytes, &sw.bar[b]);
+  mbar_arrive_expect_tx(bar, bytes);
+  bulk_g2s(buf, reinterpret_cast<const void*>(a), bytes, bar);
 }
 
-// Lane 0: make input bytes [p, p + 5) readable in the current window (or up
-// to the end of the input).  False if a copy never arrived.
-__device__ __forceinline__ bool sn_ensure(SnIn& s, SnWarp& sw, uint32_t p) {
-  const uint32_t need = p + 5 < s.in_len ? 5u : s.in_len - p;
-  if (p - s.w[s.cur] + need <= s.n[s.cur] && p - s.w[s.cur] < s.n[s.cur]) return true;
-  const int o = s.cur ^ 1;
-  if (s.pending) {
-    const bool ok = mbar_wait(&sw.bar[o], s.par[o]);
-    s.par[o] ^= 1u;
-    s.pending = 0;
+__device__ __forceinline__ void sn_prefetch(SnIn& s) {
+  const uint32_t end = s.w0 + s.n0;  // input offset just past window 0
+  if (end < s.in_len) {  // input left beyond window 0
+    sn_issue(s, s.b1, s.m1, end - 16, &s.w1, &s.n1);
+    s.e1 = 1;
+  } else {
+    s.n1 = 0;
+  }
+}
+
+// Makes input bytes [p, p + 5) readable in window 0 (bytes past the input
+// end are slack).  False if a copy never arrived.
+__device__ __forceinline__ bool sn_ensure(SnIn& s, uint32_t p) {
+  if (p - s.w0 < s.n0 && (p - s.w0 + 5 <= s.n0 || s.w0 + s.n0 >= s.in_len)) return true;
+  if (s.e1) {
+    const bool ok = mbar_wait(s.m1, s.p1);
+    s.p1 ^= 1u;
+    s.e1 = 0;
     if (!ok) return false;
-    if (p - s.w[o] < s.n[o] && p - s.w[o] + need <= s.n[o]) {
-      s.cur = o;
-      // prefetch the window after it (16 bytes of overlap for headers)
-      const uint32_t nx = s.w[o] + s.n[o] - 16;
-      if (s.w[o] + s.n[o] < s.in_len + 16 && nx < s.in_len) {
-        sn_issue(s, sw, o ^ 1, nx);
-        s.pending = 1;
-      }
+    if (p - s.w1 < s.n1 && (p - s.w1 + 5 <= s.n1 || s.w1 + s.n1 >= s.in_len)) {
+      sn_swap(s);
+      sn_prefetch(s);
       return true;
     }
   }
   // a jump past the prefetched window (a long literal): load at p
-  sn_issue(s, sw, o, p);
-  const bool ok = mbar_wait(&sw.bar[o], s.par[o]);
-  s.par[o] ^= 1u;
+  sn_issue(s, s.b1, s.m1, p, &s.w1, &s.n1);
+  const bool ok = mbar_wait(s.m1, s.p1);
+  s.p1 ^= 1u;
   if (!ok) return false;
-  s.cur = o;
-  const uint32_t nx = s.w[o] + s.n[o] - 16;
-  if (s.w[o] + s.n[o] < s.in_len + 16 && nx < s.in_len) {
-    sn_issue(s, sw, o ^ 1, nx);
-    s.pending = 1;
-  }
+  sn_swap(s);
+  sn_prefetch(s);
   return true;
-}
-
-__device__ __forceinline__ uint32_t sn_byte(const SnIn& s, const SnWarp& sw, uint32_t p) {
-  return sw.win[s.cur][p - s.w[s.cur]];
 }
 
 // `n` bytes from ring positions [from, from + n) (positions are output
@@ -113,18 +122,47 @@ __device__ __forceinline__ void ring_out(uint8_t* dst, const uint8_t* ring, uint
   const uint32_t head = head0 < n ? head0 : n;
   if (static_cast<uint32_t>(lane) < head) dst[lane] = ring[(from + lane) & RM];
   const uint32_t nv = (n - head) >> 4;
-  for (uint32_t v = lane; v < nv; v += 32) {
-    const uint32_t q = from + head + 16 * v;
-    uint32_t w4[4];
+  const uint32_t q0 = from + head;
+  if ((q0 & 15) == 0) {
+    // ring slots congruent with the destination: whole 16-byte ring words
+    for (uint32_t v = lane; v < nv; v += 32)
+      *reinterpret_cast<uint4*>(dst + head + 16 * v) = *reinterpret_cast<const uint4*>(ring + ((q0 + 16 * v) & RM));
+  } else {
+    for (uint32_t v = lane; v < nv; v += 32) {
+      const uint32_t q = q0 + 16 * v;
+      uint32_t w4[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint32_t b = q + 4 * k;
-      w4[k] = static_cast<uint32_t>(ring[b & RM]) | (static_cast<uint32_t>(ring[(b + 1) & RM]) << 8) |
-              (static_cast<uint32_t>(ring[(b + 2) & RM]) << 16) | (static_cast<uint32_t>(ring[(b + 3) & RM]) << 24);
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t b = q + 4 * k;
+        w4[k] = static_cast<uint32_t>(ring[b & RM]) | (static_cast<uint32_t>(ring[(b + 1) & RM]) << 8) |
+                (static_cast<uint32_t>(ring[(b + 2) & RM]) << 16) | (static_cast<uint32_t>(ring[(b + 3) & RM]) << 24);
+      }
+      *reinterpret_cast<uint4*>(dst + head + 16 * v) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
     }
-    *reinterpret_cast<uint4*>(dst + head + 16 * v) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
   }
   for (uint32_t i = head + (nv << 4) + lane; i < n; i += 32) dst[i] = ring[(from + i) & RM];
+}
+
+// A short literal (len <= 64) from global input to the ring: its aligned
+// 16-byte words are loaded together, then placed byte by byte.
+__device__ __forceinline__ void lit_to_ring(uint8_t* ring, uint32_t o0, const uint8_t* src, uint32_t len) {
+  constexpr uint32_t RM = kRing - 1;
+  const uint32_t sh = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 15);
+  const uint4* sv = reinterpret_cast<const uint4*>(src - sh);
+  const uint32_t nv = (sh + len + 15) >> 4;  // <= 5
+  uint4 v[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) v[k] = static_cast<uint32_t>(k) < nv ? __ldg(sv + k) : make_uint4(0, 0, 0, 0);
+  // every byte position of the five words is a constant: registers only
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const uint32_t wk[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      const uint32_t q = 16u * k + b;
+      if (q >= sh && q < sh + len) ring[(o0 + q - sh) & RM] = static_cast<uint8_t>(wk[b >> 2] >> (8 * (b & 3)));
+    }
+  }
 }
 
 __global__ void __launch_bounds__(32 * kSnappyWarps) k_snappy(const SnappyJob* __restrict__ jobs, int n_jobs,
@@ -170,17 +208,13 @@ __global__ void __launch_bounds__(32 * kSnappyWarps) k_snappy(const SnappyJob* _
       continue;
     }
     // lane 0's window state
-    SnIn sin{in, in_len, {0, 0}, {0, 0}, {par[0], par[1]}, 0, 0};
+    SnIn sin{in, in_len, sw.win[0], sw.win[1], &sw.bar[0], &sw.bar[1], 0, 0, 0, 0, par[0], par[1], 0};
     int bad = 0;
     if (lane == 0) {
-      sn_issue(sin, sw, 0, 0);
-      if (!mbar_wait(&sw.bar[0], sin.par[0])) bad = 2;
-      sin.par[0] ^= 1u;
-      const uint32_t nx = sin.w[0] + sin.n[0] - 16;
-      if (!bad && sin.w[0] + sin.n[0] < in_len + 16 && nx < in_len) {
-        sn_issue(sin, sw, 1, nx);
-        sin.pending = 1;
-      }
+      sn_issue(sin, sin.b0, sin.m0, 0, &sin.w0, &sin.n0);
+      if (!mbar_wait(sin.m0, sin.p0)) bad = 2;
+      sin.p0 ^= 1u;
+      if (!bad) sn_prefetch(sin);
     }
     uint32_t ip = static_cast<uint32_t>(pl);
     uint32_t op = 0;
@@ -191,21 +225,24 @@ __global__ void __launch_bounds__(32 * kSnappyWarps) k_snappy(const SnappyJob* _
       if (lane == 0) {
         uint32_t p = ip, o = op, bo = 0;
         for (int e = 0; e < 32 && p < in_len; ++e) {
-          if (!sn_ensure(sin, sw, p)) { bad = 2; break; }
-          const uint32_t tag = sn_byte(sin, sw, p++);
+          if (!sn_ensure(sin, p)) { bad = 2; break; }
+          // the tag and the 4 bytes after it (slack past the input end is never used)
+          const uint8_t* q = sin.b0 + (p - sin.w0);
+          const uint32_t tag = q[0], x1 = q[1], x2 = q[2], x3 = q[3], x4 = q[4];
+          ++p;
           uint32_t kind = tag & 3, len, arg;
           if (kind == 0) {
-            uint32_t l = tag >> 2;
+            const uint32_t l = tag >> 2;
             if (l < 60) {
               len = l + 1;
             } else {
-              uint32_t nb = l - 59;
+              const uint32_t nb = l - 59;
               if (nb > in_len - p) { bad = 1; break; }
-              uint32_t v = 0;
-              for (uint32_t b = 0; b < nb; ++b) v |= sn_byte(sin, sw, p + b) << (8 * b);
+              const uint32_t v = x1 | (x2 << 8) | (x3 << 16) | (x4 << 24);
+              const uint32_t vm = nb == 4 ? v : (v & ((1u << (8 * nb)) - 1u));
               p += nb;
-              if (v == 0xffffffffu) { bad = 1; break; }
-              len = v + 1;
+              if (vm == 0xffffffffu) { bad = 1; break; }
+              len = vm + 1;
             }
             if (len > in_len - p) { bad = 1; break; }
             arg = p;
@@ -213,18 +250,17 @@ __global__ void __launch_bounds__(32 * kSnappyWarps) k_snappy(const SnappyJob* _
           } else if (kind == 1) {
             if (p >= in_len) { bad = 1; break; }
             len = 4 + ((tag >> 2) & 7);
-            arg = ((tag >> 5) << 8) | sn_byte(sin, sw, p);
+            arg = ((tag >> 5) << 8) | x1;
             p += 1;
           } else if (kind == 2) {
             if (2 > in_len - p) { bad = 1; break; }
             len = (tag >> 2) + 1;
-            arg = sn_byte(sin, sw, p) | (sn_byte(sin, sw, p + 1) << 8);
+            arg = x1 | (x2 << 8);
             p += 2;
           } else {
             if (4 > in_len - p) { bad = 1; break; }
             len = (tag >> 2) + 1;
-            arg = sn_byte(sin, sw, p) | (sn_byte(sin, sw, p + 1) << 8) | (sn_byte(sin, sw, p + 2) << 16) |
-                  (sn_byte(sin, sw, p + 3) << 24);
+            arg = x1 | (x2 << 8) | (x3 << 16) | (x4 << 24);
             p += 4;
           }
           if (len > out_len - o || (kind != 0 && (arg == 0 || arg > o))) { bad = 1; break; }
@@ -271,12 +307,22 @@ __global__ void __launch_bounds__(32 * kSnappyWarps) k_snappy(const SnappyJob* _
         return pos >= rlo ? ring[pos & RM] : ld_src<false>(out + pos);
       };
       if (indep) {
-        if (kind == 0) {
-          // literal bytes from the input (global; it sits in L2)
+        if (kind == 0 && len <= 64) {
+          lit_to_ring(ring, o0, in + arg, len);  // the input sits in L2 (its window was just copied)
+        } else if (kind == 0) {
           for (uint32_t i = 0; i < len; ++i) ring[(o0 + i) & RM] = __ldg(in + arg + i);
         } else {
           const uint32_t first = o0 - arg;
-          for (uint32_t i = 0; i < len; ++i) ring[(o0 + i) & RM] = src_byte(first + i);
+          uint32_t i = 0;
+          for (; i + 4 <= len; i += 4) {  // four independent reads in flight
+            const uint8_t c0 = src_byte(first + i), c1 = src_byte(first + i + 1), c2 = src_byte(first + i + 2),
+                          c3 = src_byte(first + i + 3);
+            ring[(o0 + i) & RM] = c0;
+            ring[(o0 + i + 1) & RM] = c1;
+            ring[(o0 + i + 2) & RM] = c2;
+            ring[(o0 + i + 3) & RM] = c3;
+          }
+          for (; i < len; ++i) ring[(o0 + i) & RM] = src_byte(first + i);
         }
       }
       __syncwarp();
@@ -312,15 +358,18 @@ __global__ void __launch_bounds__(32 * kSnappyWarps) k_snappy(const SnappyJob* _
     }
     if (lane == 0) {
       // settle the window copy still in flight before the buffers are reused
-      if (sin.pending) {
-        mbar_wait(&sw.bar[sin.cur ^ 1], sin.par[sin.cur ^ 1]);
-        sin.par[sin.cur ^ 1] ^= 1u;
+      if (sin.e1) {
+        mbar_wait(sin.m1, sin.p1);
+        sin.p1 ^= 1u;
+        sin.e1 = 0;
       }
       if (bad == 2) report(st, DERR_TIMEOUT, jb.page, WHERE_SNAPPY, 5);
       else if (bad || op != out_len || ip != in_len) report(st, DERR_CORRUPT, jb.page, WHERE_SNAPPY, 4);
     }
-    par[0] = __shfl_sync(0xffffffffu, sin.par[0], 0);
-    par[1] = __shfl_sync(0xffffffffu, sin.par[1], 0);
+    // carry the physical buffers' parities to the next page
+    const bool sw0 = sin.b0 == sw.win[0];
+    par[0] = __shfl_sync(0xffffffffu, sw0 ? sin.p0 : sin.p1, 0);
+    par[1] = __shfl_sync(0xffffffffu, sw0 ? sin.p1 : sin.p0, 0);
     __syncwarp();
   }
 }
