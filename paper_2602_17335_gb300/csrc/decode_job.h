@@ -115,7 +115,8 @@ void launch_copy_small(void* dst, const void* src, uint32_t bytes, cudaStream_t 
 void launch_make_items(const DecodeArgs& a, int n_pp, cudaStream_t s);
 int expand_blocks_per_sm();
 int walk_blocks_per_sm();
-void launch_snappy(const SnappyJob* jobs, int n_jobs, int n_sms, DevStatus* st, cudaStream_t s);
+// coop: one block of 8 warps per page (large pages), else one warp per page
+void launch_snappy(const SnappyJob* jobs, int n_jobs, int n_sms, DevStatus* st, cudaStream_t s, bool coop);
 void launch_index_walk(const ChunkDev* chunks, int n_chunks, PageDev* pages, uint32_t* counts, int mode,
                        DevStatus* st, cudaStream_t s);
 void launch_gather16(const uint8_t* const* ptr, const int32_t* len, int n, uint8_t* out, cudaStream_t s);

@@ -865,6 +865,8 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
           sj.page = static_cast<int32_t>(pid);
           data_job_off.push_back(static_cast<int64_t>(scratch));
           plan->snappy_data.push_back(sj);
+          cw.snap_data_max = std::max<uint32_t>(cw.snap_data_max, sj.src_len);
+          plan->snap_data_max = std::max<uint32_t>(plan->snap_data_max, sj.src_len);
           pp.body = reinterpret_cast<const uint8_t*>(static_cast<uintptr_t>(scratch));  // rebased below
           pp.pad = 1;  // body is a scratch offset until rebased
           scratch += (static_cast<uint64_t>(pg.uncompressed) + 32 + 15) & ~uint64_t(15);
@@ -1220,6 +1222,11 @@ static void enqueue_transcode(pq_plan* plan, int begin, int n, const pqi::Decode
                         plan->tc_pool_bytes, plan->d_counter, a.st, s);
 }
 
+// Compressed data pages of at least this many bytes are decompressed by a
+// block of 8 warps each (long literals copied by all of them); smaller ones
+// by one warp each.  Dictionary pages always take a block.
+constexpr uint32_t kCoopSnappyBytes = 256 * 1024;
+
 // Expansion of one output column: copies (REQUIRED PLAIN fixed width), the
 // staged dictionary expand (REQUIRED fixed width with dictionary pages), or
 // the general warp decode.
@@ -1253,11 +1260,14 @@ static void enqueue_column(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, b
   const auto& cw = plan->colwork[oc];
   const int n_data_total = static_cast<int>(plan->snappy_data.size());
   if (with_dicts && cw.snap_dict_n)
-    pqi::launch_snappy(plan->d_snappy + n_data_total + cw.snap_dict_begin, cw.snap_dict_n, ctx->n_sms, a.st, s);
+    pqi::launch_snappy(plan->d_snappy + n_data_total + cw.snap_dict_begin, cw.snap_dict_n, ctx->n_sms, a.st, s,
+                       true);
   if (with_dicts && cw.dict_n)
     pqi::launch_dict(plan->d_dict_jobs + cw.dict_begin, cw.dict_n, cw.max_fixed_dict, cw.max_str_regions,
                      pqi::DictScratch{plan->d_sregs, plan->d_slists}, plan->idx->d_dicts, ctx->n_sms, a.st, s);
-  if (cw.snap_data_n) pqi::launch_snappy(plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, ctx->n_sms, a.st, s);
+  if (cw.snap_data_n)
+    pqi::launch_snappy(plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, ctx->n_sms, a.st, s,
+                       cw.snap_data_max >= kCoopSnappyBytes);
   enqueue_transcode(plan, cw.tc_begin, cw.tc_n, a, s);
   const auto& col = plan->outcols[oc];
   pqi::launch_walk(a, cw.walk_begin, cw.walk_n, ctx->n_sms, col.optional != 0, s);
@@ -1289,7 +1299,8 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
   const int n_dict_jobs = static_cast<int>(plan->snappy_dict.size());
   if (plan->flags & PQ_SCAN_PLAIN) {
     // baseline: per chunk, one launch per stage; one page per thread block
-    if (with_dicts && n_dict_jobs) pqi::launch_snappy(plan->d_snappy + n_data_jobs, n_dict_jobs, ctx->n_sms, a.st, s);
+    if (with_dicts && n_dict_jobs)
+      pqi::launch_snappy(plan->d_snappy + n_data_jobs, n_dict_jobs, ctx->n_sms, a.st, s, true);
     mark(2);
     if (with_dicts && !plan->dict_jobs.empty())
       pqi::launch_dict(plan->d_dict_jobs, static_cast<int>(plan->dict_jobs.size()), plan->max_fixed_dict_bytes,
@@ -1303,7 +1314,7 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
       for (int p = first; p < first + n; ++p)
         if (job + nj < plan->snappy_data.size() && plan->snappy_data[job + nj].page == static_cast<int32_t>(plan->pps[p].page))
           ++nj;
-      if (nj) pqi::launch_snappy(plan->d_snappy + job, nj, ctx->n_sms, a.st, s);
+      if (nj) pqi::launch_snappy(plan->d_snappy + job, nj, ctx->n_sms, a.st, s, plan->snap_data_max >= kCoopSnappyBytes);
       job += nj;
       int ntc = 0;
       while (tcj + ntc < plan->tc_jobs.size() && plan->tc_jobs[tcj + ntc].pp < static_cast<uint32_t>(first + n)) ++ntc;
@@ -1319,8 +1330,11 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
     for (int oc = 0; oc < ncols; ++oc) {
       const auto& cw = plan->colwork[oc];
       if (with_dicts && cw.snap_dict_n)
-        pqi::launch_snappy(plan->d_snappy + n_data_jobs + cw.snap_dict_begin, cw.snap_dict_n, ctx->n_sms, a.st, s);
-      if (cw.snap_data_n) pqi::launch_snappy(plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, ctx->n_sms, a.st, s);
+        pqi::launch_snappy(plan->d_snappy + n_data_jobs + cw.snap_dict_begin, cw.snap_dict_n, ctx->n_sms, a.st, s,
+                           true);
+      if (cw.snap_data_n)
+        pqi::launch_snappy(plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, ctx->n_sms, a.st, s,
+                           cw.snap_data_max >= kCoopSnappyBytes);
       enqueue_transcode(plan, cw.tc_begin, cw.tc_n, a, s);
     }
     mark(2);

@@ -100,6 +100,7 @@ struct pq_plan {
   std::vector<pqi::OutCol> outcols;
   std::vector<pqi::SnappyJob> snappy_data;   // data pages
   std::vector<pqi::SnappyJob> snappy_dict;   // dictionary pages (into index buffers)
+  uint32_t snap_data_max = 0;                 // largest compressed data page of the plan
   std::vector<pqi::DictJob> dict_jobs;
   std::vector<int32_t> dict_chunks;          // chunk of each dict job
   std::vector<int32_t> str_cols;             // output columns of type BYTE_ARRAY
@@ -160,6 +161,7 @@ struct pq_plan {
   // per output column: ranges into the job lists
   struct ColWork {
     int snap_data_begin = 0, snap_data_n = 0;  // into snappy_data
+    uint32_t snap_data_max = 0;                // largest compressed data page (bytes)
     int snap_dict_begin = 0, snap_dict_n = 0;  // into snappy_dict
     int dict_begin = 0, dict_n = 0;            // into dict_jobs
     int max_fixed_dict = 0;

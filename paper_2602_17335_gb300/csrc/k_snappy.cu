@@ -165,13 +165,70 @@ __device__ __forceinline__ void lit_to_ring(uint8_t* ring, uint32_t o0, const ui
   }
 }
 
-__global__ void __launch_bounds__(32 * kSnappyWarps) k_snappy(const SnappyJob* __restrict__ jobs, int n_jobs,
-                                                              DevStatus* st) {
+// Input bytes src[0, n) to ring positions [pos0, pos0 + n): whole 16-byte
+// ring words built from two aligned source words, the partial words at the
+// two ends byte by byte.
+__device__ __forceinline__ void ring_fill(uint8_t* ring, uint32_t pos0, const uint8_t* src, uint32_t n, int lane) {
+  constexpr uint32_t RM = kRing - 1;
+  const uint32_t head0 = (16 - (pos0 & 15)) & 15;
+  const uint32_t head = head0 < n ? head0 : n;
+  if (static_cast<uint32_t>(lane) < head) ring[(pos0 + lane) & RM] = __ldg(src + lane);
+  const uint32_t nv = (n - head) >> 4;
+  const uint8_t* s1 = src + head;
+  const uint32_t sh = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(s1) & 15);
+  const uint4* sa = reinterpret_cast<const uint4*>(s1 - sh);
+  for (uint32_t v = lane; v < nv; v += 32) {
+    const uint4 A = __ldg(sa + v);
+    const uint4 B = sh ? __ldg(sa + v + 1) : A;
+    *reinterpret_cast<uint4*>(ring + ((pos0 + head + 16 * v) & RM)) = sh ? shift_pair(A, B, sh) : A;
+  }
+  for (uint32_t i = head + (nv << 4) + lane; i < n; i += 32) ring[(pos0 + i) & RM] = __ldg(src + i);
+}
+
+// A cooperative copy request from warp 0 to the other warps of its block.
+struct SnCoop {
+  uint8_t* dst;
+  const uint8_t* src;
+  uint32_t len;  // 0: the page is done
+  uint32_t pad;
+};
+
+__device__ __forceinline__ void coop_bar() { asm volatile("bar.sync 1, %0;" ::"r"(32 * 8) : "memory"); }
+
+// Slice w of 8 of a copy (16-byte aligned destination boundaries).
+__device__ __forceinline__ void coop_slice(const SnCoop& c, int w, int lane) {
+  const uint64_t per = ((static_cast<uint64_t>(c.len) + 8 * 16 - 1) / (8 * 16)) * 16;
+  const uint64_t b = per * w, e = b + per < c.len ? b + per : c.len;
+  if (b < e) warp_copy<true>(c.dst + b, c.src + b, e - b, lane);
+}
+
+// kCoop: one block of 8 warps per page; warp 0 parses and executes, and the
+// literals of at least kCoopLit bytes are copied by all 8 warps.  Otherwise
+// one warp per page.
+constexpr uint32_t kCoopLit = 4096;
+
+template <bool kCoop>
+__global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(const SnappyJob* __restrict__ jobs,
+                                                                            int n_jobs, DevStatus* st) {
   extern __shared__ __align__(16) uint8_t sn_smem[];
   const int lane = threadIdx.x & 31;
-  SnWarp& sw = reinterpret_cast<SnWarp*>(sn_smem)[threadIdx.x >> 5];
-  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  SnWarp& sw = reinterpret_cast<SnWarp*>(sn_smem)[kCoop ? 0 : threadIdx.x >> 5];
+  SnCoop& cq = *reinterpret_cast<SnCoop*>(sn_smem + sizeof(SnWarp) * (kCoop ? 1 : kSnappyWarps));
+  const int wid = kCoop ? blockIdx.x : (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = kCoop ? gridDim.x : (gridDim.x * blockDim.x) >> 5;
+  if (kCoop && threadIdx.x >= 32) {
+    // helper warps: slices of warp 0's long literals until it says the page is done
+    for (int j = wid; j < n_jobs; j += nwarps) {
+      for (;;) {
+        coop_bar();
+        const SnCoop c = cq;
+        if (c.len == 0) break;
+        coop_slice(c, threadIdx.x >> 5, lane);
+        coop_bar();
+      }
+    }
+    return;
+  }
   if (lane == 0) {
     mbar_init(&sw.bar[0], 1);
     mbar_init(&sw.bar[1], 1);
@@ -181,20 +238,30 @@ __global__ void __launch_bounds__(32 * kSnappyWarps) k_snappy(const SnappyJob* _
   uint32_t par[2] = {0, 0};
   uint8_t* ring = sw.ring;
   constexpr uint32_t RM = kRing - 1;
+  auto page_done = [&]() {
+    if (kCoop) {
+      if (lane == 0) cq.len = 0;
+      __syncwarp();
+      coop_bar();
+    }
+  };
   for (int j = wid; j < n_jobs; j += nwarps) {
     const SnappyJob jb = jobs[j];
     if (jb.prefix > jb.src_len || jb.prefix > jb.dst_len) {
       if (lane == 0) report(st, DERR_CORRUPT, jb.page, WHERE_SNAPPY, 1);
+      page_done();
       continue;
     }
     warp_copy<true>(jb.dst, jb.src, jb.prefix, lane);  // V2 level bytes, never compressed
     if (jb.raw) {
       if (jb.src_len != jb.dst_len) {
         if (lane == 0) report(st, DERR_CORRUPT, jb.page, WHERE_SNAPPY, 2);
+        page_done();
         continue;
       }
       warp_copy<true>(jb.dst + jb.prefix, jb.src + jb.prefix, jb.src_len - jb.prefix, lane);
       __syncwarp();
+      page_done();
       continue;
     }
     const uint8_t* in = jb.src + jb.prefix;
@@ -205,6 +272,7 @@ __global__ void __launch_bounds__(32 * kSnappyWarps) k_snappy(const SnappyJob* _
     int pl = uleb([&](uint32_t k) { return static_cast<uint32_t>(__ldg(in + k)); }, 0, in_len, &declared);
     if (pl == 0 || declared != out_len) {
       if (lane == 0) report(st, DERR_CORRUPT, jb.page, WHERE_SNAPPY, 3);
+      page_done();
       continue;
     }
     // lane 0's window state
@@ -349,9 +417,17 @@ __global__ void __launch_bounds__(32 * kSnappyWarps) k_snappy(const SnappyJob* _
         const int e = __ffs(lm) - 1;
         const uint32_t el = __shfl_sync(0xffffffffu, len, e);
         const uint32_t ea = __shfl_sync(0xffffffffu, arg, e), eo = __shfl_sync(0xffffffffu, o0, e);
-        warp_copy<true>(out + eo, in + ea, el, lane);
+        if (kCoop && el >= kCoopLit) {
+          if (lane == 0) cq = SnCoop{out + eo, in + ea, el, 0};
+          __syncwarp();
+          coop_bar();
+          coop_slice(SnCoop{out + eo, in + ea, el, 0}, 0, lane);
+          coop_bar();
+        } else {
+          warp_copy<true>(out + eo, in + ea, el, lane);
+        }
         const uint32_t t0 = el > kRing ? el - kRing : 0u;
-        for (uint32_t i = t0 + lane; i < el; i += 32) ring[(eo + i) & RM] = __ldg(in + ea + i);
+        ring_fill(ring, eo + t0, in + ea + t0, el - t0, lane);
       }
       __syncwarp();
       op = bend;
@@ -371,23 +447,33 @@ __global__ void __launch_bounds__(32 * kSnappyWarps) k_snappy(const SnappyJob* _
     par[0] = __shfl_sync(0xffffffffu, sw0 ? sin.p0 : sin.p1, 0);
     par[1] = __shfl_sync(0xffffffffu, sw0 ? sin.p1 : sin.p0, 0);
     __syncwarp();
+    page_done();
   }
 }
 
-void launch_snappy(const SnappyJob* jobs, int n_jobs, int n_sms, DevStatus* st, cudaStream_t s) {
+void launch_snappy(const SnappyJob* jobs, int n_jobs, int n_sms, DevStatus* st, cudaStream_t s, bool coop) {
   if (n_jobs <= 0) return;
-  constexpr uint32_t smem = kSnappyWarps * sizeof(SnWarp);
   static bool attr = false;
+  constexpr uint32_t smem_w = kSnappyWarps * sizeof(SnWarp) + sizeof(SnCoop);
+  constexpr uint32_t smem_c = sizeof(SnWarp) + sizeof(SnCoop);
   if (!attr) {
-    cudaFuncSetAttribute(k_snappy, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_snappy<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_w);
+    cudaFuncSetAttribute(k_snappy<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c);
     attr = true;
   }
   int bps = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_snappy, 32 * kSnappyWarps, smem);
+  if (coop) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_snappy<true>, 256, smem_c);
+    if (bps < 1) bps = 1;
+    const int blocks = n_jobs < n_sms * bps ? n_jobs : n_sms * bps;
+    k_snappy<true><<<blocks, 256, smem_c, s>>>(jobs, n_jobs, st);
+    return;
+  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_snappy<false>, 32 * kSnappyWarps, smem_w);
   if (bps < 1) bps = 1;
   int blocks = (n_jobs + kSnappyWarps - 1) / kSnappyWarps;
   if (blocks > n_sms * bps) blocks = n_sms * bps;
-  k_snappy<<<blocks, 32 * kSnappyWarps, smem, s>>>(jobs, n_jobs, st);
+  k_snappy<false><<<blocks, 32 * kSnappyWarps, smem_w, s>>>(jobs, n_jobs, st);
 }
 
 }  // namespace pqi

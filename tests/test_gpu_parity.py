@@ -404,3 +404,15 @@ def test_hybrid_run_chains_across_regions(eng):
     spec = synth.TableSpec(n, 8 << 20, [synth.ColumnSpec(e) for e in encs])
     data = W.write_file(synth.Table(cols), spec)
     _roundtrip(eng, data, row_begin=12_345, row_count=700_001)
+
+
+def test_snappy_large_pages(eng):
+    """Snappy pages far above the size at which a block of warps takes a page
+    (hundreds of KB to MB, literals longer than the ring), with Snappy forced
+    on every chunk; V1 and V2 pages."""
+    tab = synth.config2_table(300_000, 300_000, **SMALL)
+    for version in (1, 2):
+        spec = synth.config2_spec(300_000, 4 << 20, "SNAPPY", version)
+        for c in spec.columns:
+            c.compress_threshold = -1.0
+        _roundtrip(eng, W.write_file(tab, spec))
