@@ -29,11 +29,13 @@ constexpr int kSnappyWarps = 4;     // warps per block
 constexpr uint32_t kRing = 8192;    // recent output kept in shared memory per warp (power of two)
 constexpr uint32_t kWin = 4096;     // input window (two per warp)
 constexpr uint32_t kBatchOut = kRing / 2;  // output bytes of one batch assembled in the ring
+constexpr uint32_t kMidLit = 2048;  // literals up to this long go from the input window through the ring
 
 struct SnWarp {
   uint64_t bar[2];
   uint32_t kl[32];   // kind | len << 2
   uint32_t arg[32];  // literal: input offset; copy: back offset
+  int32_t woff[32];  // literal inside the batch's input window: its offset there, else -1
   uint8_t win[2][kWin + 16];
   uint8_t ring[kRing];
 };
@@ -293,6 +295,10 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
       if (lane == 0) {
         uint32_t p = ip, o = op, bo = 0;
         for (int e = 0; e < 32 && p < in_len; ++e) {
+          // a batch's headers all sit in one window (its literals are read
+          // from there): switch windows only at a batch's first element
+          const bool here = p - sin.w0 < sin.n0 && (p - sin.w0 + 5 <= sin.n0 || sin.w0 + sin.n0 >= in_len);
+          if (!here && e > 0) break;
           if (!sn_ensure(sin, p)) { bad = 2; break; }
           // the tag and the 4 bytes after it (slack past the input end is never used)
           const uint8_t* q = sin.b0 + (p - sin.w0);
@@ -332,14 +338,17 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
             p += 4;
           }
           if (len > out_len - o || (kind != 0 && (arg == 0 || arg > o))) { bad = 1; break; }
+          const bool inwin = kind == 0 && len <= kMidLit && arg - sin.w0 + len <= sin.n0;
           sw.kl[e] = kind | (len << 2);
           sw.arg[e] = arg;
+          sw.woff[e] = inwin ? static_cast<int32_t>(arg - sin.w0) : -1;
           n_el = e + 1;
           o += len;
           bo += len;
-          // a batch's short output is assembled in the ring; a long literal
-          // ends its batch (it is copied to global memory directly)
-          if (bo >= kBatchOut - 64 || (kind == 0 && len > 256)) break;
+          // a batch's output is assembled in the ring; a literal that is not
+          // in the window (or longer than kMidLit) ends its batch: it is
+          // copied to global memory directly
+          if (bo >= kBatchOut - 64 || (kind == 0 && !inwin)) break;
         }
         ip = p;
       }
@@ -348,10 +357,13 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
       bad = __shfl_sync(0xffffffffu, bad, 0);
       ip = __shfl_sync(0xffffffffu, ip, 0);
       uint32_t kl = 0, arg = 0;
+      int32_t woff = -1;
       if (lane < n_el) {
         kl = sw.kl[lane];
         arg = sw.arg[lane];
+        woff = sw.woff[lane];
       }
+      const uint8_t* wbuf = sw.win[__shfl_sync(0xffffffffu, lane == 0 && sin.b0 == sw.win[1] ? 1 : 0, 0)];
       const uint32_t kind = kl & 3, len = kl >> 2;
       uint32_t incl = len;
 #pragma unroll
@@ -369,16 +381,16 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
       const bool valid = lane < n_el;
       // long literals (the batch's last element): global to global, the
       // tail into the ring
-      const bool longlit = valid && kind == 0 && len > 256;
+      const bool longlit = valid && kind == 0 && woff < 0;
       const bool indep = valid && !longlit && (kind == 0 || (arg >= len && o0 - arg + len <= op));
       auto src_byte = [&](uint32_t pos) -> uint8_t {
         return pos >= rlo ? ring[pos & RM] : ld_src<false>(out + pos);
       };
       if (indep) {
-        if (kind == 0 && len <= 64) {
-          lit_to_ring(ring, o0, in + arg, len);  // the input sits in L2 (its window was just copied)
+        if (kind == 0 && len <= 32) {
+          for (uint32_t i = 0; i < len; ++i) ring[(o0 + i) & RM] = wbuf[woff + i];
         } else if (kind == 0) {
-          for (uint32_t i = 0; i < len; ++i) ring[(o0 + i) & RM] = __ldg(in + arg + i);
+          // longer literals from the window: by the whole warp, below
         } else {
           const uint32_t first = o0 - arg;
           uint32_t i = 0;
@@ -392,6 +404,13 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
           }
           for (; i < len; ++i) ring[(o0 + i) & RM] = src_byte(first + i);
         }
+      }
+      __syncwarp();
+      for (uint32_t m = __ballot_sync(0xffffffffu, indep && kind == 0 && len > 32); m; m &= m - 1) {
+        const int e = __ffs(m) - 1;
+        const uint32_t el = __shfl_sync(0xffffffffu, len, e), eo = __shfl_sync(0xffffffffu, o0, e);
+        const int32_t ew = __shfl_sync(0xffffffffu, woff, e);
+        for (uint32_t i = lane; i < el; i += 32) ring[(eo + i) & RM] = wbuf[ew + i];
       }
       __syncwarp();
       for (uint32_t m = __ballot_sync(0xffffffffu, valid && !indep && !longlit); m; m &= m - 1) {
