@@ -55,7 +55,7 @@ def parse_args():
                          "(BYTE_STREAM_SPLIT, DELTA_LENGTH_BYTE_ARRAY, DELTA_BYTE_ARRAY)")
     ap.add_argument("--rg-rows", type=int, default=1 << 23)
     ap.add_argument("--page-bytes", type=int, default=MiB)
-    ap.add_argument("--codec", default="UNCOMPRESSED", choices=["UNCOMPRESSED", "SNAPPY"])
+    ap.add_argument("--codec", default="UNCOMPRESSED", choices=["UNCOMPRESSED", "SNAPPY", "ZSTD"])
     ap.add_argument("--page-version", type=int, default=1)
     ap.add_argument("--mode", default="batched", choices=["batched", "plain"])
     ap.add_argument("--no-offset-index", action="store_true")

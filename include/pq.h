@@ -19,7 +19,9 @@
  * V2 encodings of the paper's Section 3 (Insight 3): BYTE_STREAM_SPLIT
  * (fixed-width columns), DELTA_LENGTH_BYTE_ARRAY and DELTA_BYTE_ARRAY
  * (BYTE_ARRAY columns; DELTA blocks of at most 2048 values), definition
- * levels with the RLE/bit-packed hybrid, codecs UNCOMPRESSED and SNAPPY.
+ * levels with the RLE/bit-packed hybrid, codecs UNCOMPRESSED, SNAPPY and ZSTD
+ * (the codecs the paper's Section 2 names; Zstandard frames without a
+ * dictionary, every block type).
  * Anything else is rejected with PQ_ERR_UNSUPPORTED, never mis-decoded.
  *
  * Conventions for every call:
@@ -189,7 +191,9 @@ typedef struct pq_out_size {
                                 (int64 offsets) */
   uint64_t validity_bytes;   /* OPTIONAL: ceil(n_rows / 32) * 4, else 0 */
   uint64_t chars_bytes;      /* BYTE_ARRAY: chars capacity the scan needs (exact for whole
-                                chunks, an upper bound for partial ones), else 0 */
+                                chunks, an upper bound for partial ones; exact when some
+                                chunk carries no SizeStatistics and a sizing scan counted
+                                them), else 0 */
 } pq_out_size;
 
 typedef struct pq_plan_info {
@@ -208,10 +212,16 @@ typedef struct pq_plan_info {
  * range, sizes the outputs, splits the pages into decode work items and
  * reserves scratch (decompression buffers, per-item checkpoints).  When
  * `sizes` is not NULL it receives one pq_out_size per requested column.
+ * String chars are sized from each chunk's SizeStatistics
+ * (unencoded_byte_array_data_bytes).  When a requested BYTE_ARRAY chunk
+ * carries none (older writers), planning runs one sizing scan on the device
+ * -- every kernel of the scan but the chars copy, into temporary outputs,
+ * on a private stream, waited for -- and reports the exact chars bytes of
+ * the requested rows.
  * The plan is owned by the library (pq_free_plan); it must not outlive the
  * index.  Errors: PQ_ERR_INVALID_ARG (column id, row range),
- * PQ_ERR_UNSUPPORTED (a BYTE_ARRAY chunk without size statistics in its
- * metadata), PQ_ERR_OOM. */
+ * PQ_ERR_UNSUPPORTED (a DELTA_BYTE_ARRAY chunk without size statistics),
+ * PQ_ERR_OOM, and the device errors of the sizing scan (PQ_ERR_CORRUPT ...). */
 pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_plan** out,
                        pq_out_size* sizes);
 pq_status pq_plan_get_info(const pq_plan* plan, pq_plan_info* out);

@@ -335,7 +335,7 @@ def write_chunk(col, cspec: ColumnSpec, page_bytes: int, base: int, rng=None):
         (9, T.I64, data_off),
         (11, T.I64, dict_off),
     ]
-    if ptype == "BYTE_ARRAY":
+    if ptype == "BYTE_ARRAY" and cspec.size_statistics:
         meta.append((16, T.STRUCT, [(1, T.I64, int(sum(len(v) for v in nonnull)))]))
     return data, meta, locations, codec
 

@@ -102,7 +102,8 @@ void launch_dict_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_
 // Items of a column whose pages are all REQUIRED PLAIN fixed-width: copies.
 void launch_copy_items(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, int ctas_per_sm,
                        cudaStream_t s);
-void launch_strings(const DecodeArgs& a, int col, int n_items, int n_sms, cudaStream_t s);
+// copy_chars false: only the offsets pass (chars totals), no chars written
+void launch_strings(const DecodeArgs& a, int col, int n_items, int n_sms, bool copy_chars, cudaStream_t s);
 // Plain baseline: pages [pp_begin, pp_begin + n) decoded one page per block.
 void launch_plain_pages(const DecodeArgs& a, int pp_begin, int n, cudaStream_t s);
 void launch_prepare(const DecodeArgs& a, int n_cols, int grid, cudaStream_t s);
@@ -117,6 +118,8 @@ int expand_blocks_per_sm();
 int walk_blocks_per_sm();
 // coop: one block of 8 warps per page (large pages), else one warp per page
 void launch_snappy(const SnappyJob* jobs, int n_jobs, int n_sms, DevStatus* st, cudaStream_t s, bool coop);
+// Zstandard pages of jobs [0, n_jobs) (the others are skipped)
+void launch_zstd(const SnappyJob* jobs, int n_jobs, int n_sms, DevStatus* st, cudaStream_t s);
 void launch_index_walk(const ChunkDev* chunks, int n_chunks, PageDev* pages, uint32_t* counts, int mode,
                        DevStatus* st, cudaStream_t s);
 void launch_gather16(const uint8_t* const* ptr, const int32_t* len, int n, uint8_t* out, cudaStream_t s);

@@ -386,7 +386,7 @@ pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi,
           return fail(ctx, PQ_ERR_CORRUPT, "chunk type differs from the schema");
         if (cm.num_values != g.num_rows)
           return fail(ctx, PQ_ERR_CORRUPT, "chunk value count differs from its row group (nested data?)");
-        if (cm.codec != pqi::CODEC_NONE && cm.codec != pqi::CODEC_SNAPPY)
+        if (cm.codec != pqi::CODEC_NONE && cm.codec != pqi::CODEC_SNAPPY && cm.codec != pqi::CODEC_ZSTD)
           return fail(ctx, PQ_ERR_UNSUPPORTED, "codec " + std::to_string(cm.codec) + " not supported");
         if (start < 4 || cm.total_compressed < 0 ||
             static_cast<uint64_t>(start) + static_cast<uint64_t>(cm.total_compressed) + 8 + m.footer_len > fsize ||
@@ -771,11 +771,10 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
       const int64_t c1 = c0 + cd.num_values;
       if (c1 <= rb || c0 >= re) continue;
       if (cm.type == pqi::T_BYTE_ARRAY) {
-        if (idx->chunk_ba_bytes[ch] < 0) {
-          return fail(ctx, PQ_ERR_UNSUPPORTED,
-                      "BYTE_ARRAY chunk without size statistics (unencoded_byte_array_data_bytes)");
-        }
-        chars += static_cast<uint64_t>(idx->chunk_ba_bytes[ch]);
+        if (idx->chunk_ba_bytes[ch] < 0)
+          cw.unsized = true;  // no SizeStatistics: a sizing scan at upload counts the chars
+        else
+          chars += static_cast<uint64_t>(idx->chunk_ba_bytes[ch]);
       }
       const int32_t pp_first = static_cast<int32_t>(plan->pps.size());
       bool tc_chunk_counted = false;  // this visit's chars are in the pool size
@@ -794,6 +793,8 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
             sj.src_len = static_cast<uint32_t>(dp.compressed);
             sj.dst_len = static_cast<uint32_t>(dp.uncompressed);
             sj.page = cd.dict_page;
+            sj.codec = cd.codec;
+            if (cd.codec == pqi::CODEC_ZSTD) plan->zstd_jobs++;
             plan->snappy_dict.push_back(sj);
             dj.body = idx->dict_body[ch];
           } else {
@@ -863,6 +864,8 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
           sj.dst_len = static_cast<uint32_t>(pg.uncompressed);
           sj.prefix = pg.page_type == pqi::PAGE_DATA_V2 ? static_cast<uint32_t>(pg.def_len + pg.rep_len) : 0u;
           sj.page = static_cast<int32_t>(pid);
+          sj.codec = cd.codec;
+          if (cd.codec == pqi::CODEC_ZSTD) plan->zstd_jobs++;
           data_job_off.push_back(static_cast<int64_t>(scratch));
           plan->snappy_data.push_back(sj);
           cw.snap_data_max = std::max<uint32_t>(cw.snap_data_max, sj.src_len);
@@ -888,6 +891,8 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
           j.num_values = pg.num_values;
           j.required = cd.max_def ? 0 : 1;
           plan->tc_src_off.push_back(pp.pad == 1 ? static_cast<int64_t>(reinterpret_cast<uintptr_t>(pp.body)) : -1);
+          if (enc == pqi::ENC_DELTA_BA && idx->chunk_ba_bytes[ch] < 0)
+            return fail(ctx, PQ_ERR_UNSUPPORTED, "DELTA_BYTE_ARRAY chunk without size statistics");
           if (enc == pqi::ENC_DELTA_BA) {
             // the PLAIN size is known only on the device: the page takes a piece
             // of a pool that holds its levels, length words and padding, plus
@@ -963,7 +968,8 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
     cw.max_fixed_dict = plan->max_fixed_dict_bytes;
     plan->max_fixed_dict_bytes = std::max(max_fixed_before, plan->max_fixed_dict_bytes);
     plan->colwork.push_back(cw);
-    sz.chars_bytes = chars;
+    sz.chars_bytes = cw.unsized ? 0 : chars;
+    if (cw.unsized) plan->needs_sizing = true;
     if (cm.type == pqi::T_BYTE_ARRAY) plan->str_cols.push_back(static_cast<int32_t>(oc));
     plan->decoded_bytes += sz.values_bytes + sz.validity_bytes + sz.chars_bytes;
     plan->outcols.push_back(col);
@@ -986,6 +992,8 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
   *out = std::move(plan);
   return PQ_OK;
 }
+
+static pq_status plan_size_strings(pq_plan* plan);
 
 // Device half: allocations from the context's pool, uploads, work items,
 // events, pinned staging.
@@ -1092,14 +1100,14 @@ pq_status plan_upload(pq_plan* plan) {
     int n = 1;
     const bool any_dict = !plan->dict_jobs.empty();
     if (plain) {
-      n += (plan->snappy_dict.empty() ? 0 : 1) + (any_dict ? 2 : 0);
+      n += (plan->snappy_dict.empty() ? 0 : (plan->zstd_jobs ? 2 : 1)) + (any_dict ? 2 : 0);
       size_t job = 0;
       for (auto& cp : plan->chunk_pp) {
         int nj = 0;
         for (int q = cp.first; q < cp.first + cp.second; ++q)
           if (job + nj < plan->snappy_data.size() && plan->snappy_data[job + nj].page == static_cast<int32_t>(plan->pps[q].page))
             ++nj;
-        n += (nj ? 1 : 0) + 1;
+        n += (nj ? (plan->zstd_jobs ? 2 : 1) : 0) + 1;
         job += nj;
       }
       size_t tcj = 0;
@@ -1114,7 +1122,8 @@ pq_status plan_upload(pq_plan* plan) {
     } else {
       for (size_t oc = 0; oc < plan->colwork.size(); ++oc) {
         const auto& cw = plan->colwork[oc];
-        n += (cw.snap_dict_n ? 1 : 0) + (cw.dict_n ? 2 : 0) + (cw.snap_data_n ? 1 : 0) + (cw.walk_n ? 1 : 0) +
+        const int dk = plan->zstd_jobs ? 2 : 1;  // decompression kernels per job list
+        n += (cw.snap_dict_n ? dk : 0) + (cw.dict_n ? 2 : 0) + (cw.snap_data_n ? dk : 0) + (cw.walk_n ? 1 : 0) +
              (cw.delta_n ? 4 : 0) + (cw.tc_n ? 1 : 0) + (plan->outcols[oc].item_count ? 1 : 0);
       }
     }
@@ -1130,7 +1139,70 @@ pq_status plan_upload(pq_plan* plan) {
     free_plan_device(plan);
     return fail(ctx, PQ_ERR_OOM, "pinned staging");
   }
+  if (plan->needs_sizing) return plan_size_strings(plan);
   return PQ_OK;
+}
+
+// Chars of string columns whose chunks carry no SizeStatistics: one scan
+// into temporary outputs without the chars copy (the string offsets pass
+// still totals each column), on a private stream, then the totals become
+// the plan's chars_bytes.
+static pq_status plan_size_strings(pq_plan* plan) {
+  pq_ctx* ctx = plan->ctx;
+  const size_t nc = plan->outcols.size();
+  std::vector<pq_column> outs(nc);
+  std::vector<void*> tmp;
+  bool oom = false;
+  for (size_t i = 0; i < nc; ++i) {
+    const auto& sz = plan->sizes[i];
+    memset(&outs[i], 0, sizeof outs[i]);
+    void* v = ctx->pool.alloc(std::max<uint64_t>(sz.values_bytes, 16));
+    tmp.push_back(v);
+    outs[i].values = v;
+    oom |= !v;
+    if (sz.optional) {
+      void* m = ctx->pool.alloc(std::max<uint64_t>(sz.validity_bytes, 16));
+      tmp.push_back(m);
+      outs[i].validity = static_cast<uint32_t*>(m);
+      oom |= !m;
+    }
+  }
+  cudaStream_t s = nullptr;
+  pq_status st = PQ_OK;
+  if (oom) {
+    st = fail(ctx, PQ_ERR_OOM, "string sizing buffers");
+  } else if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    st = fail(ctx, PQ_ERR_CUDA, "string sizing stream");
+  } else {
+    plan->sizing = true;
+    st = scan_enqueue(plan, outs.data(), s, &s, 1, false);
+    plan->sizing = false;
+    if (st == PQ_OK) {
+      const cudaError_t e = cudaEventSynchronize(plan->done);
+      if (e != cudaSuccess) {
+        st = cuda_fail(ctx, e, "string sizing scan");
+      } else {
+        pqi::DevStatus ds;
+        memcpy(&ds, plan->h_out.p, sizeof ds);
+        st = status_from_device(ctx, ds);
+      }
+    }
+    cudaStreamDestroy(s);
+  }
+  if (st == PQ_OK) {
+    for (size_t j = 0; j < plan->str_cols.size(); ++j) {
+      int64_t v;
+      memcpy(&v, plan->h_out.p + sizeof(pqi::DevStatus) + 8 * j, 8);
+      auto& sz = plan->sizes[plan->str_cols[j]];
+      if (plan->colwork[plan->str_cols[j]].unsized) {
+        sz.chars_bytes = static_cast<uint64_t>(v);
+        plan->decoded_bytes += static_cast<uint64_t>(v);
+      }
+    }
+  }
+  for (void* p : tmp) ctx->pool.free(p);
+  return st;
 }
 
 uint64_t plan_device_bytes(const pq_plan* plan, uint64_t scratch) {
@@ -1227,6 +1299,15 @@ static void enqueue_transcode(pq_plan* plan, int begin, int n, const pqi::Decode
 // by one warp each.  Dictionary pages always take a block.
 constexpr uint32_t kCoopSnappyBytes = 256 * 1024;
 
+// Decompression of jobs [jobs, jobs + n): the Snappy kernel takes the Snappy
+// pages, the Zstandard kernel (launched when the plan has any) the others.
+static void launch_decompress(pq_plan* plan, const pqi::SnappyJob* jobs, int n, bool coop, pqi::DevStatus* st,
+                              cudaStream_t s) {
+  if (n <= 0) return;
+  pqi::launch_snappy(jobs, n, plan->ctx->n_sms, st, s, coop);
+  if (plan->zstd_jobs) pqi::launch_zstd(jobs, n, plan->ctx->n_sms, st, s);
+}
+
 // Expansion of one output column: copies (REQUIRED PLAIN fixed width), the
 // staged dictionary expand (REQUIRED fixed width with dictionary pages), or
 // the general warp decode.
@@ -1260,21 +1341,20 @@ static void enqueue_column(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, b
   const auto& cw = plan->colwork[oc];
   const int n_data_total = static_cast<int>(plan->snappy_data.size());
   if (with_dicts && cw.snap_dict_n)
-    pqi::launch_snappy(plan->d_snappy + n_data_total + cw.snap_dict_begin, cw.snap_dict_n, ctx->n_sms, a.st, s,
-                       true);
+    launch_decompress(plan, plan->d_snappy + n_data_total + cw.snap_dict_begin, cw.snap_dict_n, true, a.st, s);
   if (with_dicts && cw.dict_n)
     pqi::launch_dict(plan->d_dict_jobs + cw.dict_begin, cw.dict_n, cw.max_fixed_dict, cw.max_str_regions,
                      pqi::DictScratch{plan->d_sregs, plan->d_slists}, plan->idx->d_dicts, ctx->n_sms, a.st, s);
   if (cw.snap_data_n)
-    pqi::launch_snappy(plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, ctx->n_sms, a.st, s,
-                       cw.snap_data_max >= kCoopSnappyBytes);
+    launch_decompress(plan, plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, cw.snap_data_max >= kCoopSnappyBytes,
+                      a.st, s);
   enqueue_transcode(plan, cw.tc_begin, cw.tc_n, a, s);
   const auto& col = plan->outcols[oc];
   pqi::launch_walk(a, cw.walk_begin, cw.walk_n, ctx->n_sms, col.optional != 0, s);
   pqi::launch_delta_bases(a, cw.delta_begin, cw.delta_n, cw.max_regions, s);
   launch_column_expand(plan, oc, a, s);
   if (col.ptype == pqi::T_BYTE_ARRAY)
-    pqi::launch_strings(a, static_cast<int>(oc), static_cast<int>(col.item_count), ctx->n_sms, s);
+    pqi::launch_strings(a, static_cast<int>(oc), static_cast<int>(col.item_count), ctx->n_sms, !plan->sizing, s);
 }
 
 // Enqueues the kernels of one scan (no host synchronisation).  Default:
@@ -1300,7 +1380,7 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
   if (plan->flags & PQ_SCAN_PLAIN) {
     // baseline: per chunk, one launch per stage; one page per thread block
     if (with_dicts && n_dict_jobs)
-      pqi::launch_snappy(plan->d_snappy + n_data_jobs, n_dict_jobs, ctx->n_sms, a.st, s, true);
+      launch_decompress(plan, plan->d_snappy + n_data_jobs, n_dict_jobs, true, a.st, s);
     mark(2);
     if (with_dicts && !plan->dict_jobs.empty())
       pqi::launch_dict(plan->d_dict_jobs, static_cast<int>(plan->dict_jobs.size()), plan->max_fixed_dict_bytes,
@@ -1314,7 +1394,7 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
       for (int p = first; p < first + n; ++p)
         if (job + nj < plan->snappy_data.size() && plan->snappy_data[job + nj].page == static_cast<int32_t>(plan->pps[p].page))
           ++nj;
-      if (nj) pqi::launch_snappy(plan->d_snappy + job, nj, ctx->n_sms, a.st, s, plan->snap_data_max >= kCoopSnappyBytes);
+      if (nj) launch_decompress(plan, plan->d_snappy + job, nj, plan->snap_data_max >= kCoopSnappyBytes, a.st, s);
       job += nj;
       int ntc = 0;
       while (tcj + ntc < plan->tc_jobs.size() && plan->tc_jobs[tcj + ntc].pp < static_cast<uint32_t>(first + n)) ++ntc;
@@ -1325,16 +1405,15 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
     mark(4);
     mark(5);
     for (int32_t sc : plan->str_cols)
-      pqi::launch_strings(a, sc, static_cast<int>(plan->outcols[sc].item_count), ctx->n_sms, s);
+      pqi::launch_strings(a, sc, static_cast<int>(plan->outcols[sc].item_count), ctx->n_sms, !plan->sizing, s);
   } else if (timing) {
     for (int oc = 0; oc < ncols; ++oc) {
       const auto& cw = plan->colwork[oc];
       if (with_dicts && cw.snap_dict_n)
-        pqi::launch_snappy(plan->d_snappy + n_data_jobs + cw.snap_dict_begin, cw.snap_dict_n, ctx->n_sms, a.st, s,
-                           true);
+        launch_decompress(plan, plan->d_snappy + n_data_jobs + cw.snap_dict_begin, cw.snap_dict_n, true, a.st, s);
       if (cw.snap_data_n)
-        pqi::launch_snappy(plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, ctx->n_sms, a.st, s,
-                           cw.snap_data_max >= kCoopSnappyBytes);
+        launch_decompress(plan, plan->d_snappy + cw.snap_data_begin, cw.snap_data_n,
+                          cw.snap_data_max >= kCoopSnappyBytes, a.st, s);
       enqueue_transcode(plan, cw.tc_begin, cw.tc_n, a, s);
     }
     mark(2);
@@ -1354,7 +1433,7 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
     for (int oc = 0; oc < ncols; ++oc) launch_column_expand(plan, oc, a, s);
     mark(5);
     for (int32_t sc : plan->str_cols)
-      pqi::launch_strings(a, sc, static_cast<int>(plan->outcols[sc].item_count), ctx->n_sms, s);
+      pqi::launch_strings(a, sc, static_cast<int>(plan->outcols[sc].item_count), ctx->n_sms, !plan->sizing, s);
   } else {
     cudaEventRecord(plan->fork, s);
     for (int oc = 0; oc < ncols; ++oc) {
@@ -1390,9 +1469,9 @@ pq_status scan_enqueue(pq_plan* plan, const pq_column* outs, cudaStream_t s, con
     if (!outs[i].values && sz.values_bytes) return fail(ctx, PQ_ERR_INVALID_ARG, "missing values buffer");
     if (col.optional && !outs[i].validity && sz.n_rows)
       return fail(ctx, PQ_ERR_INVALID_ARG, "missing validity buffer for an OPTIONAL column");
-    if (col.ptype == pqi::T_BYTE_ARRAY && outs[i].chars_capacity < sz.chars_bytes)
+    if (!plan->sizing && col.ptype == pqi::T_BYTE_ARRAY && outs[i].chars_capacity < sz.chars_bytes)
       return fail(ctx, PQ_ERR_CAPACITY, "chars buffer smaller than the plan's chars_bytes");
-    if (col.ptype == pqi::T_BYTE_ARRAY && !outs[i].chars && sz.chars_bytes)
+    if (!plan->sizing && col.ptype == pqi::T_BYTE_ARRAY && !outs[i].chars && sz.chars_bytes)
       return fail(ctx, PQ_ERR_INVALID_ARG, "missing chars buffer");
     uint8_t* v = static_cast<uint8_t*>(outs[i].values);
     uint32_t* m = col.optional ? outs[i].validity : nullptr;
@@ -1401,7 +1480,7 @@ pq_status scan_enqueue(pq_plan* plan, const pq_column* outs, cudaStream_t s, con
     col.values = v;
     col.validity = m;
     col.chars = c;
-    col.chars_cap = outs[i].chars_capacity;
+    col.chars_cap = plan->sizing ? ~uint64_t(0) : outs[i].chars_capacity;
   }
   if (plan->graph && changed && (plan->str_cols.size() > 0)) {
     // the graph reads string totals through baked addresses: rebuild it

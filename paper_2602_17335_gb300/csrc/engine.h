@@ -101,6 +101,9 @@ struct pq_plan {
   std::vector<pqi::SnappyJob> snappy_data;   // data pages
   std::vector<pqi::SnappyJob> snappy_dict;   // dictionary pages (into index buffers)
   uint32_t snap_data_max = 0;                 // largest compressed data page of the plan
+  int zstd_jobs = 0;                          // Zstandard pages among the decompression jobs
+  bool needs_sizing = false;                  // string chars counted by a sizing scan at upload
+  bool sizing = false;                        // that scan is being enqueued (no chars copy)
   std::vector<pqi::DictJob> dict_jobs;
   std::vector<int32_t> dict_chunks;          // chunk of each dict job
   std::vector<int32_t> str_cols;             // output columns of type BYTE_ARRAY
@@ -174,6 +177,7 @@ struct pq_plan {
     int dict_pages = 0;                        // data pages with dictionary indices
     int64_t max_dict_n = 0;                    // most entries of one of its dictionaries
     int64_t max_dict_bytes = 0;                // largest fixed-width dictionary (bytes)
+    bool unsized = false;                      // BYTE_ARRAY chunks without SizeStatistics
   };
   std::vector<ColWork> colwork;
   cudaEvent_t fork = nullptr;

@@ -3556,9 +3556,10 @@ void launch_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, 
   k_expand<<<blocks, EXP_THREADS, 0, s>>>(a, ibegin, n, cidx);
 }
 
-void launch_strings(const DecodeArgs& a, int col, int n_items, int n_sms, cudaStream_t s) {
+void launch_strings(const DecodeArgs& a, int col, int n_items, int n_sms, bool copy_chars, cudaStream_t s) {
   if (n_items <= 0) return;
   k_str_scan<<<1, 1024, 0, s>>>(a, col);
+  if (!copy_chars) return;
   int blocks = (n_items + 7) / 8;
   if (blocks > n_sms * 8) blocks = n_sms * 8;
   static bool attr = false;

@@ -249,6 +249,10 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
   };
   for (int j = wid; j < n_jobs; j += nwarps) {
     const SnappyJob jb = jobs[j];
+    if (jb.codec != CODEC_SNAPPY) {  // another codec's kernel takes it
+      page_done();
+      continue;
+    }
     if (jb.prefix > jb.src_len || jb.prefix > jb.dst_len) {
       if (lane == 0) report(st, DERR_CORRUPT, jb.page, WHERE_SNAPPY, 1);
       page_done();

@@ -2,9 +2,8 @@
 // Snappy): one thread block per page, whose first thread runs the decoding
 // core of zstd_dec.cuh with its tables in shared memory.  The page jobs
 // have the Snappy jobs' layout (verbatim V2 level prefix, then the frame).
-// The core is checked on the CPU against the oracle; the scan does not
-// dispatch Zstandard pages here yet (chunks with that codec are rejected as
-// unsupported at index time).
+// Jobs of another codec are skipped (the Snappy kernel runs over the same
+// job list).
 #include "dev_util.cuh"
 #include "snappy_job.h"
 #include "zstd_dec.cuh"
@@ -16,6 +15,7 @@ __global__ void __launch_bounds__(32) k_zstd(const SnappyJob* __restrict__ jobs,
   __shared__ ZState z;
   for (int j = blockIdx.x; j < n_jobs; j += gridDim.x) {
     const SnappyJob jb = jobs[j];
+    if (jb.codec != CODEC_ZSTD) continue;
     if (threadIdx.x == 0) {
       int rc = 0;
       if (jb.prefix > jb.src_len || jb.prefix > jb.dst_len) {

@@ -28,7 +28,7 @@ enum : int32_t {
   T_BOOLEAN = 0, T_INT32 = 1, T_INT64 = 2, T_INT96 = 3, T_FLOAT = 4, T_DOUBLE = 5,
   T_BYTE_ARRAY = 6, T_FLBA = 7
 };
-enum : int32_t { CODEC_NONE = 0, CODEC_SNAPPY = 1 };
+enum : int32_t { CODEC_NONE = 0, CODEC_SNAPPY = 1, CODEC_ZSTD = 6 };
 
 // Device error word flags.
 enum : uint32_t {

@@ -1,4 +1,5 @@
-// One page to decompress (K1): built by the planner, read by the kernel.
+// One page to decompress (K1): built by the planner, read by the Snappy or
+// the Zstandard kernel.
 #pragma once
 #include <stdint.h>
 
@@ -12,7 +13,7 @@ struct SnappyJob {
   uint32_t prefix;     // bytes copied verbatim first (V2 level bytes)
   uint32_t raw;        // 1: no decompression (V2 page with is_compressed = false)
   int32_t page;        // page-table row, for error reports
-  int32_t pad;
+  int32_t codec;       // CODEC_SNAPPY or CODEC_ZSTD: the kernel of the other codec skips the job
 };
 
 }  // namespace pqi

@@ -205,6 +205,9 @@ class ColumnSpec:
     # compress a chunk only when it shrinks by more than this fraction
     # (None: always keep the codec's output)
     compress_threshold: Optional[float] = None
+    # BYTE_ARRAY: write the chunk's SizeStatistics (unencoded byte total);
+    # older writers leave it out
+    size_statistics: bool = True
 
 
 @dataclass

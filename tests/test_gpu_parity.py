@@ -416,3 +416,27 @@ def test_snappy_large_pages(eng):
         for c in spec.columns:
             c.compress_threshold = -1.0
         _roundtrip(eng, W.write_file(tab, spec))
+
+
+@pytest.mark.parametrize("enc", ["RLE_DICTIONARY", "PLAIN", "DELTA_LENGTH_BYTE_ARRAY"])
+def test_strings_without_size_statistics(eng, enc):
+    """BYTE_ARRAY chunks whose metadata carries no SizeStatistics (as older
+    writers leave it out): the planner sizes the chars with a sizing scan;
+    REQUIRED and OPTIONAL columns, several row groups, a row range, and a
+    second column that does carry the statistics."""
+    rng = np.random.default_rng(17)
+    n = 30_000
+    a = synth.strings_uniform(rng, n, k=500, min_len=0, max_len=40)
+    b = synth.strings_uniform(rng, n, k=900, min_len=3, max_len=20)
+    valid = rng.random(n) >= 0.2
+    cols = [synth.ColumnData("s_req", "BYTE_ARRAY", a), synth.ColumnData("s_opt", "BYTE_ARRAY", b, valid),
+            synth.ColumnData("s_stats", "BYTE_ARRAY", a)]
+    specs = [synth.ColumnSpec(enc, size_statistics=False), synth.ColumnSpec(enc, size_statistics=False),
+             synth.ColumnSpec(enc)]
+    for version in (1, 2):
+        for s in specs:
+            s.page_version = version
+        data = W.write_file(synth.Table(cols), synth.TableSpec(12_000, 8192, specs))
+        assert R.parse_footer(data).raw is not None
+        _roundtrip(eng, data)
+        _roundtrip(eng, data, row_begin=5_555, row_count=17_000)
