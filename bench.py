@@ -73,7 +73,11 @@ def parse_args():
     ap.add_argument("--c4-rows-hi", type=float, default=1e6)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve-files", type=int, default=4, help="serve: tables in the catalog index")
-    ap.add_argument("--serve-requests", type=int, default=200, help="serve: requests per offered-load point")
+    ap.add_argument("--serve-requests", type=int, default=10000, help="serve: requests per offered-load point")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="serve: arrivals stop after this many seconds at a load point")
+    ap.add_argument("--serve-max-pending", type=int, default=256,
+                    help="serve: arrivals while this many requests are pending are shed (counted, not sent)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serve: mean arrivals per second at 1x")
     ap.add_argument("--serve-loads", default="0.125,0.25,0.5,1", help="serve: offered-load multipliers")
     ap.add_argument("--serve-budget-gib", type=float, default=64.0)
@@ -657,19 +661,24 @@ def run_serve(a):
         for li, mult in enumerate(float(x) for x in a.serve_loads.split(",")):
             rate = a.serve_rate * mult
             reqs = request_stream(a, a.serve_requests, rate, 1000 + li, info.num_rows)
-            pending, lat, qms, rejected, decoded = {}, [], [], 0, 0
+            reqs = [r for r in reqs if r[0] <= a.serve_seconds]
+            pending, lat, qms, rejected, shed, decoded = {}, [], [], 0, 0, 0
+            overlap_max, on_device = 0, []
             start = time.perf_counter()
             i = 0
             while i < len(reqs) or pending:
                 now = time.perf_counter() - start
                 while i < len(reqs) and reqs[i][0] <= now:
                     _, cols, rb, rc = reqs[i]
+                    i += 1
+                    if len(pending) >= a.serve_max_pending:
+                        shed += 1  # open loop: the client sheds what the server cannot queue
+                        continue
                     st, tk = N.pq_serve_submit(srv, cols, rb, rc)
                     if st == N.PQ_OK:
                         pending[tk] = i
                     else:
                         rejected += 1
-                    i += 1
                 for tk in list(pending):
                     res = N.pq_serve_poll(srv, tk)
                     if res is None:
@@ -678,6 +687,7 @@ def run_serve(a):
                         lat.append(res.latency_ms)
                         qms.append(res.queue_ms)
                         decoded += res.decoded_bytes
+                        on_device.append((res.admit_ms, res.done_ms))
                     else:
                         rejected += 1
                     N.pq_serve_release(srv, tk)
@@ -688,7 +698,14 @@ def run_serve(a):
 
             def pct(p):
                 return lat_sorted[min(len(lat_sorted) - 1, int(np.ceil(p / 100 * len(lat_sorted))) - 1)] if lat_sorted else None
+            # most requests on the device at once (admitted, not yet completed)
+            ev = sorted([(t0, 1) for t0, _ in on_device] + [(t1, -1) for _, t1 in on_device])
+            cur = 0
+            for _, d in ev:
+                cur += d
+                overlap_max = max(overlap_max, cur)
             points.append({"offered_rps": rate, "achieved_rps": len(lat) / wall, "completed": len(lat),
+                           "arrivals": len(reqs), "shed": shed, "max_on_device": overlap_max,
                            "refused_or_failed": rejected, "p50_ms": pct(50), "p99_ms": pct(99),
                            "mean_queue_ms": float(np.mean(qms)) if qms else None, "decoded_gbs": decoded / wall / 1e9,
                            "wall_s": wall})
@@ -697,7 +714,7 @@ def run_serve(a):
     eng.close()
     knee = max(points, key=lambda p: p["decoded_gbs"])
     line = {"metric": "p50/p99 served scan latency", "value": knee["p99_ms"], "unit": "ms",
-            "n_gpus": 1, "steps": a.serve_requests * len(points), "warmup": 0, "ms_per_step": None,
+            "n_gpus": 1, "steps": sum(p["completed"] for p in points), "warmup": 0, "ms_per_step": None,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
             "config": {"workload": "serving: Poisson requests over %d eight-column tables of %d rows "
@@ -705,6 +722,9 @@ def run_serve(a):
                                        len(files), a.rows, "; ".join(d for _, d in files), a.serve_budget_gib,
                                        a.serve_slots),
                        "rows_per_request": "log-uniform 2^20..2^28, wrapping", "columns_per_request": "1..8",
+                       "arrivals": "Poisson, up to %d requests or %g s per load point; arrivals while %d requests "
+                                   "are pending are shed and counted" % (a.serve_requests, a.serve_seconds,
+                                                                         a.serve_max_pending),
                        "l2": "inputs larger than L2"},
             "serving": points, "clocks": clk.summary(),
             "detail": {"catalog_rows": info.num_rows, "write_seconds": gen_s,

@@ -320,6 +320,8 @@ typedef struct pq_serve_result {
   double queue_ms;           /* submit -> admitted */
   double latency_ms;         /* submit -> completion observed by the server */
   uint64_t decoded_bytes;
+  double admit_ms;           /* admission (enqueued on the device), ms since the server was created */
+  double done_ms;            /* completion observed, ms since the server was created */
 } pq_serve_result;
 
 /* Creates a server over the files of `idx` (the index must outlive it). */

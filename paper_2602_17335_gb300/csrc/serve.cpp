@@ -57,6 +57,7 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 
 struct pq_server {
   pq_ctx* ctx = nullptr;
+  Clock::time_point t_create = Clock::now();  // origin of the results' admit / done times
   pq_index* idx = nullptr;
   pq_serve_config cfg{};
   std::mutex mu;
@@ -359,6 +360,8 @@ pq_status pq_serve_poll(pq_server* srv, uint64_t ticket, pq_serve_result* out, i
   out->queue_ms = ms_between(r->t_submit, r->t_admit);
   out->latency_ms = ms_between(r->t_submit, r->t_done);
   out->decoded_bytes = r->decoded;
+  out->admit_ms = ms_between(srv->t_create, r->t_admit);
+  out->done_ms = ms_between(srv->t_create, r->t_done);
   return PQ_OK;
 }
 

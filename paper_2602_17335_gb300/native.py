@@ -79,7 +79,7 @@ class pq_serve_request(C.Structure):
 class pq_serve_result(C.Structure):
     _fields_ = [("status", C.c_int), ("n_columns", C.c_int32), ("columns", C.POINTER(pq_column)),
                 ("sizes", C.POINTER(pq_out_size)), ("queue_ms", C.c_double), ("latency_ms", C.c_double),
-                ("decoded_bytes", C.c_uint64)]
+                ("decoded_bytes", C.c_uint64), ("admit_ms", C.c_double), ("done_ms", C.c_double)]
 
 
 class pq_write_column(C.Structure):

@@ -98,11 +98,19 @@ def test_serving_alone_and_in_mix(setup):
             st, t = N.pq_serve_submit(srv, cols, rb, rc)
             assert st == N.PQ_OK
             tickets.append((t, cols, rb, rc))
+        spans = []
         for t, cols, rb, rc in tickets:
             res = _wait(N, srv, t)
             assert res.status == N.PQ_OK
             assert_columns_equal(server_result_outs(res), _expected(expect, cols, rb, rc))
+            assert res.done_ms >= res.admit_ms >= 0
+            spans.append((res.admit_ms, res.done_ms))
             assert N.pq_serve_release(srv, t) == N.PQ_OK
+        # continuous batching: some request was admitted while another was
+        # still on the device (their device intervals overlap)
+        overlapping = sum(1 for i, (a0, d0) in enumerate(spans) for (a1, d1) in spans[i + 1:]
+                          if a0 < d1 and a1 < d0)
+        assert overlapping > 0, spans
     finally:
         N.pq_serve_destroy(srv)
 
