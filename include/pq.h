@@ -407,6 +407,18 @@ typedef struct pq_tuning {
                                  kernels; 0 = the occupancy limit (default) */
   int32_t branches;           /* streams the columns of one scan are forked onto, 1..8
                                  (default 8) */
+  int32_t walk_window;        /* staging depth of the page walks: bytes of each of the two
+                                 shared-memory chain windows a walking block streams its
+                                 page through; 0 = chosen by page count (default), else a
+                                 power of two in 4096..65536 */
+  int32_t snappy_block_kib;   /* compressed data pages of at least this many KiB are
+                                 decompressed by a block of 8 warps each, smaller ones by one
+                                 warp (dictionary pages always by a block); 1..1048576
+                                 (default 256) */
+  int32_t staged_expand;      /* 1: REQUIRED fixed-width dictionary columns take the staged
+                                 expansion (index bytes bulk-copied to shared memory); 0: the
+                                 general warp decode (default 1) */
+  int32_t reserved;           /* 0 */
 } pq_tuning;
 
 /* Errors: PQ_ERR_INVALID_ARG (NULL, or a knob out of range). */

@@ -1,10 +1,15 @@
 """Autotuner for the batched scan's knobs (``pq_tuning`` in include/pq.h).
 
-The knobs set scheduling granularity:
+The knobs set scheduling granularity, block sizes and staging depth:
 - rows per work item (pages without definition levels, and pages with
-  them);
+  them): how much of a page one warp takes;
 - resident CTAs per SM of the expansion kernels;
-- how many streams one scan's columns are forked onto.
+- how many streams one scan's columns are forked onto;
+- the staging depth of the page walks (bytes per shared-memory chain
+  window);
+- the compressed page size from which a block of 8 warps, rather than one
+  warp, decompresses a Snappy page;
+- whether dictionary columns take the staged (shared-memory) expansion.
 
 The paper's Section 3 (Insight 1) ties a GPU reader's parallelism to its
 page count. Here parallelism comes from work items, so the best item size
@@ -22,13 +27,17 @@ from typing import Callable, Dict, List, Tuple
 
 from . import native as N
 
-DEFAULT: Dict[str, int] = {"item_rows": 2048, "item_rows_opt": 512, "expand_ctas_per_sm": 0, "branches": 8}
+DEFAULT: Dict[str, int] = {"item_rows": 2048, "item_rows_opt": 512, "expand_ctas_per_sm": 0, "branches": 8,
+                           "walk_window": 0, "snappy_block_kib": 256, "staged_expand": 1}
 
 CANDIDATES: Dict[str, List[int]] = {
     "item_rows": [1024, 2048, 4096, 8192],
     "item_rows_opt": [256, 512],
     "expand_ctas_per_sm": [0, 2],
     "branches": [4, 8],
+    "walk_window": [0, 8192, 32768],
+    "snappy_block_kib": [64, 256, 1024],
+    "staged_expand": [0, 1],
 }
 
 

@@ -89,7 +89,8 @@ void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, int max_s
                  DictDev* dicts, int n_sms, DevStatus* st, cudaStream_t s);
 // Launches over sub-ranges (one output column's share of the plan).
 // levels: the pages have definition levels (their walks use jump tables)
-void launch_walk(const DecodeArgs& a, int wbegin, int n, int n_sms, bool levels, cudaStream_t s);
+// window: bytes per chain window (0: chosen by page count)
+void launch_walk(const DecodeArgs& a, int wbegin, int n, int n_sms, bool levels, uint32_t window, cudaStream_t s);
 void launch_delta_bases(const DecodeArgs& a, int dbegin, int n, int max_regions, cudaStream_t s);
 void launch_expand(const DecodeArgs& a, int ibegin, int n, int cidx, int n_sms, int ctas_per_sm, cudaStream_t s);
 // REQUIRED fixed-width columns with dictionary pages: items staged in shared

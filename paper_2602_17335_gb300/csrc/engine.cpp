@@ -219,7 +219,10 @@ pq_status pq_ctx_set_tuning(pq_ctx* ctx, const pq_tuning* t) {
   if (!ctx || !t) return PQ_ERR_INVALID_ARG;
   if (t->item_rows < 256 || t->item_rows > 65536 || t->item_rows % 32 || t->item_rows_opt < 32 ||
       t->item_rows_opt > pqi::ITEM_ROWS_OPT || t->item_rows_opt % 32 || t->expand_ctas_per_sm < 0 ||
-      t->branches < 1 || t->branches > pq_ctx::kBranches)
+      t->branches < 1 || t->branches > pq_ctx::kBranches ||
+      (t->walk_window != 0 && (t->walk_window < 4096 || t->walk_window > 65536 ||
+                               (t->walk_window & (t->walk_window - 1)))) ||
+      t->snappy_block_kib < 1 || t->snappy_block_kib > (1 << 20) || (t->staged_expand != 0 && t->staged_expand != 1))
     return fail(ctx, PQ_ERR_INVALID_ARG, "pq_ctx_set_tuning: knob out of range");
   ctx->tuning = *t;
   return PQ_OK;
@@ -728,7 +731,7 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
   plan->n_rows = n_rows;
   const bool plain = (flags & PQ_SCAN_PLAIN) != 0;
   plan->tuning = ctx->tuning;
-  plan->staged_expand = !env_flag("PQ_NO_STAGED_EXPAND");
+  plan->staged_expand = plan->tuning.staged_expand && !env_flag("PQ_NO_STAGED_EXPAND");
   const int64_t item_rows_max = plan->tuning.item_rows;
   uint64_t scratch = 0;
   uint64_t tc_pool = 0;               // DELTA_BYTE_ARRAY pool bytes
@@ -1294,10 +1297,13 @@ static void enqueue_transcode(pq_plan* plan, int begin, int n, const pqi::Decode
                         plan->tc_pool_bytes, plan->d_counter, a.st, s);
 }
 
-// Compressed data pages of at least this many bytes are decompressed by a
-// block of 8 warps each (long literals copied by all of them); smaller ones
-// by one warp each.  Dictionary pages always take a block.
-constexpr uint32_t kCoopSnappyBytes = 256 * 1024;
+// Compressed data pages of at least this many bytes (the tuning's
+// snappy_block_kib) are decompressed by a block of 8 warps each (long
+// literals copied by all of them); smaller ones by one warp each.
+// Dictionary pages always take a block.
+static uint32_t coop_snappy_bytes(const pq_plan* plan) {
+  return static_cast<uint32_t>(std::min<int64_t>(int64_t(plan->tuning.snappy_block_kib) * 1024, 0xffffffffll));
+}
 
 // Decompression of jobs [jobs, jobs + n): the Snappy kernel takes the Snappy
 // pages, the Zstandard kernel (launched when the plan has any) the others.
@@ -1346,11 +1352,11 @@ static void enqueue_column(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, b
     pqi::launch_dict(plan->d_dict_jobs + cw.dict_begin, cw.dict_n, cw.max_fixed_dict, cw.max_str_regions,
                      pqi::DictScratch{plan->d_sregs, plan->d_slists}, plan->idx->d_dicts, ctx->n_sms, a.st, s);
   if (cw.snap_data_n)
-    launch_decompress(plan, plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, cw.snap_data_max >= kCoopSnappyBytes,
+    launch_decompress(plan, plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, cw.snap_data_max >= coop_snappy_bytes(plan),
                       a.st, s);
   enqueue_transcode(plan, cw.tc_begin, cw.tc_n, a, s);
   const auto& col = plan->outcols[oc];
-  pqi::launch_walk(a, cw.walk_begin, cw.walk_n, ctx->n_sms, col.optional != 0, s);
+  pqi::launch_walk(a, cw.walk_begin, cw.walk_n, ctx->n_sms, col.optional != 0, plan->tuning.walk_window, s);
   pqi::launch_delta_bases(a, cw.delta_begin, cw.delta_n, cw.max_regions, s);
   launch_column_expand(plan, oc, a, s);
   if (col.ptype == pqi::T_BYTE_ARRAY)
@@ -1394,7 +1400,7 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
       for (int p = first; p < first + n; ++p)
         if (job + nj < plan->snappy_data.size() && plan->snappy_data[job + nj].page == static_cast<int32_t>(plan->pps[p].page))
           ++nj;
-      if (nj) launch_decompress(plan, plan->d_snappy + job, nj, plan->snap_data_max >= kCoopSnappyBytes, a.st, s);
+      if (nj) launch_decompress(plan, plan->d_snappy + job, nj, plan->snap_data_max >= coop_snappy_bytes(plan), a.st, s);
       job += nj;
       int ntc = 0;
       while (tcj + ntc < plan->tc_jobs.size() && plan->tc_jobs[tcj + ntc].pp < static_cast<uint32_t>(first + n)) ++ntc;
@@ -1413,7 +1419,7 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
         launch_decompress(plan, plan->d_snappy + n_data_jobs + cw.snap_dict_begin, cw.snap_dict_n, true, a.st, s);
       if (cw.snap_data_n)
         launch_decompress(plan, plan->d_snappy + cw.snap_data_begin, cw.snap_data_n,
-                          cw.snap_data_max >= kCoopSnappyBytes, a.st, s);
+                          cw.snap_data_max >= coop_snappy_bytes(plan), a.st, s);
       enqueue_transcode(plan, cw.tc_begin, cw.tc_n, a, s);
     }
     mark(2);
@@ -1426,7 +1432,8 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
     mark(3);
     for (int oc = 0; oc < ncols; ++oc) {
       const auto& cw = plan->colwork[oc];
-      pqi::launch_walk(a, cw.walk_begin, cw.walk_n, ctx->n_sms, plan->outcols[oc].optional != 0, s);
+      pqi::launch_walk(a, cw.walk_begin, cw.walk_n, ctx->n_sms, plan->outcols[oc].optional != 0,
+                       plan->tuning.walk_window, s);
       pqi::launch_delta_bases(a, cw.delta_begin, cw.delta_n, cw.max_regions, s);
     }
     mark(4);

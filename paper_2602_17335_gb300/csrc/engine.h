@@ -50,7 +50,7 @@ struct pq_ctx {
   static constexpr int kBranches = 8;
   cudaStream_t branch[kBranches] = {};  // per-column branches of a scan
   std::string last_error;
-  pq_tuning tuning{pqi::ITEM_ROWS, pqi::ITEM_ROWS_OPT, 0, kBranches};
+  pq_tuning tuning{pqi::ITEM_ROWS, pqi::ITEM_ROWS_OPT, 0, kBranches, 0, 256, 1, 0};
   pqe::DevPool pool;
   pqe::Pinned tail;     // footer staging
   std::mutex mu;        // serialises use from the serving thread and the API

@@ -3468,12 +3468,13 @@ int expand_blocks_per_sm() {
   return g_exp_bps;
 }
 
-void launch_walk(const DecodeArgs& a, int wbegin, int n, int n_sms, bool levels, cudaStream_t s) {
+void launch_walk(const DecodeArgs& a, int wbegin, int n, int n_sms, bool levels, uint32_t window, cudaStream_t s) {
   if (n <= 0) return;
   walk_blocks_per_sm();  // sets the shared-memory attributes
   // few pages (long chains each): larger windows, fewer refills on the
   // chain's path; many pages: more resident walkers
-  const uint32_t cap = n <= n_sms ? CWIN_MAX : (n <= 2 * n_sms ? CWIN_MAX / 2 : CWIN);
+  const uint32_t cap = window ? (window < CWIN_MAX ? window : CWIN_MAX)
+                              : (n <= n_sms ? CWIN_MAX : (n <= 2 * n_sms ? CWIN_MAX / 2 : CWIN));
   // level walks: smaller chain windows, so that the jump tables leave room
   // for as many resident walkers
   const uint32_t jw = levels ? JW : 0u;

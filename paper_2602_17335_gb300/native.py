@@ -90,7 +90,8 @@ class pq_write_column(C.Structure):
 
 class pq_tuning(C.Structure):
     _fields_ = [("item_rows", C.c_int32), ("item_rows_opt", C.c_int32), ("expand_ctas_per_sm", C.c_int32),
-                ("branches", C.c_int32)]
+                ("branches", C.c_int32), ("walk_window", C.c_int32), ("snappy_block_kib", C.c_int32),
+                ("staged_expand", C.c_int32), ("reserved", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -348,8 +349,10 @@ def pq_serve_destroy(srv):
     lib().pq_serve_destroy(srv)
 
 
-def pq_ctx_set_tuning(ctx, item_rows=2048, item_rows_opt=512, expand_ctas_per_sm=0, branches=8):
-    t = pq_tuning(item_rows, item_rows_opt, expand_ctas_per_sm, branches)
+def pq_ctx_set_tuning(ctx, item_rows=2048, item_rows_opt=512, expand_ctas_per_sm=0, branches=8, walk_window=0,
+                      snappy_block_kib=256, staged_expand=1):
+    t = pq_tuning(item_rows, item_rows_opt, expand_ctas_per_sm, branches, walk_window, snappy_block_kib,
+                  staged_expand, 0)
     check(lib().pq_ctx_set_tuning(ctx, C.byref(t)), ctx)
 
 
@@ -357,7 +360,8 @@ def pq_ctx_get_tuning(ctx):
     t = pq_tuning()
     check(lib().pq_ctx_get_tuning(ctx, C.byref(t)), ctx)
     return {"item_rows": t.item_rows, "item_rows_opt": t.item_rows_opt,
-            "expand_ctas_per_sm": t.expand_ctas_per_sm, "branches": t.branches}
+            "expand_ctas_per_sm": t.expand_ctas_per_sm, "branches": t.branches, "walk_window": t.walk_window,
+            "snappy_block_kib": t.snappy_block_kib, "staged_expand": t.staged_expand}
 
 
 def pq_batch_create(ctx, plans, outs_per_plan, flags=0):

@@ -18,7 +18,8 @@ def _run(cost, monkeypatch, rounds=1):
 
 
 def test_finds_the_separable_optimum(monkeypatch):
-    target = {"item_rows": 4096, "item_rows_opt": 256, "expand_ctas_per_sm": 2, "branches": 4}
+    target = {"item_rows": 4096, "item_rows_opt": 256, "expand_ctas_per_sm": 2, "branches": 4,
+              "walk_window": 32768, "snappy_block_kib": 64, "staged_expand": 0}
 
     def cost(t):
         return 1.0 + sum(abs(t[k] - target[k]) / (1 + target[k]) for k in target)
