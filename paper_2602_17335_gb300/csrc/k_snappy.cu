@@ -187,94 +187,15 @@ __device__ __forceinline__ void ring_fill(uint8_t* ring, uint32_t pos0, const ui
   for (uint32_t i = head + (nv << 4) + lane; i < n; i += 32) ring[(pos0 + i) & RM] = __ldg(src + i);
 }
 
-__device__ __forceinline__ void coop_bar() { asm volatile("bar.sync 1, %0;" ::"r"(32 * 8) : "memory"); }
-
-// A cooperative request from warp 0 to the other warps of its block.
+// A cooperative copy request from warp 0 to the other warps of its block.
 struct SnCoop {
   uint8_t* dst;
-  const uint8_t* src;  // copy: source; speculative parse: the page's input
-  uint32_t len;        // copy: bytes
-  uint32_t mode;       // 0 the page is done, 1 copy, 2 speculative parse of window `wb`
-  uint32_t w0, n0;     // speculative parse: the window's input offset (mod 2^32) and bytes
-  uint32_t in_len;
-  int32_t wb;
+  const uint8_t* src;
+  uint32_t len;  // 0: the page is done
+  uint32_t pad;
 };
 
-// Element headers found by the block's speculative parse of one input
-// window, by window offset: the next header's input offset (kUnk: not
-// parsed), kind | length << 2, and the argument (literal: input offset of
-// its bytes; copy: back offset).
-constexpr uint32_t kUnk = 0xffffffffu;
-struct SnRec {
-  uint32_t next[kWin];
-  uint32_t kl[kWin];
-  uint32_t arg[kWin];
-};
-
-// Every thread of the block: parse chains from 256 evenly spaced starting
-// bytes of the window (each a guess at a header), recording each header
-// parsed.  The element following a header depends only on the header's
-// position, so a record is right wherever it was reached from; chains that
-// started inside literal bytes usually land on the true chain after a few
-// elements, and from there the records cover it.
-__device__ void spec_parse(const SnCoop& c, const uint8_t* win, SnRec& rec, int t) {
-  const uint32_t n0 = c.n0;
-  for (uint32_t q = t; q < n0; q += 256) rec.next[q] = kUnk;
-  coop_bar();
-  const uint32_t per = (n0 + 255) / 256;
-  const uint32_t start = t * per;
-  const uint32_t end = start + per + 32 < n0 ? start + per + 32 : n0;
-  const bool tail = c.w0 + n0 >= c.in_len;  // the window reaches the input's end
-  uint32_t q = start;
-  for (int steps = 0; q < end && steps < 64; ++steps) {
-    if (rec.next[q] != kUnk) break;  // parsed already: the chain goes on from there
-    if (q + 5 > n0 && !tail) break;
-    const uint32_t pa = c.w0 + q;  // input offset of the header
-    if (pa >= c.in_len) break;
-    const uint8_t* h = win + q;
-    const uint32_t tag = h[0], x1 = h[1], x2 = h[2], x3 = h[3], x4 = h[4];
-    const uint32_t kind = tag & 3, left = c.in_len - pa - 1;
-    uint32_t len, arg, hl;
-    if (kind == 0) {
-      const uint32_t l = tag >> 2;
-      if (l < 60) {
-        len = l + 1;
-        hl = 1;
-      } else {
-        const uint32_t nb = l - 59;
-        if (nb > left) break;
-        const uint32_t v = x1 | (x2 << 8) | (x3 << 16) | (x4 << 24);
-        const uint32_t vm = nb == 4 ? v : (v & ((1u << (8 * nb)) - 1u));
-        if (vm >= 0x3fffffffu) break;
-        len = vm + 1;
-        hl = 1 + nb;
-      }
-      if (len > c.in_len - pa - hl) break;
-      arg = pa + hl;
-    } else if (kind == 1) {
-      if (left < 1) break;
-      len = 4 + ((tag >> 2) & 7);
-      arg = ((tag >> 5) << 8) | x1;
-      hl = 2;
-    } else if (kind == 2) {
-      if (left < 2) break;
-      len = (tag >> 2) + 1;
-      arg = x1 | (x2 << 8);
-      hl = 3;
-    } else {
-      if (left < 4) break;
-      len = (tag >> 2) + 1;
-      arg = x1 | (x2 << 8) | (x3 << 16) | (x4 << 24);
-      hl = 5;
-    }
-    const uint32_t nx = pa + hl + (kind == 0 ? len : 0u);
-    rec.kl[q] = kind | (len << 2);
-    rec.arg[q] = arg;
-    rec.next[q] = nx;
-    q = nx - c.w0;
-  }
-}
-
+__device__ __forceinline__ void coop_bar() { asm volatile("bar.sync 1, %0;" ::"r"(32 * 8) : "memory"); }
 
 // Slice w of 8 of a copy (16-byte aligned destination boundaries).
 __device__ __forceinline__ void coop_slice(const SnCoop& c, int w, int lane) {
@@ -295,7 +216,6 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
   const int lane = threadIdx.x & 31;
   SnWarp& sw = reinterpret_cast<SnWarp*>(sn_smem)[kCoop ? 0 : threadIdx.x >> 5];
   SnCoop& cq = *reinterpret_cast<SnCoop*>(sn_smem + sizeof(SnWarp) * (kCoop ? 1 : kSnappyWarps));
-  SnRec& rec = *reinterpret_cast<SnRec*>(sn_smem + sizeof(SnWarp) + ((sizeof(SnCoop) + 15) & ~size_t(15)));
   const int wid = kCoop ? blockIdx.x : (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = kCoop ? gridDim.x : (gridDim.x * blockDim.x) >> 5;
   if (kCoop && threadIdx.x >= 32) {
@@ -304,11 +224,8 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
       for (;;) {
         coop_bar();
         const SnCoop c = cq;
-        if (c.mode == 0) break;
-        if (c.mode == 1)
-          coop_slice(c, threadIdx.x >> 5, lane);
-        else
-          spec_parse(c, reinterpret_cast<SnWarp*>(sn_smem)->win[c.wb], rec, threadIdx.x);
+        if (c.len == 0) break;
+        coop_slice(c, threadIdx.x >> 5, lane);
         coop_bar();
       }
     }
@@ -325,7 +242,7 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
   constexpr uint32_t RM = kRing - 1;
   auto page_done = [&]() {
     if (kCoop) {
-      if (lane == 0) cq.mode = 0;
+      if (lane == 0) cq.len = 0;
       __syncwarp();
       coop_bar();
     }
@@ -375,35 +292,10 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
     }
     uint32_t ip = static_cast<uint32_t>(pl);
     uint32_t op = 0;
-    uint32_t spec_w = kUnk;            // window the records describe (lane 0)
-    const uint8_t* spec_b = nullptr;
     bad = __shfl_sync(0xffffffffu, bad, 0);
     // each element consumes >= 2 input bytes, so in_len bounds the batches
     for (uint32_t guard = 0; guard <= in_len && ip < in_len && !bad; ++guard) {
       int n_el = 0;
-      if (kCoop) {
-        // the batch's window (switched now when ip left window 0), parsed
-        // speculatively by the whole block when it is new
-        int need = 0;
-        if (lane == 0) {
-          const bool here = ip - sin.w0 < sin.n0 && (ip - sin.w0 + 5 <= sin.n0 || sin.w0 + sin.n0 >= in_len);
-          if (!here && !sn_ensure(sin, ip)) bad = 2;
-          need = !bad && (sin.w0 != spec_w || sin.b0 != spec_b);
-          if (need) cq = SnCoop{nullptr, in, 0, 2, sin.w0, sin.n0, in_len, sin.b0 == sw.win[1] ? 1 : 0};
-        }
-        bad = __shfl_sync(0xffffffffu, bad, 0);
-        if (bad) break;
-        if (__shfl_sync(0xffffffffu, need, 0)) {
-          __syncwarp();
-          coop_bar();
-          spec_parse(cq, sw.win[__shfl_sync(0xffffffffu, lane == 0 ? cq.wb : 0, 0)], rec, threadIdx.x);
-          coop_bar();
-          if (lane == 0) {
-            spec_w = sin.w0;
-            spec_b = sin.b0;
-          }
-        }
-      }
       if (lane == 0) {
         uint32_t p = ip, o = op, bo = 0;
         for (int e = 0; e < 32 && p < in_len; ++e) {
@@ -412,20 +304,11 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
           const bool here = p - sin.w0 < sin.n0 && (p - sin.w0 + 5 <= sin.n0 || sin.w0 + sin.n0 >= in_len);
           if (!here && e > 0) break;
           if (!sn_ensure(sin, p)) { bad = 2; break; }
-          uint32_t kind, len, arg;
-          if (kCoop && sin.w0 == spec_w && sin.b0 == spec_b && rec.next[p - sin.w0] != kUnk) {
-            // found by the speculative parse
-            const uint32_t qq = p - sin.w0, kl = rec.kl[qq];
-            kind = kl & 3;
-            len = kl >> 2;
-            arg = rec.arg[qq];
-            p = rec.next[qq];
-          } else {
           // the tag and the 4 bytes after it (slack past the input end is never used)
           const uint8_t* q = sin.b0 + (p - sin.w0);
           const uint32_t tag = q[0], x1 = q[1], x2 = q[2], x3 = q[3], x4 = q[4];
           ++p;
-          kind = tag & 3;
+          uint32_t kind = tag & 3, len, arg;
           if (kind == 0) {
             const uint32_t l = tag >> 2;
             if (l < 60) {
@@ -457,7 +340,6 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
             len = (tag >> 2) + 1;
             arg = x1 | (x2 << 8) | (x3 << 16) | (x4 << 24);
             p += 4;
-          }
           }
           if (len > out_len - o || (kind != 0 && (arg == 0 || arg > o))) { bad = 1; break; }
           const bool inwin = kind == 0 && len <= kMidLit && arg - sin.w0 + len <= sin.n0;
@@ -559,10 +441,10 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
         const uint32_t el = __shfl_sync(0xffffffffu, len, e);
         const uint32_t ea = __shfl_sync(0xffffffffu, arg, e), eo = __shfl_sync(0xffffffffu, o0, e);
         if (kCoop && el >= kCoopLit) {
-          if (lane == 0) cq = SnCoop{out + eo, in + ea, el, 1, 0, 0, 0, 0};
+          if (lane == 0) cq = SnCoop{out + eo, in + ea, el, 0};
           __syncwarp();
           coop_bar();
-          coop_slice(SnCoop{out + eo, in + ea, el, 1, 0, 0, 0, 0}, 0, lane);
+          coop_slice(SnCoop{out + eo, in + ea, el, 0}, 0, lane);
           coop_bar();
         } else {
           warp_copy<true>(out + eo, in + ea, el, lane);
@@ -596,7 +478,7 @@ void launch_snappy(const SnappyJob* jobs, int n_jobs, int n_sms, DevStatus* st, 
   if (n_jobs <= 0) return;
   static bool attr = false;
   constexpr uint32_t smem_w = kSnappyWarps * sizeof(SnWarp) + sizeof(SnCoop);
-  constexpr uint32_t smem_c = sizeof(SnWarp) + ((sizeof(SnCoop) + 15) & ~size_t(15)) + sizeof(SnRec);
+  constexpr uint32_t smem_c = sizeof(SnWarp) + sizeof(SnCoop);
   if (!attr) {
     cudaFuncSetAttribute(k_snappy<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_w);
     cudaFuncSetAttribute(k_snappy<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c);
