@@ -176,6 +176,75 @@ __device__ bool oi_locations_fast(const uint8_t* p, const uint8_t* end, int c, c
   return true;
 }
 
+// The usual serialization again, for an OffsetIndex larger than the
+// warp's shared-memory buffer: the warp streams it through the buffer
+// (lanes copy, lane 0 parses whole page-location structs, each at most 34
+// bytes, then the unparsed rest moves to the front of the next window).
+// False (nothing assumed written) when the bytes take another form.
+__device__ bool oi_locations_windowed(uint8_t* buf, const uint8_t* oi, uint32_t oi_len, int c, const ChunkDev& ch,
+                                      int64_t file_off, PageDev* pages, int lane) {
+  constexpr uint32_t kStruct = 34;  // 0x16 + 10-byte varint + 0x15 + 5 + 0x16 + 10 + stop
+  const uint32_t slot = ch.dict_page >= 0 ? 1u : 0u;
+  uint32_t pos = 0;   // OI bytes consumed
+  uint64_t n = 0, i = 0;
+  int state = 0;      // 0 list header next, 1 structs, 2 done, 3 not the usual form
+  for (uint32_t guard = 0; guard < oi_len + 2 && state < 2; ++guard) {
+    const uint32_t wlen = oi_len - pos < OI_SMEM ? oi_len - pos : OI_SMEM;
+    for (uint32_t k = lane; k < wlen; k += 32) buf[k] = __ldg(oi + pos + k);
+    __syncwarp();
+    if (lane == 0) {
+      const uint8_t* p = buf;
+      const uint8_t* end = buf + wlen;
+      const bool last = pos + wlen == oi_len;
+      auto varint = [&](uint64_t* v) -> bool {
+        uint64_t x = 0;
+        for (int b = 0; b < 10 && p < end; ++b) {
+          const uint32_t y = *p++;
+          x |= static_cast<uint64_t>(y & 0x7f) << (7 * b);
+          if (!(y & 0x80)) {
+            *v = x;
+            return true;
+          }
+        }
+        return false;
+      };
+      if (state == 0) {
+        if (end - p < 2 || p[0] != 0x19 || (p[1] & 15) != 12) {
+          state = 3;
+        } else {
+          n = p[1] >> 4;
+          p += 2;
+          if (n == 15 && !varint(&n)) state = 3;
+          else if (n != ch.oi_pages) state = 3;
+          else state = 1;
+        }
+      }
+      while (state == 1 && i < n && (last || end - p >= static_cast<int64_t>(kStruct))) {
+        uint64_t off, skip;
+        if (p >= end || *p++ != 0x16 || !varint(&off)) { state = 3; break; }
+        if (p >= end || *p++ != 0x15 || !varint(&skip)) { state = 3; break; }
+        if (p >= end || *p++ != 0x16 || !varint(&skip)) { state = 3; break; }
+        if (p >= end || *p++ != 0x00) { state = 3; break; }
+        const int64_t rel = static_cast<int64_t>(off >> 1) ^ -static_cast<int64_t>(off & 1);
+        const int64_t r = rel - file_off;
+        if (r < 0 || static_cast<uint64_t>(r) >= ch.size) { state = 3; break; }
+        PageDev d{};
+        d.offset = static_cast<uint64_t>(r);
+        d.chunk = static_cast<uint32_t>(c);
+        pages[ch.page_begin + slot + i] = d;
+        ++i;
+      }
+      if (state == 1 && i == n) state = 2;
+      else if (state == 1 && last) state = 3;
+      pos += static_cast<uint32_t>(p - buf);
+    }
+    __syncwarp();
+    state = __shfl_sync(0xffffffffu, state, 0);
+    pos = __shfl_sync(0xffffffffu, pos, 0);
+  }
+  return state == 2;
+}
+
 __global__ void __launch_bounds__(32 * OI_WARPS) k_index_oi_locations(const ChunkDev* __restrict__ chunks,
                                                                       int n_chunks,
                                                                       const int64_t* __restrict__ chunk_file_off,
@@ -196,8 +265,8 @@ __global__ void __launch_bounds__(32 * OI_WARPS) k_index_oi_locations(const Chun
     __syncwarp();
     if (lane == 0 && !oi_locations_fast(buf[w], buf[w] + ch.oi_len, c, ch, chunk_file_off[c], pages))
       oi_locations(TRdT<false>{buf[w], buf[w] + ch.oi_len, false}, c, ch, chunk_file_off[c], pages, st);
-  } else if (lane == 0) {
-    oi_locations(TRd{ch.oi_base, ch.oi_base + ch.oi_len, false}, c, ch, chunk_file_off[c], pages, st);
+  } else if (!oi_locations_windowed(buf[w], ch.oi_base, ch.oi_len, c, ch, chunk_file_off[c], pages, lane)) {
+    if (lane == 0) oi_locations(TRd{ch.oi_base, ch.oi_base + ch.oi_len, false}, c, ch, chunk_file_off[c], pages, st);
   }
 }
 

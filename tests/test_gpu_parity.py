@@ -440,3 +440,32 @@ def test_strings_without_size_statistics(eng, enc):
         assert R.parse_footer(data).raw is not None
         _roundtrip(eng, data)
         _roundtrip(eng, data, row_begin=5_555, row_count=17_000)
+
+
+def test_large_offset_index(eng):
+    """Chunks of thousands of small pages: their OffsetIndex is larger than
+    the index kernel's shared-memory buffer and streams through it in
+    windows.  The page table equals the oracle's walk and the scan the
+    oracle's reading."""
+    from paper_2602_17335_gb300 import native as N
+    n = 200_000
+    rng = np.random.default_rng(8)
+    cols = [synth.ColumnData("a", "INT64", rng.integers(-10**12, 10**12, n).astype(np.int64)),
+            synth.ColumnData("b", "INT32", rng.integers(0, 50, n).astype(np.int32))]
+    spec = synth.TableSpec(n, 1024, [synth.ColumnSpec("PLAIN"), synth.ColumnSpec("RLE_DICTIONARY")])
+    data = W.write_file(synth.Table(cols), spec)
+    info = R.parse_footer(data)
+    assert any(ch.offset_index[1] > 8192 for ch in info.chunks)
+    idx = eng.index([to_dev(data)])
+    assert N.pq_index_get_info(idx).used_offset_index == 1
+    got = [(g.header_offset, g.page_type, g.num_values, g.first_row) for g in N.pq_index_copy_pages(idx)]
+    exp = []
+    for ch in info.chunks:
+        row = 0
+        for p in R.chunk_pages(data, ch):
+            exp.append((p.offset, p.page_type, p.num_values, 0 if p.page_type == 2 else row))
+            if p.page_type != 2:
+                row += p.num_values
+    assert got == exp
+    N.pq_free_index(idx)
+    _roundtrip(eng, data)
