@@ -2588,7 +2588,7 @@ __global__ void __launch_bounds__(EXP_THREADS, 4) k_expand(DecodeArgs a, int ibe
 // of pages that are not dictionary encoded, take the general warp decode.
 constexpr int SX_WARPS = 8;
 constexpr int SX_THREADS = 32 * SX_WARPS;
-constexpr int SX_SPAN = 64;
+constexpr int SX_SPAN = 32;
 constexpr int SX_MAXRUNS = 96;
 constexpr uint32_t SX_DICT_MAX = 48 * 1024;
 
