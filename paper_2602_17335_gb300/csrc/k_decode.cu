@@ -3044,15 +3044,6 @@ __device__ __forceinline__ void stage_from_raw(uint8_t* d, const uint8_t* raw, i
   }
 }
 
-// Word i (-1..12) of a string held in 12 registers (word -1 and words past
-// the string read as 0): a select chain, so the registers stay registers.
-__device__ __forceinline__ uint32_t str_word(const uint32_t (&r)[12], int i) {
-  uint32_t v = 0;
-#pragma unroll
-  for (int k = 0; k < 12; ++k) v = i == k ? r[k] : v;
-  return v;
-}
-
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
@@ -3076,7 +3067,7 @@ struct StrWarpSmem {
 };
 constexpr int STR_SMEM = 8 * sizeof(StrWarpSmem);
 
-__global__ void __launch_bounds__(256, 2) k_str_copy(DecodeArgs a, int c) {
+__global__ void __launch_bounds__(256, 4) k_str_copy(DecodeArgs a, int c) {
   extern __shared__ __align__(16) uint8_t str_smem[];
   StrWarpSmem& ws = reinterpret_cast<StrWarpSmem*>(str_smem)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
@@ -3119,45 +3110,17 @@ __global__ void __launch_bounds__(256, 2) k_str_copy(DecodeArgs a, int c) {
       for (int cc = 0; cc < 4; ++cc) {
         const int r0 = g0 + cc * 64;
         if (r0 >= it.nrows) break;
-        // Strings of a padded dictionary (16-byte aligned, at most 48 bytes)
-        // come straight into registers; others through the source slots by
-        // asynchronous copies, fetched together.
-        bool regok = true;
+        // source spans of the lane's two strings, fetched together
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
           const uint32_t len = static_cast<uint32_t>(ent[2 * cc + t]);
-          const uintptr_t src = reinterpret_cast<uintptr_t>(cbase + (ent[2 * cc + t] >> 32));
-          regok &= len == 0 || (len <= 48 && (src & 15) == 0);
-        }
-        const bool use_reg = __all_sync(0xffffffffu, regok);
-        uint32_t RA[12], RB[12];
-        if (use_reg) {
-#pragma unroll
-          for (int t = 0; t < 2; ++t) {
-            const uint32_t len = static_cast<uint32_t>(ent[2 * cc + t]);
-            const uint4* sv = reinterpret_cast<const uint4*>(cbase + (ent[2 * cc + t] >> 32));
-            uint32_t* R = t ? RB : RA;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              const uint4 v = static_cast<uint32_t>(16 * k) < len ? __ldg(sv + k) : make_uint4(0, 0, 0, 0);
-              R[4 * k] = v.x;
-              R[4 * k + 1] = v.y;
-              R[4 * k + 2] = v.z;
-              R[4 * k + 3] = v.w;
-            }
-          }
-        } else {
-#pragma unroll
-          for (int t = 0; t < 2; ++t) {
-            const uint32_t len = static_cast<uint32_t>(ent[2 * cc + t]);
-            const uint8_t* src = cbase + (ent[2 * cc + t] >> 32);
-            const uint32_t p = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 15);
-            const uint32_t nb = (p + len + 15) >> 4;
-            if (len && nb <= STR_RAW_BLK) {
-              const uint8_t* sa = src - p;
-              uint4* slot = ws.raw + (t * 32 + lane) * STR_SLOT;
-              for (uint32_t b = 0; b < nb; ++b) cp_async16(slot + b, sa + 16 * b);
-            }
+          const uint8_t* src = cbase + (ent[2 * cc + t] >> 32);
+          const uint32_t p = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 15);
+          const uint32_t nb = (p + len + 15) >> 4;
+          if (len && nb <= STR_RAW_BLK) {
+            const uint8_t* sa = src - p;
+            uint4* slot = ws.raw + (t * 32 + lane) * STR_SLOT;
+            for (uint32_t b = 0; b < nb; ++b) cp_async16(slot + b, sa + 16 * b);
           }
         }
         const uint32_t lena = static_cast<uint32_t>(ent[2 * cc]), lenb = static_cast<uint32_t>(ent[2 * cc + 1]);
@@ -3189,63 +3152,7 @@ __global__ void __launch_bounds__(256, 2) k_str_copy(DecodeArgs a, int c) {
             const bool has = ra < it.nrows;
             const bool good = !has || (lena + lenb >= 4 && ((pa + lena + 15) >> 4) <= STR_RAW_BLK &&
                                        ((pb + lenb + 15) >> 4) <= STR_RAW_BLK);
-            if (use_reg && __all_sync(0xffffffffu, !has || lena + lenb >= 4)) {
-              // the slot fast path with the strings in registers (both start
-              // on a 16-byte boundary, so byte k of a string is byte k & 3
-              // of its word k >> 2)
-              const int sa = static_cast<int>(a0 + rel), ea = sa + static_cast<int>(lena),
-                        eb = ea + static_cast<int>(lenb);
-              auto regw = [](const uint32_t (&R)[12], int off) -> uint32_t {  // 4 bytes at off >= -3
-                const int q = off >> 2;
-                return __funnelshift_r(str_word(R, q), str_word(R, q + 1), static_cast<uint32_t>(off & 3) * 8);
-              };
-              auto bmask = [](int n) -> uint32_t {
-                return n <= 0 ? 0u : (n >= 4 ? 0xffffffffu : ((1u << (8 * n)) - 1u));
-              };
-              auto mix = [&](int w, uint32_t nxt) -> uint32_t {
-                const int x = 4 * w;
-                const uint32_t ma = bmask(ea - x), mab = bmask(eb - x);
-                const uint32_t va = x < ea ? regw(RA, x - sa) : 0u;
-                const uint32_t vb = (x + 4 > ea && x < eb) ? regw(RB, x - ea) : 0u;
-                return (va & ma) | (vb & mab & ~ma) | (nxt & ~mab);
-              };
-              const uint32_t head = (has && (sa & 3)) ? (mix(sa >> 2, 0u) & ~bmask(sa & 3)) : 0u;
-              uint32_t nxt = __shfl_down_sync(0xffffffffu, head, 1);
-              if (lane == 31) nxt = 0;
-              if (has) {
-                uint32_t* sw = reinterpret_cast<uint32_t*>(sbuf);
-                int w = (lane == 0) ? (sa >> 2) : ((sa + 3) >> 2);
-                const int wa = ea >> 2, wb = eb >> 2;
-                {
-                  // words wholly inside the first string: word k of them is
-                  // string bytes [o0 + 4k, o0 + 4k + 4), o0 = 4w - sa in -3..3
-                  const int o0 = 4 * w - sa;
-                  const uint32_t sh = static_cast<uint32_t>(o0 & 3) * 8;
-                  const bool back = o0 < 0;  // lane 0 may start a word before its string
-                  const int n = wa - w;
-#pragma unroll
-                  for (int k = 0; k < 12; ++k) {
-                    if (k < n) {
-                      const uint32_t lo = back ? (k ? RA[k - 1] : 0u) : RA[k];
-                      const uint32_t hi = back ? RA[k] : (k < 11 ? RA[k + 1] : 0u);
-                      sw[w + k] = __funnelshift_r(lo, hi, sh);
-                    }
-                  }
-                  if (n > 0) w += n;
-                }
-                if ((ea & 3) && w == wa) sw[w++] = mix(wa, nxt);  // end of the first string
-                {
-                  const int o0 = 4 * w - ea;  // 0..3
-                  const uint32_t sh = static_cast<uint32_t>(o0 & 3) * 8;
-                  const int n = wb - w;
-#pragma unroll
-                  for (int k = 0; k < 12; ++k)
-                    if (k < n) sw[w + k] = __funnelshift_r(RB[k], k < 11 ? RB[k + 1] : 0u, sh);
-                  if (n > 0) w += n;
-                }
-                if ((eb & 3) && w == wb) sw[w] = mix(wb, nxt);  // end of the span
-              }
-            } else if (!use_reg && __all_sync(0xffffffffu, good)) {
+            if (__all_sync(0xffffffffu, good)) {
               const uint32_t* rwa = reinterpret_cast<const uint32_t*>(ws.raw + lane * STR_SLOT);
               const uint32_t* rwb = reinterpret_cast<const uint32_t*>(ws.raw + (32 + lane) * STR_SLOT);
               const int sa = static_cast<int>(a0 + rel), ea = sa + static_cast<int>(lena),
@@ -3312,7 +3219,7 @@ __global__ void __launch_bounds__(256, 2) k_str_copy(DecodeArgs a, int c) {
                 const uint8_t* src = cbase + (ent[2 * cc + t] >> 32);
                 const int p = static_cast<int>(reinterpret_cast<uintptr_t>(src) & 15);
                 uint8_t* d = sbuf + a0 + rel + (t ? lena : 0u);
-                if (!use_reg && ((p + len + 15) >> 4) <= STR_RAW_BLK)
+                if (((p + len + 15) >> 4) <= STR_RAW_BLK)
                   stage_from_raw(d, reinterpret_cast<const uint8_t*>(ws.raw + (t * 32 + lane) * STR_SLOT), p, len);
                 else
                   stage_string(d, src, len);
