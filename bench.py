@@ -322,22 +322,24 @@ class ClockSampler:
 # "roofline_scan" (dram__bytes_read.sum + dram__bytes_write.sum summed over
 # the launch's kernels).  Keyed by the layout; the capture's row count scales
 # the figure to the bench's rows (traffic grows with rows at a fixed layout).
-# `sources` is the digest of the kernel sources the counters were taken on:
-# once they change, the stored figure no longer describes the kernels and the
-# bench reports null.
+# `sources` is the digest of the kernel sources the counters were taken on
+# (the decompression kernels only for the codec that the layout uses, as the
+# others do not run): once they change, the stored figure no longer describes
+# the kernels and the bench reports null.
 TRAFFIC_CAPTURES = {
     # profiles/traffic_eight_column_2p24_1MiB.md
-    "8388608/1048576/UNCOMPRESSED/V1/batched/oi1": {"rows": 16777216, "bytes": 1350668032, "sources": "0c7bc98cd343d414"},
+    "8388608/1048576/UNCOMPRESSED/V1/batched/oi1": {"rows": 16777216, "bytes": 1349700864, "sources": "ed5da2e8d3518248"},
 }
 
-KERNEL_SOURCES = ("k_decode.cu", "k_index.cu", "k_snappy.cu", "k_transcode.cu", "k_zstd.cu", "zstd_dec.cuh",
-                  "dev_util.cuh", "thrift_dev.cuh", "decode_job.h", "pq_internal.h", "snappy_job.h", "engine.cpp")
+KERNEL_SOURCES = ("k_decode.cu", "k_index.cu", "k_transcode.cu", "dev_util.cuh", "thrift_dev.cuh", "decode_job.h",
+                  "pq_internal.h", "snappy_job.h", "engine.cpp")
+CODEC_SOURCES = {"SNAPPY": ("k_snappy.cu",), "ZSTD": ("k_zstd.cu", "zstd_dec.cuh")}
 
 
-def kernel_sources_digest():
+def kernel_sources_digest(codec="UNCOMPRESSED"):
     import hashlib
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in KERNEL_SOURCES + CODEC_SOURCES.get(codec, ()):
         with open(os.path.join(ROOT, "paper_2602_17335_gb300", "csrc", name), "rb") as f:
             h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
@@ -353,7 +355,7 @@ def stored_traffic(a):
     cap = TRAFFIC_CAPTURES.get(traffic_key(a))
     if cap is None:
         return None, "no capture for this layout"
-    if cap["sources"] != kernel_sources_digest():
+    if cap["sources"] != kernel_sources_digest(a.codec):
         return None, "kernels changed since the capture"
     return cap["bytes"] * a.rows / cap["rows"], f"ncu capture at {cap['rows']} rows, scaled by rows"
 
