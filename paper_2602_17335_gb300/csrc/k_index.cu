@@ -84,9 +84,9 @@ __global__ void k_index_walk(const ChunkDev* __restrict__ chunks, int n_chunks, 
 // list {1: offset i64, 2: compressed_page_size i32, 3: first_row_index i64}
 // into the page table's offset field (file offset, rebased to the chunk).
 // Slot 0 of a dictionary chunk is reserved for its dictionary page, which
-// starts at the chunk start.  The warp first copies the chunk's serialized
-// OffsetIndex into shared memory (when it fits), so that the serial parse by
-// lane 0 reads shared rather than global memory.
+// starts at the chunk start.  The usual serialization is parsed by the whole
+// warp from shared memory (oi_locations_tokens); any other form by lane 0
+// with the general Thrift reader.
 constexpr int OI_WARPS = 4;
 constexpr uint32_t OI_SMEM = 8192;  // bytes staged per warp
 
@@ -135,70 +135,92 @@ __device__ void oi_locations(TRdT<kGlobal> r, int c, const ChunkDev& ch, int64_t
 }
 
 // The usual serialization of the OffsetIndex: field 1, a list of n structs,
-// each {1: i64 offset, 2: i32 compressed_page_size, 3: i64
-// first_row_index} with one-byte field headers (0x16, 0x15, 0x16) and a stop
-// byte.  Read straight through; false (nothing assumed written) when the
-// bytes take any other form, which the general parser then handles.
-__device__ bool oi_locations_fast(const uint8_t* p, const uint8_t* end, int c, const ChunkDev& ch, int64_t file_off,
-                                  PageDev* pages) {
-  auto varint = [&](uint64_t* v) -> bool {
-    uint64_t x = 0;
-    for (int i = 0; i < 10 && p < end; ++i) {
-      const uint32_t b = *p++;
-      x |= static_cast<uint64_t>(b & 0x7f) << (7 * i);
-      if (!(b & 0x80)) {
-        *v = x;
-        return true;
-      }
-    }
-    return false;
-  };
-  if (end - p < 2 || p[0] != 0x19 || (p[1] & 15) != 12) return false;
-  uint64_t n = p[1] >> 4;
-  p += 2;
-  if (n == 15 && !varint(&n)) return false;
-  if (n != ch.oi_pages) return false;
-  const uint32_t slot = ch.dict_page >= 0 ? 1u : 0u;
-  for (uint64_t i = 0; i < n; ++i) {
-    uint64_t off, skip;
-    if (p >= end || *p++ != 0x16 || !varint(&off)) return false;
-    if (p >= end || *p++ != 0x15 || !varint(&skip)) return false;
-    if (p >= end || *p++ != 0x16 || !varint(&skip)) return false;
-    if (p >= end || *p++ != 0x00) return false;
-    const int64_t rel = static_cast<int64_t>(off >> 1) ^ -static_cast<int64_t>(off & 1);
-    const int64_t r = rel - file_off;
-    if (r < 0 || static_cast<uint64_t>(r) >= ch.size) return false;
-    PageDev d{};
-    d.offset = static_cast<uint64_t>(r);
-    d.chunk = static_cast<uint32_t>(c);
-    pages[ch.page_begin + slot + i] = d;
-  }
-  return true;
-}
+// each {1: i64 offset, 2: i32 compressed_page_size, 3: i64 first_row_index}
+// with one-byte field headers (0x16, 0x15, 0x16) and a stop byte.  Each of
+// those single bytes has its high bit clear, as has the last byte of a
+// varint and no other varint byte: in this form a struct is exactly seven
+// tokens, each ending at a high-bit-clear byte, and struct k starts right
+// after token 7k - 1.  The warp streams the list through shared memory in
+// windows that start at a struct (16-byte loads; the OffsetIndex lies inside
+// the file, before its footer, so the aligned words around it are readable);
+// it finds a window's struct starts by counting token ends (4 bytes per lane,
+// a warp scan per 128 bytes), then every lane parses whole structs from its
+// starts, checking each byte against the form.  False (nothing assumed
+// written) when the bytes take any other form; the general parser then
+// reads the list.
+constexpr uint32_t OI_STARTS = OI_SMEM / 7 + 2;  // a struct takes at least 7 bytes
 
-// The usual serialization again, for an OffsetIndex larger than the
-// warp's shared-memory buffer: the warp streams it through the buffer
-// (lanes copy, lane 0 parses whole page-location structs, each at most 34
-// bytes, then the unparsed rest moves to the front of the next window).
-// False (nothing assumed written) when the bytes take another form.
-__device__ bool oi_locations_windowed(uint8_t* buf, const uint8_t* oi, uint32_t oi_len, int c, const ChunkDev& ch,
-                                      int64_t file_off, PageDev* pages, int lane) {
-  constexpr uint32_t kStruct = 34;  // 0x16 + 10-byte varint + 0x15 + 5 + 0x16 + 10 + stop
+__device__ bool oi_locations_tokens(uint8_t* raw, uint16_t* starts, const uint8_t* oi, uint32_t oi_len, int c,
+                                    const ChunkDev& ch, int64_t file_off, PageDev* pages, int lane) {
   const uint32_t slot = ch.dict_page >= 0 ? 1u : 0u;
-  uint32_t pos = 0;   // OI bytes consumed
-  uint64_t n = 0, i = 0;
-  int state = 0;      // 0 list header next, 1 structs, 2 done, 3 not the usual form
-  for (uint32_t guard = 0; guard < oi_len + 2 && state < 2; ++guard) {
+  // list header (every lane reads the same bytes): 0x19, then (n << 4) | 12
+  // with n < 15, or 0xfc and n as a varint
+  if (oi_len < 2 || __ldg(oi) != 0x19 || (__ldg(oi + 1) & 15) != 12) return false;
+  uint64_t n = __ldg(oi + 1) >> 4;
+  uint32_t pos = 2;
+  if (n == 15) {
+    uint64_t v = 0;
+    int b = 0;
+    for (; b < 10 && pos < oi_len; ++b) {
+      const uint32_t y = __ldg(oi + pos++);
+      v |= static_cast<uint64_t>(y & 0x7f) << (7 * b);
+      if (!(y & 0x80)) break;
+    }
+    if (b == 10 || (__ldg(oi + pos - 1) & 0x80)) return false;
+    n = v;
+  }
+  if (n != ch.oi_pages) return false;
+  uint64_t i = 0;  // structs written
+  for (uint32_t guard = 0; i < n && guard <= oi_len; ++guard) {
+    if (pos >= oi_len) return false;
     const uint32_t wlen = oi_len - pos < OI_SMEM ? oi_len - pos : OI_SMEM;
-    for (uint32_t k = lane; k < wlen; k += 32) buf[k] = __ldg(oi + pos + k);
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(oi + pos);
+    const uint32_t sh = static_cast<uint32_t>(a0 & 15);
+    const uint4* src = reinterpret_cast<const uint4*>(a0 - sh);
+    const uint32_t nv = (sh + wlen + 15) >> 4;
+    for (uint32_t v = lane; v < nv; v += 32) reinterpret_cast<uint4*>(raw)[v] = __ldg(src + v);
+    if (lane == 0) starts[0] = 0;
     __syncwarp();
-    if (lane == 0) {
-      const uint8_t* p = buf;
-      const uint8_t* end = buf + wlen;
-      const bool last = pos + wlen == oi_len;
+    const uint8_t* w = raw + sh;
+    uint32_t tb = 0;  // token ends before this step
+    for (uint32_t q0 = 0; q0 < wlen; q0 += 128) {
+      const uint32_t q = q0 + 4 * static_cast<uint32_t>(lane);
+      uint32_t em = 0;  // bit j: byte q + j ends a token
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (q + j < wlen && !(w[q + j] & 0x80)) em |= 1u << j;
+      const uint32_t cnt = __popc(em);
+      uint32_t incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      uint32_t t = tb + incl - cnt;  // index of the lane's first token end
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if ((em >> j) & 1u) {
+          if ((t + 1) % 7 == 0) {
+            const uint32_t sidx = (t + 1) / 7;
+            if (sidx < OI_STARTS) starts[sidx] = static_cast<uint16_t>(q + j + 1);
+          }
+          ++t;
+        }
+      }
+      tb += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    // structs whose seven tokens all end in the window
+    const uint64_t whole = tb / 7;
+    const uint32_t take = static_cast<uint32_t>(whole < n - i ? whole : n - i);
+    if (take == 0) return false;  // no whole struct in a window of OI_SMEM bytes: not this form
+    bool ok = true;
+    for (uint32_t k = lane; k < take; k += 32) {
+      const uint8_t* p = w + starts[k];
+      const uint8_t* e = w + starts[k + 1];
       auto varint = [&](uint64_t* v) -> bool {
         uint64_t x = 0;
-        for (int b = 0; b < 10 && p < end; ++b) {
+        for (int b = 0; b < 10 && p < e; ++b) {
           const uint32_t y = *p++;
           x |= static_cast<uint64_t>(y & 0x7f) << (7 * b);
           if (!(y & 0x80)) {
@@ -208,48 +230,36 @@ __device__ bool oi_locations_windowed(uint8_t* buf, const uint8_t* oi, uint32_t 
         }
         return false;
       };
-      if (state == 0) {
-        if (end - p < 2 || p[0] != 0x19 || (p[1] & 15) != 12) {
-          state = 3;
-        } else {
-          n = p[1] >> 4;
-          p += 2;
-          if (n == 15 && !varint(&n)) state = 3;
-          else if (n != ch.oi_pages) state = 3;
-          else state = 1;
-        }
-      }
-      while (state == 1 && i < n && (last || end - p >= static_cast<int64_t>(kStruct))) {
-        uint64_t off, skip;
-        if (p >= end || *p++ != 0x16 || !varint(&off)) { state = 3; break; }
-        if (p >= end || *p++ != 0x15 || !varint(&skip)) { state = 3; break; }
-        if (p >= end || *p++ != 0x16 || !varint(&skip)) { state = 3; break; }
-        if (p >= end || *p++ != 0x00) { state = 3; break; }
-        const int64_t rel = static_cast<int64_t>(off >> 1) ^ -static_cast<int64_t>(off & 1);
-        const int64_t r = rel - file_off;
-        if (r < 0 || static_cast<uint64_t>(r) >= ch.size) { state = 3; break; }
+      uint64_t off = 0, skip = 0;
+      bool sok = p < e && *p++ == 0x16 && varint(&off);
+      sok = sok && p < e && *p++ == 0x15 && varint(&skip);
+      sok = sok && p < e && *p++ == 0x16 && varint(&skip);
+      sok = sok && p < e && *p++ == 0x00 && p == e;
+      const int64_t rel = static_cast<int64_t>(off >> 1) ^ -static_cast<int64_t>(off & 1);
+      const int64_t r = rel - file_off;
+      sok = sok && r >= 0 && static_cast<uint64_t>(r) < ch.size;
+      if (sok) {
         PageDev d{};
         d.offset = static_cast<uint64_t>(r);
         d.chunk = static_cast<uint32_t>(c);
-        pages[ch.page_begin + slot + i] = d;
-        ++i;
+        pages[ch.page_begin + slot + i + k] = d;
       }
-      if (state == 1 && i == n) state = 2;
-      else if (state == 1 && last) state = 3;
-      pos += static_cast<uint32_t>(p - buf);
+      ok = ok && sok;
     }
-    __syncwarp();
-    state = __shfl_sync(0xffffffffu, state, 0);
-    pos = __shfl_sync(0xffffffffu, pos, 0);
+    if (!__all_sync(0xffffffffu, ok)) return false;
+    i += take;
+    pos += starts[take];
+    __syncwarp();  // the window and its starts are reused
   }
-  return state == 2;
+  return i == n;
 }
 
 __global__ void __launch_bounds__(32 * OI_WARPS) k_index_oi_locations(const ChunkDev* __restrict__ chunks,
                                                                       int n_chunks,
                                                                       const int64_t* __restrict__ chunk_file_off,
                                                                       PageDev* pages, DevStatus* st) {
-  __shared__ __align__(16) uint8_t buf[OI_WARPS][OI_SMEM];
+  __shared__ __align__(16) uint8_t raw[OI_WARPS][OI_SMEM + 32];
+  __shared__ uint16_t starts[OI_WARPS][OI_STARTS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int c = blockIdx.x * OI_WARPS + w;
   if (c >= n_chunks) return;
@@ -260,12 +270,7 @@ __global__ void __launch_bounds__(32 * OI_WARPS) k_index_oi_locations(const Chun
     d.chunk = static_cast<uint32_t>(c);
     pages[ch.page_begin] = d;
   }
-  if (ch.oi_len <= OI_SMEM) {
-    for (uint32_t i = lane; i < ch.oi_len; i += 32) buf[w][i] = __ldg(ch.oi_base + i);
-    __syncwarp();
-    if (lane == 0 && !oi_locations_fast(buf[w], buf[w] + ch.oi_len, c, ch, chunk_file_off[c], pages))
-      oi_locations(TRdT<false>{buf[w], buf[w] + ch.oi_len, false}, c, ch, chunk_file_off[c], pages, st);
-  } else if (!oi_locations_windowed(buf[w], ch.oi_base, ch.oi_len, c, ch, chunk_file_off[c], pages, lane)) {
+  if (!oi_locations_tokens(raw[w], starts[w], ch.oi_base, ch.oi_len, c, ch, chunk_file_off[c], pages, lane)) {
     if (lane == 0) oi_locations(TRd{ch.oi_base, ch.oi_base + ch.oi_len, false}, c, ch, chunk_file_off[c], pages, st);
   }
 }
