@@ -11,20 +11,15 @@
 //
 // The compressed page streams through two shared-memory windows filled by
 // the bulk-copy engine (the next window is in flight while the current one
-// is parsed).  When the parse enters a window, the warp's 32 lanes follow
-// header chains from 32 evenly spaced offsets of it into a next-header
-// table (chains that start inside literal bytes fall onto the true chain
-// within a few elements); lane 0 then walks the table to up to 32 headers
-// and every lane decodes one of them.  The warp executes the batch into a
-// ring of recent output in shared memory -- literals and copies whose
-// source lies before the batch in parallel, one element per lane, literals
-// from the staged window by 16-byte vectors, copies that read output of the
-// same batch in order -- and writes the batch's output to global memory
-// with 16-byte stores.  Literals longer than kMidLit, or outside the
-// window, go straight from the input to the output as 16-byte vector copies
-// (by the whole block in the block-per-page mode for large pages).  Copy
-// sources older than the ring are read back from the output with coherent
-// loads (this warp wrote them).
+// is parsed).  Lane 0 parses up to 32 element headers from the window (the
+// tag stream is serial); the warp then executes the batch into a ring of
+// recent output in shared memory -- literals and copies whose source lies
+// before the batch in parallel, one element per lane (long ones by the whole
+// warp), copies that read output of the same batch in order -- and writes
+// the batch's output bytes to global memory with 16-byte stores.  Literals
+// longer than the ring go straight from the input to the output as
+// 16-byte vector copies.  Copy sources older than the ring are read back
+// from the output with coherent loads (this warp wrote them).
 #include "dev_util.cuh"
 #include "snappy_job.h"
 
@@ -35,13 +30,12 @@ constexpr uint32_t kRing = 8192;    // recent output kept in shared memory per w
 constexpr uint32_t kWin = 4096;     // input window (two per warp)
 constexpr uint32_t kBatchOut = kRing / 2;  // output bytes of one batch assembled in the ring
 constexpr uint32_t kMidLit = 2048;  // literals up to this long go from the input window through the ring
-constexpr uint16_t kNxUnk = 0xffffu;   // no chain reached this offset
-constexpr uint16_t kNxOut = 0xfffeu;   // the next header lies past the window
 
 struct SnWarp {
-  uint16_t nxt[kWin];  // window offset -> the next header's window offset (kNxUnk / kNxOut)
-  uint32_t pos[32];    // input offsets of a batch's headers
   uint64_t bar[2];
+  uint32_t kl[32];   // kind | len << 2
+  uint32_t arg[32];  // literal: input offset; copy: back offset
+  int32_t woff[32];  // literal inside the batch's input window: its offset there, else -1
   uint8_t win[2][kWin + 16];
   uint8_t ring[kRing];
 };
@@ -121,82 +115,6 @@ __device__ __forceinline__ bool sn_ensure(SnIn& s, uint32_t p) {
   return true;
 }
 
-// The element whose header sits at input offset pa, from its bytes h[0..4]
-// (bytes past the input are never used): kind, length, argument (literal:
-// input offset of its bytes; copy: back offset) and the next header's input
-// offset.  False when the header or the literal runs past the input.
-__device__ __forceinline__ bool sn_hdr(const uint8_t* h, uint32_t pa, uint32_t in_len, uint32_t* kind, uint32_t* len,
-                                       uint32_t* arg, uint32_t* next) {
-  const uint32_t tag = h[0], x1 = h[1], x2 = h[2], x3 = h[3], x4 = h[4];
-  const uint32_t k = tag & 3, left = in_len - pa - 1;  // bytes after the tag
-  uint32_t l, a, hl;
-  if (k == 0) {
-    const uint32_t t = tag >> 2;
-    if (t < 60) {
-      l = t + 1;
-      hl = 1;
-    } else {
-      const uint32_t nb = t - 59;
-      if (nb > left) return false;
-      const uint32_t v = x1 | (x2 << 8) | (x3 << 16) | (x4 << 24);
-      const uint32_t vm = nb == 4 ? v : (v & ((1u << (8 * nb)) - 1u));
-      if (vm == 0xffffffffu) return false;
-      l = vm + 1;
-      hl = 1 + nb;
-    }
-    if (l > in_len - pa - hl) return false;
-    a = pa + hl;
-  } else if (k == 1) {
-    if (left < 1) return false;
-    l = 4 + ((tag >> 2) & 7);
-    a = ((tag >> 5) << 8) | x1;
-    hl = 2;
-  } else if (k == 2) {
-    if (left < 2) return false;
-    l = (tag >> 2) + 1;
-    a = x1 | (x2 << 8);
-    hl = 3;
-  } else {
-    if (left < 4) return false;
-    l = (tag >> 2) + 1;
-    a = x1 | (x2 << 8) | (x3 << 16) | (x4 << 24);
-    hl = 5;
-  }
-  *kind = k;
-  *len = l;
-  *arg = a;
-  *next = pa + hl + (k == 0 ? l : 0u);
-  return true;
-}
-
-// The whole warp: chains of headers from 32 evenly spaced offsets of the
-// window (each a guess at a header) into the next-header table.  The
-// element after a header depends only on the header's position, so an entry
-// is right however its chain got there; chains that start inside literal
-// bytes usually land on the true chain after a few elements, and from there
-// the table covers it.
-__device__ __forceinline__ void sn_spec(uint16_t* nxt, const uint8_t* win, uint32_t w0, uint32_t n0, uint32_t in_len,
-                                        int lane) {
-  for (uint32_t q = lane; q < n0; q += 32) nxt[q] = kNxUnk;
-  __syncwarp();
-  const uint32_t per = (n0 + 31) / 32;
-  const uint32_t start = lane * per;
-  const uint32_t end = start + per + 32 < n0 ? start + per + 32 : n0;
-  const bool tail = w0 + n0 >= in_len;  // the window reaches the input's end
-  uint32_t q = start;
-  for (int steps = 0; q < end && steps < 48; ++steps) {
-    if (nxt[q] != kNxUnk) break;  // parsed already: the chain goes on from there
-    if ((q + 5 > n0 && !tail) || w0 + q >= in_len) break;
-    uint32_t kind, len, arg, next;
-    if (!sn_hdr(win + q, w0 + q, in_len, &kind, &len, &arg, &next)) break;
-    const uint32_t nr = next - w0;
-    nxt[q] = nr < n0 ? static_cast<uint16_t>(nr) : kNxOut;
-    if (nr >= n0) break;
-    q = nr;
-  }
-  __syncwarp();
-}
-
 // `n` bytes from ring positions [from, from + n) (positions are output
 // offsets; the ring holds position x at x mod kRing) to global dst, 16-byte
 // stores where the destination allows.
@@ -225,27 +143,6 @@ __device__ __forceinline__ void ring_out(uint8_t* dst, const uint8_t* ring, uint
     }
   }
   for (uint32_t i = head + (nv << 4) + lane; i < n; i += 32) dst[i] = ring[(from + i) & RM];
-}
-
-// `n` bytes from shared memory `src` (any alignment, readable for 16 bytes
-// past the end) to ring positions [pos0, pos0 + n): whole 16-byte ring words
-// from two aligned shared words, the partial words at the two ends byte by
-// byte.
-__device__ __forceinline__ void win_to_ring(uint8_t* ring, uint32_t pos0, const uint8_t* src, uint32_t n, int lane) {
-  constexpr uint32_t RM = kRing - 1;
-  const uint32_t head0 = (16 - (pos0 & 15)) & 15;
-  const uint32_t head = head0 < n ? head0 : n;
-  if (static_cast<uint32_t>(lane) < head) ring[(pos0 + lane) & RM] = src[lane];
-  const uint32_t nv = (n - head) >> 4;
-  const uint8_t* s1 = src + head;
-  const uint32_t sh = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(s1) & 15);
-  const uint4* sa = reinterpret_cast<const uint4*>(s1 - sh);
-  for (uint32_t v = lane; v < nv; v += 32) {
-    const uint4 A = sa[v];
-    const uint4 B = sh ? sa[v + 1] : A;
-    *reinterpret_cast<uint4*>(ring + ((pos0 + head + 16 * v) & RM)) = sh ? shift_pair(A, B, sh) : A;
-  }
-  for (uint32_t i = head + (nv << 4) + lane; i < n; i += 32) ring[(pos0 + i) & RM] = src[i];
 }
 
 // A short literal (len <= 64) from global input to the ring: its aligned
@@ -397,85 +294,81 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
     uint32_t op = 0;
     bad = __shfl_sync(0xffffffffu, bad, 0);
     // each element consumes >= 2 input bytes, so in_len bounds the batches
-    uint32_t tab_w0 = 0, tab_n0 = 0;   // window the next-header table describes (lane 0)
-    const uint8_t* tab_b = nullptr;
     for (uint32_t guard = 0; guard <= in_len && ip < in_len && !bad; ++guard) {
-      // the batch's window: switched now when ip has left window 0; a new
-      // window's next-header table is filled by the whole warp
-      int need = 0;
+      int n_el = 0;
       if (lane == 0) {
-        const bool here = ip - sin.w0 < sin.n0 && (ip - sin.w0 + 5 <= sin.n0 || sin.w0 + sin.n0 >= in_len);
-        if (!here && !sn_ensure(sin, ip)) bad = 2;
-        need = !bad && (sin.w0 != tab_w0 || sin.n0 != tab_n0 || sin.b0 != tab_b);
-        if (need) {
-          tab_w0 = sin.w0;
-          tab_n0 = sin.n0;
-          tab_b = sin.b0;
-        }
-      }
-      bad = __shfl_sync(0xffffffffu, bad, 0);
-      if (bad) break;
-      const int wsel = __shfl_sync(0xffffffffu, lane == 0 && sin.b0 == sw.win[1] ? 1 : 0, 0);
-      const uint8_t* wbuf = sw.win[wsel];
-      const uint32_t w0 = __shfl_sync(0xffffffffu, sin.w0, 0), n0 = __shfl_sync(0xffffffffu, sin.n0, 0);
-      if (__shfl_sync(0xffffffffu, need, 0)) sn_spec(sw.nxt, wbuf, w0, n0, in_len, lane);
-      // lane 0 follows the table (parsing itself where no chain went) to up
-      // to 32 headers inside the window
-      int n_pos = 0;
-      if (lane == 0) {
-        uint32_t p = ip;
-        while (n_pos < 32 && p < in_len) {
-          const uint32_t q = p - w0;
-          if (!(q < n0 && (q + 5 <= n0 || w0 + n0 >= in_len))) break;
-          uint32_t nx;
-          const uint16_t t = sw.nxt[q];
-          if (t < kNxOut) {
-            nx = w0 + t;
-          } else {
-            uint32_t k, l, a2;
-            if (!sn_hdr(wbuf + q, p, in_len, &k, &l, &a2, &nx)) {
-              sw.pos[n_pos++] = p;  // the lane that parses it reports it
-              break;
+        uint32_t p = ip, o = op, bo = 0;
+        for (int e = 0; e < 32 && p < in_len; ++e) {
+          // a batch's headers all sit in one window (its literals are read
+          // from there): switch windows only at a batch's first element
+          const bool here = p - sin.w0 < sin.n0 && (p - sin.w0 + 5 <= sin.n0 || sin.w0 + sin.n0 >= in_len);
+          if (!here && e > 0) break;
+          if (!sn_ensure(sin, p)) { bad = 2; break; }
+          // the tag and the 4 bytes after it (slack past the input end is never used)
+          const uint8_t* q = sin.b0 + (p - sin.w0);
+          const uint32_t tag = q[0], x1 = q[1], x2 = q[2], x3 = q[3], x4 = q[4];
+          ++p;
+          uint32_t kind = tag & 3, len, arg;
+          if (kind == 0) {
+            const uint32_t l = tag >> 2;
+            if (l < 60) {
+              len = l + 1;
+            } else {
+              const uint32_t nb = l - 59;
+              if (nb > in_len - p) { bad = 1; break; }
+              const uint32_t v = x1 | (x2 << 8) | (x3 << 16) | (x4 << 24);
+              const uint32_t vm = nb == 4 ? v : (v & ((1u << (8 * nb)) - 1u));
+              p += nb;
+              if (vm == 0xffffffffu) { bad = 1; break; }
+              len = vm + 1;
             }
+            if (len > in_len - p) { bad = 1; break; }
+            arg = p;
+            p += len;
+          } else if (kind == 1) {
+            if (p >= in_len) { bad = 1; break; }
+            len = 4 + ((tag >> 2) & 7);
+            arg = ((tag >> 5) << 8) | x1;
+            p += 1;
+          } else if (kind == 2) {
+            if (2 > in_len - p) { bad = 1; break; }
+            len = (tag >> 2) + 1;
+            arg = x1 | (x2 << 8);
+            p += 2;
+          } else {
+            if (4 > in_len - p) { bad = 1; break; }
+            len = (tag >> 2) + 1;
+            arg = x1 | (x2 << 8) | (x3 << 16) | (x4 << 24);
+            p += 4;
           }
-          sw.pos[n_pos++] = p;
-          p = nx;
+          if (len > out_len - o || (kind != 0 && (arg == 0 || arg > o))) { bad = 1; break; }
+          const bool inwin = kind == 0 && len <= kMidLit && arg - sin.w0 + len <= sin.n0;
+          sw.kl[e] = kind | (len << 2);
+          sw.arg[e] = arg;
+          sw.woff[e] = inwin ? static_cast<int32_t>(arg - sin.w0) : -1;
+          n_el = e + 1;
+          o += len;
+          bo += len;
+          // a batch's output is assembled in the ring; a literal that is not
+          // in the window (or longer than kMidLit) ends its batch: it is
+          // copied to global memory directly
+          if (bo >= kBatchOut - 64 || (kind == 0 && !inwin)) break;
         }
+        ip = p;
       }
       __syncwarp();
-      n_pos = __shfl_sync(0xffffffffu, n_pos, 0);
-      // every lane parses its header from the window
-      uint32_t kind = 0, len = 0, arg = 0, nextp = 0;
-      bool hok = true;
-      const uint32_t mypos = lane < n_pos ? sw.pos[lane] : 0u;
-      if (lane < n_pos) hok = sn_hdr(wbuf + (mypos - w0), mypos, in_len, &kind, &len, &arg, &nextp);
-      // output offsets; the batch ends after its first element that fills the
-      // ring's budget or is a literal outside the window (copied directly)
-      const uint32_t plen = lane < n_pos ? len : 0u;
-      uint32_t pinc = plen;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, pinc, o);
-        if (lane >= o) pinc += y;
-      }
-      const bool inwin0 = kind == 0 && len <= kMidLit && arg - w0 + len <= n0;
-      const bool trig = lane < n_pos && (pinc >= kBatchOut - 64 || (kind == 0 && !inwin0));
-      const uint32_t tm = __ballot_sync(0xffffffffu, trig);
-      const int n_el = tm ? __ffs(tm) : n_pos;
-      const uint32_t o_e = op + pinc - plen;
-      const bool evalid = !hok ? false : (len <= out_len - o_e && (kind == 0 || (arg != 0 && arg <= o_e)));
-      if (__any_sync(0xffffffffu, lane < n_el && !evalid)) {
-        bad = 1;
-        break;
-      }
-      if (n_el == 0) {
-        bad = 1;
-        break;
-      }
-      ip = __shfl_sync(0xffffffffu, nextp, n_el - 1);
+      n_el = __shfl_sync(0xffffffffu, n_el, 0);
+      bad = __shfl_sync(0xffffffffu, bad, 0);
+      ip = __shfl_sync(0xffffffffu, ip, 0);
+      uint32_t kl = 0, arg = 0;
       int32_t woff = -1;
-      if (lane < n_el && inwin0) woff = static_cast<int32_t>(arg - w0);
-      if (lane >= n_el) kind = len = arg = 0;
+      if (lane < n_el) {
+        kl = sw.kl[lane];
+        arg = sw.arg[lane];
+        woff = sw.woff[lane];
+      }
+      const uint8_t* wbuf = sw.win[__shfl_sync(0xffffffffu, lane == 0 && sin.b0 == sw.win[1] ? 1 : 0, 0)];
+      const uint32_t kind = kl & 3, len = kl >> 2;
       uint32_t incl = len;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -521,7 +414,7 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
         const int e = __ffs(m) - 1;
         const uint32_t el = __shfl_sync(0xffffffffu, len, e), eo = __shfl_sync(0xffffffffu, o0, e);
         const int32_t ew = __shfl_sync(0xffffffffu, woff, e);
-        win_to_ring(ring, eo, wbuf + ew, el, lane);
+        for (uint32_t i = lane; i < el; i += 32) ring[(eo + i) & RM] = wbuf[ew + i];
       }
       __syncwarp();
       for (uint32_t m = __ballot_sync(0xffffffffu, valid && !indep && !longlit); m; m &= m - 1) {
