@@ -331,7 +331,7 @@ TRAFFIC_CAPTURES = {
     "8388608/1048576/UNCOMPRESSED/V1/batched/oi1": {"rows": 16777216, "bytes": 1349700864, "sources": "ed5da2e8d3518248"},
 }
 
-KERNEL_SOURCES = ("k_decode.cu", "k_index.cu", "k_transcode.cu", "dev_util.cuh", "thrift_dev.cuh", "decode_job.h",
+KERNEL_SOURCES = ("k_decode.cu", "k_transcode.cu", "dev_util.cuh", "thrift_dev.cuh", "decode_job.h",
                   "pq_internal.h", "snappy_job.h", "engine.cpp")
 CODEC_SOURCES = {"SNAPPY": ("k_snappy.cu",), "ZSTD": ("k_zstd.cu", "zstd_dec.cuh")}
 

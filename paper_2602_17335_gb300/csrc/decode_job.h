@@ -117,8 +117,13 @@ void launch_copy_small(void* dst, const void* src, uint32_t bytes, cudaStream_t 
 void launch_make_items(const DecodeArgs& a, int n_pp, cudaStream_t s);
 int expand_blocks_per_sm();
 int walk_blocks_per_sm();
-// coop: one block of 8 warps per page (large pages), else one warp per page
+// coop: one block of 8 warps per page (large pages), else one warp per page;
+// pages with nsub > 1 are skipped (their blocks are separate jobs)
 void launch_snappy(const SnappyJob* jobs, int n_jobs, int n_sms, DevStatus* st, cudaStream_t s, bool coop);
+// The blocks of the pages of jobs [0, n_jobs) that have nsub > 1, written to
+// blocks[sub .. sub + nsub) (SNAPPY_FRAGMENT)
+void launch_snappy_split(const SnappyJob* jobs, int n_jobs, SnappyJob* blocks, int n_sms, DevStatus* st,
+                         cudaStream_t s);
 // Zstandard pages of jobs [0, n_jobs) (the others are skipped)
 void launch_zstd(const SnappyJob* jobs, int n_jobs, int n_sms, DevStatus* st, cudaStream_t s);
 void launch_index_walk(const ChunkDev* chunks, int n_chunks, PageDev* pages, uint32_t* counts, int mode,

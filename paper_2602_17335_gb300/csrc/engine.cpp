@@ -718,6 +718,18 @@ namespace pqe {
 // Host half of planning: plan pages, work item counts, job lists and the
 // scratch layout for the rows of `segs` (each segment's rows go to output
 // rows starting at its out0), nothing on the device yet.
+// A Snappy page decompressed by fragments (SNAPPY_FRAGMENT): nsub block slots
+// numbered from *counter.  Dictionary and data pages count separately (their
+// blocks sit in two ranges of the block list, like their jobs).
+static void plan_split(pqi::SnappyJob& sj, bool plain, uint32_t* counter) {
+  if (plain || sj.codec != pqi::CODEC_SNAPPY || sj.raw || sj.prefix > sj.dst_len) return;
+  const uint32_t out = sj.dst_len - sj.prefix;
+  if (out <= pqi::SNAPPY_SPLIT_MIN) return;
+  sj.nsub = (out + pqi::SNAPPY_FRAGMENT - 1) / pqi::SNAPPY_FRAGMENT;
+  sj.sub = *counter;
+  *counter += sj.nsub;
+}
+
 pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& cols, const std::vector<RowSeg>& segs,
                      int64_t n_rows, uint32_t flags, std::unique_ptr<pq_plan>* out) {
   if ((flags & PQ_SCAN_TIMING) && (flags & PQ_SCAN_GRAPH))
@@ -738,6 +750,7 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
   std::vector<int64_t> data_job_off;  // scratch offset per data snappy job
   std::vector<int64_t> walk_cost;     // estimated chain steps per walked page
   std::vector<int32_t> dict_job_of_chunk(idx->chunks.size(), -1);
+  uint32_t blk_data = 0, blk_dict = 0;  // block slots of split data / dictionary pages
   for (size_t oc = 0; oc < plan->cols.size(); ++oc) {
     const int c = plan->cols[oc];
     const auto& cm = idx->schema[c];
@@ -748,6 +761,8 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
     cw.walk_begin = static_cast<int>(plan->walk_pps.size());
     cw.delta_begin = static_cast<int>(plan->delta_pps.size());
     cw.tc_begin = static_cast<int>(plan->tc_jobs.size());
+    cw.blk_data_begin = blk_data;
+    cw.blk_dict_begin = blk_dict;
     cw.copy_only = cm.repetition != 1 && cm.type != pqi::T_BYTE_ARRAY;
     const int max_fixed_before = plan->max_fixed_dict_bytes;
     plan->max_fixed_dict_bytes = 0;
@@ -797,6 +812,7 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
             sj.dst_len = static_cast<uint32_t>(dp.uncompressed);
             sj.page = cd.dict_page;
             sj.codec = cd.codec;
+            plan_split(sj, plain, &blk_dict);
             if (cd.codec == pqi::CODEC_ZSTD) plan->zstd_jobs++;
             plan->snappy_dict.push_back(sj);
             dj.body = idx->dict_body[ch];
@@ -868,11 +884,14 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
           sj.prefix = pg.page_type == pqi::PAGE_DATA_V2 ? static_cast<uint32_t>(pg.def_len + pg.rep_len) : 0u;
           sj.page = static_cast<int32_t>(pid);
           sj.codec = cd.codec;
+          plan_split(sj, plain, &blk_data);
           if (cd.codec == pqi::CODEC_ZSTD) plan->zstd_jobs++;
           data_job_off.push_back(static_cast<int64_t>(scratch));
           plan->snappy_data.push_back(sj);
-          cw.snap_data_max = std::max<uint32_t>(cw.snap_data_max, sj.src_len);
-          plan->snap_data_max = std::max<uint32_t>(plan->snap_data_max, sj.src_len);
+          if (sj.nsub == 0) {  // (split pages are decompressed by blocks)
+            cw.snap_data_max = std::max<uint32_t>(cw.snap_data_max, sj.src_len);
+            plan->snap_data_max = std::max<uint32_t>(plan->snap_data_max, sj.src_len);
+          }
           pp.body = reinterpret_cast<const uint8_t*>(static_cast<uintptr_t>(scratch));  // rebased below
           pp.pad = 1;  // body is a scratch offset until rebased
           scratch += (static_cast<uint64_t>(pg.uncompressed) + 32 + 15) & ~uint64_t(15);
@@ -968,6 +987,8 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
     cw.walk_n = static_cast<int>(plan->walk_pps.size()) - cw.walk_begin;
     cw.delta_n = static_cast<int>(plan->delta_pps.size()) - cw.delta_begin;
     cw.tc_n = static_cast<int>(plan->tc_jobs.size()) - cw.tc_begin;
+    cw.blk_data_n = blk_data - cw.blk_data_begin;
+    cw.blk_dict_n = blk_dict - cw.blk_dict_begin;
     cw.max_fixed_dict = plan->max_fixed_dict_bytes;
     plan->max_fixed_dict_bytes = std::max(max_fixed_before, plan->max_fixed_dict_bytes);
     plan->colwork.push_back(cw);
@@ -987,6 +1008,11 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
     for (size_t i = 0; i < order.size(); ++i) sorted[i] = plan->walk_pps[order[i]];
     std::copy(sorted.begin(), sorted.end(), plan->walk_pps.begin() + cw.walk_begin);
   }
+  // the block list: data pages' blocks, then dictionary pages' blocks
+  for (auto& sj : plan->snappy_dict)
+    if (sj.nsub > 1) sj.sub += blk_data;
+  for (auto& cw : plan->colwork) cw.blk_dict_begin += blk_data;
+  plan->snap_blocks = blk_data + blk_dict;
   plan->tc_pool_off = scratch;
   plan->tc_pool_bytes = tc_pool;
   scratch += tc_pool;
@@ -1018,6 +1044,7 @@ pq_status plan_upload(pq_plan* plan) {
   plan->d_items = plan_alloc(pqi::Item, plan, nit);
   plan->d_cols = plan_alloc(pqi::OutCol, plan, plan->outcols.size());
   plan->d_snappy = plan_alloc(pqi::SnappyJob, plan, plan->snappy_data.size() + plan->snappy_dict.size());
+  plan->d_snap_blocks = plan_alloc(pqi::SnappyJob, plan, plan->snap_blocks);
   plan->d_dict_jobs = plan_alloc(pqi::DictJob, plan, plan->dict_jobs.size());
   plan->d_tc_jobs = plan_alloc(pqi::TranscodeJob, plan, plan->tc_jobs.size());
   plan->d_str_cols = plan_alloc(int32_t, plan, plan->str_cols.size());
@@ -1126,7 +1153,9 @@ pq_status plan_upload(pq_plan* plan) {
       for (size_t oc = 0; oc < plan->colwork.size(); ++oc) {
         const auto& cw = plan->colwork[oc];
         const int dk = plan->zstd_jobs ? 2 : 1;  // decompression kernels per job list
-        n += (cw.snap_dict_n ? dk : 0) + (cw.dict_n ? 2 : 0) + (cw.snap_data_n ? dk : 0) + (cw.walk_n ? 1 : 0) +
+        // (+2 per job list with split pages: the fragment scan and the blocks)
+        n += (cw.snap_dict_n ? dk + (cw.blk_dict_n ? 2 : 0) : 0) + (cw.dict_n ? 2 : 0) +
+             (cw.snap_data_n ? dk + (cw.blk_data_n ? 2 : 0) : 0) + (cw.walk_n ? 1 : 0) +
              (cw.delta_n ? 4 : 0) + (cw.tc_n ? 1 : 0) + (plan->outcols[oc].item_count ? 1 : 0);
       }
     }
@@ -1212,7 +1241,7 @@ uint64_t plan_device_bytes(const pq_plan* plan, uint64_t scratch) {
   const uint64_t npp = plan->pps.size(), nit = plan->n_items;
   const uint64_t str_rows = static_cast<uint64_t>(plan->n_rows) * plan->str_cols.size();
   return npp * sizeof(pqi::PlanPage) + nit * sizeof(pqi::Item) + plan->outcols.size() * sizeof(pqi::OutCol) +
-         (plan->snappy_data.size() + plan->snappy_dict.size()) * sizeof(pqi::SnappyJob) +
+         (plan->snappy_data.size() + plan->snappy_dict.size() + plan->snap_blocks) * sizeof(pqi::SnappyJob) +
          plan->dict_jobs.size() * sizeof(pqi::DictJob) + plan->tc_jobs.size() * sizeof(pqi::TranscodeJob) +
          4 * (plan->walk_pps.size() + plan->delta_pps.size()) +
          plan->delta_blocks * 12 +
@@ -1307,11 +1336,17 @@ static uint32_t coop_snappy_bytes(const pq_plan* plan) {
 
 // Decompression of jobs [jobs, jobs + n): the Snappy kernel takes the Snappy
 // pages, the Zstandard kernel (launched when the plan has any) the others.
-static void launch_decompress(pq_plan* plan, const pqi::SnappyJob* jobs, int n, bool coop, pqi::DevStatus* st,
-                              cudaStream_t s) {
+// Split Snappy pages (blocks [blk_begin, blk_begin + blk_n) of the plan's
+// block list) are scanned for their fragments first; their blocks are then
+// decompressed one warp each.
+static void launch_decompress(pq_plan* plan, const pqi::SnappyJob* jobs, int n, uint32_t blk_begin, uint32_t blk_n,
+                              bool coop, pqi::DevStatus* st, cudaStream_t s) {
   if (n <= 0) return;
-  pqi::launch_snappy(jobs, n, plan->ctx->n_sms, st, s, coop);
-  if (plan->zstd_jobs) pqi::launch_zstd(jobs, n, plan->ctx->n_sms, st, s);
+  const int n_sms = plan->ctx->n_sms;
+  if (blk_n) pqi::launch_snappy_split(jobs, n, plan->d_snap_blocks, n_sms, st, s);
+  pqi::launch_snappy(jobs, n, n_sms, st, s, coop);
+  if (plan->zstd_jobs) pqi::launch_zstd(jobs, n, n_sms, st, s);
+  if (blk_n) pqi::launch_snappy(plan->d_snap_blocks + blk_begin, static_cast<int>(blk_n), n_sms, st, s, false);
 }
 
 // Expansion of one output column: copies (REQUIRED PLAIN fixed width), the
@@ -1347,13 +1382,14 @@ static void enqueue_column(pq_plan* plan, size_t oc, const pqi::DecodeArgs& a, b
   const auto& cw = plan->colwork[oc];
   const int n_data_total = static_cast<int>(plan->snappy_data.size());
   if (with_dicts && cw.snap_dict_n)
-    launch_decompress(plan, plan->d_snappy + n_data_total + cw.snap_dict_begin, cw.snap_dict_n, true, a.st, s);
+    launch_decompress(plan, plan->d_snappy + n_data_total + cw.snap_dict_begin, cw.snap_dict_n, cw.blk_dict_begin,
+                      cw.blk_dict_n, true, a.st, s);
   if (with_dicts && cw.dict_n)
     pqi::launch_dict(plan->d_dict_jobs + cw.dict_begin, cw.dict_n, cw.max_fixed_dict, cw.max_str_regions,
                      pqi::DictScratch{plan->d_sregs, plan->d_slists}, plan->idx->d_dicts, ctx->n_sms, a.st, s);
   if (cw.snap_data_n)
-    launch_decompress(plan, plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, cw.snap_data_max >= coop_snappy_bytes(plan),
-                      a.st, s);
+    launch_decompress(plan, plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, cw.blk_data_begin, cw.blk_data_n,
+                      cw.snap_data_max >= coop_snappy_bytes(plan), a.st, s);
   enqueue_transcode(plan, cw.tc_begin, cw.tc_n, a, s);
   const auto& col = plan->outcols[oc];
   pqi::launch_walk(a, cw.walk_begin, cw.walk_n, ctx->n_sms, col.optional != 0, plan->tuning.walk_window, s);
@@ -1386,7 +1422,7 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
   if (plan->flags & PQ_SCAN_PLAIN) {
     // baseline: per chunk, one launch per stage; one page per thread block
     if (with_dicts && n_dict_jobs)
-      launch_decompress(plan, plan->d_snappy + n_data_jobs, n_dict_jobs, true, a.st, s);
+      launch_decompress(plan, plan->d_snappy + n_data_jobs, n_dict_jobs, 0, 0, true, a.st, s);
     mark(2);
     if (with_dicts && !plan->dict_jobs.empty())
       pqi::launch_dict(plan->d_dict_jobs, static_cast<int>(plan->dict_jobs.size()), plan->max_fixed_dict_bytes,
@@ -1400,7 +1436,7 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
       for (int p = first; p < first + n; ++p)
         if (job + nj < plan->snappy_data.size() && plan->snappy_data[job + nj].page == static_cast<int32_t>(plan->pps[p].page))
           ++nj;
-      if (nj) launch_decompress(plan, plan->d_snappy + job, nj, plan->snap_data_max >= coop_snappy_bytes(plan), a.st, s);
+      if (nj) launch_decompress(plan, plan->d_snappy + job, nj, 0, 0, plan->snap_data_max >= coop_snappy_bytes(plan), a.st, s);
       job += nj;
       int ntc = 0;
       while (tcj + ntc < plan->tc_jobs.size() && plan->tc_jobs[tcj + ntc].pp < static_cast<uint32_t>(first + n)) ++ntc;
@@ -1416,9 +1452,10 @@ static void enqueue_scan(pq_plan* plan, cudaStream_t s, bool with_dicts, const c
     for (int oc = 0; oc < ncols; ++oc) {
       const auto& cw = plan->colwork[oc];
       if (with_dicts && cw.snap_dict_n)
-        launch_decompress(plan, plan->d_snappy + n_data_jobs + cw.snap_dict_begin, cw.snap_dict_n, true, a.st, s);
+        launch_decompress(plan, plan->d_snappy + n_data_jobs + cw.snap_dict_begin, cw.snap_dict_n, cw.blk_dict_begin,
+                          cw.blk_dict_n, true, a.st, s);
       if (cw.snap_data_n)
-        launch_decompress(plan, plan->d_snappy + cw.snap_data_begin, cw.snap_data_n,
+        launch_decompress(plan, plan->d_snappy + cw.snap_data_begin, cw.snap_data_n, cw.blk_data_begin, cw.blk_data_n,
                           cw.snap_data_max >= coop_snappy_bytes(plan), a.st, s);
       enqueue_transcode(plan, cw.tc_begin, cw.tc_n, a, s);
     }

@@ -102,6 +102,7 @@ struct pq_plan {
   std::vector<pqi::SnappyJob> snappy_dict;   // dictionary pages (into index buffers)
   uint32_t snap_data_max = 0;                 // largest compressed data page of the plan
   int zstd_jobs = 0;                          // Zstandard pages among the decompression jobs
+  uint32_t snap_blocks = 0;                   // blocks of the split Snappy pages (SNAPPY_FRAGMENT)
   bool needs_sizing = false;                  // string chars counted by a sizing scan at upload
   bool sizing = false;                        // that scan is being enqueued (no chars copy)
   std::vector<pqi::DictJob> dict_jobs;
@@ -133,6 +134,7 @@ struct pq_plan {
   pqi::Item* d_items = nullptr;
   pqi::OutCol* d_cols = nullptr;
   pqi::SnappyJob* d_snappy = nullptr;        // data jobs then dict jobs
+  pqi::SnappyJob* d_snap_blocks = nullptr;   // blocks of the split Snappy pages
   pqi::DictJob* d_dict_jobs = nullptr;
   pqi::TranscodeJob* d_tc_jobs = nullptr;
   int32_t* d_str_cols = nullptr;
@@ -166,6 +168,8 @@ struct pq_plan {
     int snap_data_begin = 0, snap_data_n = 0;  // into snappy_data
     uint32_t snap_data_max = 0;                // largest compressed data page (bytes)
     int snap_dict_begin = 0, snap_dict_n = 0;  // into snappy_dict
+    uint32_t blk_data_begin = 0, blk_data_n = 0;  // blocks of its split data pages
+    uint32_t blk_dict_begin = 0, blk_dict_n = 0;  // blocks of its split dictionary pages
     int dict_begin = 0, dict_n = 0;            // into dict_jobs
     int max_fixed_dict = 0;
     int walk_begin = 0, walk_n = 0;            // into walk_pps

@@ -303,49 +303,63 @@ __global__ void k_index_oi_headers(const ChunkDev* __restrict__ chunks, PageDev*
   pages[i] = h;
 }
 
-// OffsetIndex path, step 3 (one warp per chunk): first_row of every data
-// page (an exclusive scan of num_values over the chunk's pages), a check
-// that each page starts where the previous one ends, and that the pages
-// cover the chunk's values.
-__global__ void __launch_bounds__(32 * OI_WARPS) k_index_oi_rows(const ChunkDev* __restrict__ chunks, int n_chunks,
-                                                                 PageDev* pages, DevStatus* st) {
-  const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * OI_WARPS + (threadIdx.x >> 5);
+// OffsetIndex path, step 3 (one block per chunk): first_row of every data
+// page (an exclusive scan of num_values over the chunk's pages, OI_ROWS
+// pages a step), a check that each page starts where the previous one ends,
+// and that the pages cover the chunk's values.
+constexpr int OI_ROWS = 256;
+
+__global__ void __launch_bounds__(OI_ROWS) k_index_oi_rows(const ChunkDev* __restrict__ chunks, int n_chunks,
+                                                           PageDev* pages, DevStatus* st) {
+  constexpr int kWarps = OI_ROWS / 32;
+  __shared__ int64_t wsum[kWarps];
+  __shared__ uint64_t wend[kWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c = blockIdx.x;
   if (c >= n_chunks) return;
   const ChunkDev ch = chunks[c];
   int64_t row = 0;
-  uint64_t prev_end = 0;  // end of the page before this group of 32
+  uint64_t prev_end = 0;  // end of the page before this step's pages
   bool bad = false;
-  for (uint32_t k0 = 0; k0 < ch.page_count; k0 += 32) {
-    const uint32_t k = k0 + lane;
+  for (uint32_t k0 = 0; k0 < ch.page_count; k0 += OI_ROWS) {
+    const uint32_t k = k0 + threadIdx.x;
     const bool have = k < ch.page_count;
     PageDev* pg = pages + ch.page_begin + k;
     uint64_t off = 0, end = 0;
     int64_t nv = 0;
+    int32_t type = PAGE_DICT;
     if (have) {
       off = pg->offset;
       end = off + static_cast<uint64_t>(pg->header_len) + static_cast<uint64_t>(pg->compressed);
-      nv = pg->page_type != PAGE_DICT ? pg->num_values : 0;
+      type = pg->page_type;
+      nv = type != PAGE_DICT ? pg->num_values : 0;
     }
-    uint64_t before = __shfl_up_sync(0xffffffffu, end, 1);
-    if (lane == 0) before = prev_end;
-    bad |= have && off != before;
     int64_t incl = nv;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += y;
     }
-    if (have && pg->page_type != PAGE_DICT) pg->first_row = row + incl - nv;
-    row += __shfl_sync(0xffffffffu, incl, 31);
-    prev_end = __shfl_sync(0xffffffffu, end, 31);
+    uint64_t before = __shfl_up_sync(0xffffffffu, end, 1);
+    if (lane == 31) {
+      wsum[w] = incl;
+      wend[w] = end;
+    }
+    __syncthreads();
+    if (lane == 0) before = w == 0 ? prev_end : wend[w - 1];
+    int64_t base = row;
+    for (int q = 0; q < w; ++q) base += wsum[q];
+    bad |= have && off != before;
+    if (have && type != PAGE_DICT) pg->first_row = base + incl - nv;
+    for (int q = 0; q < kWarps; ++q) row += wsum[q];
+    prev_end = wend[kWarps - 1];  // (unused after a partial last step)
+    __syncthreads();  // wsum and wend are rewritten by the next step
   }
-  const unsigned badm = __ballot_sync(0xffffffffu, bad);
-  if (badm && lane == __ffs(badm) - 1) {
-    // the first page (in this lane's last group) found out of place
-    report(st, DERR_CORRUPT, -1 - c, WHERE_INDEX, 15);
+  if (__syncthreads_or(bad)) {
+    if (threadIdx.x == 0) report(st, DERR_CORRUPT, -1 - c, WHERE_INDEX, 15);
+  } else if (threadIdx.x == 0 && row != ch.num_values) {
+    report(st, DERR_CORRUPT, -1 - c, WHERE_INDEX, 16);
   }
-  if (lane == 0 && !badm && row != ch.num_values) report(st, DERR_CORRUPT, -1 - c, WHERE_INDEX, 16);
 }
 
 // The first min(len[i], 16) bytes at ptr[i] into out[16 i ..] (the rest
@@ -375,7 +389,7 @@ void launch_index_oi(const ChunkDev* chunks, int n_chunks, const int64_t* chunk_
   const int blocks = (n_chunks + OI_WARPS - 1) / OI_WARPS;
   k_index_oi_locations<<<blocks, 32 * OI_WARPS, 0, s>>>(chunks, n_chunks, chunk_file_off, pages, st);
   if (n_pages > 0) k_index_oi_headers<<<(n_pages + 127) / 128, 128, 0, s>>>(chunks, pages, n_pages, st);
-  k_index_oi_rows<<<blocks, 32 * OI_WARPS, 0, s>>>(chunks, n_chunks, pages, st);
+  k_index_oi_rows<<<n_chunks, OI_ROWS, 0, s>>>(chunks, n_chunks, pages, st);
 }
 void launch_gather16(const uint8_t* const* ptr, const int32_t* len, int n, uint8_t* out, cudaStream_t s) {
   if (n <= 0) return;

@@ -53,6 +53,7 @@ struct SnIn {
   uint64_t* m1;
   uint32_t w0, w1, n0, n1, p0, p1;
   uint32_t e1;  // a copy into window 1 is in flight
+  uint32_t cap; // window bytes
 };
 
 __device__ __forceinline__ void sn_swap(SnIn& s) {
@@ -63,15 +64,15 @@ __device__ __forceinline__ void sn_swap(SnIn& s) {
   t = s.p0; s.p0 = s.p1; s.p1 = t;
 }
 
-// Copy of input [from, from + kWin) (16-byte aligned start, at most 16 bytes
-// past the input) into buffer `buf`.
+// Copy of input [from, from + s.cap) (16-byte aligned start, at most 16
+// bytes past the input) into buffer `buf`.
 __device__ __forceinline__ void sn_issue(const SnIn& s, uint8_t* buf, uint64_t* bar, uint32_t from, uint32_t* w,
                                          uint32_t* n) {
   const uintptr_t base = reinterpret_cast<uintptr_t>(s.in);
   const uintptr_t a = (base + from) & ~uintptr_t(15);
   const uintptr_t lim = (base + s.in_len + 16) & ~uintptr_t(15);
   uint32_t bytes = static_cast<uint32_t>(lim > a ? lim - a : 16);
-  if (bytes > kWin) bytes = kWin;
+  if (bytes > s.cap) bytes = s.cap;
   if (bytes < 16) bytes = 16;
   *w = static_cast<uint32_t>(a - base);
   *n = bytes;
@@ -88,6 +89,15 @@ __device__ __forceinline__ void sn_prefetch(SnIn& s) {
   } else {
     s.n1 = 0;
   }
+}
+
+// 32-bit load from a shared-memory address (the windows are read this way
+// on the serial header chains: fewer and cheaper loads than bytes through
+// generic pointers).
+__device__ __forceinline__ uint32_t lds32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
 }
 
 // Makes input bytes [p, p + 5) readable in window 0 (bytes past the input
@@ -249,7 +259,7 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
   };
   for (int j = wid; j < n_jobs; j += nwarps) {
     const SnappyJob jb = jobs[j];
-    if (jb.codec != CODEC_SNAPPY) {  // another codec's kernel takes it
+    if (jb.codec != CODEC_SNAPPY || jb.nsub > 1) {  // another codec's kernel, or the page's blocks, take it
       page_done();
       continue;
     }
@@ -274,15 +284,18 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
     const uint32_t in_len = jb.src_len - jb.prefix;
     uint8_t* out = jb.dst + jb.prefix;
     const uint32_t out_len = jb.dst_len - jb.prefix;
-    uint64_t declared = 0;
-    int pl = uleb([&](uint32_t k) { return static_cast<uint32_t>(__ldg(in + k)); }, 0, in_len, &declared);
-    if (pl == 0 || declared != out_len) {
-      if (lane == 0) report(st, DERR_CORRUPT, jb.page, WHERE_SNAPPY, 3);
-      page_done();
-      continue;
+    uint64_t declared = out_len;
+    int pl = 0;  // a block of a split page has no length preamble
+    if (!(jb.flags & SJ_BLOCK)) {
+      pl = uleb([&](uint32_t k) { return static_cast<uint32_t>(__ldg(in + k)); }, 0, in_len, &declared);
+      if (pl == 0 || declared != out_len) {
+        if (lane == 0) report(st, DERR_CORRUPT, jb.page, WHERE_SNAPPY, 3);
+        page_done();
+        continue;
+      }
     }
     // lane 0's window state
-    SnIn sin{in, in_len, sw.win[0], sw.win[1], &sw.bar[0], &sw.bar[1], 0, 0, 0, 0, par[0], par[1], 0};
+    SnIn sin{in, in_len, sw.win[0], sw.win[1], &sw.bar[0], &sw.bar[1], 0, 0, 0, 0, par[0], par[1], 0, kWin};
     int bad = 0;
     if (lane == 0) {
       sn_issue(sin, sin.b0, sin.m0, 0, &sin.w0, &sin.n0);
@@ -305,8 +318,11 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
           if (!here && e > 0) break;
           if (!sn_ensure(sin, p)) { bad = 2; break; }
           // the tag and the 4 bytes after it (slack past the input end is never used)
-          const uint8_t* q = sin.b0 + (p - sin.w0);
-          const uint32_t tag = q[0], x1 = q[1], x2 = q[2], x3 = q[3], x4 = q[4];
+          const uint32_t qa = smem_u32(sin.b0) + (p - sin.w0);
+          const uint64_t qv = ((static_cast<uint64_t>(lds32((qa & ~3u) + 4u)) << 32) | lds32(qa & ~3u)) >> (8 * (qa & 3u));
+          const uint32_t tag = static_cast<uint32_t>(qv) & 0xffu, x1 = static_cast<uint32_t>(qv >> 8) & 0xffu,
+                         x2 = static_cast<uint32_t>(qv >> 16) & 0xffu, x3 = static_cast<uint32_t>(qv >> 24) & 0xffu,
+                         x4 = static_cast<uint32_t>(qv >> 32) & 0xffu;
           ++p;
           uint32_t kind = tag & 3, len, arg;
           if (kind == 0) {
@@ -472,6 +488,173 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
     __syncwarp();
     page_done();
   }
+}
+
+// Fragment scan of the split pages: lane 0 of a warp parses a page's element
+// headers through two shared-memory windows (as the decoder does, wider) and
+// cuts a block wherever the output reaches a multiple of SNAPPY_FRAGMENT at
+// an element boundary.  A copy whose source lies before its block's start,
+// or anything the decoder would reject, makes the page one job again
+// (decompressed whole, where the decoder reports what is wrong).  The blocks
+// go to the plan's block list at the page's slots; slots the page does not
+// use become no-op jobs.  The header chain is serial, so each step is kept
+// short: the tag and the four bytes after it come from two 32-bit shared
+// loads.
+constexpr uint32_t kSplitWin = 8192;
+constexpr int kSplitWarps = 4;
+struct SnSplitWarp {
+  uint64_t bar[2];
+  uint8_t win[2][kSplitWin + 16];
+};
+
+__global__ void __launch_bounds__(32 * kSplitWarps) k_snappy_split(const SnappyJob* __restrict__ jobs, int n_jobs,
+                                                                   SnappyJob* blocks, DevStatus* st) {
+  extern __shared__ __align__(16) uint8_t sp_smem[];
+  const int lane = threadIdx.x & 31;
+  SnSplitWarp& sw = reinterpret_cast<SnSplitWarp*>(sp_smem)[threadIdx.x >> 5];
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  if (lane == 0) {
+    mbar_init(&sw.bar[0], 1);
+    mbar_init(&sw.bar[1], 1);
+  }
+  fence_mbar_init();
+  __syncwarp();
+  uint32_t par[2] = {0, 0};
+  for (int j = wid; j < n_jobs; j += nwarps) {
+    const SnappyJob jb = jobs[j];
+    if (jb.codec != CODEC_SNAPPY || jb.nsub <= 1) continue;
+    const bool shape = !jb.raw && jb.prefix <= jb.src_len && jb.prefix <= jb.dst_len;
+    if (shape) warp_copy<true>(jb.dst, jb.src, jb.prefix, lane);  // V2 level bytes, never compressed
+    if (lane == 0) {
+      const uint8_t* in = jb.src + jb.prefix;
+      uint8_t* out = jb.dst + jb.prefix;
+      const uint32_t in_len = shape ? jb.src_len - jb.prefix : 0u;
+      const uint32_t out_len = shape ? jb.dst_len - jb.prefix : 0u;
+      SnappyJob* bl = blocks + jb.sub;
+      auto emit = [&](uint32_t q, uint32_t i0, uint32_t i1, uint32_t o0, uint32_t o1) {
+        SnappyJob b{};
+        b.src = in + i0;
+        b.dst = out + o0;
+        b.src_len = i1 - i0;
+        b.dst_len = o1 - o0;
+        b.page = jb.page;
+        b.codec = CODEC_SNAPPY;
+        b.flags = SJ_BLOCK;
+        bl[q] = b;
+      };
+      auto empty = [&](uint32_t q) {
+        SnappyJob b{};
+        b.page = jb.page;
+        bl[q] = b;  // codec 0: no kernel takes it
+      };
+      uint64_t declared = 0;
+      int pl = 0;
+      bool ok = shape;
+      if (ok) {
+        pl = uleb([&](uint32_t k) { return static_cast<uint32_t>(__ldg(in + k)); }, 0, in_len, &declared);
+        ok = pl != 0 && declared == out_len;
+      }
+      SnIn sin{in, in_len, sw.win[0], sw.win[1], &sw.bar[0], &sw.bar[1], 0, 0, 0, 0, par[0], par[1], 0, kSplitWin};
+      bool loaded = false, timeout = false;
+      if (ok) {
+        sn_issue(sin, sin.b0, sin.m0, 0, &sin.w0, &sin.n0);
+        loaded = true;
+        if (!mbar_wait(sin.m0, sin.p0)) timeout = true;
+        sin.p0 ^= 1u;
+        if (!timeout) sn_prefetch(sin);
+        ok = !timeout;
+      }
+      uint32_t p = static_cast<uint32_t>(pl), o = 0, k = 0, bi = p, bo = 0;
+      uint32_t next_cut = SNAPPY_FRAGMENT;
+      // shared address of input offset x: sbase + x (mod 2^32)
+      uint32_t sbase = smem_u32(sin.b0) - sin.w0;
+      // each element consumes >= 2 input bytes
+      for (uint32_t guard = 0; ok && p < in_len && guard <= in_len; ++guard) {
+        if (!(p - sin.w0 < sin.n0 && (p - sin.w0 + 5 <= sin.n0 || sin.w0 + sin.n0 >= in_len))) {
+          if (!sn_ensure(sin, p)) {
+            timeout = true;
+            ok = false;
+            break;
+          }
+          sbase = smem_u32(sin.b0) - sin.w0;
+        }
+        // bytes p .. p + 4 (window slack past the input is never used)
+        const uint32_t a = sbase + p;
+        const uint32_t lo = lds32(a & ~3u), hi = lds32((a & ~3u) + 4u);
+        const uint64_t v = ((static_cast<uint64_t>(hi) << 32) | lo) >> (8 * (a & 3u));
+        const uint32_t tag = static_cast<uint32_t>(v) & 0xffu;
+        const uint32_t x = static_cast<uint32_t>(v >> 8);
+        const uint32_t kind = tag & 3, t6 = tag >> 2;
+        const uint32_t left = in_len - p - 1;  // bytes after the tag
+        uint32_t len, hl, arg;
+        if (kind == 0) {
+          const uint32_t nb = t6 < 60 ? 0u : t6 - 59;
+          const uint32_t vm = nb == 0 ? t6 : (nb == 4 ? x : (x & ((1u << (8 * nb)) - 1u)));
+          if (nb > left || vm == 0xffffffffu) { ok = false; break; }
+          len = vm + 1;
+          hl = 1 + nb;
+          if (len > left - nb) { ok = false; break; }
+          arg = 0;
+        } else {
+          hl = kind == 1 ? 2u : (kind == 2 ? 3u : 5u);
+          if (hl - 1 > left) { ok = false; break; }
+          len = kind == 1 ? 4 + (t6 & 7) : t6 + 1;
+          arg = kind == 1 ? (((tag >> 5) << 8) | (x & 0xffu)) : (kind == 2 ? (x & 0xffffu) : x);
+          // copies stay inside their block
+          if (arg == 0 || arg > o - bo) { ok = false; break; }
+        }
+        if (len > out_len - o) { ok = false; break; }
+        o += len;
+        p += hl + (kind == 0 ? len : 0u);
+        if (o >= next_cut && o < out_len) {
+          const uint32_t nk = o / SNAPPY_FRAGMENT;
+          if (nk >= jb.nsub) { ok = false; break; }
+          emit(k, bi, p, bo, o);
+          for (uint32_t e = k + 1; e < nk; ++e) empty(e);
+          k = nk;
+          bi = p;
+          bo = o;
+          next_cut = (k + 1) * SNAPPY_FRAGMENT;
+        }
+      }
+      if (ok && p == in_len && o == out_len) {
+        emit(k, bi, p, bo, o);
+        for (uint32_t e = k + 1; e < jb.nsub; ++e) empty(e);
+      } else {
+        // one job for the whole page (its prefix is copied again there)
+        SnappyJob w = jb;
+        w.nsub = 0;
+        w.sub = 0;
+        bl[0] = w;
+        for (uint32_t e = 1; e < jb.nsub; ++e) empty(e);
+        if (timeout) report(st, DERR_TIMEOUT, jb.page, WHERE_SNAPPY, 6);
+      }
+      if (loaded && sin.e1) {  // settle the window copy still in flight before the buffers are reused
+        mbar_wait(sin.m1, sin.p1);
+        sin.p1 ^= 1u;
+        sin.e1 = 0;
+      }
+      const bool sw0 = sin.b0 == sw.win[0];
+      par[0] = sw0 ? sin.p0 : sin.p1;
+      par[1] = sw0 ? sin.p1 : sin.p0;
+    }
+    __syncwarp();
+  }
+}
+
+void launch_snappy_split(const SnappyJob* jobs, int n_jobs, SnappyJob* blocks, int n_sms, DevStatus* st,
+                         cudaStream_t s) {
+  if (n_jobs <= 0) return;
+  static bool attr = false;
+  constexpr uint32_t smem = kSplitWarps * sizeof(SnSplitWarp);
+  if (!attr) {
+    cudaFuncSetAttribute(k_snappy_split, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  int blocks_n = (n_jobs + kSplitWarps - 1) / kSplitWarps;
+  if (blocks_n > n_sms * 3) blocks_n = n_sms * 3;
+  k_snappy_split<<<blocks_n, 32 * kSplitWarps, smem, s>>>(jobs, n_jobs, blocks, st);
 }
 
 void launch_snappy(const SnappyJob* jobs, int n_jobs, int n_sms, DevStatus* st, cudaStream_t s, bool coop) {

@@ -235,7 +235,10 @@ void delta_stream32(Bytes& o, const std::vector<int64_t>& v) {
 
 // ------------------------------------------------------------------ Snappy compressor
 
-// Greedy LZ77 over 4-byte sequences with a hash table of recent positions.
+// Greedy LZ77 over 4-byte sequences with a hash table of recent positions,
+// in 64 KiB fragments of the input, each on its own (the table starts empty,
+// and matches and literals stay inside the fragment), which is how the
+// reference Snappy compressor frames its output.
 void snappy_compress(const uint8_t* in, size_t n, Bytes& o) {
   o.clear();
   uleb(o, n);
@@ -273,37 +276,42 @@ void snappy_compress(const uint8_t* in, size_t n, Bytes& o) {
       len -= c;
     }
   };
-  if (n < 16) {
-    literal(0, n);
-    return;
-  }
   const int kBits = 14;
-  std::vector<int64_t> table(size_t(1) << kBits, -1);
+  std::vector<int64_t> table(size_t(1) << kBits);
   auto h4 = [&](size_t i) {
     uint32_t x;
     memcpy(&x, in + i, 4);
     return (x * 0x1e35a7bdu) >> (32 - kBits);
   };
-  size_t i = 0, lit = 0;
-  const size_t limit = n - 4;
-  while (i <= limit) {
-    uint32_t h = h4(i);
-    int64_t cand = table[h];
-    table[h] = static_cast<int64_t>(i);
-    if (cand >= 0 && i - cand < (1u << 31) && memcmp(in + cand, in + i, 4) == 0) {
-      size_t len = 4;
-      while (i + len < n && in[cand + len] == in[i + len]) ++len;
-      literal(lit, i);
-      copy(i - cand, len);
-      size_t end = i + len;
-      for (size_t k = i + 1; k < end && k <= limit; k += 2) table[h4(k)] = static_cast<int64_t>(k);
-      i = end;
-      lit = i;
-    } else {
-      ++i;
+  constexpr size_t kFragment = 65536;
+  for (size_t f0 = 0; f0 < n; f0 += kFragment) {
+    const size_t f1 = std::min(n, f0 + kFragment);
+    if (f1 - f0 < 16) {
+      literal(f0, f1);
+      continue;
     }
+    std::fill(table.begin(), table.end(), int64_t(-1));
+    size_t i = f0, lit = f0;
+    const size_t limit = f1 - 4;
+    while (i <= limit) {
+      uint32_t h = h4(i);
+      int64_t cand = table[h];
+      table[h] = static_cast<int64_t>(i);
+      if (cand >= 0 && memcmp(in + cand, in + i, 4) == 0) {
+        size_t len = 4;
+        while (i + len < f1 && in[cand + len] == in[i + len]) ++len;
+        literal(lit, i);
+        copy(i - cand, len);
+        size_t end = i + len;
+        for (size_t k = i + 1; k < end && k <= limit; k += 2) table[h4(k)] = static_cast<int64_t>(k);
+        i = end;
+        lit = i;
+      } else {
+        ++i;
+      }
+    }
+    literal(lit, f1);
   }
-  literal(lit, n);
 }
 
 // ------------------------------------------------------------------ Zstandard compressor

@@ -469,3 +469,33 @@ def test_large_offset_index(eng):
     assert got == exp
     N.pq_free_index(idx)
     _roundtrip(eng, data)
+
+
+def _concat_results(a, b):
+    """Rows of oracle ColumnResult a followed by those of b."""
+    from oracle.reader import ColumnResult
+    valid = None if a.valid is None else np.concatenate([a.valid, b.valid])
+    if a.ptype == "BYTE_ARRAY":
+        off = np.concatenate([a.offsets, b.offsets[1:] + a.offsets[-1]])
+        return ColumnResult(a.name, a.ptype, None, valid, off, np.concatenate([a.chars, b.chars]))
+    return ColumnResult(a.name, a.ptype, np.concatenate([a.values, b.values]), valid)
+
+
+def test_snappy_split_pages(eng):
+    """Snappy pages of several 64 KiB fragments from the native writer (framed
+    as the reference compressor frames them: data pages of 1 MiB, dictionary
+    pages of hundreds of KB), decompressed fragment by fragment; V1 and V2.
+    The same table from the oracle writer (whole-page matches, no such
+    framing) is read in the same scan, so that its large pages take the
+    whole-page path next to the split ones."""
+    from paper_2602_17335_gb300.tables import write_table
+    tab = synth.config2_table(240_000, 120_000, string_pool_size=20_000, zipf_k=5000)
+    for version in (1, 2):
+        spec = synth.config2_spec(120_000, 1 << 20, "SNAPPY", version)
+        for c in spec.columns:
+            c.compress_threshold = -1.0
+        native = bytes(write_table(tab, spec))
+        _roundtrip(eng, native)
+        oracle = W.write_file(tab, spec)
+        expect = [_concat_results(a, b) for a, b in zip(R.read_file(native), R.read_file(oracle))]
+        assert_columns_equal(eng.read([to_dev(native), to_dev(oracle)]), expect)

@@ -482,3 +482,80 @@ def test_pyarrow_reads_chosen_encodings_with_codecs(writer):
                     v = np.asarray(col.values).tolist()
                     exp = v if col.valid is None else [x if m else None for x, m in zip(v, col.valid)]
                 assert got == exp, (writer, codec, version, col.name)
+
+
+def _snappy_elements(b):
+    """(declared length, [(kind, output offset, length, copy offset)]) of a raw
+    Snappy block, parsed here on its own."""
+    i, x, sh = 0, 0, 0
+    while True:
+        y = b[i]
+        i += 1
+        x |= (y & 0x7F) << sh
+        sh += 7
+        if not y & 0x80:
+            break
+    out, els = 0, []
+    while i < len(b):
+        t = b[i]
+        kind = t & 3
+        if kind == 0:
+            n = t >> 2
+            i += 1
+            if n >= 60:
+                nb = n - 59
+                n = int.from_bytes(b[i:i + nb], "little")
+                i += nb
+            els.append((0, out, n + 1, 0))
+            i += n + 1
+            out += n + 1
+            continue
+        if kind == 1:
+            n, off = 4 + ((t >> 2) & 7), ((t >> 5) << 8) | b[i + 1]
+            i += 2
+        elif kind == 2:
+            n, off = (t >> 2) + 1, int.from_bytes(b[i + 1:i + 3], "little")
+            i += 3
+        else:
+            n, off = (t >> 2) + 1, int.from_bytes(b[i + 1:i + 5], "little")
+            i += 5
+        els.append((kind, out, n, off))
+        out += n
+    return x, els
+
+
+def test_native_snappy_fragments():
+    """The native writer frames Snappy pages as the reference compressor does:
+    64 KiB fragments compressed on their own, so that every multiple of 65536
+    in a page's output starts an element and no copy reads before the start
+    of its own fragment (the GPU reader decompresses large pages fragment by
+    fragment on that basis); the pages still read back to the table."""
+    _, write_table = _native()
+    tab = synth.config2_table(200_000, 200_000, string_pool_size=3000, zipf_k=5000)
+    spec = synth.config2_spec(200_000, 1 << 20, "SNAPPY", 1)
+    for c in spec.columns:
+        c.compress_threshold = -1.0
+    native = bytes(write_table(tab, spec))
+    info = R.parse_footer(native)
+    big = 0
+    for ch in info.chunks:
+        for p in R.chunk_pages(native, ch):
+            body = native[p.offset + p.header_len:p.offset + p.header_len + p.compressed]
+            n, els = _snappy_elements(body)
+            assert n == p.uncompressed
+            starts = {o for _, o, _, _ in els}
+            for f in range(65536, n, 65536):
+                assert f in starts, (ch.column, f)
+            for kind, o, ln, off in els:
+                if kind:
+                    assert o - off >= (o // 65536) * 65536, (ch.column, o, off)
+                assert (o + ln - 1) // 65536 == o // 65536, (ch.column, o, ln)
+            big += n > 2 * 65536
+    assert big >= 8  # dictionary and data pages of several fragments
+    res = R.read_file(native)
+    for col, r in zip(tab.columns, res):
+        if col.ptype == "BYTE_ARRAY":
+            got = [bytes(r.chars[r.offsets[j]:r.offsets[j + 1]]) for j in range(len(r.offsets) - 1)]
+            assert got == _string_rows(col), col.name
+        else:
+            assert np.array_equal(np.asarray(col.values).view(np.uint8), r.values.view(np.uint8)), col.name
