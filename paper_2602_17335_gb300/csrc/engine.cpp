@@ -751,6 +751,21 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
   std::vector<int64_t> walk_cost;     // estimated chain steps per walked page
   std::vector<int32_t> dict_job_of_chunk(idx->chunks.size(), -1);
   uint32_t blk_data = 0, blk_dict = 0;  // block slots of split data / dictionary pages
+  {
+    // at most every indexed page of the requested columns, once per row segment
+    size_t np = 0;
+    for (size_t ch = 0; ch < idx->chunks.size(); ++ch)
+      for (int32_t c : cols)
+        if (idx->chunk_col[ch] == c) np += idx->chunks[ch].page_count;
+    np *= segs.size();
+    plan->pps.reserve(np);
+    plan->walk_pps.reserve(np);
+    walk_cost.reserve(np);
+    if (idx->chunks.size() && idx->chunks[0].codec != pqi::CODEC_NONE) {
+      plan->snappy_data.reserve(np);
+      data_job_off.reserve(np);
+    }
+  }
   for (size_t oc = 0; oc < plan->cols.size(); ++oc) {
     const int c = plan->cols[oc];
     const auto& cm = idx->schema[c];

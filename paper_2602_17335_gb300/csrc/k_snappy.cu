@@ -33,9 +33,7 @@ constexpr uint32_t kMidLit = 2048;  // literals up to this long go from the inpu
 
 struct SnWarp {
   uint64_t bar[2];
-  uint32_t kl[32];   // kind | len << 2
-  uint32_t arg[32];  // literal: input offset; copy: back offset
-  int32_t woff[32];  // literal inside the batch's input window: its offset there, else -1
+  uint32_t pos[32];      // input offsets of a batch's headers
   uint8_t win[2][kWin + 16];
   uint8_t ring[kRing];
 };
@@ -123,6 +121,65 @@ __device__ __forceinline__ bool sn_ensure(SnIn& s, uint32_t p) {
   sn_swap(s);
   sn_prefetch(s);
   return true;
+}
+
+// The element whose header sits at input offset pa, from its bytes h[0..4]
+// (bytes past the input are never used): kind, length, argument (literal:
+// input offset of its bytes; copy: back offset) and the next header's input
+// offset.  False when the header or the literal runs past the input.
+__device__ __forceinline__ bool sn_hdr(uint32_t tag, uint32_t x, uint32_t pa, uint32_t in_len, uint32_t* kind,
+                                       uint32_t* len, uint32_t* arg, uint32_t* next) {
+  const uint32_t k = tag & 3, t6 = tag >> 2, left = in_len - pa - 1;  // bytes after the tag
+  uint32_t l, a, hl;
+  if (k == 0) {
+    const uint32_t nb = t6 < 60 ? 0u : t6 - 59;
+    const uint32_t vm = nb == 0 ? t6 : (nb == 4 ? x : (x & ((1u << (8 * nb)) - 1u)));
+    if (nb > left || vm == 0xffffffffu) return false;
+    l = vm + 1;
+    hl = 1 + nb;
+    if (l > left - nb) return false;
+    a = pa + hl;
+  } else {
+    hl = k == 1 ? 2u : (k == 2 ? 3u : 5u);
+    if (hl - 1 > left) return false;
+    l = k == 1 ? 4 + (t6 & 7) : t6 + 1;
+    a = k == 1 ? (((tag >> 5) << 8) | (x & 0xffu)) : (k == 2 ? (x & 0xffffu) : x);
+  }
+  *kind = k;
+  *len = l;
+  *arg = a;
+  *next = pa + hl + (k == 0 ? l : 0u);
+  return true;
+}
+
+// Bytes [q, q + 5) of a window as (tag, the 4 bytes after it), from two
+// 32-bit shared loads (the window buffer is readable for 16 bytes past its
+// end).
+__device__ __forceinline__ void sn_bytes5(uint32_t sa, uint32_t* tag, uint32_t* x) {
+  const uint64_t v = ((static_cast<uint64_t>(lds32((sa & ~3u) + 4u)) << 32) | lds32(sa & ~3u)) >> (8 * (sa & 3u));
+  *tag = static_cast<uint32_t>(v) & 0xffu;
+  *x = static_cast<uint32_t>(v >> 8);
+}
+
+// The element whose header sits at input offset p, from its tag and the 4
+// bytes after it, without any check (the element's own decode, or the
+// caller, checks it): the offset of the next header, the output length and
+// the copy offset.  Straight-line code: the header chain is serial, so each
+// step is kept short.
+struct SnStep {
+  uint32_t next, len, arg, kind;
+};
+__device__ __forceinline__ SnStep sn_step(uint32_t tag, uint32_t x, uint32_t p) {
+  const uint32_t kind = tag & 3, t6 = tag >> 2;
+  const uint32_t nb = t6 > 59 ? t6 - 59 : 0u;  // literal length bytes after the tag
+  const uint32_t lv = nb == 0 ? t6 : (x & (0xffffffffu >> (32 - 8 * nb)));
+  const uint32_t hl = (0x5320u >> (4 * kind)) & 15u;  // copy header bytes (kind 1, 2, 3: 2, 3, 5)
+  SnStep r;
+  r.kind = kind;
+  r.next = p + (kind == 0 ? 2 + nb + lv : hl);
+  r.len = kind == 0 ? lv + 1 : (kind == 1 ? 4 + (t6 & 7) : t6 + 1);
+  r.arg = kind == 1 ? (((tag >> 5) << 8) | (x & 0xffu)) : (kind == 2 ? (x & 0xffffu) : x);
+  return r;
 }
 
 // `n` bytes from ring positions [from, from + n) (positions are output
@@ -308,83 +365,72 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
     bad = __shfl_sync(0xffffffffu, bad, 0);
     // each element consumes >= 2 input bytes, so in_len bounds the batches
     for (uint32_t guard = 0; guard <= in_len && ip < in_len && !bad; ++guard) {
-      int n_el = 0;
+      // the batch's window: switched now when ip has left window 0 (a batch's
+      // headers and window literals all sit in one window)
       if (lane == 0) {
-        uint32_t p = ip, o = op, bo = 0;
-        for (int e = 0; e < 32 && p < in_len; ++e) {
-          // a batch's headers all sit in one window (its literals are read
-          // from there): switch windows only at a batch's first element
-          const bool here = p - sin.w0 < sin.n0 && (p - sin.w0 + 5 <= sin.n0 || sin.w0 + sin.n0 >= in_len);
-          if (!here && e > 0) break;
-          if (!sn_ensure(sin, p)) { bad = 2; break; }
-          // the tag and the 4 bytes after it (slack past the input end is never used)
-          const uint32_t qa = smem_u32(sin.b0) + (p - sin.w0);
-          const uint64_t qv = ((static_cast<uint64_t>(lds32((qa & ~3u) + 4u)) << 32) | lds32(qa & ~3u)) >> (8 * (qa & 3u));
-          const uint32_t tag = static_cast<uint32_t>(qv) & 0xffu, x1 = static_cast<uint32_t>(qv >> 8) & 0xffu,
-                         x2 = static_cast<uint32_t>(qv >> 16) & 0xffu, x3 = static_cast<uint32_t>(qv >> 24) & 0xffu,
-                         x4 = static_cast<uint32_t>(qv >> 32) & 0xffu;
-          ++p;
-          uint32_t kind = tag & 3, len, arg;
-          if (kind == 0) {
-            const uint32_t l = tag >> 2;
-            if (l < 60) {
-              len = l + 1;
-            } else {
-              const uint32_t nb = l - 59;
-              if (nb > in_len - p) { bad = 1; break; }
-              const uint32_t v = x1 | (x2 << 8) | (x3 << 16) | (x4 << 24);
-              const uint32_t vm = nb == 4 ? v : (v & ((1u << (8 * nb)) - 1u));
-              p += nb;
-              if (vm == 0xffffffffu) { bad = 1; break; }
-              len = vm + 1;
-            }
-            if (len > in_len - p) { bad = 1; break; }
-            arg = p;
-            p += len;
-          } else if (kind == 1) {
-            if (p >= in_len) { bad = 1; break; }
-            len = 4 + ((tag >> 2) & 7);
-            arg = ((tag >> 5) << 8) | x1;
-            p += 1;
-          } else if (kind == 2) {
-            if (2 > in_len - p) { bad = 1; break; }
-            len = (tag >> 2) + 1;
-            arg = x1 | (x2 << 8);
-            p += 2;
-          } else {
-            if (4 > in_len - p) { bad = 1; break; }
-            len = (tag >> 2) + 1;
-            arg = x1 | (x2 << 8) | (x3 << 16) | (x4 << 24);
-            p += 4;
-          }
-          if (len > out_len - o || (kind != 0 && (arg == 0 || arg > o))) { bad = 1; break; }
-          const bool inwin = kind == 0 && len <= kMidLit && arg - sin.w0 + len <= sin.n0;
-          sw.kl[e] = kind | (len << 2);
-          sw.arg[e] = arg;
-          sw.woff[e] = inwin ? static_cast<int32_t>(arg - sin.w0) : -1;
-          n_el = e + 1;
-          o += len;
-          bo += len;
-          // a batch's output is assembled in the ring; a literal that is not
-          // in the window (or longer than kMidLit) ends its batch: it is
-          // copied to global memory directly
-          if (bo >= kBatchOut - 64 || (kind == 0 && !inwin)) break;
+        const bool here = ip - sin.w0 < sin.n0 && (ip - sin.w0 + 5 <= sin.n0 || sin.w0 + sin.n0 >= in_len);
+        if (!here && !sn_ensure(sin, ip)) bad = 2;
+      }
+      bad = __shfl_sync(0xffffffffu, bad, 0);
+      if (bad) break;
+      const uint8_t* wbuf = sw.win[__shfl_sync(0xffffffffu, lane == 0 && sin.b0 == sw.win[1] ? 1 : 0, 0)];
+      const uint32_t w0 = __shfl_sync(0xffffffffu, sin.w0, 0), n0 = __shfl_sync(0xffffffffu, sin.n0, 0);
+      // lane 0 follows the header chain to up to 32 headers inside the window;
+      // it stops after an element that ends the batch anyway (a literal that
+      // is long or runs past the window, the output budget) or does not parse
+      // (its own lane reports it)
+      int n_pos = 0;
+      if (lane == 0) {
+        uint32_t p = ip, ob = 0;
+        const uint32_t lim = w0 + n0 >= in_len ? n0 : n0 - 4;  // offsets whose header bytes are all here
+        const uint32_t sb = smem_u32(wbuf) - w0;  // shared address of input offset x: sb + x
+        while (n_pos < 32 && p < in_len) {
+          if (p - w0 >= lim) break;
+          sw.pos[n_pos++] = p;
+          uint32_t tag, x;
+          sn_bytes5(sb + p, &tag, &x);
+          const SnStep e = sn_step(tag, x, p);
+          ob += e.len;
+          if (e.next <= p || e.next > in_len || ob >= kBatchOut - 64 ||
+              (e.kind == 0 && (e.len > kMidLit || e.next - w0 > n0)))
+            break;
+          p = e.next;
         }
-        ip = p;
       }
       __syncwarp();
-      n_el = __shfl_sync(0xffffffffu, n_el, 0);
-      bad = __shfl_sync(0xffffffffu, bad, 0);
-      ip = __shfl_sync(0xffffffffu, ip, 0);
-      uint32_t kl = 0, arg = 0;
-      int32_t woff = -1;
-      if (lane < n_el) {
-        kl = sw.kl[lane];
-        arg = sw.arg[lane];
-        woff = sw.woff[lane];
+      n_pos = __shfl_sync(0xffffffffu, n_pos, 0);
+      // every lane decodes its header from the window
+      uint32_t kind = 0, len = 0, arg = 0, nextp = 0;
+      bool hok = true;
+      if (lane < n_pos) {
+        const uint32_t mypos = sw.pos[lane];
+        uint32_t tag, x;
+        sn_bytes5(smem_u32(wbuf) + (mypos - w0), &tag, &x);
+        hok = sn_hdr(tag, x, mypos, in_len, &kind, &len, &arg, &nextp);
       }
-      const uint8_t* wbuf = sw.win[__shfl_sync(0xffffffffu, lane == 0 && sin.b0 == sw.win[1] ? 1 : 0, 0)];
-      const uint32_t kind = kl & 3, len = kl >> 2;
+      // output offsets; the batch ends after its first element that fills the
+      // ring's budget or is a literal outside the window (copied directly)
+      const uint32_t plen = lane < n_pos ? len : 0u;
+      uint32_t pinc = plen;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, pinc, o);
+        if (lane >= o) pinc += y;
+      }
+      const bool inwin = kind == 0 && len <= kMidLit && arg - w0 + len <= n0;
+      const bool trig = lane < n_pos && (!hok || pinc >= kBatchOut - 64 || (kind == 0 && !inwin));
+      const uint32_t tm = __ballot_sync(0xffffffffu, trig);
+      const int n_el = tm ? __ffs(tm) : n_pos;
+      const uint32_t o_e = op + pinc - plen;
+      const bool evalid = hok && len <= out_len - o_e && (kind == 0 || (arg != 0 && arg <= o_e));
+      if (n_el == 0 || __any_sync(0xffffffffu, lane < n_el && !evalid)) {
+        bad = 1;
+        break;
+      }
+      ip = __shfl_sync(0xffffffffu, nextp, n_el - 1);
+      int32_t woff = -1;
+      if (lane < n_el && inwin) woff = static_cast<int32_t>(arg - w0);
+      if (lane >= n_el) kind = len = arg = 0;
       uint32_t incl = len;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -490,16 +536,14 @@ __global__ void __launch_bounds__(kCoop ? 256 : 32 * kSnappyWarps) k_snappy(cons
   }
 }
 
-// Fragment scan of the split pages: lane 0 of a warp parses a page's element
-// headers through two shared-memory windows (as the decoder does, wider) and
-// cuts a block wherever the output reaches a multiple of SNAPPY_FRAGMENT at
-// an element boundary.  A copy whose source lies before its block's start,
-// or anything the decoder would reject, makes the page one job again
-// (decompressed whole, where the decoder reports what is wrong).  The blocks
-// go to the plan's block list at the page's slots; slots the page does not
-// use become no-op jobs.  The header chain is serial, so each step is kept
-// short: the tag and the four bytes after it come from two 32-bit shared
-// loads.
+// Fragment scan of the split pages: lane 0 of a warp follows a page's
+// element headers through two shared-memory windows (as the decoder does,
+// wider) and cuts a block wherever the output reaches a multiple of
+// SNAPPY_FRAGMENT at an element boundary.  A copy whose source lies before
+// its block's start, or anything the decoder would reject, makes the page
+// one job again (decompressed whole, where the decoder reports what is
+// wrong).  The blocks go to the plan's block list at the page's slots; slots
+// the page does not use become no-op jobs.
 constexpr uint32_t kSplitWin = 8192;
 constexpr int kSplitWarps = 4;
 struct SnSplitWarp {
@@ -567,8 +611,7 @@ __global__ void __launch_bounds__(32 * kSplitWarps) k_snappy_split(const SnappyJ
       }
       uint32_t p = static_cast<uint32_t>(pl), o = 0, k = 0, bi = p, bo = 0;
       uint32_t next_cut = SNAPPY_FRAGMENT;
-      // shared address of input offset x: sbase + x (mod 2^32)
-      uint32_t sbase = smem_u32(sin.b0) - sin.w0;
+      uint32_t sb = smem_u32(sin.b0) - sin.w0;  // shared address of input offset x: sb + x
       // each element consumes >= 2 input bytes
       for (uint32_t guard = 0; ok && p < in_len && guard <= in_len; ++guard) {
         if (!(p - sin.w0 < sin.n0 && (p - sin.w0 + 5 <= sin.n0 || sin.w0 + sin.n0 >= in_len))) {
@@ -577,41 +620,29 @@ __global__ void __launch_bounds__(32 * kSplitWarps) k_snappy_split(const SnappyJ
             ok = false;
             break;
           }
-          sbase = smem_u32(sin.b0) - sin.w0;
+          sb = smem_u32(sin.b0) - sin.w0;
         }
-        // bytes p .. p + 4 (window slack past the input is never used)
-        const uint32_t a = sbase + p;
-        const uint32_t lo = lds32(a & ~3u), hi = lds32((a & ~3u) + 4u);
-        const uint64_t v = ((static_cast<uint64_t>(hi) << 32) | lo) >> (8 * (a & 3u));
-        const uint32_t tag = static_cast<uint32_t>(v) & 0xffu;
-        const uint32_t x = static_cast<uint32_t>(v >> 8);
-        const uint32_t kind = tag & 3, t6 = tag >> 2;
-        const uint32_t left = in_len - p - 1;  // bytes after the tag
-        uint32_t len, hl, arg;
-        if (kind == 0) {
-          const uint32_t nb = t6 < 60 ? 0u : t6 - 59;
-          const uint32_t vm = nb == 0 ? t6 : (nb == 4 ? x : (x & ((1u << (8 * nb)) - 1u)));
-          if (nb > left || vm == 0xffffffffu) { ok = false; break; }
-          len = vm + 1;
-          hl = 1 + nb;
-          if (len > left - nb) { ok = false; break; }
-          arg = 0;
-        } else {
-          hl = kind == 1 ? 2u : (kind == 2 ? 3u : 5u);
-          if (hl - 1 > left) { ok = false; break; }
-          len = kind == 1 ? 4 + (t6 & 7) : t6 + 1;
-          arg = kind == 1 ? (((tag >> 5) << 8) | (x & 0xffu)) : (kind == 2 ? (x & 0xffffu) : x);
-          // copies stay inside their block
-          if (arg == 0 || arg > o - bo) { ok = false; break; }
+        uint32_t tag, x;
+        sn_bytes5(sb + p, &tag, &x);
+        const SnStep e = sn_step(tag, x, p);
+        // the element's bytes are in the input; a copy's source lies in its
+        // block; the output stays inside the page
+        const bool bad_lit = e.kind == 0 && (e.len == 0 || e.next < p);
+        const bool bad_copy = e.kind != 0 && (e.arg == 0 || e.arg > o - bo);
+        if (bad_lit || bad_copy || e.next > in_len || e.len > out_len - o) {
+          ok = false;
+          break;
         }
-        if (len > out_len - o) { ok = false; break; }
-        o += len;
-        p += hl + (kind == 0 ? len : 0u);
+        o += e.len;
+        p = e.next;
         if (o >= next_cut && o < out_len) {
           const uint32_t nk = o / SNAPPY_FRAGMENT;
-          if (nk >= jb.nsub) { ok = false; break; }
+          if (nk >= jb.nsub) {
+            ok = false;
+            break;
+          }
           emit(k, bi, p, bo, o);
-          for (uint32_t e = k + 1; e < nk; ++e) empty(e);
+          for (uint32_t e2 = k + 1; e2 < nk; ++e2) empty(e2);
           k = nk;
           bi = p;
           bo = o;
