@@ -156,9 +156,10 @@ __device__ __forceinline__ bool sn_hdr(uint32_t tag, uint32_t x, uint32_t pa, ui
 // 32-bit shared loads (the window buffer is readable for 16 bytes past its
 // end).
 __device__ __forceinline__ void sn_bytes5(uint32_t sa, uint32_t* tag, uint32_t* x) {
-  const uint64_t v = ((static_cast<uint64_t>(lds32((sa & ~3u) + 4u)) << 32) | lds32(sa & ~3u)) >> (8 * (sa & 3u));
-  *tag = static_cast<uint32_t>(v) & 0xffu;
-  *x = static_cast<uint32_t>(v >> 8);
+  const uint32_t a = sa & ~3u, sh = (sa & 3u) * 8;
+  const uint32_t lo = lds32(a), hi = lds32(a + 4);
+  *tag = __funnelshift_r(lo, hi, sh) & 0xffu;
+  *x = __funnelshift_rc(lo, hi, sh + 8);  // (a shift of 32 gives hi)
 }
 
 // The element whose header sits at input offset p, from its tag and the 4
@@ -172,7 +173,8 @@ struct SnStep {
 __device__ __forceinline__ SnStep sn_step(uint32_t tag, uint32_t x, uint32_t p) {
   const uint32_t kind = tag & 3, t6 = tag >> 2;
   const uint32_t nb = t6 > 59 ? t6 - 59 : 0u;  // literal length bytes after the tag
-  const uint32_t lv = nb == 0 ? t6 : (x & (0xffffffffu >> (32 - 8 * nb)));
+  // (a shift by 32 - 8 nb, nb in 1..4: the low nb bytes of x)
+  const uint32_t lv = nb == 0 ? t6 : (x & (0xffffffffu >> ((32 - 8 * nb) & 31)));
   const uint32_t hl = (0x5320u >> (4 * kind)) & 15u;  // copy header bytes (kind 1, 2, 3: 2, 3, 5)
   SnStep r;
   r.kind = kind;
@@ -612,24 +614,31 @@ __global__ void __launch_bounds__(32 * kSplitWarps) k_snappy_split(const SnappyJ
       uint32_t p = static_cast<uint32_t>(pl), o = 0, k = 0, bi = p, bo = 0;
       uint32_t next_cut = SNAPPY_FRAGMENT;
       uint32_t sb = smem_u32(sin.b0) - sin.w0;  // shared address of input offset x: sb + x
+      // offsets below plim have all their header bytes in window 0 (the
+      // window test is one compare per element)
+      auto window_end = [&]() {
+        const uint32_t e = sin.w0 + sin.n0;
+        return sin.w0 + sin.n0 >= in_len ? in_len : e - 4;
+      };
+      uint32_t plim = ok ? window_end() : 0u;
       // each element consumes >= 2 input bytes
       for (uint32_t guard = 0; ok && p < in_len && guard <= in_len; ++guard) {
-        if (!(p - sin.w0 < sin.n0 && (p - sin.w0 + 5 <= sin.n0 || sin.w0 + sin.n0 >= in_len))) {
+        if (p - sin.w0 >= plim - sin.w0) {
           if (!sn_ensure(sin, p)) {
             timeout = true;
             ok = false;
             break;
           }
           sb = smem_u32(sin.b0) - sin.w0;
+          plim = window_end();
         }
         uint32_t tag, x;
         sn_bytes5(sb + p, &tag, &x);
         const SnStep e = sn_step(tag, x, p);
-        // the element's bytes are in the input; a copy's source lies in its
-        // block; the output stays inside the page
-        const bool bad_lit = e.kind == 0 && (e.len == 0 || e.next < p);
-        const bool bad_copy = e.kind != 0 && (e.arg == 0 || e.arg > o - bo);
-        if (bad_lit || bad_copy || e.next > in_len || e.len > out_len - o) {
+        // the element's bytes are in the input (no wrap, a literal's length
+        // below 2^32); a copy's source lies in its block; the output stays
+        // inside the page
+        if ((e.next - p - 1) >= in_len - p || e.len - 1 >= out_len - o || (e.kind != 0 && e.arg - 1 >= o - bo)) {
           ok = false;
           break;
         }
