@@ -254,23 +254,204 @@ __device__ bool oi_locations_tokens(uint8_t* raw, uint16_t* starts, const uint8_
   return i == n;
 }
 
-__global__ void __launch_bounds__(32 * OI_WARPS) k_index_oi_locations(const ChunkDev* __restrict__ chunks,
-                                                                      int n_chunks,
-                                                                      const int64_t* __restrict__ chunk_file_off,
-                                                                      PageDev* pages, DevStatus* st) {
-  __shared__ __align__(16) uint8_t raw[OI_WARPS][OI_SMEM + 32];
-  __shared__ uint16_t starts[OI_WARPS][OI_STARTS];
+// Chunks whose OffsetIndex exceeds OI_SMEM take a block: the page-location
+// list is cut into OI_SEG-byte segments, one per warp per round; each warp
+// counts the token ends of its segment, a block scan gives every segment the
+// number of tokens before it, and each warp then finds the structs that
+// start in its segment (struct k starts after token 7k - 1; a segment
+// starts one when the tokens before it are a multiple of seven) and parses
+// them, one per lane, from a staged copy that runs 64 bytes into the next
+// segment (a struct takes at most 34 bytes).  Smaller ones take the warp
+// path above, one chunk per warp of the block.
+constexpr int OI_BWARPS = 8;
+constexpr uint32_t OI_SEG = 4096;
+constexpr uint32_t OI_SEG_STARTS = OI_SEG / 7 + 2;
+static_assert(OI_BWARPS == 2 * OI_WARPS, "a block holds OI_WARPS warp-path chunks or one segmented chunk");
+
+__device__ bool oi_locations_segments(uint8_t (*raw)[OI_SEG + 96], uint16_t (*starts)[OI_SEG_STARTS], uint32_t* wcnt,
+                                      int* flags, const uint8_t* oi, uint32_t oi_len, int c, const ChunkDev& ch,
+                                      int64_t file_off, PageDev* pages) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t slot = ch.dict_page >= 0 ? 1u : 0u;
+  // list header (every thread reads the same bytes)
+  if (oi_len < 2 || __ldg(oi) != 0x19 || (__ldg(oi + 1) & 15) != 12) return false;
+  uint64_t n = __ldg(oi + 1) >> 4;
+  uint32_t pos0 = 2;
+  if (n == 15) {
+    uint64_t v = 0;
+    int b = 0;
+    for (; b < 10 && pos0 < oi_len; ++b) {
+      const uint32_t y = __ldg(oi + pos0++);
+      v |= static_cast<uint64_t>(y & 0x7f) << (7 * b);
+      if (!(y & 0x80)) break;
+    }
+    if (b == 10 || (__ldg(oi + pos0 - 1) & 0x80)) return false;
+    n = v;
+  }
+  if (n != ch.oi_pages) return false;
+  const uint32_t L = oi_len - pos0;  // bytes from struct 0 on
+  if (threadIdx.x == 0) {
+    flags[0] = 0;  // a struct that does not parse
+    flags[1] = 0;  // structs written
+  }
+  __syncthreads();
+  uint64_t carry = 0;  // token ends before this round
+  for (uint32_t r0 = 0; r0 < L; r0 += OI_BWARPS * OI_SEG) {
+    const uint32_t g0 = r0 + static_cast<uint32_t>(w) * OI_SEG;
+    const uint32_t glen = g0 < L ? min(OI_SEG, L - g0) : 0u;
+    const uint32_t slen = g0 < L ? min(glen + 64, L - g0) : 0u;  // staged bytes
+    uint32_t sh = 0;
+    if (slen) {
+      const uintptr_t a0 = reinterpret_cast<uintptr_t>(oi + pos0 + g0);
+      sh = static_cast<uint32_t>(a0 & 15);
+      const uint4* src = reinterpret_cast<const uint4*>(a0 - sh);
+      const uint32_t nv = (sh + slen + 15) >> 4;
+      for (uint32_t v = lane; v < nv; v += 32) reinterpret_cast<uint4*>(raw[w])[v] = __ldg(src + v);
+    }
+    __syncwarp();
+    const uint8_t* sb = raw[w] + sh;
+    // token ends of the segment
+    uint32_t cnt = 0;
+    for (uint32_t q = 4 * static_cast<uint32_t>(lane); q < glen; q += 128)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cnt += (q + j < glen && !(sb[q + j] & 0x80)) ? 1u : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) wcnt[w] = cnt;
+    __syncthreads();
+    uint64_t base = carry;
+    uint64_t total = 0;
+    for (int k = 0; k < OI_BWARPS; ++k) {
+      if (k < w) base += wcnt[k];
+      total += wcnt[k];
+    }
+    // struct starts in [0, glen): byte 0 when the tokens before it are a
+    // multiple of seven, and the byte after every 7th token end
+    const uint64_t first = (base + 6) / 7;  // index of the first struct starting here
+    if (glen && lane == 0 && base % 7 == 0) starts[w][0] = 0;
+    uint64_t tb = base;
+    for (uint32_t q0 = 0; q0 < glen; q0 += 128) {
+      const uint32_t q = q0 + 4 * static_cast<uint32_t>(lane);
+      uint32_t em = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (q + j < glen && !(sb[q + j] & 0x80)) em |= 1u << j;
+      const uint32_t ec = __popc(em);
+      uint32_t incl = ec;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      uint64_t t = tb + incl - ec;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if ((em >> j) & 1u) {
+          if ((t + 1) % 7 == 0 && q + j + 1 < glen) {
+            const uint64_t k = (t + 1) / 7 - first;
+            if (k < OI_SEG_STARTS) starts[w][k] = static_cast<uint16_t>(q + j + 1);
+          }
+          ++t;
+        }
+      }
+      tb += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    // the structs starting here are those whose preceding token count, a
+    // multiple of seven, is reached before the segment's last byte (a token
+    // ending at the last byte starts the next segment's first struct)
+    const uint64_t tex = tb - ((glen && !(sb[glen - 1] & 0x80)) ? 1u : 0u);
+    const uint64_t last = tex / 7 + 1;  // first struct index not starting here
+    const uint64_t nhere = (glen && last > first) ? last - first : 0;
+    // (structs whose index reaches n are past the list)
+    const uint64_t left = first < n ? n - first : 0;
+    const uint64_t lim = nhere < left ? nhere : left;
+    int wrote = 0;
+    for (uint64_t k = lane; k < lim; k += 32) {
+      const uint8_t* p = sb + starts[w][k];
+      const uint8_t* e = sb + slen;
+      auto varint = [&](uint64_t* v) -> bool {
+        uint64_t x = 0;
+        for (int b = 0; b < 10 && p < e; ++b) {
+          const uint32_t y = *p++;
+          x |= static_cast<uint64_t>(y & 0x7f) << (7 * b);
+          if (!(y & 0x80)) {
+            *v = x;
+            return true;
+          }
+        }
+        return false;
+      };
+      uint64_t off = 0, skip = 0;
+      bool sok = p < e && *p++ == 0x16 && varint(&off);
+      sok = sok && p < e && *p++ == 0x15 && varint(&skip);
+      sok = sok && p < e && *p++ == 0x16 && varint(&skip);
+      sok = sok && p < e && *p++ == 0x00;
+      const int64_t rel = static_cast<int64_t>(off >> 1) ^ -static_cast<int64_t>(off & 1);
+      const int64_t r = rel - file_off;
+      sok = sok && r >= 0 && static_cast<uint64_t>(r) < ch.size;
+      if (sok) {
+        PageDev d{};
+        d.offset = static_cast<uint64_t>(r);
+        d.chunk = static_cast<uint32_t>(c);
+        pages[ch.page_begin + slot + first + k] = d;
+        ++wrote;
+      } else {
+        flags[0] = 1;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wrote += __shfl_xor_sync(0xffffffffu, wrote, o);
+    if (lane == 0 && wrote) atomicAdd(&flags[1], wrote);
+    __syncthreads();
+    const bool stop = flags[0] != 0 || (carry + total) / 7 >= n;
+    carry += total;
+    __syncthreads();  // the staged bytes, starts and counts are rewritten next round
+    if (stop) break;
+  }
+  return flags[0] == 0 && static_cast<uint64_t>(flags[1]) == n;
+}
+
+__global__ void __launch_bounds__(32 * OI_BWARPS) k_index_oi_locations(const ChunkDev* __restrict__ chunks,
+                                                                       int n_chunks,
+                                                                       const int64_t* __restrict__ chunk_file_off,
+                                                                       PageDev* pages, DevStatus* st) {
+  __shared__ __align__(16) uint8_t raw[OI_BWARPS][OI_SEG + 96];
+  __shared__ uint16_t starts[OI_BWARPS][OI_SEG_STARTS];
+  __shared__ uint32_t wcnt[OI_BWARPS];
+  __shared__ int flags[2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // block b: either chunk b when its OffsetIndex is large (segments), or
+  // chunks of the warp path: the small chunks among [OI_WARPS b, OI_WARPS (b + 1))
+  const int big = blockIdx.x;
+  if (big < n_chunks && chunks[big].oi_len > OI_SMEM) {
+    const ChunkDev ch = chunks[big];
+    if (threadIdx.x == 0 && ch.dict_page >= 0) {
+      PageDev d{};
+      d.offset = 0;
+      d.chunk = static_cast<uint32_t>(big);
+      pages[ch.page_begin] = d;
+    }
+    if (!oi_locations_segments(raw, starts, wcnt, flags, ch.oi_base, ch.oi_len, big, ch, chunk_file_off[big], pages)) {
+      if (threadIdx.x == 0)
+        oi_locations(TRd{ch.oi_base, ch.oi_base + ch.oi_len, false}, big, ch, chunk_file_off[big], pages, st);
+    }
+  }
+  __syncthreads();  // the shared buffers are reused by the warp path
+  if (w >= OI_WARPS) return;
   const int c = blockIdx.x * OI_WARPS + w;
   if (c >= n_chunks) return;
   const ChunkDev ch = chunks[c];
+  if (ch.oi_len > OI_SMEM) return;  // (its own block takes it)
   if (lane == 0 && ch.dict_page >= 0) {
     PageDev d{};
     d.offset = 0;
     d.chunk = static_cast<uint32_t>(c);
     pages[ch.page_begin] = d;
   }
-  if (!oi_locations_tokens(raw[w], starts[w], ch.oi_base, ch.oi_len, c, ch, chunk_file_off[c], pages, lane)) {
+  uint8_t* wraw = raw[2 * w];  // OI_SMEM + 32 bytes: two segment buffers
+  uint16_t* wst = starts[2 * w];
+  if (!oi_locations_tokens(wraw, wst, ch.oi_base, ch.oi_len, c, ch, chunk_file_off[c], pages, lane)) {
     if (lane == 0) oi_locations(TRd{ch.oi_base, ch.oi_base + ch.oi_len, false}, c, ch, chunk_file_off[c], pages, st);
   }
 }
@@ -386,8 +567,8 @@ void launch_index_walk(const ChunkDev* chunks, int n_chunks, PageDev* pages, uin
 void launch_index_oi(const ChunkDev* chunks, int n_chunks, const int64_t* chunk_file_off, PageDev* pages,
                      int n_pages, DevStatus* st, cudaStream_t s) {
   if (n_chunks <= 0) return;
-  const int blocks = (n_chunks + OI_WARPS - 1) / OI_WARPS;
-  k_index_oi_locations<<<blocks, 32 * OI_WARPS, 0, s>>>(chunks, n_chunks, chunk_file_off, pages, st);
+  // enough blocks for every chunk's own block and for the warp path
+  k_index_oi_locations<<<n_chunks, 32 * OI_BWARPS, 0, s>>>(chunks, n_chunks, chunk_file_off, pages, st);
   if (n_pages > 0) k_index_oi_headers<<<(n_pages + 127) / 128, 128, 0, s>>>(chunks, pages, n_pages, st);
   k_index_oi_rows<<<n_chunks, OI_ROWS, 0, s>>>(chunks, n_chunks, pages, st);
 }
