@@ -210,10 +210,14 @@ __device__ __forceinline__ bool ch_wait1(Chain& c) {
   return ok;
 }
 
-// Starts the copy of the window that follows the current one.
+// Starts the copy of the window that follows the current one.  None when
+// the current window already reaches the stream's end: for a stream shorter
+// than the overlap, the next window's start (window end - COVL) would lie
+// before the stream, and, for the first page of a file, before the buffer.
 __device__ __forceinline__ void ch_prefetch(Chain& c) {
-  const int64_t nxt = c.w0 + c.n0 - COVL;
-  if (nxt < static_cast<int64_t>(c.slen))
+  const int64_t end = c.w0 + c.n0;  // stream offset just past the window
+  const int64_t nxt = end - COVL;
+  if (end <= static_cast<int64_t>(c.slen) && nxt > c.w0)
     ch_issue(c, c.b1, c.m1, nxt, &c.w1, &c.n1, &c.e1);
   else
     c.n1 = 0;
