@@ -75,6 +75,7 @@ struct DecodeArgs {
   int64_t* dbase;           // DELTA value preceding each block
   DeltaRegion* dregs;       // DELTA region summaries
   uint32_t* dreg_lists;     // DELTA region block lists (DELTA_REGION_LIST per region)
+  uint32_t* vpos;           // transcoded string pages: value-stream offset of each value (and of the end)
   int n_pp;
   int n_items;
   int n_walk;
@@ -82,9 +83,10 @@ struct DecodeArgs {
 };
 
 // One block per job; `counters` is the plan's item_counter array (its pool
-// word); `pool` holds `pool_cap` bytes for DELTA_BYTE_ARRAY bodies.
+// word); `pool` holds `pool_cap` bytes for DELTA_BYTE_ARRAY bodies; string
+// pages with a value-position table (PlanPage::vtab) get it filled in `vpos`.
 void launch_transcode(const TranscodeJob* jobs, int n, PlanPage* pps, uint8_t* pool, uint64_t pool_cap,
-                      uint32_t* counters, DevStatus* st, cudaStream_t s);
+                      uint32_t* counters, uint32_t* vpos, DevStatus* st, cudaStream_t s);
 void launch_dict(const DictJob* jobs, int n_jobs, int max_fixed_bytes, int max_str_regions, DictScratch ds,
                  DictDev* dicts, int n_sms, DevStatus* st, cudaStream_t s);
 // Launches over sub-ranges (one output column's share of the plan).

@@ -115,6 +115,7 @@ pqi::DecodeArgs decode_args(pq_plan* plan) {
   a.dbase = plan->d_dbase;
   a.dregs = plan->d_dregs;
   a.dreg_lists = plan->d_dreg_lists;
+  a.vpos = plan->d_vpos;
   a.n_pp = static_cast<int>(plan->pps.size());
   a.n_items = static_cast<int>(plan->n_items);
   a.n_walk = static_cast<int>(plan->walk_pps.size());
@@ -949,6 +950,12 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
             plan->tc_dst_off.push_back(static_cast<int64_t>(scratch));
             scratch += (cap + 32 + 15) & ~uint64_t(15);
           }
+          if (enc != pqi::ENC_BSS) {
+            // the transcoder records where each value starts, so that the
+            // walk need not follow the (length, bytes) chain
+            pp.vtab = static_cast<uint32_t>(1 + plan->vpos_rows);
+            plan->vpos_rows += static_cast<uint64_t>(pg.num_values) + 1;
+          }
           plan->tc_jobs.push_back(j);
         }
         pp.item_begin = static_cast<uint32_t>(plan->n_items);
@@ -1060,6 +1067,7 @@ pq_status plan_upload(pq_plan* plan) {
   plan->d_cols = plan_alloc(pqi::OutCol, plan, plan->outcols.size());
   plan->d_snappy = plan_alloc(pqi::SnappyJob, plan, plan->snappy_data.size() + plan->snappy_dict.size());
   plan->d_snap_blocks = plan_alloc(pqi::SnappyJob, plan, plan->snap_blocks);
+  plan->d_vpos = plan_alloc(uint32_t, plan, plan->vpos_rows);
   plan->d_dict_jobs = plan_alloc(pqi::DictJob, plan, plan->dict_jobs.size());
   plan->d_tc_jobs = plan_alloc(pqi::TranscodeJob, plan, plan->tc_jobs.size());
   plan->d_str_cols = plan_alloc(int32_t, plan, plan->str_cols.size());
@@ -1257,6 +1265,7 @@ uint64_t plan_device_bytes(const pq_plan* plan, uint64_t scratch) {
   const uint64_t str_rows = static_cast<uint64_t>(plan->n_rows) * plan->str_cols.size();
   return npp * sizeof(pqi::PlanPage) + nit * sizeof(pqi::Item) + plan->outcols.size() * sizeof(pqi::OutCol) +
          (plan->snappy_data.size() + plan->snappy_dict.size() + plan->snap_blocks) * sizeof(pqi::SnappyJob) +
+         4 * plan->vpos_rows +
          plan->dict_jobs.size() * sizeof(pqi::DictJob) + plan->tc_jobs.size() * sizeof(pqi::TranscodeJob) +
          4 * (plan->walk_pps.size() + plan->delta_pps.size()) +
          plan->delta_blocks * 12 +
@@ -1338,7 +1347,7 @@ static int max_str_regions_all(const pq_plan* plan) {
 static void enqueue_transcode(pq_plan* plan, int begin, int n, const pqi::DecodeArgs& a, cudaStream_t s) {
   if (n <= 0) return;
   pqi::launch_transcode(plan->d_tc_jobs + begin, n, plan->d_pps, plan->d_scratch + plan->tc_pool_off,
-                        plan->tc_pool_bytes, plan->d_counter, a.st, s);
+                        plan->tc_pool_bytes, plan->d_counter, plan->d_vpos, a.st, s);
 }
 
 // Compressed data pages of at least this many bytes (the tuning's

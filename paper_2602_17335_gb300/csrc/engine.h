@@ -119,6 +119,7 @@ struct pq_plan {
   uint64_t delta_blocks = 0;                 // capacity of the DELTA block tables
   uint64_t delta_regions = 0;                // capacity of the DELTA region tables
   uint64_t dict_regions = 0;                 // capacity of the string-dictionary region tables
+  uint64_t vpos_rows = 0;                    // value-position table rows of the transcoded string pages
   // per chunk: range of plan pages (plain baseline launches per chunk)
   std::vector<std::pair<int32_t, int32_t>> chunk_pp;  // (first pp, count)
   std::vector<int32_t> chunk_pp_chunk;
@@ -135,6 +136,7 @@ struct pq_plan {
   pqi::OutCol* d_cols = nullptr;
   pqi::SnappyJob* d_snappy = nullptr;        // data jobs then dict jobs
   pqi::SnappyJob* d_snap_blocks = nullptr;   // blocks of the split Snappy pages
+  uint32_t* d_vpos = nullptr;                // value positions of the transcoded string pages
   pqi::DictJob* d_dict_jobs = nullptr;
   pqi::TranscodeJob* d_tc_jobs = nullptr;
   int32_t* d_str_cols = nullptr;

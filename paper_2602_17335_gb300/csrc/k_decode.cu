@@ -1384,7 +1384,35 @@ done:
 // PLAIN BYTE_ARRAY: thread 0 follows the (length, bytes) chain and records
 // for every item the offset of its first value and the chars before it.
 __device__ bool walk_plain_ba(WalkSmem& sm, const uint8_t* sb, uint32_t slen, int32_t total, const PlanPage& pp,
-                              Item* items, int pgid, DevStatus* st) {
+                              Item* items, int pgid, DevStatus* st, const uint32_t* vp) {
+  if (vp) {
+    // a transcoded page: the transcoder recorded where every value starts
+    // (vp[k], and vp[total] = the end of the stream it wrote), so each
+    // item's checkpoint is a lookup; the chars before value k are vp[k] - 4 k
+    int bad = 0;
+    // the table covers exactly `total` values of at least 4 bytes each
+    if (threadIdx.x == 0 && (total < 0 || static_cast<uint64_t>(total) * 4 > slen || vp[total] != slen)) bad = 1;
+    for (uint32_t i = threadIdx.x; i < pp.item_count; i += blockDim.x) {
+      Item& it = items[pp.item_begin + i];
+      if (it.nn <= 0) continue;
+      const int32_t k = it.k0;
+      const uint32_t pos = (k >= 0 && k <= total) ? vp[k] : 0xffffffffu;
+      if (pos > slen || pos < 4u * static_cast<uint32_t>(k)) {
+        bad = 1;
+        continue;
+      }
+      it.pos = static_cast<int32_t>(pos);
+      it.run_k0 = k;
+      it.base = static_cast<int64_t>(pos) - 4 * static_cast<int64_t>(k);
+    }
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+      if (bad) report(st, DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 8);
+      sm.ctl[5] = bad;
+    }
+    __syncthreads();
+    return !bad;
+  }
   if (threadIdx.x == 0) {
     int err = 0;
     Chain c = make_chain(sm);
@@ -1461,7 +1489,8 @@ __device__ void walk_page(const DecodeArgs& a, int p, WalkSmem& sm, bool serial_
   bool ok = true;
   if (pc.enc == ENC_PLAIN) {
     if (pc.ptype == T_BYTE_ARRAY) {
-      ok = walk_plain_ba(sm, sb, slen, nonnull, pp, a.items, pgid, a.st);
+      ok = walk_plain_ba(sm, sb, slen, nonnull, pp, a.items, pgid, a.st,
+                         pp.vtab && a.vpos ? a.vpos + (pp.vtab - 1) : nullptr);
     } else if (static_cast<uint64_t>(nonnull) * pc.width > slen) {
       if (tid == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_WALK_VALUES, 9);
       ok = false;
@@ -2436,10 +2465,17 @@ __device__ void expand_item(const DecodeArgs& a, int it_id, WarpSmem& ws, int la
   const int width = col.width;
   const int64_t orow0 = pp.out_row + it.row0;
   const int32_t k0 = it.k0, nn = it.nn;
+  // an item that fails leaves empty string entries behind (the string copy
+  // then reads nothing for its rows; the error is recorded)
+  auto clear_strings = [&]() {
+    if (isba)
+      for (int32_t r = lane; r < it.nrows; r += 32) col.str_scratch[orow0 + r] = 0ull;
+  };
   if (k0 < 0 || nn < 0 || static_cast<int64_t>(k0) + nn > pp.nonnull ||
       (col.optional && !isba && enc != ENC_PLAIN && nn > ITEM_ROWS_OPT) ||
       (col.optional && isba && nn > ITEM_ROWS_OPT)) {
     if (lane == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_EXPAND, 9);
+    clear_strings();
     return;
   }
   uint64_t chars = 0;
@@ -2525,6 +2561,8 @@ __device__ void expand_item(const DecodeArgs& a, int it_id, WarpSmem& ws, int la
   }
   if (!ok) {
     if (lane == 0) report(a.st, DERR_CORRUPT, pgid, WHERE_EXPAND, 1);
+    __syncwarp();
+    clear_strings();
     return;
   }
   __syncwarp();
@@ -3101,6 +3139,10 @@ __global__ void __launch_bounds__(256, 4) k_str_copy(DecodeArgs a, int c) {
     const int64_t orow0 = pp.out_row + it.row0;
     int64_t* offs = reinterpret_cast<int64_t*>(col.values);
     const uint8_t* cbase = isdict ? dd.chars : sb;
+    // PLAIN pages: every string lies inside the page's value bytes (an entry
+    // that does not is dropped and reported; the expand writes none such)
+    const uint64_t clen = isdict ? ~0ull : static_cast<uint64_t>(pp.body_len > pp.values_off
+                                                                     ? pp.body_len - pp.values_off : 0);
     for (int g0 = 0; g0 < it.nrows; g0 += 256) {
       // metadata of 4 chunks of 64 strings, loads issued together; lane l
       // takes rows 2l and 2l+1 of each chunk (adjacent in the output)
@@ -3110,6 +3152,15 @@ __global__ void __launch_bounds__(256, 4) k_str_copy(DecodeArgs a, int c) {
         const int r = g0 + (u >> 1) * 64 + 2 * lane + (u & 1);
         ent[u] = r < it.nrows ? col.str_scratch[orow0 + r] : 0ull;
       }
+      bool outside = false;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if ((ent[u] >> 32) + static_cast<uint32_t>(ent[u]) > clen) {
+          ent[u] = 0;
+          outside = true;
+        }
+      }
+      if (__any_sync(0xffffffffu, outside) && lane == 0) report(a.st, DERR_CORRUPT, static_cast<int>(pp.page), WHERE_EXPAND, 60);
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
         const int r0 = g0 + cc * 64;

@@ -49,7 +49,7 @@ struct DCursor {
   int32_t last;       // last decoded value
   int32_t started;
   int32_t pad;
-  int64_t minv;
+  int64_t minv[TC_MAX_MB];  // min delta of each buffered miniblock's block
   uint32_t mboff[TC_MAX_MB];
   uint8_t width[TC_MAX_MB];
   int32_t buf[TC_MAX_BLOCK];
@@ -151,7 +151,9 @@ __device__ __forceinline__ void dstream_rewind(DCursor& c) {
 }
 
 // All threads: decodes the next buffer of values (the header's first value,
-// then one block at a time).  Returns false on an error.
+// then as many whole blocks as the buffer holds: thread 0 lists their
+// miniblocks, every thread decodes TC_PER_THREAD values).  Returns false on
+// an error.
 __device__ bool dstream_refill(const uint8_t* b, DCursor& c, TcSmem& sm) {
   if (threadIdx.x == 0) {
     c.cnt = 0;
@@ -163,32 +165,45 @@ __device__ bool dstream_refill(const uint8_t* b, DCursor& c, TcSmem& sm) {
       c.last = c.first;
     } else if (c.left) {
       auto get = [b](uint32_t i) { return ld_u8(b + i); };
-      uint64_t mn;
-      uint32_t q = c.pos;
-      const int n = uleb(get, q, c.end, &mn);
-      if (!n || c.end - (q + n) < c.mbc) {
-        tc_fail(sm, DERR_CORRUPT, 7);
-      } else {
+      uint32_t q = c.pos, cnt = 0, nm = 0, left = c.left;
+      // whole blocks while they fit (one block always does: bs <= TC_MAX_BLOCK)
+      while (left) {
+        const uint32_t bc = left < c.bs ? left : c.bs;
+        const uint32_t need = (bc + c.vpm - 1) / c.vpm;
+        if (cnt + bc > TC_MAX_BLOCK || nm + need > TC_MAX_MB) break;
+        uint64_t mn;
+        const int n = uleb(get, q, c.end, &mn);
+        if (!n || c.end - (q + n) < c.mbc) {
+          tc_fail(sm, DERR_CORRUPT, 7);
+          break;
+        }
         q += static_cast<uint32_t>(n);
-        c.minv = unzigzag(mn);
-        const uint32_t cnt = c.left < c.bs ? c.left : c.bs;
-        const uint32_t need = (cnt + c.vpm - 1) / c.vpm;
+        const int64_t minv = unzigzag(mn);
         const uint32_t wpos = q;
         q += c.mbc;
+        bool bad = false;
         for (uint32_t m = 0; m < need; ++m) {
           const uint32_t w = ld_u8(b + wpos + m);
           const uint32_t nbytes = c.vpm * w / 8;
           if (w > 32 || c.end - q < nbytes) {
-            tc_fail(sm, DERR_CORRUPT, 8);
+            bad = true;
             break;
           }
-          c.width[m] = static_cast<uint8_t>(w);
-          c.mboff[m] = q;
+          c.width[nm + m] = static_cast<uint8_t>(w);
+          c.mboff[nm + m] = q;
+          c.minv[nm + m] = minv;
           q += nbytes;
         }
-        c.pos = q;
-        c.cnt = cnt;
+        if (bad) {
+          tc_fail(sm, DERR_CORRUPT, 8);
+          break;
+        }
+        nm += need;
+        cnt += bc;
+        left -= bc;
       }
+      c.pos = q;
+      c.cnt = cnt;
     } else {
       tc_fail(sm, DERR_CORRUPT, 9);  // more values asked for than the stream holds
     }
@@ -206,7 +221,7 @@ __device__ bool dstream_refill(const uint8_t* b, DCursor& c, TcSmem& sm) {
       if (k < cnt) {
         const uint32_t m = k / c.vpm, i = k % c.vpm;
         const int w = c.width[m];
-        s += c.minv + static_cast<int64_t>(get_bits(b, c.mboff[m], i * static_cast<uint32_t>(w), w));
+        s += c.minv[m] + static_cast<int64_t>(get_bits(b, c.mboff[m], i * static_cast<uint32_t>(w), w));
       }
       d[u] = s;
     }
@@ -242,7 +257,7 @@ __device__ __forceinline__ void copy_bytes(uint8_t* d, const uint8_t* s, int64_t
 
 // DELTA_LENGTH_BYTE_ARRAY values at src[vp, src_len) -> PLAIN at dst + v0.
 // Returns the PLAIN bytes written after v0, or -1 on an error.
-__device__ int64_t tc_dlba(const TranscodeJob& j, TcSmem& sm, uint32_t v0, uint8_t* dst) {
+__device__ int64_t tc_dlba(const TranscodeJob& j, TcSmem& sm, uint32_t v0, uint8_t* dst, uint32_t* vp) {
   DCursor& c = sm.c[0];
   if (threadIdx.x == 0) dstream_open(j.src, v0, j.src_len, c, sm);
   __syncthreads();
@@ -281,12 +296,14 @@ __device__ int64_t tc_dlba(const TranscodeJob& j, TcSmem& sm, uint32_t v0, uint8
       uint8_t* out = dst + v0 + 4 * (K + t) + C + ex;
       put_le32(out, static_cast<uint32_t>(len));
       copy_bytes(out + 4, j.src + cstart + C + ex, len);
+      if (vp) vp[K + t] = static_cast<uint32_t>(4 * (K + t) + C + ex);
     }
     K += n;
     C += tot;
     used += n;
     __syncthreads();
   }
+  if (vp && threadIdx.x == 0) vp[M] = static_cast<uint32_t>(4 * static_cast<int64_t>(M) + C);
   return 4 * static_cast<int64_t>(M) + C;
 }
 
@@ -294,7 +311,7 @@ __device__ int64_t tc_dlba(const TranscodeJob& j, TcSmem& sm, uint32_t v0, uint8
 // DELTA_BYTE_ARRAY page.  emit false: checks and totals only (*T = value
 // bytes, *S = suffix bytes); emit true: writes the PLAIN values at dst + v0.
 __device__ bool dba_pass(const TranscodeJob& j, TcSmem& sm, uint32_t v0, uint32_t cstart, bool emit, uint8_t* dst,
-                         int64_t* T_out, int64_t* S_out) {
+                         uint32_t* vp, int64_t* T_out, int64_t* S_out) {
   DCursor& cp = sm.c[0];
   DCursor& cs = sm.c[1];
   if (threadIdx.x == 0) {
@@ -347,6 +364,7 @@ __device__ bool dba_pass(const TranscodeJob& j, TcSmem& sm, uint32_t v0, uint32_
         copy_bytes(dst + dch + p, j.src + soff, s);
         sm.db[t] = dch;
         sm.sb[t] = soff;
+        if (vp) vp[K + t] = static_cast<uint32_t>(dch - 4 - v0);
       }
       __syncthreads();
       if (on) {
@@ -372,6 +390,7 @@ __device__ bool dba_pass(const TranscodeJob& j, TcSmem& sm, uint32_t v0, uint32_
     us += n;
     __syncthreads();
   }
+  if (emit && vp && threadIdx.x == 0) vp[M] = static_cast<uint32_t>(4 * static_cast<int64_t>(M) + T);
   *T_out = T;
   *S_out = S;
   return true;
@@ -381,7 +400,7 @@ __device__ bool dba_pass(const TranscodeJob& j, TcSmem& sm, uint32_t v0, uint32_
 // pool sized by a first pass.  Returns the PLAIN bytes after v0 (sm.dst_off
 // holds the piece), or -1 on an error.
 __device__ int64_t tc_dba(const TranscodeJob& j, TcSmem& sm, uint32_t v0, uint8_t* pool, uint64_t pool_cap,
-                          unsigned long long* pool_used) {
+                          unsigned long long* pool_used, uint32_t* vp) {
   if (threadIdx.x == 0) {
     dstream_open(j.src, v0, j.src_len, sm.c[0], sm);
     if (!sm.err) dstream_open(j.src, sm.c[0].pos, j.src_len, sm.c[1], sm);
@@ -397,7 +416,7 @@ __device__ int64_t tc_dba(const TranscodeJob& j, TcSmem& sm, uint32_t v0, uint8_
   }
   __syncthreads();
   int64_t T, S;
-  if (!dba_pass(j, sm, v0, cstart, false, nullptr, &T, &S)) return -1;
+  if (!dba_pass(j, sm, v0, cstart, false, nullptr, nullptr, &T, &S)) return -1;
   const int64_t vlen = 4 * static_cast<int64_t>(M) + T;
   if (threadIdx.x == 0) {
     const uint64_t need = (static_cast<uint64_t>(v0) + static_cast<uint64_t>(vlen) + 32 + 15) & ~uint64_t(15);
@@ -414,7 +433,7 @@ __device__ int64_t tc_dba(const TranscodeJob& j, TcSmem& sm, uint32_t v0, uint8_
   __syncthreads();
   if (sm.err) return -1;
   uint8_t* dst = pool + sm.dst_off;
-  if (!dba_pass(j, sm, v0, cstart, true, dst, &T, &S)) return -1;
+  if (!dba_pass(j, sm, v0, cstart, true, dst, vp, &T, &S)) return -1;
   return vlen;
 }
 
@@ -440,9 +459,13 @@ __device__ int64_t tc_bss(const TranscodeJob& j, TcSmem& sm, uint32_t v0, uint8_
 
 __global__ void __launch_bounds__(TC_THREADS) k_transcode(const TranscodeJob* jobs, PlanPage* pps, uint8_t* pool,
                                                          uint64_t pool_cap, unsigned long long* pool_used,
-                                                         DevStatus* st) {
+                                                         uint32_t* vpos, DevStatus* st) {
   __shared__ TcSmem sm;
   const TranscodeJob j = jobs[blockIdx.x];
+  // string pages: the value-position table the walk reads instead of
+  // following the (length, bytes) chain
+  const uint32_t vtab = pps[j.pp].vtab;
+  uint32_t* vp = vtab && vpos ? vpos + (vtab - 1) : nullptr;
   {
     // the page's bytes into L2 first (a hint): the stream headers are then
     // followed by one thread at L2 rather than DRAM latency
@@ -477,9 +500,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_transcode(const TranscodeJob* jo
     if (j.enc == ENC_BSS) {
       vlen = tc_bss(j, sm, v0, dst);
     } else if (j.enc == ENC_DELTA_LBA) {
-      vlen = tc_dlba(j, sm, v0, dst);
+      vlen = tc_dlba(j, sm, v0, dst, vp);
     } else if (j.enc == ENC_DELTA_BA) {
-      vlen = tc_dba(j, sm, v0, pool, pool_cap, pool_used);
+      vlen = tc_dba(j, sm, v0, pool, pool_cap, pool_used, vp);
       dst = pool + sm.dst_off;
     } else if (threadIdx.x == 0) {
       tc_fail(sm, DERR_UNSUPPORTED, 12);
@@ -495,8 +518,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_transcode(const TranscodeJob* jo
       pp->body_len = static_cast<int32_t>(v0 + vlen);
     } else {
       // the page keeps its level bytes only: later stages find no values
+      // (and the walk does not read the value-position table, which this
+      // page never filled)
       pp->body = j.src;
       pp->body_len = static_cast<int32_t>(v0);
+      pp->vtab = 0;
       report(st, static_cast<uint32_t>(sm.flag), j.page, WHERE_TRANSCODE, sm.detail);
     }
   }
@@ -505,10 +531,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_transcode(const TranscodeJob* jo
 }  // namespace
 
 void launch_transcode(const TranscodeJob* jobs, int n, PlanPage* pps, uint8_t* pool, uint64_t pool_cap,
-                      uint32_t* counters, DevStatus* st, cudaStream_t s) {
+                      uint32_t* counters, uint32_t* vpos, DevStatus* st, cudaStream_t s) {
   if (n <= 0) return;
   k_transcode<<<n, TC_THREADS, 0, s>>>(jobs, pps, pool, pool_cap,
-                                       reinterpret_cast<unsigned long long*>(counters + TC_POOL_COUNTER), st);
+                                       reinterpret_cast<unsigned long long*>(counters + TC_POOL_COUNTER), vpos, st);
 }
 
 }  // namespace pqi

@@ -124,6 +124,8 @@ struct PlanPage {
   int32_t item_rows;       // rows per work item of this page
   int32_t enc;             // encoding the kernels decode: the page's own, or PLAIN once a
                            // BYTE_STREAM_SPLIT / DELTA_(LENGTH_)BYTE_ARRAY page is transcoded
+  uint32_t vtab;           // transcoded string pages: 1 + first row of the page's value-position
+                           // table (DecodeArgs::vpos, written by the transcoder); 0 none
 };
 
 // DELTA block-chain region (speculative parallel walk): regions of
