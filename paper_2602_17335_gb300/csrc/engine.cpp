@@ -90,6 +90,41 @@ Pinned::~Pinned() {
   if (p) cudaFreeHost(p);
 }
 
+bool PinnedPool::take(size_t n, Pinned* out) {
+  n = std::max<size_t>((n + 4095) & ~size_t(4095), 4096);
+  {
+    std::lock_guard<std::mutex> g(mu_);
+    auto it = free_.lower_bound(n);
+    if (it != free_.end() && it->first <= 4 * n) {
+      out->p = it->second;
+      out->cap = it->first;
+      free_.erase(it);
+      return true;
+    }
+  }
+  return out->reserve(n);
+}
+
+void PinnedPool::give(Pinned* in) {
+  if (!in->p) return;
+  {
+    std::lock_guard<std::mutex> g(mu_);
+    if (free_.size() < 64 && in->cap <= (size_t(64) << 20)) {
+      free_.emplace(in->cap, in->p);
+      in->p = nullptr;
+      in->cap = 0;
+      return;
+    }
+  }
+  cudaFreeHost(in->p);
+  in->p = nullptr;
+  in->cap = 0;
+}
+
+PinnedPool::~PinnedPool() {
+  for (auto& kv : free_) cudaFreeHost(kv.second);
+}
+
 pq_status fail(pq_ctx* ctx, pq_status s, const std::string& msg) {
   if (ctx) ctx->last_error = msg;
   return s;
@@ -431,11 +466,40 @@ pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi,
     free_index_device(idx.get());
     return fail(ctx, PQ_ERR_OOM, "index allocation");
   }
+  // uploads go through a pinned block from the context's cache (returned
+  // once the stream has drained: every path below ends in a stream sync)
+  struct Stage {
+    pq_ctx* ctx;
+    cudaStream_t s;
+    Pinned b;
+    size_t off = 0;
+    ~Stage() {
+      if (b.p) {
+        cudaStreamSynchronize(s);
+        ctx->pinned.give(&b);
+      }
+    }
+    const void* put(const void* src, size_t n) {
+      uint8_t* d = b.p + off;
+      memcpy(d, src, n);
+      off += (n + 15) & ~size_t(15);
+      return d;
+    }
+  } up{ctx, s, {}};
+  const size_t chunk_bytes = sizeof(pqi::ChunkDev) * static_cast<size_t>(std::max(nch, 0));
+  if (!ctx->pinned.take(64 + 8 * static_cast<size_t>(nch) + 3 * (chunk_bytes + 16), &up.b)) {
+    free_index_device(idx.get());
+    return fail(ctx, PQ_ERR_OOM, "pinned staging");
+  }
+  auto upload_chunks = [&]() -> cudaError_t {
+    return cudaMemcpyAsync(idx->d_chunks, up.put(idx->chunks.data(), chunk_bytes), chunk_bytes,
+                           cudaMemcpyHostToDevice, s);
+  };
   pqi::DevStatus st0{0, -1, 0, 0};
-  CK(cudaMemcpyAsync(idx->d_status, &st0, sizeof st0, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(idx->d_status, up.put(&st0, sizeof st0), sizeof st0, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(idx->d_dicts, 0, sizeof(pqi::DictDev) * std::max(nch, 1), s));
-  CK(cudaMemcpyAsync(idx->d_chunk_file_off, idx->chunk_file_off.data(), sizeof(int64_t) * nch,
-                     cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(idx->d_chunk_file_off, up.put(idx->chunk_file_off.data(), sizeof(int64_t) * nch),
+                     sizeof(int64_t) * nch, cudaMemcpyHostToDevice, s));
   int64_t n_pages = 0;
   if (all_oi && nch > 0) {
     // 4a. OffsetIndex: page counts from the list headers (the first 16 bytes
@@ -502,13 +566,13 @@ pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi,
       free_index_device(idx.get());
       return fail(ctx, PQ_ERR_OOM, "page table");
     }
-    CK(cudaMemcpyAsync(idx->d_chunks, idx->chunks.data(), sizeof(pqi::ChunkDev) * nch, cudaMemcpyHostToDevice, s));
+    CK(upload_chunks());
     pqi::launch_index_oi(idx->d_chunks, nch, idx->d_chunk_file_off, idx->d_pages, static_cast<int>(n_pages),
                          idx->d_status, s);
     idx->used_oi = true;
   } else if (nch > 0) {
     // 4b. serial header walk: count, size, fill
-    CK(cudaMemcpyAsync(idx->d_chunks, idx->chunks.data(), sizeof(pqi::ChunkDev) * nch, cudaMemcpyHostToDevice, s));
+    CK(upload_chunks());
     uint32_t* d_counts = static_cast<uint32_t*>(pool.alloc(sizeof(uint32_t) * nch));
     if (!d_counts) {
       free_index_device(idx.get());
@@ -542,7 +606,7 @@ pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi,
       free_index_device(idx.get());
       return fail(ctx, PQ_ERR_OOM, "page table");
     }
-    CK(cudaMemcpyAsync(idx->d_chunks, idx->chunks.data(), sizeof(pqi::ChunkDev) * nch, cudaMemcpyHostToDevice, s));
+    CK(upload_chunks());
     pqi::launch_index_walk(idx->d_chunks, nch, idx->d_pages, nullptr, 1, idx->d_status, s);
   }
   // 5. page table back to the host
@@ -615,8 +679,7 @@ pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi,
       }
     }
   }
-  CK(cudaMemcpyAsync(idx->d_chunks, idx->chunks.data(), sizeof(pqi::ChunkDev) * std::max(nch, 0),
-                     cudaMemcpyHostToDevice, s));
+  CK(upload_chunks());
   CK(cudaStreamSynchronize(s));
   *out = idx.release();
   return PQ_OK;
@@ -702,6 +765,7 @@ void pq_free_plan(pq_plan* plan) {
   for (auto& e : plan->join)
     if (e) cudaEventDestroy(e);
   free_plan_device(plan);
+  for (pqe::Pinned* b : {&plan->h_cols, &plan->h_out, &plan->h_up}) plan->ctx->pinned.give(b);
   delete plan;
 }
 
@@ -1047,8 +1111,9 @@ pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& col
 static pq_status plan_size_strings(pq_plan* plan);
 
 // Device half: allocations from the context's pool, uploads, work items,
-// events, pinned staging.
-pq_status plan_upload(pq_plan* plan) {
+// events, pinned staging.  The uploads go on stream `s` (nullptr: the legacy
+// default stream), where the plan's `ready` event is recorded.
+pq_status plan_upload(pq_plan* plan, cudaStream_t s) {
   pq_ctx* ctx = plan->ctx;
   const bool plain = (plan->flags & PQ_SCAN_PLAIN) != 0;
   const uint64_t scratch = plan->host_scratch;
@@ -1113,30 +1178,37 @@ pq_status plan_upload(pq_plan* plan) {
     col.str_scratch = plan->d_str_scratch + static_cast<uint64_t>(plan->n_rows) * i;
     col.str_item_bytes = plan->d_str_items;
   }
-  // upload
-  cudaStream_t s = nullptr;
+  // upload, through one pinned staging block
   std::vector<pqi::SnappyJob> alljobs(plan->snappy_data);
   alljobs.insert(alljobs.end(), plan->snappy_dict.begin(), plan->snappy_dict.end());
-  if (npp) CK(cudaMemcpyAsync(plan->d_pps, plan->pps.data(), sizeof(pqi::PlanPage) * npp, cudaMemcpyHostToDevice, s));
+  struct Up {
+    void* dst;
+    const void* src;
+    size_t bytes;
+  };
+  const Up ups[] = {
+      {plan->d_pps, plan->pps.data(), sizeof(pqi::PlanPage) * npp},
+      {plan->d_snappy, alljobs.data(), sizeof(pqi::SnappyJob) * alljobs.size()},
+      {plan->d_dict_jobs, plan->dict_jobs.data(), sizeof(pqi::DictJob) * plan->dict_jobs.size()},
+      {plan->d_tc_jobs, plan->tc_jobs.data(), sizeof(pqi::TranscodeJob) * plan->tc_jobs.size()},
+      {plan->d_str_cols, plan->str_cols.data(), sizeof(int32_t) * plan->str_cols.size()},
+      {plan->d_walk_pps, plan->walk_pps.data(), sizeof(uint32_t) * plan->walk_pps.size()},
+      {plan->d_delta_pps, plan->delta_pps.data(), sizeof(uint32_t) * plan->delta_pps.size()},
+  };
+  size_t up_bytes = 0;
+  for (const Up& u : ups) up_bytes += (u.bytes + 15) & ~size_t(15);
+  if (!ctx->pinned.take(up_bytes, &plan->h_up)) {
+    free_plan_device(plan);
+    return fail(ctx, PQ_ERR_OOM, "pinned staging");
+  }
+  size_t up_off = 0;
+  for (const Up& u : ups) {
+    if (!u.bytes) continue;
+    memcpy(plan->h_up.p + up_off, u.src, u.bytes);
+    CK(cudaMemcpyAsync(u.dst, plan->h_up.p + up_off, u.bytes, cudaMemcpyHostToDevice, s));
+    up_off += (u.bytes + 15) & ~size_t(15);
+  }
   if (nit) pqi::launch_make_items(decode_args(plan), static_cast<int>(npp), s);
-  if (!alljobs.empty())
-    CK(cudaMemcpyAsync(plan->d_snappy, alljobs.data(), sizeof(pqi::SnappyJob) * alljobs.size(),
-                       cudaMemcpyHostToDevice, s));
-  if (!plan->dict_jobs.empty())
-    CK(cudaMemcpyAsync(plan->d_dict_jobs, plan->dict_jobs.data(), sizeof(pqi::DictJob) * plan->dict_jobs.size(),
-                       cudaMemcpyHostToDevice, s));
-  if (!plan->tc_jobs.empty())
-    CK(cudaMemcpyAsync(plan->d_tc_jobs, plan->tc_jobs.data(), sizeof(pqi::TranscodeJob) * plan->tc_jobs.size(),
-                       cudaMemcpyHostToDevice, s));
-  if (!plan->str_cols.empty())
-    CK(cudaMemcpyAsync(plan->d_str_cols, plan->str_cols.data(), sizeof(int32_t) * plan->str_cols.size(),
-                       cudaMemcpyHostToDevice, s));
-  if (!plan->walk_pps.empty())
-    CK(cudaMemcpyAsync(plan->d_walk_pps, plan->walk_pps.data(), sizeof(uint32_t) * plan->walk_pps.size(),
-                       cudaMemcpyHostToDevice, s));
-  if (!plan->delta_pps.empty())
-    CK(cudaMemcpyAsync(plan->d_delta_pps, plan->delta_pps.data(), sizeof(uint32_t) * plan->delta_pps.size(),
-                       cudaMemcpyHostToDevice, s));
   // no host wait: a scan's stream waits on this event (the host arrays are
   // plan members, alive until the plan is freed)
   CK(cudaEventCreateWithFlags(&plan->ready, cudaEventDisableTiming));
@@ -1189,8 +1261,8 @@ pq_status plan_upload(pq_plan* plan) {
   plan->walk_grid =
       static_cast<int>(std::min<size_t>(std::max<size_t>(plan->walk_pps.size(), 1), size_t(ctx->n_sms) * wbps));
   plan->expand_grid = static_cast<int>(std::min<size_t>(std::max<size_t>((nit + 7) / 8, 1), size_t(ctx->n_sms) * ebps));
-  if (!plan->h_cols.reserve(sizeof(pqi::OutCol) * std::max<size_t>(plan->outcols.size(), 1)) ||
-      !plan->h_out.reserve(sizeof(pqi::DevStatus) + 8 * std::max<size_t>(plan->outcols.size(), 1))) {
+  if (!ctx->pinned.take(sizeof(pqi::OutCol) * std::max<size_t>(plan->outcols.size(), 1), &plan->h_cols) ||
+      !ctx->pinned.take(sizeof(pqi::DevStatus) + 8 * std::max<size_t>(plan->outcols.size(), 1), &plan->h_out)) {
     free_plan_device(plan);
     return fail(ctx, PQ_ERR_OOM, "pinned staging");
   }
@@ -1279,6 +1351,15 @@ uint64_t plan_device_bytes(const pq_plan* plan, uint64_t scratch) {
 extern "C" {
 
 pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_plan** out, pq_out_size* sizes) {
+  return pqe::plan_scan_on(ctx, idx, req, nullptr, out, sizes);
+}
+
+}  // extern "C"
+
+namespace pqe {
+
+pq_status plan_scan_on(pq_ctx* ctx, pq_index* idx, const pq_request* req, cudaStream_t stream, pq_plan** out,
+                       pq_out_size* sizes) {
   if (!ctx || !idx || !req || !out) return fail(ctx, PQ_ERR_INVALID_ARG, "pq_plan_scan: bad arguments");
   *out = nullptr;
   CK(cudaSetDevice(ctx->device));
@@ -1301,13 +1382,17 @@ pq_status pq_plan_scan(pq_ctx* ctx, pq_index* idx, const pq_request* req, pq_pla
   std::unique_ptr<pq_plan> plan;
   pq_status st = plan_build(ctx, idx, cols, {RowSeg{rb, re, 0}}, re - rb, req->flags, &plan);
   if (st != PQ_OK) return st;
-  st = plan_upload(plan.get());
+  st = plan_upload(plan.get(), stream);
   if (st != PQ_OK) return st;
   if (sizes)
     for (size_t i = 0; i < plan->sizes.size(); ++i) sizes[i] = plan->sizes[i];
   *out = plan.release();
   return PQ_OK;
 }
+
+}  // namespace pqe
+
+extern "C" {
 
 pq_status pq_plan_get_info(const pq_plan* plan, pq_plan_info* out) {
   if (!plan || !out) return PQ_ERR_INVALID_ARG;

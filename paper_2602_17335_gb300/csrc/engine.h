@@ -42,6 +42,21 @@ struct Pinned {
   ~Pinned();
 };
 
+// Cache of pinned host blocks for the plans' and indexes' staging (uploads,
+// output descriptors, status words), so that a repeated index/plan cycle
+// makes no cudaMallocHost/cudaFreeHost calls after warm-up and no upload
+// is a pageable copy (which the driver may queue behind bulk copies).
+class PinnedPool {
+ public:
+  bool take(size_t n, Pinned* out);  // a block of at least n bytes into the empty *out
+  void give(Pinned* in);             // back to the cache (the caller's copies from it are done)
+  ~PinnedPool();
+
+ private:
+  std::mutex mu_;
+  std::multimap<size_t, uint8_t*> free_;
+};
+
 }  // namespace pqe
 
 struct pq_ctx {
@@ -52,6 +67,7 @@ struct pq_ctx {
   std::string last_error;
   pq_tuning tuning{pqi::ITEM_ROWS, pqi::ITEM_ROWS_OPT, 0, kBranches, 0, 256, 1, 0};
   pqe::DevPool pool;
+  pqe::PinnedPool pinned;
   pqe::Pinned tail;     // footer staging
   std::mutex mu;        // serialises use from the serving thread and the API
 };
@@ -154,9 +170,11 @@ struct pq_plan {
   uint64_t* d_slists = nullptr;
   pqi::DevStatus* d_status = nullptr;
   std::vector<void*> owned;                  // pool blocks to release
-  // host staging (pinned): output descriptors in, status + string totals out
+  // host staging (pinned, from the context's cache): output descriptors in,
+  // status + string totals out, the plan's uploads
   pqe::Pinned h_cols;
   pqe::Pinned h_out;
+  pqe::Pinned h_up;
   cudaEvent_t done = nullptr;
   cudaEvent_t ready = nullptr;  // the plan's uploads and item table are in place
   cudaGraphExec_t graph = nullptr;
@@ -200,7 +218,13 @@ struct RowSeg {
 pq_status fail(pq_ctx* ctx, pq_status s, const std::string& msg);
 pq_status plan_build(pq_ctx* ctx, pq_index* idx, const std::vector<int32_t>& cols, const std::vector<RowSeg>& segs,
                      int64_t n_rows, uint32_t flags, std::unique_ptr<pq_plan>* out);
-pq_status plan_upload(pq_plan* plan);
+pq_status plan_upload(pq_plan* plan, cudaStream_t s = nullptr);
+// pq_plan_scan with the plan's uploads on `stream` (nullptr: the legacy
+// default stream).  The row-group pipeline plans on a slot's own stream, so
+// that these small copies do not queue behind the bulk copies of other row
+// groups.
+pq_status plan_scan_on(pq_ctx* ctx, pq_index* idx, const pq_request* req, cudaStream_t stream, pq_plan** out,
+                       pq_out_size* sizes);
 uint64_t plan_device_bytes(const pq_plan* plan, uint64_t scratch);
 // Enqueues one scan of `plan` into `outs` on `s`, columns forked onto
 // `branches` (n_branches >= 1); no host synchronisation.

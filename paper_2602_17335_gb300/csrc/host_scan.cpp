@@ -3,11 +3,17 @@
 //
 // When the requested rows span several row groups whose first rows fall on
 // 32-row boundaries of the output (so that validity words do not straddle
-// them), the row groups go through a pipeline of three device slots, the
-// overlapped reading of the paper's Section 4: while row group u is
-// indexed and decoded, row group u+1 is copied in and the columns of row
-// group u-1 are copied out, each on its own stream.  Footers are parsed
-// straight from host memory.
+// them), the row groups go through a pipeline of four device slots, the
+// overlapped reading of the paper's Section 4: row group u+1 is copied in
+// while row group u is indexed and decoded and the columns of earlier row
+// groups are copied out.  Each slot scans on streams of its own, so the
+// scans of consecutive row groups also overlap one another; the host waits
+// for a row group only when its slot comes round again, three row groups
+// later, so that the copy-out (the host link's slower direction) always has
+// row groups queued while slow scans (Snappy pages) are still running.  Each slot also
+// receives the row group's OffsetIndex structures (which the file keeps
+// after its last row group), so that the index reads page locations from
+// them.  Footers are parsed straight from host memory.
 #include <stdlib.h>
 #include <string.h>
 
@@ -24,36 +30,51 @@ namespace {
 struct Unit {
   int file, rg;
   int64_t byte0, byte1;  // staged file bytes
+  int64_t oi0, oi1;      // the row group's OffsetIndex bytes (oi0 < 0: not staged)
   int64_t row0, rows;    // global first row and rows of the row group
   int64_t lo, hi;        // requested rows inside it (row-group relative)
   int64_t out0;          // first output row
+  // slot offset of the OffsetIndex copy, after the chunk bytes
+  int64_t oi_at() const { return (byte1 - byte0 + 15) & ~int64_t(15); }
 };
 
+// A device slot and the row group in flight in it.
 struct Slot {
   void* in = nullptr;
   std::vector<pq_column> outs;
   cudaEvent_t h2d = nullptr, scanned = nullptr, d2h = nullptr;
-  bool used = false;
+  cudaStream_t sc = nullptr;                        // the slot's scan stream
+  cudaStream_t br[pq_ctx::kBranches] = {};          // and its column branches
+  int64_t unit = -1;                                // row group in flight, -1 none
+  pq_index* idx = nullptr;
+  pq_plan* plan = nullptr;
+  std::vector<pq_out_size> sz;                      // its planned output sizes
 };
 
 struct PipeGuard {
   pq_ctx* ctx;
-  cudaStream_t sc = nullptr, sh = nullptr, sd = nullptr;
+  cudaStream_t sh = nullptr, sd = nullptr;
   std::vector<void*> blocks;
-  static constexpr int kSlots = 3;
+  static constexpr int kSlots = 4;
   Slot slot[kSlots];
-  pq_index* idx = nullptr;
-  pq_plan* plan = nullptr;
   ~PipeGuard() {
-    if (plan) pq_free_plan(plan);
-    for (cudaStream_t s : {sc, sh, sd})
-      if (s) cudaStreamSynchronize(s);
-    if (idx) index_release(idx);
-    for (void* b : blocks) ctx->pool.free(b);
     for (auto& sl : slot)
+      if (sl.plan) pq_free_plan(sl.plan);  // waits for its scan
+    for (cudaStream_t s : {sh, sd})
+      if (s) cudaStreamSynchronize(s);
+    for (auto& sl : slot) {
+      if (sl.sc) cudaStreamSynchronize(sl.sc);
+      if (sl.idx) index_release(sl.idx);
+    }
+    for (void* b : blocks) ctx->pool.free(b);
+    for (auto& sl : slot) {
       for (cudaEvent_t e : {sl.h2d, sl.scanned, sl.d2h})
         if (e) cudaEventDestroy(e);
-    for (cudaStream_t s : {sc, sh, sd})
+      if (sl.sc) cudaStreamDestroy(sl.sc);
+      for (cudaStream_t b : sl.br)
+        if (b) cudaStreamDestroy(b);
+    }
+    for (cudaStream_t s : {sh, sd})
       if (s) cudaStreamDestroy(s);
   }
   void* alloc(size_t n) {
@@ -133,6 +154,19 @@ pq_status scan_pipelined(pq_ctx* ctx, const pq_file* host_files, int n_files, co
       b1 = std::min<int64_t>(b1 + 64, static_cast<int64_t>(host_files[f].size));
       u.byte0 = b0;
       u.byte1 = b1;
+      // the OffsetIndex bytes of all the row group's chunks (one range)
+      int64_t o0 = INT64_MAX, o1 = 0;
+      for (const auto& cm : rg.chunks) {
+        if (cm.oi_offset < 4 || cm.oi_length <= 0) {
+          o0 = -1;
+          break;
+        }
+        o0 = std::min(o0, cm.oi_offset);
+        o1 = std::max(o1, cm.oi_offset + static_cast<int64_t>(cm.oi_length));
+      }
+      const bool oi = o0 >= 0 && o1 <= static_cast<int64_t>(host_files[f].size) && o1 - o0 <= (int64_t(64) << 20);
+      u.oi0 = oi ? o0 : -1;
+      u.oi1 = oi ? o1 : -1;
       if (u.out0 % 32) return PQ_ERR_UNSUPPORTED;  // validity words must not straddle units
       units.push_back(u);
     }
@@ -143,7 +177,7 @@ pq_status scan_pipelined(pq_ctx* ctx, const pq_file* host_files, int n_files, co
   std::vector<int64_t> max_chars(cols.size(), 0);
   std::vector<int64_t> chars_base(cols.size(), 0);
   for (const auto& u : units) {
-    max_bytes = std::max(max_bytes, u.byte1 - u.byte0);
+    max_bytes = std::max(max_bytes, u.oi_at() + (u.oi0 >= 0 ? u.oi1 - u.oi0 : 0));
     max_rows = std::max(max_rows, u.hi - u.lo);
     const auto& rg = metas[u.file].rgs[u.rg];
     for (size_t c = 0; c < cols.size(); ++c)
@@ -153,9 +187,17 @@ pq_status scan_pipelined(pq_ctx* ctx, const pq_file* host_files, int n_files, co
       }
   }
   PipeGuard g{ctx};
-  for (cudaStream_t* s : {&g.sc, &g.sh, &g.sd})
+  const size_t ns = std::min<size_t>(PipeGuard::kSlots, units.size());  // slots in use
+  const int nb = std::min<int>(std::max<int>(ctx->tuning.branches, 1), pq_ctx::kBranches);
+  for (cudaStream_t* s : {&g.sh, &g.sd})
     if (cudaStreamCreateWithFlags(s, cudaStreamNonBlocking) != cudaSuccess) return fail(ctx, PQ_ERR_CUDA, "stream");
-  for (auto& sl : g.slot) {
+  for (size_t q = 0; q < ns; ++q) {
+    Slot& sl = g.slot[q];
+    if (cudaStreamCreateWithFlags(&sl.sc, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(ctx, PQ_ERR_CUDA, "stream");
+    for (int b = 0; b < nb; ++b)
+      if (cudaStreamCreateWithFlags(&sl.br[b], cudaStreamNonBlocking) != cudaSuccess)
+        return fail(ctx, PQ_ERR_CUDA, "stream");
     for (cudaEvent_t* e : {&sl.h2d, &sl.scanned, &sl.d2h})
       if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) return fail(ctx, PQ_ERR_CUDA, "event");
     sl.in = g.alloc(static_cast<size_t>(max_bytes) + 64);
@@ -175,41 +217,68 @@ pq_status scan_pipelined(pq_ctx* ctx, const pq_file* host_files, int n_files, co
         return fail(ctx, PQ_ERR_OOM, "slot outputs");
     }
   }
+  bool any_ba = false;
+  for (size_t c = 0; c < cols.size(); ++c) any_ba |= metas[0].columns[cols[c]].type == PQ_TYPE_BYTE_ARRAY;
   auto copy_out = [&](void* host, const void* src, size_t bytes) -> cudaError_t {
     return bytes ? cudaMemcpyAsync(host, src, bytes, cudaMemcpyDeviceToHost, g.sd) : cudaSuccess;
   };
-  // copy-in of unit k into its slot, once the slot's previous copy-out is done
+  // the row group in flight in a slot: waits for its scan (status, chars
+  // against the planned sizes, which the copy-out used) and its copy-out
+  auto retire = [&](Slot& sl) -> pq_status {
+    if (sl.unit < 0) return PQ_OK;
+    std::vector<uint64_t> chars(cols.size());
+    pq_status st = pq_scan_wait(ctx, sl.plan, sl.sc, chars.data());
+    if (st != PQ_OK) return st;
+    for (size_t c = 0; c < cols.size(); ++c)
+      if (sl.sz[c].type == PQ_TYPE_BYTE_ARRAY && chars[c] != sl.sz[c].chars_bytes)
+        return fail(ctx, PQ_ERR_CORRUPT, "row-group chars differ from the chunk's size statistics");
+    if (cudaEventSynchronize(sl.d2h) != cudaSuccess) return fail(ctx, PQ_ERR_CUDA, "slot reuse");
+    pq_free_plan(sl.plan);
+    sl.plan = nullptr;
+    index_release(sl.idx);
+    sl.idx = nullptr;
+    sl.unit = -1;
+    return PQ_OK;
+  };
+  // copy-in of unit k into its slot, once the slot's previous row group is done
   auto copy_in = [&](size_t k) -> pq_status {
     const Unit& u = units[k];
-    Slot& sl = g.slot[k % PipeGuard::kSlots];
-    if (sl.used && cudaEventSynchronize(sl.d2h) != cudaSuccess) return fail(ctx, PQ_ERR_CUDA, "slot reuse");
-    sl.used = true;
+    Slot& sl = g.slot[k % ns];
+    const pq_status st = retire(sl);
+    if (st != PQ_OK) return st;
     const uint8_t* hb = static_cast<const uint8_t*>(host_files[u.file].data);
-    if (cudaMemcpyAsync(sl.in, hb + u.byte0, static_cast<size_t>(u.byte1 - u.byte0), cudaMemcpyHostToDevice, g.sh) !=
-            cudaSuccess ||
-        cudaEventRecord(sl.h2d, g.sh) != cudaSuccess)
+    cudaError_t e = cudaMemcpyAsync(sl.in, hb + u.byte0, static_cast<size_t>(u.byte1 - u.byte0),
+                                    cudaMemcpyHostToDevice, g.sh);
+    if (e == cudaSuccess && u.oi0 >= 0)
+      e = cudaMemcpyAsync(static_cast<uint8_t*>(sl.in) + u.oi_at(), hb + u.oi0, static_cast<size_t>(u.oi1 - u.oi0),
+                          cudaMemcpyHostToDevice, g.sh);
+    if (e != cudaSuccess || cudaEventRecord(sl.h2d, g.sh) != cudaSuccess)
       return fail(ctx, PQ_ERR_CUDA, "host-to-device copy");
     return PQ_OK;
   };
-  if (copy_in(0) != PQ_OK) return PQ_ERR_CUDA;
+  pq_status st = copy_in(0);
+  if (st != PQ_OK) return st;
   for (size_t k = 0; k < units.size(); ++k) {
     const Unit& u = units[k];
-    Slot& sl = g.slot[k % PipeGuard::kSlots];
-    if (cudaStreamWaitEvent(g.sc, sl.h2d, 0) != cudaSuccess) return fail(ctx, PQ_ERR_CUDA, "event");
-    // index of this row group: one file view whose chunk offsets land in the slot
+    Slot& sl = g.slot[k % ns];
+    if (cudaStreamWaitEvent(sl.sc, sl.h2d, 0) != cudaSuccess) return fail(ctx, PQ_ERR_CUDA, "event");
+    // index of this row group: one file view whose chunk offsets land in the
+    // slot, its OffsetIndex structures moved to the copy after the chunks
     auto ix = std::make_unique<pq_index>();
     ix->ctx = ctx;
     pq_file view;
     view.data = static_cast<uint8_t*>(sl.in) - u.byte0;
-    view.size = static_cast<uint64_t>(u.byte1);
+    view.size = static_cast<uint64_t>(u.oi0 >= 0 ? u.byte0 + u.oi_at() + (u.oi1 - u.oi0) : u.byte1);
     ix->files.push_back(view);
     pqh::FileMeta m;
     m.columns = metas[u.file].columns;
     m.rgs.push_back(metas[u.file].rgs[u.rg]);
+    if (u.oi0 >= 0)
+      for (auto& cm : m.rgs[0].chunks) cm.oi_offset = u.byte0 + u.oi_at() + (cm.oi_offset - u.oi0);
     m.num_rows = u.rows;
     m.footer_len = 0;
     ix->metas.push_back(std::move(m));
-    pq_status st = index_build(ctx, std::move(ix), false, g.sc, &g.idx);
+    st = index_build(ctx, std::move(ix), u.oi0 >= 0, sl.sc, &sl.idx);
     if (st != PQ_OK) return st;
     pq_request lr{};
     lr.columns = cols.data();
@@ -217,30 +286,33 @@ pq_status scan_pipelined(pq_ctx* ctx, const pq_file* host_files, int n_files, co
     lr.flags = req->flags & ~(PQ_SCAN_GRAPH | PQ_SCAN_TIMING);
     lr.row_begin = u.lo;
     lr.row_count = u.hi - u.lo;
-    std::vector<pq_out_size> sz(cols.size());
-    st = pq_plan_scan(ctx, g.idx, &lr, &g.plan, sz.data());
+    sl.sz.assign(cols.size(), pq_out_size{});
+    st = plan_scan_on(ctx, sl.idx, &lr, sl.sc, &sl.plan, sl.sz.data());
     if (st != PQ_OK) return st;
     for (size_t c = 0; c < cols.size(); ++c)
-      if (sz[c].chars_bytes > sl.outs[c].chars_capacity && sz[c].type == PQ_TYPE_BYTE_ARRAY)
+      if (sl.sz[c].chars_bytes > sl.outs[c].chars_capacity && sl.sz[c].type == PQ_TYPE_BYTE_ARRAY)
         return fail(ctx, PQ_ERR_CAPACITY, "row-group chars above the chunk's size statistics");
-    st = pq_scan_columns(ctx, g.plan, sl.outs.data(), g.sc);
+    st = scan_enqueue(sl.plan, sl.outs.data(), sl.sc, sl.br, nb, false);
     if (st != PQ_OK) return st;
-    if (k + 1 < units.size() && (st = copy_in(k + 1)) != PQ_OK) return st;
-    std::vector<uint64_t> chars(cols.size());
-    st = pq_scan_wait(ctx, g.plan, g.sc, chars.data());
-    if (st != PQ_OK) return st;
-    pq_free_plan(g.plan);
-    g.plan = nullptr;
-    index_release(g.idx);
-    g.idx = nullptr;
+    sl.unit = static_cast<int64_t>(k);
     const int64_t n = u.hi - u.lo;
+    // chars per string column: the planned sizes are exact for whole row
+    // groups; a partial one (the request's first or last) is waited for
+    std::vector<uint64_t> chars(cols.size());
+    for (size_t c = 0; c < cols.size(); ++c) chars[c] = sl.sz[c].type == PQ_TYPE_BYTE_ARRAY ? sl.sz[c].chars_bytes : 0;
+    if (any_ba && (u.lo != 0 || u.hi != u.rows)) {
+      st = pq_scan_wait(ctx, sl.plan, sl.sc, chars.data());
+      if (st != PQ_OK) return st;
+      for (size_t c = 0; c < cols.size(); ++c)
+        if (sl.sz[c].type == PQ_TYPE_BYTE_ARRAY) sl.sz[c].chars_bytes = chars[c];
+    }
     for (size_t c = 0; c < cols.size(); ++c)
-      if (sz[c].type == PQ_TYPE_BYTE_ARRAY)
-        pqi::launch_add_offsets(static_cast<int64_t*>(sl.outs[c].values), n + 1, chars_base[c], g.sc);
-    if (cudaEventRecord(sl.scanned, g.sc) != cudaSuccess || cudaStreamWaitEvent(g.sd, sl.scanned, 0) != cudaSuccess)
+      if (sl.sz[c].type == PQ_TYPE_BYTE_ARRAY)
+        pqi::launch_add_offsets(static_cast<int64_t*>(sl.outs[c].values), n + 1, chars_base[c], sl.sc);
+    if (cudaEventRecord(sl.scanned, sl.sc) != cudaSuccess || cudaStreamWaitEvent(g.sd, sl.scanned, 0) != cudaSuccess)
       return fail(ctx, PQ_ERR_CUDA, "event");
     for (size_t c = 0; c < cols.size(); ++c) {
-      const pq_out_size& z = sz[c];
+      const pq_out_size& z = sl.sz[c];
       uint8_t* hv = static_cast<uint8_t*>(host_outs[c].values);
       const bool ba = z.type == PQ_TYPE_BYTE_ARRAY;
       const int64_t w = ba ? 8 : pqi::type_width(z.type);
@@ -251,13 +323,17 @@ pq_status scan_pipelined(pq_ctx* ctx, const pq_file* host_files, int n_files, co
       if (e == cudaSuccess && ba && chars[c]) {
         if (static_cast<uint64_t>(chars_base[c]) + chars[c] > host_outs[c].chars_capacity)
           return fail(ctx, PQ_ERR_CAPACITY, "host chars buffer smaller than the scanned chars");
-        e = copy_out(host_outs[c].chars + chars_base[c], sl.outs[c].chars, chars[c]);
+        e = copy_out(static_cast<uint8_t*>(host_outs[c].chars) + chars_base[c], sl.outs[c].chars, chars[c]);
       }
       if (e != cudaSuccess) return fail(ctx, PQ_ERR_CUDA, "device-to-host copy");
       chars_base[c] += static_cast<int64_t>(chars[c]);
     }
     if (cudaEventRecord(sl.d2h, g.sd) != cudaSuccess) return fail(ctx, PQ_ERR_CUDA, "event");
+    if (k + 1 < units.size() && (st = copy_in(k + 1)) != PQ_OK) return st;
   }
+  // the row groups still in flight, in order
+  for (size_t k = units.size() - ns; k < units.size(); ++k)
+    if ((st = retire(g.slot[k % ns])) != PQ_OK) return st;
   if (cudaStreamSynchronize(g.sd) != cudaSuccess) return fail(ctx, PQ_ERR_CUDA, "synchronize");
   return PQ_OK;
 }

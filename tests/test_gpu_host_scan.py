@@ -95,9 +95,12 @@ def _check(sizes, keep, expect_cols, columns):
             assert np.array_equal(m[:len(words)], words), f"{e.name}: validity differs"
 
 
-@pytest.mark.parametrize("rb,rc", [(0, -1), (8192, 24576), (100, 30_001)])
+@pytest.mark.parametrize("rb,rc", [(0, -1), (8192, 24576), (100, 30_001), (32, 30_000)])
 @pytest.mark.parametrize("pipeline,pinned", [(True, False), (False, False), (True, True)])
 def test_host_scan_matches_oracle(ctx, rb, rc, pipeline, pinned, monkeypatch):
+    """(32, 30000): the pipeline with a partial first and last row group
+    (their string chars are waited for; the whole ones are planned exactly);
+    (100, 30001): row groups off the 32-row grid, the whole-file path."""
     from paper_2602_17335_gb300 import native as N
     if not pipeline:
         monkeypatch.setenv("PQ_HOST_NO_PIPELINE", "1")
@@ -108,3 +111,17 @@ def test_host_scan_matches_oracle(ctx, rb, rc, pipeline, pinned, monkeypatch):
     sizes, keep, _ = _host_scan(N, ctx, [data], columns, rb, rc, pinned)
     hi = 40_000 if rc < 0 else rb + rc
     _check(sizes, keep, [slice_result(expect[c], rb, hi) for c in columns], columns)
+
+
+@pytest.mark.parametrize("offset_index", [True, False])
+def test_host_scan_pipeline_offset_index(ctx, offset_index):
+    """The pipeline stages each row group's OffsetIndex structures after its
+    chunks (the index reads page locations from them); without them the
+    index walks the page headers.  Both give the oracle's columns."""
+    from paper_2602_17335_gb300 import native as N
+    tab = synth.config2_table(30_000, 4096, **SMALL)
+    data = W.write_file(tab, synth.config2_spec(4096, 8 * 1024, "UNCOMPRESSED", 1, offset_index=offset_index))
+    expect = R.read_file(data)
+    columns = [0, 1, 5, 6]
+    sizes, keep, _ = _host_scan(N, ctx, [data], columns, 0, -1)
+    _check(sizes, keep, [expect[c] for c in columns], columns)
