@@ -125,6 +125,34 @@ PinnedPool::~PinnedPool() {
   for (auto& kv : free_) cudaFreeHost(kv.second);
 }
 
+cudaError_t EventPool::take(cudaEvent_t* e) {
+  {
+    std::lock_guard<std::mutex> g(mu_);
+    if (!free_.empty()) {
+      *e = free_.back();
+      free_.pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+}
+
+void EventPool::give(cudaEvent_t e) {
+  if (!e) return;
+  {
+    std::lock_guard<std::mutex> g(mu_);
+    if (free_.size() < 1024) {
+      free_.push_back(e);
+      return;
+    }
+  }
+  cudaEventDestroy(e);
+}
+
+EventPool::~EventPool() {
+  for (cudaEvent_t e : free_) cudaEventDestroy(e);
+}
+
 pq_status fail(pq_ctx* ctx, pq_status s, const std::string& msg) {
   if (ctx) ctx->last_error = msg;
   return s;
@@ -750,20 +778,18 @@ static void free_plan_device(pq_plan* plan) {
 void pq_free_plan(pq_plan* plan) {
   if (!plan) return;
   cudaSetDevice(plan->ctx->device);
-  if (plan->done) {
-    cudaEventSynchronize(plan->done);
-    cudaEventDestroy(plan->done);
-  }
-  if (plan->ready) {
-    cudaEventSynchronize(plan->ready);
-    cudaEventDestroy(plan->ready);
-  }
+  // once `done` (recorded after the scan's last work) and `ready` have
+  // completed, so have the fork and join records: all go back to the cache
+  if (plan->done) cudaEventSynchronize(plan->done);
+  if (plan->ready) cudaEventSynchronize(plan->ready);
   if (plan->graph) cudaGraphExecDestroy(plan->graph);
   for (auto& e : plan->stage_ev)
     if (e) cudaEventDestroy(e);
-  if (plan->fork) cudaEventDestroy(plan->fork);
-  for (auto& e : plan->join)
-    if (e) cudaEventDestroy(e);
+  pqe::EventPool& ev = plan->ctx->events;
+  ev.give(plan->done);
+  ev.give(plan->ready);
+  ev.give(plan->fork);
+  for (auto& e : plan->join) ev.give(e);
   free_plan_device(plan);
   for (pqe::Pinned* b : {&plan->h_cols, &plan->h_out, &plan->h_up}) plan->ctx->pinned.give(b);
   delete plan;
@@ -1211,14 +1237,14 @@ pq_status plan_upload(pq_plan* plan, cudaStream_t s) {
   if (nit) pqi::launch_make_items(decode_args(plan), static_cast<int>(npp), s);
   // no host wait: a scan's stream waits on this event (the host arrays are
   // plan members, alive until the plan is freed)
-  CK(cudaEventCreateWithFlags(&plan->ready, cudaEventDisableTiming));
+  CK(ctx->events.take(&plan->ready));
   CK(cudaEventRecord(plan->ready, s));
-  CK(cudaEventCreateWithFlags(&plan->done, cudaEventDisableTiming));
+  CK(ctx->events.take(&plan->done));
   if (plan->flags & PQ_SCAN_TIMING)
     for (auto& e : plan->stage_ev) CK(cudaEventCreate(&e));
-  CK(cudaEventCreateWithFlags(&plan->fork, cudaEventDisableTiming));
+  CK(ctx->events.take(&plan->fork));
   plan->join.assign(plan->outcols.size(), nullptr);
-  for (auto& e : plan->join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  for (auto& e : plan->join) CK(ctx->events.take(&e));
   {
     // kernels per scan: prepare, snappy, dictionary (2), walk + expand or one
     // plain launch (+ its snappy) per chunk, strings (2)

@@ -57,6 +57,19 @@ class PinnedPool {
   std::multimap<size_t, uint8_t*> free_;
 };
 
+// Cache of the plans' synchronisation events (created without timing), so
+// that a repeated plan cycle creates and destroys none after warm-up.
+class EventPool {
+ public:
+  cudaError_t take(cudaEvent_t* e);
+  void give(cudaEvent_t e);  // the event's last record has completed
+  ~EventPool();
+
+ private:
+  std::mutex mu_;
+  std::vector<cudaEvent_t> free_;
+};
+
 }  // namespace pqe
 
 struct pq_ctx {
@@ -68,6 +81,7 @@ struct pq_ctx {
   pq_tuning tuning{pqi::ITEM_ROWS, pqi::ITEM_ROWS_OPT, 0, kBranches, 0, 256, 1, 0};
   pqe::DevPool pool;
   pqe::PinnedPool pinned;
+  pqe::EventPool events;
   pqe::Pinned tail;     // footer staging
   std::mutex mu;        // serialises use from the serving thread and the API
 };
