@@ -420,7 +420,8 @@ namespace pqe {
 // Index from parsed footers: `idx` holds files (device base, size) and
 // metas; chunks at base + chunk offset.  allow_oi: page locations may be
 // read from OffsetIndex structures on the device.
-pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi, cudaStream_t s, pq_index** out) {
+pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi, cudaStream_t s, pq_index** out,
+                      const std::vector<pqi::PageDev>* host_pages) {
   const int n_files = static_cast<int>(idx->files.size());
   const pq_file* files = idx->files.data();
   // 2. schema
@@ -529,7 +530,34 @@ pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi,
   CK(cudaMemcpyAsync(idx->d_chunk_file_off, up.put(idx->chunk_file_off.data(), sizeof(int64_t) * nch),
                      sizeof(int64_t) * nch, cudaMemcpyHostToDevice, s));
   int64_t n_pages = 0;
-  if (all_oi && nch > 0) {
+  Stage up_pages{ctx, s, {}};
+  if (host_pages) {
+    // 4. the caller's page table (chunk order), walked on the host
+    std::vector<uint32_t> count(static_cast<size_t>(std::max(nch, 0)), 0);
+    uint32_t prev = 0;
+    for (const auto& pg : *host_pages) {
+      if (static_cast<int64_t>(pg.chunk) >= nch || pg.chunk < prev) {
+        free_index_device(idx.get());
+        return fail(ctx, PQ_ERR_INVALID_ARG, "host page table out of chunk order");
+      }
+      prev = pg.chunk;
+      ++count[pg.chunk];
+    }
+    for (int c = 0; c < nch; ++c) {
+      idx->chunks[c].page_begin = static_cast<uint32_t>(n_pages);
+      idx->chunks[c].page_count = count[c];
+      n_pages += count[c];
+    }
+    const size_t bytes = sizeof(pqi::PageDev) * static_cast<size_t>(n_pages);
+    idx->d_pages = static_cast<pqi::PageDev*>(pool.alloc(std::max<size_t>(bytes, sizeof(pqi::PageDev))));
+    if (!idx->d_pages || !ctx->pinned.take(bytes + 16, &up_pages.b)) {
+      free_index_device(idx.get());
+      return fail(ctx, PQ_ERR_OOM, "page table");
+    }
+    if (bytes)
+      CK(cudaMemcpyAsync(idx->d_pages, up_pages.put(host_pages->data(), bytes), bytes, cudaMemcpyHostToDevice, s));
+    idx->pages = *host_pages;
+  } else if (all_oi && nch > 0) {
     // 4a. OffsetIndex: page counts from the list headers (the first 16 bytes
     // of every chunk's OffsetIndex, fetched in one round trip into the
     // footer staging, which is free again), then one thread per page
@@ -637,23 +665,25 @@ pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi,
     CK(upload_chunks());
     pqi::launch_index_walk(idx->d_chunks, nch, idx->d_pages, nullptr, 1, idx->d_status, s);
   }
-  // 5. page table back to the host
-  idx->pages.resize(n_pages);
-  pqi::DevStatus st{};
-  if (!ctx->tail.reserve(sizeof st + sizeof(pqi::PageDev) * n_pages)) {
-    free_index_device(idx.get());
-    return fail(ctx, PQ_ERR_OOM, "pinned staging");
-  }
-  CK(d2h_small(ctx->tail.p, idx->d_status, sizeof st, s));
-  CK(d2h_small(ctx->tail.p + sizeof st, idx->d_pages, sizeof(pqi::PageDev) * n_pages, s));
-  CK(cudaStreamSynchronize(s));
-  CK(cudaGetLastError());
-  memcpy(&st, ctx->tail.p, sizeof st);
-  if (n_pages) memcpy(idx->pages.data(), ctx->tail.p + sizeof st, sizeof(pqi::PageDev) * n_pages);
-  if (st.flags) {
-    pq_status r = status_from_device(ctx, st);
-    free_index_device(idx.get());
-    return r;
+  // 5. page table back to the host (built on the device)
+  if (!host_pages) {
+    idx->pages.resize(n_pages);
+    pqi::DevStatus st{};
+    if (!ctx->tail.reserve(sizeof st + sizeof(pqi::PageDev) * n_pages)) {
+      free_index_device(idx.get());
+      return fail(ctx, PQ_ERR_OOM, "pinned staging");
+    }
+    CK(d2h_small(ctx->tail.p, idx->d_status, sizeof st, s));
+    CK(d2h_small(ctx->tail.p + sizeof st, idx->d_pages, sizeof(pqi::PageDev) * n_pages, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    memcpy(&st, ctx->tail.p, sizeof st);
+    if (n_pages) memcpy(idx->pages.data(), ctx->tail.p + sizeof st, sizeof(pqi::PageDev) * n_pages);
+    if (st.flags) {
+      pq_status r = status_from_device(ctx, st);
+      free_index_device(idx.get());
+      return r;
+    }
   }
   // 6. host checks, dictionary buffers
   idx->dict_values.assign(nch, nullptr);

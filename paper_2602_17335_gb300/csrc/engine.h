@@ -245,7 +245,10 @@ uint64_t plan_device_bytes(const pq_plan* plan, uint64_t scratch);
 pq_status scan_enqueue(pq_plan* plan, const pq_column* outs, cudaStream_t s, const cudaStream_t* branches,
                        int n_branches, bool allow_graph);
 pq_status status_from_device(pq_ctx* ctx, const pqi::DevStatus& st);
-pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi, cudaStream_t s, pq_index** out);
+// host_pages: a page table the caller built on the host (chunk order), used
+// instead of the device walk and its readback
+pq_status index_build(pq_ctx* ctx, std::unique_ptr<pq_index> idx, bool allow_oi, cudaStream_t s, pq_index** out,
+                      const std::vector<pqi::PageDev>* host_pages = nullptr);
 void index_release(pq_index* idx);
 pq_status cuda_fail(pq_ctx* ctx, cudaError_t e, const char* what);
 pqi::DecodeArgs decode_args(pq_plan* plan);

@@ -10,10 +10,11 @@
 // scans of consecutive row groups also overlap one another; the host waits
 // for a row group only when its slot comes round again, three row groups
 // later, so that the copy-out (the host link's slower direction) always has
-// row groups queued while slow scans (Snappy pages) are still running.  Each slot also
-// receives the row group's OffsetIndex structures (which the file keeps
-// after its last row group), so that the index reads page locations from
-// them.  Footers are parsed straight from host memory.
+// row groups queued while slow scans (Snappy pages) are still running.
+// Footers are parsed and each row group's page table is walked straight
+// from host memory (host_page_walk): the device indexes nothing and reads
+// nothing back, so no row group waits for SMs held by an earlier one's
+// scan or for a page-table readback queued behind the copy-out.
 #include <stdlib.h>
 #include <string.h>
 
@@ -22,6 +23,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "host_pages.h"
 
 using namespace pqe;
 
@@ -30,12 +32,9 @@ namespace {
 struct Unit {
   int file, rg;
   int64_t byte0, byte1;  // staged file bytes
-  int64_t oi0, oi1;      // the row group's OffsetIndex bytes (oi0 < 0: not staged)
   int64_t row0, rows;    // global first row and rows of the row group
   int64_t lo, hi;        // requested rows inside it (row-group relative)
   int64_t out0;          // first output row
-  // slot offset of the OffsetIndex copy, after the chunk bytes
-  int64_t oi_at() const { return (byte1 - byte0 + 15) & ~int64_t(15); }
 };
 
 // A device slot and the row group in flight in it.
@@ -154,19 +153,6 @@ pq_status scan_pipelined(pq_ctx* ctx, const pq_file* host_files, int n_files, co
       b1 = std::min<int64_t>(b1 + 64, static_cast<int64_t>(host_files[f].size));
       u.byte0 = b0;
       u.byte1 = b1;
-      // the OffsetIndex bytes of all the row group's chunks (one range)
-      int64_t o0 = INT64_MAX, o1 = 0;
-      for (const auto& cm : rg.chunks) {
-        if (cm.oi_offset < 4 || cm.oi_length <= 0) {
-          o0 = -1;
-          break;
-        }
-        o0 = std::min(o0, cm.oi_offset);
-        o1 = std::max(o1, cm.oi_offset + static_cast<int64_t>(cm.oi_length));
-      }
-      const bool oi = o0 >= 0 && o1 <= static_cast<int64_t>(host_files[f].size) && o1 - o0 <= (int64_t(64) << 20);
-      u.oi0 = oi ? o0 : -1;
-      u.oi1 = oi ? o1 : -1;
       if (u.out0 % 32) return PQ_ERR_UNSUPPORTED;  // validity words must not straddle units
       units.push_back(u);
     }
@@ -177,7 +163,7 @@ pq_status scan_pipelined(pq_ctx* ctx, const pq_file* host_files, int n_files, co
   std::vector<int64_t> max_chars(cols.size(), 0);
   std::vector<int64_t> chars_base(cols.size(), 0);
   for (const auto& u : units) {
-    max_bytes = std::max(max_bytes, u.oi_at() + (u.oi0 >= 0 ? u.oi1 - u.oi0 : 0));
+    max_bytes = std::max(max_bytes, u.byte1 - u.byte0);
     max_rows = std::max(max_rows, u.hi - u.lo);
     const auto& rg = metas[u.file].rgs[u.rg];
     for (size_t c = 0; c < cols.size(); ++c)
@@ -247,11 +233,8 @@ pq_status scan_pipelined(pq_ctx* ctx, const pq_file* host_files, int n_files, co
     const pq_status st = retire(sl);
     if (st != PQ_OK) return st;
     const uint8_t* hb = static_cast<const uint8_t*>(host_files[u.file].data);
-    cudaError_t e = cudaMemcpyAsync(sl.in, hb + u.byte0, static_cast<size_t>(u.byte1 - u.byte0),
-                                    cudaMemcpyHostToDevice, g.sh);
-    if (e == cudaSuccess && u.oi0 >= 0)
-      e = cudaMemcpyAsync(static_cast<uint8_t*>(sl.in) + u.oi_at(), hb + u.oi0, static_cast<size_t>(u.oi1 - u.oi0),
-                          cudaMemcpyHostToDevice, g.sh);
+    const cudaError_t e = cudaMemcpyAsync(sl.in, hb + u.byte0, static_cast<size_t>(u.byte1 - u.byte0),
+                                          cudaMemcpyHostToDevice, g.sh);
     if (e != cudaSuccess || cudaEventRecord(sl.h2d, g.sh) != cudaSuccess)
       return fail(ctx, PQ_ERR_CUDA, "host-to-device copy");
     return PQ_OK;
@@ -263,22 +246,34 @@ pq_status scan_pipelined(pq_ctx* ctx, const pq_file* host_files, int n_files, co
     Slot& sl = g.slot[k % ns];
     if (cudaStreamWaitEvent(sl.sc, sl.h2d, 0) != cudaSuccess) return fail(ctx, PQ_ERR_CUDA, "event");
     // index of this row group: one file view whose chunk offsets land in the
-    // slot, its OffsetIndex structures moved to the copy after the chunks
+    // slot, and the page table walked from the host's copy of the chunks
+    const auto& rgm = metas[u.file].rgs[u.rg];
+    const uint8_t* hb = static_cast<const uint8_t*>(host_files[u.file].data);
+    std::vector<pqi::PageDev> pages;
+    for (size_t c = 0; c < rgm.chunks.size(); ++c) {
+      const auto& cm = rgm.chunks[c];
+      if (cm.start() < 4 || cm.total_compressed < 0 ||
+          static_cast<uint64_t>(cm.start()) + static_cast<uint64_t>(cm.total_compressed) > host_files[u.file].size)
+        return fail(ctx, PQ_ERR_CORRUPT, "chunk byte range outside the file");
+      std::string err;
+      if (!host_page_walk(hb + cm.start(), static_cast<uint64_t>(cm.total_compressed), cm.num_values,
+                          static_cast<uint32_t>(c), &pages, &err))
+        return fail(ctx, PQ_ERR_CORRUPT, "row group " + std::to_string(u.rg) + ", column " + std::to_string(c) +
+                                             ": " + err);
+    }
     auto ix = std::make_unique<pq_index>();
     ix->ctx = ctx;
     pq_file view;
     view.data = static_cast<uint8_t*>(sl.in) - u.byte0;
-    view.size = static_cast<uint64_t>(u.oi0 >= 0 ? u.byte0 + u.oi_at() + (u.oi1 - u.oi0) : u.byte1);
+    view.size = static_cast<uint64_t>(u.byte1);
     ix->files.push_back(view);
     pqh::FileMeta m;
     m.columns = metas[u.file].columns;
-    m.rgs.push_back(metas[u.file].rgs[u.rg]);
-    if (u.oi0 >= 0)
-      for (auto& cm : m.rgs[0].chunks) cm.oi_offset = u.byte0 + u.oi_at() + (cm.oi_offset - u.oi0);
+    m.rgs.push_back(rgm);
     m.num_rows = u.rows;
     m.footer_len = 0;
     ix->metas.push_back(std::move(m));
-    st = index_build(ctx, std::move(ix), u.oi0 >= 0, sl.sc, &sl.idx);
+    st = index_build(ctx, std::move(ix), false, sl.sc, &sl.idx, &pages);
     if (st != PQ_OK) return st;
     pq_request lr{};
     lr.columns = cols.data();

@@ -115,9 +115,9 @@ def test_host_scan_matches_oracle(ctx, rb, rc, pipeline, pinned, monkeypatch):
 
 @pytest.mark.parametrize("offset_index", [True, False])
 def test_host_scan_pipeline_offset_index(ctx, offset_index):
-    """The pipeline stages each row group's OffsetIndex structures after its
-    chunks (the index reads page locations from them); without them the
-    index walks the page headers.  Both give the oracle's columns."""
+    """The pipeline walks each row group's page headers on the host, with or
+    without OffsetIndex structures in the file (which it does not read);
+    both give the oracle's columns."""
     from paper_2602_17335_gb300 import native as N
     tab = synth.config2_table(30_000, 4096, **SMALL)
     data = W.write_file(tab, synth.config2_spec(4096, 8 * 1024, "UNCOMPRESSED", 1, offset_index=offset_index))
