@@ -14,7 +14,9 @@
 // Footers are parsed and each row group's page table is walked straight
 // from host memory (host_page_walk): the device indexes nothing and reads
 // nothing back, so no row group waits for SMs held by an earlier one's
-// scan or for a page-table readback queued behind the copy-out.
+// scan or for a page-table readback queued behind the copy-out.  Files
+// with compressed pages of 512 KiB or more take the whole-file path (their
+// scans are latency-bound; see scan_pipelined).
 #include <stdlib.h>
 #include <string.h>
 
@@ -158,6 +160,27 @@ pq_status scan_pipelined(pq_ctx* ctx, const pq_file* host_files, int n_files, co
     }
   }
   if (units.size() < 2) return PQ_ERR_UNSUPPORTED;
+  {
+    // Compressed pages of kLongPage or more: one row group's scan then takes
+    // as long as its longest page's element chain (about 17 ms at 1 MiB
+    // Snappy pages), which the pipeline would pay per row group and the
+    // whole-file path pays once; the first row group's pages decide.
+    constexpr int32_t kLongPage = 512 * 1024;
+    const Unit& u = units[0];
+    const uint8_t* hb = static_cast<const uint8_t*>(host_files[u.file].data);
+    for (const auto& cm : metas[u.file].rgs[u.rg].chunks) {
+      if (cm.codec == pqi::CODEC_NONE || cm.start() < 4 || cm.total_compressed < 0 ||
+          static_cast<uint64_t>(cm.start()) + static_cast<uint64_t>(cm.total_compressed) > host_files[u.file].size)
+        continue;
+      std::vector<pqi::PageDev> pages;
+      std::string err;
+      if (!host_page_walk(hb + cm.start(), static_cast<uint64_t>(cm.total_compressed), cm.num_values, 0, &pages,
+                          &err))
+        continue;  // the per-row-group walk reports it
+      for (const auto& pg : pages)
+        if (pg.page_type != pqi::PAGE_DICT && pg.uncompressed >= kLongPage) return PQ_ERR_UNSUPPORTED;
+    }
+  }
   // capacities (the largest unit) per column
   int64_t max_bytes = 0, max_rows = 0;
   std::vector<int64_t> max_chars(cols.size(), 0);
