@@ -283,7 +283,14 @@ pq_status pq_scan_wait(pq_ctx* ctx, pq_plan* plan, void* stream, uint64_t* chars
  * planned and scanned, and the columns copied back; the call is
  * synchronous.  When `host_outs` is NULL only `sizes` is filled (one entry
  * per requested column), so that the caller can allocate the outputs.
- * `req` as for pq_plan_scan.  Errors as for index/plan/scan. */
+ * `req` as for pq_plan_scan.  Errors as for index/plan/scan.
+ * Row groups go through the overlapped reading of the paper's Section 4 (a
+ * pipeline of device slots: copy-in, decode and copy-out of different row
+ * groups at once, page tables walked on the host) when the request spans
+ * several row groups whose first output rows are multiples of 32 and the
+ * first row group has no compressed page of 512 KiB or more; otherwise the
+ * whole file is copied in, scanned and copied out in turn.  The environment
+ * variable PQ_HOST_NO_PIPELINE=1 forces the latter. */
 pq_status pq_scan_host(pq_ctx* ctx, const pq_file* host_files, int n_files, const pq_request* req,
                        const pq_column* host_outs, pq_out_size* sizes);
 
