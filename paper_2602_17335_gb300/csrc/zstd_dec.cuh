@@ -364,7 +364,13 @@ PQ_HD inline int z_literals(const uint8_t* p, uint32_t len, ZState* z, uint8_t* 
     *nlit = regen;
     if (type == 0) {
       if (hlen + regen > len) return ZE_LIT;
-      for (uint32_t i = 0; i < regen; ++i) dst[*lit0 + i] = p[hlen + i];
+      uint32_t i = 0;
+      for (; i + 16 <= regen; i += 16) {  // 16 loads in flight, then the stores
+        uint8_t t[16];
+        for (int k = 0; k < 16; ++k) t[k] = p[hlen + i + k];
+        for (int k = 0; k < 16; ++k) dst[*lit0 + i + k] = t[k];
+      }
+      for (; i < regen; ++i) dst[*lit0 + i] = p[hlen + i];
       *used = hlen + regen;
     } else {
       if (hlen + 1 > len) return ZE_LIT;
@@ -560,18 +566,36 @@ PQ_HD inline int z_seq_next(ZState* z, ZSeqState* s, uint32_t* ll_out, uint32_t*
   return ZE_OK;
 }
 
+// dst[d, d + n) = dst[s, s + n), with the result of a byte-by-byte forward
+// copy.  When the source lies ahead of the destination, or at least 16
+// bytes behind it, no byte of a 16-byte step is written before it is read,
+// so each step loads its 16 bytes before storing them: one thread keeps 16
+// loads in flight instead of one (the output was just written and is read
+// back from L2).  A nearer source (an overlapping match) goes byte by byte.
+PQ_HD inline void z_copy(uint8_t* dst, uint64_t d, uint64_t s, uint32_t n) {
+  uint32_t k = 0;
+  if (s > d || d - s >= 16) {
+    for (; k + 16 <= n; k += 16) {
+      uint8_t t[16];
+      for (int i = 0; i < 16; ++i) t[i] = dst[s + k + i];
+      for (int i = 0; i < 16; ++i) dst[d + k + i] = t[i];
+    }
+  }
+  for (; k < n; ++k) dst[d + k] = dst[s + k];
+}
+
 // One sequence into dst: ll literals from the block's literals at *r (which
-// end at lit_end), then ml bytes from `off` back (byte by byte: a match may
-// overlap its own output).  The frame's output starts at out0.
+// end at lit_end, ahead of the output), then ml bytes from `off` back (a
+// match may overlap its own output).  The frame's output starts at out0.
 PQ_HD inline int z_exec(uint8_t* dst, uint64_t* w, uint64_t* r, uint64_t lit_end, uint64_t out0, uint32_t ll,
                         uint32_t off, uint32_t ml) {
   if (*r + ll > lit_end) return ZE_SEQ;
-  for (uint32_t k = 0; k < ll; ++k) dst[*w + k] = dst[*r + k];
+  z_copy(dst, *w, *r, ll);
   *w += ll;
   *r += ll;
   if (off == 0 || off > *w - out0) return ZE_OFFSET;
   if (*w + ml > *r) return ZE_SIZE;  // the output would run into unread literals: the page is too small
-  for (uint32_t k = 0; k < ml; ++k) dst[*w + k] = dst[*w - off + k];
+  z_copy(dst, *w, *w - off, ml);
   *w += ml;
   return ZE_OK;
 }
@@ -593,7 +617,8 @@ PQ_HD inline int z_sequences(const uint8_t* p, uint32_t len, ZState* z, uint8_t*
     if (e) return e;
   }
   if (s.nseq && s.b.pos != 0) return ZE_STREAM;
-  for (; r < lit_end; ++r, ++w) dst[w] = dst[r];
+  z_copy(dst, w, r, static_cast<uint32_t>(lit_end - r));
+  w += lit_end - r;
   *out_pos = w;
   return ZE_OK;
 }
